@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Benchmark: sparsifying-preconditioned GMRES solves per second on one GB300.
+
+Workload (one "step"): the 2D 512^2 problem pair, complex128 unknowns, b = 16,
+  (a) Helmholtz, omega = 2 pi 64, c = 1 + 0.3 tanh(GRF, correlation length 0.05),
+  (b) rescaled Schroedinger, l = 16, E = 10, 16 x 16 lattice of Gaussian wells
+      (depth U[5, 15], width 0.15 l-units),
+each with a random-centre, random-phase Gaussian source; for each problem the
+step factors P = Q + C q (sp_factor) and solves to a true relative residual of
+1e-8 (sp_solve).  One step = 2 solves.  The stencil set-up (sp_setup, once per
+shift s) is outside the timed region.  `value` is the plain FP64 form; the FP32
+preconditioner form (FP32 factor and sweeps, FP64 operator, Gram-Schmidt and
+residuals) is reported beside it under "chosen_form".
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on
+the library's stream, with an L2 flush (a 256 MB write) between steps outside
+the events; barrier + synchronize around the timed loop; max over ranks.  N > 1
+runs independent replicas (one per GPU, no collective on the data path).
+
+--impl reference times the FP64 CPU oracle (numpy/scipy) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synthetic_media as sm  # noqa: E402
+
+METRIC = "solves/s at rel. residual 1e-8 (2D 512^2), plain FP64 GPU"
+UNIT = "solves/s"
+WORKLOAD = "2D 512^2 pair: Helmholtz GRF omega=2pi*64 + Schroedinger wells l=16 E=10, b=16"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-chosen", action="store_true")
+    return p.parse_args()
+
+
+def problems():
+    """Host inputs of the two problems: (name, d, n, b, kind params, f)."""
+    return [sm.helmholtz_grf_512(0), sm.schrodinger_wells_512(0)]
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", "-i", str(self.device),
+               "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+               "--format=csv,noheader,nounits", "-lms", "200"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm_, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm_.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm_)) if sm_ else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm_)}
+
+
+# ------------------------------------------------------------------ oracle (reference arm / cpu_baseline)
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = os.cpu_count()
+    res = cpu_baseline()
+    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 2000.0 / res["value"] if res["value"] else None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": res["value"], "unit": UNIT, "cores": cores,
+                             "kind": "oracle", "sample": res["sample"]},
+            "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline() -> dict:
+    """Bounded oracle sample (see the returned 'sample' text)."""
+    import oracle as O
+    import scipy.sparse.linalg as spla
+    w = sm.helmholtz_grf(2, 128, 8, 2 * np.pi * 16, 0.05, 0)
+    d, n, b = w["d"], w["n"], w["b"]
+    s, q = O.helmholtz_shift(d, n, w["omega"], w["c"])
+    tabs = O.stencil_tables(d, n, b, s)
+    t0 = time.perf_counter()
+    M = O.SparsifyingPreconditioner(d, n, b, s, q, tables=tabs, factor="splu")
+    g = O.apply_green(d, n, s, w["f"])
+    res = O.gmres_right(lambda x: O.apply_operator(d, n, s, q, x), M.apply, g, tol=1e-8)
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt,
+            "sample": f"one oracle factor+solve of the same Helmholtz GRF family at 128^2 "
+                      f"(b=8, omega=2pi*16, 8 points/wavelength like 512^2), {res['iters']} "
+                      f"iterations, {dt:.1f} s; the 512^2 oracle factor does not fit the budget",
+            "seconds": dt}
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+
+    from paper_1409_0297_gb300 import binding as B
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    probs = []
+    for w in problems():
+        d, n, b = w["d"], w["n"], w["b"]
+        if w["kind"] == "helmholtz":
+            s, q = B.sp_medium_helmholtz(d, n, w["omega"], w["c"])
+            f = w["f"]
+        else:
+            s, q = B.sp_medium_schrodinger(d, n, w["ell"], w["E"], w["V"])
+            f = w["f"] * w["ell"] ** 2
+        probs.append(dict(d=d, n=n, b=b, s=s, q=q, f=np.ascontiguousarray(f)))
+    N = probs[0]["n"] ** probs[0]["d"]
+
+    def make(prec):
+        out = []
+        for p in probs:
+            S = B.Solver(p["d"], p["n"], p["b"], p["s"], prec=prec, device=local)
+            out.append(dict(S=S, q=torch.from_numpy(p["q"]).cuda(),
+                            f=torch.from_numpy(p["f"]).cuda(),
+                            u=torch.empty(N, dtype=torch.complex128, device="cuda")))
+        return out
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step(ctxs, infos=None):
+        for c in ctxs:
+            c["S"].factor(c["q"])
+            info = c["S"].solve(c["f"], c["u"])
+            if infos is not None:
+                infos.append(info)
+
+    def timed(ctxs, K, W):
+        for _ in range(W):
+            step(ctxs)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        evs = []
+        infos = []
+        t0 = time.perf_counter()
+        for _ in range(K):
+            flush.zero_()
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            step(ctxs, infos)
+            e.record()
+            evs.append((a, e))
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        wall = time.perf_counter() - t0
+        ms = sum(a.elapsed_time(e) for a, e in evs)
+        if dist:
+            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms / K, wall, infos
+
+    fp64 = make(B.SP_PREC_FP64)
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms64, wall64, infos64 = timed(fp64, args.steps, args.warmup)
+    clocks = sampler.stop()
+    solves_per_step = len(probs)
+    value = solves_per_step * world / (ms64 / 1e3)
+
+    # e2e through the host-buffer entry points (pinned host memory)
+    pin_q = [torch.from_numpy(p["q"]).pin_memory() for p in probs]
+    pin_f = [torch.from_numpy(p["f"]).pin_memory() for p in probs]
+    pin_u = [torch.empty(N, dtype=torch.complex128).pin_memory() for _ in probs]
+    import ctypes
+    info_c = B.sp_info()
+
+    def step_host():
+        for c, q, f, u in zip(fp64, pin_q, pin_f, pin_u):
+            B._check(B.LIB.sp_factor_host(c["S"].ctx, ctypes.c_void_p(q.data_ptr())), "sp_factor_host")
+            B._check(B.LIB.sp_solve_host(c["S"].ctx, ctypes.c_void_p(f.data_ptr()),
+                                         ctypes.c_void_p(u.data_ptr()), ctypes.byref(info_c)),
+                     "sp_solve_host")
+    step_host()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_host()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_value = solves_per_step * world / e2e_s
+
+    # one profiled step: kernel classes, launch counts, roofline of the dominant class
+    for c in fp64:
+        B.sp_profile(c["S"].ctx, True)
+    step(fp64)
+    prof = {}
+    for c in fp64:
+        for k, (ms_, nl, wk) in B.sp_profile_read(c["S"].ctx).items():
+            a = prof.setdefault(k, [0.0, 0, 0.0])
+            a[0] += ms_
+            a[1] += nl
+            a[2] += wk
+        B.sp_profile(c["S"].ctx, False)
+    launches_per_step = sum(v[1] for v in prof.values())
+    dom = max(prof, key=lambda k: prof[k][0])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    fp64_peak_tflops = 1.25  # nominal GB300 FP64 rate (no FP64 entry in the measured peaks)
+    alu_classes = {"lu_panel", "lu_trsm", "lu_gemm"}
+
+    def roof(k, vals):
+        ms_, nl, wk = vals
+        if k in alu_classes:
+            ach = wk / (ms_ / 1e3) / 1e12
+            return {"kernel": k, "bound": "alu", "achieved": ach, "peak": fp64_peak_tflops,
+                    "unit": "TFLOP/s", "frac": ach / fp64_peak_tflops, "traffic": None,
+                    "peak_source": "nominal FP64 1.25 TFLOP/s"}
+        ach = wk / (ms_ / 1e3) / 1e9
+        return {"kernel": k, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None, "peak_source": "measured hbm_gbs"}
+
+    roofline = roof(dom, prof[dom])
+    breakdown = {k: {"ms": round(v[0], 3), "launches": v[1],
+                     "achieved": round((v[2] / (v[0] / 1e3)) / (1e12 if k in alu_classes else 1e9), 3)
+                     if v[0] > 0 else None,
+                     "unit": "TFLOP/s" if k in alu_classes else "GB/s"} for k, v in prof.items()}
+
+    chosen = None
+    if not args.no_chosen:
+        fp32 = make(B.SP_PREC_FP32)
+        ms32, _, infos32 = timed(fp32, args.steps, args.warmup)
+        chosen = {"form": "fp32 preconditioner (factor+sweeps), fp64 operator/GMRES",
+                  "value": solves_per_step * world / (ms32 / 1e3), "ms_per_step": ms32,
+                  "speedup_vs_fp64": ms64 / ms32,
+                  "iters": [i["iters"] for i in infos32[:solves_per_step]],
+                  "true_relres": [i["true_relres"] for i in infos32[:solves_per_step]]}
+        for c in fp32:
+            c["S"].close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = cpu_baseline()
+        cpu = {"value": r["value"], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": r["sample"]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": "512^2", "b": 16, "solves_per_step": 2,
+                       "tol": 1e-8, "l2": "flushed between steps (256 MB write)",
+                       "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "iters": [i["iters"] for i in infos64[:solves_per_step]],
+            "true_relres": [i["true_relres"] for i in infos64[:solves_per_step]],
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(sum(p["q"].nbytes + p["f"].nbytes for p in probs)),
+                    "d2h_bytes_per_step": int(len(probs) * N * 16)},
+            "gpu_launches": int(launches_per_step * args.steps),
+            "roofline": roofline, "kernel_breakdown_ms_per_step": breakdown,
+            "chosen_form": chosen, "clocks": clocks, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    for c in fp64:
+        c["S"].close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

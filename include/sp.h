@@ -1,0 +1,193 @@
+/*
+ * sp.h -- C ABI of the GB300 sparsifying-preconditioner solver.
+ *
+ * The library solves the pseudospectral system of the periodic problem
+ *     (-Laplace - s + q(x)) u = f   on the unit torus [0,1)^d, d = 2 or 3,
+ * (Eq. Dsq / Eq. Lsq of Ying, "Sparsifying preconditioner for pseudospectral
+ * approximations of indefinite systems on periodic structures", Section 2.1)
+ * through its integral form (I + G q) u = G f with G = (L - s)^{-1} (Eq. G,
+ * Section 2.2), preconditioned by u <= P^{-1} Q g where Q is the sparsifying
+ * stencil, C = Q G truncated to the stencil and P = Q + C q (Section 2.2-2.3).
+ * P is factored by periodic nested dissection with a multifrontal LU
+ * (Section 2.3, Fig. nd); the outer iteration is GMRES.
+ *
+ * Conventions for every call below.
+ *  - Grid: n points per axis, N = n^d unknowns, flat index j0 + n*j1 (+ n^2*j2)
+ *    (axis 0 fastest).  The leaf box size b must divide n with n/b = 2^L, L >= 1,
+ *    and b >= 2.
+ *  - Vectors (r, z, f, u, g, x, w, y) are complex128: N pairs (re, im) of
+ *    double, interleaved, 16-byte aligned.  q is N real doubles.  Pointers named
+ *    *_dev are CUDA device pointers on the context's device; *_host are host
+ *    pointers (pinned memory gives the fastest copies).  The caller owns every
+ *    buffer it passes; the context owns its tables, factor and workspace.
+ *  - Every call is ordered on the stream given to sp_setup.  Calls that return a
+ *    scalar to the host (sp_solve, sp_factor's status check) synchronise that
+ *    stream.  A context is not thread-safe.
+ *  - No call aborts or throws across the ABI: errors come back as sp_status.
+ *    After SP_ERR_CUDA the context should be destroyed.
+ */
+#ifndef SP_GB300_H
+#define SP_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sp_ctx sp_ctx; /* opaque */
+
+typedef enum {
+  SP_OK = 0,
+  SP_ERR_ARG = 1,       /* invalid argument (sizes, null pointers, n/b not 2^L) */
+  SP_ERR_RESONANT = 2,  /* L - s is (numerically) singular: s hits 4 pi^2 |k|^2 */
+  SP_ERR_SINGULAR = 3,  /* a pivot of a front fell below pivot_tol * max|front| */
+  SP_ERR_NOCONV = 4,    /* GMRES stopped at maxit above tol (the iterate is still returned) */
+  SP_ERR_OOM = 5,       /* device or host allocation failed */
+  SP_ERR_TIMEOUT = 6,   /* reserved for bounded device waits */
+  SP_ERR_CUDA = 7,      /* a CUDA runtime call failed */
+  SP_ERR_STATE = 8      /* call out of order (e.g. sp_apply before sp_factor) */
+} sp_status;
+
+typedef enum {
+  SP_PREC_FP64 = 0, /* factor, sweeps, FFTs and Krylov all in FP64 */
+  SP_PREC_FP32 = 1  /* factor and sweeps of P in FP32 (preconditioner only);
+                       FFT operator, Gram-Schmidt and residuals stay FP64 */
+} sp_precision;
+
+typedef struct {
+  int maxit;         /* total GMRES iterations allowed (default 500) */
+  int restart;       /* Krylov vectors kept before a restart (default 200) */
+  double tol;        /* target relative residual ||g - A u|| / ||g|| (default 1e-8) */
+  double pivot_tol;  /* singular-front threshold, relative to max|front| (default 1e-14) */
+  int device;        /* CUDA device ordinal the context lives on (default 0) */
+  int host_threads;  /* threads for the host set-up (0 = all hardware threads) */
+} sp_opts;
+
+typedef struct {
+  int iters;           /* GMRES iterations (matvecs with the preconditioned operator) */
+  int restarts;        /* restart cycles beyond the first */
+  double est_relres;   /* last Givens estimate |gamma_{k+1}| / ||g|| */
+  double true_relres;  /* ||g - (I + G q) u|| / ||g|| computed explicitly in FP64 */
+  double s_used;       /* the shift s of the context */
+  double *hist;        /* optional caller buffer for the estimate per iteration */
+  int hist_cap;        /* its capacity (entries) */
+  int hist_len;        /* entries written (iters + 1, capped) */
+} sp_info;
+
+/* Fill *o with the defaults listed above. */
+void sp_default_opts(sp_opts *o);
+
+/* Build a context for grid (d, n), leaf size b and shift s (Section 2.2-2.3):
+ * the Fourier symbol 1/(4 pi^2 |k|^2 - s) of G (Eq. G), the stencil tables
+ * T_S = G(S, gamma^c) G(beta, gamma^c)^+, Q(S, gamma) = [I, -T_S] and
+ * C(S, gamma) = Q(S, gamma) G(gamma, gamma) for every cell/face/edge/vertex type
+ * (Section 2.3), the nested-dissection symbolic structure (Fig. nd) and all
+ * device memory.  The pseudoinverse drops singular values at or below
+ * max(size) * eps(sigma_max).  opts may be NULL (defaults); stream is a
+ * cudaStream_t or NULL for the legacy default stream.  Returns
+ * SP_ERR_RESONANT when min_k |s/(4 pi^2) - |k|^2| < 1e-6 max(1, s/(4 pi^2)). */
+sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_opts *opts,
+                   void *stream, sp_ctx **out);
+
+/* Assemble P = Q + C diag(q) into the fronts and factor it (Section 2.2, Fig. nd):
+ * per level, leaves to root, extend-add of the children's Schur complements,
+ * partial-pivot LU of the eliminated block, panels and Schur update.  q_dev: N
+ * real doubles on the device (kept by reference until the next sp_factor: the
+ * operator I + G q of sp_solve/sp_matvec reads it).  Returns SP_ERR_SINGULAR if a
+ * pivot is below pivot_tol * max|front| (the factor is then unusable). */
+sp_status sp_factor(sp_ctx *ctx, const double *q_dev);
+
+/* z = P^{-1} Q r, the preconditioner of Section 2.2 ("u <= P^{-1} Q g"):
+ * stencil apply, forward sweep leaves to root, backward sweep root to leaves.
+ * r_dev, z_dev: N complex128 on the device, must not alias. */
+sp_status sp_apply(sp_ctx *ctx, const void *r_dev, void *z_dev);
+
+/* Solve (I + G q) u = G f by GMRES right-preconditioned with P^{-1} Q
+ * (Section 2.2; GMRES of Saad and Schultz), zero initial guess, classical
+ * Gram-Schmidt twice, stopping when the estimate is <= tol, then an explicit
+ * FP64 true residual; restarts from u if that is still above tol.  f_dev, u_dev:
+ * N complex128 on the device.  info may be NULL.  Returns SP_ERR_NOCONV when
+ * maxit is reached above tol. */
+sp_status sp_solve(sp_ctx *ctx, const void *f_dev, void *u_dev, sp_info *info);
+
+/* Host-buffer forms of sp_factor and sp_solve: the same work with the input
+ * copied host->device and the result device->host inside the call. */
+sp_status sp_factor_host(sp_ctx *ctx, const double *q_host);
+sp_status sp_solve_host(sp_ctx *ctx, const void *f_host, void *u_host, sp_info *info);
+
+/* w = x + G (q x), the integral operator of Section 2.2 (needs sp_factor's q). */
+sp_status sp_matvec(sp_ctx *ctx, const void *x_dev, void *w_dev);
+
+/* g = G f = F^{-1} diag(1/(4 pi^2 |k|^2 - s)) F f (Eq. G). */
+sp_status sp_green(sp_ctx *ctx, const void *f_dev, void *g_dev);
+
+/* y = Q r, the sparsifying stencil alone (Section 2.3, Q(S, gamma) = [I, -T_S]). */
+sp_status sp_qapply(sp_ctx *ctx, const void *r_dev, void *y_dev);
+
+/* Copy set type t's tables to the host (t = sum of 2^a over axes a with
+ * p_a = 0 mod b: 0 = cell, 2^d - 1 = vertex).  Q_out, C_out: |S| x |gamma|
+ * row-major (rows in S order, columns in gamma order, points ordered with axis 0
+ * fastest); either may be NULL.  *rows = |S|, *cols = |gamma|, *rank = rank kept
+ * by the pseudoinverse. */
+sp_status sp_get_table(const sp_ctx *ctx, int t, double *Q_out, double *C_out, int *rows,
+                       int *cols, int *rank);
+
+/* Host-only (no GPU): the same tables as sp_setup computes for (d, n, b, s),
+ * type t.  Pass Q_out = C_out = NULL to query *rows / *cols first.
+ * sigma_out (may be NULL) receives min(|beta|, 64) leading singular values of
+ * G(beta, gamma^c) in descending order. */
+sp_status sp_stencil_table(int d, int n, int b, double s, int t, int host_threads,
+                           double *Q_out, double *C_out, int *rows, int *cols, int *rank,
+                           double *sigma_out);
+
+/* Host-only: the nested-dissection structure (Fig. nd).  Writes, for levels
+ * 0 (leaves) .. L (root), the number of fronts, eliminated unknowns k and front
+ * size m into the caller's arrays of capacity cap; *nlevels = L + 1. */
+sp_status sp_front_sizes(int d, int n, int b, int cap, int *nlevels, int *nfronts, int *k,
+                         int *m);
+
+/* Host-only: the symbolic data of one nested-dissection level (Fig. nd), for
+ * inspection and tests.  Pass NULL arrays to query the sizes first.
+ * gidx: nf x m grid indices of the front unknowns (eliminated ones first);
+ * ea_map: 2^d x (mc - kc) positions in this level's fronts of the children's
+ * boundary unknowns (child position delta = sum_a 2^a * (child box coordinate a
+ * is odd)); asm_slot / asm_cvar: nasm front slots (r + c*m, column-major) and
+ * front positions of the column point of the original entries of P assembled
+ * into every front of the level. */
+sp_status sp_level_info(int d, int n, int b, int level, int *nf, int *k, int *m, int *mc,
+                        int *kc, int *nasm, int *gidx, int *ea_map, int *asm_slot,
+                        int *asm_cvar);
+
+/* Algorithmic sizes of the context: factor entries (sum over fronts of
+ * k^2 + 2 k (m - k)), factor flops (sum of (2/3) k^3 + 2 k^2 (m-k) + 2 k (m-k)^2
+ * real operations) and bytes of one preconditioner application. */
+sp_status sp_costs(const sp_ctx *ctx, double *factor_entries, double *factor_flops,
+                   double *apply_bytes);
+
+/* Section 2.1 shift/potential split on host arrays of N values.
+ * Helmholtz: s = mean(omega^2 / c^2), q = s - omega^2 / c^2.
+ * Schroedinger (rescaled, Eq. schr): s = mean(l^2 E - l^2 V), q = l^2 V - l^2 E + s;
+ * the caller multiplies f by l^2.  If L - s is numerically singular (see
+ * sp_setup) s is raised by 1e-3 * 4 pi^2 until it is not; q follows s. */
+sp_status sp_medium_helmholtz(int d, int n, double omega, const double *c_host, double *s_out,
+                              double *q_host);
+sp_status sp_medium_schrodinger(int d, int n, double ell, double E, const double *V_host,
+                                double *s_out, double *q_host);
+
+/* Kernel-class timing for roofline measurements: with sp_profile(ctx, 1) every
+ * later call records CUDA events around its kernel launches on the context's
+ * stream.  sp_profile_read synchronises, writes per class c (0 assembly and
+ * extend-add, 1 LU panels, 2 LU row-block solves, 3 LU Schur updates, 4 stencil
+ * apply, 5 forward sweep, 6 backward sweep, 7 FFT passes, 8 Arnoldi/GMRES vector
+ * kernels) the summed device milliseconds, the number of kernel launches and the
+ * algorithmic work (flops for classes 1-3, bytes for the others: the data a
+ * kernel must move at least once), then clears the record.  Arrays of cap >= 9. */
+sp_status sp_profile(sp_ctx *ctx, int enable);
+sp_status sp_profile_read(sp_ctx *ctx, int cap, double *ms, int *launches, double *work);
+
+void sp_destroy(sp_ctx *ctx);
+const char *sp_status_str(sp_status st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SP_GB300_H */

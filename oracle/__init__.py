@@ -29,7 +29,7 @@ from .spectral import (wavenumber_grid, laplacian_symbol, green_symbol, green_ke
                        resonance_gap, dft_matrix)
 from .stencil import (set_types, canonical_set, canonical_gamma, canonical_beta, green_block,
                       stencil_tables, matlab_pinv, annihilation_ratio)
-from .precond import SparsifyingPreconditioner, assemble_sparse
+from .precond import SparsifyingPreconditioner, assemble_sparse, sampled_rows, sampled_apply_residual
 from .gmres import gmres_right
 
 __all__ = [
@@ -37,5 +37,6 @@ __all__ = [
     "apply_operator", "helmholtz_shift", "schrodinger_shift", "resonance_gap", "dft_matrix",
     "set_types", "canonical_set", "canonical_gamma", "canonical_beta", "green_block",
     "stencil_tables", "matlab_pinv", "annihilation_ratio",
-    "SparsifyingPreconditioner", "assemble_sparse", "gmres_right",
+    "SparsifyingPreconditioner", "assemble_sparse", "sampled_rows", "sampled_apply_residual",
+    "gmres_right",
 ]

@@ -97,3 +97,37 @@ class SparsifyingPreconditioner:
         """||P z - Q r|| / ||Q r||: checks any candidate z = P^{-1} Q r without a factor."""
         Qr = self.apply_Q(r)
         return float(np.linalg.norm(self.P @ np.asarray(z) - Qr) / np.linalg.norm(Qr))
+
+
+def sampled_rows(d: int, n: int, b: int, tables: list[dict], q: np.ndarray, rows: np.ndarray):
+    """Rows of Q and P = Q + C q for the listed grid points, one by one (Section 2.2-2.3).
+
+    Returns a list of (cols, Q_row, P_row): row j belongs to the set of type
+    t = sum_{a : j_a mod b = 0} 2^a of the leaf box with origin b * floor(j / b);
+    its entries sit on gamma(S) of that instance.  Lets a caller check
+    (P z - Q r) at sampled rows of a grid too large to assemble.
+    """
+    out = []
+    q = np.asarray(q, dtype=np.float64)
+    for j in np.asarray(rows):
+        p = np.array([(j // n ** a) % n for a in range(d)], dtype=np.int64)
+        t = sum(1 << a for a in range(d) if p[a] % b == 0)
+        o = (p // b) * b
+        tab = tables[t]
+        loc = p - o
+        a_idx = int(np.nonzero(np.all(tab["S"] == loc[None, :], axis=1))[0][0])
+        cols = flat_index(tab["gamma"] + o, n)
+        Qr = tab["Q"][a_idx]
+        out.append((cols, Qr, Qr + tab["C"][a_idx] * q[cols]))
+    return out
+
+
+def sampled_apply_residual(d, n, b, tables, q, r, z, rows) -> float:
+    """||(P z - Q r)[rows]|| / ||(Q r)[rows]|| from rows computed one by one."""
+    num = den = 0.0
+    for cols, Qr, Pr in sampled_rows(d, n, b, tables, q, rows):
+        qr = Qr @ np.asarray(r)[cols]
+        pz = Pr @ np.asarray(z)[cols]
+        num += abs(pz - qr) ** 2
+        den += abs(qr) ** 2
+    return float(np.sqrt(num / den))

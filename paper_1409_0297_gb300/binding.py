@@ -1,0 +1,338 @@
+"""ctypes binding of the C ABI in include/sp.h (argument marshalling only).
+
+Every function below forwards to the function of the same name in
+libsp_gb300.so; all arithmetic happens in the library's CUDA kernels.  Device
+buffers are passed as integer addresses (e.g. torch.Tensor.data_ptr()); the
+convenience class Solver takes torch CUDA tensors and checks their dtype, size
+and contiguity before passing the pointers on.  If the library is missing the
+import of this module raises: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsp_gb300.so")
+
+SP_OK, SP_ERR_ARG, SP_ERR_RESONANT, SP_ERR_SINGULAR, SP_ERR_NOCONV = 0, 1, 2, 3, 4
+SP_ERR_OOM, SP_ERR_TIMEOUT, SP_ERR_CUDA, SP_ERR_STATE = 5, 6, 7, 8
+SP_PREC_FP64, SP_PREC_FP32 = 0, 1
+
+EXPORTED = [
+    "sp_default_opts", "sp_setup", "sp_factor", "sp_apply", "sp_solve", "sp_factor_host",
+    "sp_solve_host", "sp_matvec", "sp_green", "sp_qapply", "sp_get_table", "sp_stencil_table",
+    "sp_front_sizes", "sp_level_info", "sp_costs", "sp_medium_helmholtz", "sp_medium_schrodinger", "sp_profile",
+    "sp_profile_read", "sp_destroy", "sp_status_str",
+]
+PROF_CLASSES = ["assemble", "lu_panel", "lu_trsm", "lu_gemm", "qapply", "forward", "backward",
+                "fft", "krylov"]
+
+
+class sp_opts(ctypes.Structure):
+    _fields_ = [("maxit", ctypes.c_int), ("restart", ctypes.c_int), ("tol", ctypes.c_double),
+                ("pivot_tol", ctypes.c_double), ("device", ctypes.c_int),
+                ("host_threads", ctypes.c_int)]
+
+
+class sp_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("est_relres", ctypes.c_double), ("true_relres", ctypes.c_double),
+                ("s_used", ctypes.c_double), ("hist", ctypes.POINTER(ctypes.c_double)),
+                ("hist_cap", ctypes.c_int), ("hist_len", ctypes.c_int)]
+
+
+class SpError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_str(status)} (status {status})")
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run paper_1409_0297_gb300.build.build() "
+                          "(or __graft_entry__.build()) first")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, None
+    pI, pD = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "sp_default_opts": (V, [ctypes.POINTER(sp_opts)]),
+        "sp_setup": (I, [I, I, I, D, I, ctypes.POINTER(sp_opts), P, ctypes.POINTER(P)]),
+        "sp_factor": (I, [P, P]),
+        "sp_apply": (I, [P, P, P]),
+        "sp_solve": (I, [P, P, P, ctypes.POINTER(sp_info)]),
+        "sp_factor_host": (I, [P, P]),
+        "sp_solve_host": (I, [P, P, P, ctypes.POINTER(sp_info)]),
+        "sp_matvec": (I, [P, P, P]),
+        "sp_green": (I, [P, P, P]),
+        "sp_qapply": (I, [P, P, P]),
+        "sp_get_table": (I, [P, I, pD, pD, pI, pI, pI]),
+        "sp_stencil_table": (I, [I, I, I, D, I, I, pD, pD, pI, pI, pI, pD]),
+        "sp_front_sizes": (I, [I, I, I, I, pI, pI, pI, pI]),
+        "sp_costs": (I, [P, pD, pD, pD]),
+        "sp_level_info": (I, [I, I, I, I, pI, pI, pI, pI, pI, pI, pI, pI, pI, pI]),
+        "sp_medium_helmholtz": (I, [I, I, D, P, pD, P]),
+        "sp_medium_schrodinger": (I, [I, I, D, D, P, pD, P]),
+        "sp_profile": (I, [P, I]),
+        "sp_profile_read": (I, [P, I, pD, pI, pD]),
+        "sp_destroy": (V, [P]),
+        "sp_status_str": (ctypes.c_char_p, [I]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+LIB = _load()
+
+
+def status_str(st: int) -> str:
+    return LIB.sp_status_str(st).decode()
+
+
+def _check(st: int, where: str, ok=(SP_OK,)):
+    if st not in ok:
+        raise SpError(st, where)
+    return st
+
+
+def _dptr(a):
+    """numpy float64 array -> POINTER(c_double)."""
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# ------------------------------------------------------------------ same-name wrappers
+def sp_default_opts() -> sp_opts:
+    o = sp_opts()
+    LIB.sp_default_opts(ctypes.byref(o))
+    return o
+
+
+def sp_setup(d: int, n: int, b: int, s: float, prec: int = SP_PREC_FP64, opts: sp_opts | None = None,
+             stream: int = 0) -> int:
+    ctx = ctypes.c_void_p()
+    _check(LIB.sp_setup(d, n, b, float(s), prec, ctypes.byref(opts) if opts else None,
+                        ctypes.c_void_p(stream), ctypes.byref(ctx)), "sp_setup")
+    return ctx.value
+
+
+def sp_factor(ctx: int, q_dev: int) -> None:
+    _check(LIB.sp_factor(ctx, q_dev), "sp_factor")
+
+
+def sp_factor_host(ctx: int, q_host) -> None:
+    _check(LIB.sp_factor_host(ctx, q_host.ctypes.data), "sp_factor_host")
+
+
+def sp_apply(ctx: int, r_dev: int, z_dev: int) -> None:
+    _check(LIB.sp_apply(ctx, r_dev, z_dev), "sp_apply")
+
+
+def sp_qapply(ctx: int, r_dev: int, y_dev: int) -> None:
+    _check(LIB.sp_qapply(ctx, r_dev, y_dev), "sp_qapply")
+
+
+def sp_matvec(ctx: int, x_dev: int, w_dev: int) -> None:
+    _check(LIB.sp_matvec(ctx, x_dev, w_dev), "sp_matvec")
+
+
+def sp_green(ctx: int, f_dev: int, g_dev: int) -> None:
+    _check(LIB.sp_green(ctx, f_dev, g_dev), "sp_green")
+
+
+def _info(hist_cap: int):
+    import numpy as np
+    info = sp_info()
+    hist = np.zeros(max(1, hist_cap), dtype=np.float64)
+    info.hist = _dptr(hist)
+    info.hist_cap = hist_cap
+    return info, hist
+
+
+def _info_dict(info, hist, st):
+    return dict(status=st, iters=info.iters, restarts=info.restarts, est_relres=info.est_relres,
+                true_relres=info.true_relres, s_used=info.s_used,
+                hist=hist[: info.hist_len].copy())
+
+
+def sp_solve(ctx: int, f_dev: int, u_dev: int, hist_cap: int = 1024, allow_noconv=False) -> dict:
+    info, hist = _info(hist_cap)
+    st = LIB.sp_solve(ctx, f_dev, u_dev, ctypes.byref(info))
+    _check(st, "sp_solve", (SP_OK, SP_ERR_NOCONV) if allow_noconv else (SP_OK,))
+    return _info_dict(info, hist, st)
+
+
+def sp_solve_host(ctx: int, f_host, u_host, hist_cap: int = 1024, allow_noconv=False) -> dict:
+    info, hist = _info(hist_cap)
+    st = LIB.sp_solve_host(ctx, f_host.ctypes.data, u_host.ctypes.data, ctypes.byref(info))
+    _check(st, "sp_solve_host", (SP_OK, SP_ERR_NOCONV) if allow_noconv else (SP_OK,))
+    return _info_dict(info, hist, st)
+
+
+def sp_get_table(ctx: int, t: int):
+    import numpy as np
+    rows, cols, rank = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(LIB.sp_get_table(ctx, t, None, None, ctypes.byref(rows), ctypes.byref(cols),
+                            ctypes.byref(rank)), "sp_get_table")
+    Q = np.zeros((rows.value, cols.value))
+    C = np.zeros((rows.value, cols.value))
+    _check(LIB.sp_get_table(ctx, t, _dptr(Q), _dptr(C), ctypes.byref(rows), ctypes.byref(cols),
+                            ctypes.byref(rank)), "sp_get_table")
+    return Q, C, rank.value
+
+
+def sp_stencil_table(d: int, n: int, b: int, s: float, t: int, host_threads: int = 0):
+    """Host-only stencil tables (no GPU needed): returns (Q, C, rank, sigma)."""
+    import numpy as np
+    rows, cols, rank = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(LIB.sp_stencil_table(d, n, b, float(s), t, host_threads, None, None,
+                                ctypes.byref(rows), ctypes.byref(cols), None, None),
+           "sp_stencil_table")
+    Q = np.zeros((rows.value, cols.value))
+    C = np.zeros((rows.value, cols.value))
+    sig = np.zeros(64)
+    _check(LIB.sp_stencil_table(d, n, b, float(s), t, host_threads, _dptr(Q), _dptr(C),
+                                ctypes.byref(rows), ctypes.byref(cols), ctypes.byref(rank),
+                                _dptr(sig)), "sp_stencil_table")
+    nb = Q.shape[1] - Q.shape[0]
+    return Q, C, rank.value, sig[: min(64, nb)]
+
+
+def sp_front_sizes(d: int, n: int, b: int):
+    cap = 64
+    nl = ctypes.c_int()
+    nf, k, m = (ctypes.c_int * cap)(), (ctypes.c_int * cap)(), (ctypes.c_int * cap)()
+    _check(LIB.sp_front_sizes(d, n, b, cap, ctypes.byref(nl), nf, k, m), "sp_front_sizes")
+    return [(nf[i], k[i], m[i]) for i in range(nl.value)]
+
+
+def sp_level_info(d: int, n: int, b: int, level: int) -> dict:
+    """Host-only symbolic data of one nested-dissection level (see include/sp.h)."""
+    import numpy as np
+    v = [ctypes.c_int() for _ in range(6)]
+    _check(LIB.sp_level_info(d, n, b, level, *[ctypes.byref(x) for x in v], None, None, None, None),
+           "sp_level_info")
+    nf, k, m, mc, kc, nasm = (x.value for x in v)
+    gidx = np.zeros(nf * m, dtype=np.int32)
+    ea = np.zeros(max(1, (1 << d) * (mc - kc)), dtype=np.int32)
+    slot = np.zeros(max(1, nasm), dtype=np.int32)
+    cvar = np.zeros(max(1, nasm), dtype=np.int32)
+    ip = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    _check(LIB.sp_level_info(d, n, b, level, *[ctypes.byref(x) for x in v], ip(gidx), ip(ea),
+                             ip(slot), ip(cvar)), "sp_level_info")
+    return dict(nf=nf, k=k, m=m, mc=mc, kc=kc, gidx=gidx.reshape(nf, m),
+                ea_map=ea[: (1 << d) * (mc - kc)].reshape(1 << d, mc - kc) if mc else None,
+                asm_slot=slot[:nasm], asm_cvar=cvar[:nasm])
+
+
+def sp_costs(ctx: int):
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(LIB.sp_costs(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "sp_costs")
+    return dict(factor_entries=a.value, factor_flops=b.value, apply_bytes=c.value)
+
+
+def sp_medium_helmholtz(d: int, n: int, omega: float, c):
+    import numpy as np
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    q = np.empty_like(c)
+    s = ctypes.c_double()
+    _check(LIB.sp_medium_helmholtz(d, n, float(omega), c.ctypes.data, ctypes.byref(s),
+                                   q.ctypes.data), "sp_medium_helmholtz")
+    return s.value, q
+
+
+def sp_medium_schrodinger(d: int, n: int, ell: float, E: float, V):
+    import numpy as np
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    q = np.empty_like(V)
+    s = ctypes.c_double()
+    _check(LIB.sp_medium_schrodinger(d, n, float(ell), float(E), V.ctypes.data, ctypes.byref(s),
+                                     q.ctypes.data), "sp_medium_schrodinger")
+    return s.value, q
+
+
+def sp_profile(ctx: int, enable: bool) -> None:
+    _check(LIB.sp_profile(ctx, 1 if enable else 0), "sp_profile")
+
+
+def sp_profile_read(ctx: int) -> dict:
+    """{class: (ms, launches, work)} since the last read (work: flops or bytes)."""
+    import numpy as np
+    k = len(PROF_CLASSES)
+    ms, wk = np.zeros(k), np.zeros(k)
+    ln = (ctypes.c_int * k)()
+    _check(LIB.sp_profile_read(ctx, k, _dptr(ms), ln, _dptr(wk)), "sp_profile_read")
+    return {c: (float(ms[i]), int(ln[i]), float(wk[i])) for i, c in enumerate(PROF_CLASSES)}
+
+
+def sp_destroy(ctx: int) -> None:
+    LIB.sp_destroy(ctx)
+
+
+# ------------------------------------------------------------------ convenience class
+class Solver:
+    """Owns one context.  Vectors are torch complex128 CUDA tensors of n^d entries,
+    q a float64 CUDA tensor; the solver keeps a reference to q (the library reads
+    it until the next factor call)."""
+
+    def __init__(self, d: int, n: int, b: int, s: float, prec: int = SP_PREC_FP64,
+                 maxit: int = 500, restart: int = 200, tol: float = 1e-8, device: int = 0,
+                 stream: int = 0):
+        o = sp_default_opts()
+        o.maxit, o.restart, o.tol, o.device = maxit, restart, tol, device
+        self.d, self.n, self.b, self.s, self.prec = d, n, b, s, prec
+        self.N = n ** d
+        self.ctx = sp_setup(d, n, b, s, prec, o, stream)
+        self._q = None
+
+    def _vec(self, x, dtype):
+        import torch
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == dtype and
+                x.is_contiguous() and x.numel() == self.N):
+            raise ValueError(f"expected a contiguous CUDA {dtype} tensor of {self.N} entries")
+        return x.data_ptr()
+
+    def factor(self, q):
+        import torch
+        p = self._vec(q, torch.float64)
+        self._q = q
+        sp_factor(self.ctx, p)
+
+    def apply(self, r, z):
+        import torch
+        sp_apply(self.ctx, self._vec(r, torch.complex128), self._vec(z, torch.complex128))
+
+    def qapply(self, r, y):
+        import torch
+        sp_qapply(self.ctx, self._vec(r, torch.complex128), self._vec(y, torch.complex128))
+
+    def matvec(self, x, w):
+        import torch
+        sp_matvec(self.ctx, self._vec(x, torch.complex128), self._vec(w, torch.complex128))
+
+    def green(self, f, g):
+        import torch
+        sp_green(self.ctx, self._vec(f, torch.complex128), self._vec(g, torch.complex128))
+
+    def solve(self, f, u, **kw):
+        import torch
+        return sp_solve(self.ctx, self._vec(f, torch.complex128), self._vec(u, torch.complex128), **kw)
+
+    def table(self, t: int):
+        return sp_get_table(self.ctx, t)
+
+    def costs(self):
+        return sp_costs(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            sp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,675 @@
+// C ABI of the library (include/sp.h): context set-up, factorisation, preconditioner
+// application and the GMRES driver.  The driver runs on the host but every vector
+// operation is a device kernel; the host reads two scalars per iteration (the
+// Givens estimate and the new Arnoldi norm) to decide whether to stop.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <vector>
+
+#include "sp_internal.h"
+
+using namespace sp;
+
+namespace sp {
+thread_local Profiler* g_prof = nullptr;
+
+cudaEvent_t Profiler::get() {
+  if (used < pool.size()) return pool[used++];
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  pool.push_back(e);
+  ++used;
+  return e;
+}
+int Profiler::begin(int cls, cudaStream_t st) {
+  Rec r{cls, get(), get(), 0.0, 0};
+  cudaEventRecord(r.a, st);
+  recs.push_back(r);
+  return (int)recs.size() - 1;
+}
+void Profiler::end(int tok, double work, int launches, cudaStream_t st) {
+  Rec& r = recs[tok];
+  r.work = work;
+  r.launches = launches;
+  cudaEventRecord(r.b, st);
+}
+cudaError_t Profiler::read(double* ms, int* launches, double* work, int cap) {
+  for (int c = 0; c < cap; ++c) {
+    if (ms) ms[c] = 0;
+    if (launches) launches[c] = 0;
+    if (work) work[c] = 0;
+  }
+  cudaError_t err = cudaSuccess;
+  for (auto& r : recs) {
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e != cudaSuccess) err = e;
+    float t = 0;
+    cudaEventElapsedTime(&t, r.a, r.b);
+    if (r.cls < cap) {
+      if (ms) ms[r.cls] += t;
+      if (launches) launches[r.cls] += r.launches;
+      if (work) work[r.cls] += r.work;
+    }
+  }
+  recs.clear();
+  used = 0;
+  return err;
+}
+void Profiler::destroy() {
+  for (auto e : pool) cudaEventDestroy(e);
+  pool.clear();
+  recs.clear();
+  used = 0;
+}
+}  // namespace sp
+
+struct sp_ctx {
+  int d = 0, n = 0, b = 0, L = 0, nl = 0;
+  long N = 0;
+  double s = 0;
+  sp_precision prec = SP_PREC_FP64;
+  sp_opts opts{};
+  cudaStream_t stream = nullptr;
+  std::vector<StencilTable> tabs;
+  Symbolic sym;
+  std::vector<DevLevel> lv;
+  std::vector<QTypeDev> qtypes;
+  std::vector<void*> allocs;
+  double* Qcat = nullptr;
+  double* Ccat = nullptr;
+  float* Qcat32 = nullptr;
+  FftPlan fft;
+  const double* q = nullptr;  // current medium (caller's or qbuf)
+  double* qbuf = nullptr;     // used by sp_factor_host
+  int* status = nullptr;
+  void* rhsQ = nullptr;       // N vector (VT) of Q r
+  // Krylov workspace
+  int maxv = 0;
+  double2 *V = nullptr, *Z = nullptr, *H = nullptr, *gam = nullptr, *sn = nullptr;
+  double2 *h1 = nullptr, *h2 = nullptr, *y = nullptr;
+  double *cs = nullptr, *nrm = nullptr, *est = nullptr;
+  double2 *g = nullptr, *r = nullptr, *t = nullptr, *fbuf = nullptr, *ubuf = nullptr;
+  double* host_sc = nullptr;  // pinned scalars
+  KrylovWork K;
+  Profiler prof;
+  bool profiling = false;
+  bool factored = false;
+  double factor_entries = 0, factor_flops = 0, apply_bytes = 0;
+};
+
+namespace {
+
+// Makes the context's profiler current for the duration of one API call.
+struct ProfGuard {
+  Profiler* saved;
+  explicit ProfGuard(sp_ctx* c) : saved(g_prof) { g_prof = (c && c->profiling) ? &c->prof : nullptr; }
+  ~ProfGuard() { g_prof = saved; }
+};
+
+const double kPi = 3.141592653589793238462643383279502884;
+
+template <class P>
+cudaError_t dalloc(sp_ctx* c, P** p, size_t bytes) {
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, bytes ? bytes : 16);
+  if (e != cudaSuccess) return e;
+  c->allocs.push_back(v);
+  *p = (P*)v;
+  return cudaSuccess;
+}
+
+template <class P>
+cudaError_t upload(sp_ctx* c, P** p, const std::vector<P>& h) {
+  cudaError_t e = dalloc(c, p, h.size() * sizeof(P));
+  if (e != cudaSuccess) return e;
+  if (!h.empty()) e = cudaMemcpy(*p, h.data(), h.size() * sizeof(P), cudaMemcpyHostToDevice);
+  return e;
+}
+
+sp_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return SP_OK;
+  if (e == cudaErrorMemoryAllocation) return SP_ERR_OOM;
+  return SP_ERR_CUDA;
+}
+
+#define SP_CK(x)                              \
+  do {                                        \
+    cudaError_t e_ = (x);                     \
+    if (e_ != cudaSuccess) return cuda_status(e_); \
+  } while (0)
+
+double shift_gap(int d, int n, double s) { return resonance_gap(d, n, s); }
+
+double perturb_shift(int d, int n, double s) {
+  int guard = 0;
+  while (shift_gap(d, n, s) < 1e-6 && guard++ < 1000000) s += 1e-3 * 4.0 * kPi * kPi;
+  return s;
+}
+
+sp_status apply_impl(sp_ctx* c, const double2* r, double2* z) {
+  cudaStream_t st = c->stream;
+  SP_CK(q_apply(c->prec, c->d, c->n, c->nl, c->qtypes, c->Qcat, c->Qcat32, r, c->rhsQ, st));
+  for (int l = 0; l <= c->L; ++l)
+    SP_CK(forward_level(c->prec, c->d, c->lv[l], l ? &c->lv[l - 1] : nullptr, c->rhsQ, st));
+  for (int l = c->L; l >= 0; --l) SP_CK(backward_level(c->prec, c->d, c->lv[l], z, st));
+  return SP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sp_default_opts(sp_opts* o) {
+  if (!o) return;
+  o->maxit = 500;
+  o->restart = 200;
+  o->tol = 1e-8;
+  o->pivot_tol = 1e-14;
+  o->device = 0;
+  o->host_threads = 0;
+}
+
+const char* sp_status_str(sp_status st) {
+  switch (st) {
+    case SP_OK: return "ok";
+    case SP_ERR_ARG: return "invalid argument";
+    case SP_ERR_RESONANT: return "L - s is numerically singular (resonant shift)";
+    case SP_ERR_SINGULAR: return "singular front pivot";
+    case SP_ERR_NOCONV: return "GMRES did not reach the tolerance";
+    case SP_ERR_OOM: return "out of memory";
+    case SP_ERR_TIMEOUT: return "device wait timed out";
+    case SP_ERR_CUDA: return "CUDA runtime error";
+    case SP_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+sp_status sp_front_sizes(int d, int n, int b, int cap, int* nlevels, int* nfronts, int* k, int* m) {
+  std::vector<int> nf, kk, mm;
+  if (!nlevels || front_sizes(d, n, b, &nf, &kk, &mm)) return SP_ERR_ARG;
+  *nlevels = (int)nf.size();
+  for (int i = 0; i < (int)nf.size() && i < cap; ++i) {
+    if (nfronts) nfronts[i] = nf[i];
+    if (k) k[i] = kk[i];
+    if (m) m[i] = mm[i];
+  }
+  return SP_OK;
+}
+
+sp_status sp_stencil_table(int d, int n, int b, double s, int t, int host_threads, double* Q_out,
+                           double* C_out, int* rows, int* cols, int* rank, double* sigma_out) {
+  int L;
+  if (check_grid(d, n, b, &L) || t < 0 || t >= (1 << d)) return SP_ERR_ARG;
+  if (!rows || !cols) return SP_ERR_ARG;
+  long nS = 1, nG = 1;
+  for (int a = 0; a < d; ++a) {
+    bool z = (t >> a) & 1;
+    nS *= z ? 1 : (b - 1);
+    nG *= z ? 3 : (b + 1);
+  }
+  *rows = (int)nS;
+  *cols = (int)nG;
+  if (!Q_out && !C_out && !sigma_out && !rank) return SP_OK;
+  if (shift_gap(d, n, s) < 1e-6) return SP_ERR_RESONANT;
+  try {
+    std::vector<double> g = green_kernel(d, n, s);
+    StencilTable tb;
+    if (stencil_table(d, n, b, t, g, host_threads, &tb)) return SP_ERR_ARG;
+    if (Q_out) std::memcpy(Q_out, tb.Q.data(), tb.Q.size() * sizeof(double));
+    if (C_out) std::memcpy(C_out, tb.C.data(), tb.C.size() * sizeof(double));
+    if (rank) *rank = tb.rank;
+    if (sigma_out)
+      for (int i = 0; i < std::min<int>(64, (int)tb.sigma.size()); ++i) sigma_out[i] = tb.sigma[i];
+  } catch (const std::bad_alloc&) {
+    return SP_ERR_OOM;
+  }
+  return SP_OK;
+}
+
+sp_status sp_level_info(int d, int n, int b, int level, int* nf, int* k, int* m, int* mc, int* kc,
+                        int* nasm, int* gidx, int* ea_map, int* asm_slot, int* asm_cvar) {
+  int L;
+  if (check_grid(d, n, b, &L) || level < 0 || level > L) return SP_ERR_ARG;
+  try {
+    // the assembly lists need the table geometry only, not the values
+    std::vector<StencilTable> tabs(1 << d);
+    for (int t = 0; t < (1 << d); ++t) {
+      StencilTable& tb = tabs[t];
+      tb.t = t;
+      tb.nS = 1;
+      tb.nG = 1;
+      int lo[3], hi[3], glo[3], ghi[3];
+      for (int a = 0; a < d; ++a) {
+        bool z = (t >> a) & 1;
+        lo[a] = z ? 0 : 1;
+        hi[a] = z ? 0 : b - 1;
+        glo[a] = z ? -1 : 0;
+        ghi[a] = z ? 1 : b;
+        tb.nS *= hi[a] - lo[a] + 1;
+        tb.nG *= ghi[a] - glo[a] + 1;
+      }
+      for (int c = 0; c < tb.nS; ++c) {
+        int cc = c;
+        for (int a = 0; a < d; ++a) {
+          int span = hi[a] - lo[a] + 1;
+          tb.S.push_back(lo[a] + cc % span);
+          cc /= span;
+        }
+      }
+      for (int c = 0; c < tb.nG; ++c) {
+        int cc = c;
+        for (int a = 0; a < d; ++a) {
+          int span = ghi[a] - glo[a] + 1;
+          tb.G.push_back(glo[a] + cc % span);
+          cc /= span;
+        }
+      }
+    }
+    Symbolic sym;
+    if (build_symbolic(d, n, b, tabs, &sym)) return SP_ERR_ARG;
+    const Level& V = sym.lv[level];
+    if (nf) *nf = V.nf;
+    if (k) *k = V.k;
+    if (m) *m = V.m;
+    if (mc) *mc = V.mc;
+    if (kc) *kc = V.kc;
+    if (nasm) *nasm = (int)V.asm_slot.size();
+    if (gidx) std::memcpy(gidx, V.gidx.data(), V.gidx.size() * sizeof(int));
+    if (ea_map && !V.ea_map.empty()) std::memcpy(ea_map, V.ea_map.data(), V.ea_map.size() * sizeof(int));
+    if (asm_slot) std::memcpy(asm_slot, V.asm_slot.data(), V.asm_slot.size() * sizeof(int));
+    if (asm_cvar) std::memcpy(asm_cvar, V.asm_cvar.data(), V.asm_cvar.size() * sizeof(int));
+  } catch (const std::bad_alloc&) {
+    return SP_ERR_OOM;
+  }
+  return SP_OK;
+}
+
+sp_status sp_medium_helmholtz(int d, int n, double omega, const double* c_host, double* s_out,
+                              double* q_host) {
+  if ((d != 2 && d != 3) || n < 2 || !c_host || !s_out || !q_host) return SP_ERR_ARG;
+  long N = 1;
+  for (int a = 0; a < d; ++a) N *= n;
+  double sum = 0;
+  for (long j = 0; j < N; ++j) {
+    if (!(c_host[j] != 0.0)) return SP_ERR_ARG;
+    sum += omega * omega / (c_host[j] * c_host[j]);
+  }
+  double s = perturb_shift(d, n, sum / (double)N);
+  for (long j = 0; j < N; ++j) q_host[j] = s - omega * omega / (c_host[j] * c_host[j]);
+  *s_out = s;
+  return SP_OK;
+}
+
+sp_status sp_medium_schrodinger(int d, int n, double ell, double E, const double* V_host,
+                                double* s_out, double* q_host) {
+  if ((d != 2 && d != 3) || n < 2 || !V_host || !s_out || !q_host) return SP_ERR_ARG;
+  long N = 1;
+  for (int a = 0; a < d; ++a) N *= n;
+  const double l2 = ell * ell;
+  double sum = 0;
+  for (long j = 0; j < N; ++j) sum += -(l2 * V_host[j] - l2 * E);
+  double s = perturb_shift(d, n, sum / (double)N);
+  for (long j = 0; j < N; ++j) q_host[j] = (l2 * V_host[j] - l2 * E) + s;
+  *s_out = s;
+  return SP_OK;
+}
+
+void sp_destroy(sp_ctx* c) {
+  if (!c) return;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaSetDevice(c->opts.device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->host_sc) cudaFreeHost(c->host_sc);
+  c->prof.destroy();
+  cudaSetDevice(dev);
+  delete c;
+}
+
+sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_opts* opts,
+                   void* stream, sp_ctx** out) {
+  if (!out) return SP_ERR_ARG;
+  *out = nullptr;
+  int L;
+  if (check_grid(d, n, b, &L)) return SP_ERR_ARG;
+  if (n & (n - 1)) return SP_ERR_ARG;  // the device FFT handles powers of two
+  if (prec != SP_PREC_FP64 && prec != SP_PREC_FP32) return SP_ERR_ARG;
+  if (!(std::isfinite(s))) return SP_ERR_ARG;
+  if (shift_gap(d, n, s) < 1e-6) return SP_ERR_RESONANT;
+  std::unique_ptr<sp_ctx> c(new (std::nothrow) sp_ctx());
+  if (!c) return SP_ERR_OOM;
+  sp_default_opts(&c->opts);
+  if (opts) c->opts = *opts;
+  if (c->opts.maxit < 1 || c->opts.restart < 1 || c->opts.restart > 1000 || !(c->opts.tol > 0))
+    return SP_ERR_ARG;
+  c->d = d;
+  c->n = n;
+  c->b = b;
+  c->L = L;
+  c->nl = n / b;
+  c->s = s;
+  c->prec = prec;
+  c->stream = (cudaStream_t)stream;
+  c->N = 1;
+  for (int a = 0; a < d; ++a) c->N *= n;
+  const long N = c->N;
+  SP_CK(cudaSetDevice(c->opts.device));
+  // ---- host set-up: Green's kernel, stencil tables, symbolic structure
+  try {
+    std::vector<double> g = green_kernel(d, n, s);
+    c->tabs.resize(1 << d);
+    for (int t = 0; t < (1 << d); ++t)
+      if (stencil_table(d, n, b, t, g, c->opts.host_threads, &c->tabs[t])) return SP_ERR_ARG;
+    if (build_symbolic(d, n, b, c->tabs, &c->sym)) return SP_ERR_ARG;
+  } catch (const std::bad_alloc&) {
+    return SP_ERR_OOM;
+  }
+  // ---- tables on the device (column-major per type, concatenated)
+  {
+    std::vector<double> Qc, Cc;
+    std::vector<float> Q32;
+    long off = 0;
+    for (int t = 0; t < (1 << d); ++t) {
+      const StencilTable& tb = c->tabs[t];
+      QTypeDev qt;
+      qt.nS = tb.nS;
+      qt.nG = tb.nG;
+      qt.tab_off = off;
+      for (int col = 0; col < tb.nG; ++col)
+        for (int a = 0; a < tb.nS; ++a) {
+          Qc.push_back(tb.Q[(size_t)a * tb.nG + col]);
+          Cc.push_back(tb.C[(size_t)a * tb.nG + col]);
+          Q32.push_back((float)tb.Q[(size_t)a * tb.nG + col]);
+        }
+      off += (long)tb.nS * tb.nG;
+      SP_CK(upload(c.get(), &qt.S, tb.S));
+      SP_CK(upload(c.get(), &qt.G, tb.G));
+      c->qtypes.push_back(qt);
+    }
+    SP_CK(upload(c.get(), &c->Qcat, Qc));
+    SP_CK(upload(c.get(), &c->Ccat, Cc));
+    SP_CK(upload(c.get(), &c->Qcat32, Q32));
+  }
+  // ---- levels
+  const size_t fsz = (prec == SP_PREC_FP32) ? sizeof(float) : sizeof(double);
+  const size_t vsz = (prec == SP_PREC_FP32) ? sizeof(float2) : sizeof(double2);
+  c->lv.resize(L + 1);
+  for (int l = 0; l <= L; ++l) {
+    const Level& S = c->sym.lv[l];
+    DevLevel& D = c->lv[l];
+    D.nf = S.nf;
+    D.k = S.k;
+    D.m = S.m;
+    D.nb1 = S.nb1;
+    D.mc = S.mc;
+    D.kc = S.kc;
+    D.nasm = (int)S.asm_slot.size();
+    SP_CK(upload(c.get(), &D.gidx, S.gidx));
+    SP_CK(upload(c.get(), &D.asm_slot, S.asm_slot));
+    SP_CK(upload(c.get(), &D.asm_tidx, S.asm_tidx));
+    SP_CK(upload(c.get(), &D.asm_cvar, S.asm_cvar));
+    SP_CK(upload(c.get(), &D.ea_map, S.ea_map));
+    SP_CK(dalloc(c.get(), &D.front, fsz * (size_t)S.nf * S.m * S.m));
+    SP_CK(dalloc(c.get(), &D.perm, sizeof(int) * (size_t)S.nf * std::max(1, S.k)));
+    SP_CK(dalloc(c.get(), &D.piv, sizeof(int) * (size_t)S.nf * std::max(1, S.k)));
+    SP_CK(dalloc(c.get(), &D.scale, sizeof(double) * S.nf));
+    SP_CK(dalloc(c.get(), &D.upd, vsz * (size_t)S.nf * std::max(1, S.m - S.k)));
+    SP_CK(dalloc(c.get(), &D.y, vsz * (size_t)S.nf * std::max(1, S.k)));
+    double k = S.k, mk = S.m - S.k;
+    c->factor_entries += S.nf * (k * k + 2 * k * mk);
+    c->factor_flops += S.nf * ((2.0 / 3.0) * k * k * k + 2 * k * k * mk + 2 * k * mk * mk);
+  }
+  c->apply_bytes = c->factor_entries * fsz;
+  // ---- FFT plan
+  {
+    FftPlan& P = c->fft;
+    P.d = d;
+    P.n = n;
+    P.logn = 0;
+    while ((1 << P.logn) < n) ++P.logn;
+    std::vector<double2> tw(n / 2);
+    for (int t = 0; t < n / 2; ++t) {
+      double a = 2.0 * kPi * (double)t / (double)n;
+      tw[t] = make_double2(std::cos(a), -std::sin(a));
+    }
+    SP_CK(upload(c.get(), &P.tw, tw));
+    std::vector<double> Dn(N);
+    for (long j = 0; j < N; ++j) {
+      long r = j;
+      double k2 = 0;
+      for (int a = 0; a < d; ++a) {
+        int i = (int)(r % n);
+        r /= n;
+        int k = i < n / 2 ? i : i - n;
+        k2 += (double)k * k;
+      }
+      Dn[j] = 1.0 / (4.0 * kPi * kPi * k2 - s) / (double)N;
+    }
+    SP_CK(upload(c.get(), &P.Dn, Dn));
+    SP_CK(dalloc(c.get(), &P.tmp, sizeof(double2) * N));
+  }
+  // ---- solve workspace
+  c->maxv = c->opts.restart + 1;
+  SP_CK(dalloc(c.get(), &c->rhsQ, vsz * N));
+  SP_CK(dalloc(c.get(), &c->status, sizeof(int)));
+  SP_CK(dalloc(c.get(), &c->qbuf, sizeof(double) * N));
+  SP_CK(dalloc(c.get(), &c->V, sizeof(double2) * N * c->maxv));
+  SP_CK(dalloc(c.get(), &c->Z, sizeof(double2) * N * c->opts.restart));
+  SP_CK(dalloc(c.get(), &c->H, sizeof(double2) * c->maxv * c->opts.restart));
+  SP_CK(dalloc(c.get(), &c->gam, sizeof(double2) * (c->maxv + 1)));
+  SP_CK(dalloc(c.get(), &c->sn, sizeof(double2) * (c->maxv + 1)));
+  SP_CK(dalloc(c.get(), &c->cs, sizeof(double) * (c->maxv + 1)));
+  SP_CK(dalloc(c.get(), &c->h1, sizeof(double2) * 1024));
+  SP_CK(dalloc(c.get(), &c->h2, sizeof(double2) * 1024));
+  SP_CK(dalloc(c.get(), &c->y, sizeof(double2) * 1024));
+  SP_CK(dalloc(c.get(), &c->nrm, sizeof(double) * 4));
+  SP_CK(dalloc(c.get(), &c->est, sizeof(double) * 4));
+  SP_CK(dalloc(c.get(), &c->g, sizeof(double2) * N));
+  SP_CK(dalloc(c.get(), &c->r, sizeof(double2) * N));
+  SP_CK(dalloc(c.get(), &c->t, sizeof(double2) * N));
+  SP_CK(dalloc(c.get(), &c->fbuf, sizeof(double2) * N));
+  SP_CK(dalloc(c.get(), &c->ubuf, sizeof(double2) * N));
+  c->K.nblk = (int)std::min<long>(304, std::max<long>(1, (N + 1023) / 1024));
+  SP_CK(dalloc(c.get(), &c->K.partial, sizeof(double2) * (size_t)c->K.nblk * 1024));
+  SP_CK(dalloc(c.get(), &c->K.h, sizeof(double2) * 1024));
+  SP_CK(cudaMallocHost(&c->host_sc, 8 * sizeof(double)));
+  SP_CK(cudaDeviceSynchronize());
+  *out = c.release();
+  return SP_OK;
+}
+
+sp_status sp_factor(sp_ctx* c, const double* q_dev) {
+  if (!c || !q_dev) return SP_ERR_ARG;
+  ProfGuard pg_(c);
+  SP_CK(cudaSetDevice(c->opts.device));
+  cudaStream_t st = c->stream;
+  c->factored = false;
+  c->q = q_dev;
+  SP_CK(cudaMemsetAsync(c->status, 0, sizeof(int), st));
+  for (int l = 0; l <= c->L; ++l)
+    SP_CK(factor_level(c->prec, c->d, c->lv[l], l ? &c->lv[l - 1] : nullptr, c->Qcat, c->Ccat,
+                       q_dev, c->opts.pivot_tol, c->status, st));
+  int hs = 0;
+  SP_CK(cudaMemcpyAsync(&hs, c->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SP_CK(cudaStreamSynchronize(st));
+  if (hs) return SP_ERR_SINGULAR;
+  c->factored = true;
+  return SP_OK;
+}
+
+sp_status sp_factor_host(sp_ctx* c, const double* q_host) {
+  if (!c || !q_host) return SP_ERR_ARG;
+  SP_CK(cudaSetDevice(c->opts.device));
+  SP_CK(cudaMemcpyAsync(c->qbuf, q_host, sizeof(double) * c->N, cudaMemcpyHostToDevice, c->stream));
+  return sp_factor(c, c->qbuf);
+}
+
+sp_status sp_apply(sp_ctx* c, const void* r_dev, void* z_dev) {
+  if (!c || !r_dev || !z_dev || r_dev == z_dev) return SP_ERR_ARG;
+  ProfGuard pg_(c);
+  if (!c->factored) return SP_ERR_STATE;
+  SP_CK(cudaSetDevice(c->opts.device));
+  return apply_impl(c, (const double2*)r_dev, (double2*)z_dev);
+}
+
+sp_status sp_qapply(sp_ctx* c, const void* r_dev, void* y_dev) {
+  if (!c || !r_dev || !y_dev) return SP_ERR_ARG;
+  ProfGuard pg_(c);
+  SP_CK(cudaSetDevice(c->opts.device));
+  if (c->prec == SP_PREC_FP64)
+    return cuda_status(q_apply(c->prec, c->d, c->n, c->nl, c->qtypes, c->Qcat, c->Qcat32,
+                               (const double2*)r_dev, y_dev, c->stream));
+  // FP32 form: stage through the context's buffer and widen
+  SP_CK(q_apply(SP_PREC_FP64, c->d, c->n, c->nl, c->qtypes, c->Qcat, c->Qcat32,
+                (const double2*)r_dev, y_dev, c->stream));
+  return SP_OK;
+}
+
+sp_status sp_matvec(sp_ctx* c, const void* x_dev, void* w_dev) {
+  if (!c || !x_dev || !w_dev) return SP_ERR_ARG;
+  ProfGuard pg_(c);
+  if (!c->q) return SP_ERR_STATE;
+  SP_CK(cudaSetDevice(c->opts.device));
+  return cuda_status(fft_green_apply(c->fft, (const double2*)x_dev, c->q, true, (double2*)w_dev, c->stream));
+}
+
+sp_status sp_green(sp_ctx* c, const void* f_dev, void* g_dev) {
+  if (!c || !f_dev || !g_dev) return SP_ERR_ARG;
+  ProfGuard pg_(c);
+  SP_CK(cudaSetDevice(c->opts.device));
+  return cuda_status(fft_green_apply(c->fft, (const double2*)f_dev, nullptr, false, (double2*)g_dev, c->stream));
+}
+
+sp_status sp_solve(sp_ctx* c, const void* f_dev, void* u_dev, sp_info* info) {
+  if (!c || !f_dev || !u_dev) return SP_ERR_ARG;
+  ProfGuard pg_(c);
+  if (!c->factored) return SP_ERR_STATE;
+  SP_CK(cudaSetDevice(c->opts.device));
+  cudaStream_t st = c->stream;
+  const long N = c->N;
+  double2* u = (double2*)u_dev;
+  double* hsc = c->host_sc;
+  const int restart = c->opts.restart;
+  const double tol = c->opts.tol;
+  if (info) {
+    info->iters = 0;
+    info->restarts = 0;
+    info->hist_len = 0;
+    info->s_used = c->s;
+  }
+  auto push_hist = [&](double v) {
+    if (info && info->hist && info->hist_len < info->hist_cap) info->hist[info->hist_len++] = v;
+  };
+  // g = G f, ||g||
+  SP_CK(fft_green_apply(c->fft, (const double2*)f_dev, nullptr, false, c->g, st));
+  SP_CK(kr_norm(c->g, N, c->K, c->nrm + 2, st));
+  SP_CK(cudaMemcpyAsync(hsc, c->nrm + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+  SP_CK(cudaMemsetAsync(u, 0, sizeof(double2) * N, st));
+  SP_CK(cudaStreamSynchronize(st));
+  const double bnorm = hsc[0];
+  push_hist(1.0);
+  if (bnorm == 0.0) {
+    if (info) info->true_relres = info->est_relres = 0.0;
+    return SP_OK;
+  }
+  SP_CK(cudaMemcpyAsync(c->r, c->g, sizeof(double2) * N, cudaMemcpyDeviceToDevice, st));
+  SP_CK(cudaMemcpyAsync(c->nrm + 3, c->nrm + 2, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  int total = 0, restarts = 0;
+  double est_rel = 1.0, true_rel = 1.0;
+  const int maxit = c->opts.maxit;
+  for (;;) {
+    SP_CK(kr_start(c->r, N, c->nrm + 3, c->V, c->gam, c->maxv + 1, st));
+    int k = 0;
+    for (int j = 0; j < restart; ++j) {
+      double2* vj = c->V + (long)j * N;
+      double2* zj = c->Z + (long)j * N;
+      double2* w = c->V + (long)(j + 1) * N;
+      sp_status ss = apply_impl(c, vj, zj);
+      if (ss != SP_OK) return ss;
+      SP_CK(fft_green_apply(c->fft, zj, c->q, true, w, st));
+      // classical Gram-Schmidt, twice
+      SP_CK(kr_dots(c->V, N, j + 1, w, N, c->K, c->h1, st));
+      SP_CK(kr_update_dots(c->V, N, j + 1, w, N, c->h1, c->K, c->h2, st));
+      SP_CK(kr_update_dots(c->V, N, j + 1, w, N, c->h2, c->K, nullptr, st));
+      SP_CK(kr_norm(w, N, c->K, c->nrm, st));
+      SP_CK(kr_givens(c->H, c->maxv, j, c->h1, c->h2, c->nrm, c->cs, c->sn, c->gam, c->est, st));
+      SP_CK(cudaMemcpyAsync(hsc, c->est, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      SP_CK(cudaStreamSynchronize(st));
+      ++total;
+      k = j + 1;
+      est_rel = hsc[0] / bnorm;
+      push_hist(est_rel);
+      if (est_rel <= tol || total >= maxit || hsc[1] == 0.0) break;
+      SP_CK(kr_scale(w, N, c->nrm, w, st));
+    }
+    SP_CK(kr_update_solution(c->H, c->maxv, k, c->gam, c->y, c->Z, N, N, u, st));
+    // true residual r = g - A u
+    SP_CK(fft_green_apply(c->fft, u, c->q, true, c->t, st));
+    SP_CK(kr_sub(c->g, c->t, N, c->r, st));
+    SP_CK(kr_norm(c->r, N, c->K, c->nrm + 3, st));
+    SP_CK(cudaMemcpyAsync(hsc + 2, c->nrm + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SP_CK(cudaStreamSynchronize(st));
+    true_rel = hsc[2] / bnorm;
+    if (true_rel <= tol || total >= maxit) break;
+    ++restarts;
+  }
+  if (info) {
+    info->iters = total;
+    info->restarts = restarts;
+    info->est_relres = est_rel;
+    info->true_relres = true_rel;
+  }
+  return true_rel <= tol ? SP_OK : SP_ERR_NOCONV;
+}
+
+sp_status sp_solve_host(sp_ctx* c, const void* f_host, void* u_host, sp_info* info) {
+  if (!c || !f_host || !u_host) return SP_ERR_ARG;
+  SP_CK(cudaSetDevice(c->opts.device));
+  SP_CK(cudaMemcpyAsync(c->fbuf, f_host, sizeof(double2) * c->N, cudaMemcpyHostToDevice, c->stream));
+  sp_status st = sp_solve(c, c->fbuf, c->ubuf, info);
+  if (st != SP_OK && st != SP_ERR_NOCONV) return st;
+  SP_CK(cudaMemcpyAsync(u_host, c->ubuf, sizeof(double2) * c->N, cudaMemcpyDeviceToHost, c->stream));
+  SP_CK(cudaStreamSynchronize(c->stream));
+  return st;
+}
+
+sp_status sp_get_table(const sp_ctx* c, int t, double* Q_out, double* C_out, int* rows, int* cols,
+                       int* rank) {
+  if (!c || t < 0 || t >= (int)c->tabs.size()) return SP_ERR_ARG;
+  const StencilTable& tb = c->tabs[t];
+  if (rows) *rows = tb.nS;
+  if (cols) *cols = tb.nG;
+  if (rank) *rank = tb.rank;
+  if (Q_out) std::memcpy(Q_out, tb.Q.data(), tb.Q.size() * sizeof(double));
+  if (C_out) std::memcpy(C_out, tb.C.data(), tb.C.size() * sizeof(double));
+  return SP_OK;
+}
+
+sp_status sp_profile(sp_ctx* c, int enable) {
+  if (!c) return SP_ERR_ARG;
+  c->profiling = enable != 0;
+  return SP_OK;
+}
+
+sp_status sp_profile_read(sp_ctx* c, int cap, double* ms, int* launches, double* work) {
+  if (!c || cap < PROF_NCLASS) return SP_ERR_ARG;
+  SP_CK(cudaSetDevice(c->opts.device));
+  return cuda_status(c->prof.read(ms, launches, work, cap));
+}
+
+sp_status sp_costs(const sp_ctx* c, double* factor_entries, double* factor_flops,
+                   double* apply_bytes) {
+  if (!c) return SP_ERR_ARG;
+  if (factor_entries) *factor_entries = c->factor_entries;
+  if (factor_flops) *factor_flops = c->factor_flops;
+  if (apply_bytes) *apply_bytes = c->apply_bytes;
+  return SP_OK;
+}
+
+}  // extern "C"

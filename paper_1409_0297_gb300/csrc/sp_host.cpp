@@ -1,0 +1,655 @@
+// Host-side set-up: Green's kernel, stencil tables and nested-dissection symbolic
+// structure.  See sp_host.h.
+#include "sp_host.h"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <thread>
+#include <unordered_map>
+
+namespace sp {
+
+using cd = std::complex<double>;
+static const double kPi = 3.141592653589793238462643383279502884;
+
+int check_grid(int d, int n, int b, int* L) {
+  if (d != 2 && d != 3) return 1;
+  if (b < 2 || n < 2 * b || n % b) return 1;
+  int r = n / b, l = 0;
+  while (r > 1) {
+    if (r & 1) return 1;
+    r >>= 1;
+    ++l;
+  }
+  if (l < 1) return 1;
+  if (L) *L = l;
+  return 0;
+}
+
+// ---------------------------------------------------------------- host FFT
+// exp(sign * 2 pi i t / n) with t reduced mod n first.
+static cd twiddle(long t, long n, int sign) {
+  t %= n;
+  if (t < 0) t += n;
+  double a = 2.0 * kPi * (double)t / (double)n;
+  return cd(std::cos(a), sign * std::sin(a));
+}
+
+// Mixed-radix decimation-in-time DFT of the contiguous line x[0..n).
+static void fft_line(cd* x, int n, int sign) {
+  if (n == 1) return;
+  int p = 2;
+  while (n % p) ++p;
+  int m = n / p;
+  std::vector<cd> sub(n);
+  for (int r = 0; r < p; ++r)
+    for (int j = 0; j < m; ++j) sub[(size_t)r * m + j] = x[(size_t)j * p + r];
+  for (int r = 0; r < p; ++r) fft_line(&sub[(size_t)r * m], m, sign);
+  for (int k = 0; k < n; ++k) {
+    cd acc = 0.0;
+    int kk = k % m;
+    for (int r = 0; r < p; ++r) acc += sub[(size_t)r * m + kk] * twiddle((long)r * k, n, sign);
+    x[k] = acc;
+  }
+}
+
+static void fft_nd(std::vector<cd>& a, int d, int n, int sign) {
+  size_t N = 1;
+  for (int i = 0; i < d; ++i) N *= n;
+  std::vector<cd> line(n);
+  size_t S = 1;
+  for (int ax = 0; ax < d; ++ax) {
+    // lines along axis ax: element i at base + i*S
+    for (size_t base0 = 0; base0 < N; ++base0) {
+      if ((base0 / S) % n != 0) continue;
+      for (int i = 0; i < n; ++i) line[i] = a[base0 + (size_t)i * S];
+      fft_line(line.data(), n, sign);
+      for (int i = 0; i < n; ++i) a[base0 + (size_t)i * S] = line[i];
+    }
+    S *= n;
+  }
+}
+
+static inline int kfreq(int i, int n) { return i < n / 2 ? i : i - n; }
+
+std::vector<double> green_kernel(int d, int n, double s) {
+  size_t N = 1;
+  for (int i = 0; i < d; ++i) N *= n;
+  std::vector<cd> a(N);
+  for (size_t j = 0; j < N; ++j) {
+    size_t r = j;
+    double k2 = 0;
+    for (int ax = 0; ax < d; ++ax) {
+      int k = kfreq((int)(r % n), n);
+      r /= n;
+      k2 += (double)k * k;
+    }
+    a[j] = 1.0 / (4.0 * kPi * kPi * k2 - s);
+  }
+  fft_nd(a, d, n, +1);
+  std::vector<double> g(N);
+  for (size_t j = 0; j < N; ++j) g[j] = a[j].real() / (double)N;
+  return g;
+}
+
+double resonance_gap(int d, int n, double s) {
+  double kappa = s / (4.0 * kPi * kPi);
+  double best = 1e300;
+  // |k|^2 takes integer values; scan all of K in one dimension combinations
+  if (d == 2) {
+    for (int i = -n / 2; i < n / 2; ++i)
+      for (int j = -n / 2; j < n / 2; ++j) best = std::min(best, std::fabs(kappa - (double)(i * i + j * j)));
+  } else {
+    for (int i = -n / 2; i < n / 2; ++i)
+      for (int j = -n / 2; j < n / 2; ++j)
+        for (int l = -n / 2; l < n / 2; ++l)
+          best = std::min(best, std::fabs(kappa - (double)(i * i + j * j + l * l)));
+  }
+  return best / std::max(1.0, std::fabs(kappa));
+}
+
+// ---------------------------------------------------------------- set geometry
+// Cartesian product of per-axis ranges [lo_a, hi_a], axis 0 fastest.
+static std::vector<int> box_points(int d, const int* lo, const int* hi) {
+  std::vector<int> pts;
+  int cnt = 1;
+  for (int a = 0; a < d; ++a) cnt *= (hi[a] - lo[a] + 1);
+  pts.reserve((size_t)cnt * d);
+  int p[3];
+  for (int a = 0; a < d; ++a) p[a] = lo[a];
+  for (int c = 0; c < cnt; ++c) {
+    for (int a = 0; a < d; ++a) pts.push_back(p[a]);
+    for (int a = 0; a < d; ++a) {
+      if (++p[a] <= hi[a]) break;
+      p[a] = lo[a];
+    }
+  }
+  return pts;
+}
+
+static void set_geometry(int d, int b, int t, std::vector<int>* S, std::vector<int>* G,
+                         std::vector<int>* Bt) {
+  int lo[3], hi[3], glo[3], ghi[3];
+  for (int a = 0; a < d; ++a) {
+    bool z = (t >> a) & 1;
+    lo[a] = z ? 0 : 1;
+    hi[a] = z ? 0 : b - 1;
+    glo[a] = z ? -1 : 0;
+    ghi[a] = z ? 1 : b;
+  }
+  *S = box_points(d, lo, hi);
+  *G = box_points(d, glo, ghi);
+  Bt->clear();
+  int nG = (int)G->size() / d;
+  for (int i = 0; i < nG; ++i) {
+    bool in = true;
+    for (int a = 0; a < d; ++a) {
+      int v = (*G)[(size_t)i * d + a];
+      if (v < lo[a] || v > hi[a]) in = false;
+    }
+    if (!in)
+      for (int a = 0; a < d; ++a) Bt->push_back((*G)[(size_t)i * d + a]);
+  }
+}
+
+static inline long flat_of(const int* p, int d, int n) {
+  long f = 0, s = 1;
+  for (int a = 0; a < d; ++a) {
+    int v = p[a] % n;
+    if (v < 0) v += n;
+    f += (long)v * s;
+    s *= n;
+  }
+  return f;
+}
+
+// ---------------------------------------------------------------- dense kernels
+// Householder QR of the column-major h x c matrix X (leading dimension h);
+// on return its upper c x c triangle is R (rows below are zeroed).
+static void house_qr(double* X, int h, int c) {
+  for (int j = 0; j < c && j < h; ++j) {
+    double* xj = X + (size_t)j * h;
+    double nrm2 = 0;
+    for (int i = j; i < h; ++i) nrm2 += xj[i] * xj[i];
+    if (nrm2 == 0.0) continue;
+    double nrm = std::sqrt(nrm2);
+    double alpha = xj[j] > 0 ? -nrm : nrm;
+    xj[j] -= alpha;
+    double vv = 0;
+    for (int i = j; i < h; ++i) vv += xj[i] * xj[i];
+    if (vv > 0) {
+      for (int k = j + 1; k < c; ++k) {
+        double* xk = X + (size_t)k * h;
+        double d0 = 0, d1 = 0, d2 = 0, d3 = 0;
+        int i = j;
+        for (; i + 3 < h; i += 4) {
+          d0 += xj[i] * xk[i];
+          d1 += xj[i + 1] * xk[i + 1];
+          d2 += xj[i + 2] * xk[i + 2];
+          d3 += xj[i + 3] * xk[i + 3];
+        }
+        for (; i < h; ++i) d0 += xj[i] * xk[i];
+        double f = 2.0 * ((d0 + d1) + (d2 + d3)) / vv;
+        for (int ii = j; ii < h; ++ii) xk[ii] -= f * xj[ii];
+      }
+    }
+    xj[j] = alpha;
+    for (int i = j + 1; i < h; ++i) xj[i] = 0.0;
+  }
+}
+
+// One-sided Jacobi SVD of the square column-major r x r matrix A: A V = U_s with
+// orthogonal columns; sigma_i = |U_s(:,i)|.  Returns U (normalised), sigma, V.
+static void jacobi_svd(int r, std::vector<double> A, std::vector<double>* U,
+                       std::vector<double>* sig, std::vector<double>* V) {
+  std::vector<double> W(A);
+  std::vector<double> Vm((size_t)r * r, 0.0);
+  for (int i = 0; i < r; ++i) Vm[(size_t)i * r + i] = 1.0;
+  for (int sweep = 0; sweep < 80; ++sweep) {
+    double off = 0;
+    for (int i = 0; i < r - 1; ++i)
+      for (int j = i + 1; j < r; ++j) {
+        double* wi = &W[(size_t)i * r];
+        double* wj = &W[(size_t)j * r];
+        double al = 0, be = 0, ga = 0;
+        for (int k = 0; k < r; ++k) {
+          al += wi[k] * wi[k];
+          be += wj[k] * wj[k];
+          ga += wi[k] * wj[k];
+        }
+        if (al == 0.0 || be == 0.0) continue;
+        double rel = std::fabs(ga) / std::sqrt(al * be);
+        if (rel <= 1e-16) continue;
+        off = std::max(off, rel);
+        double zeta = (be - al) / (2.0 * ga);
+        double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+        double c = 1.0 / std::sqrt(1.0 + t * t), s = c * t;
+        for (int k = 0; k < r; ++k) {
+          double a = wi[k], bb = wj[k];
+          wi[k] = c * a - s * bb;
+          wj[k] = s * a + c * bb;
+        }
+        double* vi = &Vm[(size_t)i * r];
+        double* vj = &Vm[(size_t)j * r];
+        for (int k = 0; k < r; ++k) {
+          double a = vi[k], bb = vj[k];
+          vi[k] = c * a - s * bb;
+          vj[k] = s * a + c * bb;
+        }
+      }
+    if (off <= 1e-15) break;
+  }
+  // sort by descending singular value
+  std::vector<double> sv(r);
+  for (int i = 0; i < r; ++i) {
+    double s2 = 0;
+    for (int k = 0; k < r; ++k) s2 += W[(size_t)i * r + k] * W[(size_t)i * r + k];
+    sv[i] = std::sqrt(s2);
+  }
+  std::vector<int> ord(r);
+  for (int i = 0; i < r; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b2) { return sv[a] > sv[b2]; });
+  U->assign((size_t)r * r, 0.0);
+  V->assign((size_t)r * r, 0.0);
+  sig->assign(r, 0.0);
+  for (int ii = 0; ii < r; ++ii) {
+    int i = ord[ii];
+    (*sig)[ii] = sv[i];
+    for (int k = 0; k < r; ++k) {
+      (*U)[(size_t)ii * r + k] = sv[i] > 0 ? W[(size_t)i * r + k] / sv[i] : 0.0;
+      (*V)[(size_t)ii * r + k] = Vm[(size_t)i * r + k];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- stencil tables
+int stencil_table(int d, int n, int b, int t, const std::vector<double>& g, int threads,
+                  StencilTable* out) {
+  StencilTable& T = *out;
+  T.t = t;
+  set_geometry(d, b, t, &T.S, &T.G, &T.Bt);
+  T.nS = (int)T.S.size() / d;
+  T.nG = (int)T.G.size() / d;
+  T.nB = (int)T.Bt.size() / d;
+  long N = 1;
+  for (int a = 0; a < d; ++a) N *= n;
+  // complement of gamma (flat indices)
+  std::vector<char> ing(N, 0);
+  for (int i = 0; i < T.nG; ++i) ing[flat_of(&T.G[(size_t)i * d], d, n)] = 1;
+  std::vector<long> comp;
+  comp.reserve(N - T.nG);
+  for (long j = 0; j < N; ++j)
+    if (!ing[j]) comp.push_back(j);
+  const long Np = (long)comp.size();
+  const int r = T.nB, p = T.nS, c = r + p;
+  // rows of [B^T | A^T]: for column point j, G(beta_q, j) then G(S_a, j)
+  std::vector<int> pts;  // r + p points: beta then S
+  pts.insert(pts.end(), T.Bt.begin(), T.Bt.end());
+  pts.insert(pts.end(), T.S.begin(), T.S.end());
+  auto fill_rows = [&](double* X, int h, int row0, long j0, int cnt) {
+    for (int rr = 0; rr < cnt; ++rr) {
+      long j = comp[j0 + rr];
+      int jc[3];
+      long jj = j;
+      for (int a = 0; a < d; ++a) {
+        jc[a] = (int)(jj % n);
+        jj /= n;
+      }
+      for (int col = 0; col < c; ++col) {
+        long f = 0, sc = 1;
+        for (int a = 0; a < d; ++a) {
+          int v = pts[(size_t)col * d + a] - jc[a];
+          v %= n;
+          if (v < 0) v += n;
+          f += v * sc;
+          sc *= n;
+        }
+        X[(size_t)col * h + row0 + rr] = g[f];
+      }
+    }
+  };
+  if (threads <= 0) threads = (int)std::max(1u, std::thread::hardware_concurrency());
+  threads = std::min(threads, 64);
+  const int R = 1024;
+  long nchunks = (Np + R - 1) / R;
+  int nth = (int)std::min<long>(threads, std::max<long>(1, nchunks));
+  std::vector<std::vector<double>> Rs(nth);
+  auto worker = [&](int id) {
+    const int h = c + R;
+    std::vector<double> X((size_t)h * c, 0.0);
+    bool any = false;
+    for (long ch = id; ch < nchunks; ch += nth) {
+      long j0 = ch * R;
+      int cnt = (int)std::min<long>(R, Np - j0);
+      // zero the rows below the current R and the strict lower triangle of R
+      for (int col = 0; col < c; ++col) {
+        double* xc = &X[(size_t)col * h];
+        for (int i = col + 1; i < h; ++i) xc[i] = 0.0;
+      }
+      fill_rows(X.data(), h, c, j0, cnt);
+      house_qr(X.data(), h, c);
+      any = true;
+    }
+    Rs[id].assign((size_t)c * c, 0.0);
+    if (any)
+      for (int col = 0; col < c; ++col)
+        for (int i = 0; i <= col; ++i) Rs[id][(size_t)col * c + i] = X[(size_t)col * h + i];
+  };
+  {
+    std::vector<std::thread> th;
+    for (int i = 1; i < nth; ++i) th.emplace_back(worker, i);
+    worker(0);
+    for (auto& x : th) x.join();
+  }
+  // combine the per-thread triangles
+  std::vector<double> Rf((size_t)c * c, 0.0);
+  {
+    const int h = nth * c;
+    std::vector<double> X((size_t)h * c, 0.0);
+    for (int id = 0; id < nth; ++id)
+      for (int col = 0; col < c; ++col)
+        for (int i = 0; i < c; ++i) X[(size_t)col * h + (size_t)id * c + i] = Rs[id][(size_t)col * c + i];
+    house_qr(X.data(), h, c);
+    for (int col = 0; col < c; ++col)
+      for (int i = 0; i <= col && i < c; ++i) Rf[(size_t)col * c + i] = X[(size_t)col * h + i];
+  }
+  // R11 (r x r), R12 (r x p); B^T = Q1 R11, A^T = Q1 R12 + Q2 R22, so
+  // T^T = pinv(B^T) A^T = pinv(R11) R12 and sigma(R11) = sigma(B).
+  std::vector<double> R11((size_t)r * r), R12((size_t)r * p);
+  for (int col = 0; col < r; ++col)
+    for (int i = 0; i < r; ++i) R11[(size_t)col * r + i] = Rf[(size_t)col * c + i];
+  for (int col = 0; col < p; ++col)
+    for (int i = 0; i < r; ++i) R12[(size_t)col * r + i] = Rf[(size_t)(r + col) * c + i];
+  std::vector<double> U, sg, V;
+  jacobi_svd(r, R11, &U, &sg, &V);
+  T.sigma = sg;
+  double smax = sg.empty() ? 0.0 : sg[0];
+  int rank = 0;
+  if (smax > 0) {
+    double tol = (double)std::max<long>(r, Np) * std::ldexp(1.0, std::ilogb(smax) - 52);
+    for (int i = 0; i < r; ++i)
+      if (sg[i] > tol) ++rank;
+  }
+  T.rank = rank;
+  // Tt = V diag(1/sigma) U^T R12 (r x p), T = Tt^T (p x r)
+  std::vector<double> W((size_t)rank * p, 0.0);  // W = diag(1/s) U^T R12 (rank x p)
+  for (int col = 0; col < p; ++col)
+    for (int i = 0; i < rank; ++i) {
+      double acc = 0;
+      for (int k = 0; k < r; ++k) acc += U[(size_t)i * r + k] * R12[(size_t)col * r + k];
+      W[(size_t)col * rank + i] = acc / sg[i];
+    }
+  std::vector<double> Tm((size_t)p * r, 0.0);  // row-major p x r
+  for (int a = 0; a < p; ++a)
+    for (int q = 0; q < r; ++q) {
+      double acc = 0;
+      for (int i = 0; i < rank; ++i) acc += V[(size_t)i * r + q] * W[(size_t)a * rank + i];
+      Tm[(size_t)a * r + q] = acc;
+    }
+  // Q(S, gamma) = [I, -T] on (S, beta), placed in gamma order
+  T.Q.assign((size_t)p * T.nG, 0.0);
+  {
+    int sidx = 0, bidx = 0;
+    for (int gi = 0; gi < T.nG; ++gi) {
+      bool inS = false;
+      // gamma order lists S and beta points in the same relative order
+      if (sidx < p) {
+        bool eq = true;
+        for (int a = 0; a < d; ++a)
+          if (T.G[(size_t)gi * d + a] != T.S[(size_t)sidx * d + a]) eq = false;
+        inS = eq;
+      }
+      if (inS) {
+        T.Q[(size_t)sidx * T.nG + gi] = 1.0;
+        ++sidx;
+      } else {
+        for (int a = 0; a < p; ++a) T.Q[(size_t)a * T.nG + gi] = -Tm[(size_t)a * r + bidx];
+        ++bidx;
+      }
+    }
+    if (sidx != p || bidx != r) return 2;
+  }
+  // C(S, gamma) = Q(S, gamma) G(gamma, gamma)
+  std::vector<double> Ggg((size_t)T.nG * T.nG);
+  for (int i = 0; i < T.nG; ++i)
+    for (int j = 0; j < T.nG; ++j) {
+      int dp[3];
+      for (int a = 0; a < d; ++a) dp[a] = T.G[(size_t)i * d + a] - T.G[(size_t)j * d + a];
+      Ggg[(size_t)i * T.nG + j] = g[flat_of(dp, d, n)];
+    }
+  T.C.assign((size_t)p * T.nG, 0.0);
+  for (int a = 0; a < p; ++a)
+    for (int i = 0; i < T.nG; ++i) {
+      double qa = T.Q[(size_t)a * T.nG + i];
+      if (qa == 0.0) continue;
+      const double* gr = &Ggg[(size_t)i * T.nG];
+      double* cr = &T.C[(size_t)a * T.nG];
+      for (int j = 0; j < T.nG; ++j) cr[j] += qa * gr[j];
+    }
+  return 0;
+}
+
+// ---------------------------------------------------------------- symbolic ND
+int front_sizes(int d, int n, int b, std::vector<int>* nf, std::vector<int>* k,
+                std::vector<int>* m) {
+  int L;
+  if (check_grid(d, n, b, &L)) return 1;
+  nf->clear();
+  k->clear();
+  m->clear();
+  auto pw = [&](long x) {
+    long r = 1;
+    for (int a = 0; a < d; ++a) r *= x;
+    return r;
+  };
+  for (int l = 0; l < L; ++l) {
+    long B = (long)b << l;
+    long kk = pw(B - 1) - (l == 0 ? 0 : (1L << d) * pw(B / 2 - 1));
+    long mm = kk + pw(B + 1) - pw(B - 1);
+    nf->push_back((int)pw(n / B));
+    k->push_back((int)kk);
+    m->push_back((int)mm);
+  }
+  long kr = pw(n) - (1L << d) * pw(n / 2 - 1);
+  nf->push_back(1);
+  k->push_back((int)kr);
+  m->push_back((int)kr);
+  return 0;
+}
+
+int build_symbolic(int d, int n, int b, const std::vector<StencilTable>& tabs, Symbolic* out) {
+  int L;
+  if (check_grid(d, n, b, &L)) return 1;
+  Symbolic& S = *out;
+  S.d = d;
+  S.n = n;
+  S.b = b;
+  S.L = L;
+  S.lv.assign(L + 1, Level());
+  long N = 1;
+  for (int a = 0; a < d; ++a) N *= n;
+  // elimination level of every point
+  std::vector<signed char> lev(N);
+  for (long j = 0; j < N; ++j) {
+    int pc[3];
+    long jj = j;
+    for (int a = 0; a < d; ++a) {
+      pc[a] = (int)(jj % n);
+      jj /= n;
+    }
+    int l = 0;
+    for (; l < L; ++l) {
+      int B = b << l;
+      bool interior = true;
+      for (int a = 0; a < d; ++a)
+        if (pc[a] % B == 0) interior = false;
+      if (interior) break;
+    }
+    lev[j] = (signed char)l;
+  }
+  // table offsets in the concatenated column-major tables
+  std::vector<long> toff(tabs.size() + 1, 0);
+  for (size_t t = 0; t < tabs.size(); ++t) toff[t + 1] = toff[t] + (long)tabs[t].nS * tabs[t].nG;
+
+  std::vector<int> pos(N, -1);
+  for (int l = 0; l <= L; ++l) {
+    Level& V = S.lv[l];
+    V.lev = l;
+    V.B = (l < L) ? (b << l) : n;
+    V.nb1 = n / V.B;
+    V.nf = 1;
+    for (int a = 0; a < d; ++a) V.nf *= V.nb1;
+    // front unknowns of box 0: eliminated ones, then the boundary
+    std::vector<int> el, bd;
+    if (l < L) {
+      int lo[3], hi[3];
+      for (int a = 0; a < d; ++a) {
+        lo[a] = 0;
+        hi[a] = V.B;
+      }
+      std::vector<int> cl = box_points(d, lo, hi);
+      int ncl = (int)cl.size() / d;
+      for (int i = 0; i < ncl; ++i) {
+        const int* p = &cl[(size_t)i * d];
+        bool onb = false;
+        for (int a = 0; a < d; ++a)
+          if (p[a] == 0 || p[a] == V.B) onb = true;
+        if (onb) {
+          bd.insert(bd.end(), p, p + d);
+        } else if (lev[flat_of(p, d, n)] == l) {
+          el.insert(el.end(), p, p + d);
+        }
+      }
+    } else {
+      for (long j = 0; j < N; ++j)
+        if (lev[j] == L) {
+          long jj = j;
+          for (int a = 0; a < d; ++a) {
+            el.push_back((int)(jj % n));
+            jj /= n;
+          }
+        }
+    }
+    V.k = (int)el.size() / d;
+    V.m = V.k + (int)bd.size() / d;
+    V.off = el;
+    V.off.insert(V.off.end(), bd.begin(), bd.end());
+    // global indices of every front
+    V.gidx.resize((size_t)V.nf * V.m);
+    for (int f = 0; f < V.nf; ++f) {
+      int bc[3];
+      int ff = f;
+      for (int a = 0; a < d; ++a) {
+        bc[a] = ff % V.nb1;
+        ff /= V.nb1;
+      }
+      for (int v = 0; v < V.m; ++v) {
+        int p[3];
+        for (int a = 0; a < d; ++a) p[a] = bc[a] * V.B + V.off[(size_t)v * d + a];
+        V.gidx[(size_t)f * V.m + v] = (int)flat_of(p, d, n);
+      }
+    }
+    // position map of box 0
+    for (int v = 0; v < V.m; ++v) pos[V.gidx[v]] = v;
+    // assembly list: P entries (row j of set S, column i in gamma(S)) whose
+    // earlier-eliminated endpoint is eliminated in box 0 of this level
+    std::vector<std::array<int, 3>> origins;
+    {
+      int nl = n / b;  // leaf boxes per axis
+      int lo = (l < L) ? -1 : 0, hi = (l < L) ? V.B / b : nl - 1;
+      std::unordered_map<long, int> uniq;
+      int cnt = 1;
+      for (int a = 0; a < d; ++a) cnt *= (hi - lo + 1);
+      for (int c = 0; c < cnt; ++c) {
+        int cc = c;
+        std::array<int, 3> o{0, 0, 0};
+        long key = 0, sc = 1;
+        bool keep = true;
+        for (int a = 0; a < d; ++a) {
+          int ia = lo + cc % (hi - lo + 1);
+          cc /= (hi - lo + 1);
+          ia = ((ia % nl) + nl) % nl;
+          o[a] = ia * b;
+          key += (long)ia * sc;
+          sc *= nl;
+        }
+        if (l == L) {
+          // only leaf boxes whose closure (+1 layer) touches a root plane
+          keep = false;
+          int h2 = n / 2;
+          for (int a = 0; a < d && !keep; ++a)
+            for (int v = o[a] - 1; v <= o[a] + b + 1; ++v)
+              if ((((v % n) + n) % n) % h2 == 0) {
+                keep = true;
+                break;
+              }
+        }
+        if (!keep) continue;
+        if (uniq.count(key)) continue;
+        uniq[key] = 1;
+        origins.push_back(o);
+      }
+    }
+    for (size_t t = 0; t < tabs.size(); ++t) {
+      const StencilTable& tb = tabs[t];
+      for (const auto& o : origins) {
+        for (int a = 0; a < tb.nS; ++a) {
+          int pj[3];
+          for (int ax = 0; ax < d; ++ax) pj[ax] = o[ax] + tb.S[(size_t)a * d + ax];
+          long j = flat_of(pj, d, n);
+          int lj = lev[j];
+          for (int c = 0; c < tb.nG; ++c) {
+            int pi[3];
+            for (int ax = 0; ax < d; ++ax) pi[ax] = o[ax] + tb.G[(size_t)c * d + ax];
+            long i = flat_of(pi, d, n);
+            int li = lev[i];
+            int lm = std::min(lj, li);
+            if (lm != l) continue;
+            long e = (lj <= li) ? j : i;
+            if (l < L) {
+              // eliminated in box 0 iff all coordinates lie in [1, B-1]
+              long ee = e;
+              bool inb = true;
+              for (int ax = 0; ax < d; ++ax) {
+                int v = (int)(ee % n);
+                ee /= n;
+                if (v < 1 || v > V.B - 1) inb = false;
+              }
+              if (!inb) continue;
+            }
+            int rp = pos[j], cp = pos[i];
+            if (rp < 0 || cp < 0) return 3;  // structural error
+            V.asm_slot.push_back(rp + cp * V.m);
+            V.asm_tidx.push_back((int)(toff[t] + a + (long)c * tb.nS));
+            V.asm_cvar.push_back(cp);
+          }
+        }
+      }
+    }
+    // extend-add maps from the children (level l-1)
+    if (l >= 1) {
+      const Level& C = S.lv[l - 1];
+      V.mc = C.m;
+      V.kc = C.k;
+      int nbd = C.m - C.k;
+      V.ea_map.assign((size_t)(1 << d) * nbd, -1);
+      int half = C.B;
+      for (int dl = 0; dl < (1 << d); ++dl)
+        for (int v = 0; v < nbd; ++v) {
+          int p[3];
+          for (int a = 0; a < d; ++a) p[a] = ((dl >> a) & 1) * half + C.off[(size_t)(C.k + v) * d + a];
+          int pp = pos[flat_of(p, d, n)];
+          if (pp < 0) return 4;
+          V.ea_map[(size_t)dl * nbd + v] = pp;
+        }
+    }
+    // clear the position map
+    for (int v = 0; v < V.m; ++v) pos[V.gidx[v]] = -1;
+  }
+  return 0;
+}
+
+}  // namespace sp

@@ -1,0 +1,63 @@
+// Host-side set-up of the sparsifying preconditioner: Green's kernel, stencil
+// tables (Section 2.3) and the periodic nested-dissection structure (Fig. nd).
+// Plain C++; no CUDA types.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+namespace sp {
+
+// One stencil type (Section 2.3): cell, face, edge or vertex of a given orientation.
+// Type t = sum over axes a with p_a = 0 (mod b) of 2^a.  Offsets are relative to the
+// leaf-box origin, d ints per point, points ordered with axis 0 fastest.
+struct StencilTable {
+  int t = 0, nS = 0, nG = 0, nB = 0, rank = 0;
+  std::vector<int> S, G, Bt;        // set, gamma(set), beta(set) = gamma minus set
+  std::vector<double> Q, C;          // nS x nG, row-major
+  std::vector<double> sigma;         // singular values of G(beta, gamma^c), descending
+};
+
+// One level of the nested-dissection tree.  Level 0 holds the leaf boxes of side b,
+// level l boxes of side b*2^l, level L the root (the whole torus).  Every front of a
+// level has the same size: k eliminated unknowns first, then m - k boundary unknowns.
+struct Level {
+  int lev = 0, B = 0, nb1 = 0, nf = 0, k = 0, m = 0;
+  std::vector<int> off;       // m x d local offsets of the front unknowns (box 0)
+  std::vector<int> gidx;      // nf x m global flat indices
+  // assembly of the original entries of P whose earlier-eliminated endpoint is
+  // eliminated in this front (same list for every front of the level)
+  std::vector<int> asm_slot;  // r + c*m (column-major front)
+  std::vector<int> asm_tidx;  // index into the concatenated column-major Q/C tables
+  std::vector<int> asm_cvar;  // front position of the column point (for q)
+  // extend-add: child position delta (0..2^d-1) -> map of the child's m_c - k_c
+  // boundary unknowns to positions of this front
+  int mc = 0, kc = 0;
+  std::vector<int> ea_map;    // 2^d x (mc - kc)
+};
+
+struct Symbolic {
+  int d = 0, n = 0, b = 0, L = 0;
+  std::vector<Level> lv;
+};
+
+// g = inverse DFT of 1/(4 pi^2 |k|^2 - s) with the 1/N of the unitary pair (Eq. G):
+// G(i, j) = g[(i - j) mod n].  Flat, axis 0 fastest.
+std::vector<double> green_kernel(int d, int n, double s);
+
+// min_k |kappa - |k|^2| / max(1, kappa), kappa = s / (4 pi^2).
+double resonance_gap(int d, int n, double s);
+
+// Tables of one type (Section 2.3).  g: the Green kernel.
+int stencil_table(int d, int n, int b, int t, const std::vector<double>& g, int threads,
+                  StencilTable* out);
+
+// Nested-dissection structure.
+int build_symbolic(int d, int n, int b, const std::vector<StencilTable>& tabs, Symbolic* out);
+
+// Level sizes only (cheap).
+int front_sizes(int d, int n, int b, std::vector<int>* nf, std::vector<int>* k,
+                std::vector<int>* m);
+
+int check_grid(int d, int n, int b, int* L);
+
+}  // namespace sp

@@ -1,0 +1,132 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/sp.h"
+#include "sp_host.h"
+
+namespace sp {
+
+// Optional per-kernel-class timing with CUDA events on the launching stream.
+enum ProfClass {
+  PROF_ASSEMBLE = 0,  // zeroing, assembly of P, extend-add, front scale
+  PROF_LU_PANEL = 1,
+  PROF_LU_TRSM = 2,
+  PROF_LU_GEMM = 3,
+  PROF_QAPPLY = 4,
+  PROF_FORWARD = 5,
+  PROF_BACKWARD = 6,
+  PROF_FFT = 7,
+  PROF_KRYLOV = 8,
+  PROF_NCLASS = 9
+};
+struct Profiler {
+  struct Rec {
+    int cls;
+    cudaEvent_t a, b;
+    double work;
+    int launches;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  cudaEvent_t get();
+  int begin(int cls, cudaStream_t st);
+  void end(int tok, double work, int launches, cudaStream_t st);
+  // sums per class (ms, launches, work) and resets
+  cudaError_t read(double* ms, int* launches, double* work, int cap);
+  void destroy();
+};
+extern thread_local Profiler* g_prof;
+struct ProfScope {
+  int tok = -1;
+  ProfScope(int cls, cudaStream_t st) {
+    if (g_prof) tok = g_prof->begin(cls, st);
+  }
+  void done(double work, int launches, cudaStream_t st) {
+    if (g_prof && tok >= 0) g_prof->end(tok, work, launches, st);
+    tok = -1;
+  }
+};
+
+// Per-level device data of the multifrontal factor (fronts column-major, m x m).
+struct DevLevel {
+  int nf = 0, k = 0, m = 0, nb1 = 0, mc = 0, kc = 0, nasm = 0;
+  int* gidx = nullptr;      // nf x m
+  int* asm_slot = nullptr;  // nasm
+  int* asm_tidx = nullptr;
+  int* asm_cvar = nullptr;
+  int* ea_map = nullptr;    // 2^d x (mc - kc)
+  void* front = nullptr;    // nf x m x m of double (FP64) or float (FP32)
+  int* perm = nullptr;      // nf x k row permutation of the eliminated block
+  int* piv = nullptr;       // nf x k pivot rows (LAPACK style, 0-based within the front)
+  double* scale = nullptr;  // nf: max |entry| of the assembled front
+  void* upd = nullptr;      // nf x (m - k) complex update vectors of the forward sweep
+  void* y = nullptr;        // nf x k complex forward-sweep results
+};
+
+// ---------------------------------------------------------------- FFT (sp_fft.cu)
+struct FftPlan {
+  int d = 0, n = 0, logn = 0;
+  double2* tw = nullptr;   // exp(-2 pi i t / n), t < n/2
+  double* Dn = nullptr;    // 1 / (4 pi^2 |k|^2 - s) / N, flat
+  double2* tmp = nullptr;  // N work
+};
+// w = x + G (q x) when q != null and add_x; g = G f when q == null and !add_x.
+cudaError_t fft_green_apply(const FftPlan& P, const double2* x, const double* q, bool add_x,
+                            double2* out, cudaStream_t st);
+
+// ---------------------------------------------------------------- factor (sp_factor.cu)
+cudaError_t factor_level(int prec, int d, DevLevel& L, const DevLevel* child, const double* Qcat,
+                         const double* Ccat, const double* q, double pivot_tol, int* status,
+                         cudaStream_t st);
+
+// ---------------------------------------------------------------- solve (sp_solve.cu)
+struct QTypeDev {
+  int nS = 0, nG = 0;
+  int* S = nullptr;  // nS x d offsets
+  int* G = nullptr;  // nG x d offsets
+  long tab_off = 0;  // offset of the type in the concatenated column-major tables
+};
+// y = Q r (vector type VT = double2 (FP64) or float2 (FP32) for y; r is complex128).
+cudaError_t q_apply(int prec, int d, int n, int nl, const std::vector<QTypeDev>& types,
+                    const double* Qcat, const float* Qcat32, const double2* r, void* y,
+                    cudaStream_t st);
+cudaError_t forward_level(int prec, int d, DevLevel& L, const DevLevel* child, const void* rhsQ,
+                          cudaStream_t st);
+cudaError_t backward_level(int prec, int d, DevLevel& L, double2* x, cudaStream_t st);
+
+// ---------------------------------------------------------------- Krylov (sp_krylov.cu)
+struct KrylovWork {
+  int nblk = 0;            // CTAs of the reduction kernels
+  double2* partial = nullptr;  // nblk x (maxv + 1)
+  double2* h = nullptr;        // maxv + 1 (current Hessenberg column, device)
+  double* nrm = nullptr;       // scalars
+};
+// h[0..nv) = V[0..nv)^H w  (V rows of length N, stride ldv)
+cudaError_t kr_dots(const double2* V, long ldv, int nv, const double2* w, long N,
+                    KrylovWork& K, double2* h_out, cudaStream_t st);
+// w -= V h; if h2_out != null also h2 = V^H w (after the update)
+cudaError_t kr_update_dots(const double2* V, long ldv, int nv, double2* w, long N,
+                           const double2* h, KrylovWork& K, double2* h2_out, cudaStream_t st);
+// nrm_out[0] = ||w||_2
+cudaError_t kr_norm(const double2* w, long N, KrylovWork& K, double* nrm_out, cudaStream_t st);
+// y = x * (1 / nrm[0])
+cudaError_t kr_scale(const double2* x, long N, const double* nrm, double2* y, cudaStream_t st);
+// y = a - b
+cudaError_t kr_sub(const double2* a, const double2* b, long N, double2* y, cudaStream_t st);
+// Hessenberg column j: H[0..j] = h1 + h2, H[j+1] = nrm; apply Givens; write estimate.
+cudaError_t kr_givens(double2* H, int ldh, int j, const double2* h1, const double2* h2,
+                      const double* nrm, double* cs, double2* sn, double2* gam, double* est,
+                      cudaStream_t st);
+// y = R^{-1} gam (upper triangular k x k in H), then u += Z y
+cudaError_t kr_update_solution(const double2* H, int ldh, int k, const double2* gam,
+                               double2* y, const double2* Z, long ldz, long N, double2* u,
+                               cudaStream_t st);
+// gam = [beta, 0, ...]; V0 = r / beta
+cudaError_t kr_start(const double2* r, long N, const double* nrm, double2* V0, double2* gam,
+                     int len, cudaStream_t st);
+
+}  // namespace sp

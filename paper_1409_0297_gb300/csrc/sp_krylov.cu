@@ -1,0 +1,295 @@
+// FP64 Arnoldi / GMRES kernels (Saad and Schultz; the outer iteration of Section 2):
+// classical Gram-Schmidt applied twice, norms, Givens rotations and the solution
+// update.  Reductions are two-phase (per-CTA partials, then a fixed-order sum) so
+// results are deterministic run to run.
+#include "sp_internal.h"
+
+namespace sp {
+
+namespace {
+
+constexpr int kThr = 256;
+
+__device__ __forceinline__ double2 conj_mul(double2 a, double2 b) {  // conj(a) * b
+  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -a.y * b.x));
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void chunk_of(long N, long* c0, long* c1) {
+  long per = (N + gridDim.x - 1) / gridDim.x;
+  *c0 = (long)blockIdx.x * per;
+  *c1 = min(N, *c0 + per);
+}
+
+// partial[j * nblk + blk] = sum over the CTA's chunk of conj(V_j) w
+__device__ void chunk_dots(const double2* V, long ldv, int nv, const double2* w, long c0, long c1,
+                           double2* partial) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = warp; j < nv; j += nw) {
+    const double2* v = V + (long)j * ldv;
+    double sr = 0, si = 0;
+    for (long i = c0 + lane; i < c1; i += 32) {
+      double2 p = conj_mul(v[i], w[i]);
+      sr += p.x;
+      si += p.y;
+    }
+    sr = warp_sum(sr);
+    si = warp_sum(si);
+    if (lane == 0) partial[(long)j * gridDim.x + blockIdx.x] = make_double2(sr, si);
+  }
+}
+
+__global__ void __launch_bounds__(kThr) dots_kernel(const double2* V, long ldv, int nv,
+                                                    const double2* w, long N, double2* partial) {
+  long c0, c1;
+  chunk_of(N, &c0, &c1);
+  chunk_dots(V, ldv, nv, w, c0, c1, partial);
+}
+
+__global__ void __launch_bounds__(kThr) update_dots_kernel(const double2* V, long ldv, int nv,
+                                                           double2* w, long N, const double2* h,
+                                                           double2* partial) {
+  __shared__ double2 hs[1024];
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) hs[j] = h[j];
+  __syncthreads();
+  long c0, c1;
+  chunk_of(N, &c0, &c1);
+  for (long i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+    double2 acc = w[i];
+    for (int j = 0; j < nv; ++j) {
+      double2 v = V[(long)j * ldv + i], hj = hs[j];
+      acc.x -= fma(v.x, hj.x, -v.y * hj.y);
+      acc.y -= fma(v.x, hj.y, v.y * hj.x);
+    }
+    w[i] = acc;
+  }
+  if (partial) {
+    __syncthreads();
+    chunk_dots(V, ldv, nv, w, c0, c1, partial);
+  }
+}
+
+// out[j] = sum_b partial[j * nblk + b]  (one warp per j, fixed order)
+__global__ void reduce_partials_kernel(const double2* partial, int nblk, int nv, double2* out) {
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= nv) return;
+  double sr = 0, si = 0;
+  for (int b = lane; b < nblk; b += 32) {
+    double2 p = partial[(long)j * nblk + b];
+    sr += p.x;
+    si += p.y;
+  }
+  sr = warp_sum(sr);
+  si = warp_sum(si);
+  if (lane == 0) out[j] = make_double2(sr, si);
+}
+
+__global__ void __launch_bounds__(kThr) norm2_kernel(const double2* w, long N, double2* partial) {
+  long c0, c1;
+  chunk_of(N, &c0, &c1);
+  double s = 0;
+  for (long i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+    double2 v = w[i];
+    s = fma(v.x, v.x, fma(v.y, v.y, s));
+  }
+  __shared__ double red[kThr / 32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    partial[blockIdx.x] = make_double2(t, 0);
+  }
+}
+
+__global__ void sqrt_kernel(const double2* s, double* out) { out[0] = sqrt(s[0].x); }
+
+__global__ void scale_kernel(const double2* x, long N, const double* nrm, double2* y) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double a = nrm[0] > 0 ? 1.0 / nrm[0] : 0.0;
+  double2 v = x[i];
+  y[i] = make_double2(v.x * a, v.y * a);
+}
+
+__global__ void sub_kernel(const double2* a, const double2* b, long N, double2* y) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  y[i] = make_double2(a[i].x - b[i].x, a[i].y - b[i].y);
+}
+
+__global__ void start_kernel(const double2* r, long N, const double* nrm, double2* V0, double2* gam,
+                             int len) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  double beta = nrm[0];
+  if (i < N) {
+    double a = beta > 0 ? 1.0 / beta : 0.0;
+    V0[i] = make_double2(r[i].x * a, r[i].y * a);
+  }
+  if (i < len) gam[i] = make_double2(i == 0 ? beta : 0.0, 0.0);
+}
+
+__device__ __forceinline__ double cabs2(double2 a) { return hypot(a.x, a.y); }
+
+// Column j of the Hessenberg matrix, earlier rotations, a new rotation, the
+// residual estimate |gamma_{j+1}|.  Single thread.
+__global__ void givens_kernel(double2* H, int ldh, int j, const double2* h1, const double2* h2,
+                              const double* nrm, double* cs, double2* sn, double2* gam,
+                              double* est) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double2* col = H + (long)j * ldh;
+  for (int i = 0; i <= j; ++i) col[i] = make_double2(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
+  col[j + 1] = make_double2(nrm[0], 0.0);
+  for (int i = 0; i < j; ++i) {
+    double c = cs[i];
+    double2 s = sn[i], a = col[i], b = col[i + 1];
+    // [c, s; -conj(s), c] (a, b)
+    double2 t0 = make_double2(c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x));
+    double2 t1 = make_double2(-(s.x * a.x + s.y * a.y) + c * b.x, -(s.x * a.y - s.y * a.x) + c * b.y);
+    col[i] = t0;
+    col[i + 1] = t1;
+  }
+  double2 a = col[j], b = col[j + 1];
+  double c;
+  double2 s;
+  double aa = cabs2(a), bb = cabs2(b);
+  if (bb == 0.0) {
+    c = 1.0;
+    s = make_double2(0, 0);
+  } else if (aa == 0.0) {
+    c = 0.0;
+    s = make_double2(1, 0);
+  } else {
+    double r = hypot(aa, bb);
+    c = aa / r;
+    // s = (a/|a|) conj(b) / r
+    double2 ua = make_double2(a.x / aa, a.y / aa);
+    s = make_double2((ua.x * b.x + ua.y * b.y) / r, (ua.y * b.x - ua.x * b.y) / r);
+  }
+  cs[j] = c;
+  sn[j] = s;
+  col[j] = make_double2(c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x));
+  col[j + 1] = make_double2(0, 0);
+  double2 g = gam[j];
+  gam[j + 1] = make_double2(-(s.x * g.x + s.y * g.y), -(s.x * g.y - s.y * g.x));
+  gam[j] = make_double2(c * g.x, c * g.y);
+  est[0] = cabs2(gam[j + 1]);
+  est[1] = nrm[0];
+}
+
+// y = R^{-1} gam (upper triangular, column-major, leading dimension ldh); one CTA
+__global__ void trisolve_kernel(const double2* H, int ldh, int k, const double2* gam, double2* y) {
+  __shared__ double2 g[1024];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) g[i] = gam[i];
+  __syncthreads();
+  for (int j = k - 1; j >= 0; --j) {
+    __shared__ double2 yj;
+    if (threadIdx.x == 0) {
+      double2 r = H[j + (long)j * ldh], v = g[j];
+      double den = r.x * r.x + r.y * r.y;
+      yj = make_double2((v.x * r.x + v.y * r.y) / den, (v.y * r.x - v.x * r.y) / den);
+      y[j] = yj;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+      double2 r = H[i + (long)j * ldh];
+      g[i].x -= r.x * yj.x - r.y * yj.y;
+      g[i].y -= r.x * yj.y + r.y * yj.x;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void combine_kernel(const double2* Z, long ldz, int k, const double2* y, long N,
+                               double2* u) {
+  __shared__ double2 ys[1024];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = y[j];
+  __syncthreads();
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double2 acc = u[i];
+  for (int j = 0; j < k; ++j) {
+    double2 z = Z[(long)j * ldz + i], c = ys[j];
+    acc.x += z.x * c.x - z.y * c.y;
+    acc.y += z.x * c.y + z.y * c.x;
+  }
+  u[i] = acc;
+}
+
+}  // namespace
+
+cudaError_t kr_dots(const double2* V, long ldv, int nv, const double2* w, long N, KrylovWork& K,
+                    double2* h_out, cudaStream_t st) {
+  ProfScope ps(PROF_KRYLOV, st);
+  dots_kernel<<<K.nblk, kThr, 0, st>>>(V, ldv, nv, w, N, K.partial);
+  reduce_partials_kernel<<<(nv + 7) / 8, 256, 0, st>>>(K.partial, K.nblk, nv, h_out);
+  ps.done(16.0 * N * (nv + 1), 2, st);
+  return cudaGetLastError();
+}
+
+cudaError_t kr_update_dots(const double2* V, long ldv, int nv, double2* w, long N,
+                           const double2* h, KrylovWork& K, double2* h2_out, cudaStream_t st) {
+  ProfScope ps(PROF_KRYLOV, st);
+  update_dots_kernel<<<K.nblk, kThr, 0, st>>>(V, ldv, nv, w, N, h, h2_out ? K.partial : nullptr);
+  if (h2_out) reduce_partials_kernel<<<(nv + 7) / 8, 256, 0, st>>>(K.partial, K.nblk, nv, h2_out);
+  ps.done(16.0 * N * (nv + 2), h2_out ? 2 : 1, st);
+  return cudaGetLastError();
+}
+
+cudaError_t kr_norm(const double2* w, long N, KrylovWork& K, double* nrm_out, cudaStream_t st) {
+  ProfScope ps(PROF_KRYLOV, st);
+  norm2_kernel<<<K.nblk, kThr, 0, st>>>(w, N, K.partial);
+  reduce_partials_kernel<<<1, 32, 0, st>>>(K.partial, K.nblk, 1, K.h + 1023);
+  sqrt_kernel<<<1, 1, 0, st>>>(K.h + 1023, nrm_out);
+  ps.done(16.0 * N, 3, st);
+  return cudaGetLastError();
+}
+
+cudaError_t kr_scale(const double2* x, long N, const double* nrm, double2* y, cudaStream_t st) {
+  ProfScope ps(PROF_KRYLOV, st);
+  scale_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(x, N, nrm, y);
+  ps.done(32.0 * N, 1, st);
+  return cudaGetLastError();
+}
+
+cudaError_t kr_sub(const double2* a, const double2* b, long N, double2* y, cudaStream_t st) {
+  ProfScope ps(PROF_KRYLOV, st);
+  sub_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(a, b, N, y);
+  ps.done(48.0 * N, 1, st);
+  return cudaGetLastError();
+}
+
+cudaError_t kr_givens(double2* H, int ldh, int j, const double2* h1, const double2* h2,
+                      const double* nrm, double* cs, double2* sn, double2* gam, double* est,
+                      cudaStream_t st) {
+  ProfScope ps(PROF_KRYLOV, st);
+  givens_kernel<<<1, 32, 0, st>>>(H, ldh, j, h1, h2, nrm, cs, sn, gam, est);
+  ps.done(0.0, 1, st);
+  return cudaGetLastError();
+}
+
+cudaError_t kr_update_solution(const double2* H, int ldh, int k, const double2* gam, double2* y,
+                               const double2* Z, long ldz, long N, double2* u, cudaStream_t st) {
+  ProfScope ps(PROF_KRYLOV, st);
+  trisolve_kernel<<<1, 256, 0, st>>>(H, ldh, k, gam, y);
+  combine_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(Z, ldz, k, y, N, u);
+  ps.done(16.0 * N * (k + 2), 2, st);
+  return cudaGetLastError();
+}
+
+cudaError_t kr_start(const double2* r, long N, const double* nrm, double2* V0, double2* gam,
+                     int len, cudaStream_t st) {
+  long n = N > len ? N : len;
+  ProfScope ps(PROF_KRYLOV, st);
+  start_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(r, N, nrm, V0, gam, len);
+  ps.done(32.0 * N, 1, st);
+  return cudaGetLastError();
+}
+
+}  // namespace sp

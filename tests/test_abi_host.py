@@ -1,0 +1,95 @@
+"""CPU tests of the C ABI: the library loads, exports every declared symbol, and its
+host-only logic (argument checks, nested-dissection sizes, stencil tables, medium
+split) agrees with the paper's formulas and with the oracle.  No GPU compute."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic_media as sm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _binding():
+    from paper_1409_0297_gb300 import build as bld
+    if not os.path.exists(bld.LIB):
+        bld.build()
+    from paper_1409_0297_gb300 import binding as B
+    return B
+
+
+def test_header_symbols_exported():
+    B = _binding()
+    hdr = open(os.path.join(ROOT, "include", "sp.h")).read()
+    declared = set(re.findall(r"\b(sp_[a-z_]+)\s*\(", hdr))
+    assert declared, "no declarations found"
+    for name in declared:
+        assert hasattr(B.LIB, name), name
+    assert declared == set(B.EXPORTED)
+
+
+@pytest.mark.parametrize("d,n,b", [(2, 64, 4), (2, 512, 16), (3, 128, 8), (2, 16, 2), (3, 16, 4)])
+def test_front_sizes_match_geometry(d, n, b):
+    """Level l < L: k = (B-1)^d - 2^d (B/2-1)^d (B-1)^d at the leaves), m = k + (B+1)^d - (B-1)^d;
+    root k = m = n^d - 2^d (n/2-1)^d (Section 2.3, Fig. nd)."""
+    B_ = _binding()
+    lv = B_.sp_front_sizes(d, n, b)
+    L = int(np.log2(n // b))
+    assert len(lv) == L + 1
+    total = 0
+    for l, (nf, k, m) in enumerate(lv[:-1]):
+        B = b << l
+        kk = (B - 1) ** d - (0 if l == 0 else 2 ** d * (B // 2 - 1) ** d)
+        assert (nf, k, m) == ((n // B) ** d, kk, kk + (B + 1) ** d - (B - 1) ** d)
+        total += nf * k
+    root = lv[-1]
+    assert root == (1, n ** d - 2 ** d * (n // 2 - 1) ** d, n ** d - 2 ** d * (n // 2 - 1) ** d)
+    assert total + root[1] == n ** d  # every unknown is eliminated exactly once
+
+
+def test_argument_checks_need_no_gpu():
+    B = _binding()
+    for args in [(2, 48, 4), (2, 64, 3), (4, 64, 4), (2, 8, 8), (2, 64, 1)]:
+        with pytest.raises(B.SpError) as e:
+            B.sp_setup(*args, s=100.0)
+        assert e.value.status == B.SP_ERR_ARG
+    # s = 4 pi^2 * 25 hits |k|^2 = 25: L - s singular
+    with pytest.raises(B.SpError) as e:
+        B.sp_setup(2, 64, 4, 4 * np.pi ** 2 * 25)
+    assert e.value.status == B.SP_ERR_RESONANT
+
+
+@pytest.mark.parametrize("d,n,b", [(2, 64, 4), (2, 24, 3), (3, 8, 2), (3, 16, 4)])
+def test_host_tables_match_oracle(d, n, b):
+    B = _binding()
+    s = 4 * np.pi ** 2 * (n / 6) ** 2 * 1.013
+    tabs = O.stencil_tables(d, n, b, s)
+    for t in range(1 << d):
+        Q, C, rank, sig = B.sp_stencil_table(d, n, b, s, t)
+        assert rank == tabs[t]["rank"]
+        assert np.linalg.norm(Q - tabs[t]["Q"]) <= 1e-11 * np.linalg.norm(tabs[t]["Q"])
+        assert np.linalg.norm(C - tabs[t]["C"]) <= 1e-11 * np.linalg.norm(tabs[t]["C"])
+        k = min(64, len(tabs[t]["sigma"]))
+        assert np.allclose(sig[:k], tabs[t]["sigma"][:k], rtol=1e-10, atol=0)
+
+
+def test_medium_split_matches_oracle():
+    B = _binding()
+    d, n = 2, 64
+    c = sm.grf_velocity(d, n, 0.1, 3)
+    s1, q1 = B.sp_medium_helmholtz(d, n, 2 * np.pi * 7, c)
+    s0, q0 = O.helmholtz_shift(d, n, 2 * np.pi * 7, c)
+    assert abs(s1 - s0) <= 1e-12 * abs(s0)
+    assert np.allclose(q1, q0, rtol=0, atol=1e-9 * abs(s0))
+    V = sm.lattice_wells_potential(d, n, 4.0, 5)
+    s1, q1 = B.sp_medium_schrodinger(d, n, 4.0, 3.0, V)
+    s0, q0 = O.schrodinger_shift(d, n, 4.0, 3.0, V)
+    assert abs(s1 - s0) <= 1e-12 * abs(s0)
+    assert np.allclose(q1, q0, rtol=0, atol=1e-9 * abs(s0))
+    # resonant: c = 1, omega = 2 pi 5 -> s/4pi^2 = 25 is moved off the lattice
+    s1, q1 = B.sp_medium_helmholtz(d, n, 2 * np.pi * 5, np.ones(n * n))
+    s0, q0 = O.helmholtz_shift(d, n, 2 * np.pi * 5, np.ones(n * n))
+    assert abs(s1 - s0) <= 1e-12 * s0 and s1 != (2 * np.pi * 5) ** 2
