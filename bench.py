@@ -49,12 +49,18 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-chosen", action="store_true")
+    p.add_argument("--profile-step", default=None, choices=["fp64", "fp32"],
+                   help="run exactly one untimed step (factor + solve of both problems) in the "
+                        "given form after set-up and exit: the command profiled under ncu")
+    p.add_argument("--problems", default="helmholtz,schrodinger",
+                   help="comma list of the step's problems (default both)")
     return p.parse_args()
 
 
-def problems():
-    """Host inputs of the two problems: (name, d, n, b, kind params, f)."""
-    return [sm.helmholtz_grf_512(0), sm.schrodinger_wells_512(0)]
+def problems(which="helmholtz,schrodinger"):
+    """Host inputs of the step's problems (dicts of synthetic_media)."""
+    make = {"helmholtz": sm.helmholtz_grf_512, "schrodinger": sm.schrodinger_wells_512}
+    return [make[w](0) for w in which.split(",")]
 
 
 # ------------------------------------------------------------------ clocks
@@ -165,7 +171,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
 
     probs = []
-    for w in problems():
+    for w in problems(args.problems):
         d, n, b = w["d"], w["n"], w["b"]
         if w["kind"] == "helmholtz":
             s, q = B.sp_medium_helmholtz(d, n, w["omega"], w["c"])
@@ -186,6 +192,21 @@ def run_ours(args):
         return out
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    if args.profile_step:
+        ctxs = make(B.SP_PREC_FP64 if args.profile_step == "fp64" else B.SP_PREC_FP32)
+        torch.cuda.synchronize()
+        infos = []
+        for c in ctxs:
+            c["S"].factor(c["q"])
+            infos.append(c["S"].solve(c["f"], c["u"]))
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_step": args.profile_step,
+                          "iters": [i["iters"] for i in infos],
+                          "true_relres": [i["true_relres"] for i in infos]}), flush=True)
+        for c in ctxs:
+            c["S"].close()
+        return
 
     def step(ctxs, infos=None):
         for c in ctxs:
@@ -273,7 +294,7 @@ def run_ours(args):
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
     fp64_peak_tflops = 1.25  # nominal GB300 FP64 rate (no FP64 entry in the measured peaks)
-    alu_classes = {"lu_panel", "lu_trsm", "lu_gemm"}
+    alu_classes = {"lu_panel", "lu_trsm", "lu_gemm", "lu_trinv"}
 
     def roof(k, vals):
         ms_, nl, wk = vals

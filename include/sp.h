@@ -178,9 +178,10 @@ sp_status sp_medium_schrodinger(int d, int n, double ell, double E, const double
  * stream.  sp_profile_read synchronises, writes per class c (0 assembly and
  * extend-add, 1 LU panels, 2 LU row-block solves, 3 LU Schur updates, 4 stencil
  * apply, 5 forward sweep, 6 backward sweep, 7 FFT passes, 8 Arnoldi/GMRES vector
- * kernels) the summed device milliseconds, the number of kernel launches and the
- * algorithmic work (flops for classes 1-3, bytes for the others: the data a
- * kernel must move at least once), then clears the record.  Arrays of cap >= 9. */
+ * kernels, 9 triangular inverses of the few-front levels) the summed device
+ * milliseconds, the number of kernel launches and the algorithmic work (flops
+ * for classes 1-3 and 9, bytes for the others: the data a kernel must move at
+ * least once), then clears the record.  Arrays of cap >= 10. */
 sp_status sp_profile(sp_ctx *ctx, int enable);
 sp_status sp_profile_read(sp_ctx *ctx, int cap, double *ms, int *launches, double *work);
 

@@ -26,7 +26,7 @@ EXPORTED = [
     "sp_profile_read", "sp_destroy", "sp_status_str",
 ]
 PROF_CLASSES = ["assemble", "lu_panel", "lu_trsm", "lu_gemm", "qapply", "forward", "backward",
-                "fft", "krylov"]
+                "fft", "krylov", "lu_trinv"]
 
 
 class sp_opts(ctypes.Structure):

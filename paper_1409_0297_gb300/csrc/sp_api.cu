@@ -82,7 +82,9 @@ struct sp_ctx {
   std::vector<void*> allocs;
   double* Qcat = nullptr;
   double* Ccat = nullptr;
-  float* Qcat32 = nullptr;
+  double* Tcat = nullptr;
+  float* Tcat32 = nullptr;
+  void* scratch = nullptr;  // triangular-inverse work of the few-front levels
   FftPlan fft;
   const double* q = nullptr;  // current medium (caller's or qbuf)
   double* qbuf = nullptr;     // used by sp_factor_host
@@ -153,7 +155,7 @@ double perturb_shift(int d, int n, double s) {
 
 sp_status apply_impl(sp_ctx* c, const double2* r, double2* z) {
   cudaStream_t st = c->stream;
-  SP_CK(q_apply(c->prec, c->d, c->n, c->nl, c->qtypes, c->Qcat, c->Qcat32, r, c->rhsQ, st));
+  SP_CK(q_apply(c->prec, c->d, c->n, c->nl, c->qtypes, c->Tcat, c->Tcat32, r, c->rhsQ, st));
   for (int l = 0; l <= c->L; ++l)
     SP_CK(forward_level(c->prec, c->d, c->lv[l], l ? &c->lv[l - 1] : nullptr, c->rhsQ, st));
   for (int l = c->L; l >= 0; --l) SP_CK(backward_level(c->prec, c->d, c->lv[l], z, st));
@@ -370,36 +372,61 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   } catch (const std::bad_alloc&) {
     return SP_ERR_OOM;
   }
-  // ---- tables on the device (column-major per type, concatenated)
+  // ---- tables on the device (column-major per type, concatenated): Q and C on
+  // gamma for the assembly, T on beta for the stencil apply
   {
-    std::vector<double> Qc, Cc;
-    std::vector<float> Q32;
-    long off = 0;
+    std::vector<double> Qc, Cc, Tc;
+    std::vector<float> T32;
+    long off = 0, toff = 0;
     for (int t = 0; t < (1 << d); ++t) {
       const StencilTable& tb = c->tabs[t];
       QTypeDev qt;
       qt.nS = tb.nS;
       qt.nG = tb.nG;
+      qt.nB = tb.nB;
       qt.tab_off = off;
+      qt.t_off = toff;
       for (int col = 0; col < tb.nG; ++col)
         for (int a = 0; a < tb.nS; ++a) {
           Qc.push_back(tb.Q[(size_t)a * tb.nG + col]);
           Cc.push_back(tb.C[(size_t)a * tb.nG + col]);
-          Q32.push_back((float)tb.Q[(size_t)a * tb.nG + col]);
+        }
+      // T = -Q restricted to the beta columns (gamma order lists beta in beta order)
+      std::vector<int> bcols;
+      {
+        int sidx = 0;
+        for (int gi = 0; gi < tb.nG; ++gi) {
+          bool inS = sidx < tb.nS;
+          for (int a = 0; a < d && inS; ++a)
+            if (tb.G[(size_t)gi * d + a] != tb.S[(size_t)sidx * d + a]) inS = false;
+          if (inS) ++sidx;
+          else bcols.push_back(gi);
+        }
+      }
+      if ((int)bcols.size() != tb.nB) return SP_ERR_ARG;
+      for (int cb = 0; cb < tb.nB; ++cb)
+        for (int a = 0; a < tb.nS; ++a) {
+          double v = -tb.Q[(size_t)a * tb.nG + bcols[cb]];
+          Tc.push_back(v);
+          T32.push_back((float)v);
         }
       off += (long)tb.nS * tb.nG;
+      toff += (long)tb.nS * tb.nB;
       SP_CK(upload(c.get(), &qt.S, tb.S));
       SP_CK(upload(c.get(), &qt.G, tb.G));
+      SP_CK(upload(c.get(), &qt.Bt, tb.Bt));
       c->qtypes.push_back(qt);
     }
     SP_CK(upload(c.get(), &c->Qcat, Qc));
     SP_CK(upload(c.get(), &c->Ccat, Cc));
-    SP_CK(upload(c.get(), &c->Qcat32, Q32));
+    SP_CK(upload(c.get(), &c->Tcat, Tc));
+    SP_CK(upload(c.get(), &c->Tcat32, T32));
   }
   // ---- levels
   const size_t fsz = (prec == SP_PREC_FP32) ? sizeof(float) : sizeof(double);
   const size_t vsz = (prec == SP_PREC_FP32) ? sizeof(float2) : sizeof(double2);
   c->lv.resize(L + 1);
+  size_t scratch_bytes = 0;
   for (int l = 0; l <= L; ++l) {
     const Level& S = c->sym.lv[l];
     DevLevel& D = c->lv[l];
@@ -421,11 +448,19 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
     SP_CK(dalloc(c.get(), &D.scale, sizeof(double) * S.nf));
     SP_CK(dalloc(c.get(), &D.upd, vsz * (size_t)S.nf * std::max(1, S.m - S.k)));
     SP_CK(dalloc(c.get(), &D.y, vsz * (size_t)S.nf * std::max(1, S.k)));
+    if (factor_panel_width(prec, S.m) == 0) return SP_ERR_ARG;  // front too large to stage
+    // few fronts: keep the inverses of L11 and U11 so the sweeps spread over the GPU
+    D.inv = S.nf < 152;
+    if (D.inv) {
+      SP_CK(dalloc(c.get(), &D.tmp, vsz * (size_t)S.nf * S.m));
+      scratch_bytes = std::max(scratch_bytes, 2 * fsz * (size_t)S.nf * S.k * S.k);
+    }
     double k = S.k, mk = S.m - S.k;
     c->factor_entries += S.nf * (k * k + 2 * k * mk);
     c->factor_flops += S.nf * ((2.0 / 3.0) * k * k * k + 2 * k * k * mk + 2 * k * mk * mk);
   }
   c->apply_bytes = c->factor_entries * fsz;
+  if (scratch_bytes) SP_CK(dalloc(c.get(), &c->scratch, scratch_bytes));
   // ---- FFT plan
   {
     FftPlan& P = c->fft;
@@ -494,7 +529,7 @@ sp_status sp_factor(sp_ctx* c, const double* q_dev) {
   SP_CK(cudaMemsetAsync(c->status, 0, sizeof(int), st));
   for (int l = 0; l <= c->L; ++l)
     SP_CK(factor_level(c->prec, c->d, c->lv[l], l ? &c->lv[l - 1] : nullptr, c->Qcat, c->Ccat,
-                       q_dev, c->opts.pivot_tol, c->status, st));
+                       q_dev, c->opts.pivot_tol, c->status, c->scratch, st));
   int hs = 0;
   SP_CK(cudaMemcpyAsync(&hs, c->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   SP_CK(cudaStreamSynchronize(st));
@@ -522,13 +557,9 @@ sp_status sp_qapply(sp_ctx* c, const void* r_dev, void* y_dev) {
   if (!c || !r_dev || !y_dev) return SP_ERR_ARG;
   ProfGuard pg_(c);
   SP_CK(cudaSetDevice(c->opts.device));
-  if (c->prec == SP_PREC_FP64)
-    return cuda_status(q_apply(c->prec, c->d, c->n, c->nl, c->qtypes, c->Qcat, c->Qcat32,
-                               (const double2*)r_dev, y_dev, c->stream));
-  // FP32 form: stage through the context's buffer and widen
-  SP_CK(q_apply(SP_PREC_FP64, c->d, c->n, c->nl, c->qtypes, c->Qcat, c->Qcat32,
-                (const double2*)r_dev, y_dev, c->stream));
-  return SP_OK;
+  // always the FP64 tables: the output is complex128 in both forms
+  return cuda_status(q_apply(SP_PREC_FP64, c->d, c->n, c->nl, c->qtypes, c->Tcat, c->Tcat32,
+                             (const double2*)r_dev, y_dev, c->stream));
 }
 
 sp_status sp_matvec(sp_ctx* c, const void* x_dev, void* w_dev) {

@@ -71,87 +71,131 @@ __global__ void front_scale_kernel(const T* fronts, long mm, double* scale) {
   if (threadIdx.x == 0) scale[blockIdx.x] = red[0];
 }
 
-// Unblocked LU of the panel columns [j0, j0+jb) of every front (one CTA per front).
-// Pivot rows are searched among the eliminated rows [j, k) only; the swap moves
-// whole rows (all m columns), LAPACK style.
+// LU of the panel columns [j0, j0+jb) of every front (one CTA per front).  The
+// panel rows [j0, m) are staged in shared memory (column-major, leading
+// dimension rows = m - j0); pivot rows are searched among the eliminated rows
+// [j, k) only.  Row swaps inside the panel happen in shared memory; the same
+// swaps are applied here to the columns left of the panel and by the row-block
+// solve to the columns right of it (LAPACK-style full-row interchanges).
 template <class T>
 __global__ void __launch_bounds__(256) lu_panel_kernel(T* fronts, int m, int k, int j0, int jb,
                                                        int* piv, const double* scale,
                                                        double ptol, int* status) {
+  extern __shared__ unsigned char smraw[];
+  T* P = reinterpret_cast<T*>(smraw);
+  __shared__ double wv[8];
+  __shared__ int wi[8];
+  __shared__ int spiv[kNB];
   T* A = fronts + (long)blockIdx.x * m * m;
-  __shared__ double rv[256];
-  __shared__ int ri[256];
-  __shared__ T prow[kNB];
-  __shared__ int s_p;
+  const int rows = m - j0;
+  const int kl = k - j0;  // pivot candidates are local rows < kl
   const double thresh = ptol * scale[blockIdx.x];
-  for (int j = j0; j < j0 + jb; ++j) {
-    // argmax |A[r, j]| over r in [j, k), ties to the smallest row
+  for (long e = threadIdx.x; e < (long)rows * jb; e += blockDim.x) {
+    int r = (int)(e % rows), c = (int)(e / rows);
+    P[e] = A[(j0 + r) + (long)(j0 + c) * m];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int jj = 0; jj < jb; ++jj) {
+    T* pc = P + (long)jj * rows;
     double best = -1.0;
-    int bi = j;
-    for (int r = j + threadIdx.x; r < k; r += blockDim.x) {
-      double v = fabs((double)A[r + (long)j * m]);
+    int bi = jj;
+    for (int r = jj + threadIdx.x; r < kl; r += blockDim.x) {
+      double v = fabs((double)pc[r]);
       if (v > best) {
         best = v;
         bi = r;
       }
     }
-    rv[threadIdx.x] = best;
-    ri[threadIdx.x] = bi;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) {
-        double o = rv[threadIdx.x + s];
-        int oi = ri[threadIdx.x + s];
-        if (o > rv[threadIdx.x] || (o == rv[threadIdx.x] && oi < ri[threadIdx.x])) {
-          rv[threadIdx.x] = o;
-          ri[threadIdx.x] = oi;
-        }
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_down_sync(0xffffffffu, best, o);
+      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
       }
-      __syncthreads();
     }
+    if (lane == 0) {
+      wv[warp] = best;
+      wi[warp] = bi;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-      s_p = ri[0];
-      piv[(long)blockIdx.x * k + j] = ri[0];
-      if (!(rv[0] > thresh)) atomicOr(status, 1);
+      double b0 = wv[0];
+      int i0 = wi[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+        if (wv[w] > b0 || (wv[w] == b0 && wi[w] < i0)) {
+          b0 = wv[w];
+          i0 = wi[w];
+        }
+      spiv[jj] = i0;
+      piv[(long)blockIdx.x * k + j0 + jj] = j0 + i0;
+      if (!(b0 > thresh)) atomicOr(status, 1);
     }
     __syncthreads();
-    const int p = s_p;
-    if (p != j) {
-      for (int c = threadIdx.x; c < m; c += blockDim.x) {
-        T t = A[j + (long)c * m];
-        A[j + (long)c * m] = A[p + (long)c * m];
-        A[p + (long)c * m] = t;
+    const int p = spiv[jj];
+    if (p != jj)
+      for (int c = threadIdx.x; c < jb; c += blockDim.x) {
+        T t = P[jj + (long)c * rows];
+        P[jj + (long)c * rows] = P[p + (long)c * rows];
+        P[p + (long)c * rows] = t;
       }
-      __syncthreads();
-    }
-    for (int c = j + 1 + threadIdx.x; c < j0 + jb; c += blockDim.x) prow[c - j0] = A[j + (long)c * m];
     __syncthreads();
-    T pv = A[j + (long)j * m];
+    T pv = pc[jj];
     if (!(fabs((double)pv) > 0.0)) pv = (T)(thresh > 0 ? thresh : 1e-30);
     const T inv = (T)1 / pv;
-    for (int r = j + 1 + threadIdx.x; r < m; r += blockDim.x) {
-      T l = A[r + (long)j * m] * inv;
-      A[r + (long)j * m] = l;
-      for (int c = j + 1; c < j0 + jb; ++c) A[r + (long)c * m] -= l * prow[c - j0];
+    for (int r = jj + 1 + threadIdx.x; r < rows; r += blockDim.x) {
+      T l = pc[r] * inv;
+      pc[r] = l;
+      for (int c = jj + 1; c < jb; ++c) P[r + (long)c * rows] -= l * P[jj + (long)c * rows];
     }
     __syncthreads();
   }
+  for (long e = threadIdx.x; e < (long)rows * jb; e += blockDim.x) {
+    int r = (int)(e % rows), c = (int)(e / rows);
+    A[(j0 + r) + (long)(j0 + c) * m] = P[e];
+  }
+  // interchanges on the columns left of the panel
+  for (int c = threadIdx.x; c < j0; c += blockDim.x) {
+    T* col = A + (long)c * m;
+    for (int jj = 0; jj < jb; ++jj) {
+      int p = j0 + spiv[jj];
+      if (p != j0 + jj) {
+        T t = col[j0 + jj];
+        col[j0 + jj] = col[p];
+        col[p] = t;
+      }
+    }
+  }
 }
 
-// U12 row block: A[j0:j0+jb, c] = L_pp^{-1} A[j0:j0+jb, c] for c >= j0 + jb.
+// Row-block solve right of the panel: interchanges, then
+// A[j0:j0+jb, c] = L_pp^{-1} A[j0:j0+jb, c] for c >= j0 + jb (one thread per column).
 template <class T>
-__global__ void __launch_bounds__(256) lu_trsm_kernel(T* fronts, int m, int j0, int jb) {
+__global__ void __launch_bounds__(256) lu_trsm_kernel(T* fronts, int m, int k, int j0, int jb,
+                                                      const int* piv) {
   T* A = fronts + (long)blockIdx.y * m * m;
   __shared__ T Lp[kNB][kNB + 1];
+  __shared__ int sp_[kNB];
   for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) {
     int i = e % jb, l = e / jb;
     Lp[i][l] = A[(j0 + i) + (long)(j0 + l) * m];
   }
+  for (int e = threadIdx.x; e < jb; e += blockDim.x) sp_[e] = piv[(long)blockIdx.y * k + j0 + e];
   __syncthreads();
   int c = j0 + jb + blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= m) return;
+  T* colg = A + (long)c * m;
+  for (int jj = 0; jj < jb; ++jj) {
+    int p = sp_[jj];
+    if (p != j0 + jj) {
+      T t = colg[j0 + jj];
+      colg[j0 + jj] = colg[p];
+      colg[p] = t;
+    }
+  }
   T x[kNB];
-  T* col = A + (long)c * m + j0;
+  T* col = colg + j0;
 #pragma unroll
   for (int i = 0; i < kNB; ++i)
     if (i < jb) x[i] = col[i];
@@ -170,25 +214,30 @@ __global__ void __launch_bounds__(256) lu_trsm_kernel(T* fronts, int m, int j0, 
     if (i < jb) col[i] = x[i];
 }
 
-// Schur update of the trailing matrix: A[r, c] -= sum_l A[r, j0+l] A[j0+l, c],
-// r, c >= j0 + jb.  kTile x kTile per CTA, 4 x 4 per thread.
+// Batched C[M x N] -= A[M x K] B[K x N], K <= kNB, column-major with leading
+// dimensions lda/ldb/ldc and per-batch strides (blockIdx.y = batch).  kTile x
+// kTile per CTA, 4 x 4 per thread.  Used for the Schur update of the LU and for
+// the triangular inverses.
 template <class T>
-__global__ void __launch_bounds__(256) lu_gemm_kernel(T* fronts, int m, int j0, int jb, int tiles) {
-  T* A = fronts + (long)blockIdx.y * m * m;
-  const int base = j0 + jb;
-  const int tr = blockIdx.x % tiles, tc = blockIdx.x / tiles;
-  const int r0 = base + tr * kTile, c0 = base + tc * kTile;
+__global__ void __launch_bounds__(256) gemm_sub_kernel(int M, int N, int K, const T* A, int lda,
+                                                       long sA, const T* B, int ldb, long sB,
+                                                       T* C, int ldc, long sC, int tilesM) {
+  A += blockIdx.y * sA;
+  B += blockIdx.y * sB;
+  C += blockIdx.y * sC;
+  const int tr = blockIdx.x % tilesM, tc = blockIdx.x / tilesM;
+  const int r0 = tr * kTile, c0 = tc * kTile;
   __shared__ T As[kNB][kTile];
   __shared__ T Bs[kNB][kTile + 1];
-  for (int e = threadIdx.x; e < jb * kTile; e += blockDim.x) {
+  for (int e = threadIdx.x; e < K * kTile; e += blockDim.x) {
     int i = e % kTile, l = e / kTile;
     int r = r0 + i;
-    As[l][i] = (r < m) ? A[r + (long)(j0 + l) * m] : (T)0;
+    As[l][i] = (r < M) ? A[r + (long)l * lda] : (T)0;
   }
-  for (int e = threadIdx.x; e < jb * kTile; e += blockDim.x) {
-    int l = e % jb, jc = e / jb;
+  for (int e = threadIdx.x; e < K * kTile; e += blockDim.x) {
+    int l = e % K, jc = e / K;
     int c = c0 + jc;
-    Bs[l][jc] = (c < m) ? A[(j0 + l) + (long)c * m] : (T)0;
+    Bs[l][jc] = (c < N) ? B[l + (long)c * ldb] : (T)0;
   }
   __syncthreads();
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -197,7 +246,7 @@ __global__ void __launch_bounds__(256) lu_gemm_kernel(T* fronts, int m, int j0, 
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0;
-  for (int l = 0; l < jb; ++l) {
+  for (int l = 0; l < K; ++l) {
     T av[4], bv[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) av[a] = As[l][tx + 16 * a];
@@ -211,11 +260,11 @@ __global__ void __launch_bounds__(256) lu_gemm_kernel(T* fronts, int m, int j0, 
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
     int c = c0 + ty + 16 * b;
-    if (c >= m) continue;
+    if (c >= N) continue;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       int r = r0 + tx + 16 * a;
-      if (r < m) A[r + (long)c * m] -= acc[a][b];
+      if (r < M) C[r + (long)c * ldc] -= acc[a][b];
     }
   }
 }
@@ -233,10 +282,157 @@ __global__ void lu_perm_kernel(const int* piv, int* perm, int k, int nf) {
   }
 }
 
+// ---- explicit triangular inverses for levels with few fronts -------------------
+// X (k x k per front, leading dimension k) is set to the identity.
+template <class T>
+__global__ void set_identity_kernel(T* X, int k, long total) {
+  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  long w = e % ((long)k * k);
+  int r = (int)(w % k), c = (int)(w / k);
+  X[e] = (r == c) ? (T)1 : (T)0;
+}
+
+// Diagonal-block step of X = L11^{-1} (unit lower): rows [j0, j0+jb) of X,
+// columns [0, ncol), replaced by L_JJ^{-1} times themselves (one thread per column).
+template <class T>
+__global__ void trinv_lower_diag_kernel(const T* fronts, int m, T* X, int k, int j0, int jb, int ncol) {
+  const T* A = fronts + (long)blockIdx.y * m * m;
+  T* Xf = X + (long)blockIdx.y * k * k;
+  __shared__ T Lp[kNB][kNB + 1];
+  for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) {
+    int i = e % jb, l = e / jb;
+    Lp[i][l] = A[(j0 + i) + (long)(j0 + l) * m];
+  }
+  __syncthreads();
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncol) return;
+  T* col = Xf + (long)c * k + j0;
+  T x[kNB];
+#pragma unroll
+  for (int i = 0; i < kNB; ++i)
+    if (i < jb) x[i] = col[i];
+#pragma unroll
+  for (int i = 1; i < kNB; ++i)
+    if (i < jb) {
+      T acc = x[i];
+#pragma unroll
+      for (int l = 0; l < kNB; ++l)
+        if (l < i) acc -= Lp[i][l] * x[l];
+      x[i] = acc;
+    }
+#pragma unroll
+  for (int i = 0; i < kNB; ++i)
+    if (i < jb) col[i] = x[i];
+}
+
+// Diagonal-block step of X = U11^{-1} (upper, non-unit): rows [j0, j0+jb) of X,
+// columns [c_lo, k), replaced by U_JJ^{-1} times themselves.
+template <class T>
+__global__ void trinv_upper_diag_kernel(const T* fronts, int m, T* X, int k, int j0, int jb) {
+  const T* A = fronts + (long)blockIdx.y * m * m;
+  T* Xf = X + (long)blockIdx.y * k * k;
+  __shared__ T Up[kNB][kNB + 1];
+  for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) {
+    int i = e % jb, l = e / jb;
+    Up[i][l] = A[(j0 + i) + (long)(j0 + l) * m];
+  }
+  __syncthreads();
+  int c = j0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= k) return;
+  T* col = Xf + (long)c * k + j0;
+  T x[kNB];
+#pragma unroll
+  for (int i = 0; i < kNB; ++i)
+    if (i < jb) x[i] = col[i];
+#pragma unroll
+  for (int i = kNB - 1; i >= 0; --i)
+    if (i < jb) {
+      T acc = x[i];
+#pragma unroll
+      for (int l = 0; l < kNB; ++l)
+        if (l > i && l < jb) acc -= Up[i][l] * x[l];
+      x[i] = acc / Up[i][i];
+    }
+#pragma unroll
+  for (int i = 0; i < kNB; ++i)
+    if (i < jb) col[i] = x[i];
+}
+
+// F11 <- strict lower part of Linv, upper part (with the diagonal) of Uinv.
+template <class T>
+__global__ void trinv_store_kernel(T* fronts, int m, const T* Xl, const T* Xu, int k) {
+  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long)k * k) return;
+  int r = (int)(e % k), c = (int)(e / k);
+  long f = blockIdx.y;
+  T v = (r > c) ? Xl[f * k * k + e] : Xu[f * k * k + e];
+  fronts[f * (long)m * m + r + (long)c * m] = v;
+}
+
+template <class T>
+void gemm_sub(int M, int N, int K, const T* A, int lda, long sA, const T* B, int ldb, long sB,
+              T* C, int ldc, long sC, int batch, cudaStream_t st) {
+  if (M <= 0 || N <= 0 || K <= 0) return;
+  int tilesM = (M + kTile - 1) / kTile, tilesN = (N + kTile - 1) / kTile;
+  dim3 g(tilesM * tilesN, batch);
+  gemm_sub_kernel<T><<<g, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, tilesM);
+}
+
+// Replace L11, U11 of every front of the level by L11^{-1} (strict lower part;
+// the unit diagonal is implied) and U11^{-1} (upper part).  The sweeps of such a
+// level are then plain matrix-vector products spread over many CTAs.
+template <class T>
+void invert_triangles(DevLevel& L, T* scratch, cudaStream_t st) {
+  const int k = L.k, m = L.m;
+  const long kk = (long)k * k, mm = (long)m * m;
+  T* F = (T*)L.front;
+  T* Xl = scratch;
+  T* Xu = scratch + kk * L.nf;
+  long tot = kk * L.nf;
+  set_identity_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Xl, k, tot);
+  set_identity_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Xu, k, tot);
+  // L X = I, block rows top to bottom
+  for (int j0 = 0; j0 < k; j0 += kNB) {
+    int jb = k - j0 < kNB ? k - j0 : kNB;
+    int ncol = j0 + jb;
+    dim3 g((ncol + 255) / 256, L.nf);
+    trinv_lower_diag_kernel<T><<<g, 256, 0, st>>>(F, m, Xl, k, j0, jb, ncol);
+    int rows = k - j0 - jb;
+    gemm_sub<T>(rows, ncol, jb, F + (j0 + jb) + (long)j0 * m, m, mm, Xl + j0, k, kk,
+                Xl + (j0 + jb), k, kk, L.nf, st);
+  }
+  // U X = I, block rows bottom to top
+  int nblk = (k + kNB - 1) / kNB;
+  for (int bi = nblk - 1; bi >= 0; --bi) {
+    int j0 = bi * kNB;
+    int jb = k - j0 < kNB ? k - j0 : kNB;
+    dim3 g((k - j0 + 255) / 256, L.nf);
+    trinv_upper_diag_kernel<T><<<g, 256, 0, st>>>(F, m, Xu, k, j0, jb);
+    gemm_sub<T>(j0, k - j0, jb, F + (long)j0 * m, m, mm, Xu + j0 + (long)j0 * k, k, kk,
+                Xu + (long)j0 * k, k, kk, L.nf, st);
+  }
+  dim3 g((unsigned)((kk + 255) / 256), L.nf);
+  trinv_store_kernel<T><<<g, 256, 0, st>>>(F, m, Xl, Xu, k);
+}
+
+template <class T>
+int panel_width(int m) {
+  // widest of 32 / 16 / 8 whose staged panel fits in 160 KB of shared memory
+  for (int jb = kNB; jb >= 8; jb >>= 1)
+    if ((size_t)m * jb * sizeof(T) <= 160 * 1024) return jb;
+  return 0;
+}
+
 template <class T>
 cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const double* Qcat,
                            const double* Ccat, const double* q, double ptol, int* status,
-                           cudaStream_t st) {
+                           void* scratch, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(lu_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
   const long mm = (long)L.m * L.m;
   T* F = (T*)L.front;
   ProfScope pa(PROF_ASSEMBLE, st);
@@ -262,27 +458,35 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
   }
   front_scale_kernel<T><<<L.nf, 256, 0, st>>>(F, mm, L.scale);
   pa.done(abytes, na + 1, st);
-  for (int j0 = 0; j0 < L.k; j0 += kNB) {
-    int jb = L.k - j0 < kNB ? L.k - j0 : kNB;
+  const int NB = panel_width<T>(L.m);
+  if (NB == 0) return cudaErrorInvalidValue;
+  for (int j0 = 0; j0 < L.k; j0 += NB) {
+    int jb = L.k - j0 < NB ? L.k - j0 : NB;
     double pf = 0;
     for (int j = j0; j < j0 + jb; ++j) pf += (double)(L.m - j - 1) * (1.0 + 2.0 * (j0 + jb - j - 1));
     ProfScope pp(PROF_LU_PANEL, st);
-    lu_panel_kernel<T><<<L.nf, 256, 0, st>>>(F, L.m, L.k, j0, jb, L.piv, L.scale, ptol, status);
+    size_t sm = sizeof(T) * (size_t)(L.m - j0) * jb;
+    lu_panel_kernel<T><<<L.nf, 256, sm, st>>>(F, L.m, L.k, j0, jb, L.piv, L.scale, ptol, status);
     pp.done(pf * L.nf, 1, st);
     int rem = L.m - j0 - jb;
     if (rem > 0) {
       dim3 gt((rem + 255) / 256, L.nf);
       ProfScope pt(PROF_LU_TRSM, st);
-      lu_trsm_kernel<T><<<gt, 256, 0, st>>>(F, L.m, j0, jb);
+      lu_trsm_kernel<T><<<gt, 256, 0, st>>>(F, L.m, L.k, j0, jb, L.piv);
       pt.done((double)rem * jb * (jb - 1) * L.nf, 1, st);
-      int tiles = (rem + kTile - 1) / kTile;
-      dim3 gg(tiles * tiles, L.nf);
       ProfScope pg(PROF_LU_GEMM, st);
-      lu_gemm_kernel<T><<<gg, 256, 0, st>>>(F, L.m, j0, jb, tiles);
+      const int base = j0 + jb;
+      gemm_sub<T>(rem, rem, jb, F + base + (long)j0 * L.m, L.m, mm, F + j0 + (long)base * L.m, L.m,
+                  mm, F + base + (long)base * L.m, L.m, mm, L.nf, st);
       pg.done(2.0 * rem * rem * jb * L.nf, 1, st);
     }
   }
   lu_perm_kernel<<<(L.nf + 127) / 128, 128, 0, st>>>(L.piv, L.perm, L.k, L.nf);
+  if (L.inv) {
+    ProfScope pi(PROF_LU_TRINV, st);
+    invert_triangles<T>(L, (T*)scratch, st);
+    pi.done((2.0 / 3.0) * (double)L.k * L.k * L.k * L.nf, 1, st);
+  }
   return cudaGetLastError();
 }
 
@@ -290,10 +494,14 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
 
 cudaError_t factor_level(int prec, int d, DevLevel& L, const DevLevel* child, const double* Qcat,
                          const double* Ccat, const double* q, double pivot_tol, int* status,
-                         cudaStream_t st) {
+                         void* scratch, cudaStream_t st) {
   if (prec == SP_PREC_FP32)
-    return factor_level_t<float>(d, L, child, Qcat, Ccat, q, pivot_tol, status, st);
-  return factor_level_t<double>(d, L, child, Qcat, Ccat, q, pivot_tol, status, st);
+    return factor_level_t<float>(d, L, child, Qcat, Ccat, q, pivot_tol, status, scratch, st);
+  return factor_level_t<double>(d, L, child, Qcat, Ccat, q, pivot_tol, status, scratch, st);
+}
+
+int factor_panel_width(int prec, int m) {
+  return prec == SP_PREC_FP32 ? panel_width<float>(m) : panel_width<double>(m);
 }
 
 }  // namespace sp

