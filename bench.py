@@ -273,18 +273,22 @@ def run_ours(args):
     e2e_s = (time.perf_counter() - t0) / args.steps
     e2e_value = solves_per_step * world / e2e_s
 
+    def profiled(ctxs):
+        for c in ctxs:
+            B.sp_profile(c["S"].ctx, True)
+        step(ctxs)
+        out = {}
+        for c in ctxs:
+            for k, (ms_, nl, wk) in B.sp_profile_read(c["S"].ctx).items():
+                a = out.setdefault(k, [0.0, 0, 0.0])
+                a[0] += ms_
+                a[1] += nl
+                a[2] += wk
+            B.sp_profile(c["S"].ctx, False)
+        return out
+
     # one profiled step: kernel classes, launch counts, roofline of the dominant class
-    for c in fp64:
-        B.sp_profile(c["S"].ctx, True)
-    step(fp64)
-    prof = {}
-    for c in fp64:
-        for k, (ms_, nl, wk) in B.sp_profile_read(c["S"].ctx).items():
-            a = prof.setdefault(k, [0.0, 0, 0.0])
-            a[0] += ms_
-            a[1] += nl
-            a[2] += wk
-        B.sp_profile(c["S"].ctx, False)
+    prof = profiled(fp64)
     launches_per_step = sum(v[1] for v in prof.values())
     dom = max(prof, key=lambda k: prof[k][0])
     peaks = {}
@@ -317,11 +321,14 @@ def run_ours(args):
     if not args.no_chosen:
         fp32 = make(B.SP_PREC_FP32)
         ms32, _, infos32 = timed(fp32, args.steps, args.warmup)
+        prof32 = profiled(fp32)
         chosen = {"form": "fp32 preconditioner (factor+sweeps), fp64 operator/GMRES",
                   "value": solves_per_step * world / (ms32 / 1e3), "ms_per_step": ms32,
                   "speedup_vs_fp64": ms64 / ms32,
                   "iters": [i["iters"] for i in infos32[:solves_per_step]],
-                  "true_relres": [i["true_relres"] for i in infos32[:solves_per_step]]}
+                  "true_relres": [i["true_relres"] for i in infos32[:solves_per_step]],
+                  "kernel_breakdown_ms_per_step": {k: {"ms": round(v[0], 3), "launches": v[1]}
+                                                   for k, v in prof32.items()}}
         for c in fp32:
             c["S"].close()
 

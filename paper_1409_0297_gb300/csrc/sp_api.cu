@@ -453,7 +453,7 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
     D.inv = S.nf < 152;
     if (D.inv) {
       SP_CK(dalloc(c.get(), &D.tmp, vsz * (size_t)S.nf * S.m));
-      scratch_bytes = std::max(scratch_bytes, 2 * fsz * (size_t)S.nf * S.k * S.k);
+      scratch_bytes = std::max(scratch_bytes, 3 * fsz * (size_t)S.nf * S.k * S.k);
     }
     double k = S.k, mk = S.m - S.k;
     c->factor_entries += S.nf * (k * k + 2 * k * mk);

@@ -12,6 +12,7 @@
 // Every front of a level has the same size, so each step is one batched launch
 // over all fronts of the level.  Fronts are column-major m x m.  T = double for
 // the FP64 form, float for the FP32 preconditioner form.
+#include <algorithm>
 #include <cfloat>
 
 #include "sp_internal.h"
@@ -22,6 +23,7 @@ namespace {
 
 constexpr int kNB = 32;       // panel width
 constexpr int kTile = 64;     // Schur update tile (kTile x kTile per CTA)
+constexpr int kInvBlock = kInvBlockSize;  // diagonal-block size of the inverse-form levels
 
 template <class T>
 __global__ void assemble_kernel(T* fronts, int m, int nasm, const int* __restrict__ slot,
@@ -56,27 +58,27 @@ __global__ void extend_add_kernel(T* parent, int m, int nb1, const T* __restrict
   parent[(long)f * m * m + map[i] + (long)map[j] * m] += v;
 }
 
+// max |entry| of every front: CTAs over (chunk, front), atomicMax on the bit
+// pattern (non-negative doubles order like their unsigned integer bits); scale
+// must be zeroed first.
 template <class T>
 __global__ void front_scale_kernel(const T* fronts, long mm, double* scale) {
-  const T* A = fronts + blockIdx.x * mm;
+  const T* A = fronts + blockIdx.y * mm;
   double mx = 0;
-  for (long i = threadIdx.x; i < mm; i += blockDim.x) mx = fmax(mx, fabs((double)A[i]));
-  __shared__ double red[256];
-  red[threadIdx.x] = mx;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) scale[blockIdx.x] = red[0];
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < mm; i += (long)gridDim.x * blockDim.x)
+    mx = fmax(mx, fabs((double)A[i]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0)
+    atomicMax(reinterpret_cast<unsigned long long*>(scale + blockIdx.y),
+              (unsigned long long)__double_as_longlong(mx));
 }
 
 // LU of the panel columns [j0, j0+jb) of every front (one CTA per front).  The
 // panel rows [j0, m) are staged in shared memory (column-major, leading
 // dimension rows = m - j0); pivot rows are searched among the eliminated rows
 // [j, k) only.  Row swaps inside the panel happen in shared memory; the same
-// swaps are applied here to the columns left of the panel and by the row-block
-// solve to the columns right of it (LAPACK-style full-row interchanges).
+// swaps are applied to the columns left and right of the panel by the row-block
+// solve kernel (LAPACK-style full-row interchanges).
 template <class T>
 __global__ void __launch_bounds__(256) lu_panel_kernel(T* fronts, int m, int k, int j0, int jb,
                                                        int* piv, const double* scale,
@@ -155,22 +157,12 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(T* fronts, int m, int k, 
     int r = (int)(e % rows), c = (int)(e / rows);
     A[(j0 + r) + (long)(j0 + c) * m] = P[e];
   }
-  // interchanges on the columns left of the panel
-  for (int c = threadIdx.x; c < j0; c += blockDim.x) {
-    T* col = A + (long)c * m;
-    for (int jj = 0; jj < jb; ++jj) {
-      int p = j0 + spiv[jj];
-      if (p != j0 + jj) {
-        T t = col[j0 + jj];
-        col[j0 + jj] = col[p];
-        col[p] = t;
-      }
-    }
-  }
 }
 
-// Row-block solve right of the panel: interchanges, then
-// A[j0:j0+jb, c] = L_pp^{-1} A[j0:j0+jb, c] for c >= j0 + jb (one thread per column).
+// Interchanges of the panel's pivots on every column outside the panel, and the
+// row-block solve A[j0:j0+jb, c] = L_pp^{-1} A[j0:j0+jb, c] right of it.  Thread
+// cc < j0 owns left column cc (interchanges only); thread cc >= j0 owns column
+// c = cc + jb >= j0 + jb.
 template <class T>
 __global__ void __launch_bounds__(256) lu_trsm_kernel(T* fronts, int m, int k, int j0, int jb,
                                                       const int* piv) {
@@ -183,7 +175,8 @@ __global__ void __launch_bounds__(256) lu_trsm_kernel(T* fronts, int m, int k, i
   }
   for (int e = threadIdx.x; e < jb; e += blockDim.x) sp_[e] = piv[(long)blockIdx.y * k + j0 + e];
   __syncthreads();
-  int c = j0 + jb + blockIdx.x * blockDim.x + threadIdx.x;
+  const int cc = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = cc < j0 ? cc : cc + jb;
   if (c >= m) return;
   T* colg = A + (long)c * m;
   for (int jj = 0; jj < jb; ++jj) {
@@ -194,6 +187,7 @@ __global__ void __launch_bounds__(256) lu_trsm_kernel(T* fronts, int m, int k, i
       colg[p] = t;
     }
   }
+  if (cc < j0) return;
   T x[kNB];
   T* col = colg + j0;
 #pragma unroll
@@ -269,6 +263,80 @@ __global__ void __launch_bounds__(256) gemm_sub_kernel(int M, int N, int K, cons
   }
 }
 
+// Batched C = beta C + alpha A B (column-major, any K) with triangle-aware K
+// ranges: tri_a = 1 when A is lower triangular (A[r, l] = 0 for l > r), 2 when
+// upper (A[r, l] = 0 for l < r); tri_b = 1 when B is lower (B[l, c] = 0 for
+// l < c), 2 when upper (B[l, c] = 0 for l > c).  Zero tiles are skipped, entries
+// inside a computed tile must hold their zeros.  beta is 0 or 1.
+template <class T>
+__global__ void __launch_bounds__(256) gemm_gen_kernel(int M, int N, int K, T alpha, int beta_one,
+                                                       const T* A, int lda, long sA, const T* B,
+                                                       int ldb, long sB, T* C, int ldc, long sC,
+                                                       int tilesM, int tri_a, int tri_b, int nb2,
+                                                       long sA2, long sB2, long sC2) {
+  // batch index = outer * nb2 + inner with strides (sA, sB, sC) and (sA2, sB2, sC2)
+  const long bo = blockIdx.y / nb2, bi = blockIdx.y % nb2;
+  A += bo * sA + bi * sA2;
+  B += bo * sB + bi * sB2;
+  C += bo * sC + bi * sC2;
+  const int tr = blockIdx.x % tilesM, tc = blockIdx.x / tilesM;
+  const int r0 = tr * kTile, c0 = tc * kTile;
+  int klo = 0, khi = K;
+  if (tri_a == 1) khi = min(khi, r0 + kTile);
+  if (tri_a == 2) klo = max(klo, r0);
+  if (tri_b == 1) klo = max(klo, c0);
+  if (tri_b == 2) khi = min(khi, c0 + kTile);
+  __shared__ T As[kNB][kTile];
+  __shared__ T Bs[kNB][kTile + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+  for (int k0 = klo; k0 < khi; k0 += kNB) {
+    const int kc = min(kNB, khi - k0);
+    for (int e = threadIdx.x; e < kNB * kTile; e += blockDim.x) {
+      int i = e % kTile, l = e / kTile;
+      int r = r0 + i;
+      As[l][i] = (r < M && l < kc) ? A[r + (long)(k0 + l) * lda] : (T)0;
+    }
+    for (int e = threadIdx.x; e < kNB * kTile; e += blockDim.x) {
+      int l = e % kNB, jc = e / kNB;
+      int c = c0 + jc;
+      Bs[l][jc] = (c < N && l < kc) ? B[(k0 + l) + (long)c * ldb] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int l = 0; l < kNB; ++l) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[l][tx + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[l][ty + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    int c = c0 + ty + 16 * b;
+    if (c >= N) continue;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      int r = r0 + tx + 16 * a;
+      if (r < M) {
+        T v = alpha * acc[a][b];
+        if (beta_one) v += C[r + (long)c * ldc];
+        C[r + (long)c * ldc] = v;
+      }
+    }
+  }
+}
+
 __global__ void lu_perm_kernel(const int* piv, int* perm, int k, int nf) {
   int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= nf) return;
@@ -283,88 +351,108 @@ __global__ void lu_perm_kernel(const int* piv, int* perm, int k, int nf) {
 }
 
 // ---- explicit triangular inverses for levels with few fronts -------------------
-// X (k x k per front, leading dimension k) is set to the identity.
+// Inverse of every 32 x 32 diagonal block of L11 (unit lower; upper == 0) or U11
+// (upper == 1) of every front, written to the matching diagonal block of X
+// (k x k per front, leading dimension k).  One CTA per (block, front); thread c
+// solves column c by substitution.
 template <class T>
-__global__ void set_identity_kernel(T* X, int k, long total) {
-  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= total) return;
-  long w = e % ((long)k * k);
-  int r = (int)(w % k), c = (int)(w / k);
-  X[e] = (r == c) ? (T)1 : (T)0;
-}
-
-// Diagonal-block step of X = L11^{-1} (unit lower): rows [j0, j0+jb) of X,
-// columns [0, ncol), replaced by L_JJ^{-1} times themselves (one thread per column).
-template <class T>
-__global__ void trinv_lower_diag_kernel(const T* fronts, int m, T* X, int k, int j0, int jb, int ncol) {
+__global__ void trinv_diag32_kernel(const T* fronts, int m, T* X, int k, int upper) {
+  const int j0 = blockIdx.x * kNB;
+  const int jb = min(kNB, k - j0);
   const T* A = fronts + (long)blockIdx.y * m * m;
   T* Xf = X + (long)blockIdx.y * k * k;
-  __shared__ T Lp[kNB][kNB + 1];
+  __shared__ T Bk[kNB][kNB + 1];
   for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) {
     int i = e % jb, l = e / jb;
-    Lp[i][l] = A[(j0 + i) + (long)(j0 + l) * m];
+    Bk[i][l] = A[(j0 + i) + (long)(j0 + l) * m];
   }
   __syncthreads();
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncol) return;
-  T* col = Xf + (long)c * k + j0;
+  const int c = threadIdx.x;
+  if (c >= jb) return;
   T x[kNB];
 #pragma unroll
-  for (int i = 0; i < kNB; ++i)
-    if (i < jb) x[i] = col[i];
+  for (int i = 0; i < kNB; ++i) x[i] = (i == c) ? (T)1 : (T)0;
+  if (!upper) {
 #pragma unroll
-  for (int i = 1; i < kNB; ++i)
-    if (i < jb) {
-      T acc = x[i];
+    for (int i = 0; i < kNB; ++i)
+      if (i < jb) {
+        T acc = x[i];
 #pragma unroll
-      for (int l = 0; l < kNB; ++l)
-        if (l < i) acc -= Lp[i][l] * x[l];
-      x[i] = acc;
-    }
+        for (int l = 0; l < kNB; ++l)
+          if (l < i) acc -= Bk[i][l] * x[l];
+        x[i] = acc;
+      }
+  } else {
+#pragma unroll
+    for (int i = kNB - 1; i >= 0; --i)
+      if (i < jb) {
+        T acc = x[i];
+#pragma unroll
+        for (int l = 0; l < kNB; ++l)
+          if (l > i && l < jb) acc -= Bk[i][l] * x[l];
+        x[i] = acc / Bk[i][i];
+      }
+  }
+  T* col = Xf + j0 + (long)(j0 + c) * k;
 #pragma unroll
   for (int i = 0; i < kNB; ++i)
     if (i < jb) col[i] = x[i];
 }
 
-// Diagonal-block step of X = U11^{-1} (upper, non-unit): rows [j0, j0+jb) of X,
-// columns [c_lo, k), replaced by U_JJ^{-1} times themselves.
+// In-place inversion of the 32 x 32 diagonal blocks of L11 (unit lower) and U11
+// (upper) of every front: afterwards the block's strict lower part holds the
+// block of L11^{-1} and its upper part (with the diagonal) the block of U11^{-1}.
+// The sweeps then resolve a diagonal block with a 32 x 32 matrix-vector product
+// instead of 32 dependent steps and 32 divisions.  One CTA (32 threads) per
+// (block, front); thread c computes column c of both inverses.
 template <class T>
-__global__ void trinv_upper_diag_kernel(const T* fronts, int m, T* X, int k, int j0, int jb) {
-  const T* A = fronts + (long)blockIdx.y * m * m;
-  T* Xf = X + (long)blockIdx.y * k * k;
-  __shared__ T Up[kNB][kNB + 1];
+__global__ void diag32_inplace_kernel(T* fronts, int m, int k) {
+  const int j0 = blockIdx.x * kNB;
+  const int jb = min(kNB, k - j0);
+  T* A = fronts + (long)blockIdx.y * m * m;
+  __shared__ T Bk[kNB][kNB + 1];
   for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) {
     int i = e % jb, l = e / jb;
-    Up[i][l] = A[(j0 + i) + (long)(j0 + l) * m];
+    Bk[i][l] = A[(j0 + i) + (long)(j0 + l) * m];
   }
   __syncthreads();
-  int c = j0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= k) return;
-  T* col = Xf + (long)c * k + j0;
-  T x[kNB];
+  const int c = threadIdx.x;
+  T xl[kNB], xu[kNB];
+#pragma unroll
+  for (int i = 0; i < kNB; ++i) xl[i] = xu[i] = (i == c) ? (T)1 : (T)0;
 #pragma unroll
   for (int i = 0; i < kNB; ++i)
-    if (i < jb) x[i] = col[i];
+    if (i < jb) {
+      T acc = xl[i];
+#pragma unroll
+      for (int l = 0; l < kNB; ++l)
+        if (l < i) acc -= Bk[i][l] * xl[l];
+      xl[i] = acc;
+    }
 #pragma unroll
   for (int i = kNB - 1; i >= 0; --i)
     if (i < jb) {
-      T acc = x[i];
+      T acc = xu[i];
 #pragma unroll
       for (int l = 0; l < kNB; ++l)
-        if (l > i && l < jb) acc -= Up[i][l] * x[l];
-      x[i] = acc / Up[i][i];
+        if (l > i && l < jb) acc -= Bk[i][l] * xu[l];
+      xu[i] = acc / Bk[i][i];
     }
+  if (c >= jb) return;
+  T* col = A + j0 + (long)(j0 + c) * m;
 #pragma unroll
   for (int i = 0; i < kNB; ++i)
-    if (i < jb) col[i] = x[i];
+    if (i < jb) col[i] = (i > c) ? xl[i] : xu[i];
 }
 
 // F11 <- strict lower part of Linv, upper part (with the diagonal) of Uinv.
+// (only the diagonal blocks of size Bsz: the off-diagonal blocks keep L11, U11)
 template <class T>
-__global__ void trinv_store_kernel(T* fronts, int m, const T* Xl, const T* Xu, int k) {
+__global__ void trinv_store_kernel(T* fronts, int m, const T* Xl, const T* Xu, int k, int Bsz) {
   long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long)k * k) return;
   int r = (int)(e % k), c = (int)(e / k);
+  if (r / Bsz != c / Bsz) return;
   long f = blockIdx.y;
   T v = (r > c) ? Xl[f * k * k + e] : Xu[f * k * k + e];
   fronts[f * (long)m * m + r + (long)c * m] = v;
@@ -379,41 +467,77 @@ void gemm_sub(int M, int N, int K, const T* A, int lda, long sA, const T* B, int
   gemm_sub_kernel<T><<<g, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, tilesM);
 }
 
-// Replace L11, U11 of every front of the level by L11^{-1} (strict lower part;
-// the unit diagonal is implied) and U11^{-1} (upper part).  The sweeps of such a
-// level are then plain matrix-vector products spread over many CTAs.
 template <class T>
-void invert_triangles(DevLevel& L, T* scratch, cudaStream_t st) {
-  const int k = L.k, m = L.m;
+void gemm_gen(int M, int N, int K, T alpha, bool beta_one, const T* A, int lda, long sA,
+              const T* B, int ldb, long sB, T* C, int ldc, long sC, int batch, int tri_a,
+              int tri_b, cudaStream_t st, int nb2 = 1, long sA2 = 0, long sB2 = 0, long sC2 = 0) {
+  if (M <= 0 || N <= 0 || K <= 0 || batch <= 0 || nb2 <= 0) return;
+  int tilesM = (M + kTile - 1) / kTile, tilesN = (N + kTile - 1) / kTile;
+  dim3 g(tilesM * tilesN, batch * nb2);
+  gemm_gen_kernel<T><<<g, 256, 0, st>>>(M, N, K, alpha, beta_one ? 1 : 0, A, lda, sA, B, ldb, sB,
+                                        C, ldc, sC, tilesM, tri_a, tri_b, nb2, sA2, sB2, sC2);
+}
+
+// Replace the diagonal blocks (size Bsz, a power of two >= 32) of L11 and U11 of
+// every front of the level by the blocks of L11^{-1} (strict lower part; the unit
+// diagonal is implied) and U11^{-1} (upper part).  The sweeps of such a level are
+// then short chains of matrix-vector products spread over many CTAs.
+// Recursive doubling on the diagonal blocks (32, 64, 128, ... up to Bsz):
+//   [A 0; B C]^{-1} = [A^{-1} 0; -C^{-1} (B A^{-1}), C^{-1}]
+//   [A B; 0 C]^{-1} = [A^{-1}, -(A^{-1} B) C^{-1}; 0 C^{-1}]
+// with the two products of each merge as batched GEMMs over fronts and pairs.
+// scratch: Xl, Xu (k x k per front) and a k x k work block per front.
+template <class T>
+void invert_triangles(DevLevel& L, T* scratch, int Bsz, cudaStream_t st) {
+  const int k = L.k, m = L.m, nf = L.nf;
   const long kk = (long)k * k, mm = (long)m * m;
   T* F = (T*)L.front;
   T* Xl = scratch;
-  T* Xu = scratch + kk * L.nf;
-  long tot = kk * L.nf;
-  set_identity_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Xl, k, tot);
-  set_identity_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Xu, k, tot);
-  // L X = I, block rows top to bottom
-  for (int j0 = 0; j0 < k; j0 += kNB) {
-    int jb = k - j0 < kNB ? k - j0 : kNB;
-    int ncol = j0 + jb;
-    dim3 g((ncol + 255) / 256, L.nf);
-    trinv_lower_diag_kernel<T><<<g, 256, 0, st>>>(F, m, Xl, k, j0, jb, ncol);
-    int rows = k - j0 - jb;
-    gemm_sub<T>(rows, ncol, jb, F + (j0 + jb) + (long)j0 * m, m, mm, Xl + j0, k, kk,
-                Xl + (j0 + jb), k, kk, L.nf, st);
+  T* Xu = scratch + kk * nf;
+  T* W = scratch + 2 * kk * nf;
+  cudaMemsetAsync(Xl, 0, sizeof(T) * kk * nf, st);
+  cudaMemsetAsync(Xu, 0, sizeof(T) * kk * nf, st);
+  const int nb = (k + kNB - 1) / kNB;
+  dim3 gd(nb, nf);
+  trinv_diag32_kernel<T><<<gd, kNB, 0, st>>>(F, m, Xl, k, 0);
+  trinv_diag32_kernel<T><<<gd, kNB, 0, st>>>(F, m, Xu, k, 1);
+  for (int s = kNB; s < k && s < Bsz; s *= 2) {
+    // pairs p: A at [2ps, 2ps+s), C at [2ps+s, min(2ps+2s, k)); the pairs with a
+    // full-size C go in one batched launch (fronts x pairs), a ragged last pair in
+    // a second one.  W holds pair p's product at rows [2ps, 2ps+s) of the front's
+    // k x k work block.
+    const int npairs = (k + 2 * s - 1) / (2 * s);
+    const int last_c = k - ((npairs - 1) * 2 * s + s);
+    const int nfull = (last_c >= s) ? npairs : npairs - 1;
+    const long ps_k = 2L * s * (1 + k), ps_m = 2L * s * (1 + m), ps_w = 2L * s;
+    for (int pass = 0; pass < 2; ++pass) {
+      int cnt, p0, sc;
+      if (pass == 0) {
+        cnt = nfull;
+        p0 = 0;
+        sc = s;
+      } else {
+        if (nfull == npairs || last_c <= 0) continue;
+        cnt = 1;
+        p0 = npairs - 1;
+        sc = last_c;
+      }
+      if (cnt <= 0) continue;
+      const int a0 = p0 * 2 * s, c0 = a0 + s;
+      // lower: W = B Ainv (B = L[c0.., a0..], Ainv lower), Xl[c0.., a0..] = -Cinv W
+      gemm_gen<T>(sc, s, s, (T)1, false, F + c0 + (long)a0 * m, m, mm, Xl + a0 + (long)a0 * k, k,
+                  kk, W + a0, k, kk, nf, 0, 1, st, cnt, ps_m, ps_k, ps_w);
+      gemm_gen<T>(sc, s, sc, (T)-1, false, Xl + c0 + (long)c0 * k, k, kk, W + a0, k, kk,
+                  Xl + c0 + (long)a0 * k, k, kk, nf, 1, 0, st, cnt, ps_k, ps_w, ps_k);
+      // upper: W = Ainv B (B = U[a0.., c0..], Ainv upper), Xu[a0.., c0..] = -W Cinv
+      gemm_gen<T>(s, sc, s, (T)1, false, Xu + a0 + (long)a0 * k, k, kk, F + a0 + (long)c0 * m, m,
+                  mm, W + a0, k, kk, nf, 2, 0, st, cnt, ps_k, ps_m, ps_w);
+      gemm_gen<T>(s, sc, sc, (T)-1, false, W + a0, k, kk, Xu + c0 + (long)c0 * k, k, kk,
+                  Xu + a0 + (long)c0 * k, k, kk, nf, 0, 2, st, cnt, ps_w, ps_k, ps_k);
+    }
   }
-  // U X = I, block rows bottom to top
-  int nblk = (k + kNB - 1) / kNB;
-  for (int bi = nblk - 1; bi >= 0; --bi) {
-    int j0 = bi * kNB;
-    int jb = k - j0 < kNB ? k - j0 : kNB;
-    dim3 g((k - j0 + 255) / 256, L.nf);
-    trinv_upper_diag_kernel<T><<<g, 256, 0, st>>>(F, m, Xu, k, j0, jb);
-    gemm_sub<T>(j0, k - j0, jb, F + (long)j0 * m, m, mm, Xu + j0 + (long)j0 * k, k, kk,
-                Xu + (long)j0 * k, k, kk, L.nf, st);
-  }
-  dim3 g((unsigned)((kk + 255) / 256), L.nf);
-  trinv_store_kernel<T><<<g, 256, 0, st>>>(F, m, Xl, Xu, k);
+  dim3 g((unsigned)((kk + 255) / 256), nf);
+  trinv_store_kernel<T><<<g, 256, 0, st>>>(F, m, Xl, Xu, k, Bsz);
 }
 
 template <class T>
@@ -456,7 +580,12 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
     na += 1 << d;
     abytes += (double)sizeof(T) * work * child->nf;
   }
-  front_scale_kernel<T><<<L.nf, 256, 0, st>>>(F, mm, L.scale);
+  cudaMemsetAsync(L.scale, 0, sizeof(double) * L.nf, st);
+  {
+    long chunks = std::min<long>(std::max<long>(1, mm / (256 * 16)), std::max<long>(1, 1216 / L.nf));
+    dim3 gs((unsigned)chunks, L.nf);
+    front_scale_kernel<T><<<gs, 256, 0, st>>>(F, mm, L.scale);
+  }
   pa.done(abytes, na + 1, st);
   const int NB = panel_width<T>(L.m);
   if (NB == 0) return cudaErrorInvalidValue;
@@ -469,11 +598,13 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
     lu_panel_kernel<T><<<L.nf, 256, sm, st>>>(F, L.m, L.k, j0, jb, L.piv, L.scale, ptol, status);
     pp.done(pf * L.nf, 1, st);
     int rem = L.m - j0 - jb;
-    if (rem > 0) {
-      dim3 gt((rem + 255) / 256, L.nf);
+    if (rem + j0 > 0) {
+      dim3 gt((rem + j0 + 255) / 256, L.nf);
       ProfScope pt(PROF_LU_TRSM, st);
       lu_trsm_kernel<T><<<gt, 256, 0, st>>>(F, L.m, L.k, j0, jb, L.piv);
       pt.done((double)rem * jb * (jb - 1) * L.nf, 1, st);
+    }
+    if (rem > 0) {
       ProfScope pg(PROF_LU_GEMM, st);
       const int base = j0 + jb;
       gemm_sub<T>(rem, rem, jb, F + base + (long)j0 * L.m, L.m, mm, F + j0 + (long)base * L.m, L.m,
@@ -482,11 +613,18 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
     }
   }
   lu_perm_kernel<<<(L.nf + 127) / 128, 128, 0, st>>>(L.piv, L.perm, L.k, L.nf);
+  ProfScope pi(PROF_LU_TRINV, st);
+  double bw = 0;
   if (L.inv) {
-    ProfScope pi(PROF_LU_TRINV, st);
-    invert_triangles<T>(L, (T*)scratch, st);
-    pi.done((2.0 / 3.0) * (double)L.k * L.k * L.k * L.nf, 1, st);
+    invert_triangles<T>(L, (T*)scratch, kInvBlock, st);
+    const int Bz = kInvBlock < L.k ? kInvBlock : L.k;
+    bw = (2.0 / 3.0) * (double)Bz * Bz * L.k * L.nf;
+  } else {
+    dim3 gd((L.k + kNB - 1) / kNB, L.nf);
+    diag32_inplace_kernel<T><<<gd, kNB, 0, st>>>(F, L.m, L.k);
+    bw = (2.0 / 3.0) * (double)kNB * kNB * L.k * L.nf;
   }
+  pi.done(bw, 1, st);
   return cudaGetLastError();
 }
 

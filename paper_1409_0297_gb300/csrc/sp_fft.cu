@@ -1,4 +1,5 @@
-// FP64 complex FFT passes for the pseudospectral operator (Section 2.1, Eq. G).
+// Complex FFT passes for the pseudospectral operator (Section 2.1, Eq. G), in
+// FP64 (double2) and, for the inner solve of the mixed-precision form, FP32 (float2).
 //
 //   G x = F^{-1} diag(1/(4 pi^2 |k|^2 - s)) F x       (Eq. G)
 //   A x = x + G (q x)                                   (Section 2.2)
@@ -25,19 +26,30 @@ namespace {
 
 constexpr int kThreads = 256;
 
+template <class VT> struct Real;
+template <> struct Real<double2> { using T = double; };
+template <> struct Real<float2> { using T = float; };
+
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 
+template <class VT>
 struct PassArgs {
-  const double2* in;
-  double2* out;
-  const double* q;      // PRE_Q
-  const double* Dn;     // MID
-  const double2* addx;  // POST_ADD
-  const double2* tw;
+  using T = typename Real<VT>::T;
+  const VT* in;
+  VT* out;
+  const T* q;      // PRE_Q
+  const T* Dn;     // MID
+  const VT* addx;  // POST_ADD
+  const VT* tw;
   long S;               // stride between consecutive elements of a line
   long nlines;          // number of lines of this axis
   int n, logn, W, pad;
@@ -45,12 +57,14 @@ struct PassArgs {
 };
 
 // global address of element i of line t
-__device__ __forceinline__ long line_addr(const PassArgs& a, long t, int i) {
+template <class VT>
+__device__ __forceinline__ long line_addr(const PassArgs<VT>& a, long t, int i) {
   long lo = t % a.S, hi = t / a.S;
   return lo + hi * a.S * a.n + (long)i * a.S;
 }
 
-__device__ __forceinline__ void dit_stages(double2* sm, const PassArgs& a, bool conj_tw) {
+template <class VT>
+__device__ __forceinline__ void dit_stages(VT* sm, const PassArgs<VT>& a, bool conj_tw) {
   const int n = a.n, half_n = n >> 1, ld = n + a.pad;
   const int work = a.W * half_n;
   for (int s = 1; s <= a.logn; ++s) {
@@ -60,10 +74,10 @@ __device__ __forceinline__ void dit_stages(double2* sm, const PassArgs& a, bool 
       int jj = p & (half - 1);
       int i0 = ((p >> (s - 1)) << s) + jj;
       int i1 = i0 + half;
-      double2 t = __ldg(&a.tw[jj << (a.logn - s)]);
+      VT t = a.tw[jj << (a.logn - s)];
       if (conj_tw) t.y = -t.y;
-      double2* row = sm + w * ld;
-      double2 u = row[i0], v = cmul(row[i1], t);
+      VT* row = sm + w * ld;
+      VT u = row[i0], v = cmul(row[i1], t);
       row[i0] = cadd(u, v);
       row[i1] = csub(u, v);
     }
@@ -71,7 +85,8 @@ __device__ __forceinline__ void dit_stages(double2* sm, const PassArgs& a, bool 
   }
 }
 
-__device__ __forceinline__ void dif_stages(double2* sm, const PassArgs& a, bool conj_tw) {
+template <class VT>
+__device__ __forceinline__ void dif_stages(VT* sm, const PassArgs<VT>& a, bool conj_tw) {
   const int n = a.n, half_n = n >> 1, ld = n + a.pad;
   const int work = a.W * half_n;
   for (int s = a.logn; s >= 1; --s) {
@@ -81,10 +96,10 @@ __device__ __forceinline__ void dif_stages(double2* sm, const PassArgs& a, bool 
       int jj = p & (half - 1);
       int i0 = ((p >> (s - 1)) << s) + jj;
       int i1 = i0 + half;
-      double2 t = __ldg(&a.tw[jj << (a.logn - s)]);
+      VT t = a.tw[jj << (a.logn - s)];
       if (conj_tw) t.y = -t.y;
-      double2* row = sm + w * ld;
-      double2 u = row[i0], v = row[i1];
+      VT* row = sm + w * ld;
+      VT u = row[i0], v = row[i1];
       row[i0] = cadd(u, v);
       row[i1] = cmul(csub(u, v), t);
     }
@@ -92,8 +107,11 @@ __device__ __forceinline__ void dif_stages(double2* sm, const PassArgs& a, bool 
   }
 }
 
-__global__ void __launch_bounds__(kThreads) fft_pass_kernel(PassArgs a) {
-  extern __shared__ double2 sm[];
+template <class VT>
+__global__ void __launch_bounds__(kThreads) fft_pass_kernel(PassArgs<VT> a) {
+  using T = typename Real<VT>::T;
+  extern __shared__ unsigned char smraw[];
+  VT* sm = reinterpret_cast<VT*>(smraw);
   const int n = a.n, ld = n + a.pad, W = a.W;
   const long t0 = (long)blockIdx.x * W;
   const int total = W * n;
@@ -112,9 +130,9 @@ __global__ void __launch_bounds__(kThreads) fft_pass_kernel(PassArgs a) {
     long t = t0 + w;
     if (t >= a.nlines) continue;
     long g = line_addr(a, t, i);
-    double2 v = a.in[g];
+    VT v = a.in[g];
     if (a.q) {
-      double qq = a.q[g];
+      T qq = a.q[g];
       v.x *= qq;
       v.y *= qq;
     }
@@ -139,8 +157,8 @@ __global__ void __launch_bounds__(kThreads) fft_pass_kernel(PassArgs a) {
       }
       long t = t0 + w;
       if (t >= a.nlines) continue;
-      double dn = a.Dn[line_addr(a, t, i)];
-      double2* p = &sm[w * ld + i];
+      T dn = a.Dn[line_addr(a, t, i)];
+      VT* p = &sm[w * ld + i];
       p->x *= dn;
       p->y *= dn;
     }
@@ -161,79 +179,105 @@ __global__ void __launch_bounds__(kThreads) fft_pass_kernel(PassArgs a) {
     if (t >= a.nlines) continue;
     long g = line_addr(a, t, i);
     int pos = bitrev_store ? (int)(__brev((unsigned)i) >> (32 - a.logn)) : i;
-    double2 v = sm[w * ld + pos];
+    VT v = sm[w * ld + pos];
     if (a.addx) v = cadd(v, a.addx[g]);
     a.out[g] = v;
   }
 }
 
-int lines_per_cta(int n, long nlines) {
+int lines_per_cta(int n, long nlines, int esize) {
   // enough lines for >= 256 butterflies per stage, at most 64 KB of lines, and
   // at least ~2 CTAs per SM on 152 SMs when the grid allows it
   int W = 1;
   while (W * n < 2 * kThreads && W < 64) W <<= 1;
-  while (W > 1 && (long)W * n * 16 > 64 * 1024) W >>= 1;
+  while (W > 1 && (long)W * n * esize > 64 * 1024) W >>= 1;
   while (W > 1 && nlines / W < 304) W >>= 1;
   return W;
 }
 
-cudaError_t run_pass(const FftPlan& P, int axis, int mode, const double2* in, double2* out,
-                     const double* q, const double2* addx, cudaStream_t st) {
-  PassArgs a{};
+template <class VT>
+cudaError_t run_pass(int d, int n, int logn, const VT* tw, const typename Real<VT>::T* Dn, int axis,
+                     int mode, const VT* in, VT* out, const typename Real<VT>::T* q,
+                     const VT* addx, cudaStream_t st) {
+  PassArgs<VT> a{};
   a.mode = mode;
   a.in = in;
   a.out = out;
   a.q = q;
-  a.Dn = (mode == 2) ? P.Dn : nullptr;
+  a.Dn = (mode == 2) ? Dn : nullptr;
   a.addx = addx;
-  a.tw = P.tw;
-  a.n = P.n;
-  a.logn = P.logn;
+  a.tw = tw;
+  a.n = n;
+  a.logn = logn;
   long S = 1;
-  for (int i = 0; i < axis; ++i) S *= P.n;
+  for (int i = 0; i < axis; ++i) S *= n;
   a.S = S;
   long N = 1;
-  for (int i = 0; i < P.d; ++i) N *= P.n;
-  a.nlines = N / P.n;
-  a.W = lines_per_cta(P.n, a.nlines);
+  for (int i = 0; i < d; ++i) N *= n;
+  a.nlines = N / n;
+  a.W = lines_per_cta(n, a.nlines, (int)sizeof(VT));
   // axis > 0 lines are grouped W at a time inside one S-block: W must divide S
   if (axis > 0)
     while (a.W > 1 && (S % a.W)) a.W >>= 1;
   a.pad = 1;
-  size_t smem = (size_t)a.W * (P.n + a.pad) * sizeof(double2);
+  size_t smem = (size_t)a.W * (n + a.pad) * sizeof(VT);
   long grid = (a.nlines + a.W - 1) / a.W;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(fft_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(fft_pass_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
+  const double es = sizeof(VT);
   ProfScope ps(PROF_FFT, st);
-  fft_pass_kernel<<<(unsigned)grid, kThreads, smem, st>>>(a);
-  ps.done((double)N * (32.0 + (q ? 8.0 : 0.0) + (mode == 2 ? 8.0 : 0.0) + (addx ? 16.0 : 0.0)), 1, st);
+  fft_pass_kernel<VT><<<(unsigned)grid, kThreads, smem, st>>>(a);
+  ps.done((double)N * (2 * es + (q ? es / 2 : 0.0) + (mode == 2 ? es / 2 : 0.0) + (addx ? es : 0.0)),
+          1, st);
   return cudaGetLastError();
+}
+
+template <class VT>
+cudaError_t green_apply_t(int d, int n, int logn, const VT* tw, const typename Real<VT>::T* Dn,
+                          VT* tmp, const VT* x, const typename Real<VT>::T* q, bool add_x, VT* out,
+                          cudaStream_t st) {
+  cudaError_t e;
+  // forward along axes 0..d-2, middle pass on axis d-1, inverse along d-2..0
+  const VT* src = x;
+  for (int ax = 0; ax < d - 1; ++ax) {
+    e = run_pass<VT>(d, n, logn, tw, Dn, ax, 0, src, tmp, ax == 0 ? q : nullptr, nullptr, st);
+    if (e != cudaSuccess) return e;
+    src = tmp;
+  }
+  e = run_pass<VT>(d, n, logn, tw, Dn, d - 1, 2, src, tmp, nullptr, nullptr, st);
+  if (e != cudaSuccess) return e;
+  for (int ax = d - 2; ax >= 0; --ax) {
+    bool last = (ax == 0);
+    e = run_pass<VT>(d, n, logn, tw, Dn, ax, 1, tmp, last ? out : tmp, nullptr,
+                     (last && add_x) ? x : nullptr, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+__global__ void to_float_kernel(const double* a, float* b, long N) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) b[i] = (float)a[i];
 }
 
 }  // namespace
 
 cudaError_t fft_green_apply(const FftPlan& P, const double2* x, const double* q, bool add_x,
                             double2* out, cudaStream_t st) {
-  cudaError_t e;
-  const int d = P.d;
-  // forward along axes 0..d-2, middle pass on axis d-1, inverse along d-2..0
-  const double2* src = x;
-  for (int ax = 0; ax < d - 1; ++ax) {
-    e = run_pass(P, ax, 0, src, P.tmp, ax == 0 ? q : nullptr, nullptr, st);
-    if (e != cudaSuccess) return e;
-    src = P.tmp;
-  }
-  e = run_pass(P, d - 1, 2, src, P.tmp, nullptr, nullptr, st);
-  if (e != cudaSuccess) return e;
-  for (int ax = d - 2; ax >= 0; --ax) {
-    bool last = (ax == 0);
-    e = run_pass(P, ax, 1, P.tmp, last ? out : P.tmp, nullptr, (last && add_x) ? x : nullptr, st);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  return green_apply_t<double2>(P.d, P.n, P.logn, P.tw, P.Dn, P.tmp, x, q, add_x, out, st);
+}
+
+cudaError_t fft_green_apply32(const FftPlan& P, const float2* x, const float* q, bool add_x,
+                              float2* out, cudaStream_t st) {
+  return green_apply_t<float2>(P.d, P.n, P.logn, P.tw32, P.Dn32, P.tmp32, x, q, add_x, out, st);
+}
+
+cudaError_t to_float(const double* a, float* b, long N, cudaStream_t st) {
+  to_float_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(a, b, N);
+  return cudaGetLastError();
 }
 
 }  // namespace sp

@@ -9,6 +9,10 @@
 
 namespace sp {
 
+// Levels with few fronts keep the inverses of the diagonal blocks of this size of
+// L11 and U11 (the sweep is a chain of k / kInvBlockSize matrix-vector steps).
+constexpr int kInvBlockSize = 512;
+
 // Optional per-kernel-class timing with CUDA events on the launching stream.
 enum ProfClass {
   PROF_ASSEMBLE = 0,  // zeroing, assembly of P, extend-add, front scale
@@ -76,13 +80,19 @@ struct FftPlan {
   double2* tw = nullptr;   // exp(-2 pi i t / n), t < n/2
   double* Dn = nullptr;    // 1 / (4 pi^2 |k|^2 - s) / N, flat
   double2* tmp = nullptr;  // N work
+  float2* tw32 = nullptr;  // FP32 copies for the mixed-precision inner solve
+  float* Dn32 = nullptr;
+  float2* tmp32 = nullptr;
 };
 // w = x + G (q x) when q != null and add_x; g = G f when q == null and !add_x.
 cudaError_t fft_green_apply(const FftPlan& P, const double2* x, const double* q, bool add_x,
                             double2* out, cudaStream_t st);
+cudaError_t fft_green_apply32(const FftPlan& P, const float2* x, const float* q, bool add_x,
+                              float2* out, cudaStream_t st);
+cudaError_t to_float(const double* a, float* b, long N, cudaStream_t st);
 
 // ---------------------------------------------------------------- factor (sp_factor.cu)
-// scratch: 2 nf k^2 entries of the factor type when L.inv (triangular inverses)
+// scratch: 3 nf k^2 entries of the factor type when L.inv (triangular inverses)
 cudaError_t factor_level(int prec, int d, DevLevel& L, const DevLevel* child, const double* Qcat,
                          const double* Ccat, const double* q, double pivot_tol, int* status,
                          void* scratch, cudaStream_t st);

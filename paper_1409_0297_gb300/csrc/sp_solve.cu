@@ -5,12 +5,13 @@
 //      y1 = L11^{-1} Pi b1 and the update b2 - L21 y1 handed to the parent;
 //   3. the backward sweep, root to leaves: x1 = U11^{-1} (y1 - U12 x2).
 // Levels with many fronts: one CTA per front, right-hand side in shared memory,
-// triangular solves blocked by 32 (the 32 x 32 diagonal block is staged in shared
-// memory and resolved by one warp with shuffles, then all warps apply the block's
-// columns with coalesced column reads of the column-major front).
-// Levels with few fronts (L11, U11 replaced by their inverses at factor time):
-// the sweep is a pair of matrix-vector products, 16 rows per CTA, so the large
-// upper fronts are spread over the whole GPU.
+// triangular solves blocked by 32 (the inverse of each 32 x 32 diagonal block is
+// formed at factor time; the block step is a 32 x 32 matrix-vector product, then
+// all warps apply the block's columns with coalesced column reads of the
+// column-major front).
+// Levels with few fronts (the 512 x 512 diagonal blocks of L11, U11 replaced by
+// their inverses at factor time): the sweep is a short chain of matrix-vector
+// products, 16 rows per CTA, so the large upper fronts spread over the whole GPU.
 // VT = double2 (FP64 form) or float2 (FP32 form).
 #include "sp_internal.h"
 
@@ -126,6 +127,7 @@ __global__ void __launch_bounds__(256) forward_kernel(
   VT* b = reinterpret_cast<VT*>(smraw);  // m
   VT* b1 = b + m;                         // k (permuted eliminated part)
   __shared__ T Ld[kBS][kBS + 1];
+  __shared__ VT yd[kBS];
   const int f = blockIdx.x;
   const T* A = fronts + (long)f * m * m;
   gather_rhs(d, f, m, k, nb1, gidx, rhsQ, cupd, mc, kc, ea_map, b);
@@ -133,7 +135,6 @@ __global__ void __launch_bounds__(256) forward_kernel(
   for (int j = threadIdx.x; j < k; j += blockDim.x) b1[j] = b[pr[j]];
   __syncthreads();
   for (int j = threadIdx.x; j < k; j += blockDim.x) b[j] = b1[j];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int jb = 0; jb < k; jb += kBS) {
     const int bs = min(kBS, k - jb);
     for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
@@ -141,15 +142,23 @@ __global__ void __launch_bounds__(256) forward_kernel(
       Ld[i][j] = A[(jb + i) + (long)(jb + j) * m];
     }
     __syncthreads();
-    if (warp == 0) {
-      VT val = (lane < bs) ? b[jb + lane] : vzero<VT>();
-      for (int j = 0; j < bs; ++j) {
-        VT yj;
-        yj.x = __shfl_sync(0xffffffffu, val.x, j);
-        yj.y = __shfl_sync(0xffffffffu, val.y, j);
-        if (lane > j && lane < bs) axpy_neg(val, Ld[lane][j], yj);
+    // y_J = Linv_JJ b_J (the diagonal block holds the inverse, unit diagonal
+    // implied): 8 threads per row, partial sums reduced with shuffles
+    {
+      const int i = threadIdx.x >> 3, cl = threadIdx.x & 7;
+      VT acc = vzero<VT>();
+      if (i < bs)
+        for (int l = cl; l < i; l += 8) axpy(acc, Ld[i][l], b[jb + l]);
+      for (int o = 4; o > 0; o >>= 1) {
+        acc.x += __shfl_down_sync(0xffffffffu, acc.x, o, 8);
+        acc.y += __shfl_down_sync(0xffffffffu, acc.y, o, 8);
       }
-      if (lane < bs) b[jb + lane] = val;
+      if (cl == 0 && i < bs) {
+        VT bi = b[jb + i];
+        yd[i] = VT{bi.x + acc.x, bi.y + acc.y};
+      }
+      __syncthreads();
+      if (threadIdx.x < bs) b[jb + threadIdx.x] = yd[threadIdx.x];
     }
     __syncthreads();
     for (int r = jb + bs + threadIdx.x; r < m; r += blockDim.x) {
@@ -172,6 +181,7 @@ __global__ void __launch_bounds__(256) backward_kernel(const T* __restrict__ fro
   extern __shared__ unsigned char smraw[];
   VT* xb = reinterpret_cast<VT*>(smraw);  // m: x1 then x2
   __shared__ T Ud[kBS][kBS + 1];
+  __shared__ VT xd[kBS];
   const int f = blockIdx.x;
   const T* A = fronts + (long)f * m * m;
   const int* gi = gidx + (long)f * m;
@@ -184,7 +194,6 @@ __global__ void __launch_bounds__(256) backward_kernel(const T* __restrict__ fro
     xb[i] = acc;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nblk = (k + kBS - 1) / kBS;
   for (int bi = nblk - 1; bi >= 0; --bi) {
     const int jb = bi * kBS;
@@ -194,20 +203,20 @@ __global__ void __launch_bounds__(256) backward_kernel(const T* __restrict__ fro
       Ud[i][j] = A[(jb + i) + (long)(jb + j) * m];
     }
     __syncthreads();
-    if (warp == 0) {
-      VT val = (lane < bs) ? xb[jb + lane] : vzero<VT>();
-      for (int j = bs - 1; j >= 0; --j) {
-        if (lane == j) {
-          const T dgi = Ud[j][j];
-          val.x /= dgi;
-          val.y /= dgi;
-        }
-        VT xj;
-        xj.x = __shfl_sync(0xffffffffu, val.x, j);
-        xj.y = __shfl_sync(0xffffffffu, val.y, j);
-        if (lane < j) axpy_neg(val, Ud[lane][j], xj);
+    // x_J = Uinv_JJ t_J (the diagonal block holds the inverse, upper part with
+    // the diagonal)
+    {
+      const int i = threadIdx.x >> 3, cl = threadIdx.x & 7;
+      VT acc = vzero<VT>();
+      if (i < bs)
+        for (int l = i + cl; l < bs; l += 8) axpy(acc, Ud[i][l], xb[jb + l]);
+      for (int o = 4; o > 0; o >>= 1) {
+        acc.x += __shfl_down_sync(0xffffffffu, acc.x, o, 8);
+        acc.y += __shfl_down_sync(0xffffffffu, acc.y, o, 8);
       }
-      if (lane < bs) xb[jb + lane] = val;
+      if (cl == 0 && i < bs) xd[i] = acc;
+      __syncthreads();
+      if (threadIdx.x < bs) xb[jb + threadIdx.x] = xd[threadIdx.x];
     }
     __syncthreads();
     for (int r = threadIdx.x; r < jb; r += blockDim.x) {
@@ -238,52 +247,55 @@ __global__ void __launch_bounds__(256) inv_gather_kernel(
   for (int j = k + threadIdx.x; j < m; j += blockDim.x) t[j] = b[j];
 }
 
-// Row-block matrix-vector product over columns [clo(r), chi(r)) of the front:
-// 16 rows per CTA, 16 column lanes per row, partial sums reduced in shared memory.
-// mode 0 (forward, rows [0,k)):   y1[r]  = v[r] + sum_{c<r} Linv[r,c] v[c],  v = Pi b1
-// mode 1 (forward, rows [k,m)):   upd[r] = b2[r] - sum_{c<k} L21[r,c] y1[c]
-// mode 2 (backward, rows [0,k)):  t[r]   = y1[r] - sum_{c in [k,m)} U12[r,c] x2[c]
-// mode 3 (backward, rows [0,k)):  x[r]   = sum_{c in [r,k)} Uinv[r,c] t[c]
+// Row-block matrix-vector products of the levels whose diagonal blocks (size
+// kInvBlockSize) hold the inverses of those of L11 / U11.  16 rows per CTA, 16
+// column lanes per row, partial sums reduced in shared memory.  [j0, j1) is the
+// current diagonal block.
+// mode 4 (forward, rows [j0,j1)):  tmp[r] -= sum_{c<j0} L[r,c] y[c]
+// mode 0 (forward, rows [j0,j1)):  y[r] = tmp[r] + sum_{j0<=c<r} Linv[r,c] tmp[c]
+// mode 1 (forward, rows [k,m)):    upd[r] = tmp[r] - sum_{c<k} L21[r,c] y[c]
+// mode 2 (backward, rows [0,k)):   tmp[r] = y[r] - sum_{k<=c<m} U12[r,c] x[c]
+// mode 6 (backward, rows [j0,j1)): tmp[r] -= sum_{j1<=c<k} U[r,c] y[c]
+// mode 3 (backward, rows [j0,j1)): y[r] = x[r] = sum_{r<=c<j1} Uinv[r,c] tmp[c]
+// (in the backward sweep y holds x1 once mode 2 has consumed y1)
 template <class VT, class T>
 __global__ void __launch_bounds__(256) inv_gemv_kernel(int mode, const T* __restrict__ fronts,
-                                                        int m, int k, const int* __restrict__ gidx,
-                                                        VT* tmp, VT* y, VT* upd, double2* x) {
+                                                        int m, int k, int j0, int j1,
+                                                        const int* __restrict__ gidx, VT* tmp,
+                                                        VT* y, VT* upd, double2* x) {
   extern __shared__ unsigned char smraw[];
-  VT* v = reinterpret_cast<VT*>(smraw);  // input vector
+  VT* v = reinterpret_cast<VT*>(smraw);  // input vector entries [vlo, vhi)
   __shared__ VT red[kRB][kRB + 1];
   const int f = blockIdx.y;
   const T* A = fronts + (long)f * m * m;
   VT* tf = tmp + (long)f * m;
-  int rlo, rhi, vlo, vhi;  // rows of this mode; columns [vlo, vhi) of the input vector
-  if (mode == 1) {
-    rlo = k; rhi = m; vlo = 0; vhi = k;
-  } else if (mode == 2) {
-    rlo = 0; rhi = k; vlo = k; vhi = m;
-  } else {
-    rlo = 0; rhi = k; vlo = 0; vhi = k;
+  VT* yf = y + (long)f * k;
+  int rlo, rhi, vlo, vhi;
+  switch (mode) {
+    case 4: rlo = j0; rhi = j1; vlo = 0; vhi = j0; break;
+    case 0: rlo = j0; rhi = j1; vlo = j0; vhi = j1; break;
+    case 1: rlo = k; rhi = m; vlo = 0; vhi = k; break;
+    case 2: rlo = 0; rhi = k; vlo = k; vhi = m; break;
+    case 6: rlo = j0; rhi = j1; vlo = j1; vhi = k; break;
+    default: rlo = j0; rhi = j1; vlo = j0; vhi = j1; break;  // 3
   }
-  // input vector into shared memory
   for (int c = vlo + threadIdx.x; c < vhi; c += blockDim.x) {
     VT val;
     if (mode == 0 || mode == 3) val = tf[c];
-    else if (mode == 1) val = y[(long)f * k + c];
-    else val = from_d2<VT>(x[gidx[(long)f * m + c]]);
+    else if (mode == 2) val = from_d2<VT>(x[gidx[(long)f * m + c]]);
+    else val = yf[c];
     v[c - vlo] = val;
   }
   __syncthreads();
   const int tx = threadIdx.x % kRB, ty = threadIdx.x / kRB;
   const int r0 = rlo + blockIdx.x * kRB;
   const int r = r0 + tx;
-  int cb, ce;  // column range of the whole row block (union over its rows)
-  if (mode == 0) {
-    cb = 0; ce = min(r0 + kRB, k);
-  } else if (mode == 3) {
-    cb = r0; ce = k;
-  } else {
-    cb = vlo; ce = vhi;
-  }
+  int cb = vlo, ce = vhi;  // column range of the whole row block
+  if (mode == 0) ce = min(r0 + kRB, vhi);
+  if (mode == 3) cb = max(r0, vlo);
   VT acc = vzero<VT>();
   if (r < rhi) {
+#pragma unroll 4
     for (int c = cb + ty; c < ce; c += kRB) {
       bool use = (mode == 0) ? (c < r) : (mode == 3) ? (c >= r) : true;
       if (use) axpy(acc, A[r + (long)c * m], v[c - vlo]);
@@ -297,17 +309,31 @@ __global__ void __launch_bounds__(256) inv_gemv_kernel(int mode, const T* __rest
       s.x += red[l][tx].x;
       s.y += red[l][tx].y;
     }
-    if (mode == 0) {
-      VT o = tf[r];
-      y[(long)f * k + r] = VT{o.x + s.x, o.y + s.y};
-    } else if (mode == 1) {
-      VT o = tf[r];
-      upd[(long)f * (m - k) + (r - k)] = VT{o.x - s.x, o.y - s.y};
-    } else if (mode == 2) {
-      VT o = y[(long)f * k + r];
-      tf[r] = VT{o.x - s.x, o.y - s.y};
-    } else {
-      x[gidx[(long)f * m + r]] = to_d2(s);
+    switch (mode) {
+      case 4:
+      case 6: {
+        VT o = tf[r];
+        tf[r] = VT{o.x - s.x, o.y - s.y};
+        break;
+      }
+      case 0: {
+        VT o = tf[r];
+        yf[r] = VT{o.x + s.x, o.y + s.y};
+        break;
+      }
+      case 1: {
+        VT o = tf[r];
+        upd[(long)f * (m - k) + (r - k)] = VT{o.x - s.x, o.y - s.y};
+        break;
+      }
+      case 2: {
+        VT o = yf[r];
+        tf[r] = VT{o.x - s.x, o.y - s.y};
+        break;
+      }
+      default:
+        yf[r] = s;
+        x[gidx[(long)f * m + r]] = to_d2(s);
     }
   }
 }
@@ -359,15 +385,23 @@ cudaError_t forward_t(int d, DevLevel& L, const DevLevel* child, const void* rhs
   } else {
     inv_gather_kernel<VT><<<L.nf, 256, sizeof(VT) * L.m, st>>>(
         d, L.m, L.k, L.nb1, L.gidx, L.perm, (const VT*)rhsQ, cup, L.mc, L.kc, L.ea_map, (VT*)L.tmp);
-    dim3 g0((L.k + kRB - 1) / kRB, L.nf);
-    inv_gemv_kernel<VT, T><<<g0, 256, sizeof(VT) * L.k, st>>>(0, (const T*)L.front, L.m, L.k,
-                                                              L.gidx, (VT*)L.tmp, (VT*)L.y,
-                                                              (VT*)L.upd, nullptr);
-    launches = 2;
+    launches = 1;
+    for (int j0 = 0; j0 < L.k; j0 += kInvBlockSize) {
+      const int j1 = min(L.k, j0 + kInvBlockSize);
+      dim3 g((j1 - j0 + kRB - 1) / kRB, L.nf);
+      if (j0 > 0) {
+        inv_gemv_kernel<VT, T><<<g, 256, sizeof(VT) * j0, st>>>(
+            4, (const T*)L.front, L.m, L.k, j0, j1, L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, nullptr);
+        ++launches;
+      }
+      inv_gemv_kernel<VT, T><<<g, 256, sizeof(VT) * (j1 - j0), st>>>(
+          0, (const T*)L.front, L.m, L.k, j0, j1, L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, nullptr);
+      ++launches;
+    }
     if (L.m > L.k) {
       dim3 g1((L.m - L.k + kRB - 1) / kRB, L.nf);
-      inv_gemv_kernel<VT, T><<<g1, 256, sizeof(VT) * L.k, st>>>(1, (const T*)L.front, L.m, L.k,
-                                                                L.gidx, (VT*)L.tmp, (VT*)L.y,
+      inv_gemv_kernel<VT, T><<<g1, 256, sizeof(VT) * L.k, st>>>(1, (const T*)L.front, L.m, L.k, 0,
+                                                                L.k, L.gidx, (VT*)L.tmp, (VT*)L.y,
                                                                 (VT*)L.upd, nullptr);
       ++launches;
     }
@@ -386,17 +420,30 @@ cudaError_t backward_t(DevLevel& L, double2* x, cudaStream_t st) {
     backward_kernel<VT, T><<<L.nf, 256, sizeof(VT) * (size_t)L.m, st>>>(
         (const T*)L.front, L.m, L.k, L.gidx, (const VT*)L.y, x);
   } else {
-    dim3 g((L.k + kRB - 1) / kRB, L.nf);
+    launches = 0;
     if (L.m > L.k) {
+      dim3 g((L.k + kRB - 1) / kRB, L.nf);
       inv_gemv_kernel<VT, T><<<g, 256, sizeof(VT) * (L.m - L.k), st>>>(
-          2, (const T*)L.front, L.m, L.k, L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x);
+          2, (const T*)L.front, L.m, L.k, 0, L.k, L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x);
+      ++launches;
     } else {
       // root: t = y1
-      cudaMemcpyAsync(L.tmp, L.y, sizeof(VT) * (size_t)L.k * L.nf, cudaMemcpyDeviceToDevice, st);
+      cudaMemcpy2DAsync(L.tmp, sizeof(VT) * L.m, L.y, sizeof(VT) * L.k, sizeof(VT) * L.k, L.nf,
+                        cudaMemcpyDeviceToDevice, st);
     }
-    inv_gemv_kernel<VT, T><<<g, 256, sizeof(VT) * L.k, st>>>(3, (const T*)L.front, L.m, L.k, L.gidx,
-                                                             (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x);
-    launches = 2;
+    const int nbk = (L.k + kInvBlockSize - 1) / kInvBlockSize;
+    for (int bi = nbk - 1; bi >= 0; --bi) {
+      const int j0 = bi * kInvBlockSize, j1 = min(L.k, j0 + kInvBlockSize);
+      dim3 g((j1 - j0 + kRB - 1) / kRB, L.nf);
+      if (j1 < L.k) {
+        inv_gemv_kernel<VT, T><<<g, 256, sizeof(VT) * (L.k - j1), st>>>(
+            6, (const T*)L.front, L.m, L.k, j0, j1, L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x);
+        ++launches;
+      }
+      inv_gemv_kernel<VT, T><<<g, 256, sizeof(VT) * (j1 - j0), st>>>(
+          3, (const T*)L.front, L.m, L.k, j0, j1, L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x);
+      ++launches;
+    }
   }
   ps.done(L.nf * sizeof(T) * (kk * (kk + 1) / 2 + mk * kk), launches, st);
   return cudaGetLastError();
