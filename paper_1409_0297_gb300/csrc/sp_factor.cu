@@ -12,6 +12,8 @@
 // Every front of a level has the same size, so each step is one batched launch
 // over all fronts of the level.  Fronts are column-major m x m.  T = double for
 // the FP64 form, float for the FP32 preconditioner form.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cfloat>
 
@@ -159,6 +161,147 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(T* fronts, int m, int k, 
   }
 }
 
+// Panel LU of a large front by a cluster of kCL CTAs (thread-block cluster, one
+// front per cluster).  The panel rows [j0, m) are split in kCL contiguous chunks
+// of physical rows ("slots"), each staged in its CTA's shared memory.  Rows are
+// never moved during the panel: every CTA keeps the same position <-> slot maps
+// and applies the pivot interchanges to the maps only.  Per pivot column the CTAs
+// publish their best candidate (double-buffered), one cluster barrier, every CTA
+// reads all candidates and the pivot row through distributed shared memory
+// (the pivot row is final from then on), updates the maps and its own rows.  The
+// panel is written back in position order.  Same pivots and results as
+// lu_panel_kernel (largest magnitude, ties to the smallest position).
+constexpr int kCL = 8;
+template <class T>
+__global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(256)
+    lu_panel_cluster_kernel(T* fronts, int m, int k, int j0, int jb, int* piv,
+                            const double* scale, double ptol, int* status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int f = blockIdx.x / kCL;
+  T* A = fronts + (long)f * m * m;
+  const int rows = m - j0, kl = k - j0;
+  const int chunk = (rows + kCL - 1) / kCL;
+  const int rbeg = rank * chunk, rend = min(rows, rbeg + chunk);
+  const int nmy = max(0, rend - rbeg);
+  extern __shared__ unsigned char smraw[];
+  T* P = reinterpret_cast<T*>(smraw);                        // chunk x jb, column-major
+  int* pos2slot = reinterpret_cast<int*>(P + (long)chunk * jb);  // rows
+  int* slot2pos = pos2slot + rows;                            // rows
+  __shared__ double cval[2];
+  __shared__ int cidx[2];
+  __shared__ T prow[kNB];
+  __shared__ double wv[8];
+  __shared__ int wi[8];
+  __shared__ int s_slot;
+  const double thresh = ptol * scale[f];
+  for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+    pos2slot[i] = i;
+    slot2pos[i] = i;
+  }
+  for (long e = threadIdx.x; e < (long)nmy * jb; e += blockDim.x) {
+    int r = (int)(e % nmy), c = (int)(e / nmy);
+    P[r + (long)c * chunk] = A[(j0 + rbeg + r) + (long)(j0 + c) * m];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int jj = 0; jj < jb; ++jj) {
+    // best candidate among my slots whose position is in [jj, kl)
+    double best = -1.0;
+    int bp = -1;
+    for (int sl = rbeg + threadIdx.x; sl < rend; sl += blockDim.x) {
+      const int ps = slot2pos[sl];
+      if (ps < jj || ps >= kl) continue;
+      double v = fabs((double)P[(sl - rbeg) + (long)jj * chunk]);
+      if (v > best || (v == best && ps < bp)) {
+        best = v;
+        bp = ps;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_down_sync(0xffffffffu, best, o);
+      int op = __shfl_down_sync(0xffffffffu, bp, o);
+      if (ov > best || (ov == best && op >= 0 && (bp < 0 || op < bp))) {
+        best = ov;
+        bp = op;
+      }
+    }
+    if (lane == 0) {
+      wv[warp] = best;
+      wi[warp] = bp;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b0 = wv[0];
+      int i0 = wi[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+        if (wv[w] > b0 || (wv[w] == b0 && wi[w] >= 0 && (i0 < 0 || wi[w] < i0))) {
+          b0 = wv[w];
+          i0 = wi[w];
+        }
+      cval[jj & 1] = b0;
+      cidx[jj & 1] = i0;
+    }
+    cl.sync();  // candidates of column jj published
+    if (warp == 0) {
+      double b0 = -1.0;
+      int i0 = -1;
+      if (lane < kCL) {
+        b0 = *cl.map_shared_rank(&cval[jj & 1], lane);
+        i0 = *cl.map_shared_rank(&cidx[jj & 1], lane);
+        if (i0 < 0) b0 = -1.0;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_down_sync(0xffffffffu, b0, o);
+        int oi = __shfl_down_sync(0xffffffffu, i0, o);
+        if (ov > b0 || (ov == b0 && oi >= 0 && (i0 < 0 || oi < i0))) {
+          b0 = ov;
+          i0 = oi;
+        }
+      }
+      if (lane == 0) {
+        const int p = i0 < 0 ? jj : i0;  // position of the pivot row
+        const int sa = pos2slot[jj], sb = pos2slot[p];
+        pos2slot[jj] = sb;
+        pos2slot[p] = sa;
+        slot2pos[sb] = jj;
+        slot2pos[sa] = p;
+        s_slot = sb;
+        if (rank == 0) {
+          piv[(long)f * k + j0 + jj] = j0 + p;
+          if (!(b0 > thresh)) atomicOr(status, 1);
+        }
+      }
+    }
+    __syncthreads();
+    const int sp = s_slot, owner = sp / chunk;
+    if (threadIdx.x < jb) {
+      const T* Po = cl.map_shared_rank(P, owner);
+      prow[threadIdx.x] = Po[(sp - owner * chunk) + (long)threadIdx.x * chunk];
+    }
+    __syncthreads();
+    T pv = prow[jj];
+    if (!(fabs((double)pv) > 0.0)) pv = (T)(thresh > 0 ? thresh : 1e-30);
+    const T inv = (T)1 / pv;
+    for (int sl = rbeg + threadIdx.x; sl < rend; sl += blockDim.x) {
+      if (slot2pos[sl] <= jj) continue;
+      T* pr = P + (sl - rbeg);
+      T l = pr[(long)jj * chunk] * inv;
+      pr[(long)jj * chunk] = l;
+      for (int c = jj + 1; c < jb; ++c) pr[(long)c * chunk] -= l * prow[c];
+    }
+    __syncthreads();
+  }
+  // the pivot rows read by other CTAs are final, but keep this CTA's shared
+  // memory alive until every CTA has read its last pivot row
+  cl.sync();
+  for (long e = threadIdx.x; e < (long)nmy * jb; e += blockDim.x) {
+    int r = (int)(e % nmy), c = (int)(e / nmy);
+    A[(j0 + slot2pos[rbeg + r]) + (long)(j0 + c) * m] = P[r + (long)c * chunk];
+  }
+}
+
 // Interchanges of the panel's pivots on every column outside the panel, and the
 // row-block solve A[j0:j0+jb, c] = L_pp^{-1} A[j0:j0+jb, c] right of it.  Thread
 // cc < j0 owns left column cc (interchanges only); thread cc >= j0 owns column
@@ -268,40 +411,41 @@ __global__ void __launch_bounds__(256) gemm_sub_kernel(int M, int N, int K, cons
 // upper (A[r, l] = 0 for l < r); tri_b = 1 when B is lower (B[l, c] = 0 for
 // l < c), 2 when upper (B[l, c] = 0 for l > c).  Zero tiles are skipped, entries
 // inside a computed tile must hold their zeros.  beta is 0 or 1.
-template <class T>
+template <class T, int TILE>
 __global__ void __launch_bounds__(256) gemm_gen_kernel(int M, int N, int K, T alpha, int beta_one,
                                                        const T* A, int lda, long sA, const T* B,
                                                        int ldb, long sB, T* C, int ldc, long sC,
                                                        int tilesM, int tri_a, int tri_b, int nb2,
                                                        long sA2, long sB2, long sC2) {
+  constexpr int R = TILE / 16;  // outputs per thread along each dimension
   // batch index = outer * nb2 + inner with strides (sA, sB, sC) and (sA2, sB2, sC2)
   const long bo = blockIdx.y / nb2, bi = blockIdx.y % nb2;
   A += bo * sA + bi * sA2;
   B += bo * sB + bi * sB2;
   C += bo * sC + bi * sC2;
   const int tr = blockIdx.x % tilesM, tc = blockIdx.x / tilesM;
-  const int r0 = tr * kTile, c0 = tc * kTile;
+  const int r0 = tr * TILE, c0 = tc * TILE;
   int klo = 0, khi = K;
-  if (tri_a == 1) khi = min(khi, r0 + kTile);
+  if (tri_a == 1) khi = min(khi, r0 + TILE);
   if (tri_a == 2) klo = max(klo, r0);
   if (tri_b == 1) klo = max(klo, c0);
-  if (tri_b == 2) khi = min(khi, c0 + kTile);
-  __shared__ T As[kNB][kTile];
-  __shared__ T Bs[kNB][kTile + 1];
+  if (tri_b == 2) khi = min(khi, c0 + TILE);
+  __shared__ T As[kNB][TILE];
+  __shared__ T Bs[kNB][TILE + 1];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  T acc[4][4];
+  T acc[R][R];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < R; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+    for (int b = 0; b < R; ++b) acc[a][b] = 0;
   for (int k0 = klo; k0 < khi; k0 += kNB) {
     const int kc = min(kNB, khi - k0);
-    for (int e = threadIdx.x; e < kNB * kTile; e += blockDim.x) {
-      int i = e % kTile, l = e / kTile;
+    for (int e = threadIdx.x; e < kNB * TILE; e += blockDim.x) {
+      int i = e % TILE, l = e / TILE;
       int r = r0 + i;
       As[l][i] = (r < M && l < kc) ? A[r + (long)(k0 + l) * lda] : (T)0;
     }
-    for (int e = threadIdx.x; e < kNB * kTile; e += blockDim.x) {
+    for (int e = threadIdx.x; e < kNB * TILE; e += blockDim.x) {
       int l = e % kNB, jc = e / kNB;
       int c = c0 + jc;
       Bs[l][jc] = (c < N && l < kc) ? B[(k0 + l) + (long)c * ldb] : (T)0;
@@ -309,24 +453,24 @@ __global__ void __launch_bounds__(256) gemm_gen_kernel(int M, int N, int K, T al
     __syncthreads();
 #pragma unroll 4
     for (int l = 0; l < kNB; ++l) {
-      T av[4], bv[4];
+      T av[R], bv[R];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) av[a] = As[l][tx + 16 * a];
+      for (int a = 0; a < R; ++a) av[a] = As[l][tx + 16 * a];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) bv[b] = Bs[l][ty + 16 * b];
+      for (int b = 0; b < R; ++b) bv[b] = Bs[l][ty + 16 * b];
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < R; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+        for (int b = 0; b < R; ++b) acc[a][b] += av[a] * bv[b];
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int b = 0; b < 4; ++b) {
+  for (int b = 0; b < R; ++b) {
     int c = c0 + ty + 16 * b;
     if (c >= N) continue;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
+    for (int a = 0; a < R; ++a) {
       int r = r0 + tx + 16 * a;
       if (r < M) {
         T v = alpha * acc[a][b];
@@ -473,9 +617,20 @@ void gemm_gen(int M, int N, int K, T alpha, bool beta_one, const T* A, int lda, 
               int tri_b, cudaStream_t st, int nb2 = 1, long sA2 = 0, long sB2 = 0, long sC2 = 0) {
   if (M <= 0 || N <= 0 || K <= 0 || batch <= 0 || nb2 <= 0) return;
   int tilesM = (M + kTile - 1) / kTile, tilesN = (N + kTile - 1) / kTile;
+  if ((long)tilesM * tilesN * batch * nb2 < 304) {
+    // small problem: 32 x 32 tiles give four times the CTAs
+    tilesM = (M + 31) / 32;
+    tilesN = (N + 31) / 32;
+    dim3 g(tilesM * tilesN, batch * nb2);
+    gemm_gen_kernel<T, 32><<<g, 256, 0, st>>>(M, N, K, alpha, beta_one ? 1 : 0, A, lda, sA, B, ldb,
+                                              sB, C, ldc, sC, tilesM, tri_a, tri_b, nb2, sA2, sB2,
+                                              sC2);
+    return;
+  }
   dim3 g(tilesM * tilesN, batch * nb2);
-  gemm_gen_kernel<T><<<g, 256, 0, st>>>(M, N, K, alpha, beta_one ? 1 : 0, A, lda, sA, B, ldb, sB,
-                                        C, ldc, sC, tilesM, tri_a, tri_b, nb2, sA2, sB2, sC2);
+  gemm_gen_kernel<T, kTile><<<g, 256, 0, st>>>(M, N, K, alpha, beta_one ? 1 : 0, A, lda, sA, B, ldb,
+                                               sB, C, ldc, sC, tilesM, tri_a, tri_b, nb2, sA2, sB2,
+                                               sC2);
 }
 
 // Replace the diagonal blocks (size Bsz, a power of two >= 32) of L11 and U11 of
@@ -540,12 +695,19 @@ void invert_triangles(DevLevel& L, T* scratch, int Bsz, cudaStream_t st) {
   trinv_store_kernel<T><<<g, 256, 0, st>>>(F, m, Xl, Xu, k, Bsz);
 }
 
+// Panel staging: one CTA when the 32-column panel fits in 160 KB of shared
+// memory, else a cluster of kCL CTAs (each holding m / kCL rows).  Returns the
+// panel width, 0 if neither fits.
 template <class T>
 int panel_width(int m) {
-  // widest of 32 / 16 / 8 whose staged panel fits in 160 KB of shared memory
-  for (int jb = kNB; jb >= 8; jb >>= 1)
-    if ((size_t)m * jb * sizeof(T) <= 160 * 1024) return jb;
+  if ((size_t)m * kNB * sizeof(T) <= 160 * 1024) return kNB;
+  if ((size_t)((m + kCL - 1) / kCL) * kNB * sizeof(T) + 2 * sizeof(int) * (size_t)m <= 160 * 1024)
+    return kNB;
   return 0;
+}
+template <class T>
+bool panel_clustered(int m) {
+  return (size_t)m * kNB * sizeof(T) > 160 * 1024;
 }
 
 template <class T>
@@ -555,6 +717,8 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(lu_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(lu_panel_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
     attr = true;
   }
   const long mm = (long)L.m * L.m;
@@ -594,8 +758,15 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
     double pf = 0;
     for (int j = j0; j < j0 + jb; ++j) pf += (double)(L.m - j - 1) * (1.0 + 2.0 * (j0 + jb - j - 1));
     ProfScope pp(PROF_LU_PANEL, st);
-    size_t sm = sizeof(T) * (size_t)(L.m - j0) * jb;
-    lu_panel_kernel<T><<<L.nf, 256, sm, st>>>(F, L.m, L.k, j0, jb, L.piv, L.scale, ptol, status);
+    if (panel_clustered<T>(L.m)) {
+      size_t sm = sizeof(T) * (size_t)((L.m - j0 + kCL - 1) / kCL) * jb +
+                  2 * sizeof(int) * (size_t)(L.m - j0);
+      lu_panel_cluster_kernel<T><<<L.nf * kCL, 256, sm, st>>>(F, L.m, L.k, j0, jb, L.piv, L.scale,
+                                                              ptol, status);
+    } else {
+      size_t sm = sizeof(T) * (size_t)(L.m - j0) * jb;
+      lu_panel_kernel<T><<<L.nf, 256, sm, st>>>(F, L.m, L.k, j0, jb, L.piv, L.scale, ptol, status);
+    }
     pp.done(pf * L.nf, 1, st);
     int rem = L.m - j0 - jb;
     if (rem + j0 > 0) {

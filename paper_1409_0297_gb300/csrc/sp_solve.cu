@@ -258,14 +258,15 @@ __global__ void __launch_bounds__(256) inv_gather_kernel(
 // mode 6 (backward, rows [j0,j1)): tmp[r] -= sum_{j1<=c<k} U[r,c] y[c]
 // mode 3 (backward, rows [j0,j1)): y[r] = x[r] = sum_{r<=c<j1} Uinv[r,c] tmp[c]
 // (in the backward sweep y holds x1 once mode 2 has consumed y1)
-template <class VT, class T>
+template <class VT, class T, int RB>
 __global__ void __launch_bounds__(256) inv_gemv_kernel(int mode, const T* __restrict__ fronts,
                                                         int m, int k, int j0, int j1,
                                                         const int* __restrict__ gidx, VT* tmp,
                                                         VT* y, VT* upd, double2* x) {
   extern __shared__ unsigned char smraw[];
   VT* v = reinterpret_cast<VT*>(smraw);  // input vector entries [vlo, vhi)
-  __shared__ VT red[kRB][kRB + 1];
+  constexpr int CL = 256 / RB;  // column lanes per row
+  __shared__ VT red[CL][RB + 1];
   const int f = blockIdx.y;
   const T* A = fronts + (long)f * m * m;
   VT* tf = tmp + (long)f * m;
@@ -287,16 +288,16 @@ __global__ void __launch_bounds__(256) inv_gemv_kernel(int mode, const T* __rest
     v[c - vlo] = val;
   }
   __syncthreads();
-  const int tx = threadIdx.x % kRB, ty = threadIdx.x / kRB;
-  const int r0 = rlo + blockIdx.x * kRB;
+  const int tx = threadIdx.x % RB, ty = threadIdx.x / RB;
+  const int r0 = rlo + blockIdx.x * RB;
   const int r = r0 + tx;
   int cb = vlo, ce = vhi;  // column range of the whole row block
-  if (mode == 0) ce = min(r0 + kRB, vhi);
+  if (mode == 0) ce = min(r0 + RB, vhi);
   if (mode == 3) cb = max(r0, vlo);
   VT acc = vzero<VT>();
   if (r < rhi) {
 #pragma unroll 4
-    for (int c = cb + ty; c < ce; c += kRB) {
+    for (int c = cb + ty; c < ce; c += CL) {
       bool use = (mode == 0) ? (c < r) : (mode == 3) ? (c >= r) : true;
       if (use) axpy(acc, A[r + (long)c * m], v[c - vlo]);
     }
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(256) inv_gemv_kernel(int mode, const T* __rest
   __syncthreads();
   if (ty == 0 && r < rhi) {
     VT s = red[0][tx];
-    for (int l = 1; l < kRB; ++l) {
+    for (int l = 1; l < CL; ++l) {
       s.x += red[l][tx].x;
       s.y += red[l][tx].y;
     }
@@ -363,7 +364,25 @@ void set_attrs() {
   cudaFuncSetAttribute(forward_kernel<VT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(backward_kernel<VT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(inv_gather_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(inv_gemv_kernel<VT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(inv_gemv_kernel<VT, T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(inv_gemv_kernel<VT, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+// One inv_gemv launch over rows [rlo, rhi) of every front: 16 rows per CTA, or 4
+// rows per CTA (64 column lanes) when that leaves fewer CTAs than SMs.
+template <class VT, class T>
+void inv_gemv(int mode, DevLevel& L, int j0, int j1, int rlo, int rhi, size_t smem, double2* x,
+              cudaStream_t st) {
+  const int rows = rhi - rlo;
+  if ((long)((rows + 15) / 16) * L.nf >= 152) {
+    dim3 g((rows + 15) / 16, L.nf);
+    inv_gemv_kernel<VT, T, 16><<<g, 256, smem, st>>>(mode, (const T*)L.front, L.m, L.k, j0, j1,
+                                                     L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x);
+  } else {
+    dim3 g((rows + 3) / 4, L.nf);
+    inv_gemv_kernel<VT, T, 4><<<g, 256, smem, st>>>(mode, (const T*)L.front, L.m, L.k, j0, j1,
+                                                    L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x);
+  }
 }
 
 template <class VT>
@@ -388,21 +407,15 @@ cudaError_t forward_t(int d, DevLevel& L, const DevLevel* child, const void* rhs
     launches = 1;
     for (int j0 = 0; j0 < L.k; j0 += kInvBlockSize) {
       const int j1 = min(L.k, j0 + kInvBlockSize);
-      dim3 g((j1 - j0 + kRB - 1) / kRB, L.nf);
       if (j0 > 0) {
-        inv_gemv_kernel<VT, T><<<g, 256, sizeof(VT) * j0, st>>>(
-            4, (const T*)L.front, L.m, L.k, j0, j1, L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, nullptr);
+        inv_gemv<VT, T>(4, L, j0, j1, j0, j1, sizeof(VT) * j0, nullptr, st);
         ++launches;
       }
-      inv_gemv_kernel<VT, T><<<g, 256, sizeof(VT) * (j1 - j0), st>>>(
-          0, (const T*)L.front, L.m, L.k, j0, j1, L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, nullptr);
+      inv_gemv<VT, T>(0, L, j0, j1, j0, j1, sizeof(VT) * (j1 - j0), nullptr, st);
       ++launches;
     }
     if (L.m > L.k) {
-      dim3 g1((L.m - L.k + kRB - 1) / kRB, L.nf);
-      inv_gemv_kernel<VT, T><<<g1, 256, sizeof(VT) * L.k, st>>>(1, (const T*)L.front, L.m, L.k, 0,
-                                                                L.k, L.gidx, (VT*)L.tmp, (VT*)L.y,
-                                                                (VT*)L.upd, nullptr);
+      inv_gemv<VT, T>(1, L, 0, L.k, L.k, L.m, sizeof(VT) * L.k, nullptr, st);
       ++launches;
     }
   }
@@ -422,9 +435,7 @@ cudaError_t backward_t(DevLevel& L, double2* x, cudaStream_t st) {
   } else {
     launches = 0;
     if (L.m > L.k) {
-      dim3 g((L.k + kRB - 1) / kRB, L.nf);
-      inv_gemv_kernel<VT, T><<<g, 256, sizeof(VT) * (L.m - L.k), st>>>(
-          2, (const T*)L.front, L.m, L.k, 0, L.k, L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x);
+      inv_gemv<VT, T>(2, L, 0, L.k, 0, L.k, sizeof(VT) * (L.m - L.k), x, st);
       ++launches;
     } else {
       // root: t = y1
@@ -434,14 +445,11 @@ cudaError_t backward_t(DevLevel& L, double2* x, cudaStream_t st) {
     const int nbk = (L.k + kInvBlockSize - 1) / kInvBlockSize;
     for (int bi = nbk - 1; bi >= 0; --bi) {
       const int j0 = bi * kInvBlockSize, j1 = min(L.k, j0 + kInvBlockSize);
-      dim3 g((j1 - j0 + kRB - 1) / kRB, L.nf);
       if (j1 < L.k) {
-        inv_gemv_kernel<VT, T><<<g, 256, sizeof(VT) * (L.k - j1), st>>>(
-            6, (const T*)L.front, L.m, L.k, j0, j1, L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x);
+        inv_gemv<VT, T>(6, L, j0, j1, j0, j1, sizeof(VT) * (L.k - j1), x, st);
         ++launches;
       }
-      inv_gemv_kernel<VT, T><<<g, 256, sizeof(VT) * (j1 - j0), st>>>(
-          3, (const T*)L.front, L.m, L.k, j0, j1, L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x);
+      inv_gemv<VT, T>(3, L, j0, j1, j0, j1, sizeof(VT) * (j1 - j0), x, st);
       ++launches;
     }
   }
