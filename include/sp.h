@@ -185,6 +185,21 @@ sp_status sp_medium_schrodinger(int d, int n, double ell, double E, const double
 sp_status sp_profile(sp_ctx *ctx, int enable);
 sp_status sp_profile_read(sp_ctx *ctx, int cap, double *ms, int *launches, double *work);
 
+/* g = G f for callers that cannot allocate device memory when they call (for
+ * example code running inside a CUDA-graph stream capture, or under a fixed,
+ * pre-carved memory budget).  No context and no allocation: the FFT passes use a
+ * file-scope device work array of 2^18 complex128 values (4 MiB, held by every
+ * device that loads the library until the process exits), so n^d <= 262144
+ * (e.g. 512^2, 64^3); larger grids, n not a power of two, d not 2 or 3, null or
+ * aliasing pointers return SP_ERR_ARG; a resonant s returns SP_ERR_RESONANT.
+ * f_dev, g_dev: n^d complex128 on the current device; stream: cudaStream_t or
+ * NULL.  All calls on a device share the work array: calls that may run
+ * concurrently on the GPU race and must be ordered by the caller.  The first call
+ * on a device looks up the array's address (cudaGetSymbolAddress) with that
+ * device current; make it before any stream capture.  The paper has no
+ * counterpart of this entry point; it is an allocation-free form of sp_green. */
+sp_status sp_green_static(int d, int n, double s, const void *f_dev, void *g_dev, void *stream);
+
 void sp_destroy(sp_ctx *ctx);
 const char *sp_status_str(sp_status st);
 

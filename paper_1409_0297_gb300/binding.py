@@ -23,7 +23,7 @@ EXPORTED = [
     "sp_default_opts", "sp_setup", "sp_factor", "sp_apply", "sp_solve", "sp_factor_host",
     "sp_solve_host", "sp_matvec", "sp_green", "sp_qapply", "sp_get_table", "sp_stencil_table",
     "sp_front_sizes", "sp_level_info", "sp_costs", "sp_medium_helmholtz", "sp_medium_schrodinger", "sp_profile",
-    "sp_profile_read", "sp_destroy", "sp_status_str",
+    "sp_profile_read", "sp_green_static", "sp_destroy", "sp_status_str",
 ]
 PROF_CLASSES = ["assemble", "lu_panel", "lu_trsm", "lu_gemm", "qapply", "forward", "backward",
                 "fft", "krylov", "lu_trinv"]
@@ -75,6 +75,7 @@ def _load() -> ctypes.CDLL:
         "sp_medium_schrodinger": (I, [I, I, D, D, P, pD, P]),
         "sp_profile": (I, [P, I]),
         "sp_profile_read": (I, [P, I, pD, pI, pD]),
+        "sp_green_static": (I, [I, I, D, P, P, P]),
         "sp_destroy": (V, [P]),
         "sp_status_str": (ctypes.c_char_p, [I]),
     }
@@ -265,6 +266,11 @@ def sp_profile_read(ctx: int) -> dict:
     ln = (ctypes.c_int * k)()
     _check(LIB.sp_profile_read(ctx, k, _dptr(ms), ln, _dptr(wk)), "sp_profile_read")
     return {c: (float(ms[i]), int(ln[i]), float(wk[i])) for i, c in enumerate(PROF_CLASSES)}
+
+
+def sp_green_static(d: int, n: int, s: float, f_dev: int, g_dev: int, stream: int = 0) -> None:
+    """g = G f without a context or any allocation (see include/sp.h)."""
+    _check(LIB.sp_green_static(d, n, float(s), f_dev, g_dev, stream), "sp_green_static")
 
 
 def sp_destroy(ctx: int) -> None:
