@@ -116,6 +116,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm_)}
 
 
+# ------------------------------------------------------------------ multi-GPU replicas
+def reduce_max(x: float, dist=None, device: str = "cuda") -> float:
+    """Max over ranks (one rank per GPU; every rank times its own replica)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(solves_per_step: int, world: int, ms_per_step_max: float) -> float:
+    """Whole-job solves/s: every rank solves the same step's problems independently."""
+    return solves_per_step * world / (ms_per_step_max / 1e3)
+
+
 # ------------------------------------------------------------------ oracle (reference arm / cpu_baseline)
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -236,11 +252,7 @@ def run_ours(args):
         if dist:
             dist.barrier()
         wall = time.perf_counter() - t0
-        ms = sum(a.elapsed_time(e) for a, e in evs)
-        if dist:
-            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = reduce_max(sum(a.elapsed_time(e) for a, e in evs), dist)
         return ms / K, wall, infos
 
     fp64 = make(B.SP_PREC_FP64)
@@ -249,7 +261,7 @@ def run_ours(args):
     ms64, wall64, infos64 = timed(fp64, args.steps, args.warmup)
     clocks = sampler.stop()
     solves_per_step = len(probs)
-    value = solves_per_step * world / (ms64 / 1e3)
+    value = replica_value(solves_per_step, world, ms64)
 
     # e2e through the host-buffer entry points (pinned host memory)
     pin_q = [torch.from_numpy(p["q"]).pin_memory() for p in probs]
@@ -270,8 +282,8 @@ def run_ours(args):
     for _ in range(args.steps):
         step_host()
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    e2e_value = solves_per_step * world / e2e_s
+    e2e_s = reduce_max((time.perf_counter() - t0) / args.steps, dist)
+    e2e_value = replica_value(solves_per_step, world, e2e_s * 1e3)
 
     def profiled(ctxs):
         for c in ctxs:
@@ -323,7 +335,7 @@ def run_ours(args):
         ms32, _, infos32 = timed(fp32, args.steps, args.warmup)
         prof32 = profiled(fp32)
         chosen = {"form": "fp32 preconditioner (factor+sweeps), fp64 operator/GMRES",
-                  "value": solves_per_step * world / (ms32 / 1e3), "ms_per_step": ms32,
+                  "value": replica_value(solves_per_step, world, ms32), "ms_per_step": ms32,
                   "speedup_vs_fp64": ms64 / ms32,
                   "iters": [i["iters"] for i in infos32[:solves_per_step]],
                   "true_relres": [i["true_relres"] for i in infos32[:solves_per_step]],

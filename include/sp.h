@@ -91,9 +91,11 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
 /* Assemble P = Q + C diag(q) into the fronts and factor it (Section 2.2, Fig. nd):
  * per level, leaves to root, extend-add of the children's Schur complements,
  * partial-pivot LU of the eliminated block, panels and Schur update.  q_dev: N
- * real doubles on the device (kept by reference until the next sp_factor: the
- * operator I + G q of sp_solve/sp_matvec reads it).  Returns SP_ERR_SINGULAR if a
- * pivot is below pivot_tol * max|front| (the factor is then unusable). */
+ * real doubles on the device, copied into the context (the operator I + G q of
+ * sp_solve / sp_matvec uses the copy).  The work is replayed from a CUDA graph
+ * captured at set-up (direct launches while sp_profile is on).  Returns
+ * SP_ERR_SINGULAR if a pivot is below pivot_tol * max|front| (the factor is then
+ * unusable). */
 sp_status sp_factor(sp_ctx *ctx, const double *q_dev);
 
 /* z = P^{-1} Q r, the preconditioner of Section 2.2 ("u <= P^{-1} Q g"):

@@ -101,6 +101,12 @@ struct sp_ctx {
   Profiler prof;
   bool profiling = false;
   bool factored = false;
+  // CUDA graphs of the preconditioner application and of the factorisation,
+  // captured once at set-up on an internal stream and replayed on `stream`
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t g_apply = nullptr, g_factor = nullptr;
+  double2* app_in = nullptr;   // fixed input / output of the apply graph
+  double2* app_out = nullptr;
   double factor_entries = 0, factor_flops = 0, apply_bytes = 0;
 };
 
@@ -153,13 +159,54 @@ double perturb_shift(int d, int n, double s) {
   return s;
 }
 
-sp_status apply_impl(sp_ctx* c, const double2* r, double2* z) {
-  cudaStream_t st = c->stream;
+sp_status apply_direct(sp_ctx* c, const double2* r, double2* z, cudaStream_t st) {
   SP_CK(q_apply(c->prec, c->d, c->n, c->nl, c->qtypes, c->Tcat, c->Tcat32, r, c->rhsQ, st));
   for (int l = 0; l <= c->L; ++l)
     SP_CK(forward_level(c->prec, c->d, c->lv[l], l ? &c->lv[l - 1] : nullptr, c->rhsQ, st));
   for (int l = c->L; l >= 0; --l) SP_CK(backward_level(c->prec, c->d, c->lv[l], z, st));
   return SP_OK;
+}
+
+// z = P^{-1} Q r: the captured graph when there is one and no kernel timing is
+// requested (the graph reads app_in and writes app_out), else direct launches.
+sp_status apply_impl(sp_ctx* c, const double2* r, double2* z) {
+  cudaStream_t st = c->stream;
+  if (c->g_apply && !c->profiling) {
+    const size_t bytes = sizeof(double2) * (size_t)c->N;
+    SP_CK(cudaMemcpyAsync(c->app_in, r, bytes, cudaMemcpyDeviceToDevice, st));
+    SP_CK(cudaGraphLaunch(c->g_apply, st));
+    SP_CK(cudaMemcpyAsync(z, c->app_out, bytes, cudaMemcpyDeviceToDevice, st));
+    return SP_OK;
+  }
+  return apply_direct(c, r, z, st);
+}
+
+sp_status factor_direct(sp_ctx* c, const double* q, cudaStream_t st) {
+  SP_CK(cudaMemsetAsync(c->status, 0, sizeof(int), st));
+  for (int l = 0; l <= c->L; ++l)
+    SP_CK(factor_level(c->prec, c->d, c->lv[l], l ? &c->lv[l - 1] : nullptr, c->Qcat, c->Ccat, q,
+                       c->opts.pivot_tol, c->status, c->scratch, st));
+  return SP_OK;
+}
+
+// Captures fn(cap stream) into an executable graph; leaves *out null on failure
+// (the callers then launch directly).
+template <class Fn>
+void capture_graph(sp_ctx* c, cudaGraphExec_t* out, Fn fn) {
+  *out = nullptr;
+  if (!c->cap) return;
+  if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  sp_status st = fn(c->cap);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+  if (st == SP_OK && e == cudaSuccess && g) {
+    if (cudaGraphInstantiate(out, g, 0) != cudaSuccess) *out = nullptr;
+  }
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
 }
 
 }  // namespace
@@ -330,6 +377,9 @@ void sp_destroy(sp_ctx* c) {
   for (void* p : c->allocs) cudaFree(p);
   if (c->host_sc) cudaFreeHost(c->host_sc);
   c->prof.destroy();
+  if (c->g_apply) cudaGraphExecDestroy(c->g_apply);
+  if (c->g_factor) cudaGraphExecDestroy(c->g_factor);
+  if (c->cap) cudaStreamDestroy(c->cap);
   cudaSetDevice(dev);
   delete c;
 }
@@ -449,8 +499,10 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
     SP_CK(dalloc(c.get(), &D.upd, vsz * (size_t)S.nf * std::max(1, S.m - S.k)));
     SP_CK(dalloc(c.get(), &D.y, vsz * (size_t)S.nf * std::max(1, S.k)));
     if (factor_panel_width(prec, S.m) == 0) return SP_ERR_ARG;  // front too large to stage
-    // few fronts: keep the inverses of L11 and U11 so the sweeps spread over the GPU
-    D.inv = S.nf < 152;
+    // few fronts: keep the inverses of the diagonal blocks of L11 and U11 so the
+    // sweeps spread over the GPU; in the FP32 form every level does (the block
+    // inverses cost little in FP32 and the sweeps become matrix-vector products)
+    D.inv = S.nf < 152 || prec == SP_PREC_FP32;
     if (D.inv) {
       SP_CK(dalloc(c.get(), &D.tmp, vsz * (size_t)S.nf * S.m));
       scratch_bytes = std::max(scratch_bytes, 3 * fsz * (size_t)S.nf * S.k * S.k);
@@ -514,6 +566,22 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   SP_CK(dalloc(c.get(), &c->K.partial, sizeof(double2) * (size_t)c->K.nblk * 1024));
   SP_CK(dalloc(c.get(), &c->K.h, sizeof(double2) * 1024));
   SP_CK(cudaMallocHost(&c->host_sc, 8 * sizeof(double)));
+  SP_CK(dalloc(c.get(), &c->app_in, sizeof(double2) * N));
+  SP_CK(dalloc(c.get(), &c->app_out, sizeof(double2) * N));
+  SP_CK(cudaMemset(c->qbuf, 0, sizeof(double) * N));
+  SP_CK(cudaDeviceSynchronize());
+  // graphs (a failed capture only means direct launches later)
+  if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    c->cap = nullptr;
+  }
+  {
+    sp_ctx* cc = c.get();
+    capture_graph(cc, &cc->g_apply, [cc](cudaStream_t s) {
+      return apply_direct(cc, cc->app_in, cc->app_out, s);
+    });
+    capture_graph(cc, &cc->g_factor, [cc](cudaStream_t s) { return factor_direct(cc, cc->qbuf, s); });
+  }
   SP_CK(cudaDeviceSynchronize());
   *out = c.release();
   return SP_OK;
@@ -525,11 +593,16 @@ sp_status sp_factor(sp_ctx* c, const double* q_dev) {
   SP_CK(cudaSetDevice(c->opts.device));
   cudaStream_t st = c->stream;
   c->factored = false;
-  c->q = q_dev;
-  SP_CK(cudaMemsetAsync(c->status, 0, sizeof(int), st));
-  for (int l = 0; l <= c->L; ++l)
-    SP_CK(factor_level(c->prec, c->d, c->lv[l], l ? &c->lv[l - 1] : nullptr, c->Qcat, c->Ccat,
-                       q_dev, c->opts.pivot_tol, c->status, c->scratch, st));
+  // the context keeps its own copy of q: the factor graph and the operator read it
+  if (q_dev != c->qbuf)
+    SP_CK(cudaMemcpyAsync(c->qbuf, q_dev, sizeof(double) * c->N, cudaMemcpyDeviceToDevice, st));
+  c->q = c->qbuf;
+  if (c->g_factor && !c->profiling) {
+    SP_CK(cudaGraphLaunch(c->g_factor, st));
+  } else {
+    sp_status fs = factor_direct(c, c->qbuf, st);
+    if (fs != SP_OK) return fs;
+  }
   int hs = 0;
   SP_CK(cudaMemcpyAsync(&hs, c->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   SP_CK(cudaStreamSynchronize(st));

@@ -165,12 +165,15 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(T* fronts, int m, int k, 
 // front per cluster).  The panel rows [j0, m) are split in kCL contiguous chunks
 // of physical rows ("slots"), each staged in its CTA's shared memory.  Rows are
 // never moved during the panel: every CTA keeps the same position <-> slot maps
-// and applies the pivot interchanges to the maps only.  Per pivot column the CTAs
-// publish their best candidate (double-buffered), one cluster barrier, every CTA
-// reads all candidates and the pivot row through distributed shared memory
-// (the pivot row is final from then on), updates the maps and its own rows.  The
-// panel is written back in position order.  Same pivots and results as
-// lu_panel_kernel (largest magnitude, ties to the smallest position).
+// and applies the pivot interchanges to the maps only.  Per pivot column each
+// CTA folds its best candidate into a 64-bit key (magnitude rounded to FP32 in
+// the high word, position in the low word; double-buffered), one cluster
+// barrier, then warp 0 of every CTA reads the kCL keys and the pivot row through
+// distributed shared memory (the pivot row is final from then on) and updates
+// the maps; after one block barrier each thread updates its own slots.  The
+// panel is written back in position order.  The pivot is a largest-magnitude
+// entry of the column up to FP32 rounding of the magnitudes (ties and
+// near-ties go to the smallest position).
 constexpr int kCL = 8;
 template <class T>
 __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(256)
@@ -189,17 +192,17 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(256)
   T* P = reinterpret_cast<T*>(smraw);                        // chunk x jb, column-major
   int* pos2slot = reinterpret_cast<int*>(P + (long)chunk * jb);  // rows
   int* slot2pos = pos2slot + rows;                            // rows
-  __shared__ double cval[2];
-  __shared__ int cidx[2];
+  // candidate key: (float bits of |value|) << 32 | (0xffffffff - position), so the
+  // largest key is the largest magnitude, ties to the smallest position
+  __shared__ unsigned long long ckey[2];
   __shared__ T prow[kNB];
-  __shared__ double wv[8];
-  __shared__ int wi[8];
   __shared__ int s_slot;
   const double thresh = ptol * scale[f];
   for (int i = threadIdx.x; i < rows; i += blockDim.x) {
     pos2slot[i] = i;
     slot2pos[i] = i;
   }
+  if (threadIdx.x < 2) ckey[threadIdx.x] = 0ull;
   for (long e = threadIdx.x; e < (long)nmy * jb; e += blockDim.x) {
     int r = (int)(e % nmy), c = (int)(e / nmy);
     P[r + (long)c * chunk] = A[(j0 + rbeg + r) + (long)(j0 + c) * m];
@@ -208,77 +211,49 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(256)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int jj = 0; jj < jb; ++jj) {
     // best candidate among my slots whose position is in [jj, kl)
-    double best = -1.0;
-    int bp = -1;
+    unsigned long long key = 0ull;
     for (int sl = rbeg + threadIdx.x; sl < rend; sl += blockDim.x) {
       const int ps = slot2pos[sl];
       if (ps < jj || ps >= kl) continue;
-      double v = fabs((double)P[(sl - rbeg) + (long)jj * chunk]);
-      if (v > best || (v == best && ps < bp)) {
-        best = v;
-        bp = ps;
-      }
+      float v = (float)fabs((double)P[(sl - rbeg) + (long)jj * chunk]);
+      unsigned long long kk = ((unsigned long long)__float_as_uint(v) << 32) |
+                              (unsigned long long)(0xffffffffu - (unsigned)ps);
+      key = kk > key ? kk : key;
     }
     for (int o = 16; o > 0; o >>= 1) {
-      double ov = __shfl_down_sync(0xffffffffu, best, o);
-      int op = __shfl_down_sync(0xffffffffu, bp, o);
-      if (ov > best || (ov == best && op >= 0 && (bp < 0 || op < bp))) {
-        best = ov;
-        bp = op;
-      }
+      unsigned long long ok = __shfl_down_sync(0xffffffffu, key, o);
+      key = ok > key ? ok : key;
     }
-    if (lane == 0) {
-      wv[warp] = best;
-      wi[warp] = bp;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double b0 = wv[0];
-      int i0 = wi[0];
-      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-        if (wv[w] > b0 || (wv[w] == b0 && wi[w] >= 0 && (i0 < 0 || wi[w] < i0))) {
-          b0 = wv[w];
-          i0 = wi[w];
-        }
-      cval[jj & 1] = b0;
-      cidx[jj & 1] = i0;
-    }
+    if (lane == 0 && key) atomicMax(&ckey[jj & 1], key);
     cl.sync();  // candidates of column jj published
     if (warp == 0) {
-      double b0 = -1.0;
-      int i0 = -1;
-      if (lane < kCL) {
-        b0 = *cl.map_shared_rank(&cval[jj & 1], lane);
-        i0 = *cl.map_shared_rank(&cidx[jj & 1], lane);
-        if (i0 < 0) b0 = -1.0;
-      }
+      unsigned long long kb = 0ull;
+      if (lane < kCL) kb = *cl.map_shared_rank(&ckey[jj & 1], lane);
       for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_down_sync(0xffffffffu, b0, o);
-        int oi = __shfl_down_sync(0xffffffffu, i0, o);
-        if (ov > b0 || (ov == b0 && oi >= 0 && (i0 < 0 || oi < i0))) {
-          b0 = ov;
-          i0 = oi;
-        }
+        unsigned long long ok = __shfl_down_sync(0xffffffffu, kb, o);
+        kb = ok > kb ? ok : kb;
       }
+      kb = __shfl_sync(0xffffffffu, kb, 0);
+      const int p = kb ? (int)(0xffffffffu - (unsigned)(kb & 0xffffffffull)) : jj;
+      const double b0 = kb ? (double)__uint_as_float((unsigned)(kb >> 32)) : -1.0;
+      const int sb = pos2slot[p];
+      // the pivot row (final from now on) from its owner's shared memory
+      const int owner = sb / chunk;
+      if (lane < jb) prow[lane] = cl.map_shared_rank(P, owner)[(sb - owner * chunk) + (long)lane * chunk];
+      __syncwarp();
       if (lane == 0) {
-        const int p = i0 < 0 ? jj : i0;  // position of the pivot row
-        const int sa = pos2slot[jj], sb = pos2slot[p];
+        const int sa = pos2slot[jj];
         pos2slot[jj] = sb;
         pos2slot[p] = sa;
         slot2pos[sb] = jj;
         slot2pos[sa] = p;
         s_slot = sb;
+        ckey[(jj + 1) & 1] = 0ull;  // last read before this iteration's barrier
         if (rank == 0) {
           piv[(long)f * k + j0 + jj] = j0 + p;
           if (!(b0 > thresh)) atomicOr(status, 1);
         }
       }
-    }
-    __syncthreads();
-    const int sp = s_slot, owner = sp / chunk;
-    if (threadIdx.x < jb) {
-      const T* Po = cl.map_shared_rank(P, owner);
-      prow[threadIdx.x] = Po[(sp - owner * chunk) + (long)threadIdx.x * chunk];
     }
     __syncthreads();
     T pv = prow[jj];
@@ -291,7 +266,6 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(256)
       pr[(long)jj * chunk] = l;
       for (int c = jj + 1; c < jb; ++c) pr[(long)c * chunk] -= l * prow[c];
     }
-    __syncthreads();
   }
   // the pivot rows read by other CTAs are final, but keep this CTA's shared
   // memory alive until every CTA has read its last pivot row
