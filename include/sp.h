@@ -48,9 +48,14 @@ typedef enum {
 } sp_status;
 
 typedef enum {
-  SP_PREC_FP64 = 0, /* factor, sweeps, FFTs and Krylov all in FP64 */
-  SP_PREC_FP32 = 1  /* factor and sweeps of P in FP32 (preconditioner only);
-                       FFT operator, Gram-Schmidt and residuals stay FP64 */
+  SP_PREC_FP64 = 0,  /* factor, sweeps, FFTs and Krylov all in FP64 */
+  SP_PREC_FP32 = 1,  /* factor and sweeps of P in FP32 (preconditioner only);
+                        FFT operator, Gram-Schmidt and residuals stay FP64 */
+  SP_PREC_MIXED = 2  /* GMRES-IR: FP32 factor and sweeps, an inner flexible GMRES
+                        in complex64 (FFT operator and Gram-Schmidt in FP32,
+                        Hessenberg and rotations in FP64) solves A d = r to
+                        inner_tol; the outer FP64 refinement forms u += d and the
+                        true residual r = g - A u with the FP64 operator */
 } sp_precision;
 
 typedef struct {
@@ -60,6 +65,7 @@ typedef struct {
   double pivot_tol;  /* singular-front threshold, relative to max|front| (default 1e-14) */
   int device;        /* CUDA device ordinal the context lives on (default 0) */
   int host_threads;  /* threads for the host set-up (0 = all hardware threads) */
+  double inner_tol;  /* SP_PREC_MIXED: relative tolerance of each inner solve (default 1e-5) */
 } sp_opts;
 
 typedef struct {
@@ -106,7 +112,9 @@ sp_status sp_apply(sp_ctx *ctx, const void *r_dev, void *z_dev);
 /* Solve (I + G q) u = G f by GMRES right-preconditioned with P^{-1} Q
  * (Section 2.2; GMRES of Saad and Schultz), zero initial guess, classical
  * Gram-Schmidt twice, stopping when the estimate is <= tol, then an explicit
- * FP64 true residual; restarts from u if that is still above tol.  f_dev, u_dev:
+ * FP64 true residual; restarts from u if that is still above tol (with
+ * SP_PREC_MIXED: refinement steps of FP32 inner solves, see sp_precision; iters
+ * counts inner iterations, restarts the refinement steps beyond the first).  f_dev, u_dev:
  * N complex128 on the device.  info may be NULL.  Returns SP_ERR_NOCONV when
  * maxit is reached above tol. */
 sp_status sp_solve(sp_ctx *ctx, const void *f_dev, void *u_dev, sp_info *info);

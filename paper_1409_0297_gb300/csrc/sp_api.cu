@@ -101,6 +101,9 @@ struct sp_ctx {
   Profiler prof;
   bool profiling = false;
   bool factored = false;
+  bool mixed = false;          // SP_PREC_MIXED: prec is FP32 for the factor and sweeps
+  float* q32 = nullptr;        // complex64 operator of the inner solve
+  float2* z32 = nullptr;
   // CUDA graphs of the preconditioner application and of the factorisation,
   // captured once at set-up on an internal stream and replayed on `stream`
   cudaStream_t cap = nullptr;
@@ -221,6 +224,7 @@ void sp_default_opts(sp_opts* o) {
   o->pivot_tol = 1e-14;
   o->device = 0;
   o->host_threads = 0;
+  o->inner_tol = 1e-5;
 }
 
 const char* sp_status_str(sp_status st) {
@@ -391,7 +395,9 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   int L;
   if (check_grid(d, n, b, &L)) return SP_ERR_ARG;
   if (n & (n - 1)) return SP_ERR_ARG;  // the device FFT handles powers of two
-  if (prec != SP_PREC_FP64 && prec != SP_PREC_FP32) return SP_ERR_ARG;
+  if (prec != SP_PREC_FP64 && prec != SP_PREC_FP32 && prec != SP_PREC_MIXED) return SP_ERR_ARG;
+  const bool mixed = (prec == SP_PREC_MIXED);
+  if (mixed) prec = SP_PREC_FP32;
   if (!(std::isfinite(s))) return SP_ERR_ARG;
   if (shift_gap(d, n, s) < 1e-6) return SP_ERR_RESONANT;
   std::unique_ptr<sp_ctx> c(new (std::nothrow) sp_ctx());
@@ -407,6 +413,8 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   c->nl = n / b;
   c->s = s;
   c->prec = prec;
+  c->mixed = mixed;
+  if (mixed && !(c->opts.inner_tol > 0 && c->opts.inner_tol < 1)) return SP_ERR_ARG;
   c->stream = (cudaStream_t)stream;
   c->N = 1;
   for (int a = 0; a < d; ++a) c->N *= n;
@@ -540,6 +548,16 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
     }
     SP_CK(upload(c.get(), &P.Dn, Dn));
     SP_CK(dalloc(c.get(), &P.tmp, sizeof(double2) * N));
+    if (mixed) {
+      std::vector<float2> tw32(tw.size());
+      for (size_t i = 0; i < tw.size(); ++i) tw32[i] = make_float2((float)tw[i].x, (float)tw[i].y);
+      std::vector<float> Dn32(Dn.begin(), Dn.end());
+      SP_CK(upload(c.get(), &P.tw32, tw32));
+      SP_CK(upload(c.get(), &P.Dn32, Dn32));
+      SP_CK(dalloc(c.get(), &P.tmp32, sizeof(float2) * N));
+      SP_CK(dalloc(c.get(), &c->q32, sizeof(float) * N));
+      SP_CK(dalloc(c.get(), &c->z32, sizeof(float2) * N));
+    }
   }
   // ---- solve workspace
   c->maxv = c->opts.restart + 1;
@@ -603,6 +621,7 @@ sp_status sp_factor(sp_ctx* c, const double* q_dev) {
     sp_status fs = factor_direct(c, c->qbuf, st);
     if (fs != SP_OK) return fs;
   }
+  if (c->mixed) SP_CK(to_float(c->qbuf, c->q32, c->N, st));
   int hs = 0;
   SP_CK(cudaMemcpyAsync(&hs, c->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   SP_CK(cudaStreamSynchronize(st));
@@ -650,11 +669,14 @@ sp_status sp_green(sp_ctx* c, const void* f_dev, void* g_dev) {
   return cuda_status(fft_green_apply(c->fft, (const double2*)f_dev, nullptr, false, (double2*)g_dev, c->stream));
 }
 
+static sp_status solve_mixed(sp_ctx* c, const double2* f, double2* u, sp_info* info);
+
 sp_status sp_solve(sp_ctx* c, const void* f_dev, void* u_dev, sp_info* info) {
   if (!c || !f_dev || !u_dev) return SP_ERR_ARG;
   ProfGuard pg_(c);
   if (!c->factored) return SP_ERR_STATE;
   SP_CK(cudaSetDevice(c->opts.device));
+  if (c->mixed) return solve_mixed(c, (const double2*)f_dev, (double2*)u_dev, info);
   cudaStream_t st = c->stream;
   const long N = c->N;
   double2* u = (double2*)u_dev;
@@ -730,6 +752,89 @@ sp_status sp_solve(sp_ctx* c, const void* f_dev, void* u_dev, sp_info* info) {
     info->true_relres = true_rel;
   }
   return true_rel <= tol ? SP_OK : SP_ERR_NOCONV;
+}
+
+// GMRES-IR: outer refinement in FP64, inner flexible GMRES in complex64.
+static sp_status solve_mixed(sp_ctx* c, const double2* f, double2* u, sp_info* info) {
+  cudaStream_t st = c->stream;
+  const long N = c->N;
+  double* hsc = c->host_sc;
+  const int restart = c->opts.restart;
+  const double tol = c->opts.tol, tin = c->opts.inner_tol;
+  if (info) {
+    info->iters = 0;
+    info->restarts = 0;
+    info->hist_len = 0;
+    info->s_used = c->s;
+  }
+  auto push_hist = [&](double v) {
+    if (info && info->hist && info->hist_len < info->hist_cap) info->hist[info->hist_len++] = v;
+  };
+  float2* V32 = reinterpret_cast<float2*>(c->V);  // (restart + 1) complex64 vectors
+  SP_CK(fft_green_apply(c->fft, f, nullptr, false, c->g, st));
+  SP_CK(kr_norm(c->g, N, c->K, c->nrm + 2, st));
+  SP_CK(cudaMemcpyAsync(hsc, c->nrm + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+  SP_CK(cudaMemsetAsync(u, 0, sizeof(double2) * N, st));
+  SP_CK(cudaStreamSynchronize(st));
+  const double bnorm = hsc[0];
+  push_hist(1.0);
+  if (bnorm == 0.0) {
+    if (info) info->true_relres = info->est_relres = 0.0;
+    return SP_OK;
+  }
+  SP_CK(cudaMemcpyAsync(c->r, c->g, sizeof(double2) * N, cudaMemcpyDeviceToDevice, st));
+  SP_CK(cudaMemcpyAsync(c->nrm + 3, c->nrm + 2, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  double rel = 1.0, est_rel = 1.0;
+  int total = 0, outer = 0;
+  const int maxit = c->opts.maxit;
+  for (;;) {
+    // inner: A d = r / ||r|| in complex64, flexible GMRES, Z_j kept in FP64
+    SP_CK(kr32_start(c->r, N, c->nrm + 3, V32, c->gam, c->maxv + 1, st));
+    int k = 0;
+    for (int j = 0; j < restart; ++j) {
+      const float2* vj = V32 + (long)j * N;
+      double2* zj = c->Z + (long)j * N;
+      float2* w = V32 + (long)(j + 1) * N;
+      SP_CK(kr_widen(vj, N, c->t, st));
+      sp_status ss = apply_impl(c, c->t, zj);
+      if (ss != SP_OK) return ss;
+      SP_CK(kr_narrow(zj, N, c->z32, st));
+      SP_CK(fft_green_apply32(c->fft, c->z32, c->q32, true, w, st));
+      SP_CK(kr32_dots(V32, N, j + 1, w, N, c->K, c->h1, st));
+      SP_CK(kr32_update_dots(V32, N, j + 1, w, N, c->h1, c->K, c->h2, st));
+      SP_CK(kr32_update_dots(V32, N, j + 1, w, N, c->h2, c->K, nullptr, st));
+      SP_CK(kr32_norm(w, N, c->K, c->nrm, st));
+      SP_CK(kr_givens(c->H, c->maxv, j, c->h1, c->h2, c->nrm, c->cs, c->sn, c->gam, c->est, st));
+      SP_CK(cudaMemcpyAsync(hsc, c->est, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      SP_CK(cudaStreamSynchronize(st));
+      ++total;
+      k = j + 1;
+      est_rel = hsc[0] * rel;  // inner estimate scaled to ||g||
+      push_hist(est_rel);
+      if (hsc[0] <= tin || est_rel <= tol || total >= maxit || hsc[1] == 0.0) break;
+      SP_CK(kr32_scale(w, N, c->nrm, st));
+    }
+    // u += ||r|| Z y
+    SP_CK(kr_trisolve(c->H, c->maxv, k, c->gam, c->y, st));
+    SP_CK(kr_scale_y(c->y, k, c->nrm + 3, st));
+    SP_CK(kr_combine(c->Z, N, k, c->y, N, u, st));
+    // FP64 residual
+    SP_CK(fft_green_apply(c->fft, u, c->q, true, c->t, st));
+    SP_CK(kr_sub(c->g, c->t, N, c->r, st));
+    SP_CK(kr_norm(c->r, N, c->K, c->nrm + 3, st));
+    SP_CK(cudaMemcpyAsync(hsc + 2, c->nrm + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SP_CK(cudaStreamSynchronize(st));
+    rel = hsc[2] / bnorm;
+    ++outer;
+    if (rel <= tol || total >= maxit) break;
+  }
+  if (info) {
+    info->iters = total;
+    info->restarts = outer - 1;
+    info->est_relres = est_rel;
+    info->true_relres = rel;
+  }
+  return rel <= tol ? SP_OK : SP_ERR_NOCONV;
 }
 
 sp_status sp_solve_host(sp_ctx* c, const void* f_host, void* u_host, sp_info* info) {

@@ -744,9 +744,11 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
     pp.done(pf * L.nf, 1, st);
     int rem = L.m - j0 - jb;
     if (rem + j0 > 0) {
-      dim3 gt((rem + j0 + 255) / 256, L.nf);
+      // one thread per column; narrow CTAs when few fronts would leave SMs idle
+      const int tb = ((long)((rem + j0 + 255) / 256) * L.nf >= 152) ? 256 : 64;
+      dim3 gt((rem + j0 + tb - 1) / tb, L.nf);
       ProfScope pt(PROF_LU_TRSM, st);
-      lu_trsm_kernel<T><<<gt, 256, 0, st>>>(F, L.m, L.k, j0, jb, L.piv);
+      lu_trsm_kernel<T><<<gt, tb, 0, st>>>(F, L.m, L.k, j0, jb, L.piv);
       pt.done((double)rem * jb * (jb - 1) * L.nf, 1, st);
     }
     if (rem > 0) {

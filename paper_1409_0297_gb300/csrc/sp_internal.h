@@ -144,8 +144,26 @@ cudaError_t kr_givens(double2* H, int ldh, int j, const double2* h1, const doubl
 cudaError_t kr_update_solution(const double2* H, int ldh, int k, const double2* gam,
                                double2* y, const double2* Z, long ldz, long N, double2* u,
                                cudaStream_t st);
+// y = R^{-1} gam; u += Z y
+cudaError_t kr_trisolve(const double2* H, int ldh, int k, const double2* gam, double2* y,
+                        cudaStream_t st);
+cudaError_t kr_combine(const double2* Z, long ldz, int k, const double2* y, long N, double2* u,
+                       cudaStream_t st);
 // gam = [beta, 0, ...]; V0 = r / beta
 cudaError_t kr_start(const double2* r, long N, const double* nrm, double2* V0, double2* gam,
                      int len, cudaStream_t st);
+// complex64 counterparts for the inner solve of the mixed-precision form
+cudaError_t kr32_dots(const float2* V, long ldv, int nv, const float2* w, long N, KrylovWork& K,
+                      double2* h_out, cudaStream_t st);
+cudaError_t kr32_update_dots(const float2* V, long ldv, int nv, float2* w, long N, const double2* h,
+                             KrylovWork& K, double2* h2_out, cudaStream_t st);
+cudaError_t kr32_norm(const float2* w, long N, KrylovWork& K, double* nrm_out, cudaStream_t st);
+cudaError_t kr32_scale(float2* x, long N, const double* nrm, cudaStream_t st);
+// y = x / nrm[0] in complex64, gam = [1, 0, ...]
+cudaError_t kr32_start(const double2* x, long N, const double* nrm, float2* y, double2* gam,
+                       int len, cudaStream_t st);
+cudaError_t kr_widen(const float2* x, long N, double2* y, cudaStream_t st);
+cudaError_t kr_narrow(const double2* x, long N, float2* y, cudaStream_t st);
+cudaError_t kr_scale_y(double2* y, int k, const double* s, cudaStream_t st);
 
 }  // namespace sp

@@ -283,12 +283,193 @@ cudaError_t kr_update_solution(const double2* H, int ldh, int k, const double2* 
   return cudaGetLastError();
 }
 
+cudaError_t kr_trisolve(const double2* H, int ldh, int k, const double2* gam, double2* y,
+                        cudaStream_t st) {
+  trisolve_kernel<<<1, 256, 0, st>>>(H, ldh, k, gam, y);
+  return cudaGetLastError();
+}
+
+cudaError_t kr_combine(const double2* Z, long ldz, int k, const double2* y, long N, double2* u,
+                       cudaStream_t st) {
+  ProfScope ps(PROF_KRYLOV, st);
+  combine_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(Z, ldz, k, y, N, u);
+  ps.done(16.0 * N * (k + 2), 1, st);
+  return cudaGetLastError();
+}
+
 cudaError_t kr_start(const double2* r, long N, const double* nrm, double2* V0, double2* gam,
                      int len, cudaStream_t st) {
   long n = N > len ? N : len;
   ProfScope ps(PROF_KRYLOV, st);
   start_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(r, N, nrm, V0, gam, len);
   ps.done(32.0 * N, 1, st);
+  return cudaGetLastError();
+}
+
+}  // namespace sp
+
+// ---------------------------------------------------------------------------------
+// FP32 vector kernels of the inner solve of the mixed-precision form (GMRES-IR):
+// Krylov vectors in complex64, per-thread sums in FP32, everything from the warp
+// reductions on in FP64, Hessenberg matrix and rotations in FP64 (the kernels
+// above).
+namespace sp {
+
+namespace {
+
+__device__ __forceinline__ void chunk_dots32(const float2* V, long ldv, int nv, const float2* w,
+                                             long c0, long c1, double2* partial) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = warp; j < nv; j += nw) {
+    const float2* v = V + (long)j * ldv;
+    float sr = 0.f, si = 0.f;
+    for (long i = c0 + lane; i < c1; i += 32) {
+      float2 a = v[i], b = w[i];
+      sr = fmaf(a.x, b.x, fmaf(a.y, b.y, sr));
+      si = fmaf(a.x, b.y, fmaf(-a.y, b.x, si));
+    }
+    double dr = warp_sum((double)sr), di = warp_sum((double)si);
+    if (lane == 0) partial[(long)j * gridDim.x + blockIdx.x] = make_double2(dr, di);
+  }
+}
+
+__global__ void __launch_bounds__(kThr) dots32_kernel(const float2* V, long ldv, int nv,
+                                                      const float2* w, long N, double2* partial) {
+  long c0, c1;
+  chunk_of(N, &c0, &c1);
+  chunk_dots32(V, ldv, nv, w, c0, c1, partial);
+}
+
+__global__ void __launch_bounds__(kThr) update_dots32_kernel(const float2* V, long ldv, int nv,
+                                                             float2* w, long N, const double2* h,
+                                                             double2* partial) {
+  __shared__ float2 hs[1024];
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) hs[j] = make_float2((float)h[j].x, (float)h[j].y);
+  __syncthreads();
+  long c0, c1;
+  chunk_of(N, &c0, &c1);
+  for (long i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+    float2 acc = w[i];
+    for (int j = 0; j < nv; ++j) {
+      float2 v = V[(long)j * ldv + i], hj = hs[j];
+      acc.x -= fmaf(v.x, hj.x, -v.y * hj.y);
+      acc.y -= fmaf(v.x, hj.y, v.y * hj.x);
+    }
+    w[i] = acc;
+  }
+  if (partial) {
+    __syncthreads();
+    chunk_dots32(V, ldv, nv, w, c0, c1, partial);
+  }
+}
+
+__global__ void __launch_bounds__(kThr) norm32_kernel(const float2* w, long N, double2* partial) {
+  long c0, c1;
+  chunk_of(N, &c0, &c1);
+  float s = 0.f;
+  for (long i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+    float2 v = w[i];
+    s = fmaf(v.x, v.x, fmaf(v.y, v.y, s));
+  }
+  __shared__ double red[kThr / 32];
+  double ds = warp_sum((double)s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ds;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    partial[blockIdx.x] = make_double2(t, 0);
+  }
+}
+
+__global__ void scale32_kernel(float2* x, long N, const double* nrm) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  float a = nrm[0] > 0 ? (float)(1.0 / nrm[0]) : 0.f;
+  float2 v = x[i];
+  x[i] = make_float2(v.x * a, v.y * a);
+}
+
+// y = x / nrm[0] rounded to complex64; gam = [1, 0, ...]
+__global__ void start32_kernel(const double2* x, long N, const double* nrm, float2* y,
+                               double2* gam, int len) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
+    double a = nrm[0] > 0 ? 1.0 / nrm[0] : 0.0;
+    y[i] = make_float2((float)(x[i].x * a), (float)(x[i].y * a));
+  }
+  if (i < len) gam[i] = make_double2(i == 0 ? 1.0 : 0.0, 0.0);
+}
+
+__global__ void widen_kernel(const float2* x, long N, double2* y) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) y[i] = make_double2(x[i].x, x[i].y);
+}
+
+__global__ void narrow_kernel(const double2* x, long N, float2* y) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) y[i] = make_float2((float)x[i].x, (float)x[i].y);
+}
+
+// y[0..k) *= s[0]
+__global__ void scale_y_kernel(double2* y, int k, const double* s) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < k) y[i] = make_double2(y[i].x * s[0], y[i].y * s[0]);
+}
+
+}  // namespace
+
+cudaError_t kr32_dots(const float2* V, long ldv, int nv, const float2* w, long N, KrylovWork& K,
+                      double2* h_out, cudaStream_t st) {
+  ProfScope ps(PROF_KRYLOV, st);
+  dots32_kernel<<<K.nblk, kThr, 0, st>>>(V, ldv, nv, w, N, K.partial);
+  reduce_partials_kernel<<<(nv + 7) / 8, 256, 0, st>>>(K.partial, K.nblk, nv, h_out);
+  ps.done(8.0 * N * (nv + 1), 2, st);
+  return cudaGetLastError();
+}
+
+cudaError_t kr32_update_dots(const float2* V, long ldv, int nv, float2* w, long N, const double2* h,
+                             KrylovWork& K, double2* h2_out, cudaStream_t st) {
+  ProfScope ps(PROF_KRYLOV, st);
+  update_dots32_kernel<<<K.nblk, kThr, 0, st>>>(V, ldv, nv, w, N, h, h2_out ? K.partial : nullptr);
+  if (h2_out) reduce_partials_kernel<<<(nv + 7) / 8, 256, 0, st>>>(K.partial, K.nblk, nv, h2_out);
+  ps.done(8.0 * N * (nv + 2), h2_out ? 2 : 1, st);
+  return cudaGetLastError();
+}
+
+cudaError_t kr32_norm(const float2* w, long N, KrylovWork& K, double* nrm_out, cudaStream_t st) {
+  ProfScope ps(PROF_KRYLOV, st);
+  norm32_kernel<<<K.nblk, kThr, 0, st>>>(w, N, K.partial);
+  reduce_partials_kernel<<<1, 32, 0, st>>>(K.partial, K.nblk, 1, K.h + 1023);
+  sqrt_kernel<<<1, 1, 0, st>>>(K.h + 1023, nrm_out);
+  ps.done(8.0 * N, 3, st);
+  return cudaGetLastError();
+}
+
+cudaError_t kr32_scale(float2* x, long N, const double* nrm, cudaStream_t st) {
+  scale32_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(x, N, nrm);
+  return cudaGetLastError();
+}
+
+cudaError_t kr32_start(const double2* x, long N, const double* nrm, float2* y, double2* gam,
+                       int len, cudaStream_t st) {
+  long n = N > len ? N : len;
+  start32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, N, nrm, y, gam, len);
+  return cudaGetLastError();
+}
+
+cudaError_t kr_widen(const float2* x, long N, double2* y, cudaStream_t st) {
+  widen_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(x, N, y);
+  return cudaGetLastError();
+}
+
+cudaError_t kr_narrow(const double2* x, long N, float2* y, cudaStream_t st) {
+  narrow_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(x, N, y);
+  return cudaGetLastError();
+}
+
+cudaError_t kr_scale_y(double2* y, int k, const double* s, cudaStream_t st) {
+  scale_y_kernel<<<(k + 255) / 256, 256, 0, st>>>(y, k, s);
   return cudaGetLastError();
 }
 

@@ -126,7 +126,7 @@ def test_solve_matches_oracle_64(B):
     M = O.SparsifyingPreconditioner(d, n, b, s, q)
     g = O.apply_green(d, n, s, f)
     ref = O.gmres_right(lambda x: O.apply_operator(d, n, s, q, x), M.apply, g, tol=1e-8)
-    for prec in (0, 1):
+    for prec in (0, 1, 2):
         S = B.Solver(d, n, b, s, prec=prec)
         S.factor(dev(q))
         u = torch.empty(n * n, dtype=torch.complex128, device="cuda")
@@ -141,14 +141,18 @@ def test_solve_matches_oracle_64(B):
             assert abs(info["iters"] - ref["iters"]) <= 1
             h = np.array(ref["hist"][: len(info["hist"])])
             assert np.allclose(info["hist"][: len(h)], h, rtol=1e-6, atol=1e-12)
-        else:
+            assert np.all(np.diff(info["hist"]) <= 1e-15)
+        elif prec == 1:
             assert info["iters"] <= ref["iters"] + 3
-        assert np.all(np.diff(info["hist"]) <= 1e-15)
+            assert np.all(np.diff(info["hist"]) <= 1e-15)
+        else:
+            # GMRES-IR: inner solves to 1e-5 in complex64, FP64 refinement
+            assert info["iters"] <= 2 * ref["iters"] + 5
         S.close()
 
 
 @pytest.mark.parametrize("which", ["helmholtz", "schrodinger"])
-@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("prec", [0, 1, 2], ids=["fp64", "fp32", "mixed"])
 def test_solve_512(B, which, prec):
     """Full 512^2 workloads: the preconditioner checked at 4000 sampled rows of
     P z - Q r computed one by one by the oracle from the library's tables, the
