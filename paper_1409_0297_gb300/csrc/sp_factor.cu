@@ -326,54 +326,56 @@ __global__ void __launch_bounds__(256) lu_trsm_kernel(T* fronts, int m, int k, i
 }
 
 // Batched C[M x N] -= A[M x K] B[K x N], K <= kNB, column-major with leading
-// dimensions lda/ldb/ldc and per-batch strides (blockIdx.y = batch).  kTile x
-// kTile per CTA, 4 x 4 per thread.  Used for the Schur update of the LU and for
-// the triangular inverses.
-template <class T>
+// dimensions lda/ldb/ldc and per-batch strides (blockIdx.y = batch).  TILE x TILE
+// per CTA (TILE = 64: 4 x 4 per thread, TILE = 32: 2 x 2 per thread; the launcher
+// picks the one that wastes less work on the padding of the last tile row and
+// column).  Used for the Schur update of the LU.
+template <class T, int TILE>
 __global__ void __launch_bounds__(256) gemm_sub_kernel(int M, int N, int K, const T* A, int lda,
                                                        long sA, const T* B, int ldb, long sB,
                                                        T* C, int ldc, long sC, int tilesM) {
+  constexpr int R = TILE / 16;
   A += blockIdx.y * sA;
   B += blockIdx.y * sB;
   C += blockIdx.y * sC;
   const int tr = blockIdx.x % tilesM, tc = blockIdx.x / tilesM;
-  const int r0 = tr * kTile, c0 = tc * kTile;
-  __shared__ T As[kNB][kTile];
-  __shared__ T Bs[kNB][kTile + 1];
-  for (int e = threadIdx.x; e < K * kTile; e += blockDim.x) {
-    int i = e % kTile, l = e / kTile;
+  const int r0 = tr * TILE, c0 = tc * TILE;
+  __shared__ T As[kNB][TILE];
+  __shared__ T Bs[kNB][TILE + 1];
+  for (int e = threadIdx.x; e < K * TILE; e += blockDim.x) {
+    int i = e % TILE, l = e / TILE;
     int r = r0 + i;
     As[l][i] = (r < M) ? A[r + (long)l * lda] : (T)0;
   }
-  for (int e = threadIdx.x; e < K * kTile; e += blockDim.x) {
+  for (int e = threadIdx.x; e < K * TILE; e += blockDim.x) {
     int l = e % K, jc = e / K;
     int c = c0 + jc;
     Bs[l][jc] = (c < N) ? B[l + (long)c * ldb] : (T)0;
   }
   __syncthreads();
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  T acc[4][4];
+  T acc[R][R];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < R; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+    for (int b = 0; b < R; ++b) acc[a][b] = 0;
   for (int l = 0; l < K; ++l) {
-    T av[4], bv[4];
+    T av[R], bv[R];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) av[a] = As[l][tx + 16 * a];
+    for (int a = 0; a < R; ++a) av[a] = As[l][tx + 16 * a];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) bv[b] = Bs[l][ty + 16 * b];
+    for (int b = 0; b < R; ++b) bv[b] = Bs[l][ty + 16 * b];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < R; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+      for (int b = 0; b < R; ++b) acc[a][b] += av[a] * bv[b];
   }
 #pragma unroll
-  for (int b = 0; b < 4; ++b) {
+  for (int b = 0; b < R; ++b) {
     int c = c0 + ty + 16 * b;
     if (c >= N) continue;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
+    for (int a = 0; a < R; ++a) {
       int r = r0 + tx + 16 * a;
       if (r < M) C[r + (long)c * ldc] -= acc[a][b];
     }
@@ -580,9 +582,18 @@ template <class T>
 void gemm_sub(int M, int N, int K, const T* A, int lda, long sA, const T* B, int ldb, long sB,
               T* C, int ldc, long sC, int batch, cudaStream_t st) {
   if (M <= 0 || N <= 0 || K <= 0) return;
-  int tilesM = (M + kTile - 1) / kTile, tilesN = (N + kTile - 1) / kTile;
-  dim3 g(tilesM * tilesN, batch);
-  gemm_sub_kernel<T><<<g, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, tilesM);
+  // padded work of 64- and 32-wide tiles relative to M N
+  const double w64 = (double)((M + 63) / 64 * 64) * ((N + 63) / 64 * 64);
+  const double w32 = (double)((M + 31) / 32 * 32) * ((N + 31) / 32 * 32);
+  if (w64 > 1.1 * w32) {
+    int tilesM = (M + 31) / 32, tilesN = (N + 31) / 32;
+    dim3 g(tilesM * tilesN, batch);
+    gemm_sub_kernel<T, 32><<<g, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, tilesM);
+  } else {
+    int tilesM = (M + 63) / 64, tilesN = (N + 63) / 64;
+    dim3 g(tilesM * tilesN, batch);
+    gemm_sub_kernel<T, 64><<<g, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, tilesM);
+  }
 }
 
 template <class T>
