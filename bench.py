@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-chosen", action="store_true")
-    p.add_argument("--profile-step", default=None, choices=["fp64", "fp32"],
+    p.add_argument("--profile-step", default=None, choices=["fp64", "fp32", "tf32"],
                    help="run exactly one untimed step (factor + solve of both problems) in the "
                         "given form after set-up and exit: the command profiled under ncu")
     p.add_argument("--problems", default="helmholtz,schrodinger",
@@ -210,7 +210,8 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     if args.profile_step:
-        ctxs = make(B.SP_PREC_FP64 if args.profile_step == "fp64" else B.SP_PREC_FP32)
+        ctxs = make({"fp64": B.SP_PREC_FP64, "fp32": B.SP_PREC_FP32,
+                     "tf32": B.SP_PREC_TF32}[args.profile_step])
         torch.cuda.synchronize()
         infos = []
         for c in ctxs:
@@ -334,6 +335,9 @@ def run_ours(args):
     if not args.no_chosen:
         for name, prec, desc in (
                 ("fp32", B.SP_PREC_FP32, "FP32 factor and sweeps; FP64 operator, Gram-Schmidt, residuals"),
+                ("tf32", B.SP_PREC_TF32, "FP32 factor and sweeps, Schur updates of fronts m >= 1024 "
+                                         "on tcgen05 tensor cores (TF32 x TF32 -> FP32); FP64 "
+                                         "operator, Gram-Schmidt, residuals"),
                 ("mixed", B.SP_PREC_MIXED, "GMRES-IR: FP32 factor and sweeps, complex64 inner FGMRES "
                                            "(FFT, Gram-Schmidt) to 1e-5, FP64 refinement residuals")):
             ctxs = make(prec)

@@ -42,7 +42,7 @@ typedef enum {
   SP_ERR_SINGULAR = 3,  /* a pivot of a front fell below pivot_tol * max|front| */
   SP_ERR_NOCONV = 4,    /* GMRES stopped at maxit above tol (the iterate is still returned) */
   SP_ERR_OOM = 5,       /* device or host allocation failed */
-  SP_ERR_TIMEOUT = 6,   /* reserved for bounded device waits */
+  SP_ERR_TIMEOUT = 6,   /* a bounded device wait (tensor-core pipeline) ran out */
   SP_ERR_CUDA = 7,      /* a CUDA runtime call failed */
   SP_ERR_STATE = 8      /* call out of order (e.g. sp_apply before sp_factor) */
 } sp_status;
@@ -51,11 +51,15 @@ typedef enum {
   SP_PREC_FP64 = 0,  /* factor, sweeps, FFTs and Krylov all in FP64 */
   SP_PREC_FP32 = 1,  /* factor and sweeps of P in FP32 (preconditioner only);
                         FFT operator, Gram-Schmidt and residuals stay FP64 */
-  SP_PREC_MIXED = 2  /* GMRES-IR: FP32 factor and sweeps, an inner flexible GMRES
+  SP_PREC_MIXED = 2, /* GMRES-IR: FP32 factor and sweeps, an inner flexible GMRES
                         in complex64 (FFT operator and Gram-Schmidt in FP32,
                         Hessenberg and rotations in FP64) solves A d = r to
                         inner_tol; the outer FP64 refinement forms u += d and the
                         true residual r = g - A u with the FP64 operator */
+  SP_PREC_TF32 = 3     /* as SP_PREC_FP32, and fronts with m >= 1024 are factored in
+                        outer blocks of 256 columns whose Schur updates
+                        S -= L21 U12 run on the tensor cores (TF32 products,
+                        FP32 accumulation; Section 2.3's update S = F22 - L21 U12) */
 } sp_precision;
 
 typedef struct {
@@ -191,9 +195,25 @@ sp_status sp_medium_schrodinger(int d, int n, double ell, double E, const double
  * kernels, 9 triangular inverses of the few-front levels) the summed device
  * milliseconds, the number of kernel launches and the algorithmic work (flops
  * for classes 1-3 and 9, bytes for the others: the data a kernel must move at
- * least once), then clears the record.  Arrays of cap >= 10. */
+ * least once; 10 tensor-core Schur updates of the blocked fronts, flops), then
+ * clears the record.  Arrays of cap >= 11. */
 sp_status sp_profile(sp_ctx *ctx, int enable);
 sp_status sp_profile_read(sp_ctx *ctx, int cap, double *ms, int *launches, double *work);
+
+/* One Schur-complement update of the multifrontal LU (Section 2.3: the block
+ * S = F22 - L21 U12 handed to the parent front), for checking the update kernels
+ * in isolation: C[M x N] -= A[M x K] B[K x N] for `batch` column-major problems
+ * on the current device (leading dimensions lda, ldb, ldc >= the row counts;
+ * batch strides sA, sB, sC in elements), with the kernel the factorisation uses
+ * for the form: SP_PREC_FP64 doubles, SP_PREC_FP32 floats (SIMT FMA units),
+ * SP_PREC_TF32 floats with TF32 products on the tensor cores and FP32
+ * accumulation (K <= 256; the call allocates and frees its operand buffers).
+ * A, B, C: device pointers owned by the caller; C must not overlap A or B.
+ * Synchronous on `stream` (cudaStream_t or NULL).  SP_ERR_ARG for bad sizes or
+ * forms, SP_ERR_TIMEOUT if a tensor-core pipeline wait ran out. */
+sp_status sp_schur_update(sp_precision prec, int M, int N, int K, const void *A, int lda,
+                          long long sA, const void *B, int ldb, long long sB, void *C, int ldc,
+                          long long sC, int batch, void *stream);
 
 /* g = G f for callers that cannot allocate device memory when they call (for
  * example code running inside a CUDA-graph stream capture, or under a fixed,

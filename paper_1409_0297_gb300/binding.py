@@ -17,16 +17,16 @@ LIB_PATH = os.path.join(_HERE, "libsp_gb300.so")
 
 SP_OK, SP_ERR_ARG, SP_ERR_RESONANT, SP_ERR_SINGULAR, SP_ERR_NOCONV = 0, 1, 2, 3, 4
 SP_ERR_OOM, SP_ERR_TIMEOUT, SP_ERR_CUDA, SP_ERR_STATE = 5, 6, 7, 8
-SP_PREC_FP64, SP_PREC_FP32, SP_PREC_MIXED = 0, 1, 2
+SP_PREC_FP64, SP_PREC_FP32, SP_PREC_MIXED, SP_PREC_TF32 = 0, 1, 2, 3
 
 EXPORTED = [
     "sp_default_opts", "sp_setup", "sp_factor", "sp_apply", "sp_solve", "sp_factor_host",
     "sp_solve_host", "sp_matvec", "sp_green", "sp_qapply", "sp_get_table", "sp_stencil_table",
     "sp_front_sizes", "sp_level_info", "sp_costs", "sp_medium_helmholtz", "sp_medium_schrodinger", "sp_profile",
-    "sp_profile_read", "sp_green_static", "sp_destroy", "sp_status_str",
+    "sp_profile_read", "sp_green_static", "sp_schur_update", "sp_destroy", "sp_status_str",
 ]
 PROF_CLASSES = ["assemble", "lu_panel", "lu_trsm", "lu_gemm", "qapply", "forward", "backward",
-                "fft", "krylov", "lu_trinv"]
+                "fft", "krylov", "lu_trinv", "lu_tc"]
 
 
 class sp_opts(ctypes.Structure):
@@ -76,6 +76,8 @@ def _load() -> ctypes.CDLL:
         "sp_profile": (I, [P, I]),
         "sp_profile_read": (I, [P, I, pD, pI, pD]),
         "sp_green_static": (I, [I, I, D, P, P, P]),
+        "sp_schur_update": (I, [I, I, I, I, P, I, ctypes.c_longlong, P, I, ctypes.c_longlong, P, I,
+                                ctypes.c_longlong, I, P]),
         "sp_destroy": (V, [P]),
         "sp_status_str": (ctypes.c_char_p, [I]),
     }
@@ -271,6 +273,14 @@ def sp_profile_read(ctx: int) -> dict:
 def sp_green_static(d: int, n: int, s: float, f_dev: int, g_dev: int, stream: int = 0) -> None:
     """g = G f without a context or any allocation (see include/sp.h)."""
     _check(LIB.sp_green_static(d, n, float(s), f_dev, g_dev, stream), "sp_green_static")
+
+
+def sp_schur_update(prec: int, M: int, N: int, K: int, A_dev: int, lda: int, sA: int, B_dev: int,
+                    ldb: int, sB: int, C_dev: int, ldc: int, sC: int, batch: int,
+                    stream: int = 0) -> None:
+    """C -= A B (column-major, batched) with the factorisation's update kernel."""
+    _check(LIB.sp_schur_update(prec, M, N, K, A_dev, lda, sA, B_dev, ldb, sB, C_dev, ldc, sC, batch,
+                               stream), "sp_schur_update")
 
 
 def sp_destroy(ctx: int) -> None:

@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsp_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["sp_host.cpp", "sp_fft.cu", "sp_factor.cu", "sp_solve.cu", "sp_krylov.cu", "sp_api.cu",
-           "sp_static.cu"]
+           "sp_static.cu", "sp_tc.cu"]
 HEADERS = ["sp_host.h", "sp_internal.h"]
 
 

@@ -84,7 +84,7 @@ struct sp_ctx {
   double* Ccat = nullptr;
   double* Tcat = nullptr;
   float* Tcat32 = nullptr;
-  void* scratch = nullptr;  // triangular-inverse work of the few-front levels
+  FactorWork work;          // triangular-inverse scratch, tensor-core operand buffers
   FftPlan fft;
   const double* q = nullptr;  // current medium (caller's or qbuf)
   double* qbuf = nullptr;     // used by sp_factor_host
@@ -188,7 +188,7 @@ sp_status factor_direct(sp_ctx* c, const double* q, cudaStream_t st) {
   SP_CK(cudaMemsetAsync(c->status, 0, sizeof(int), st));
   for (int l = 0; l <= c->L; ++l)
     SP_CK(factor_level(c->prec, c->d, c->lv[l], l ? &c->lv[l - 1] : nullptr, c->Qcat, c->Ccat, q,
-                       c->opts.pivot_tol, c->status, c->scratch, st));
+                       c->opts.pivot_tol, c->status, c->work, st));
   return SP_OK;
 }
 
@@ -395,9 +395,12 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   int L;
   if (check_grid(d, n, b, &L)) return SP_ERR_ARG;
   if (n & (n - 1)) return SP_ERR_ARG;  // the device FFT handles powers of two
-  if (prec != SP_PREC_FP64 && prec != SP_PREC_FP32 && prec != SP_PREC_MIXED) return SP_ERR_ARG;
+  if (prec != SP_PREC_FP64 && prec != SP_PREC_FP32 && prec != SP_PREC_MIXED &&
+      prec != SP_PREC_TF32)
+    return SP_ERR_ARG;
   const bool mixed = (prec == SP_PREC_MIXED);
-  if (mixed) prec = SP_PREC_FP32;
+  const bool tc = (prec == SP_PREC_TF32);
+  if (mixed || tc) prec = SP_PREC_FP32;
   if (!(std::isfinite(s))) return SP_ERR_ARG;
   if (shift_gap(d, n, s) < 1e-6) return SP_ERR_RESONANT;
   std::unique_ptr<sp_ctx> c(new (std::nothrow) sp_ctx());
@@ -414,6 +417,7 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   c->s = s;
   c->prec = prec;
   c->mixed = mixed;
+  c->work.tc = tc;
   if (mixed && !(c->opts.inner_tol > 0 && c->opts.inner_tol < 1)) return SP_ERR_ARG;
   c->stream = (cudaStream_t)stream;
   c->N = 1;
@@ -484,7 +488,7 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   const size_t fsz = (prec == SP_PREC_FP32) ? sizeof(float) : sizeof(double);
   const size_t vsz = (prec == SP_PREC_FP32) ? sizeof(float2) : sizeof(double2);
   c->lv.resize(L + 1);
-  size_t scratch_bytes = 0;
+  size_t scratch_bytes = 0, pack_floats = 0;
   for (int l = 0; l <= L; ++l) {
     const Level& S = c->sym.lv[l];
     DevLevel& D = c->lv[l];
@@ -515,12 +519,18 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
       SP_CK(dalloc(c.get(), &D.tmp, vsz * (size_t)S.nf * S.m));
       scratch_bytes = std::max(scratch_bytes, 3 * fsz * (size_t)S.nf * S.k * S.k);
     }
+    if (factor_outer_block(prec, tc, S.m, S.k) > 0)
+      pack_floats = std::max(pack_floats, tc_pack_floats(S.m, kTcMaxK, S.nf));
     double k = S.k, mk = S.m - S.k;
     c->factor_entries += S.nf * (k * k + 2 * k * mk);
     c->factor_flops += S.nf * ((2.0 / 3.0) * k * k * k + 2 * k * k * mk + 2 * k * mk * mk);
   }
   c->apply_bytes = c->factor_entries * fsz;
-  if (scratch_bytes) SP_CK(dalloc(c.get(), &c->scratch, scratch_bytes));
+  if (scratch_bytes) SP_CK(dalloc(c.get(), &c->work.inv, scratch_bytes));
+  if (pack_floats) {
+    SP_CK(dalloc(c.get(), &c->work.packA, sizeof(float) * pack_floats));
+    SP_CK(dalloc(c.get(), &c->work.packB, sizeof(float) * pack_floats));
+  }
   // ---- FFT plan
   {
     FftPlan& P = c->fft;
@@ -625,6 +635,7 @@ sp_status sp_factor(sp_ctx* c, const double* q_dev) {
   int hs = 0;
   SP_CK(cudaMemcpyAsync(&hs, c->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   SP_CK(cudaStreamSynchronize(st));
+  if (hs & 2) return SP_ERR_TIMEOUT;
   if (hs) return SP_ERR_SINGULAR;
   c->factored = true;
   return SP_OK;
@@ -846,6 +857,41 @@ sp_status sp_solve_host(sp_ctx* c, const void* f_host, void* u_host, sp_info* in
   SP_CK(cudaMemcpyAsync(u_host, c->ubuf, sizeof(double2) * c->N, cudaMemcpyDeviceToHost, c->stream));
   SP_CK(cudaStreamSynchronize(c->stream));
   return st;
+}
+
+sp_status sp_schur_update(sp_precision prec, int M, int N, int K, const void* A, int lda,
+                          long long sA, const void* B, int ldb, long long sB, void* C, int ldc,
+                          long long sC, int batch, void* stream) {
+  if (prec != SP_PREC_FP64 && prec != SP_PREC_FP32 && prec != SP_PREC_TF32) return SP_ERR_ARG;
+  if (M < 0 || N < 0 || K < 0 || batch < 0 || !A || !B || !C) return SP_ERR_ARG;
+  if (lda < std::max(1, M) || ldb < std::max(1, K) || ldc < std::max(1, M)) return SP_ERR_ARG;
+  if (sA < 0 || sB < 0 || sC < 0 || batch > 65535) return SP_ERR_ARG;
+  const bool tc = prec == SP_PREC_TF32;
+  if (tc && K > kTcMaxK) return SP_ERR_ARG;
+  if ((long long)M * N * K * batch == 0) return SP_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  float *pa = nullptr, *pb = nullptr;
+  int* status = nullptr;
+  sp_status rs = SP_OK;
+  cudaError_t e = cudaSuccess;
+  if (tc) {
+    e = cudaMalloc(&pa, sizeof(float) * tc_pack_floats(M, K, batch));
+    if (e == cudaSuccess) e = cudaMalloc(&pb, sizeof(float) * tc_pack_floats(N, K, batch));
+    if (e == cudaSuccess) e = cudaMalloc(&status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), st);
+  }
+  if (e == cudaSuccess)
+    e = schur_update_raw(tc ? SP_PREC_FP32 : prec, tc, M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC,
+                         batch, pa, pb, status, st);
+  int hs = 0;
+  if (e == cudaSuccess && tc) e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  rs = cuda_status(e);
+  if (rs == SP_OK && (hs & 2)) rs = SP_ERR_TIMEOUT;
+  if (pa) cudaFree(pa);
+  if (pb) cudaFree(pb);
+  if (status) cudaFree(status);
+  return rs;
 }
 
 sp_status sp_get_table(const sp_ctx* c, int t, double* Q_out, double* C_out, int* rows, int* cols,

@@ -26,6 +26,7 @@ namespace {
 constexpr int kNB = 32;       // panel width
 constexpr int kTile = 64;     // Schur update tile (kTile x kTile per CTA)
 constexpr int kInvBlock = kInvBlockSize;  // diagonal-block size of the inverse-form levels
+constexpr int kTcMinFront = 1024;         // smallest front blocked for the tensor cores
 
 template <class T>
 __global__ void assemble_kernel(T* fronts, int m, int nasm, const int* __restrict__ slot,
@@ -276,13 +277,15 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(256)
   }
 }
 
-// Interchanges of the panel's pivots on every column outside the panel, and the
-// row-block solve A[j0:j0+jb, c] = L_pp^{-1} A[j0:j0+jb, c] right of it.  Thread
-// cc < j0 owns left column cc (interchanges only); thread cc >= j0 owns column
-// c = cc + jb >= j0 + jb.
+// Interchanges of the panel's pivots and the row-block solve
+// A[j0:j0+jb, c] = L_pp^{-1} A[j0:j0+jb, c] on the columns c in [c_lo, c_hi)
+// outside the panel [j0, j0+jb): columns left of the panel get the interchanges
+// only, columns right of it the interchanges (when do_swap) and the solve.  One
+// thread per column.  The full-front form is c_lo = 0, c_hi = m, do_swap = 1.
 template <class T>
 __global__ void __launch_bounds__(256) lu_trsm_kernel(T* fronts, int m, int k, int j0, int jb,
-                                                      const int* piv) {
+                                                      const int* piv, int c_lo, int c_hi,
+                                                      int do_swap) {
   T* A = fronts + (long)blockIdx.y * m * m;
   __shared__ T Lp[kNB][kNB + 1];
   __shared__ int sp_[kNB];
@@ -292,19 +295,22 @@ __global__ void __launch_bounds__(256) lu_trsm_kernel(T* fronts, int m, int k, i
   }
   for (int e = threadIdx.x; e < jb; e += blockDim.x) sp_[e] = piv[(long)blockIdx.y * k + j0 + e];
   __syncthreads();
+  const int nleft = max(0, min(j0, c_hi) - c_lo);
+  const int rbeg = max(j0 + jb, c_lo);
   const int cc = blockIdx.x * blockDim.x + threadIdx.x;
-  const int c = cc < j0 ? cc : cc + jb;
-  if (c >= m) return;
+  const int c = cc < nleft ? c_lo + cc : rbeg + (cc - nleft);
+  if (c >= c_hi) return;
   T* colg = A + (long)c * m;
-  for (int jj = 0; jj < jb; ++jj) {
-    int p = sp_[jj];
-    if (p != j0 + jj) {
-      T t = colg[j0 + jj];
-      colg[j0 + jj] = colg[p];
-      colg[p] = t;
+  if (do_swap)
+    for (int jj = 0; jj < jb; ++jj) {
+      int p = sp_[jj];
+      if (p != j0 + jj) {
+        T t = colg[j0 + jj];
+        colg[j0 + jj] = colg[p];
+        colg[p] = t;
+      }
     }
-  }
-  if (cc < j0) return;
+  if (cc < nleft) return;
   T x[kNB];
   T* col = colg + j0;
 #pragma unroll
@@ -323,6 +329,27 @@ __global__ void __launch_bounds__(256) lu_trsm_kernel(T* fronts, int m, int k, i
 #pragma unroll
   for (int i = 0; i < kNB; ++i)
     if (i < jb) col[i] = x[i];
+}
+
+// Row interchanges piv[p0 .. p0+cnt) (in order) on the columns [0, a1) and
+// [b0, m) of every front; one thread per column.
+template <class T>
+__global__ void lu_laswp_kernel(T* fronts, int m, int k, int p0, int cnt, const int* piv, int a1,
+                                int b0) {
+  T* A = fronts + (long)blockIdx.y * m * m;
+  const int cc = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = cc < a1 ? cc : b0 + (cc - a1);
+  if (c >= m) return;
+  const int* pv = piv + (long)blockIdx.y * k;
+  T* col = A + (long)c * m;
+  for (int j = p0; j < p0 + cnt; ++j) {
+    const int p = pv[j];
+    if (p != j) {
+      T t = col[j];
+      col[j] = col[p];
+      col[p] = t;
+    }
+  }
 }
 
 // Batched C[M x N] -= A[M x K] B[K x N], K <= kNB, column-major with leading
@@ -695,10 +722,71 @@ bool panel_clustered(int m) {
   return (size_t)m * kNB * sizeof(T) > 160 * 1024;
 }
 
+// Panel LU of columns [j0, j0+jb) followed by the interchanges and the row-block
+// solve on the columns [c_lo, c_hi) outside the panel.
+template <class T>
+void panel_step(DevLevel& L, T* F, int j0, int jb, int c_lo, int c_hi, double ptol, int* status,
+                cudaStream_t st) {
+  double pf = 0;
+  for (int j = j0; j < j0 + jb; ++j) pf += (double)(L.m - j - 1) * (1.0 + 2.0 * (j0 + jb - j - 1));
+  ProfScope pp(PROF_LU_PANEL, st);
+  if (panel_clustered<T>(L.m)) {
+    size_t sm = sizeof(T) * (size_t)((L.m - j0 + kCL - 1) / kCL) * jb +
+                2 * sizeof(int) * (size_t)(L.m - j0);
+    lu_panel_cluster_kernel<T><<<L.nf * kCL, 256, sm, st>>>(F, L.m, L.k, j0, jb, L.piv, L.scale,
+                                                            ptol, status);
+  } else {
+    size_t sm = sizeof(T) * (size_t)(L.m - j0) * jb;
+    lu_panel_kernel<T><<<L.nf, 256, sm, st>>>(F, L.m, L.k, j0, jb, L.piv, L.scale, ptol, status);
+  }
+  pp.done(pf * L.nf, 1, st);
+  const int nleft = std::max(0, std::min(j0, c_hi) - c_lo);
+  const int nright = std::max(0, c_hi - std::max(j0 + jb, c_lo));
+  const int ncols = nleft + nright;
+  if (ncols > 0) {
+    // one thread per column; narrow CTAs when few fronts would leave SMs idle
+    const int tb = ((long)((ncols + 255) / 256) * L.nf >= 152) ? 256 : 64;
+    dim3 gt((ncols + tb - 1) / tb, L.nf);
+    ProfScope pt(PROF_LU_TRSM, st);
+    lu_trsm_kernel<T><<<gt, tb, 0, st>>>(F, L.m, L.k, j0, jb, L.piv, c_lo, c_hi, 1);
+    pt.done((double)nright * jb * (jb - 1) * L.nf, 1, st);
+  }
+}
+
+// C -= A B on the fronts (M x N x K sub-blocks at the given offsets, leading
+// dimension m, front stride m^2): SIMT tiles for K <= 32, else the general GEMM
+// or, for the tensor-core form, TF32 tensor cores.
+template <class T>
+void schur_update(DevLevel& L, T* F, int M, int N, int K, long offA, long offB, long offC,
+                  const FactorWork& W, int* status, cudaStream_t st) {
+  if (M <= 0 || N <= 0 || K <= 0) return;
+  const long mm = (long)L.m * L.m;
+  const double fl = 2.0 * M * N * K * L.nf;
+  if (K <= kNB) {
+    ProfScope pg(PROF_LU_GEMM, st);
+    gemm_sub<T>(M, N, K, F + offA, L.m, mm, F + offB, L.m, mm, F + offC, L.m, mm, L.nf, st);
+    pg.done(fl, 1, st);
+    return;
+  }
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (W.tc) {
+      ProfScope pc(PROF_LU_TC, st);
+      tc_schur_update(M, N, K, (const float*)(F + offA), L.m, mm, (const float*)(F + offB), L.m, mm,
+                      (float*)(F + offC), L.m, mm, L.nf, W.packA, W.packB, status, st);
+      pc.done(fl, 3, st);
+      return;
+    }
+  }
+  ProfScope pg(PROF_LU_GEMM, st);
+  gemm_gen<T>(M, N, K, (T)-1, true, F + offA, L.m, mm, F + offB, L.m, mm, F + offC, L.m, mm, L.nf,
+              0, 0, st);
+  pg.done(fl, 1, st);
+}
+
 template <class T>
 cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const double* Qcat,
                            const double* Ccat, const double* q, double ptol, int* status,
-                           void* scratch, cudaStream_t st) {
+                           const FactorWork& W, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(lu_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -707,6 +795,7 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
     attr = true;
   }
   const long mm = (long)L.m * L.m;
+  const int m = L.m, k = L.k;
   T* F = (T*)L.front;
   ProfScope pa(PROF_ASSEMBLE, st);
   cudaError_t e = cudaMemsetAsync(F, 0, sizeof(T) * mm * L.nf, st);
@@ -736,45 +825,66 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
     front_scale_kernel<T><<<gs, 256, 0, st>>>(F, mm, L.scale);
   }
   pa.done(abytes, na + 1, st);
-  const int NB = panel_width<T>(L.m);
+  const int NB = panel_width<T>(m);
   if (NB == 0) return cudaErrorInvalidValue;
-  for (int j0 = 0; j0 < L.k; j0 += NB) {
-    int jb = L.k - j0 < NB ? L.k - j0 : NB;
-    double pf = 0;
-    for (int j = j0; j < j0 + jb; ++j) pf += (double)(L.m - j - 1) * (1.0 + 2.0 * (j0 + jb - j - 1));
-    ProfScope pp(PROF_LU_PANEL, st);
-    if (panel_clustered<T>(L.m)) {
-      size_t sm = sizeof(T) * (size_t)((L.m - j0 + kCL - 1) / kCL) * jb +
-                  2 * sizeof(int) * (size_t)(L.m - j0);
-      lu_panel_cluster_kernel<T><<<L.nf * kCL, 256, sm, st>>>(F, L.m, L.k, j0, jb, L.piv, L.scale,
-                                                              ptol, status);
-    } else {
-      size_t sm = sizeof(T) * (size_t)(L.m - j0) * jb;
-      lu_panel_kernel<T><<<L.nf, 256, sm, st>>>(F, L.m, L.k, j0, jb, L.piv, L.scale, ptol, status);
+  const int OB = factor_outer_block(sizeof(T) == sizeof(float) ? SP_PREC_FP32 : SP_PREC_FP64, W.tc,
+                                    m, k);
+  if (OB == 0) {
+    // right-looking LU with a Schur update after every 32-column panel
+    for (int j0 = 0; j0 < k; j0 += NB) {
+      const int jb = std::min(NB, k - j0);
+      panel_step<T>(L, F, j0, jb, 0, m, ptol, status, st);
+      const int base = j0 + jb, rem = m - base;
+      schur_update<T>(L, F, rem, rem, jb, base + (long)j0 * m, j0 + (long)base * m,
+                      base + (long)base * m, W, status, st);
     }
-    pp.done(pf * L.nf, 1, st);
-    int rem = L.m - j0 - jb;
-    if (rem + j0 > 0) {
-      // one thread per column; narrow CTAs when few fronts would leave SMs idle
-      const int tb = ((long)((rem + j0 + 255) / 256) * L.nf >= 152) ? 256 : 64;
-      dim3 gt((rem + j0 + tb - 1) / tb, L.nf);
-      ProfScope pt(PROF_LU_TRSM, st);
-      lu_trsm_kernel<T><<<gt, tb, 0, st>>>(F, L.m, L.k, j0, jb, L.piv);
-      pt.done((double)rem * jb * (jb - 1) * L.nf, 1, st);
-    }
-    if (rem > 0) {
-      ProfScope pg(PROF_LU_GEMM, st);
-      const int base = j0 + jb;
-      gemm_sub<T>(rem, rem, jb, F + base + (long)j0 * L.m, L.m, mm, F + j0 + (long)base * L.m, L.m,
-                  mm, F + base + (long)base * L.m, L.m, mm, L.nf, st);
-      pg.done(2.0 * rem * rem * jb * L.nf, 1, st);
+  } else {
+    // blocked LU with outer blocks of OB columns: the outer panel [J0, e) is
+    // factored by 32-column steps whose interchanges, row-block solves and
+    // updates stay inside it; then its interchanges go to the other columns, the
+    // row band U12 = L11^{-1} A12 is solved in 32-row steps, and the trailing
+    // matrix gets one update of depth OB.
+    for (int J0 = 0; J0 < k; J0 += OB) {
+      const int e1 = std::min(k, J0 + OB);
+      for (int j0 = J0; j0 < e1; j0 += NB) {
+        const int jb = std::min(NB, e1 - j0);
+        panel_step<T>(L, F, j0, jb, J0, e1, ptol, status, st);
+        const int base = j0 + jb;
+        schur_update<T>(L, F, m - base, e1 - base, jb, base + (long)j0 * m, j0 + (long)base * m,
+                        base + (long)base * m, W, status, st);
+      }
+      const int ncols = J0 + (m - e1);
+      if (ncols > 0) {
+        ProfScope pt(PROF_LU_TRSM, st);
+        dim3 g((ncols + 255) / 256, L.nf);
+        lu_laswp_kernel<T><<<g, 256, 0, st>>>(F, m, k, J0, e1 - J0, L.piv, J0, e1);
+        pt.done(0, 1, st);
+      }
+      if (e1 < m) {
+        for (int j0 = J0; j0 < e1; j0 += NB) {
+          const int jb = std::min(NB, e1 - j0);
+          {
+            const int ncol = m - e1;
+            const int tb = ((long)((ncol + 255) / 256) * L.nf >= 152) ? 256 : 64;
+            dim3 gt((ncol + tb - 1) / tb, L.nf);
+            ProfScope pt(PROF_LU_TRSM, st);
+            lu_trsm_kernel<T><<<gt, tb, 0, st>>>(F, m, k, j0, jb, L.piv, e1, m, 0);
+            pt.done((double)ncol * jb * (jb - 1) * L.nf, 1, st);
+          }
+          const int base = j0 + jb;
+          schur_update<T>(L, F, e1 - base, m - e1, jb, base + (long)j0 * m, j0 + (long)e1 * m,
+                          base + (long)e1 * m, W, status, st);
+        }
+        schur_update<T>(L, F, m - e1, m - e1, e1 - J0, e1 + (long)J0 * m, J0 + (long)e1 * m,
+                        e1 + (long)e1 * m, W, status, st);
+      }
     }
   }
   lu_perm_kernel<<<(L.nf + 127) / 128, 128, 0, st>>>(L.piv, L.perm, L.k, L.nf);
   ProfScope pi(PROF_LU_TRINV, st);
   double bw = 0;
   if (L.inv) {
-    invert_triangles<T>(L, (T*)scratch, kInvBlock, st);
+    invert_triangles<T>(L, (T*)W.inv, kInvBlock, st);
     const int Bz = kInvBlock < L.k ? kInvBlock : L.k;
     bw = (2.0 / 3.0) * (double)Bz * Bz * L.k * L.nf;
   } else {
@@ -790,10 +900,42 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
 
 cudaError_t factor_level(int prec, int d, DevLevel& L, const DevLevel* child, const double* Qcat,
                          const double* Ccat, const double* q, double pivot_tol, int* status,
-                         void* scratch, cudaStream_t st) {
+                         const FactorWork& W, cudaStream_t st) {
   if (prec == SP_PREC_FP32)
-    return factor_level_t<float>(d, L, child, Qcat, Ccat, q, pivot_tol, status, scratch, st);
-  return factor_level_t<double>(d, L, child, Qcat, Ccat, q, pivot_tol, status, scratch, st);
+    return factor_level_t<float>(d, L, child, Qcat, Ccat, q, pivot_tol, status, W, st);
+  return factor_level_t<double>(d, L, child, Qcat, Ccat, q, pivot_tol, status, W, st);
+}
+
+cudaError_t schur_update_raw(int prec, bool tc, int M, int N, int K, const void* A, int lda, long sA,
+                             const void* B, int ldb, long sB, void* C, int ldc, long sC, int batch,
+                             float* packA, float* packB, int* status, cudaStream_t st) {
+  if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return cudaSuccess;
+  if (prec == SP_PREC_FP32 && tc)
+    return tc_schur_update(M, N, K, (const float*)A, lda, sA, (const float*)B, ldb, sB, (float*)C,
+                           ldc, sC, batch, packA, packB, status, st);
+  if (prec == SP_PREC_FP32) {
+    if (K <= kNB)
+      gemm_sub<float>(M, N, K, (const float*)A, lda, sA, (const float*)B, ldb, sB, (float*)C, ldc,
+                      sC, batch, st);
+    else
+      gemm_gen<float>(M, N, K, -1.f, true, (const float*)A, lda, sA, (const float*)B, ldb, sB,
+                      (float*)C, ldc, sC, batch, 0, 0, st);
+  } else {
+    if (K <= kNB)
+      gemm_sub<double>(M, N, K, (const double*)A, lda, sA, (const double*)B, ldb, sB, (double*)C,
+                       ldc, sC, batch, st);
+    else
+      gemm_gen<double>(M, N, K, -1.0, true, (const double*)A, lda, sA, (const double*)B, ldb, sB,
+                       (double*)C, ldc, sC, batch, 0, 0, st);
+  }
+  return cudaGetLastError();
+}
+
+int factor_outer_block(int prec, bool tc, int m, int k) {
+  // the tensor-core form blocks the fronts whose trailing updates are large
+  // enough to fill the GPU with 128 x 128 tiles
+  if (prec == SP_PREC_FP32 && tc && m >= kTcMinFront && k > kNB) return kTcMaxK;
+  return 0;
 }
 
 int factor_panel_width(int prec, int m) {

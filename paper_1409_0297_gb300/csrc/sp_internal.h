@@ -25,7 +25,8 @@ enum ProfClass {
   PROF_FFT = 7,
   PROF_KRYLOV = 8,
   PROF_LU_TRINV = 9,  // explicit triangular inverses of few-front levels
-  PROF_NCLASS = 10
+  PROF_LU_TC = 10,    // tensor-core Schur updates of the blocked fronts (with operand packing)
+  PROF_NCLASS = 11
 };
 struct Profiler {
   struct Rec {
@@ -92,12 +93,38 @@ cudaError_t fft_green_apply32(const FftPlan& P, const float2* x, const float* q,
 cudaError_t to_float(const double* a, float* b, long N, cudaStream_t st);
 
 // ---------------------------------------------------------------- factor (sp_factor.cu)
-// scratch: 3 nf k^2 entries of the factor type when L.inv (triangular inverses)
+// Work buffers of the factorisation, shared by all levels.
+struct FactorWork {
+  void* inv = nullptr;        // 3 nf k^2 entries of the factor type when L.inv (triangular inverses)
+  float* packA = nullptr;     // tensor-core operand buffers (tc_pack_floats each)
+  float* packB = nullptr;
+  bool tc = false;            // Schur updates of the blocked fronts on the tensor cores
+};
+// status bits: 1 = pivot below the threshold, 2 = a bounded device wait ran out
 cudaError_t factor_level(int prec, int d, DevLevel& L, const DevLevel* child, const double* Qcat,
                          const double* Ccat, const double* q, double pivot_tol, int* status,
-                         void* scratch, cudaStream_t st);
+                         const FactorWork& W, cudaStream_t st);
 // panel width used for fronts of size m (0 if the staged panel cannot fit)
 int factor_panel_width(int prec, int m);
+// outer block width of the blocked LU of a front (0: the 32-column right-looking
+// LU with a Schur update after every panel)
+int factor_outer_block(int prec, bool tc, int m, int k);
+
+// C[M x N] -= A[M x K] B[K x N] with the kernel the factorisation uses for the
+// form (FP64 or FP32 SIMT; FP32 with tc: tensor cores, K <= kTcMaxK)
+cudaError_t schur_update_raw(int prec, bool tc, int M, int N, int K, const void* A, int lda, long sA,
+                             const void* B, int ldb, long sB, void* C, int ldc, long sC, int batch,
+                             float* packA, float* packB, int* status, cudaStream_t st);
+
+// ---------------------------------------------------------------- tensor cores (sp_tc.cu)
+constexpr int kTcMaxK = 256;
+// floats of one packed operand buffer for `rows` rows, K columns, batch fronts
+size_t tc_pack_floats(int rows, int K, int batch);
+// C[M x N] -= A[M x K] B[K x N] (column-major, batch strides sA, sB, sC) with
+// TF32 tensor-core products and FP32 accumulation; K <= kTcMaxK.
+cudaError_t tc_schur_update(int M, int N, int K, const float* A, int lda, long sA, const float* B,
+                            int ldb, long sB, float* C, int ldc, long sC, int batch, float* packA,
+                            float* packB, int* status, cudaStream_t st);
 
 // ---------------------------------------------------------------- solve (sp_solve.cu)
 struct QTypeDev {

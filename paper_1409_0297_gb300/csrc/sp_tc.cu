@@ -1,0 +1,342 @@
+// Schur-complement update of the large fronts on the tensor cores, for the
+// tensor-core form of the preconditioner (Section 2.3: S = F22 - L21 U12 of each
+// front, here with the K = 256 columns of one outer block of the blocked LU):
+//
+//   C[M x N] -= A[M x K] B[K x N]      (column-major, batched over fronts)
+//
+// A = L21 and B = U12 are first copied into K-major operand buffers rounded to
+// TF32 (round to nearest), padded to a multiple of 32 in K with zeros: packA
+// [batch][M][Kp], packB [batch][N][Kp].  Those are read by TMA (3-D tensor maps,
+// 128-byte swizzle) into a ring of shared-memory stages; one thread issues
+// tcgen05.mma kind::tf32 (M = 128, N = BN, K = 8 per instruction) with the FP32
+// accumulator in tensor memory; all eight warps then read the accumulator with
+// tcgen05.ld and subtract it from C in global memory (the front keeps its
+// column-major layout with leading dimension m, which needs no alignment).
+//
+// Every wait on an mbarrier is bounded (about 2 s of global timer); a wait that
+// runs out sets bit 2 of *status, the CTA drains the copies it issued, frees its
+// tensor memory and returns without touching C.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "sp_internal.h"
+
+namespace sp {
+
+namespace {
+
+constexpr int kBM = 128;       // tile rows = tensor-memory lanes
+constexpr int kBK = 32;        // K per stage: 32 FP32 = one 128-byte swizzle row
+constexpr int kUK = 8;         // K of one kind::tf32 instruction
+constexpr int kThreads = 256;  // 8 warps
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for the phase with the given parity to complete
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try(bar, parity))
+    if (gtimer() - t0 > kWaitNs) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// groups 1024 bytes apart (start address and offsets in 16-byte units; bit 46 is
+// the descriptor version of this architecture; layout 2 = 128-byte swizzle)
+__device__ __forceinline__ unsigned long long sw128_desc(uint32_t saddr) {
+  return (unsigned long long)((saddr & 0x3FFFFu) >> 4) | ((unsigned long long)(1024u >> 4) << 32) |
+         (1ull << 46) | (2ull << 61);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, unsigned long long ad,
+                                         unsigned long long bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+  return __uint_as_float(u);
+}
+
+// C -= A B for one BM x BN tile of one front (blockIdx.y); nk stages of K = 32.
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(kThreads, 2) tc_gemm_sub_kernel(
+    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M,
+    int N, int nk, float* C, int ldc, long sC, int tilesM, int* status) {
+  constexpr uint32_t kABytes = kBM * kBK * 4;
+  constexpr uint32_t kBBytes = BN * kBK * 4;
+  constexpr uint32_t kStage = kABytes + kBBytes;
+  // instruction descriptor: D = F32 (bits 4-5), A = B = TF32 (bits 7-9, 10-12),
+  // both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+  constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                              ((uint32_t)(kBM >> 4) << 24);
+  extern __shared__ unsigned char smraw[];
+  __shared__ __align__(8) unsigned long long full[STAGES], empty[STAGES], done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_abort, s_issued, s_consumed;
+  const uint32_t base = (smem_u32(smraw) + 1023u) & ~1023u;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int f = blockIdx.y;
+  const int m0 = (blockIdx.x % tilesM) * kBM, n0 = (blockIdx.x / tilesM) * BN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(&done), 1);
+    s_abort = 0;
+    s_issued = 0;
+    s_consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"((uint32_t)BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // producer: TMA loads of the A and B stages
+    int kb = 0;
+    for (; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (kb >= STAGES && !mbar_wait(smem_u32(&empty[s]), ((kb / STAGES) - 1) & 1)) {
+        atomicOr(&s_abort, 1);
+        break;
+      }
+      const uint32_t fb = smem_u32(&full[s]);
+      mbar_expect_tx(fb, kStage);
+      tma_load_3d(base + s * kStage, &tmA, kb * kBK, m0, f, fb);
+      tma_load_3d(base + s * kStage + kABytes, &tmB, kb * kBK, n0, f, fb);
+    }
+    s_issued = kb;
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    int kb = 0;
+    for (; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(smem_u32(&full[s]), (kb / STAGES) & 1)) {
+        atomicOr(&s_abort, 1);
+        break;
+      }
+      tc_fence_after();
+      const unsigned long long ad = sw128_desc(base + s * kStage);
+      const unsigned long long bd = sw128_desc(base + s * kStage + kABytes);
+#pragma unroll
+      for (int kk = 0; kk < kBK / kUK; ++kk)  // +32 bytes along K = +2 in the address field
+        mma_tf32(tmem, ad + 2 * kk, bd + 2 * kk, kIdesc, (kb | kk) != 0 ? 1u : 0u);
+      mma_commit(smem_u32(&empty[s]));
+    }
+    s_consumed = kb;
+    mma_commit(smem_u32(&done));  // arrives once every MMA issued above has completed
+  }
+  __syncwarp();
+  const bool ok = mbar_wait(smem_u32(&done), 0);
+  tc_fence_after();
+  __syncthreads();
+  const bool abort = !ok || s_abort != 0;
+  // epilogue: warp w reads lanes 32 (w % 4) .. +31 (tile rows) and half w / 4 of
+  // the columns, 32 columns per tensor-memory load
+  const int qw = warp & 3, h = warp >> 2;
+  const int row = m0 + qw * 32 + lane;
+  float* Cf = C + (long)f * sC;
+  if (!abort) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN / 2; c0 += 32) {
+      const int colb = n0 + h * (BN / 2) + c0;
+      float cv[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int col = colb + j;
+        cv[j] = (row < M && col < N) ? Cf[row + (long)col * ldc] : 0.f;
+      }
+      uint32_t v[32];
+      tmem_ld32(tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)(h * (BN / 2) + c0), v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int col = colb + j;
+        if (row < M && col < N) Cf[row + (long)col * ldc] = cv[j] - __uint_as_float(v[j]);
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    atomicOr(status, 2);
+    // drain: wait (bounded) for the copies issued but never consumed
+    for (int kb = s_consumed; kb < s_issued; ++kb)
+      (void)mbar_wait(smem_u32(&full[kb % STAGES]), (kb / STAGES) & 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)BN)
+                 : "memory");
+  }
+}
+
+// packA[f][i][kk] = tf32(A[f sA + i + kk lda]) for kk < K, 0 for K <= kk < Kp.
+// 32 x 32 tiles transposed through shared memory; block (32, 8).
+__global__ void tc_pack_a_kernel(const float* __restrict__ A, int lda, long sA, int M, int K,
+                                 int Kp, float* __restrict__ P) {
+  __shared__ float t[32][33];
+  const long f = blockIdx.z;
+  const int i0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int kk = k0 + r, i = i0 + threadIdx.x;
+    t[r][threadIdx.x] = (i < M && kk < K) ? A[f * sA + i + (long)kk * lda] : 0.f;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int i = i0 + r, kk = k0 + threadIdx.x;
+    if (i < M) P[(f * M + i) * (long)Kp + kk] = to_tf32(t[threadIdx.x][r]);
+  }
+}
+
+// packB[f][j][kk] = tf32(B[f sB + kk + j ldb]) for kk < K, 0 for K <= kk < Kp.
+__global__ void tc_pack_b_kernel(const float* __restrict__ B, int ldb, long sB, int N, int K,
+                                 int Kp, float* __restrict__ P) {
+  const long f = blockIdx.y;
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long)N * Kp) return;
+  const int kk = (int)(e % Kp);
+  const long j = e / Kp;
+  P[f * N * (long)Kp + e] = kk < K ? to_tf32(B[f * sB + kk + j * ldb]) : 0.f;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+cudaError_t encode_operand(CUtensorMap* map, float* P, int rows, int Kp, int batch, int box_rows) {
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  });
+  if (!g_encode) return cudaErrorNotSupported;
+  const cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)batch};
+  const cuuint64_t strides[2] = {(cuuint64_t)Kp * 4, (cuuint64_t)rows * Kp * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)box_rows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, P, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+constexpr int kBN = 128;
+constexpr int kStages = 3;
+constexpr size_t kSmem = (size_t)kStages * (kBM * kBK * 4 + kBN * kBK * 4) + 1024;
+
+}  // namespace
+
+size_t tc_pack_floats(int rows, int K, int batch) {
+  return (size_t)batch * rows * (size_t)((K + kBK - 1) / kBK * kBK);
+}
+
+cudaError_t tc_schur_update(int M, int N, int K, const float* A, int lda, long sA, const float* B,
+                            int ldb, long sB, float* C, int ldc, long sC, int batch, float* packA,
+                            float* packB, int* status, cudaStream_t st) {
+  if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return cudaSuccess;
+  if (K > kTcMaxK || batch > 65535 || !packA || !packB) return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_sub_kernel<kBN, kStages>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int Kp = (K + kBK - 1) / kBK * kBK;
+  {
+    dim3 g((M + 31) / 32, Kp / 32, batch);
+    tc_pack_a_kernel<<<g, dim3(32, 8), 0, st>>>(A, lda, sA, M, K, Kp, packA);
+    const long nb = (long)N * Kp;
+    dim3 gb((unsigned)((nb + 255) / 256), batch);
+    tc_pack_b_kernel<<<gb, 256, 0, st>>>(B, ldb, sB, N, K, Kp, packB);
+  }
+  CUtensorMap ta, tb;
+  cudaError_t e = encode_operand(&ta, packA, M, Kp, batch, kBM);
+  if (e != cudaSuccess) return e;
+  e = encode_operand(&tb, packB, N, Kp, batch, kBN);
+  if (e != cudaSuccess) return e;
+  const int tilesM = (M + kBM - 1) / kBM, tilesN = (N + kBN - 1) / kBN;
+  dim3 g((unsigned)((long)tilesM * tilesN), batch);
+  tc_gemm_sub_kernel<kBN, kStages><<<g, kThreads, kSmem, st>>>(ta, tb, M, N, Kp / kBK, C, ldc, sC,
+                                                              tilesM, status);
+  return cudaGetLastError();
+}
+
+}  // namespace sp
