@@ -164,11 +164,11 @@ sp_status sp_front_sizes(int d, int n, int b, int cap, int *nlevels, int *nfront
  * gidx: nf x m grid indices of the front unknowns (eliminated ones first);
  * ea_map: 2^d x (mc - kc) positions in this level's fronts of the children's
  * boundary unknowns (child position delta = sum_a 2^a * (child box coordinate a
- * is odd)); asm_slot / asm_cvar: nasm front slots (r + c*m, column-major) and
- * front positions of the column point of the original entries of P assembled
- * into every front of the level. */
+ * is odd)); asm_row / asm_cvar: front row r and front column c (the position of
+ * the column point; entry r + c m of the column-major front) of the nasm
+ * original entries of P assembled into every front of the level. */
 sp_status sp_level_info(int d, int n, int b, int level, int *nf, int *k, int *m, int *mc,
-                        int *kc, int *nasm, int *gidx, int *ea_map, int *asm_slot,
+                        int *kc, int *nasm, int *gidx, int *ea_map, int *asm_row,
                         int *asm_cvar);
 
 /* Algorithmic sizes of the context: factor entries (sum over fronts of

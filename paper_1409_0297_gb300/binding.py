@@ -220,14 +220,14 @@ def sp_level_info(d: int, n: int, b: int, level: int) -> dict:
     nf, k, m, mc, kc, nasm = (x.value for x in v)
     gidx = np.zeros(nf * m, dtype=np.int32)
     ea = np.zeros(max(1, (1 << d) * (mc - kc)), dtype=np.int32)
-    slot = np.zeros(max(1, nasm), dtype=np.int32)
+    row = np.zeros(max(1, nasm), dtype=np.int32)
     cvar = np.zeros(max(1, nasm), dtype=np.int32)
     ip = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
     _check(LIB.sp_level_info(d, n, b, level, *[ctypes.byref(x) for x in v], ip(gidx), ip(ea),
-                             ip(slot), ip(cvar)), "sp_level_info")
+                             ip(row), ip(cvar)), "sp_level_info")
     return dict(nf=nf, k=k, m=m, mc=mc, kc=kc, gidx=gidx.reshape(nf, m),
                 ea_map=ea[: (1 << d) * (mc - kc)].reshape(1 << d, mc - kc) if mc else None,
-                asm_slot=slot[:nasm], asm_cvar=cvar[:nasm])
+                asm_row=row[:nasm], asm_cvar=cvar[:nasm])
 
 
 def sp_costs(ctx: int):

@@ -285,7 +285,7 @@ sp_status sp_stencil_table(int d, int n, int b, double s, int t, int host_thread
 }
 
 sp_status sp_level_info(int d, int n, int b, int level, int* nf, int* k, int* m, int* mc, int* kc,
-                        int* nasm, int* gidx, int* ea_map, int* asm_slot, int* asm_cvar) {
+                        int* nasm, int* gidx, int* ea_map, int* asm_row, int* asm_cvar) {
   int L;
   if (check_grid(d, n, b, &L) || level < 0 || level > L) return SP_ERR_ARG;
   try {
@@ -331,10 +331,10 @@ sp_status sp_level_info(int d, int n, int b, int level, int* nf, int* k, int* m,
     if (m) *m = V.m;
     if (mc) *mc = V.mc;
     if (kc) *kc = V.kc;
-    if (nasm) *nasm = (int)V.asm_slot.size();
+    if (nasm) *nasm = (int)V.asm_row.size();
     if (gidx) std::memcpy(gidx, V.gidx.data(), V.gidx.size() * sizeof(int));
     if (ea_map && !V.ea_map.empty()) std::memcpy(ea_map, V.ea_map.data(), V.ea_map.size() * sizeof(int));
-    if (asm_slot) std::memcpy(asm_slot, V.asm_slot.data(), V.asm_slot.size() * sizeof(int));
+    if (asm_row) std::memcpy(asm_row, V.asm_row.data(), V.asm_row.size() * sizeof(int));
     if (asm_cvar) std::memcpy(asm_cvar, V.asm_cvar.data(), V.asm_cvar.size() * sizeof(int));
   } catch (const std::bad_alloc&) {
     return SP_ERR_OOM;
@@ -488,7 +488,7 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   const size_t fsz = (prec == SP_PREC_FP32) ? sizeof(float) : sizeof(double);
   const size_t vsz = (prec == SP_PREC_FP32) ? sizeof(float2) : sizeof(double2);
   c->lv.resize(L + 1);
-  size_t scratch_bytes = 0, pack_floats = 0;
+  size_t scratch_bytes = 0, pack_floats = 0, gp_bytes = 0, gp_keys = 0, gp_maps = 0, gp_bar = 0;
   for (int l = 0; l <= L; ++l) {
     const Level& S = c->sym.lv[l];
     DevLevel& D = c->lv[l];
@@ -498,9 +498,9 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
     D.nb1 = S.nb1;
     D.mc = S.mc;
     D.kc = S.kc;
-    D.nasm = (int)S.asm_slot.size();
+    D.nasm = (int)S.asm_row.size();
     SP_CK(upload(c.get(), &D.gidx, S.gidx));
-    SP_CK(upload(c.get(), &D.asm_slot, S.asm_slot));
+    SP_CK(upload(c.get(), &D.asm_row, S.asm_row));
     SP_CK(upload(c.get(), &D.asm_tidx, S.asm_tidx));
     SP_CK(upload(c.get(), &D.asm_cvar, S.asm_cvar));
     SP_CK(upload(c.get(), &D.ea_map, S.ea_map));
@@ -514,10 +514,17 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
     // few fronts: keep the inverses of the diagonal blocks of L11 and U11 so the
     // sweeps spread over the GPU; in the FP32 form every level does (the block
     // inverses cost little in FP32 and the sweeps become matrix-vector products)
-    D.inv = S.nf < 152 || prec == SP_PREC_FP32;
+    D.inv = S.nf < 152 || prec == SP_PREC_FP32 || vsz * (size_t)(S.m + S.k) > 192 * 1024;
     if (D.inv) {
       SP_CK(dalloc(c.get(), &D.tmp, vsz * (size_t)S.nf * S.m));
-      scratch_bytes = std::max(scratch_bytes, 3 * fsz * (size_t)S.nf * S.k * S.k);
+      scratch_bytes = std::max(scratch_bytes, fsz * invert_scratch_elems(S.nf, S.k));
+    }
+    if (factor_grid_panel(prec, S.m)) {
+      const int G = grid_panel_ctas(S.nf, S.m);
+      gp_bytes = std::max(gp_bytes, fsz * (size_t)S.nf * S.m * 32);
+      gp_keys = std::max(gp_keys, (size_t)S.nf * 2 * G);
+      gp_maps = std::max(gp_maps, (size_t)S.nf * 2 * S.m);
+      gp_bar = std::max(gp_bar, (size_t)S.nf * 2);
     }
     if (factor_outer_block(prec, tc, S.m, S.k) > 0)
       pack_floats = std::max(pack_floats, tc_pack_floats(S.m, kTcMaxK, S.nf));
@@ -527,6 +534,12 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   }
   c->apply_bytes = c->factor_entries * fsz;
   if (scratch_bytes) SP_CK(dalloc(c.get(), &c->work.inv, scratch_bytes));
+  if (gp_bytes) {
+    SP_CK(dalloc(c.get(), &c->work.gpanel, gp_bytes));
+    SP_CK(dalloc(c.get(), &c->work.gkeys, sizeof(unsigned long long) * gp_keys));
+    SP_CK(dalloc(c.get(), &c->work.gmaps, sizeof(int) * gp_maps));
+    SP_CK(dalloc(c.get(), &c->work.gbar, sizeof(unsigned) * gp_bar));
+  }
   if (pack_floats) {
     SP_CK(dalloc(c.get(), &c->work.packA, sizeof(float) * pack_floats));
     SP_CK(dalloc(c.get(), &c->work.packB, sizeof(float) * pack_floats));

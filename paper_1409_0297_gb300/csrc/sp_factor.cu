@@ -27,9 +27,10 @@ constexpr int kNB = 32;       // panel width
 constexpr int kTile = 64;     // Schur update tile (kTile x kTile per CTA)
 constexpr int kInvBlock = kInvBlockSize;  // diagonal-block size of the inverse-form levels
 constexpr int kTcMinFront = 1024;         // smallest front blocked for the tensor cores
+constexpr int kGridPanelCTAs = 152;       // CTAs of a grid-panel launch (one per SM)
 
 template <class T>
-__global__ void assemble_kernel(T* fronts, int m, int nasm, const int* __restrict__ slot,
+__global__ void assemble_kernel(T* fronts, int m, int nasm, const int* __restrict__ row,
                                 const int* __restrict__ tidx, const int* __restrict__ cvar,
                                 const int* __restrict__ gidx, const double* __restrict__ Qcat,
                                 const double* __restrict__ Ccat, const double* __restrict__ q) {
@@ -37,8 +38,9 @@ __global__ void assemble_kernel(T* fronts, int m, int nasm, const int* __restric
   if (e >= nasm) return;
   long f = blockIdx.y;
   int ti = tidx[e];
-  double qi = q[gidx[f * m + cvar[e]]];
-  fronts[f * (long)m * m + slot[e]] = (T)fma(Ccat[ti], qi, Qcat[ti]);
+  const int c = cvar[e];
+  double qi = q[gidx[f * m + c]];
+  fronts[f * (long)m * m + row[e] + (long)c * m] = (T)fma(Ccat[ti], qi, Qcat[ti]);
 }
 
 template <class T>
@@ -277,6 +279,178 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(256)
   }
 }
 
+// Panel LU of a front too tall for the cluster panel: G CTAs per front in one
+// cooperative launch (every CTA resident).  The panel rows [j0, m) are copied to
+// a work array W (rows x jb, column-major, in global memory and small enough to
+// stay in L2) and factored there; CTA g owns the rows ("slots") [g c, (g+1) c).
+// Rows never move during the panel.  A slot is a pivot candidate while its
+// starting position is below k (interchanges only exchange positions below k) and
+// it has not been a pivot yet.  Per pivot column every CTA publishes its best
+// candidate as a 64-bit key (FP32 magnitude high, complemented slot low; double
+// buffered), one barrier of the front's CTAs (counter and generation in global
+// memory, bounded spin), then every CTA reads the keys and the pivot row (final
+// from then on, read through L2) and updates its rows.  CTA 0 keeps the
+// position <-> slot maps and the pivot record; the panel is written back in
+// position order after a last barrier.  A barrier that does not complete within
+// about 2 s sets bit 2 of *status and the kernel returns without writing back.
+__device__ __forceinline__ unsigned long long gtimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+// barrier of the G CTAs of one front; false if it timed out
+__device__ bool group_sync(unsigned* cnt, unsigned* gen, int G, unsigned* s_gen, int* s_abort) {
+  __syncthreads();
+  if (threadIdx.x == 0 && !*s_abort) {
+    const unsigned g0 = *s_gen;
+    __threadfence();
+    if (atomicAdd(cnt, 1u) == (unsigned)G - 1) {
+      atomicExch(cnt, 0u);
+      __threadfence();
+      atomicExch(gen, g0 + 1);
+    } else {
+      const unsigned long long t0 = gtimer_ns();
+      while (ld_acquire(gen) == g0) {
+        if (gtimer_ns() - t0 > 2000000000ull) {
+          *s_abort = 1;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    *s_gen = g0 + 1;
+  }
+  __syncthreads();
+  return !*s_abort;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) lu_panel_grid_kernel(T* fronts, int m, int k, int j0, int jb,
+                                                            int G, int* piv, const double* scale,
+                                                            double ptol, int* status, T* W,
+                                                            unsigned long long* keys, int* maps,
+                                                            unsigned* bar) {
+  const int f = blockIdx.x / G, g = blockIdx.x % G;
+  T* A = fronts + (long)f * m * m;
+  const int rows = m - j0, kl = k - j0;
+  const int chunk = (rows + G - 1) / G;
+  const int s0 = min(rows, g * chunk), s1 = min(rows, s0 + chunk);
+  T* Wf = W + (long)f * rows * jb;
+  unsigned long long* kf = keys + (long)f * 2 * G;
+  int* s2p = maps + (long)f * 2 * rows;  // slot -> position
+  int* p2s = s2p + rows;                  // position -> slot
+  unsigned* cnt = bar + 2 * f;
+  unsigned* gen = cnt + 1;
+  extern __shared__ unsigned char smraw[];
+  unsigned char* elim = smraw;  // my slots already used as pivots
+  __shared__ T prow[kNB];
+  __shared__ unsigned long long wkey[8];
+  __shared__ int s_sb, s_abort;
+  __shared__ unsigned s_gen;
+  __shared__ T s_pv;
+  const double thresh = ptol * scale[f];
+  for (long e = threadIdx.x; e < (long)(s1 - s0) * jb; e += blockDim.x) {
+    const int r = s0 + (int)(e % (s1 - s0)), c = (int)(e / (s1 - s0));
+    Wf[r + (long)c * rows] = A[(j0 + r) + (long)(j0 + c) * m];
+  }
+  for (int sl = s0 + threadIdx.x; sl < s1; sl += blockDim.x) {
+    s2p[sl] = sl;
+    p2s[sl] = sl;
+    elim[sl - s0] = 0;
+  }
+  if (threadIdx.x == 0) {
+    s_gen = ld_acquire(gen);
+    s_abort = 0;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  for (int jj = 0; jj < jb; ++jj) {
+    unsigned long long key = 0ull;
+    for (int sl = s0 + threadIdx.x; sl < s1; sl += blockDim.x) {
+      if (sl >= kl || elim[sl - s0]) continue;
+      const float v = (float)fabs((double)Wf[sl + (long)jj * rows]);
+      const unsigned long long kk = ((unsigned long long)__float_as_uint(v) << 32) |
+                                    (unsigned long long)(0xffffffffu - (unsigned)sl);
+      key = kk > key ? kk : key;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long ok = __shfl_down_sync(0xffffffffu, key, o);
+      key = ok > key ? ok : key;
+    }
+    if (lane == 0) wkey[warp] = key;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long kb = wkey[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) kb = wkey[w] > kb ? wkey[w] : kb;
+      __stcg(&kf[(jj & 1) * G + g], kb);
+    }
+    if (!group_sync(cnt, gen, G, &s_gen, &s_abort)) break;
+    if (warp == 0) {
+      unsigned long long kb = 0ull;
+      for (int l = lane; l < G; l += 32) {
+        const unsigned long long o = __ldcg(&kf[(jj & 1) * G + l]);
+        kb = o > kb ? o : kb;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long ok = __shfl_down_sync(0xffffffffu, kb, o);
+        kb = ok > kb ? ok : kb;
+      }
+      if (lane == 0) {
+        int sb = (int)(0xffffffffu - (unsigned)(kb & 0xffffffffull));
+        if (kb == 0ull || sb < 0 || sb >= rows) {  // no candidate: cannot happen for jj < kl
+          sb = 0;
+          atomicOr(status, 1);
+        }
+        s_sb = sb;
+      }
+    }
+    __syncthreads();
+    const int sb = s_sb;
+    if (threadIdx.x < jb - jj) {
+      const T v = __ldcg(&Wf[sb + (long)(jj + threadIdx.x) * rows]);
+      if (threadIdx.x == 0) s_pv = v;
+      else prow[threadIdx.x - 1] = v;
+    }
+    if (threadIdx.x == 0) {
+      if (sb >= s0 && sb < s1) elim[sb - s0] = 1;
+      if (g == 0) {
+        const int p = s2p[sb], sa = p2s[jj];
+        s2p[sb] = jj;
+        s2p[sa] = p;
+        p2s[jj] = sb;
+        p2s[p] = sa;
+        piv[(long)f * k + j0 + jj] = j0 + p;
+      }
+    }
+    __syncthreads();
+    T pv = s_pv;
+    if (g == 0 && threadIdx.x == 0 && !(fabs((double)pv) > thresh)) atomicOr(status, 1);
+    if (!(fabs((double)pv) > 0.0)) pv = (T)(thresh > 0 ? thresh : 1e-30);
+    const T inv = (T)1 / pv;
+    for (int sl = s0 + threadIdx.x; sl < s1; sl += blockDim.x) {
+      if (elim[sl - s0]) continue;
+      T* pr = Wf + sl;
+      const T l = pr[(long)jj * rows] * inv;
+      pr[(long)jj * rows] = l;
+      for (int c = jj + 1; c < jb; ++c) pr[(long)c * rows] -= l * prow[c - jj - 1];
+    }
+  }
+  if (!group_sync(cnt, gen, G, &s_gen, &s_abort)) {
+    if (threadIdx.x == 0) atomicOr(status, 2);
+    return;
+  }
+  for (long e = threadIdx.x; e < (long)(s1 - s0) * jb; e += blockDim.x) {
+    const int r = s0 + (int)(e % (s1 - s0)), c = (int)(e / (s1 - s0));
+    A[(j0 + __ldcg(&s2p[r])) + (long)(j0 + c) * m] = Wf[r + (long)c * rows];
+  }
+}
+
 // Interchanges of the panel's pivots and the row-block solve
 // A[j0:j0+jb, c] = L_pp^{-1} A[j0:j0+jb, c] on the columns c in [c_lo, c_hi)
 // outside the panel [j0, j0+jb): columns left of the panel get the interchanges
@@ -500,14 +674,15 @@ __global__ void lu_perm_kernel(const int* piv, int* perm, int k, int nf) {
 // ---- explicit triangular inverses for levels with few fronts -------------------
 // Inverse of every 32 x 32 diagonal block of L11 (unit lower; upper == 0) or U11
 // (upper == 1) of every front, written to the matching diagonal block of X
-// (k x k per front, leading dimension k).  One CTA per (block, front); thread c
-// solves column c by substitution.
+// (entry (i, j) at i + j ldx, front stride sX).  One CTA per (block, front);
+// thread c solves column c by substitution.
 template <class T>
-__global__ void trinv_diag32_kernel(const T* fronts, int m, T* X, int k, int upper) {
+__global__ void trinv_diag32_kernel(const T* fronts, int m, T* X, int ldx, long sX, int k,
+                                    int upper) {
   const int j0 = blockIdx.x * kNB;
   const int jb = min(kNB, k - j0);
   const T* A = fronts + (long)blockIdx.y * m * m;
-  T* Xf = X + (long)blockIdx.y * k * k;
+  T* Xf = X + (long)blockIdx.y * sX;
   __shared__ T Bk[kNB][kNB + 1];
   for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) {
     int i = e % jb, l = e / jb;
@@ -540,7 +715,7 @@ __global__ void trinv_diag32_kernel(const T* fronts, int m, T* X, int k, int upp
         x[i] = acc / Bk[i][i];
       }
   }
-  T* col = Xf + j0 + (long)(j0 + c) * k;
+  T* col = Xf + j0 + (long)(j0 + c) * ldx;
 #pragma unroll
   for (int i = 0; i < kNB; ++i)
     if (i < jb) col[i] = x[i];
@@ -592,17 +767,20 @@ __global__ void diag32_inplace_kernel(T* fronts, int m, int k) {
     if (i < jb) col[i] = (i > c) ? xl[i] : xu[i];
 }
 
-// F11 <- strict lower part of Linv, upper part (with the diagonal) of Uinv.
-// (only the diagonal blocks of size Bsz: the off-diagonal blocks keep L11, U11)
+// F11 <- strict lower part of Linv, upper part (with the diagonal) of Uinv, on
+// the diagonal blocks of size Bsz only (the off-diagonal blocks keep L11, U11).
+// X entry (r, c) at r + c Bsz (front stride sX); one thread per block entry.
 template <class T>
-__global__ void trinv_store_kernel(T* fronts, int m, const T* Xl, const T* Xu, int k, int Bsz) {
-  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (long)k * k) return;
-  int r = (int)(e % k), c = (int)(e / k);
-  if (r / Bsz != c / Bsz) return;
-  long f = blockIdx.y;
-  T v = (r > c) ? Xl[f * k * k + e] : Xu[f * k * k + e];
-  fronts[f * (long)m * m + r + (long)c * m] = v;
+__global__ void trinv_store_kernel(T* fronts, int m, const T* Xl, const T* Xu, long sX, int k,
+                                   int Bsz) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long bb = (long)Bsz * Bsz;
+  const long blk = e / bb, rem = e % bb;
+  const long r = blk * Bsz + rem % Bsz, c = blk * Bsz + rem / Bsz;
+  if (r >= k || c >= k) return;
+  const long f = blockIdx.y;
+  const long x = f * sX + r + c * Bsz;
+  fronts[f * (long)m * m + r + c * m] = (r > c) ? Xl[x] : Xu[x];
 }
 
 template <class T>
@@ -653,30 +831,35 @@ void gemm_gen(int M, int N, int K, T alpha, bool beta_one, const T* A, int lda, 
 //   [A 0; B C]^{-1} = [A^{-1} 0; -C^{-1} (B A^{-1}), C^{-1}]
 //   [A B; 0 C]^{-1} = [A^{-1}, -(A^{-1} B) C^{-1}; 0 C^{-1}]
 // with the two products of each merge as batched GEMMs over fronts and pairs.
-// scratch: Xl, Xu (k x k per front) and a k x k work block per front.
+// Storage: the inverses Xl, Xu keep entry (i, j) of a diagonal block at
+// i + j Bsz (a column-major array with leading dimension Bsz whose columns
+// overlap: the diagonal blocks never collide, and a pair's diagonal step is
+// 2 s (1 + Bsz) everywhere), k (Bsz + 1) entries per front; the work array W
+// holds pair p's product at rows [2ps, 2ps+s) of a k x Bsz/2 block per front.
 template <class T>
 void invert_triangles(DevLevel& L, T* scratch, int Bsz, cudaStream_t st) {
   const int k = L.k, m = L.m, nf = L.nf;
-  const long kk = (long)k * k, mm = (long)m * m;
+  const long mm = (long)m * m;
+  const int ldx = Bsz;
+  const long sX = (long)k * (Bsz + 1), sW = (long)k * (Bsz / 2);
   T* F = (T*)L.front;
   T* Xl = scratch;
-  T* Xu = scratch + kk * nf;
-  T* W = scratch + 2 * kk * nf;
-  cudaMemsetAsync(Xl, 0, sizeof(T) * kk * nf, st);
-  cudaMemsetAsync(Xu, 0, sizeof(T) * kk * nf, st);
+  T* Xu = scratch + sX * nf;
+  T* W = scratch + 2 * sX * nf;
+  cudaMemsetAsync(Xl, 0, sizeof(T) * sX * nf, st);
+  cudaMemsetAsync(Xu, 0, sizeof(T) * sX * nf, st);
   const int nb = (k + kNB - 1) / kNB;
   dim3 gd(nb, nf);
-  trinv_diag32_kernel<T><<<gd, kNB, 0, st>>>(F, m, Xl, k, 0);
-  trinv_diag32_kernel<T><<<gd, kNB, 0, st>>>(F, m, Xu, k, 1);
+  trinv_diag32_kernel<T><<<gd, kNB, 0, st>>>(F, m, Xl, ldx, sX, k, 0);
+  trinv_diag32_kernel<T><<<gd, kNB, 0, st>>>(F, m, Xu, ldx, sX, k, 1);
   for (int s = kNB; s < k && s < Bsz; s *= 2) {
     // pairs p: A at [2ps, 2ps+s), C at [2ps+s, min(2ps+2s, k)); the pairs with a
     // full-size C go in one batched launch (fronts x pairs), a ragged last pair in
-    // a second one.  W holds pair p's product at rows [2ps, 2ps+s) of the front's
-    // k x k work block.
+    // a second one.
     const int npairs = (k + 2 * s - 1) / (2 * s);
     const int last_c = k - ((npairs - 1) * 2 * s + s);
     const int nfull = (last_c >= s) ? npairs : npairs - 1;
-    const long ps_k = 2L * s * (1 + k), ps_m = 2L * s * (1 + m), ps_w = 2L * s;
+    const long ps_x = 2L * s * (1 + ldx), ps_m = 2L * s * (1 + m), ps_w = 2L * s;
     for (int pass = 0; pass < 2; ++pass) {
       int cnt, p0, sc;
       if (pass == 0) {
@@ -692,45 +875,65 @@ void invert_triangles(DevLevel& L, T* scratch, int Bsz, cudaStream_t st) {
       if (cnt <= 0) continue;
       const int a0 = p0 * 2 * s, c0 = a0 + s;
       // lower: W = B Ainv (B = L[c0.., a0..], Ainv lower), Xl[c0.., a0..] = -Cinv W
-      gemm_gen<T>(sc, s, s, (T)1, false, F + c0 + (long)a0 * m, m, mm, Xl + a0 + (long)a0 * k, k,
-                  kk, W + a0, k, kk, nf, 0, 1, st, cnt, ps_m, ps_k, ps_w);
-      gemm_gen<T>(sc, s, sc, (T)-1, false, Xl + c0 + (long)c0 * k, k, kk, W + a0, k, kk,
-                  Xl + c0 + (long)a0 * k, k, kk, nf, 1, 0, st, cnt, ps_k, ps_w, ps_k);
+      gemm_gen<T>(sc, s, s, (T)1, false, F + c0 + (long)a0 * m, m, mm, Xl + a0 + (long)a0 * ldx,
+                  ldx, sX, W + a0, k, sW, nf, 0, 1, st, cnt, ps_m, ps_x, ps_w);
+      gemm_gen<T>(sc, s, sc, (T)-1, false, Xl + c0 + (long)c0 * ldx, ldx, sX, W + a0, k, sW,
+                  Xl + c0 + (long)a0 * ldx, ldx, sX, nf, 1, 0, st, cnt, ps_x, ps_w, ps_x);
       // upper: W = Ainv B (B = U[a0.., c0..], Ainv upper), Xu[a0.., c0..] = -W Cinv
-      gemm_gen<T>(s, sc, s, (T)1, false, Xu + a0 + (long)a0 * k, k, kk, F + a0 + (long)c0 * m, m,
-                  mm, W + a0, k, kk, nf, 2, 0, st, cnt, ps_k, ps_m, ps_w);
-      gemm_gen<T>(s, sc, sc, (T)-1, false, W + a0, k, kk, Xu + c0 + (long)c0 * k, k, kk,
-                  Xu + a0 + (long)c0 * k, k, kk, nf, 0, 2, st, cnt, ps_w, ps_k, ps_k);
+      gemm_gen<T>(s, sc, s, (T)1, false, Xu + a0 + (long)a0 * ldx, ldx, sX, F + a0 + (long)c0 * m,
+                  m, mm, W + a0, k, sW, nf, 2, 0, st, cnt, ps_x, ps_m, ps_w);
+      gemm_gen<T>(s, sc, sc, (T)-1, false, W + a0, k, sW, Xu + c0 + (long)c0 * ldx, ldx, sX,
+                  Xu + a0 + (long)c0 * ldx, ldx, sX, nf, 0, 2, st, cnt, ps_w, ps_x, ps_x);
     }
   }
-  dim3 g((unsigned)((kk + 255) / 256), nf);
-  trinv_store_kernel<T><<<g, 256, 0, st>>>(F, m, Xl, Xu, k, Bsz);
+  const long nbk = (k + Bsz - 1) / Bsz;
+  dim3 g((unsigned)((nbk * Bsz * Bsz + 255) / 256), nf);
+  trinv_store_kernel<T><<<g, 256, 0, st>>>(F, m, Xl, Xu, sX, k, Bsz);
 }
 
 // Panel staging: one CTA when the 32-column panel fits in 160 KB of shared
-// memory, else a cluster of kCL CTAs (each holding m / kCL rows).  Returns the
-// panel width, 0 if neither fits.
+// memory, else a cluster of kCL CTAs (each holding m / kCL rows) when that fits,
+// else the cooperative grid panel working in global memory.
 template <class T>
 int panel_width(int m) {
-  if ((size_t)m * kNB * sizeof(T) <= 160 * 1024) return kNB;
-  if ((size_t)((m + kCL - 1) / kCL) * kNB * sizeof(T) + 2 * sizeof(int) * (size_t)m <= 160 * 1024)
-    return kNB;
-  return 0;
+  return m > 0 ? kNB : 0;
 }
 template <class T>
-bool panel_clustered(int m) {
-  return (size_t)m * kNB * sizeof(T) > 160 * 1024;
+int panel_kind(int m) {  // 0 one CTA, 1 cluster, 2 grid
+  if ((size_t)m * kNB * sizeof(T) <= 160 * 1024) return 0;
+  if ((size_t)((m + kCL - 1) / kCL) * kNB * sizeof(T) + 2 * sizeof(int) * (size_t)m <= 160 * 1024)
+    return 1;
+  return 2;
 }
 
 // Panel LU of columns [j0, j0+jb) followed by the interchanges and the row-block
 // solve on the columns [c_lo, c_hi) outside the panel.
 template <class T>
 void panel_step(DevLevel& L, T* F, int j0, int jb, int c_lo, int c_hi, double ptol, int* status,
-                cudaStream_t st) {
+                const FactorWork& W, cudaStream_t st) {
   double pf = 0;
   for (int j = j0; j < j0 + jb; ++j) pf += (double)(L.m - j - 1) * (1.0 + 2.0 * (j0 + jb - j - 1));
   ProfScope pp(PROF_LU_PANEL, st);
-  if (panel_clustered<T>(L.m)) {
+  const int kind = panel_kind<T>(L.m);
+  if (kind == 2) {
+    const int rows = L.m - j0;
+    const int G = grid_panel_ctas(L.nf, L.m);
+    cudaMemsetAsync(W.gbar, 0, sizeof(unsigned) * 2 * (size_t)L.nf, st);
+    const size_t sm = (size_t)((rows + G - 1) / G);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(L.nf * G));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, lu_panel_grid_kernel<T>, F, L.m, L.k, j0, jb, G, L.piv,
+                       (const double*)L.scale, ptol, status, (T*)W.gpanel, W.gkeys, W.gmaps,
+                       W.gbar);
+  } else if (kind == 1) {
     size_t sm = sizeof(T) * (size_t)((L.m - j0 + kCL - 1) / kCL) * jb +
                 2 * sizeof(int) * (size_t)(L.m - j0);
     lu_panel_cluster_kernel<T><<<L.nf * kCL, 256, sm, st>>>(F, L.m, L.k, j0, jb, L.piv, L.scale,
@@ -803,7 +1006,7 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
   int na = 1;
   if (L.nasm > 0) {
     dim3 g((L.nasm + 255) / 256, L.nf);
-    assemble_kernel<T><<<g, 256, 0, st>>>(F, L.m, L.nasm, L.asm_slot, L.asm_tidx, L.asm_cvar,
+    assemble_kernel<T><<<g, 256, 0, st>>>(F, L.m, L.nasm, L.asm_row, L.asm_tidx, L.asm_cvar,
                                           L.gidx, Qcat, Ccat, q);
     ++na;
   }
@@ -833,7 +1036,7 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
     // right-looking LU with a Schur update after every 32-column panel
     for (int j0 = 0; j0 < k; j0 += NB) {
       const int jb = std::min(NB, k - j0);
-      panel_step<T>(L, F, j0, jb, 0, m, ptol, status, st);
+      panel_step<T>(L, F, j0, jb, 0, m, ptol, status, W, st);
       const int base = j0 + jb, rem = m - base;
       schur_update<T>(L, F, rem, rem, jb, base + (long)j0 * m, j0 + (long)base * m,
                       base + (long)base * m, W, status, st);
@@ -848,7 +1051,7 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
       const int e1 = std::min(k, J0 + OB);
       for (int j0 = J0; j0 < e1; j0 += NB) {
         const int jb = std::min(NB, e1 - j0);
-        panel_step<T>(L, F, j0, jb, J0, e1, ptol, status, st);
+        panel_step<T>(L, F, j0, jb, J0, e1, ptol, status, W, st);
         const int base = j0 + jb;
         schur_update<T>(L, F, m - base, e1 - base, jb, base + (long)j0 * m, j0 + (long)base * m,
                         base + (long)base * m, W, status, st);
@@ -936,6 +1139,20 @@ int factor_outer_block(int prec, bool tc, int m, int k) {
   // enough to fill the GPU with 128 x 128 tiles
   if (prec == SP_PREC_FP32 && tc && m >= kTcMinFront && k > kNB) return kTcMaxK;
   return 0;
+}
+
+size_t invert_scratch_elems(int nf, int k) {
+  return (size_t)nf * ((size_t)2 * k * (kInvBlock + 1) + (size_t)k * (kInvBlock / 2));
+}
+
+int grid_panel_ctas(int nf, int m) {
+  // one resident CTA per SM for the whole level, at least 64 rows per CTA
+  const int per = std::max(1, kGridPanelCTAs / std::max(1, nf));
+  return std::max(1, std::min(per, (m + 63) / 64));
+}
+
+bool factor_grid_panel(int prec, int m) {
+  return prec == SP_PREC_FP32 ? panel_kind<float>(m) == 2 : panel_kind<double>(m) == 2;
 }
 
 int factor_panel_width(int prec, int m) {

@@ -622,7 +622,7 @@ int build_symbolic(int d, int n, int b, const std::vector<StencilTable>& tabs, S
             }
             int rp = pos[j], cp = pos[i];
             if (rp < 0 || cp < 0) return 3;  // structural error
-            V.asm_slot.push_back(rp + cp * V.m);
+            V.asm_row.push_back(rp);
             V.asm_tidx.push_back((int)(toff[t] + a + (long)c * tb.nS));
             V.asm_cvar.push_back(cp);
           }

@@ -26,7 +26,7 @@ struct Level {
   std::vector<int> gidx;      // nf x m global flat indices
   // assembly of the original entries of P whose earlier-eliminated endpoint is
   // eliminated in this front (same list for every front of the level)
-  std::vector<int> asm_slot;  // r + c*m (column-major front)
+  std::vector<int> asm_row;   // front row r of the entry (its column is asm_cvar)
   std::vector<int> asm_tidx;  // index into the concatenated column-major Q/C tables
   std::vector<int> asm_cvar;  // front position of the column point (for q)
   // extend-add: child position delta (0..2^d-1) -> map of the child's m_c - k_c

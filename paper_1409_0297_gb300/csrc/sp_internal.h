@@ -61,7 +61,7 @@ struct ProfScope {
 struct DevLevel {
   int nf = 0, k = 0, m = 0, nb1 = 0, mc = 0, kc = 0, nasm = 0;
   int* gidx = nullptr;      // nf x m
-  int* asm_slot = nullptr;  // nasm
+  int* asm_row = nullptr;   // nasm front rows (columns: asm_cvar)
   int* asm_tidx = nullptr;
   int* asm_cvar = nullptr;
   int* ea_map = nullptr;    // 2^d x (mc - kc)
@@ -95,10 +95,16 @@ cudaError_t to_float(const double* a, float* b, long N, cudaStream_t st);
 // ---------------------------------------------------------------- factor (sp_factor.cu)
 // Work buffers of the factorisation, shared by all levels.
 struct FactorWork {
-  void* inv = nullptr;        // 3 nf k^2 entries of the factor type when L.inv (triangular inverses)
+  void* inv = nullptr;        // invert_scratch_elems entries of the factor type (L.inv levels)
   float* packA = nullptr;     // tensor-core operand buffers (tc_pack_floats each)
   float* packB = nullptr;
   bool tc = false;            // Schur updates of the blocked fronts on the tensor cores
+  // grid panel (fronts too tall for a cluster): per front the panel copy
+  // (m x 32 of the factor type), 2 G pivot keys, 2 m position maps, a barrier pair
+  void* gpanel = nullptr;
+  unsigned long long* gkeys = nullptr;
+  int* gmaps = nullptr;
+  unsigned* gbar = nullptr;
 };
 // status bits: 1 = pivot below the threshold, 2 = a bounded device wait ran out
 cudaError_t factor_level(int prec, int d, DevLevel& L, const DevLevel* child, const double* Qcat,
@@ -106,6 +112,11 @@ cudaError_t factor_level(int prec, int d, DevLevel& L, const DevLevel* child, co
                          const FactorWork& W, cudaStream_t st);
 // panel width used for fronts of size m (0 if the staged panel cannot fit)
 int factor_panel_width(int prec, int m);
+// entries of the triangular-inverse scratch of a level with nf fronts of k eliminated
+size_t invert_scratch_elems(int nf, int k);
+// whether fronts of size m use the cooperative grid panel, and its CTAs per front
+bool factor_grid_panel(int prec, int m);
+int grid_panel_ctas(int nf, int m);
 // outer block width of the blocked LU of a front (0: the 32-column right-looking
 // LU with a Schur update after every panel)
 int factor_outer_block(int prec, bool tc, int m, int k);

@@ -20,7 +20,7 @@ namespace sp {
 namespace {
 
 constexpr int kBS = 32;
-constexpr int kRB = 16;  // rows per CTA of the GEMV sweeps
+constexpr size_t kVecSmem = 192 * 1024;  // largest vector staged in shared memory
 
 template <class VT> struct Scalar;
 template <> struct Scalar<double2> { using T = double; };
@@ -247,6 +247,58 @@ __global__ void __launch_bounds__(256) inv_gather_kernel(
   for (int j = k + threadIdx.x; j < m; j += blockDim.x) t[j] = b[j];
 }
 
+// The same for fronts whose right-hand side does not fit in shared memory: the
+// front's work vector tmp is assembled in place in global memory, the eliminated
+// part permuted through the forward-result buffer y (free at this point).
+template <class VT>
+__global__ void __launch_bounds__(1024) inv_gather_global_kernel(
+    int d, int m, int k, int nb1, const int* __restrict__ gidx, const int* __restrict__ perm,
+    const VT* __restrict__ rhsQ, const VT* __restrict__ cupd, int mc, int kc,
+    const int* __restrict__ ea_map, VT* tmp, VT* ybuf) {
+  const int f = blockIdx.x;
+  VT* t = tmp + (long)f * m;
+  for (int v = threadIdx.x; v < m; v += blockDim.x)
+    t[v] = (v < k) ? rhsQ[gidx[(long)f * m + v]] : vzero<VT>();
+  __syncthreads();
+  if (cupd) {
+    const int nbd = mc - kc;
+    for (int dl = 0; dl < (1 << d); ++dl) {
+      int ff = f, cid = 0, stride = 1;
+      for (int a = 0; a < d; ++a) {
+        int bc = ff % nb1;
+        ff /= nb1;
+        cid += (2 * bc + ((dl >> a) & 1)) * stride;
+        stride *= 2 * nb1;
+      }
+      const VT* cu = cupd + (long)cid * nbd;
+      const int* mp = ea_map + (long)dl * nbd;
+      for (int i = threadIdx.x; i < nbd; i += blockDim.x) {
+        VT v = cu[i];
+        VT& tt = t[mp[i]];
+        tt.x += v.x;
+        tt.y += v.y;
+      }
+      __syncthreads();
+    }
+  }
+  const int* pr = perm + (long)f * k;
+  VT* y = ybuf + (long)f * k;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) y[j] = t[pr[j]];
+  __syncthreads();
+  for (int j = threadIdx.x; j < k; j += blockDim.x) t[j] = y[j];
+}
+
+// tmp[c] = x[gidx[c]] for c in [k, m) of every front (the input of the backward
+// row-block product when it is read from global memory)
+template <class VT>
+__global__ void x_gather_kernel(int m, int k, const int* __restrict__ gidx,
+                                const double2* __restrict__ x, VT* tmp) {
+  const int c = k + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m) return;
+  const long f = blockIdx.y;
+  tmp[f * m + c] = from_d2<VT>(x[gidx[f * m + c]]);
+}
+
 // Row-block matrix-vector products of the levels whose diagonal blocks (size
 // kInvBlockSize) hold the inverses of those of L11 / U11.  16 rows per CTA, 16
 // column lanes per row, partial sums reduced in shared memory.  [j0, j1) is the
@@ -257,12 +309,14 @@ __global__ void __launch_bounds__(256) inv_gather_kernel(
 // mode 2 (backward, rows [0,k)):   tmp[r] = y[r] - sum_{k<=c<m} U12[r,c] x[c]
 // mode 6 (backward, rows [j0,j1)): tmp[r] -= sum_{j1<=c<k} U[r,c] y[c]
 // mode 3 (backward, rows [j0,j1)): y[r] = x[r] = sum_{r<=c<j1} Uinv[r,c] tmp[c]
-// (in the backward sweep y holds x1 once mode 2 has consumed y1)
+// (in the backward sweep y holds x1 once mode 2 has consumed y1).  vglobal: the
+// input vector is read from global memory instead of being staged (mode 2 then
+// reads tmp[k..m), gathered beforehand).
 template <class VT, class T, int RB>
 __global__ void __launch_bounds__(256) inv_gemv_kernel(int mode, const T* __restrict__ fronts,
                                                         int m, int k, int j0, int j1,
                                                         const int* __restrict__ gidx, VT* tmp,
-                                                        VT* y, VT* upd, double2* x) {
+                                                        VT* y, VT* upd, double2* x, int vglobal) {
   extern __shared__ unsigned char smraw[];
   VT* v = reinterpret_cast<VT*>(smraw);  // input vector entries [vlo, vhi)
   constexpr int CL = 256 / RB;  // column lanes per row
@@ -280,12 +334,17 @@ __global__ void __launch_bounds__(256) inv_gemv_kernel(int mode, const T* __rest
     case 6: rlo = j0; rhi = j1; vlo = j1; vhi = k; break;
     default: rlo = j0; rhi = j1; vlo = j0; vhi = j1; break;  // 3
   }
-  for (int c = vlo + threadIdx.x; c < vhi; c += blockDim.x) {
-    VT val;
-    if (mode == 0 || mode == 3) val = tf[c];
-    else if (mode == 2) val = from_d2<VT>(x[gidx[(long)f * m + c]]);
-    else val = yf[c];
-    v[c - vlo] = val;
+  const VT* vs = v;
+  if (vglobal) {
+    vs = (mode == 0 || mode == 3 || mode == 2) ? tf + vlo : yf + vlo;
+  } else {
+    for (int c = vlo + threadIdx.x; c < vhi; c += blockDim.x) {
+      VT val;
+      if (mode == 0 || mode == 3) val = tf[c];
+      else if (mode == 2) val = from_d2<VT>(x[gidx[(long)f * m + c]]);
+      else val = yf[c];
+      v[c - vlo] = val;
+    }
   }
   __syncthreads();
   const int tx = threadIdx.x % RB, ty = threadIdx.x / RB;
@@ -299,7 +358,7 @@ __global__ void __launch_bounds__(256) inv_gemv_kernel(int mode, const T* __rest
 #pragma unroll 4
     for (int c = cb + ty; c < ce; c += CL) {
       bool use = (mode == 0) ? (c < r) : (mode == 3) ? (c >= r) : true;
-      if (use) axpy(acc, A[r + (long)c * m], v[c - vlo]);
+      if (use) axpy(acc, A[r + (long)c * m], vs[c - vlo]);
     }
   }
   red[ty][tx] = acc;
@@ -374,14 +433,25 @@ template <class VT, class T>
 void inv_gemv(int mode, DevLevel& L, int j0, int j1, int rlo, int rhi, size_t smem, double2* x,
               cudaStream_t st) {
   const int rows = rhi - rlo;
+  int vglobal = 0;
+  if (smem > kVecSmem) {
+    vglobal = 1;
+    smem = 0;
+    if (mode == 2) {
+      dim3 gg((L.m - L.k + 255) / 256, L.nf);
+      x_gather_kernel<VT><<<gg, 256, 0, st>>>(L.m, L.k, L.gidx, x, (VT*)L.tmp);
+    }
+  }
   if ((long)((rows + 15) / 16) * L.nf >= 152) {
     dim3 g((rows + 15) / 16, L.nf);
     inv_gemv_kernel<VT, T, 16><<<g, 256, smem, st>>>(mode, (const T*)L.front, L.m, L.k, j0, j1,
-                                                     L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x);
+                                                     L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x,
+                                                     vglobal);
   } else {
     dim3 g((rows + 3) / 4, L.nf);
     inv_gemv_kernel<VT, T, 4><<<g, 256, smem, st>>>(mode, (const T*)L.front, L.m, L.k, j0, j1,
-                                                    L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x);
+                                                    L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x,
+                                                    vglobal);
   }
 }
 
@@ -402,8 +472,14 @@ cudaError_t forward_t(int d, DevLevel& L, const DevLevel* child, const void* rhs
         d, (const T*)L.front, L.m, L.k, L.nb1, L.gidx, L.perm, (const VT*)rhsQ, cup, L.mc, L.kc,
         L.ea_map, (VT*)L.upd, (VT*)L.y);
   } else {
-    inv_gather_kernel<VT><<<L.nf, 256, sizeof(VT) * L.m, st>>>(
-        d, L.m, L.k, L.nb1, L.gidx, L.perm, (const VT*)rhsQ, cup, L.mc, L.kc, L.ea_map, (VT*)L.tmp);
+    if (sizeof(VT) * (size_t)L.m <= kVecSmem)
+      inv_gather_kernel<VT><<<L.nf, 256, sizeof(VT) * L.m, st>>>(
+          d, L.m, L.k, L.nb1, L.gidx, L.perm, (const VT*)rhsQ, cup, L.mc, L.kc, L.ea_map,
+          (VT*)L.tmp);
+    else
+      inv_gather_global_kernel<VT><<<L.nf, 1024, 0, st>>>(d, L.m, L.k, L.nb1, L.gidx, L.perm,
+                                                           (const VT*)rhsQ, cup, L.mc, L.kc,
+                                                           L.ea_map, (VT*)L.tmp, (VT*)L.y);
     launches = 1;
     for (int j0 = 0; j0 < L.k; j0 += kInvBlockSize) {
       const int j1 = min(L.k, j0 + kInvBlockSize);

@@ -182,6 +182,37 @@ def test_solve_3d16_matches_oracle(B):
         S.close()
 
 
+@pytest.mark.parametrize("prec", [0, 1, 3], ids=["fp64", "fp32", "tf32"])
+def test_solve_3d32(B, prec):
+    """3D 32^3, b = 4 (root front m = 5768: the cooperative grid panel in FP64, the
+    cluster panel in FP32, outer blocks with tensor-core updates in TF32): the
+    preconditioner at 2000 sampled rows of P z - Q r (oracle, from the library's
+    tables) and the solution by the oracle's FFT residual."""
+    w = sm.helmholtz_grf_3d(32, 4, 0)
+    d, n, b = w["d"], w["n"], w["b"]
+    s, q, f = medium(w)
+    S = B.Solver(d, n, b, s, prec=prec)
+    S.factor(dev(q))
+    tabs = []
+    for t in range(1 << d):
+        Q, C, rank = S.table(t)
+        tabs.append(dict(S=O.canonical_set(d, b, t), gamma=O.canonical_gamma(d, b, t), Q=Q, C=C))
+    r = sm.random_complex_vector(n ** d, 41)
+    z = torch.empty(n ** d, dtype=torch.complex128, device="cuda")
+    S.apply(dev(r), z)
+    rows = np.random.default_rng(5).choice(n ** d, 2000, replace=False)
+    res = O.sampled_apply_residual(d, n, b, tabs, q, r, host(z), rows)
+    assert res <= {0: 1e-10, 1: 5e-3, 3: 5e-2}[prec], res
+    u = torch.empty(n ** d, dtype=torch.complex128, device="cuda")
+    info = S.solve(dev(f), u)
+    g = O.apply_green(d, n, s, f)
+    true = float(np.linalg.norm(g - O.apply_operator(d, n, s, q, host(u))) / np.linalg.norm(g))
+    assert true <= 1e-8, (true, info)
+    assert abs(info["true_relres"] - true) <= 1e-10
+    assert info["iters"] < 100
+    S.close()
+
+
 @pytest.mark.parametrize("which", ["helmholtz", "schrodinger"])
 @pytest.mark.parametrize("prec", [0, 1, 2, 3], ids=["fp64", "fp32", "mixed", "tf32"])
 def test_solve_512(B, which, prec):

@@ -73,10 +73,10 @@ def test_assembly_covers_pattern_of_P_once(d, n, b):
     for l in range(L + 1):
         V = B.sp_level_info(d, n, b, l)
         m = V["m"]
-        slots = V["asm_slot"]
+        r, c = V["asm_row"].astype(np.int64), V["asm_cvar"].astype(np.int64)
+        slots = r + c * m
         assert len(set(slots.tolist())) == len(slots)
-        r, c = slots % m, slots // m
-        assert np.array_equal(c, V["asm_cvar"])
+        assert np.all((r >= 0) & (r < m) & (c >= 0) & (c < m))
         # the earlier-eliminated endpoint is eliminated in this front
         assert np.all((r < V["k"]) | (c < V["k"]))
         for f in range(V["nf"]):
