@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libsp_gb300.so")
 
 SP_OK, SP_ERR_ARG, SP_ERR_RESONANT, SP_ERR_SINGULAR, SP_ERR_NOCONV = 0, 1, 2, 3, 4
 SP_ERR_OOM, SP_ERR_TIMEOUT, SP_ERR_CUDA, SP_ERR_STATE = 5, 6, 7, 8
-SP_PREC_FP64, SP_PREC_FP32, SP_PREC_MIXED, SP_PREC_TF32 = 0, 1, 2, 3
+SP_PREC_FP64, SP_PREC_FP32, SP_PREC_MIXED, SP_PREC_TF32, SP_PREC_TF32X3 = 0, 1, 2, 3, 4
 
 EXPORTED = [
     "sp_default_opts", "sp_setup", "sp_factor", "sp_apply", "sp_solve", "sp_factor_host",

@@ -90,6 +90,7 @@ struct sp_ctx {
   double* qbuf = nullptr;     // used by sp_factor_host
   int* status = nullptr;
   void* rhsQ = nullptr;       // N vector (VT) of Q r
+  void* gemv_part = nullptr;  // partial sums of the split row products of the sweeps
   // Krylov workspace
   int maxv = 0;
   double2 *V = nullptr, *Z = nullptr, *H = nullptr, *gam = nullptr, *sn = nullptr;
@@ -165,8 +166,10 @@ double perturb_shift(int d, int n, double s) {
 sp_status apply_direct(sp_ctx* c, const double2* r, double2* z, cudaStream_t st) {
   SP_CK(q_apply(c->prec, c->d, c->n, c->nl, c->qtypes, c->Tcat, c->Tcat32, r, c->rhsQ, st));
   for (int l = 0; l <= c->L; ++l)
-    SP_CK(forward_level(c->prec, c->d, c->lv[l], l ? &c->lv[l - 1] : nullptr, c->rhsQ, st));
-  for (int l = c->L; l >= 0; --l) SP_CK(backward_level(c->prec, c->d, c->lv[l], z, st));
+    SP_CK(forward_level(c->prec, c->d, c->lv[l], l ? &c->lv[l - 1] : nullptr, c->rhsQ,
+                        c->gemv_part, st));
+  for (int l = c->L; l >= 0; --l)
+    SP_CK(backward_level(c->prec, c->d, c->lv[l], z, c->gemv_part, st));
   return SP_OK;
 }
 
@@ -396,10 +399,11 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   if (check_grid(d, n, b, &L)) return SP_ERR_ARG;
   if (n & (n - 1)) return SP_ERR_ARG;  // the device FFT handles powers of two
   if (prec != SP_PREC_FP64 && prec != SP_PREC_FP32 && prec != SP_PREC_MIXED &&
-      prec != SP_PREC_TF32)
+      prec != SP_PREC_TF32 && prec != SP_PREC_TF32X3)
     return SP_ERR_ARG;
   const bool mixed = (prec == SP_PREC_MIXED);
-  const bool tc = (prec == SP_PREC_TF32);
+  const bool tc = (prec == SP_PREC_TF32 || prec == SP_PREC_TF32X3);
+  const bool split = (prec == SP_PREC_TF32X3);
   if (mixed || tc) prec = SP_PREC_FP32;
   if (!(std::isfinite(s))) return SP_ERR_ARG;
   if (shift_gap(d, n, s) < 1e-6) return SP_ERR_RESONANT;
@@ -418,6 +422,7 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   c->prec = prec;
   c->mixed = mixed;
   c->work.tc = tc;
+  c->work.tc_split = split;
   if (mixed && !(c->opts.inner_tol > 0 && c->opts.inner_tol < 1)) return SP_ERR_ARG;
   c->stream = (cudaStream_t)stream;
   c->N = 1;
@@ -488,7 +493,7 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   const size_t fsz = (prec == SP_PREC_FP32) ? sizeof(float) : sizeof(double);
   const size_t vsz = (prec == SP_PREC_FP32) ? sizeof(float2) : sizeof(double2);
   c->lv.resize(L + 1);
-  size_t scratch_bytes = 0, pack_floats = 0, gp_bytes = 0, gp_keys = 0, gp_maps = 0, gp_bar = 0;
+  size_t scratch_bytes = 0, pack_floats = 0, gp_words = 0;
   for (int l = 0; l <= L; ++l) {
     const Level& S = c->sym.lv[l];
     DevLevel& D = c->lv[l];
@@ -519,27 +524,17 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
       SP_CK(dalloc(c.get(), &D.tmp, vsz * (size_t)S.nf * S.m));
       scratch_bytes = std::max(scratch_bytes, fsz * invert_scratch_elems(S.nf, S.k));
     }
-    if (factor_grid_panel(prec, S.m)) {
-      const int G = grid_panel_ctas(S.nf, S.m);
-      gp_bytes = std::max(gp_bytes, fsz * (size_t)S.nf * S.m * 32);
-      gp_keys = std::max(gp_keys, (size_t)S.nf * 2 * G);
-      gp_maps = std::max(gp_maps, (size_t)S.nf * 2 * S.m);
-      gp_bar = std::max(gp_bar, (size_t)S.nf * 2);
-    }
+    if (factor_grid_panel(prec, S.m)) gp_words = std::max(gp_words, grid_panel_pub_words(S.nf));
     if (factor_outer_block(prec, tc, S.m, S.k) > 0)
-      pack_floats = std::max(pack_floats, tc_pack_floats(S.m, kTcMaxK, S.nf));
+      pack_floats = std::max(pack_floats, tc_pack_floats(S.m, kTcMaxK, S.nf, split));
     double k = S.k, mk = S.m - S.k;
     c->factor_entries += S.nf * (k * k + 2 * k * mk);
     c->factor_flops += S.nf * ((2.0 / 3.0) * k * k * k + 2 * k * k * mk + 2 * k * mk * mk);
   }
   c->apply_bytes = c->factor_entries * fsz;
   if (scratch_bytes) SP_CK(dalloc(c.get(), &c->work.inv, scratch_bytes));
-  if (gp_bytes) {
-    SP_CK(dalloc(c.get(), &c->work.gpanel, gp_bytes));
-    SP_CK(dalloc(c.get(), &c->work.gkeys, sizeof(unsigned long long) * gp_keys));
-    SP_CK(dalloc(c.get(), &c->work.gmaps, sizeof(int) * gp_maps));
-    SP_CK(dalloc(c.get(), &c->work.gbar, sizeof(unsigned) * gp_bar));
-  }
+  SP_CK(dalloc(c.get(), &c->gemv_part, sweep_partial_bytes()));
+  if (gp_words) SP_CK(dalloc(c.get(), &c->work.gpub, sizeof(unsigned long long) * gp_words));
   if (pack_floats) {
     SP_CK(dalloc(c.get(), &c->work.packA, sizeof(float) * pack_floats));
     SP_CK(dalloc(c.get(), &c->work.packB, sizeof(float) * pack_floats));
@@ -875,11 +870,14 @@ sp_status sp_solve_host(sp_ctx* c, const void* f_host, void* u_host, sp_info* in
 sp_status sp_schur_update(sp_precision prec, int M, int N, int K, const void* A, int lda,
                           long long sA, const void* B, int ldb, long long sB, void* C, int ldc,
                           long long sC, int batch, void* stream) {
-  if (prec != SP_PREC_FP64 && prec != SP_PREC_FP32 && prec != SP_PREC_TF32) return SP_ERR_ARG;
+  if (prec != SP_PREC_FP64 && prec != SP_PREC_FP32 && prec != SP_PREC_TF32 &&
+      prec != SP_PREC_TF32X3)
+    return SP_ERR_ARG;
   if (M < 0 || N < 0 || K < 0 || batch < 0 || !A || !B || !C) return SP_ERR_ARG;
   if (lda < std::max(1, M) || ldb < std::max(1, K) || ldc < std::max(1, M)) return SP_ERR_ARG;
   if (sA < 0 || sB < 0 || sC < 0 || batch > 65535) return SP_ERR_ARG;
-  const bool tc = prec == SP_PREC_TF32;
+  const bool tc = prec == SP_PREC_TF32 || prec == SP_PREC_TF32X3;
+  const bool split = prec == SP_PREC_TF32X3;
   if (tc && K > kTcMaxK) return SP_ERR_ARG;
   if ((long long)M * N * K * batch == 0) return SP_OK;
   cudaStream_t st = (cudaStream_t)stream;
@@ -888,14 +886,14 @@ sp_status sp_schur_update(sp_precision prec, int M, int N, int K, const void* A,
   sp_status rs = SP_OK;
   cudaError_t e = cudaSuccess;
   if (tc) {
-    e = cudaMalloc(&pa, sizeof(float) * tc_pack_floats(M, K, batch));
-    if (e == cudaSuccess) e = cudaMalloc(&pb, sizeof(float) * tc_pack_floats(N, K, batch));
+    e = cudaMalloc(&pa, sizeof(float) * tc_pack_floats(M, K, batch, split));
+    if (e == cudaSuccess) e = cudaMalloc(&pb, sizeof(float) * tc_pack_floats(N, K, batch, split));
     if (e == cudaSuccess) e = cudaMalloc(&status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), st);
   }
   if (e == cudaSuccess)
-    e = schur_update_raw(tc ? SP_PREC_FP32 : prec, tc, M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC,
-                         batch, pa, pb, status, st);
+    e = schur_update_raw(tc ? SP_PREC_FP32 : prec, tc, split, M, N, K, A, lda, sA, B, ldb, sB, C,
+                         ldc, sC, batch, pa, pb, status, st);
   int hs = 0;
   if (e == cudaSuccess && tc) e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

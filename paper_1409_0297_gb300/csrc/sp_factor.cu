@@ -28,6 +28,7 @@ constexpr int kTile = 64;     // Schur update tile (kTile x kTile per CTA)
 constexpr int kInvBlock = kInvBlockSize;  // diagonal-block size of the inverse-form levels
 constexpr int kTcMinFront = 1024;         // smallest front blocked for the tensor cores
 constexpr int kGridPanelCTAs = 152;       // CTAs of a grid-panel launch (one per SM)
+constexpr size_t kGridPanelSmem = 200 * 1024;  // staged rows of one grid-panel CTA
 
 template <class T>
 __global__ void assemble_kernel(T* fronts, int m, int nasm, const int* __restrict__ row,
@@ -280,103 +281,75 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(256)
 }
 
 // Panel LU of a front too tall for the cluster panel: G CTAs per front in one
-// cooperative launch (every CTA resident).  The panel rows [j0, m) are copied to
-// a work array W (rows x jb, column-major, in global memory and small enough to
-// stay in L2) and factored there; CTA g owns the rows ("slots") [g c, (g+1) c).
-// Rows never move during the panel.  A slot is a pivot candidate while its
-// starting position is below k (interchanges only exchange positions below k) and
-// it has not been a pivot yet.  Per pivot column every CTA publishes its best
-// candidate as a 64-bit key (FP32 magnitude high, complemented slot low; double
-// buffered), one barrier of the front's CTAs (counter and generation in global
-// memory, bounded spin), then every CTA reads the keys and the pivot row (final
-// from then on, read through L2) and updates its rows.  CTA 0 keeps the
-// position <-> slot maps and the pivot record; the panel is written back in
-// position order after a last barrier.  A barrier that does not complete within
-// about 2 s sets bit 2 of *status and the kernel returns without writing back.
+// cooperative launch (every CTA resident), the fronts of a level in groups of
+// nfl per launch.  CTA g stages the panel rows ("slots") [g c, (g+1) c) of rows
+// [j0, m) in shared memory; rows never move during the panel.  A slot is a pivot
+// candidate while its starting position is below k (interchanges only exchange
+// positions below k) and it has not been a pivot yet.  Per pivot column every
+// CTA publishes the row of its best candidate, then (release) one 64-bit word:
+// FP32 magnitude in bits 32-63, 2^20 - 1 - slot in bits 8-27, the column tag in
+// bits 0-7 (words of one column compare like their keys); each CTA polls the
+// words of its front's G CTAs (acquire, all in flight at once), takes the
+// largest and copies the winner's row: no other barrier.  The publication slots alternate between two
+// buffers by column parity (a CTA cannot publish column j+2 before every CTA has
+// published j+1, i.e. finished reading column j).  The pivot positions are
+// reconstructed after the panel from the sequence of pivot slots; each CTA then
+// writes its rows back in position order.  A poll that does not complete within
+// about 2 s sets bit 2 of *status and the CTA returns without writing back.
+constexpr int kPubWords = 1 + kNB;  // word, row (in units of 8 bytes; T <= 8 bytes)
 __device__ __forceinline__ unsigned long long gtimer_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
-// barrier of the G CTAs of one front; false if it timed out
-__device__ bool group_sync(unsigned* cnt, unsigned* gen, int G, unsigned* s_gen, int* s_abort) {
-  __syncthreads();
-  if (threadIdx.x == 0 && !*s_abort) {
-    const unsigned g0 = *s_gen;
-    __threadfence();
-    if (atomicAdd(cnt, 1u) == (unsigned)G - 1) {
-      atomicExch(cnt, 0u);
-      __threadfence();
-      atomicExch(gen, g0 + 1);
-    } else {
-      const unsigned long long t0 = gtimer_ns();
-      while (ld_acquire(gen) == g0) {
-        if (gtimer_ns() - t0 > 2000000000ull) {
-          *s_abort = 1;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    *s_gen = g0 + 1;
-  }
-  __syncthreads();
-  return !*s_abort;
+__device__ __forceinline__ void st_release64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 template <class T>
 __global__ void __launch_bounds__(256) lu_panel_grid_kernel(T* fronts, int m, int k, int j0, int jb,
-                                                            int G, int* piv, const double* scale,
-                                                            double ptol, int* status, T* W,
-                                                            unsigned long long* keys, int* maps,
-                                                            unsigned* bar) {
-  const int f = blockIdx.x / G, g = blockIdx.x % G;
+                                                            int f0, int G, int* piv,
+                                                            const double* scale, double ptol,
+                                                            int* status,
+                                                            unsigned long long* pub) {
+  const int f = f0 + blockIdx.x / G, g = blockIdx.x % G;
   T* A = fronts + (long)f * m * m;
   const int rows = m - j0, kl = k - j0;
   const int chunk = (rows + G - 1) / G;
-  const int s0 = min(rows, g * chunk), s1 = min(rows, s0 + chunk);
-  T* Wf = W + (long)f * rows * jb;
-  unsigned long long* kf = keys + (long)f * 2 * G;
-  int* s2p = maps + (long)f * 2 * rows;  // slot -> position
-  int* p2s = s2p + rows;                  // position -> slot
-  unsigned* cnt = bar + 2 * f;
-  unsigned* gen = cnt + 1;
-  extern __shared__ unsigned char smraw[];
-  unsigned char* elim = smraw;  // my slots already used as pivots
+  const int s0 = min(rows, g * chunk), s1 = min(rows, s0 + chunk), nmy = s1 - s0;
+  // publication slots of this front: [parity][g][kPubWords]
+  unsigned long long* pf = pub + (long)f * 2 * kGridPanelMaxG * kPubWords;
+  extern __shared__ unsigned long long smraw_u64[];
+  T* P = reinterpret_cast<T*>(smraw_u64);                      // chunk x jb, column-major
+  unsigned char* elim = reinterpret_cast<unsigned char*>(P + (long)chunk * jb);
   __shared__ T prow[kNB];
   __shared__ unsigned long long wkey[8];
-  __shared__ int s_sb, s_abort;
-  __shared__ unsigned s_gen;
-  __shared__ T s_pv;
+  __shared__ int pslot[kNB];
+  __shared__ int ds[2 * kNB], dp[2 * kNB];
+  __shared__ int s_nd, s_abort;
   const double thresh = ptol * scale[f];
-  for (long e = threadIdx.x; e < (long)(s1 - s0) * jb; e += blockDim.x) {
-    const int r = s0 + (int)(e % (s1 - s0)), c = (int)(e / (s1 - s0));
-    Wf[r + (long)c * rows] = A[(j0 + r) + (long)(j0 + c) * m];
+  for (long e = threadIdx.x; e < (long)nmy * jb; e += blockDim.x) {
+    const int r = (int)(e % nmy), c = (int)(e / nmy);
+    P[r + (long)c * chunk] = A[(j0 + s0 + r) + (long)(j0 + c) * m];
   }
-  for (int sl = s0 + threadIdx.x; sl < s1; sl += blockDim.x) {
-    s2p[sl] = sl;
-    p2s[sl] = sl;
-    elim[sl - s0] = 0;
-  }
-  if (threadIdx.x == 0) {
-    s_gen = ld_acquire(gen);
-    s_abort = 0;
-  }
+  for (int r = threadIdx.x; r < nmy; r += blockDim.x) elim[r] = 0;
+  if (threadIdx.x == 0) s_abort = 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __syncthreads();
   for (int jj = 0; jj < jb; ++jj) {
+    const unsigned long long tag = (unsigned long long)(jj + 1);
     unsigned long long key = 0ull;
-    for (int sl = s0 + threadIdx.x; sl < s1; sl += blockDim.x) {
-      if (sl >= kl || elim[sl - s0]) continue;
-      const float v = (float)fabs((double)Wf[sl + (long)jj * rows]);
+    for (int r = threadIdx.x; r < nmy; r += blockDim.x) {
+      const int sl = s0 + r;
+      if (sl >= kl || elim[r]) continue;
+      const float v = (float)fabs((double)P[r + (long)jj * chunk]);
       const unsigned long long kk = ((unsigned long long)__float_as_uint(v) << 32) |
-                                    (unsigned long long)(0xffffffffu - (unsigned)sl);
+                                    ((unsigned long long)(0xFFFFFu - (unsigned)sl) << 8);
       key = kk > key ? kk : key;
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -385,69 +358,136 @@ __global__ void __launch_bounds__(256) lu_panel_grid_kernel(T* fronts, int m, in
     }
     if (lane == 0) wkey[warp] = key;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned long long kb = wkey[0];
-      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) kb = wkey[w] > kb ? wkey[w] : kb;
-      __stcg(&kf[(jj & 1) * G + g], kb);
-    }
-    if (!group_sync(cnt, gen, G, &s_gen, &s_abort)) break;
+    unsigned long long* base = pf + (long)(jj & 1) * kGridPanelMaxG * kPubWords;
     if (warp == 0) {
-      unsigned long long kb = 0ull;
-      for (int l = lane; l < G; l += 32) {
-        const unsigned long long o = __ldcg(&kf[(jj & 1) * G + l]);
-        kb = o > kb ? o : kb;
-      }
-      for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long kb = wkey[lane & 7];
+      for (int o = 4; o > 0; o >>= 1) {
         unsigned long long ok = __shfl_down_sync(0xffffffffu, kb, o);
         kb = ok > kb ? ok : kb;
       }
       if (lane == 0) {
-        int sb = (int)(0xffffffffu - (unsigned)(kb & 0xffffffffull));
-        if (kb == 0ull || sb < 0 || sb >= rows) {  // no candidate: cannot happen for jj < kl
-          sb = 0;
-          atomicOr(status, 1);
+        unsigned long long* mine = base + (long)g * kPubWords;
+        if (kb) {
+          const int r = (int)(0xFFFFFu - (unsigned)((kb >> 8) & 0xFFFFFu)) - s0;
+          T* row = reinterpret_cast<T*>(mine + 1);
+          for (int c = 0; c < jb; ++c) row[c] = P[r + (long)c * chunk];
         }
-        s_sb = sb;
+        st_release64(mine, kb | tag);  // orders the row stores before the word
+      }
+      // the G words of this column, all loads in flight at once
+      constexpr int kPer = (kGridPanelMaxG + 31) / 32;
+      unsigned long long w[kPer];
+      bool rdy[kPer];
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        w[i] = 0ull;
+        rdy[i] = lane + 32 * i >= G;
+      }
+      const unsigned long long t0 = gtimer_ns();
+      bool ok = true;
+      while (true) {
+#pragma unroll
+        for (int i = 0; i < kPer; ++i)
+          if (!rdy[i]) w[i] = ld_acquire64(base + (long)(lane + 32 * i) * kPubWords);
+        bool mine_ok = true;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+          if (!rdy[i]) rdy[i] = (w[i] & 0xFFull) == tag;
+          mine_ok = mine_ok && rdy[i];
+        }
+        if (__all_sync(0xffffffffu, mine_ok)) break;
+        if (gtimer_ns() - t0 > 2000000000ull) {
+          ok = false;
+          break;
+        }
+      }
+      __syncwarp();  // the lanes' acquires order the row reads of every lane below
+      unsigned long long best = 0ull;
+#pragma unroll
+      for (int i = 0; i < kPer; ++i)
+        if (lane + 32 * i < G) best = w[i] > best ? w[i] : best;
+      for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long ob = __shfl_down_sync(0xffffffffu, best, o);
+        best = ob > best ? ob : best;
+      }
+      best = __shfl_sync(0xffffffffu, best, 0);
+      int sb = (int)(0xFFFFFu - (unsigned)((best >> 8) & 0xFFFFFu));
+      const bool valid = ok && (best >> 8) != 0ull && sb >= 0 && sb < rows;
+      if (!valid) {
+        if (lane == 0) {
+          s_abort = 1;
+          atomicOr(status, ok ? 1 : 2);
+        }
+        sb = 0;
+      } else {
+        const T* orow = reinterpret_cast<const T*>(base + (long)(sb / chunk) * kPubWords + 1);
+        if (lane < jb) prow[lane] = __ldcg(orow + lane);
+      }
+      if (lane == 0) {
+        pslot[jj] = sb;
+        if (sb >= s0 && sb < s1) elim[sb - s0] = 1;
       }
     }
     __syncthreads();
-    const int sb = s_sb;
-    if (threadIdx.x < jb - jj) {
-      const T v = __ldcg(&Wf[sb + (long)(jj + threadIdx.x) * rows]);
-      if (threadIdx.x == 0) s_pv = v;
-      else prow[threadIdx.x - 1] = v;
-    }
-    if (threadIdx.x == 0) {
-      if (sb >= s0 && sb < s1) elim[sb - s0] = 1;
-      if (g == 0) {
-        const int p = s2p[sb], sa = p2s[jj];
-        s2p[sb] = jj;
-        s2p[sa] = p;
-        p2s[jj] = sb;
-        p2s[p] = sa;
-        piv[(long)f * k + j0 + jj] = j0 + p;
-      }
-    }
-    __syncthreads();
-    T pv = s_pv;
+    if (s_abort) return;
+    T pv = prow[jj];
     if (g == 0 && threadIdx.x == 0 && !(fabs((double)pv) > thresh)) atomicOr(status, 1);
     if (!(fabs((double)pv) > 0.0)) pv = (T)(thresh > 0 ? thresh : 1e-30);
     const T inv = (T)1 / pv;
-    for (int sl = s0 + threadIdx.x; sl < s1; sl += blockDim.x) {
-      if (elim[sl - s0]) continue;
-      T* pr = Wf + sl;
-      const T l = pr[(long)jj * rows] * inv;
-      pr[(long)jj * rows] = l;
-      for (int c = jj + 1; c < jb; ++c) pr[(long)c * rows] -= l * prow[c - jj - 1];
+    for (int r = threadIdx.x; r < nmy; r += blockDim.x) {
+      if (elim[r]) continue;
+      T* pr = P + r;
+      const T l = pr[(long)jj * chunk] * inv;
+      pr[(long)jj * chunk] = l;
+      for (int c = jj + 1; c < jb; ++c) pr[(long)c * chunk] -= l * prow[c];
     }
   }
-  if (!group_sync(cnt, gen, G, &s_gen, &s_abort)) {
-    if (threadIdx.x == 0) atomicOr(status, 2);
-    return;
+  // positions: replay the interchanges (pivot slot pslot[jj] moves to position jj,
+  // the slot at jj moves to the pivot's position); displaced slots in ds/dp
+  if (threadIdx.x == 0) {
+    int nd = 0;
+    for (int jj = 0; jj < jb; ++jj) {
+      const int sb = pslot[jj];
+      int p = sb, ib = -1, sa = jj, ia = -1;
+      for (int i = 0; i < nd; ++i) {
+        if (ds[i] == sb) {
+          p = dp[i];
+          ib = i;
+        }
+      }
+      for (int i = 0; i < nd; ++i)
+        if (dp[i] == jj) {
+          sa = ds[i];
+          ia = i;
+        }
+      if (ia < 0)
+        for (int i = 0; i < nd; ++i)
+          if (ds[i] == sa) ia = i;
+      if (ib < 0) {
+        ib = nd++;
+        ds[ib] = sb;
+      }
+      dp[ib] = jj;
+      if (sa != sb) {
+        if (ia < 0) {
+          ia = nd++;
+          ds[ia] = sa;
+        }
+        dp[ia] = p;
+      }
+      if (g == 0) piv[(long)f * k + j0 + jj] = j0 + p;
+    }
+    s_nd = nd;
   }
-  for (long e = threadIdx.x; e < (long)(s1 - s0) * jb; e += blockDim.x) {
-    const int r = s0 + (int)(e % (s1 - s0)), c = (int)(e / (s1 - s0));
-    A[(j0 + __ldcg(&s2p[r])) + (long)(j0 + c) * m] = Wf[r + (long)c * rows];
+  __syncthreads();
+  const int nd = s_nd;
+  for (long e = threadIdx.x; e < (long)nmy * jb; e += blockDim.x) {
+    const int r = (int)(e % nmy), c = (int)(e / nmy);
+    const int sl = s0 + r;
+    int pos = sl;
+    for (int i = 0; i < nd; ++i)
+      if (ds[i] == sl) pos = dp[i];
+    A[(j0 + pos) + (long)(j0 + c) * m] = P[r + (long)c * chunk];
   }
 }
 
@@ -898,6 +938,16 @@ template <class T>
 int panel_width(int m) {
   return m > 0 ? kNB : 0;
 }
+// Fronts per launch (nfl) and CTAs per front (G) of the grid panel for `rows`
+// panel rows: every CTA's rows fit in kGridPanelSmem, nfl G <= kGridPanelCTAs.
+template <class T>
+void grid_panel_shape(int nf, int rows, int* nfl, int* G) {
+  const long cmax = (long)(kGridPanelSmem / (sizeof(T) * kNB + 1));
+  const int gmin = (int)std::max<long>(1, (rows + cmax - 1) / cmax);
+  *nfl = std::max(1, std::min(nf, kGridPanelCTAs / gmin));
+  *G = std::max(1, std::min(kGridPanelMaxG, std::min(kGridPanelCTAs / *nfl, (rows + 31) / 32)));
+}
+
 template <class T>
 int panel_kind(int m) {  // 0 one CTA, 1 cluster, 2 grid
   if ((size_t)m * kNB * sizeof(T) <= 160 * 1024) return 0;
@@ -917,22 +967,30 @@ void panel_step(DevLevel& L, T* F, int j0, int jb, int c_lo, int c_hi, double pt
   const int kind = panel_kind<T>(L.m);
   if (kind == 2) {
     const int rows = L.m - j0;
-    const int G = grid_panel_ctas(L.nf, L.m);
-    cudaMemsetAsync(W.gbar, 0, sizeof(unsigned) * 2 * (size_t)L.nf, st);
-    const size_t sm = (size_t)((rows + G - 1) / G);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(L.nf * G));
-    cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = sm;
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeCooperative;
-    at[0].val.cooperative = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, lu_panel_grid_kernel<T>, F, L.m, L.k, j0, jb, G, L.piv,
-                       (const double*)L.scale, ptol, status, (T*)W.gpanel, W.gkeys, W.gmaps,
-                       W.gbar);
+    if (rows >= (1 << 20)) return;  // slot field of the pivot word; factor_level_t rejects it
+    int nfl, G;
+    grid_panel_shape<T>(L.nf, rows, &nfl, &G);
+    const int chunk = (rows + G - 1) / G;
+    const size_t sm = sizeof(T) * (size_t)chunk * jb + (size_t)chunk;
+    for (int f0 = 0; f0 < L.nf; f0 += nfl) {
+      const int nfg = std::min(nfl, L.nf - f0);
+      // fresh publication tags for every launch (graph replays reuse the buffer)
+      cudaMemsetAsync(W.gpub + (size_t)f0 * 2 * kGridPanelMaxG * kPubWords, 0,
+                      sizeof(unsigned long long) * (size_t)nfg * 2 * kGridPanelMaxG * kPubWords,
+                      st);
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(nfg * G));
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = sm;
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeCooperative;
+      at[0].val.cooperative = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      cudaLaunchKernelEx(&cfg, lu_panel_grid_kernel<T>, F, L.m, L.k, j0, jb, f0, G, L.piv,
+                         (const double*)L.scale, ptol, status, W.gpub);
+    }
   } else if (kind == 1) {
     size_t sm = sizeof(T) * (size_t)((L.m - j0 + kCL - 1) / kCL) * jb +
                 2 * sizeof(int) * (size_t)(L.m - j0);
@@ -975,7 +1033,7 @@ void schur_update(DevLevel& L, T* F, int M, int N, int K, long offA, long offB, 
     if (W.tc) {
       ProfScope pc(PROF_LU_TC, st);
       tc_schur_update(M, N, K, (const float*)(F + offA), L.m, mm, (const float*)(F + offB), L.m, mm,
-                      (float*)(F + offC), L.m, mm, L.nf, W.packA, W.packB, status, st);
+                      (float*)(F + offC), L.m, mm, L.nf, W.packA, W.packB, W.tc_split, status, st);
       pc.done(fl, 3, st);
       return;
     }
@@ -995,6 +1053,8 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
     cudaFuncSetAttribute(lu_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(lu_panel_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
+    cudaFuncSetAttribute(lu_panel_grid_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kGridPanelSmem + 1024);
     attr = true;
   }
   const long mm = (long)L.m * L.m;
@@ -1029,7 +1089,7 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
   }
   pa.done(abytes, na + 1, st);
   const int NB = panel_width<T>(m);
-  if (NB == 0) return cudaErrorInvalidValue;
+  if (NB == 0 || m >= (1 << 20)) return cudaErrorInvalidValue;
   const int OB = factor_outer_block(sizeof(T) == sizeof(float) ? SP_PREC_FP32 : SP_PREC_FP64, W.tc,
                                     m, k);
   if (OB == 0) {
@@ -1109,13 +1169,14 @@ cudaError_t factor_level(int prec, int d, DevLevel& L, const DevLevel* child, co
   return factor_level_t<double>(d, L, child, Qcat, Ccat, q, pivot_tol, status, W, st);
 }
 
-cudaError_t schur_update_raw(int prec, bool tc, int M, int N, int K, const void* A, int lda, long sA,
-                             const void* B, int ldb, long sB, void* C, int ldc, long sC, int batch,
-                             float* packA, float* packB, int* status, cudaStream_t st) {
+cudaError_t schur_update_raw(int prec, bool tc, bool split, int M, int N, int K, const void* A,
+                             int lda, long sA, const void* B, int ldb, long sB, void* C, int ldc,
+                             long sC, int batch, float* packA, float* packB, int* status,
+                             cudaStream_t st) {
   if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return cudaSuccess;
   if (prec == SP_PREC_FP32 && tc)
     return tc_schur_update(M, N, K, (const float*)A, lda, sA, (const float*)B, ldb, sB, (float*)C,
-                           ldc, sC, batch, packA, packB, status, st);
+                           ldc, sC, batch, packA, packB, split, status, st);
   if (prec == SP_PREC_FP32) {
     if (K <= kNB)
       gemm_sub<float>(M, N, K, (const float*)A, lda, sA, (const float*)B, ldb, sB, (float*)C, ldc,
@@ -1145,11 +1206,7 @@ size_t invert_scratch_elems(int nf, int k) {
   return (size_t)nf * ((size_t)2 * k * (kInvBlock + 1) + (size_t)k * (kInvBlock / 2));
 }
 
-int grid_panel_ctas(int nf, int m) {
-  // one resident CTA per SM for the whole level, at least 64 rows per CTA
-  const int per = std::max(1, kGridPanelCTAs / std::max(1, nf));
-  return std::max(1, std::min(per, (m + 63) / 64));
-}
+size_t grid_panel_pub_words(int nf) { return (size_t)nf * 2 * kGridPanelMaxG * kPubWords; }
 
 bool factor_grid_panel(int prec, int m) {
   return prec == SP_PREC_FP32 ? panel_kind<float>(m) == 2 : panel_kind<double>(m) == 2;

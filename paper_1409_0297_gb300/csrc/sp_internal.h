@@ -99,13 +99,12 @@ struct FactorWork {
   float* packA = nullptr;     // tensor-core operand buffers (tc_pack_floats each)
   float* packB = nullptr;
   bool tc = false;            // Schur updates of the blocked fronts on the tensor cores
-  // grid panel (fronts too tall for a cluster): per front the panel copy
-  // (m x 32 of the factor type), 2 G pivot keys, 2 m position maps, a barrier pair
-  void* gpanel = nullptr;
-  unsigned long long* gkeys = nullptr;
-  int* gmaps = nullptr;
-  unsigned* gbar = nullptr;
+  bool tc_split = false;      // ... as 3xTF32 (hi/lo split, FP32 accuracy)
+  // grid panel (fronts too tall for a cluster): per front 2 x kGridPanelMaxG
+  // publication slots of grid_panel_pub_words() 8-byte words
+  unsigned long long* gpub = nullptr;
 };
+constexpr int kGridPanelMaxG = 152;
 // status bits: 1 = pivot below the threshold, 2 = a bounded device wait ran out
 cudaError_t factor_level(int prec, int d, DevLevel& L, const DevLevel* child, const double* Qcat,
                          const double* Ccat, const double* q, double pivot_tol, int* status,
@@ -114,28 +113,30 @@ cudaError_t factor_level(int prec, int d, DevLevel& L, const DevLevel* child, co
 int factor_panel_width(int prec, int m);
 // entries of the triangular-inverse scratch of a level with nf fronts of k eliminated
 size_t invert_scratch_elems(int nf, int k);
-// whether fronts of size m use the cooperative grid panel, and its CTAs per front
+// whether fronts of size m use the cooperative grid panel; 8-byte words of its
+// publication buffer for nf fronts
 bool factor_grid_panel(int prec, int m);
-int grid_panel_ctas(int nf, int m);
+size_t grid_panel_pub_words(int nf);
 // outer block width of the blocked LU of a front (0: the 32-column right-looking
 // LU with a Schur update after every panel)
 int factor_outer_block(int prec, bool tc, int m, int k);
 
 // C[M x N] -= A[M x K] B[K x N] with the kernel the factorisation uses for the
 // form (FP64 or FP32 SIMT; FP32 with tc: tensor cores, K <= kTcMaxK)
-cudaError_t schur_update_raw(int prec, bool tc, int M, int N, int K, const void* A, int lda, long sA,
-                             const void* B, int ldb, long sB, void* C, int ldc, long sC, int batch,
-                             float* packA, float* packB, int* status, cudaStream_t st);
+cudaError_t schur_update_raw(int prec, bool tc, bool split, int M, int N, int K, const void* A,
+                             int lda, long sA, const void* B, int ldb, long sB, void* C, int ldc,
+                             long sC, int batch, float* packA, float* packB, int* status,
+                             cudaStream_t st);
 
 // ---------------------------------------------------------------- tensor cores (sp_tc.cu)
 constexpr int kTcMaxK = 256;
 // floats of one packed operand buffer for `rows` rows, K columns, batch fronts
-size_t tc_pack_floats(int rows, int K, int batch);
+size_t tc_pack_floats(int rows, int K, int batch, bool split);
 // C[M x N] -= A[M x K] B[K x N] (column-major, batch strides sA, sB, sC) with
-// TF32 tensor-core products and FP32 accumulation; K <= kTcMaxK.
+// TF32 tensor-core products and FP32 accumulation (split: 3xTF32); K <= kTcMaxK.
 cudaError_t tc_schur_update(int M, int N, int K, const float* A, int lda, long sA, const float* B,
                             int ldb, long sB, float* C, int ldc, long sC, int batch, float* packA,
-                            float* packB, int* status, cudaStream_t st);
+                            float* packB, bool split, int* status, cudaStream_t st);
 
 // ---------------------------------------------------------------- solve (sp_solve.cu)
 struct QTypeDev {
@@ -151,9 +152,11 @@ struct QTypeDev {
 cudaError_t q_apply(int prec, int d, int n, int nl, const std::vector<QTypeDev>& types,
                     const double* Tcat, const float* Tcat32, const double2* r, void* y,
                     cudaStream_t st);
+// part: sweep_partial_bytes() of work for the split row products (shared by levels)
 cudaError_t forward_level(int prec, int d, DevLevel& L, const DevLevel* child, const void* rhsQ,
-                          cudaStream_t st);
-cudaError_t backward_level(int prec, int d, DevLevel& L, double2* x, cudaStream_t st);
+                          void* part, cudaStream_t st);
+cudaError_t backward_level(int prec, int d, DevLevel& L, double2* x, void* part, cudaStream_t st);
+size_t sweep_partial_bytes();
 
 // ---------------------------------------------------------------- Krylov (sp_krylov.cu)
 struct KrylovWork {

@@ -11,8 +11,12 @@
 // column-major front).
 // Levels with few fronts (the 512 x 512 diagonal blocks of L11, U11 replaced by
 // their inverses at factor time): the sweep is a short chain of matrix-vector
-// products, 16 rows per CTA, so the large upper fronts spread over the whole GPU.
+// products (the diagonal blocks 16 rows per CTA; the off-diagonal blocks one row
+// per thread with the columns split over CTAs), so the large upper fronts spread
+// over the whole GPU.
 // VT = double2 (FP64 form) or float2 (FP32 form).
+#include <algorithm>
+
 #include "sp_internal.h"
 
 namespace sp {
@@ -288,17 +292,6 @@ __global__ void __launch_bounds__(1024) inv_gather_global_kernel(
   for (int j = threadIdx.x; j < k; j += blockDim.x) t[j] = y[j];
 }
 
-// tmp[c] = x[gidx[c]] for c in [k, m) of every front (the input of the backward
-// row-block product when it is read from global memory)
-template <class VT>
-__global__ void x_gather_kernel(int m, int k, const int* __restrict__ gidx,
-                                const double2* __restrict__ x, VT* tmp) {
-  const int c = k + blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= m) return;
-  const long f = blockIdx.y;
-  tmp[f * m + c] = from_d2<VT>(x[gidx[f * m + c]]);
-}
-
 // Row-block matrix-vector products of the levels whose diagonal blocks (size
 // kInvBlockSize) hold the inverses of those of L11 / U11.  16 rows per CTA, 16
 // column lanes per row, partial sums reduced in shared memory.  [j0, j1) is the
@@ -309,14 +302,13 @@ __global__ void x_gather_kernel(int m, int k, const int* __restrict__ gidx,
 // mode 2 (backward, rows [0,k)):   tmp[r] = y[r] - sum_{k<=c<m} U12[r,c] x[c]
 // mode 6 (backward, rows [j0,j1)): tmp[r] -= sum_{j1<=c<k} U[r,c] y[c]
 // mode 3 (backward, rows [j0,j1)): y[r] = x[r] = sum_{r<=c<j1} Uinv[r,c] tmp[c]
-// (in the backward sweep y holds x1 once mode 2 has consumed y1).  vglobal: the
-// input vector is read from global memory instead of being staged (mode 2 then
-// reads tmp[k..m), gathered beforehand).
+// (in the backward sweep y holds x1 once mode 2 has consumed y1).  Modes 1, 2, 4
+// and 6 of large fronts go through gemv_rows_kernel below.
 template <class VT, class T, int RB>
 __global__ void __launch_bounds__(256) inv_gemv_kernel(int mode, const T* __restrict__ fronts,
                                                         int m, int k, int j0, int j1,
                                                         const int* __restrict__ gidx, VT* tmp,
-                                                        VT* y, VT* upd, double2* x, int vglobal) {
+                                                        VT* y, VT* upd, double2* x) {
   extern __shared__ unsigned char smraw[];
   VT* v = reinterpret_cast<VT*>(smraw);  // input vector entries [vlo, vhi)
   constexpr int CL = 256 / RB;  // column lanes per row
@@ -334,17 +326,12 @@ __global__ void __launch_bounds__(256) inv_gemv_kernel(int mode, const T* __rest
     case 6: rlo = j0; rhi = j1; vlo = j1; vhi = k; break;
     default: rlo = j0; rhi = j1; vlo = j0; vhi = j1; break;  // 3
   }
-  const VT* vs = v;
-  if (vglobal) {
-    vs = (mode == 0 || mode == 3 || mode == 2) ? tf + vlo : yf + vlo;
-  } else {
-    for (int c = vlo + threadIdx.x; c < vhi; c += blockDim.x) {
-      VT val;
-      if (mode == 0 || mode == 3) val = tf[c];
-      else if (mode == 2) val = from_d2<VT>(x[gidx[(long)f * m + c]]);
-      else val = yf[c];
-      v[c - vlo] = val;
-    }
+  for (int c = vlo + threadIdx.x; c < vhi; c += blockDim.x) {
+    VT val;
+    if (mode == 0 || mode == 3) val = tf[c];
+    else if (mode == 2) val = from_d2<VT>(x[gidx[(long)f * m + c]]);
+    else val = yf[c];
+    v[c - vlo] = val;
   }
   __syncthreads();
   const int tx = threadIdx.x % RB, ty = threadIdx.x / RB;
@@ -358,7 +345,7 @@ __global__ void __launch_bounds__(256) inv_gemv_kernel(int mode, const T* __rest
 #pragma unroll 4
     for (int c = cb + ty; c < ce; c += CL) {
       bool use = (mode == 0) ? (c < r) : (mode == 3) ? (c >= r) : true;
-      if (use) axpy(acc, A[r + (long)c * m], vs[c - vlo]);
+      if (use) axpy(acc, A[r + (long)c * m], v[c - vlo]);
     }
   }
   red[ty][tx] = acc;
@@ -398,6 +385,95 @@ __global__ void __launch_bounds__(256) inv_gemv_kernel(int mode, const T* __rest
   }
 }
 
+// Row-parallel products of modes 1, 2, 4 and 6 for fronts of any size: one thread
+// per row, 256 rows per CTA (a warp reads 128 contiguous bytes of a column of the
+// column-major front), the input vector staged in shared memory in chunks of
+// 1024 entries, the column range split over gridDim.y when the rows alone would
+// leave the GPU idle.  With one split the kernel applies the mode's update; with
+// several it writes partial sums part[(split nf + f) rows + (r - rlo)], which
+// gemv_finish_kernel adds in split order (the result does not depend on timing).
+template <class VT, class T>
+__device__ __forceinline__ void gemv_ranges(int mode, int m, int k, int j0, int j1, int& rlo,
+                                            int& rhi, int& vlo, int& vhi) {
+  switch (mode) {
+    case 4: rlo = j0; rhi = j1; vlo = 0; vhi = j0; break;
+    case 1: rlo = k; rhi = m; vlo = 0; vhi = k; break;
+    case 2: rlo = 0; rhi = k; vlo = k; vhi = m; break;
+    default: rlo = j0; rhi = j1; vlo = j1; vhi = k; break;  // 6
+  }
+}
+template <class VT>
+__device__ __forceinline__ void gemv_apply(int mode, int m, int k, int r, VT s, VT* tf, VT* yf,
+                                           VT* upd, int f) {
+  if (mode == 1) {
+    VT o = tf[r];
+    upd[(long)f * (m - k) + (r - k)] = VT{o.x - s.x, o.y - s.y};
+  } else if (mode == 2) {
+    VT o = yf[r];
+    tf[r] = VT{o.x - s.x, o.y - s.y};
+  } else {
+    VT o = tf[r];
+    tf[r] = VT{o.x - s.x, o.y - s.y};
+  }
+}
+template <class VT, class T>
+__global__ void __launch_bounds__(256) gemv_rows_kernel(int mode, const T* __restrict__ fronts,
+                                                         int m, int k, int j0, int j1,
+                                                         const int* __restrict__ gidx, VT* tmp,
+                                                         VT* y, VT* upd, const double2* x,
+                                                         int nsplit, VT* part) {
+  __shared__ VT vs[1024];
+  const int f = blockIdx.z, sp = blockIdx.y, nf = gridDim.z;
+  const T* A = fronts + (long)f * m * m;
+  VT* tf = tmp + (long)f * m;
+  VT* yf = y + (long)f * k;
+  int rlo, rhi, vlo, vhi;
+  gemv_ranges<VT, T>(mode, m, k, j0, j1, rlo, rhi, vlo, vhi);
+  const int r = rlo + blockIdx.x * 256 + threadIdx.x;
+  const int per = (vhi - vlo + nsplit - 1) / nsplit;
+  const int cb = vlo + sp * per, ce = min(vhi, cb + per);
+  VT acc = vzero<VT>();
+  for (int c0 = cb; c0 < ce; c0 += 1024) {
+    const int cn = min(1024, ce - c0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < cn; i += 256)
+      vs[i] = (mode == 2) ? from_d2<VT>(x[gidx[(long)f * m + c0 + i]]) : yf[c0 + i];
+    __syncthreads();
+    if (r < rhi) {
+      const T* Ar = A + r + (long)c0 * m;
+      int j = 0;
+      for (; j + 4 <= cn; j += 4) {
+        const T a0 = Ar[(long)j * m], a1 = Ar[(long)(j + 1) * m];
+        const T a2 = Ar[(long)(j + 2) * m], a3 = Ar[(long)(j + 3) * m];
+        axpy(acc, a0, vs[j]);
+        axpy(acc, a1, vs[j + 1]);
+        axpy(acc, a2, vs[j + 2]);
+        axpy(acc, a3, vs[j + 3]);
+      }
+      for (; j < cn; ++j) axpy(acc, Ar[(long)j * m], vs[j]);
+    }
+  }
+  if (r >= rhi) return;
+  if (nsplit == 1) gemv_apply(mode, m, k, r, acc, tf, yf, upd, f);
+  else part[((long)sp * nf + f) * (rhi - rlo) + (r - rlo)] = acc;
+}
+template <class VT, class T>
+__global__ void gemv_finish_kernel(int mode, int m, int k, int j0, int j1, VT* tmp, VT* y, VT* upd,
+                                   int nsplit, const VT* __restrict__ part) {
+  const int f = blockIdx.y, nf = gridDim.y;
+  int rlo, rhi, vlo, vhi;
+  gemv_ranges<VT, T>(mode, m, k, j0, j1, rlo, rhi, vlo, vhi);
+  const int r = rlo + blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rhi) return;
+  VT s = vzero<VT>();
+  for (int sp = 0; sp < nsplit; ++sp) {
+    const VT p = part[((long)sp * nf + f) * (rhi - rlo) + (r - rlo)];
+    s.x += p.x;
+    s.y += p.y;
+  }
+  gemv_apply(mode, m, k, r, s, tmp + (long)f * m, y + (long)f * k, upd, f);
+}
+
 template <class VT>
 cudaError_t q_apply_t(int d, int n, int nl, const std::vector<QTypeDev>& types, const void* Tt,
                       const double2* r, VT* y, cudaStream_t st) {
@@ -427,36 +503,52 @@ void set_attrs() {
   cudaFuncSetAttribute(inv_gemv_kernel<VT, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
+constexpr int kGemvTarget = 1216;  // CTAs a row-parallel product aims for (8 per SM)
+
+int gemv_splits(int rows, int cols, int nf) {
+  const long tiles = (long)((rows + 255) / 256) * nf;
+  if (tiles >= kGemvTarget || cols < 256) return 1;
+  return (int)std::max<long>(1, std::min<long>((kGemvTarget + tiles - 1) / tiles, cols / 128));
+}
+
+// Modes 1, 2, 4, 6 through gemv_rows_kernel (+ gemv_finish_kernel when split).
+template <class VT, class T>
+int gemv_rows(int mode, DevLevel& L, int j0, int j1, int rlo, int rhi, int vlo, int vhi,
+              const double2* x, void* part, cudaStream_t st) {
+  const int rows = rhi - rlo, cols = vhi - vlo;
+  if (rows <= 0) return 0;
+  int ns = gemv_splits(rows, cols, L.nf);
+  if (!part) ns = 1;
+  dim3 g((rows + 255) / 256, ns, L.nf);
+  gemv_rows_kernel<VT, T><<<g, 256, 0, st>>>(mode, (const T*)L.front, L.m, L.k, j0, j1, L.gidx,
+                                             (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x, ns, (VT*)part);
+  if (ns == 1) return 1;
+  dim3 gf((rows + 255) / 256, L.nf);
+  gemv_finish_kernel<VT, T><<<gf, 256, 0, st>>>(mode, L.m, L.k, j0, j1, (VT*)L.tmp, (VT*)L.y,
+                                                (VT*)L.upd, ns, (const VT*)part);
+  return 2;
+}
+
 // One inv_gemv launch over rows [rlo, rhi) of every front: 16 rows per CTA, or 4
 // rows per CTA (64 column lanes) when that leaves fewer CTAs than SMs.
 template <class VT, class T>
 void inv_gemv(int mode, DevLevel& L, int j0, int j1, int rlo, int rhi, size_t smem, double2* x,
               cudaStream_t st) {
   const int rows = rhi - rlo;
-  int vglobal = 0;
-  if (smem > kVecSmem) {
-    vglobal = 1;
-    smem = 0;
-    if (mode == 2) {
-      dim3 gg((L.m - L.k + 255) / 256, L.nf);
-      x_gather_kernel<VT><<<gg, 256, 0, st>>>(L.m, L.k, L.gidx, x, (VT*)L.tmp);
-    }
-  }
   if ((long)((rows + 15) / 16) * L.nf >= 152) {
     dim3 g((rows + 15) / 16, L.nf);
     inv_gemv_kernel<VT, T, 16><<<g, 256, smem, st>>>(mode, (const T*)L.front, L.m, L.k, j0, j1,
-                                                     L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x,
-                                                     vglobal);
+                                                     L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x);
   } else {
     dim3 g((rows + 3) / 4, L.nf);
     inv_gemv_kernel<VT, T, 4><<<g, 256, smem, st>>>(mode, (const T*)L.front, L.m, L.k, j0, j1,
-                                                    L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x,
-                                                    vglobal);
+                                                    L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x);
   }
 }
 
 template <class VT>
-cudaError_t forward_t(int d, DevLevel& L, const DevLevel* child, const void* rhsQ, cudaStream_t st) {
+cudaError_t forward_t(int d, DevLevel& L, const DevLevel* child, const void* rhsQ, void* part,
+                      cudaStream_t st) {
   using T = typename Scalar<VT>::T;
   static bool attr = false;
   if (!attr) {
@@ -483,24 +575,18 @@ cudaError_t forward_t(int d, DevLevel& L, const DevLevel* child, const void* rhs
     launches = 1;
     for (int j0 = 0; j0 < L.k; j0 += kInvBlockSize) {
       const int j1 = min(L.k, j0 + kInvBlockSize);
-      if (j0 > 0) {
-        inv_gemv<VT, T>(4, L, j0, j1, j0, j1, sizeof(VT) * j0, nullptr, st);
-        ++launches;
-      }
+      if (j0 > 0) launches += gemv_rows<VT, T>(4, L, j0, j1, j0, j1, 0, j0, nullptr, part, st);
       inv_gemv<VT, T>(0, L, j0, j1, j0, j1, sizeof(VT) * (j1 - j0), nullptr, st);
       ++launches;
     }
-    if (L.m > L.k) {
-      inv_gemv<VT, T>(1, L, 0, L.k, L.k, L.m, sizeof(VT) * L.k, nullptr, st);
-      ++launches;
-    }
+    if (L.m > L.k) launches += gemv_rows<VT, T>(1, L, 0, L.k, L.k, L.m, 0, L.k, nullptr, part, st);
   }
   ps.done(L.nf * sizeof(T) * (kk * (kk - 1) / 2 + mk * kk), launches, st);
   return cudaGetLastError();
 }
 
 template <class VT>
-cudaError_t backward_t(DevLevel& L, double2* x, cudaStream_t st) {
+cudaError_t backward_t(DevLevel& L, double2* x, void* part, cudaStream_t st) {
   using T = typename Scalar<VT>::T;
   const double kk = L.k, mk = L.m - L.k;
   ProfScope ps(PROF_BACKWARD, st);
@@ -511,8 +597,7 @@ cudaError_t backward_t(DevLevel& L, double2* x, cudaStream_t st) {
   } else {
     launches = 0;
     if (L.m > L.k) {
-      inv_gemv<VT, T>(2, L, 0, L.k, 0, L.k, sizeof(VT) * (L.m - L.k), x, st);
-      ++launches;
+      launches += gemv_rows<VT, T>(2, L, 0, L.k, 0, L.k, L.k, L.m, x, part, st);
     } else {
       // root: t = y1
       cudaMemcpy2DAsync(L.tmp, sizeof(VT) * L.m, L.y, sizeof(VT) * L.k, sizeof(VT) * L.k, L.nf,
@@ -521,10 +606,7 @@ cudaError_t backward_t(DevLevel& L, double2* x, cudaStream_t st) {
     const int nbk = (L.k + kInvBlockSize - 1) / kInvBlockSize;
     for (int bi = nbk - 1; bi >= 0; --bi) {
       const int j0 = bi * kInvBlockSize, j1 = min(L.k, j0 + kInvBlockSize);
-      if (j1 < L.k) {
-        inv_gemv<VT, T>(6, L, j0, j1, j0, j1, sizeof(VT) * (L.k - j1), x, st);
-        ++launches;
-      }
+      if (j1 < L.k) launches += gemv_rows<VT, T>(6, L, j0, j1, j0, j1, j1, L.k, x, part, st);
       inv_gemv<VT, T>(3, L, j0, j1, j0, j1, sizeof(VT) * (j1 - j0), x, st);
       ++launches;
     }
@@ -543,15 +625,17 @@ cudaError_t q_apply(int prec, int d, int n, int nl, const std::vector<QTypeDev>&
 }
 
 cudaError_t forward_level(int prec, int d, DevLevel& L, const DevLevel* child, const void* rhsQ,
-                          cudaStream_t st) {
-  if (prec == SP_PREC_FP32) return forward_t<float2>(d, L, child, rhsQ, st);
-  return forward_t<double2>(d, L, child, rhsQ, st);
+                          void* part, cudaStream_t st) {
+  if (prec == SP_PREC_FP32) return forward_t<float2>(d, L, child, rhsQ, part, st);
+  return forward_t<double2>(d, L, child, rhsQ, part, st);
 }
 
-cudaError_t backward_level(int prec, int d, DevLevel& L, double2* x, cudaStream_t st) {
+cudaError_t backward_level(int prec, int d, DevLevel& L, double2* x, void* part, cudaStream_t st) {
   (void)d;
-  if (prec == SP_PREC_FP32) return backward_t<float2>(L, x, st);
-  return backward_t<double2>(L, x, st);
+  if (prec == SP_PREC_FP32) return backward_t<float2>(L, x, part, st);
+  return backward_t<double2>(L, x, part, st);
 }
+
+size_t sweep_partial_bytes() { return (size_t)2 * kGemvTarget * 256 * sizeof(double2); }
 
 }  // namespace sp

@@ -6,7 +6,11 @@
 //
 // A = L21 and B = U12 are first copied into K-major operand buffers rounded to
 // TF32 (round to nearest), padded to a multiple of 32 in K with zeros: packA
-// [batch][M][Kp], packB [batch][N][Kp].  Those are read by TMA (3-D tensor maps,
+// [batch][M][Kp], packB [batch][N][Kp].  The split form (3xTF32) recovers FP32
+// accuracy: with a = a_hi + a_lo (a_hi = tf32(a), a_lo = tf32(a - a_hi)) the
+// operands are extended along K to [a_lo | a_hi | a_hi] and [b_hi | b_lo | b_hi],
+// so one product of depth 3 Kp sums a_lo b_hi + a_hi b_lo + a_hi b_hi (the
+// dropped a_lo b_lo and the rounding of the low parts are ~2^-22 |a||b|).  Those are read by TMA (3-D tensor maps,
 // 128-byte swizzle) into a ring of shared-memory stages; one thread issues
 // tcgen05.mma kind::tf32 (M = 128, N = BN, K = 8 per instruction) with the FP32
 // accumulator in tensor memory; all eight warps then read the accumulator with
@@ -142,6 +146,13 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_sub_kernel(
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int f = blockIdx.y;
   const int m0 = (blockIdx.x % tilesM) * kBM, n0 = (blockIdx.x / tilesM) * BN;
+  // epilogue mapping: warp w owns tile rows 32 (w % 4) .. +31 (its tensor-memory
+  // lanes) and the column half w / 4
+  const int qw = warp & 3, h = warp >> 2;
+  const int row = m0 + qw * 32 + lane;
+  constexpr int kHalf = BN / 2;
+  const int ncol = row < M ? min(kHalf, N - (n0 + h * kHalf)) : 0;  // valid columns of mine
+  float* cp = C + (long)f * sC + row + (long)(n0 + h * kHalf) * ldc;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -206,28 +217,18 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_sub_kernel(
   tc_fence_after();
   __syncthreads();
   const bool abort = !ok || s_abort != 0;
-  // epilogue: warp w reads lanes 32 (w % 4) .. +31 (tile rows) and half w / 4 of
-  // the columns, 32 columns per tensor-memory load
-  const int qw = warp & 3, h = warp >> 2;
-  const int row = m0 + qw * 32 + lane;
-  float* Cf = C + (long)f * sC;
+  // epilogue: 32 columns per tensor-memory load
   if (!abort) {
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN / 2; c0 += 32) {
-      const int colb = n0 + h * (BN / 2) + c0;
+    for (int c0 = 0; c0 < kHalf; c0 += 32) {
       float cv[32];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int col = colb + j;
-        cv[j] = (row < M && col < N) ? Cf[row + (long)col * ldc] : 0.f;
-      }
+      for (int j = 0; j < 32; ++j) cv[j] = c0 + j < ncol ? cp[(long)(c0 + j) * ldc] : 0.f;
       uint32_t v[32];
-      tmem_ld32(tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)(h * (BN / 2) + c0), v);
+      tmem_ld32(tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)(h * kHalf + c0), v);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int col = colb + j;
-        if (row < M && col < N) Cf[row + (long)col * ldc] = cv[j] - __uint_as_float(v[j]);
-      }
+      for (int j = 0; j < 32; ++j)
+        if (c0 + j < ncol) cp[(long)(c0 + j) * ldc] = cv[j] - __uint_as_float(v[j]);
     }
   } else if (threadIdx.x == 0) {
     atomicOr(status, 2);
@@ -245,10 +246,11 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_sub_kernel(
   }
 }
 
-// packA[f][i][kk] = tf32(A[f sA + i + kk lda]) for kk < K, 0 for K <= kk < Kp.
-// 32 x 32 tiles transposed through shared memory; block (32, 8).
+// packA[f][i][kk] = tf32(A[f sA + i + kk lda]) for kk < K, 0 for K <= kk < Kp
+// (row length Kp; split: row length 3 Kp holding lo, hi, hi).  32 x 32 tiles
+// transposed through shared memory; block (32, 8).
 __global__ void tc_pack_a_kernel(const float* __restrict__ A, int lda, long sA, int M, int K,
-                                 int Kp, float* __restrict__ P) {
+                                 int Kp, int split, float* __restrict__ P) {
   __shared__ float t[32][33];
   const long f = blockIdx.z;
   const int i0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
@@ -259,19 +261,38 @@ __global__ void tc_pack_a_kernel(const float* __restrict__ A, int lda, long sA, 
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += 8) {
     const int i = i0 + r, kk = k0 + threadIdx.x;
-    if (i < M) P[(f * M + i) * (long)Kp + kk] = to_tf32(t[threadIdx.x][r]);
+    if (i >= M) continue;
+    const float a = t[threadIdx.x][r], hi = to_tf32(a);
+    if (!split) {
+      P[(f * M + i) * (long)Kp + kk] = hi;
+    } else {
+      float* row = P + (f * M + i) * (long)(3 * Kp);
+      row[kk] = to_tf32(a - hi);
+      row[Kp + kk] = hi;
+      row[2 * Kp + kk] = hi;
+    }
   }
 }
 
-// packB[f][j][kk] = tf32(B[f sB + kk + j ldb]) for kk < K, 0 for K <= kk < Kp.
+// packB[f][j][kk] = tf32(B[f sB + kk + j ldb]) for kk < K, 0 for K <= kk < Kp
+// (split: row length 3 Kp holding hi, lo, hi).
 __global__ void tc_pack_b_kernel(const float* __restrict__ B, int ldb, long sB, int N, int K,
-                                 int Kp, float* __restrict__ P) {
+                                 int Kp, int split, float* __restrict__ P) {
   const long f = blockIdx.y;
   const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long)N * Kp) return;
   const int kk = (int)(e % Kp);
   const long j = e / Kp;
-  P[f * N * (long)Kp + e] = kk < K ? to_tf32(B[f * sB + kk + j * ldb]) : 0.f;
+  const float b = kk < K ? B[f * sB + kk + j * ldb] : 0.f;
+  const float hi = to_tf32(b);
+  if (!split) {
+    P[f * N * (long)Kp + e] = hi;
+  } else {
+    float* row = P + (f * N + j) * (long)(3 * Kp);
+    row[kk] = hi;
+    row[Kp + kk] = to_tf32(b - hi);
+    row[2 * Kp + kk] = hi;
+  }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -303,13 +324,13 @@ constexpr size_t kSmem = (size_t)kStages * (kBM * kBK * 4 + kBN * kBK * 4) + 102
 
 }  // namespace
 
-size_t tc_pack_floats(int rows, int K, int batch) {
-  return (size_t)batch * rows * (size_t)((K + kBK - 1) / kBK * kBK);
+size_t tc_pack_floats(int rows, int K, int batch, bool split) {
+  return (size_t)batch * rows * (size_t)((K + kBK - 1) / kBK * kBK) * (split ? 3 : 1);
 }
 
 cudaError_t tc_schur_update(int M, int N, int K, const float* A, int lda, long sA, const float* B,
                             int ldb, long sB, float* C, int ldc, long sC, int batch, float* packA,
-                            float* packB, int* status, cudaStream_t st) {
+                            float* packB, bool split, int* status, cudaStream_t st) {
   if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return cudaSuccess;
   if (K > kTcMaxK || batch > 65535 || !packA || !packB) return cudaErrorInvalidValue;
   static bool attr = false;
@@ -320,21 +341,22 @@ cudaError_t tc_schur_update(int M, int N, int K, const float* A, int lda, long s
     attr = true;
   }
   const int Kp = (K + kBK - 1) / kBK * kBK;
+  const int Ke = split ? 3 * Kp : Kp;  // depth of the packed product
   {
     dim3 g((M + 31) / 32, Kp / 32, batch);
-    tc_pack_a_kernel<<<g, dim3(32, 8), 0, st>>>(A, lda, sA, M, K, Kp, packA);
+    tc_pack_a_kernel<<<g, dim3(32, 8), 0, st>>>(A, lda, sA, M, K, Kp, split ? 1 : 0, packA);
     const long nb = (long)N * Kp;
     dim3 gb((unsigned)((nb + 255) / 256), batch);
-    tc_pack_b_kernel<<<gb, 256, 0, st>>>(B, ldb, sB, N, K, Kp, packB);
+    tc_pack_b_kernel<<<gb, 256, 0, st>>>(B, ldb, sB, N, K, Kp, split ? 1 : 0, packB);
   }
   CUtensorMap ta, tb;
-  cudaError_t e = encode_operand(&ta, packA, M, Kp, batch, kBM);
+  cudaError_t e = encode_operand(&ta, packA, M, Ke, batch, kBM);
   if (e != cudaSuccess) return e;
-  e = encode_operand(&tb, packB, N, Kp, batch, kBN);
+  e = encode_operand(&tb, packB, N, Ke, batch, kBN);
   if (e != cudaSuccess) return e;
   const int tilesM = (M + kBM - 1) / kBM, tilesN = (N + kBN - 1) / kBN;
   dim3 g((unsigned)((long)tilesM * tilesN), batch);
-  tc_gemm_sub_kernel<kBN, kStages><<<g, kThreads, kSmem, st>>>(ta, tb, M, N, Kp / kBK, C, ldc, sC,
+  tc_gemm_sub_kernel<kBN, kStages><<<g, kThreads, kSmem, st>>>(ta, tb, M, N, Ke / kBK, C, ldc, sC,
                                                               tilesM, status);
   return cudaGetLastError();
 }

@@ -8,8 +8,10 @@ inputs; for the tensor-core form the inputs are first rounded to TF32 (10-bit
 mantissa, round to nearest with ties away from zero, the rounding the operand
 packing applies), so what remains is the FP32 accumulation error, bounded
 elementwise by (K + 2) * 2^-24 * (|A| |B|) + 2^-24 |C| (Higham, Thm 3.5 with FP32
-unit roundoff).  A wrong descriptor, swizzle or tile offset breaks this bound by
-orders of magnitude.
+unit roundoff).  The split form (3xTF32) is compared with the unrounded FP32
+inputs: its extra error is the dropped lo*lo product and the rounding of the low
+parts, 4 * 2^-22 |A||B| at most.  A wrong descriptor, swizzle or tile offset
+breaks these bounds by orders of magnitude.
 """
 import numpy as np
 import pytest
@@ -49,7 +51,7 @@ SHAPES = [
 
 
 @pytest.mark.parametrize("M,N,K,batch", SHAPES)
-@pytest.mark.parametrize("prec", [0, 1, 3], ids=["fp64", "fp32", "tf32"])
+@pytest.mark.parametrize("prec", [0, 1, 3, 4], ids=["fp64", "fp32", "tf32", "tf32x3"])
 def test_schur_update(B, M, N, K, batch, prec):
     dtype = np.float64 if prec == 0 else np.float32
     lda, ldb, ldc = M + 3, K + 5, M + 7
@@ -70,6 +72,10 @@ def test_schur_update(B, M, N, K, batch, prec):
         got = out[f, :, :M].T.astype(np.float64)
         u = 2.0 ** -53 if prec == 0 else 2.0 ** -24
         bound = (K + 2) * u * (np.abs(a) @ np.abs(b)) + u * np.abs(c) + 1e-300
+        if prec == 4:
+            # 3xTF32: the dropped lo*lo term and the TF32 rounding of the low parts
+            # add at most 2^-22 |a||b| each per product (|a_lo| <= 2^-11 |a|)
+            bound = bound + 4 * 2.0 ** -22 * (np.abs(a) @ np.abs(b))
         assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) / bound))
         # rows beyond M and the padding of C are untouched
         assert np.array_equal(out[f, :, M:], C[f, :, M:])
@@ -88,6 +94,21 @@ def test_tf32_rounding_is_applied(B):
                       M, N * M, 1)
     torch.cuda.synchronize()
     assert np.all(tC.cpu().numpy() == -float(K))
+
+
+def test_split_recovers_fp32_accuracy(B):
+    """With A = 1 + 2^-20 and B = 1 the split form keeps the low part: the update
+    is K (1 + 2^-20) to FP32 rounding, where plain TF32 gives exactly K."""
+    M, N, K = 128, 128, 64
+    A = np.full((1, K, M), 1 + 2.0 ** -20, dtype=np.float32)
+    Bm = np.ones((1, N, K), dtype=np.float32)
+    C = np.zeros((1, N, M), dtype=np.float32)
+    tA, tB, tC = (torch.from_numpy(x).cuda() for x in (A, Bm, C))
+    B.sp_schur_update(4, M, N, K, tA.data_ptr(), M, K * M, tB.data_ptr(), K, N * K, tC.data_ptr(),
+                      M, N * M, 1)
+    torch.cuda.synchronize()
+    # K (1 + 2^-20) = 64 + 2^-14; plain TF32 would give 64 (2^-14 away)
+    assert np.all(np.abs(tC.cpu().numpy().astype(np.float64) + K * (1 + 2.0 ** -20)) < 2.0 ** -16)
 
 
 def test_schur_update_arguments(B):
