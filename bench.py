@@ -8,9 +8,14 @@ Workload (one "step"): the 2D 512^2 problem pair, complex128 unknowns, b = 16,
 each with a random-centre, random-phase Gaussian source; for each problem the
 step factors P = Q + C q (sp_factor) and solves to a true relative residual of
 1e-8 (sp_solve).  One step = 2 solves.  The stencil set-up (sp_setup, once per
-shift s) is outside the timed region.  `value` is the plain FP64 form; the FP32
-preconditioner form (FP32 factor and sweeps, FP64 operator, Gram-Schmidt and
-residuals) is reported beside it under "chosen_form".
+shift s) is outside the timed region.  `value` is the plain FP64 form; the
+reduced-precision preconditioner forms (FP32 factor and sweeps, with or without
+TF32 / 3xTF32 tensor-core Schur updates, GMRES-IR; FP64 operator, Gram-Schmidt
+and residuals throughout) are reported beside it, the fastest as "chosen_form".
+
+"workload_3d": the 3D 128^3 Helmholtz problem (omega = 2 pi 16, c = 1 + 0.3
+tanh(GRF, correlation length 0.08), b = 8; one step = factor + solve of one
+problem) in the tensor-core forms, with the roofline of the tcgen05 Schur update.
 
 Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on
 the library's stream, with an L2 flush (a 256 MB write) between steps outside
@@ -37,6 +42,7 @@ import numpy as np  # noqa: E402
 import synthetic_media as sm  # noqa: E402
 
 METRIC = "solves/s at rel. residual 1e-8 (2D 512^2), plain FP64 GPU"
+WORKLOAD_3D = "3D 128^3 Helmholtz GRF omega=2pi*16 (corr. length 0.08), b=8"
 UNIT = "solves/s"
 WORKLOAD = "2D 512^2 pair: Helmholtz GRF omega=2pi*64 + Schroedinger wells l=16 E=10, b=16"
 
@@ -54,6 +60,10 @@ def parse():
                         "given form after set-up and exit: the command profiled under ncu")
     p.add_argument("--problems", default="helmholtz,schrodinger",
                    help="comma list of the step's problems (default both)")
+    p.add_argument("--no-3d", action="store_true", help="skip the 3D 128^3 workload")
+    p.add_argument("--forms-3d", default="tf32",
+                   help="comma list of the tensor-core forms timed at 3D 128^3 (tf32, tf32x3)")
+    p.add_argument("--steps-3d", type=int, default=1)
     return p.parse_args()
 
 
@@ -169,6 +179,69 @@ def cpu_baseline() -> dict:
                       f"(b=8, omega=2pi*16, 8 points/wavelength like 512^2), {res['iters']} "
                       f"iterations, {dt:.1f} s; the 512^2 oracle factor does not fit the budget",
             "seconds": dt}
+
+
+# ------------------------------------------------------------------ 3D 128^3
+def measure_3d(args, B, torch, flush, peaks, dist, world):
+    """The 3D 128^3 Helmholtz workload (one step = sp_factor + sp_solve of one
+    problem) in the tensor-core forms: W = args.warmup untimed steps, then
+    args.steps_3d timed steps with CUDA events and an L2 flush in between."""
+    w = sm.helmholtz_grf_3d(128, 8, 0)
+    d, n, b = 3, 128, 8
+    s, q = B.sp_medium_helmholtz(d, n, w["omega"], w["c"])
+    qd = torch.from_numpy(q).cuda()
+    fd = torch.from_numpy(np.ascontiguousarray(w["f"])).cuda()
+    u = torch.empty(n ** d, dtype=torch.complex128, device="cuda")
+    tf32_peak = peaks.get("bf16_tflops", 1911.1) * (1.1 / 2.25)
+    out = {}
+    for name in args.forms_3d.split(","):
+        prec = {"tf32": B.SP_PREC_TF32, "tf32x3": B.SP_PREC_TF32X3}[name]
+        t0 = time.perf_counter()
+        S = B.Solver(d, n, b, s, prec=prec, device=int(os.environ.get("LOCAL_RANK", "0")))
+        setup_s = time.perf_counter() - t0
+        for _ in range(args.warmup):
+            S.factor(qd)
+            S.solve(fd, u)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ms, infos = 0.0, []
+        for _ in range(args.steps_3d):
+            flush.zero_()
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            S.factor(qd)
+            infos.append(S.solve(fd, u))
+            e.record()
+            torch.cuda.synchronize()
+            ms += a.elapsed_time(e)
+        ms = reduce_max(ms / args.steps_3d, dist)
+        B.sp_profile(S.ctx, True)
+        S.factor(qd)
+        S.solve(fd, u)
+        prof = B.sp_profile_read(S.ctx)
+        B.sp_profile(S.ctx, False)
+        tc_ms, tc_n, tc_fl = prof["lu_tc"]
+        ach = tc_fl / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else 0.0
+        out[name] = {
+            "value": replica_value(1, world, ms), "ms_per_step": ms, "setup_s": setup_s,
+            "iters": infos[0]["iters"], "true_relres": infos[0]["true_relres"],
+            "roofline": {"kernel": "lu_tc (tcgen05 TF32 Schur update)", "bound": "tensor",
+                         "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s",
+                         "frac": ach / tf32_peak, "traffic": None,
+                         "peak_source": "measured bf16_tflops x nominal TF32/BF16 ratio 1.1/2.25"},
+            "kernel_breakdown_ms_per_step": {k: {"ms": round(v[0], 2), "launches": v[1]}
+                                             for k, v in prof.items() if v[1]},
+        }
+        S.close()
+        torch.cuda.synchronize()
+    best = max(out, key=lambda k: out[k]["value"])
+    return {"workload": WORKLOAD_3D, "grid": "128^3", "b": 8, "solves_per_step": 1,
+            "warmup": args.warmup, "steps": args.steps_3d,
+            "l2": "flushed between steps (256 MB write)", "data": "synthetic",
+            "plain_fp64": "not run: the FP64 fronts alone take 237 GB and the FP64 factor "
+                          "~8e14 flop at 1.25 TFLOP/s",
+            "chosen": dict(out[best], name=best), "forms": out}
 
 
 # ------------------------------------------------------------------ our arm
@@ -338,6 +411,8 @@ def run_ours(args):
                 ("tf32", B.SP_PREC_TF32, "FP32 factor and sweeps, Schur updates of fronts m >= 1024 "
                                          "on tcgen05 tensor cores (TF32 x TF32 -> FP32); FP64 "
                                          "operator, Gram-Schmidt, residuals"),
+                ("tf32x3", B.SP_PREC_TF32X3, "as tf32 with 3xTF32 split operands (FP32-accurate "
+                                             "updates)"),
                 ("mixed", B.SP_PREC_MIXED, "GMRES-IR: FP32 factor and sweeps, complex64 inner FGMRES "
                                            "(FFT, Gram-Schmidt) to 1e-5, FP64 refinement residuals")):
             ctxs = make(prec)
@@ -353,6 +428,14 @@ def run_ours(args):
                 c["S"].close()
         best = max(forms, key=lambda k: forms[k]["value"])
         chosen = dict(forms[best], name=best)
+
+    for c in fp64:
+        c["S"].close()
+    fp64 = []
+    torch.cuda.synchronize()
+    w3d = None
+    if not args.no_3d:
+        w3d = measure_3d(args, B, torch, flush, peaks, dist, world)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -377,11 +460,9 @@ def run_ours(args):
             "roofline": roofline, "kernel_breakdown_ms_per_step": breakdown,
             "chosen_form": chosen, "forms": {k: {kk: v[kk] for kk in ("value", "ms_per_step", "iters")}
                                              for k, v in forms.items()},
-            "clocks": clocks, "cpu_baseline": cpu,
+            "clocks": clocks, "cpu_baseline": cpu, "workload_3d": w3d,
         }
         print(json.dumps(line), flush=True)
-    for c in fp64:
-        c["S"].close()
     if dist:
         dist.destroy_process_group()
 

@@ -57,9 +57,10 @@ typedef enum {
                         inner_tol; the outer FP64 refinement forms u += d and the
                         true residual r = g - A u with the FP64 operator */
   SP_PREC_TF32 = 3,  /* as SP_PREC_FP32, and fronts with m >= 1024 are factored in
-                        outer blocks of 256 columns whose Schur updates
-                        S -= L21 U12 run on the tensor cores (TF32 products,
-                        FP32 accumulation; Section 2.3's update S = F22 - L21 U12) */
+                        outer blocks of 512 columns (sub-blocks of 256) whose
+                        Schur updates S -= L21 U12 run on the tensor cores (TF32
+                        products, FP32 accumulation; Section 2.3's update
+                        S = F22 - L21 U12) */
   SP_PREC_TF32X3 = 4 /* as SP_PREC_TF32 with each operand split into a TF32 high
                         part and a TF32 low part and the three products
                         hi*hi + hi*lo + lo*hi summed on the tensor cores
@@ -211,7 +212,7 @@ sp_status sp_profile_read(sp_ctx *ctx, int cap, double *ms, int *launches, doubl
  * batch strides sA, sB, sC in elements), with the kernel the factorisation uses
  * for the form: SP_PREC_FP64 doubles, SP_PREC_FP32 floats (SIMT FMA units),
  * SP_PREC_TF32 floats with TF32 products on the tensor cores and FP32
- * accumulation, SP_PREC_TF32X3 the same with split operands (K <= 256 for both;
+ * accumulation, SP_PREC_TF32X3 the same with split operands (K <= 512 for both;
  * the call allocates and frees its operand buffers).
  * A, B, C: device pointers owned by the caller; C must not overlap A or B.
  * Synchronous on `stream` (cudaStream_t or NULL).  SP_ERR_ARG for bad sizes or

@@ -545,15 +545,16 @@ __global__ void __launch_bounds__(256) lu_trsm_kernel(T* fronts, int m, int k, i
     if (i < jb) col[i] = x[i];
 }
 
-// Row interchanges piv[p0 .. p0+cnt) (in order) on the columns [0, a1) and
-// [b0, m) of every front; one thread per column.
+// Row interchanges piv[p0 .. p0+cnt) (in order) on the columns [a0, a1) and
+// [b0, b1) of every front; one thread per column.
 template <class T>
-__global__ void lu_laswp_kernel(T* fronts, int m, int k, int p0, int cnt, const int* piv, int a1,
-                                int b0) {
+__global__ void lu_laswp_kernel(T* fronts, int m, int k, int p0, int cnt, const int* piv, int a0,
+                                int a1, int b0, int b1) {
   T* A = fronts + (long)blockIdx.y * m * m;
   const int cc = blockIdx.x * blockDim.x + threadIdx.x;
-  const int c = cc < a1 ? cc : b0 + (cc - a1);
-  if (c >= m) return;
+  const int na = a1 - a0;
+  const int c = cc < na ? a0 + cc : b0 + (cc - na);
+  if (c >= (cc < na ? a1 : b1)) return;
   const int* pv = piv + (long)blockIdx.y * k;
   T* col = A + (long)c * m;
   for (int j = p0; j < p0 + cnt; ++j) {
@@ -1102,42 +1103,70 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
                       base + (long)base * m, W, status, st);
     }
   } else {
-    // blocked LU with outer blocks of OB columns: the outer panel [J0, e) is
-    // factored by 32-column steps whose interchanges, row-block solves and
-    // updates stay inside it; then its interchanges go to the other columns, the
-    // row band U12 = L11^{-1} A12 is solved in 32-row steps, and the trailing
-    // matrix gets one update of depth OB.
-    for (int J0 = 0; J0 < k; J0 += OB) {
-      const int e1 = std::min(k, J0 + OB);
-      for (int j0 = J0; j0 < e1; j0 += NB) {
-        const int jb = std::min(NB, e1 - j0);
-        panel_step<T>(L, F, j0, jb, J0, e1, ptol, status, W, st);
-        const int base = j0 + jb;
-        schur_update<T>(L, F, m - base, e1 - base, jb, base + (long)j0 * m, j0 + (long)base * m,
-                        base + (long)base * m, W, status, st);
-      }
-      const int ncols = J0 + (m - e1);
-      if (ncols > 0) {
-        ProfScope pt(PROF_LU_TRSM, st);
-        dim3 g((ncols + 255) / 256, L.nf);
-        lu_laswp_kernel<T><<<g, 256, 0, st>>>(F, m, k, J0, e1 - J0, L.piv, J0, e1);
-        pt.done(0, 1, st);
-      }
-      if (e1 < m) {
-        for (int j0 = J0; j0 < e1; j0 += NB) {
-          const int jb = std::min(NB, e1 - j0);
+    // Two-level blocked LU.  An outer block [J0, e1) of OB columns is factored in
+    // sub-blocks [J1, e2) of IB columns; a sub-block is factored by 32-column
+    // panel steps whose interchanges, row-block solves and updates stay inside it,
+    // then its interchanges go to the rest of the outer block, its row band
+    // [J1, e2) x [e2, e1) is solved and the outer block's remaining columns get
+    // one update of depth IB.  After the outer block its interchanges go to the
+    // other columns, the row band U12 = L11^{-1} A12 is solved in the same
+    // sub-block pattern, and the trailing matrix gets one update of depth OB.
+    // The updates of depth > 32 run on the tensor cores in the tensor-core forms.
+    const int IB = std::min(OB, kTcMaxK / 2);
+    auto laswp = [&](int p0, int cnt, int a0, int a1, int b0, int b1) {
+      const int ncols = std::max(0, a1 - a0) + std::max(0, b1 - b0);
+      if (ncols <= 0 || cnt <= 0) return;
+      ProfScope pt(PROF_LU_TRSM, st);
+      dim3 g((ncols + 255) / 256, L.nf);
+      lu_laswp_kernel<T><<<g, 256, 0, st>>>(F, m, k, p0, cnt, L.piv, a0, std::max(a0, a1), b0,
+                                            std::max(b0, b1));
+      pt.done(0, 1, st);
+    };
+    // row band [r0, r1) x [c0, m') solved with the unit lower block at [r0, r1),
+    // sub-blocks of IB rows, 32-row steps inside a sub-block
+    auto band = [&](int r0, int r1, int c0, int c1) {
+      if (c1 <= c0) return;
+      for (int B0 = r0; B0 < r1; B0 += IB) {
+        const int B1 = std::min(r1, B0 + IB);
+        for (int j0 = B0; j0 < B1; j0 += NB) {
+          const int jb = std::min(NB, B1 - j0);
           {
-            const int ncol = m - e1;
+            const int ncol = c1 - c0;
             const int tb = ((long)((ncol + 255) / 256) * L.nf >= 152) ? 256 : 64;
             dim3 gt((ncol + tb - 1) / tb, L.nf);
             ProfScope pt(PROF_LU_TRSM, st);
-            lu_trsm_kernel<T><<<gt, tb, 0, st>>>(F, m, k, j0, jb, L.piv, e1, m, 0);
+            lu_trsm_kernel<T><<<gt, tb, 0, st>>>(F, m, k, j0, jb, L.piv, c0, c1, 0);
             pt.done((double)ncol * jb * (jb - 1) * L.nf, 1, st);
           }
           const int base = j0 + jb;
-          schur_update<T>(L, F, e1 - base, m - e1, jb, base + (long)j0 * m, j0 + (long)e1 * m,
-                          base + (long)e1 * m, W, status, st);
+          schur_update<T>(L, F, B1 - base, c1 - c0, jb, base + (long)j0 * m, j0 + (long)c0 * m,
+                          base + (long)c0 * m, W, status, st);
         }
+        schur_update<T>(L, F, r1 - B1, c1 - c0, B1 - B0, B1 + (long)B0 * m, B0 + (long)c0 * m,
+                        B1 + (long)c0 * m, W, status, st);
+      }
+    };
+    for (int J0 = 0; J0 < k; J0 += OB) {
+      const int e1 = std::min(k, J0 + OB);
+      for (int J1 = J0; J1 < e1; J1 += IB) {
+        const int e2 = std::min(e1, J1 + IB);
+        for (int j0 = J1; j0 < e2; j0 += NB) {
+          const int jb = std::min(NB, e2 - j0);
+          panel_step<T>(L, F, j0, jb, J1, e2, ptol, status, W, st);
+          const int base = j0 + jb;
+          schur_update<T>(L, F, m - base, e2 - base, jb, base + (long)j0 * m, j0 + (long)base * m,
+                          base + (long)base * m, W, status, st);
+        }
+        laswp(J1, e2 - J1, J0, J1, e2, e1);
+        if (e2 < e1) {
+          band(J1, e2, e2, e1);
+          schur_update<T>(L, F, m - e2, e1 - e2, e2 - J1, e2 + (long)J1 * m, J1 + (long)e2 * m,
+                          e2 + (long)e2 * m, W, status, st);
+        }
+      }
+      laswp(J0, e1 - J0, 0, J0, e1, m);
+      if (e1 < m) {
+        band(J0, e1, e1, m);
         schur_update<T>(L, F, m - e1, m - e1, e1 - J0, e1 + (long)J0 * m, J0 + (long)e1 * m,
                         e1 + (long)e1 * m, W, status, st);
       }

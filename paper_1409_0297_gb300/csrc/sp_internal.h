@@ -129,7 +129,7 @@ cudaError_t schur_update_raw(int prec, bool tc, bool split, int M, int N, int K,
                              cudaStream_t st);
 
 // ---------------------------------------------------------------- tensor cores (sp_tc.cu)
-constexpr int kTcMaxK = 256;
+constexpr int kTcMaxK = 512;
 // floats of one packed operand buffer for `rows` rows, K columns, batch fronts
 size_t tc_pack_floats(int rows, int K, int batch, bool split);
 // C[M x N] -= A[M x K] B[K x N] (column-major, batch strides sA, sB, sC) with

@@ -442,13 +442,12 @@ __global__ void __launch_bounds__(256) gemv_rows_kernel(int mode, const T* __res
     if (r < rhi) {
       const T* Ar = A + r + (long)c0 * m;
       int j = 0;
-      for (; j + 4 <= cn; j += 4) {
-        const T a0 = Ar[(long)j * m], a1 = Ar[(long)(j + 1) * m];
-        const T a2 = Ar[(long)(j + 2) * m], a3 = Ar[(long)(j + 3) * m];
-        axpy(acc, a0, vs[j]);
-        axpy(acc, a1, vs[j + 1]);
-        axpy(acc, a2, vs[j + 2]);
-        axpy(acc, a3, vs[j + 3]);
+      for (; j + 8 <= cn; j += 8) {
+        T a[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = Ar[(long)(j + u) * m];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) axpy(acc, a[u], vs[j + u]);
       }
       for (; j < cn; ++j) axpy(acc, Ar[(long)j * m], vs[j]);
     }

@@ -13,9 +13,11 @@
 // dropped a_lo b_lo and the rounding of the low parts are ~2^-22 |a||b|).  Those are read by TMA (3-D tensor maps,
 // 128-byte swizzle) into a ring of shared-memory stages; one thread issues
 // tcgen05.mma kind::tf32 (M = 128, N = BN, K = 8 per instruction) with the FP32
-// accumulator in tensor memory; all eight warps then read the accumulator with
-// tcgen05.ld and subtract it from C in global memory (the front keeps its
-// column-major layout with leading dimension m, which needs no alignment).
+// accumulators in tensor memory (two, so one tile's epilogue overlaps the next
+// tile's products); eight epilogue warps read an accumulator with tcgen05.ld and
+// subtract it from C in global memory (the front keeps its column-major layout
+// with leading dimension m, which needs no alignment).  Persistent: one CTA per
+// SM walks the tiles of all fronts.
 //
 // Every wait on an mbarrier is bounded (about 2 s of global timer); a wait that
 // runs out sets bit 2 of *status, the CTA drains the copies it issued, frees its
@@ -24,6 +26,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "sp_internal.h"
@@ -35,7 +38,6 @@ namespace {
 constexpr int kBM = 128;       // tile rows = tensor-memory lanes
 constexpr int kBK = 32;        // K per stage: 32 FP32 = one 128-byte swizzle row
 constexpr int kUK = 8;         // K of one kind::tf32 instruction
-constexpr int kThreads = 256;  // 8 warps
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -126,49 +128,90 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(u);
 }
 
-// C -= A B for one BM x BN tile of one front (blockIdx.y); nk stages of K = 32.
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// bounded wait that also gives up once another role has aborted
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, volatile int* ab) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try(bar, parity)) {
+    if (*ab) return false;
+    if (gtimer() - t0 > kWaitNs) {
+      *ab = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+constexpr int kEpiWarps = 8;                  // warps 0-7: epilogue (2 per TMEM lane quarter)
+constexpr int kPThreads = 32 * (kEpiWarps + 2);  // + warp 8 (TMA producer), warp 9 (MMA issuer)
+constexpr int kGroupM = 8;                    // row tiles per group of the tile order
+
+// tile t -> front f and tile origin (m0, n0): fronts outermost, then groups of
+// kGroupM row tiles whose column tiles are visited in turn (the group's A rows and
+// the current B columns stay in L2)
+__device__ __forceinline__ void tile_coords(long t, int tilesM, int tilesN, int BN, int* f,
+                                            int* m0, int* n0) {
+  const long per = (long)tilesM * tilesN;
+  *f = (int)(t / per);
+  const long tl = t % per;
+  const long gs = (long)kGroupM * tilesN;
+  const int g = (int)(tl / gs);
+  const int r = (int)(tl % gs);
+  const int gm = min(kGroupM, tilesM - g * kGroupM);
+  *m0 = (g * kGroupM + r % gm) * kBM;
+  *n0 = (r / gm) * BN;
+}
+
+// Persistent C -= A B over all tiles of all fronts: one CTA per SM, a ring of
+// STAGES shared-memory stages filled by TMA (warp 8), tcgen05.mma issued by one
+// thread of warp 9 into one of two tensor-memory accumulators, and the epilogue
+// (warps 0-7) draining the other accumulator: warp w reads TMEM lanes 32 (w % 4)
+// .. +31 (tile rows) and column half w / 4, subtracts from C with the C loads of
+// the next chunk (also of the next tile) already in flight.
 template <int BN, int STAGES>
-__global__ void __launch_bounds__(kThreads, 2) tc_gemm_sub_kernel(
+__global__ void __launch_bounds__(kPThreads, 1) tc_gemm_sub_kernel(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M,
-    int N, int nk, float* C, int ldc, long sC, int tilesM, int* status) {
+    int N, int nk, float* C, int ldc, long sC, int tilesM, int tilesN, long ntiles, int* status) {
   constexpr uint32_t kABytes = kBM * kBK * 4;
   constexpr uint32_t kBBytes = BN * kBK * 4;
   constexpr uint32_t kStage = kABytes + kBBytes;
+  constexpr int kHalf = BN / 2;
   // instruction descriptor: D = F32 (bits 4-5), A = B = TF32 (bits 7-9, 10-12),
   // both K-major, N >> 3 at bit 17, M >> 4 at bit 24
   constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
                               ((uint32_t)(kBM >> 4) << 24);
   extern __shared__ unsigned char smraw[];
-  __shared__ __align__(8) unsigned long long full[STAGES], empty[STAGES], done;
+  __shared__ __align__(8) unsigned long long full[STAGES], empty[STAGES], acc_full[2],
+      acc_empty[2], drain;
   __shared__ uint32_t tmem_slot;
-  __shared__ int s_abort, s_issued, s_consumed;
+  __shared__ int s_abort;
+  __shared__ long long s_issued, s_consumed;
+  volatile int* ab = &s_abort;
   const uint32_t base = (smem_u32(smraw) + 1023u) & ~1023u;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int f = blockIdx.y;
-  const int m0 = (blockIdx.x % tilesM) * kBM, n0 = (blockIdx.x / tilesM) * BN;
-  // epilogue mapping: warp w owns tile rows 32 (w % 4) .. +31 (its tensor-memory
-  // lanes) and the column half w / 4
-  const int qw = warp & 3, h = warp >> 2;
-  const int row = m0 + qw * 32 + lane;
-  constexpr int kHalf = BN / 2;
-  const int ncol = row < M ? min(kHalf, N - (n0 + h * kHalf)) : 0;  // valid columns of mine
-  float* cp = C + (long)f * sC + row + (long)(n0 + h * kHalf) * ldc;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
       mbar_init(smem_u32(&empty[s]), 1);
     }
-    mbar_init(smem_u32(&done), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&acc_full[b]), 1);
+      mbar_init(smem_u32(&acc_empty[b]), kEpiWarps);
+    }
+    mbar_init(smem_u32(&drain), 1);
     s_abort = 0;
     s_issued = 0;
     s_consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 2) {
+  if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_slot)),
-                 "r"((uint32_t)BN)
+                 "r"((uint32_t)(2 * BN))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -177,71 +220,125 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_sub_kernel(
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
-  if (warp == 0 && lane == 0) {
-    // producer: TMA loads of the A and B stages
-    int kb = 0;
-    for (; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      if (kb >= STAGES && !mbar_wait(smem_u32(&empty[s]), ((kb / STAGES) - 1) & 1)) {
-        atomicOr(&s_abort, 1);
-        break;
+  if (warp == kEpiWarps) {
+    if (lane == 0) {  // TMA producer
+      long long g = 0;
+      for (long t = blockIdx.x; t < ntiles && !*ab; t += gridDim.x) {
+        int f, m0, n0;
+        tile_coords(t, tilesM, tilesN, BN, &f, &m0, &n0);
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = (int)(g % STAGES);
+          if (g >= STAGES &&
+              !mbar_wait_ab(smem_u32(&empty[s]), (uint32_t)(((g / STAGES) & 1) ^ 1), ab))
+            break;
+          const uint32_t fb = smem_u32(&full[s]);
+          mbar_expect_tx(fb, kStage);
+          tma_load_3d(base + s * kStage, &tmA, kb * kBK, m0, f, fb);
+          tma_load_3d(base + s * kStage + kABytes, &tmB, kb * kBK, n0, f, fb);
+        }
+        if (*ab) break;
       }
-      const uint32_t fb = smem_u32(&full[s]);
-      mbar_expect_tx(fb, kStage);
-      tma_load_3d(base + s * kStage, &tmA, kb * kBK, m0, f, fb);
-      tma_load_3d(base + s * kStage + kABytes, &tmB, kb * kBK, n0, f, fb);
+      s_issued = g;
     }
-    s_issued = kb;
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    int kb = 0;
-    for (; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      if (!mbar_wait(smem_u32(&full[s]), (kb / STAGES) & 1)) {
-        atomicOr(&s_abort, 1);
-        break;
+  } else if (warp == kEpiWarps + 1) {
+    if (lane == 0) {  // MMA issuer
+      long long g = 0;
+      long i = 0;
+      for (long t = blockIdx.x; t < ntiles && !*ab; t += gridDim.x, ++i) {
+        const int buf = (int)(i & 1);
+        const long u = i >> 1;
+        if (u >= 1 && !mbar_wait_ab(smem_u32(&acc_empty[buf]), (uint32_t)((u - 1) & 1), ab)) break;
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(buf * BN);
+        bool okk = true;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = (int)(g % STAGES);
+          if (!mbar_wait_ab(smem_u32(&full[s]), (uint32_t)((g / STAGES) & 1), ab)) {
+            okk = false;
+            break;
+          }
+          tc_fence_after();
+          const unsigned long long ad = sw128_desc(base + s * kStage);
+          const unsigned long long bd = sw128_desc(base + s * kStage + kABytes);
+#pragma unroll
+          for (int kk = 0; kk < kBK / kUK; ++kk)  // +32 bytes along K = +2 in the address field
+            mma_tf32(d, ad + 2 * kk, bd + 2 * kk, kIdesc, (kb | kk) != 0 ? 1u : 0u);
+          mma_commit(smem_u32(&empty[s]));
+        }
+        if (!okk) break;
+        mma_commit(smem_u32(&acc_full[buf]));
       }
+      s_consumed = g;
+      mma_commit(smem_u32(&drain));  // every MMA issued above has completed
+      if (!mbar_wait(smem_u32(&drain), 0)) *ab = 1;
+    }
+  } else {
+    // epilogue
+    const int qw = warp & 3, h = warp >> 2;
+    float c0[32], c1[32];
+    long t = blockIdx.x;
+    int f, m0, n0;
+    int row = 0, ncol = 0;
+    float* cp = C;
+    auto locate = [&](long tt) {
+      tile_coords(tt, tilesM, tilesN, BN, &f, &m0, &n0);
+      row = m0 + qw * 32 + lane;
+      ncol = row < M ? min(kHalf, N - (n0 + h * kHalf)) : 0;
+      cp = C + (long)f * sC + row + (long)(n0 + h * kHalf) * ldc;
+    };
+    if (t < ntiles) {
+      locate(t);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) c0[j] = j < ncol ? cp[(long)j * ldc] : 0.f;
+    }
+    for (long i = 0; t < ntiles; t += gridDim.x, ++i) {
+      const int buf = (int)(i & 1);
+      const long u = i >> 1;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) c1[j] = 32 + j < ncol ? cp[(long)(32 + j) * ldc] : 0.f;
+      // one lane waits, the warp follows (tcgen05.ld below is warp-collective)
+      int okw = 0;
+      if (lane == 0) okw = mbar_wait_ab(smem_u32(&acc_full[buf]), (uint32_t)(u & 1), ab) ? 1 : 0;
+      __syncwarp();
+      okw = __shfl_sync(0xffffffffu, okw, 0);
+      if (!okw) break;
       tc_fence_after();
-      const unsigned long long ad = sw128_desc(base + s * kStage);
-      const unsigned long long bd = sw128_desc(base + s * kStage + kABytes);
-#pragma unroll
-      for (int kk = 0; kk < kBK / kUK; ++kk)  // +32 bytes along K = +2 in the address field
-        mma_tf32(tmem, ad + 2 * kk, bd + 2 * kk, kIdesc, (kb | kk) != 0 ? 1u : 0u);
-      mma_commit(smem_u32(&empty[s]));
-    }
-    s_consumed = kb;
-    mma_commit(smem_u32(&done));  // arrives once every MMA issued above has completed
-  }
-  __syncwarp();
-  const bool ok = mbar_wait(smem_u32(&done), 0);
-  tc_fence_after();
-  __syncthreads();
-  const bool abort = !ok || s_abort != 0;
-  // epilogue: 32 columns per tensor-memory load
-  if (!abort) {
-#pragma unroll 1
-    for (int c0 = 0; c0 < kHalf; c0 += 32) {
-      float cv[32];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) cv[j] = c0 + j < ncol ? cp[(long)(c0 + j) * ldc] : 0.f;
+      const uint32_t ta = tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)(buf * BN + h * kHalf);
       uint32_t v[32];
-      tmem_ld32(tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)(h * kHalf + c0), v);
+      tmem_ld32(ta, v);
 #pragma unroll
       for (int j = 0; j < 32; ++j)
-        if (c0 + j < ncol) cp[(long)(c0 + j) * ldc] = cv[j] - __uint_as_float(v[j]);
+        if (j < ncol) cp[(long)j * ldc] = c0[j] - __uint_as_float(v[j]);
+      // next tile: its first chunk goes in flight before this tile's second chunk
+      float* cp_cur = cp;
+      const int ncol_cur = ncol;
+      if (t + gridDim.x < ntiles) {
+        locate(t + gridDim.x);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) c0[j] = j < ncol ? cp[(long)j * ldc] : 0.f;
+      }
+      tmem_ld32(ta + 32, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (32 + j < ncol_cur) cp_cur[(long)(32 + j) * ldc] = c1[j] - __uint_as_float(v[j]);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&acc_empty[buf]));
     }
-  } else if (threadIdx.x == 0) {
+  }
+  __syncthreads();
+  if (*ab && threadIdx.x == 0) {
     atomicOr(status, 2);
     // drain: wait (bounded) for the copies issued but never consumed
-    for (int kb = s_consumed; kb < s_issued; ++kb)
-      (void)mbar_wait(smem_u32(&full[kb % STAGES]), (kb / STAGES) & 1);
+    for (long long g = s_consumed; g < s_issued; ++g)
+      (void)mbar_wait(smem_u32(&full[g % STAGES]), (uint32_t)((g / STAGES) & 1));
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 2) {
+  if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"((uint32_t)BN)
+                 "r"((uint32_t)(2 * BN))
                  : "memory");
   }
 }
@@ -319,8 +416,9 @@ cudaError_t encode_operand(CUtensorMap* map, float* P, int rows, int Kp, int bat
 }
 
 constexpr int kBN = 128;
-constexpr int kStages = 3;
+constexpr int kStages = 4;
 constexpr size_t kSmem = (size_t)kStages * (kBM * kBK * 4 + kBN * kBK * 4) + 1024;
+int g_num_sms[64] = {0};
 
 }  // namespace
 
@@ -355,9 +453,14 @@ cudaError_t tc_schur_update(int M, int N, int K, const float* A, int lda, long s
   e = encode_operand(&tb, packB, N, Ke, batch, kBN);
   if (e != cudaSuccess) return e;
   const int tilesM = (M + kBM - 1) / kBM, tilesN = (N + kBN - 1) / kBN;
-  dim3 g((unsigned)((long)tilesM * tilesN), batch);
-  tc_gemm_sub_kernel<kBN, kStages><<<g, kThreads, kSmem, st>>>(ta, tb, M, N, Ke / kBK, C, ldc, sC,
-                                                              tilesM, status);
+  const long ntiles = (long)tilesM * tilesN * batch;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!g_num_sms[dev]) cudaDeviceGetAttribute(&g_num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
+  const unsigned grid = (unsigned)std::min<long>(ntiles, std::max(1, g_num_sms[dev]));
+  tc_gemm_sub_kernel<kBN, kStages><<<grid, kPThreads, kSmem, st>>>(
+      ta, tb, M, N, Ke / kBK, C, ldc, sC, tilesM, tilesN, ntiles, status);
   return cudaGetLastError();
 }
 

@@ -43,7 +43,8 @@ def make(M, N, K, batch, lda, ldb, ldc, dtype, seed):
 
 
 SHAPES = [
-    (300, 277, 256, 2),   # 3 x 3 tiles (ragged), full outer block depth
+    (300, 277, 256, 2),   # 3 x 3 tiles (ragged), sub-block depth
+    (260, 390, 512, 1),   # full outer block depth
     (129, 130, 40, 3),    # K not a multiple of 32
     (1000, 64, 200, 1),   # tall
     (17, 900, 33, 2),     # one partial row tile, wide
@@ -115,7 +116,7 @@ def test_schur_update_arguments(B):
     t = torch.zeros(64, device="cuda", dtype=torch.float32)
     p = t.data_ptr()
     with pytest.raises(B.SpError):  # K beyond the tensor-core outer block
-        B.sp_schur_update(3, 4, 4, 300, p, 4, 0, p, 300, 0, p, 4, 0, 1)
+        B.sp_schur_update(3, 4, 4, 600, p, 4, 0, p, 600, 0, p, 4, 0, 1)
     with pytest.raises(B.SpError):  # leading dimension below the row count
         B.sp_schur_update(1, 8, 4, 4, p, 4, 0, p, 4, 0, p, 8, 0, 1)
     with pytest.raises(B.SpError):  # the mixed form has no update kernel of its own
