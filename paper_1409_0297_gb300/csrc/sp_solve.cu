@@ -11,9 +11,9 @@
 // column-major front).
 // Levels with few fronts (the 512 x 512 diagonal blocks of L11, U11 replaced by
 // their inverses at factor time): the sweep is a short chain of matrix-vector
-// products (the diagonal blocks 16 rows per CTA; the off-diagonal blocks one row
-// per thread with the columns split over CTAs), so the large upper fronts spread
-// over the whole GPU.
+// products (the diagonal blocks 16 rows per CTA; after each diagonal block the
+// rows below (forward) or above (backward) take that column block's contribution,
+// one row per thread), so the large upper fronts spread over the whole GPU.
 // VT = double2 (FP64 form) or float2 (FP32 form).
 #include <algorithm>
 
@@ -302,8 +302,9 @@ __global__ void __launch_bounds__(1024) inv_gather_global_kernel(
 // mode 2 (backward, rows [0,k)):   tmp[r] = y[r] - sum_{k<=c<m} U12[r,c] x[c]
 // mode 6 (backward, rows [j0,j1)): tmp[r] -= sum_{j1<=c<k} U[r,c] y[c]
 // mode 3 (backward, rows [j0,j1)): y[r] = x[r] = sum_{r<=c<j1} Uinv[r,c] tmp[c]
-// (in the backward sweep y holds x1 once mode 2 has consumed y1).  Modes 1, 2, 4
-// and 6 of large fronts go through gemv_rows_kernel below.
+// (in the backward sweep y holds x1 once mode 2 has consumed y1).  The sweeps use
+// modes 0 and 3 (the diagonal blocks); the off-diagonal products go through
+// gemv_kernel below.
 template <class VT, class T, int RB>
 __global__ void __launch_bounds__(256) inv_gemv_kernel(int mode, const T* __restrict__ fronts,
                                                         int m, int k, int j0, int j1,
@@ -385,30 +386,26 @@ __global__ void __launch_bounds__(256) inv_gemv_kernel(int mode, const T* __rest
   }
 }
 
-// Row-parallel products of modes 1, 2, 4 and 6 for fronts of any size: one thread
-// per row, 256 rows per CTA (a warp reads 128 contiguous bytes of a column of the
-// column-major front), the input vector staged in shared memory in chunks of
-// 1024 entries, the column range split over gridDim.y when the rows alone would
-// leave the GPU idle.  With one split the kernel applies the mode's update; with
-// several it writes partial sums part[(split nf + f) rows + (r - rlo)], which
+// Off-diagonal products of the sweeps for fronts of any size,
+//   out[r] op= sum_{c in [vlo, vhi)} A[r, c] v[c],   r in [rlo, rhi),
+// with v = y (vsrc 0) or x at the front's grid points (vsrc 1), and
+//   op 0: tmp[r] -= s   op 1: upd[r - k] = tmp[r] - s   op 2: tmp[r] = y[r] - s.
+// One thread per row, 256 rows per CTA (a warp reads 128 contiguous bytes of a
+// column of the column-major front), v staged in shared memory in chunks of
+// 1024, the column range split over gridDim.y when the rows alone would leave
+// the GPU idle.  With one split the kernel applies op itself; with several it
+// writes partial sums part[(split nf + f) rows + (r - rlo)], which
 // gemv_finish_kernel adds in split order (the result does not depend on timing).
-template <class VT, class T>
-__device__ __forceinline__ void gemv_ranges(int mode, int m, int k, int j0, int j1, int& rlo,
-                                            int& rhi, int& vlo, int& vhi) {
-  switch (mode) {
-    case 4: rlo = j0; rhi = j1; vlo = 0; vhi = j0; break;
-    case 1: rlo = k; rhi = m; vlo = 0; vhi = k; break;
-    case 2: rlo = 0; rhi = k; vlo = k; vhi = m; break;
-    default: rlo = j0; rhi = j1; vlo = j1; vhi = k; break;  // 6
-  }
-}
+struct GemvArgs {
+  int rlo, rhi, vlo, vhi, vsrc, op;
+};
 template <class VT>
-__device__ __forceinline__ void gemv_apply(int mode, int m, int k, int r, VT s, VT* tf, VT* yf,
-                                           VT* upd, int f) {
-  if (mode == 1) {
+__device__ __forceinline__ void gemv_out(int op, int m, int k, int r, VT s, VT* tf, const VT* yf,
+                                         VT* upd, int f) {
+  if (op == 1) {
     VT o = tf[r];
     upd[(long)f * (m - k) + (r - k)] = VT{o.x - s.x, o.y - s.y};
-  } else if (mode == 2) {
+  } else if (op == 2) {
     VT o = yf[r];
     tf[r] = VT{o.x - s.x, o.y - s.y};
   } else {
@@ -417,29 +414,26 @@ __device__ __forceinline__ void gemv_apply(int mode, int m, int k, int r, VT s, 
   }
 }
 template <class VT, class T>
-__global__ void __launch_bounds__(256) gemv_rows_kernel(int mode, const T* __restrict__ fronts,
-                                                         int m, int k, int j0, int j1,
-                                                         const int* __restrict__ gidx, VT* tmp,
-                                                         VT* y, VT* upd, const double2* x,
-                                                         int nsplit, VT* part) {
+__global__ void __launch_bounds__(256) gemv_kernel(GemvArgs ga, const T* __restrict__ fronts,
+                                                    int m, int k, const int* __restrict__ gidx,
+                                                    VT* tmp, VT* y, VT* upd, const double2* x,
+                                                    int nsplit, VT* part) {
   __shared__ VT vs[1024];
   const int f = blockIdx.z, sp = blockIdx.y, nf = gridDim.z;
   const T* A = fronts + (long)f * m * m;
   VT* tf = tmp + (long)f * m;
   VT* yf = y + (long)f * k;
-  int rlo, rhi, vlo, vhi;
-  gemv_ranges<VT, T>(mode, m, k, j0, j1, rlo, rhi, vlo, vhi);
-  const int r = rlo + blockIdx.x * 256 + threadIdx.x;
-  const int per = (vhi - vlo + nsplit - 1) / nsplit;
-  const int cb = vlo + sp * per, ce = min(vhi, cb + per);
+  const int r = ga.rlo + blockIdx.x * 256 + threadIdx.x;
+  const int per = (ga.vhi - ga.vlo + nsplit - 1) / nsplit;
+  const int cb = ga.vlo + sp * per, ce = min(ga.vhi, cb + per);
   VT acc = vzero<VT>();
   for (int c0 = cb; c0 < ce; c0 += 1024) {
     const int cn = min(1024, ce - c0);
     __syncthreads();
     for (int i = threadIdx.x; i < cn; i += 256)
-      vs[i] = (mode == 2) ? from_d2<VT>(x[gidx[(long)f * m + c0 + i]]) : yf[c0 + i];
+      vs[i] = ga.vsrc ? from_d2<VT>(x[gidx[(long)f * m + c0 + i]]) : yf[c0 + i];
     __syncthreads();
-    if (r < rhi) {
+    if (r < ga.rhi) {
       const T* Ar = A + r + (long)c0 * m;
       int j = 0;
       for (; j + 8 <= cn; j += 8) {
@@ -452,25 +446,23 @@ __global__ void __launch_bounds__(256) gemv_rows_kernel(int mode, const T* __res
       for (; j < cn; ++j) axpy(acc, Ar[(long)j * m], vs[j]);
     }
   }
-  if (r >= rhi) return;
-  if (nsplit == 1) gemv_apply(mode, m, k, r, acc, tf, yf, upd, f);
-  else part[((long)sp * nf + f) * (rhi - rlo) + (r - rlo)] = acc;
+  if (r >= ga.rhi) return;
+  if (nsplit == 1) gemv_out(ga.op, m, k, r, acc, tf, yf, upd, f);
+  else part[((long)sp * nf + f) * (ga.rhi - ga.rlo) + (r - ga.rlo)] = acc;
 }
-template <class VT, class T>
-__global__ void gemv_finish_kernel(int mode, int m, int k, int j0, int j1, VT* tmp, VT* y, VT* upd,
-                                   int nsplit, const VT* __restrict__ part) {
+template <class VT>
+__global__ void gemv_finish_kernel(GemvArgs ga, int m, int k, VT* tmp, VT* y, VT* upd, int nsplit,
+                                   const VT* __restrict__ part) {
   const int f = blockIdx.y, nf = gridDim.y;
-  int rlo, rhi, vlo, vhi;
-  gemv_ranges<VT, T>(mode, m, k, j0, j1, rlo, rhi, vlo, vhi);
-  const int r = rlo + blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= rhi) return;
+  const int r = ga.rlo + blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= ga.rhi) return;
   VT s = vzero<VT>();
   for (int sp = 0; sp < nsplit; ++sp) {
-    const VT p = part[((long)sp * nf + f) * (rhi - rlo) + (r - rlo)];
+    const VT p = part[((long)sp * nf + f) * (ga.rhi - ga.rlo) + (r - ga.rlo)];
     s.x += p.x;
     s.y += p.y;
   }
-  gemv_apply(mode, m, k, r, s, tmp + (long)f * m, y + (long)f * k, upd, f);
+  gemv_out(ga.op, m, k, r, s, tmp + (long)f * m, y + (long)f * k, upd, f);
 }
 
 template <class VT>
@@ -510,21 +502,20 @@ int gemv_splits(int rows, int cols, int nf) {
   return (int)std::max<long>(1, std::min<long>((kGemvTarget + tiles - 1) / tiles, cols / 128));
 }
 
-// Modes 1, 2, 4, 6 through gemv_rows_kernel (+ gemv_finish_kernel when split).
+// One off-diagonal product (gemv_kernel, + gemv_finish_kernel when split).
 template <class VT, class T>
-int gemv_rows(int mode, DevLevel& L, int j0, int j1, int rlo, int rhi, int vlo, int vhi,
-              const double2* x, void* part, cudaStream_t st) {
-  const int rows = rhi - rlo, cols = vhi - vlo;
+int gemv(const GemvArgs& ga, DevLevel& L, const double2* x, void* part, cudaStream_t st) {
+  const int rows = ga.rhi - ga.rlo, cols = ga.vhi - ga.vlo;
   if (rows <= 0) return 0;
-  int ns = gemv_splits(rows, cols, L.nf);
+  int ns = cols > 0 ? gemv_splits(rows, cols, L.nf) : 1;
   if (!part) ns = 1;
   dim3 g((rows + 255) / 256, ns, L.nf);
-  gemv_rows_kernel<VT, T><<<g, 256, 0, st>>>(mode, (const T*)L.front, L.m, L.k, j0, j1, L.gidx,
-                                             (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x, ns, (VT*)part);
+  gemv_kernel<VT, T><<<g, 256, 0, st>>>(ga, (const T*)L.front, L.m, L.k, L.gidx, (VT*)L.tmp,
+                                        (VT*)L.y, (VT*)L.upd, x, ns, (VT*)part);
   if (ns == 1) return 1;
   dim3 gf((rows + 255) / 256, L.nf);
-  gemv_finish_kernel<VT, T><<<gf, 256, 0, st>>>(mode, L.m, L.k, j0, j1, (VT*)L.tmp, (VT*)L.y,
-                                                (VT*)L.upd, ns, (const VT*)part);
+  gemv_finish_kernel<VT><<<gf, 256, 0, st>>>(ga, L.m, L.k, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, ns,
+                                             (const VT*)part);
   return 2;
 }
 
@@ -572,13 +563,18 @@ cudaError_t forward_t(int d, DevLevel& L, const DevLevel* child, const void* rhs
                                                            (const VT*)rhsQ, cup, L.mc, L.kc,
                                                            L.ea_map, (VT*)L.tmp, (VT*)L.y);
     launches = 1;
+    // right-looking: after the diagonal block [j0, j1) of y, the rows below take
+    // that column block's contribution; the last block's rows are those of L21,
+    // which hand their result to the parent as the update vector
     for (int j0 = 0; j0 < L.k; j0 += kInvBlockSize) {
       const int j1 = min(L.k, j0 + kInvBlockSize);
-      if (j0 > 0) launches += gemv_rows<VT, T>(4, L, j0, j1, j0, j1, 0, j0, nullptr, part, st);
       inv_gemv<VT, T>(0, L, j0, j1, j0, j1, sizeof(VT) * (j1 - j0), nullptr, st);
       ++launches;
+      if (j1 < L.m) {
+        const GemvArgs ga{j1, L.m, j0, j1, 0, j1 == L.k ? 1 : 0};
+        launches += gemv<VT, T>(ga, L, nullptr, part, st);
+      }
     }
-    if (L.m > L.k) launches += gemv_rows<VT, T>(1, L, 0, L.k, L.k, L.m, 0, L.k, nullptr, part, st);
   }
   ps.done(L.nf * sizeof(T) * (kk * (kk - 1) / 2 + mk * kk), launches, st);
   return cudaGetLastError();
@@ -596,18 +592,24 @@ cudaError_t backward_t(DevLevel& L, double2* x, void* part, cudaStream_t st) {
   } else {
     launches = 0;
     if (L.m > L.k) {
-      launches += gemv_rows<VT, T>(2, L, 0, L.k, 0, L.k, L.k, L.m, x, part, st);
+      const GemvArgs ga{0, L.k, L.k, L.m, 1, 2};  // t = y1 - U12 x2
+      launches += gemv<VT, T>(ga, L, x, part, st);
     } else {
       // root: t = y1
       cudaMemcpy2DAsync(L.tmp, sizeof(VT) * L.m, L.y, sizeof(VT) * L.k, sizeof(VT) * L.k, L.nf,
                         cudaMemcpyDeviceToDevice, st);
     }
+    // right-looking: after the diagonal block [j0, j1) of x1, the rows above take
+    // that column block's contribution
     const int nbk = (L.k + kInvBlockSize - 1) / kInvBlockSize;
     for (int bi = nbk - 1; bi >= 0; --bi) {
       const int j0 = bi * kInvBlockSize, j1 = min(L.k, j0 + kInvBlockSize);
-      if (j1 < L.k) launches += gemv_rows<VT, T>(6, L, j0, j1, j0, j1, j1, L.k, x, part, st);
       inv_gemv<VT, T>(3, L, j0, j1, j0, j1, sizeof(VT) * (j1 - j0), x, st);
       ++launches;
+      if (j0 > 0) {
+        const GemvArgs ga{0, j0, j0, j1, 0, 0};
+        launches += gemv<VT, T>(ga, L, x, part, st);
+      }
     }
   }
   ps.done(L.nf * sizeof(T) * (kk * (kk + 1) / 2 + mk * kk), launches, st);
