@@ -55,9 +55,14 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-chosen", action="store_true")
-    p.add_argument("--profile-step", default=None, choices=["fp64", "fp32", "tf32"],
+    p.add_argument("--profile-step", default=None, choices=["fp64", "fp32", "tf32", "tf32x3"],
                    help="run exactly one untimed step (factor + solve of both problems) in the "
                         "given form after set-up and exit: the command profiled under ncu")
+    p.add_argument("--profile-workload", default="2d512", choices=["2d512", "3d64", "3d128"],
+                   help="workload of --profile-step (3d: one Helmholtz GRF problem, b = 8)")
+    p.add_argument("--profile-gemm", default=None, metavar="M,N,K,FORM",
+                   help="run the isolated Schur update C -= A B (sp_schur_update, FORM fp32 | "
+                        "tf32 | tf32x3) three times on device-resident random operands and exit")
     p.add_argument("--problems", default="helmholtz,schrodinger",
                    help="comma list of the step's problems (default both)")
     p.add_argument("--no-3d", action="store_true", help="skip the 3D 128^3 workload")
@@ -282,9 +287,37 @@ def run_ours(args):
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
+    form_prec = {"fp64": B.SP_PREC_FP64, "fp32": B.SP_PREC_FP32, "tf32": B.SP_PREC_TF32,
+                 "tf32x3": B.SP_PREC_TF32X3}
+    if args.profile_gemm:
+        M, Nn, K, form = args.profile_gemm.split(",")
+        M, Nn, K = int(M), int(Nn), int(K)
+        gen = torch.Generator(device="cuda").manual_seed(7)
+        A = torch.randn(K, M, device="cuda", generator=gen)
+        Bt = torch.randn(Nn, K, device="cuda", generator=gen)
+        C = torch.randn(Nn, M, device="cuda", generator=gen)
+        for _ in range(3):
+            B.sp_schur_update(form_prec[form], M, Nn, K, A.data_ptr(), M, 0, Bt.data_ptr(), K, 0,
+                              C.data_ptr(), M, 0, 1)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_gemm": [M, Nn, K, form]}), flush=True)
+        return
+    if args.profile_step and args.profile_workload != "2d512":
+        n = 64 if args.profile_workload == "3d64" else 128
+        w = sm.helmholtz_grf_3d(n, 8, 0)
+        s3, q3 = B.sp_medium_helmholtz(3, n, w["omega"], w["c"])
+        S = B.Solver(3, n, 8, s3, prec=form_prec[args.profile_step], device=local)
+        u = torch.empty(n ** 3, dtype=torch.complex128, device="cuda")
+        torch.cuda.synchronize()
+        S.factor(torch.from_numpy(q3).cuda())
+        info = S.solve(torch.from_numpy(np.ascontiguousarray(w["f"])).cuda(), u)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_step": args.profile_step, "workload": args.profile_workload,
+                          "iters": info["iters"], "true_relres": info["true_relres"]}), flush=True)
+        S.close()
+        return
     if args.profile_step:
-        ctxs = make({"fp64": B.SP_PREC_FP64, "fp32": B.SP_PREC_FP32,
-                     "tf32": B.SP_PREC_TF32}[args.profile_step])
+        ctxs = make(form_prec[args.profile_step])
         torch.cuda.synchronize()
         infos = []
         for c in ctxs:
