@@ -98,8 +98,10 @@ void sp_default_opts(sp_opts *o);
  * (Section 2.3), the nested-dissection symbolic structure (Fig. nd) and all
  * device memory.  The pseudoinverse drops singular values at or below
  * max(size) * eps(sigma_max).  opts may be NULL (defaults); stream is a
- * cudaStream_t or NULL for the legacy default stream.  Returns
- * SP_ERR_RESONANT when min_k |s/(4 pi^2) - |k|^2| < 1e-6 max(1, s/(4 pi^2)). */
+ * cudaStream_t or NULL for the legacy default stream.  Grids: d = 2 or 3, n = 2^p
+ * or 3 2^p (the paper's 48 ... 384 included), n / b a power of two >= 2;
+ * otherwise SP_ERR_ARG.  Returns SP_ERR_RESONANT when
+ * min_k |s/(4 pi^2) - |k|^2| < 1e-6 max(1, s/(4 pi^2)). */
 sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_opts *opts,
                    void *stream, sp_ctx **out);
 

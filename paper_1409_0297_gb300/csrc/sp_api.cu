@@ -397,7 +397,10 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   *out = nullptr;
   int L;
   if (check_grid(d, n, b, &L)) return SP_ERR_ARG;
-  if (n & (n - 1)) return SP_ERR_ARG;  // the device FFT handles powers of two
+  {  // the device FFT handles n = 2^p and n = 3 2^p
+    const int m2 = (n % 3 == 0) ? n / 3 : n;
+    if (m2 < 2 || (m2 & (m2 - 1))) return SP_ERR_ARG;
+  }
   if (prec != SP_PREC_FP64 && prec != SP_PREC_FP32 && prec != SP_PREC_MIXED &&
       prec != SP_PREC_TF32 && prec != SP_PREC_TF32X3)
     return SP_ERR_ARG;

@@ -15,7 +15,13 @@
 //   final pass   out = x + result      (POST_ADD)
 // Forward transforms are decimation-in-time (bit-reversed load), inverse ones
 // decimation-in-frequency (bit-reversed store), so no extra permutation pass is
-// needed.  n must be a power of two (<= 4096).
+// needed.  n = R M with M a power of two and R = 1 or 3: for R = 3 the line is
+// split by j mod 3 into three M-point lines (element j = 3 j' + r goes to
+// sub-line r at the bit-reversed position of j'), the three M-point transforms
+// run side by side, and one radix-3 step combines them in place,
+//   X[k1 + M k2] = sum_r w_n^(r k1) w_3^(r k2) Y_r[k1],
+// which leaves the spectrum in natural order (sub-line k2 holds X[k1 + M k2]);
+// the inverse runs the conjugate steps in the opposite order.
 #include <cstdio>
 
 #include "sp_internal.h"
@@ -49,12 +55,31 @@ struct PassArgs {
   const T* q;      // PRE_Q
   const T* Dn;     // MID
   const VT* addx;  // POST_ADD
-  const VT* tw;
+  const VT* tw;         // w_n^t = exp(-2 pi i t / n), t < n / 2
   long S;               // stride between consecutive elements of a line
   long nlines;          // number of lines of this axis
-  int n, logn, W, pad;
+  int n, W, pad;
+  int R, M, logM;       // n = R M, R in {1, 3}, M = 2^logM
   int mode;             // 0 forward, 1 inverse, 2 middle (forward, scale, inverse)
 };
+
+// position in the staged row of element i of a line in permuted (DIT input /
+// DIF output) order
+template <int R, class VT>
+__device__ __forceinline__ int perm_pos(const PassArgs<VT>& a, int i) {
+  const int r = i % R, j = i / R;
+  return r * a.M + (a.logM ? (int)(__brev((unsigned)j) >> (32 - a.logM)) : 0);
+}
+// w_n^t for 0 <= t < n (w_n^(t + n/2) = -w_n^t)
+template <class VT>
+__device__ __forceinline__ VT tw_at(const PassArgs<VT>& a, int t) {
+  const int h = a.n >> 1;
+  if (t < h) return a.tw[t];
+  VT v = a.tw[t - h];
+  v.x = -v.x;
+  v.y = -v.y;
+  return v;
+}
 
 // global address of element i of line t
 template <class VT>
@@ -63,51 +88,98 @@ __device__ __forceinline__ long line_addr(const PassArgs<VT>& a, long t, int i) 
   return lo + hi * a.S * a.n + (long)i * a.S;
 }
 
-template <class VT>
+// radix-2 stages of the W R sub-lines of length M (sub-line r of row w at
+// offset r M); the M-point twiddle w_M^t is w_n^(R t)
+template <int R, class VT>
 __device__ __forceinline__ void dit_stages(VT* sm, const PassArgs<VT>& a, bool conj_tw) {
-  const int n = a.n, half_n = n >> 1, ld = n + a.pad;
-  const int work = a.W * half_n;
-  for (int s = 1; s <= a.logn; ++s) {
+  const int M = a.M, half_m = M >> 1, ld = a.n + a.pad;
+  const int work = a.W * R * half_m;
+  for (int s = 1; s <= a.logM; ++s) {
     const int half = 1 << (s - 1);
     for (int it = threadIdx.x; it < work; it += blockDim.x) {
-      int w = it / half_n, p = it - w * half_n;
+      int u = it / half_m, p = it - u * half_m;
+      int w = u / R, r = u - w * R;
       int jj = p & (half - 1);
       int i0 = ((p >> (s - 1)) << s) + jj;
       int i1 = i0 + half;
-      VT t = a.tw[jj << (a.logn - s)];
+      VT t = a.tw[(jj << (a.logM - s)) * R];
       if (conj_tw) t.y = -t.y;
-      VT* row = sm + w * ld;
-      VT u = row[i0], v = cmul(row[i1], t);
-      row[i0] = cadd(u, v);
-      row[i1] = csub(u, v);
+      VT* row = sm + w * ld + r * M;
+      VT x0 = row[i0], v = cmul(row[i1], t);
+      row[i0] = cadd(x0, v);
+      row[i1] = csub(x0, v);
     }
     __syncthreads();
   }
 }
 
-template <class VT>
+template <int R, class VT>
 __device__ __forceinline__ void dif_stages(VT* sm, const PassArgs<VT>& a, bool conj_tw) {
-  const int n = a.n, half_n = n >> 1, ld = n + a.pad;
-  const int work = a.W * half_n;
-  for (int s = a.logn; s >= 1; --s) {
+  const int M = a.M, half_m = M >> 1, ld = a.n + a.pad;
+  const int work = a.W * R * half_m;
+  for (int s = a.logM; s >= 1; --s) {
     const int half = 1 << (s - 1);
     for (int it = threadIdx.x; it < work; it += blockDim.x) {
-      int w = it / half_n, p = it - w * half_n;
+      int u = it / half_m, p = it - u * half_m;
+      int w = u / R, r = u - w * R;
       int jj = p & (half - 1);
       int i0 = ((p >> (s - 1)) << s) + jj;
       int i1 = i0 + half;
-      VT t = a.tw[jj << (a.logn - s)];
+      VT t = a.tw[(jj << (a.logM - s)) * R];
       if (conj_tw) t.y = -t.y;
-      VT* row = sm + w * ld;
-      VT u = row[i0], v = row[i1];
-      row[i0] = cadd(u, v);
-      row[i1] = cmul(csub(u, v), t);
+      VT* row = sm + w * ld + r * M;
+      VT x0 = row[i0], v = row[i1];
+      row[i0] = cadd(x0, v);
+      row[i1] = cmul(csub(x0, v), t);
     }
     __syncthreads();
   }
 }
 
+// radix-3 step over the three sub-lines of every row (R = 3 only).  Forward:
+// X[k1 + M k2] = sum_r w_3^(r k2) (w_n^(r k1) Y_r[k1]); inverse (conjugate):
+// Z_r[k1] = w_n^(-r k1) sum_k2 w_3^(-r k2) X[k1 + M k2].
 template <class VT>
+__device__ __forceinline__ void radix3_step(VT* sm, const PassArgs<VT>& a, bool inverse) {
+  using T = typename Real<VT>::T;
+  const int M = a.M, ld = a.n + a.pad;
+  const T h3 = (T)0.86602540378443864676372317075294;  // sin(2 pi / 3)
+  for (int it = threadIdx.x; it < a.W * M; it += blockDim.x) {
+    const int w = it / M, k1 = it - w * M;
+    VT* row = sm + w * ld;
+    VT w1 = tw_at(a, k1), w2 = tw_at(a, 2 * k1);
+    if (!inverse) {
+      const VT a0 = row[k1], b1 = cmul(row[M + k1], w1), b2 = cmul(row[2 * M + k1], w2);
+      const VT t1 = cadd(b1, b2), t2 = csub(b1, b2);
+      VT mm = a0;
+      mm.x -= (T)0.5 * t1.x;
+      mm.y -= (T)0.5 * t1.y;
+      VT rot;  // -i sin(2 pi / 3) t2
+      rot.x = h3 * t2.y;
+      rot.y = -h3 * t2.x;
+      row[k1] = cadd(a0, t1);
+      row[M + k1] = cadd(mm, rot);
+      row[2 * M + k1] = csub(mm, rot);
+    } else {
+      const VT x0 = row[k1], x1 = row[M + k1], x2 = row[2 * M + k1];
+      const VT u1 = cadd(x1, x2), u2 = csub(x1, x2);
+      VT mm = x0;
+      mm.x -= (T)0.5 * u1.x;
+      mm.y -= (T)0.5 * u1.y;
+      VT rot;  // +i sin(2 pi / 3) u2
+      rot.x = -h3 * u2.y;
+      rot.y = h3 * u2.x;
+      w1.y = -w1.y;
+      w2.y = -w2.y;
+      row[k1] = cadd(x0, u1);
+      row[M + k1] = cmul(cadd(mm, rot), w1);
+      row[2 * M + k1] = cmul(csub(mm, rot), w2);
+    }
+  }
+  __syncthreads();
+}
+
+template <class VT, int R>
 __global__ void __launch_bounds__(kThreads) fft_pass_kernel(PassArgs<VT> a) {
   using T = typename Real<VT>::T;
   extern __shared__ unsigned char smraw[];
@@ -136,16 +208,19 @@ __global__ void __launch_bounds__(kThreads) fft_pass_kernel(PassArgs<VT> a) {
       v.x *= qq;
       v.y *= qq;
     }
-    int pos = bitrev_load ? (int)(__brev((unsigned)i) >> (32 - a.logn)) : i;
+    int pos = bitrev_load ? perm_pos<R>(a, i) : i;
     sm[w * ld + pos] = v;
   }
   __syncthreads();
   if (a.mode == 0) {
-    dit_stages(sm, a, false);
+    dit_stages<R>(sm, a, false);
+    if (R == 3) radix3_step(sm, a, false);
   } else if (a.mode == 1) {
-    dif_stages(sm, a, true);
+    if (R == 3) radix3_step(sm, a, true);
+    dif_stages<R>(sm, a, true);
   } else {
-    dit_stages(sm, a, false);
+    dit_stages<R>(sm, a, false);
+    if (R == 3) radix3_step(sm, a, false);
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
       int w, i;
       if (axis0) {
@@ -163,7 +238,8 @@ __global__ void __launch_bounds__(kThreads) fft_pass_kernel(PassArgs<VT> a) {
       p->y *= dn;
     }
     __syncthreads();
-    dif_stages(sm, a, true);
+    if (R == 3) radix3_step(sm, a, true);
+    dif_stages<R>(sm, a, true);
   }
   const bool bitrev_store = (a.mode != 0);  // inverse transforms are DIF
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
@@ -178,7 +254,7 @@ __global__ void __launch_bounds__(kThreads) fft_pass_kernel(PassArgs<VT> a) {
     long t = t0 + w;
     if (t >= a.nlines) continue;
     long g = line_addr(a, t, i);
-    int pos = bitrev_store ? (int)(__brev((unsigned)i) >> (32 - a.logn)) : i;
+    int pos = bitrev_store ? perm_pos<R>(a, i) : i;
     VT v = sm[w * ld + pos];
     if (a.addx) v = cadd(v, a.addx[g]);
     a.out[g] = v;
@@ -196,7 +272,7 @@ int lines_per_cta(int n, long nlines, int esize) {
 }
 
 template <class VT>
-cudaError_t run_pass(int d, int n, int logn, const VT* tw, const typename Real<VT>::T* Dn, int axis,
+cudaError_t run_pass(int d, int n, const VT* tw, const typename Real<VT>::T* Dn, int axis,
                      int mode, const VT* in, VT* out, const typename Real<VT>::T* q,
                      const VT* addx, cudaStream_t st) {
   PassArgs<VT> a{};
@@ -208,7 +284,10 @@ cudaError_t run_pass(int d, int n, int logn, const VT* tw, const typename Real<V
   a.addx = addx;
   a.tw = tw;
   a.n = n;
-  a.logn = logn;
+  a.R = (n % 3 == 0) ? 3 : 1;
+  a.M = n / a.R;
+  a.logM = 0;
+  while ((1 << a.logM) < a.M) ++a.logM;
   long S = 1;
   for (int i = 0; i < axis; ++i) S *= n;
   a.S = S;
@@ -224,34 +303,38 @@ cudaError_t run_pass(int d, int n, int logn, const VT* tw, const typename Real<V
   long grid = (a.nlines + a.W - 1) / a.W;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(fft_pass_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(fft_pass_kernel<VT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(fft_pass_kernel<VT, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
   const double es = sizeof(VT);
   ProfScope ps(PROF_FFT, st);
-  fft_pass_kernel<VT><<<(unsigned)grid, kThreads, smem, st>>>(a);
+  if (a.R == 3)
+    fft_pass_kernel<VT, 3><<<(unsigned)grid, kThreads, smem, st>>>(a);
+  else
+    fft_pass_kernel<VT, 1><<<(unsigned)grid, kThreads, smem, st>>>(a);
   ps.done((double)N * (2 * es + (q ? es / 2 : 0.0) + (mode == 2 ? es / 2 : 0.0) + (addx ? es : 0.0)),
           1, st);
   return cudaGetLastError();
 }
 
 template <class VT>
-cudaError_t green_apply_t(int d, int n, int logn, const VT* tw, const typename Real<VT>::T* Dn,
+cudaError_t green_apply_t(int d, int n, const VT* tw, const typename Real<VT>::T* Dn,
                           VT* tmp, const VT* x, const typename Real<VT>::T* q, bool add_x, VT* out,
                           cudaStream_t st) {
   cudaError_t e;
   // forward along axes 0..d-2, middle pass on axis d-1, inverse along d-2..0
   const VT* src = x;
   for (int ax = 0; ax < d - 1; ++ax) {
-    e = run_pass<VT>(d, n, logn, tw, Dn, ax, 0, src, tmp, ax == 0 ? q : nullptr, nullptr, st);
+    e = run_pass<VT>(d, n, tw, Dn, ax, 0, src, tmp, ax == 0 ? q : nullptr, nullptr, st);
     if (e != cudaSuccess) return e;
     src = tmp;
   }
-  e = run_pass<VT>(d, n, logn, tw, Dn, d - 1, 2, src, tmp, nullptr, nullptr, st);
+  e = run_pass<VT>(d, n, tw, Dn, d - 1, 2, src, tmp, nullptr, nullptr, st);
   if (e != cudaSuccess) return e;
   for (int ax = d - 2; ax >= 0; --ax) {
     bool last = (ax == 0);
-    e = run_pass<VT>(d, n, logn, tw, Dn, ax, 1, tmp, last ? out : tmp, nullptr,
+    e = run_pass<VT>(d, n, tw, Dn, ax, 1, tmp, last ? out : tmp, nullptr,
                      (last && add_x) ? x : nullptr, st);
     if (e != cudaSuccess) return e;
   }
@@ -267,12 +350,12 @@ __global__ void to_float_kernel(const double* a, float* b, long N) {
 
 cudaError_t fft_green_apply(const FftPlan& P, const double2* x, const double* q, bool add_x,
                             double2* out, cudaStream_t st) {
-  return green_apply_t<double2>(P.d, P.n, P.logn, P.tw, P.Dn, P.tmp, x, q, add_x, out, st);
+  return green_apply_t<double2>(P.d, P.n, P.tw, P.Dn, P.tmp, x, q, add_x, out, st);
 }
 
 cudaError_t fft_green_apply32(const FftPlan& P, const float2* x, const float* q, bool add_x,
                               float2* out, cudaStream_t st) {
-  return green_apply_t<float2>(P.d, P.n, P.logn, P.tw32, P.Dn32, P.tmp32, x, q, add_x, out, st);
+  return green_apply_t<float2>(P.d, P.n, P.tw32, P.Dn32, P.tmp32, x, q, add_x, out, st);
 }
 
 cudaError_t to_float(const double* a, float* b, long N, cudaStream_t st) {

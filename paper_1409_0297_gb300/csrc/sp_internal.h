@@ -77,7 +77,7 @@ struct DevLevel {
 
 // ---------------------------------------------------------------- FFT (sp_fft.cu)
 struct FftPlan {
-  int d = 0, n = 0, logn = 0;
+  int d = 0, n = 0, logn = 0;  // n = 2^p or 3 2^p
   double2* tw = nullptr;   // exp(-2 pi i t / n), t < n/2
   double* Dn = nullptr;    // 1 / (4 pi^2 |k|^2 - s) / N, flat
   double2* tmp = nullptr;  // N work

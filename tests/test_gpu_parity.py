@@ -60,6 +60,12 @@ SMALL = [
     ("3d_n8_b2", lambda: dict(d=3, n=8, b=2, kind="helmholtz", omega=2 * np.pi * 1.1,
                               c=sm.grf_velocity(3, 8, 0.2, 13), f=sm.random_gaussian_source(3, 8, 14, 0.15))),
     ("3d_n16_b4", lambda: sm.helmholtz_grf_3d(16, 4, 0)),
+    # n = 3 2^p (radix-3 FFT step; the paper's own grid sizes 48 ... 384)
+    ("2d_n48_b3", lambda: dict(d=2, n=48, b=3, kind="helmholtz", omega=2 * np.pi * 6,
+                               c=sm.grf_velocity(2, 48, 0.08, 15), f=sm.random_gaussian_source(2, 48, 16, 0.05))),
+    ("2d_n96_b6_schr", lambda: sm.schrodinger_wells(2, 96, 6, 6.0, 5.0, 17)),
+    ("3d_n24_b3", lambda: dict(d=3, n=24, b=3, kind="helmholtz", omega=2 * np.pi * 2.5,
+                               c=sm.grf_velocity(3, 24, 0.15, 18), f=sm.random_gaussian_source(3, 24, 19, 0.1))),
 ]
 
 
