@@ -69,6 +69,9 @@ def parse():
     p.add_argument("--forms-3d", default="tf32",
                    help="comma list of the tensor-core forms timed at 3D 128^3 (tf32, tf32x3)")
     p.add_argument("--steps-3d", type=int, default=1)
+    p.add_argument("--no-batch", action="store_true",
+                   help="skip the batched heterogeneous 2D workload (64 problems x 8 right-hand sides)")
+    p.add_argument("--batch-workers", type=int, default=8)
     return p.parse_args()
 
 
@@ -247,6 +250,99 @@ def measure_3d(args, B, torch, flush, peaks, dist, world):
             "plain_fp64": "not run: the FP64 fronts alone take 237 GB and the FP64 factor "
                           "~8e14 flop at 1.25 TFLOP/s",
             "chosen": dict(out[best], name=best), "forms": out}
+
+
+# ------------------------------------------------------------------ batched 2D
+def measure_batch(args, B, torch, dist, world):
+    """64 heterogeneous 2D problems (n in {128, 192, 256, 384, 512}, half Helmholtz,
+    half Schroedinger) with 8 right-hand sides each; one step = for every problem
+    sp_factor + 8 x sp_solve (the factor amortised over its right-hand sides), the
+    problems spread over `batch_workers` host threads, each context on its own CUDA
+    stream so small problems run side by side.  FP32 preconditioner form.  Timed on
+    the device: an event on the launching stream before, every worker stream waits on
+    it, and the launching stream waits on every worker's end event."""
+    import concurrent.futures as cf
+    probs = sm.batched_2d_problems()
+    nw = max(1, args.batch_workers)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    t0 = time.perf_counter()
+    streams = [torch.cuda.Stream() for _ in probs]
+
+    def setup(i):
+        p = probs[i]
+        if p["kind"] == "helmholtz":
+            s, q = B.sp_medium_helmholtz(2, p["n"], p["omega"], p["c"])
+            scale = 1.0
+        else:
+            s, q = B.sp_medium_schrodinger(2, p["n"], p["ell"], p["E"], p["V"])
+            scale = p["ell"] ** 2
+        S = B.Solver(2, p["n"], p["b"], s, prec=B.SP_PREC_FP32, restart=100, device=local,
+                     stream=streams[i].cuda_stream,
+                     host_threads=max(1, (os.cpu_count() or 1) // nw))
+        return S, q, [np.ascontiguousarray(f * scale) for f in p["rhs"]]
+
+    with cf.ThreadPoolExecutor(nw) as ex:
+        made = list(ex.map(setup, range(len(probs))))
+    setup_s = time.perf_counter() - t0
+    ctx = []
+    for (S, q, fs), p in zip(made, probs):
+        N = p["n"] ** 2
+        ctx.append(dict(S=S, q=torch.from_numpy(q).cuda(),
+                        f=[torch.from_numpy(f).cuda() for f in fs],
+                        u=torch.empty(N, dtype=torch.complex128, device="cuda")))
+    torch.cuda.synchronize()
+    order = sorted(range(len(probs)), key=lambda i: -probs[i]["n"])  # largest first
+    groups = [order[w::nw] for w in range(nw)]
+
+    def work(w, infos):
+        for i in groups[w]:
+            c = ctx[i]
+            c["S"].factor(c["q"])
+            for f in c["f"]:
+                infos.append((i, c["S"].solve(f, c["u"])))
+
+    def step(infos):
+        start = torch.cuda.Event(enable_timing=True)
+        start.record()
+        for i in range(len(probs)):
+            streams[i].wait_event(start)
+        with cf.ThreadPoolExecutor(nw) as ex:
+            list(ex.map(lambda w: work(w, infos), range(nw)))
+        cur = torch.cuda.current_stream()
+        for st_ in streams:
+            ev = torch.cuda.Event()
+            ev.record(st_)
+            cur.wait_event(ev)
+        end = torch.cuda.Event(enable_timing=True)
+        end.record()
+        torch.cuda.synchronize()
+        return start.elapsed_time(end)
+
+    for _ in range(args.warmup):
+        step([])
+    if dist:
+        dist.barrier()
+    infos = []
+    ms = reduce_max(step(infos), dist)
+    nsolve = sum(len(p["rhs"]) for p in probs)
+    by_n = {}
+    for i, inf in infos:
+        e = by_n.setdefault(str(probs[i]["n"]), {"solves": 0, "iters": 0})
+        e["solves"] += 1
+        e["iters"] += inf["iters"]
+    for c in ctx:
+        c["S"].close()
+    torch.cuda.synchronize()
+    return {"workload": "batched 2D: 64 problems, n drawn from {128,192,256,384,512} (seed 3000), "
+                        "half Helmholtz (omega = 2 pi n / 8, GRF c) half Schroedinger (l x l "
+                        "lattice wells, l in {4,8,16}, E = 10), 8 random Gaussian sources each",
+            "form": "FP32 preconditioner (FP64 operator, Gram-Schmidt, residuals)",
+            "value": replica_value(nsolve, world, ms), "unit": "solves/s", "ms_per_step": ms,
+            "solves_per_step": nsolve, "warmup": args.warmup, "steps": 1,
+            "concurrency": f"{nw} host threads, one CUDA stream per problem",
+            "setup_s": setup_s,
+            "max_true_relres": max(inf["true_relres"] for _, inf in infos),
+            "by_grid": by_n, "data": "synthetic"}
 
 
 # ------------------------------------------------------------------ our arm
@@ -466,6 +562,9 @@ def run_ours(args):
         c["S"].close()
     fp64 = []
     torch.cuda.synchronize()
+    wbatch = None
+    if not args.no_batch:
+        wbatch = measure_batch(args, B, torch, dist, world)
     w3d = None
     if not args.no_3d:
         w3d = measure_3d(args, B, torch, flush, peaks, dist, world)
@@ -493,7 +592,7 @@ def run_ours(args):
             "roofline": roofline, "kernel_breakdown_ms_per_step": breakdown,
             "chosen_form": chosen, "forms": {k: {kk: v[kk] for kk in ("value", "ms_per_step", "iters")}
                                              for k, v in forms.items()},
-            "clocks": clocks, "cpu_baseline": cpu, "workload_3d": w3d,
+            "clocks": clocks, "cpu_baseline": cpu, "workload_3d": w3d, "workload_batch": wbatch,
         }
         print(json.dumps(line), flush=True)
     if dist:

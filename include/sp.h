@@ -22,7 +22,9 @@
  *    buffer it passes; the context owns its tables, factor and workspace.
  *  - Every call is ordered on the stream given to sp_setup.  Calls that return a
  *    scalar to the host (sp_solve, sp_factor's status check) synchronise that
- *    stream.  A context is not thread-safe.
+ *    stream.  A context is not thread-safe; different contexts may be driven
+ *    from different host threads at the same time (sp_setup synchronises only
+ *    its own streams, so it does not disturb another context's graph capture).
  *  - No call aborts or throws across the ABI: errors come back as sp_status.
  *    After SP_ERR_CUDA the context should be destroyed.
  */

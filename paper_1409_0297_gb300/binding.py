@@ -295,9 +295,10 @@ class Solver:
 
     def __init__(self, d: int, n: int, b: int, s: float, prec: int = SP_PREC_FP64,
                  maxit: int = 500, restart: int = 200, tol: float = 1e-8, device: int = 0,
-                 stream: int = 0):
+                 stream: int = 0, host_threads: int = 0):
         o = sp_default_opts()
         o.maxit, o.restart, o.tol, o.device = maxit, restart, tol, device
+        o.host_threads = host_threads
         self.d, self.n, self.b, self.s, self.prec = d, n, b, s, prec
         self.N = n ** d
         self.ctx = sp_setup(d, n, b, s, prec, o, stream)

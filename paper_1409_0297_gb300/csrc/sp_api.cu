@@ -607,8 +607,10 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   SP_CK(cudaMallocHost(&c->host_sc, 8 * sizeof(double)));
   SP_CK(dalloc(c.get(), &c->app_in, sizeof(double2) * N));
   SP_CK(dalloc(c.get(), &c->app_out, sizeof(double2) * N));
-  SP_CK(cudaMemset(c->qbuf, 0, sizeof(double) * N));
-  SP_CK(cudaDeviceSynchronize());
+  SP_CK(cudaMemsetAsync(c->qbuf, 0, sizeof(double) * N, c->stream));
+  // only this context's streams are synchronised: a device-wide synchronisation
+  // would break a graph capture that another thread's context has in progress
+  SP_CK(cudaStreamSynchronize(c->stream));
   // graphs (a failed capture only means direct launches later)
   if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
@@ -621,7 +623,8 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
     });
     capture_graph(cc, &cc->g_factor, [cc](cudaStream_t s) { return factor_direct(cc, cc->qbuf, s); });
   }
-  SP_CK(cudaDeviceSynchronize());
+  if (c->cap) SP_CK(cudaStreamSynchronize(c->cap));
+  SP_CK(cudaStreamSynchronize(c->stream));
   *out = c.release();
   return SP_OK;
 }

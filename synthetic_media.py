@@ -165,3 +165,33 @@ def schrodinger_wells_512(i: int = 0) -> dict:
 def helmholtz_grf_3d(n: int = 128, b: int = 8, i: int = 0) -> dict:
     """3D Helmholtz on n^3, omega = 2 pi n/8, c = 1 + 0.3 tanh(GRF, corr. length 0.08)."""
     return helmholtz_grf(3, n, b, 2 * np.pi * n / 8, 0.08, i)
+
+
+# ---------------------------------------------------------------- batched 2D problems
+BATCH_SIZES = {128: 8, 192: 6, 256: 8, 384: 12, 512: 16}  # grid n -> leaf size b (n / b = 16 or 32)
+
+
+def batched_2d_problems(count: int = 64, nrhs: int = 8, seed: int = 3000) -> list:
+    """Heterogeneous 2D batch: grid sizes drawn uniformly from {128, 192, 256, 384, 512}
+    (seeded), even-indexed problems Helmholtz (omega = 2 pi n / 8, c = 1 + 0.3 tanh(GRF,
+    correlation length 0.05)), odd-indexed Schroedinger (an l x l lattice of Gaussian wells,
+    l drawn from {4, 8, 16}, E = 10); nrhs random-centre, random-phase Gaussian sources
+    each.  Problem i uses medium seed 1100 + i and source seeds 3000 + nrhs i + r."""
+    rng = np.random.default_rng(seed)
+    sizes = rng.choice(sorted(BATCH_SIZES), size=count)
+    ells = rng.choice([4.0, 8.0, 16.0], size=count)
+    out = []
+    for i in range(count):
+        n = int(sizes[i])
+        b = BATCH_SIZES[n]
+        if i % 2 == 0:
+            c = grf_velocity(2, n, 0.05, MEDIUM_SEED_BASE + 100 + i)
+            p = dict(d=2, n=n, b=b, kind="helmholtz", omega=2 * np.pi * n / 8, c=c)
+        else:
+            V = lattice_wells_potential(2, n, float(ells[i]), MEDIUM_SEED_BASE + 100 + i)
+            p = dict(d=2, n=n, b=b, kind="schrodinger", ell=float(ells[i]), E=10.0, V=V)
+        p["rhs"] = [random_gaussian_source(2, n, RHS_SEED_BASE + 1000 + nrhs * i + r)
+                    for r in range(nrhs)]
+        out.append(p)
+    return out
+
