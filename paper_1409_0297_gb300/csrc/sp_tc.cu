@@ -147,7 +147,7 @@ __device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, vola
 
 constexpr int kEpiWarps = 8;                  // warps 0-7: epilogue (2 per TMEM lane quarter)
 constexpr int kPThreads = 32 * (kEpiWarps + 2);  // + warp 8 (TMA producer), warp 9 (MMA issuer)
-constexpr int kGroupM = 8;                    // row tiles per group of the tile order
+constexpr int kGroupM = 32;                   // row tiles per group of the tile order
 
 // tile t -> front f and tile origin (m0, n0): fronts outermost, then groups of
 // kGroupM row tiles whose column tiles are visited in turn (the group's A rows and
@@ -273,29 +273,34 @@ __global__ void __launch_bounds__(kPThreads, 1) tc_gemm_sub_kernel(
       if (!mbar_wait(smem_u32(&drain), 0)) *ab = 1;
     }
   } else {
-    // epilogue
+    // epilogue: chunks of 32 columns, two register buffers in rotation so the C
+    // loads of the next chunk (and, at the end of a tile, of the next tile's first
+    // chunk) are in flight while the current one is stored
+    constexpr int kChunks = kHalf / 32;
     const int qw = warp & 3, h = warp >> 2;
-    float c0[32], c1[32];
-    long t = blockIdx.x;
-    int f, m0, n0;
-    int row = 0, ncol = 0;
-    float* cp = C;
-    auto locate = [&](long tt) {
+    float cA[32], cB[32];
+    auto locate = [&](long tt, float** cp, int* ncol) {
+      int f, m0, n0;
       tile_coords(tt, tilesM, tilesN, BN, &f, &m0, &n0);
-      row = m0 + qw * 32 + lane;
-      ncol = row < M ? min(kHalf, N - (n0 + h * kHalf)) : 0;
-      cp = C + (long)f * sC + row + (long)(n0 + h * kHalf) * ldc;
+      const int row = m0 + qw * 32 + lane;
+      *ncol = row < M ? min(kHalf, N - (n0 + h * kHalf)) : 0;
+      *cp = C + (long)f * sC + row + (long)(n0 + h * kHalf) * ldc;
     };
-    if (t < ntiles) {
-      locate(t);
+    auto load = [&](float* buf, const float* cp, int ncol, int c0) {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) c0[j] = j < ncol ? cp[(long)j * ldc] : 0.f;
+      for (int j = 0; j < 32; ++j) buf[j] = c0 + j < ncol ? cp[(long)(c0 + j) * ldc] : 0.f;
+    };
+    long t = blockIdx.x;
+    float* cp = C;
+    int ncol = 0;
+    if (t < ntiles) {
+      locate(t, &cp, &ncol);
+      load(cA, cp, ncol, 0);
     }
     for (long i = 0; t < ntiles; t += gridDim.x, ++i) {
       const int buf = (int)(i & 1);
       const long u = i >> 1;
-#pragma unroll
-      for (int j = 0; j < 32; ++j) c1[j] = 32 + j < ncol ? cp[(long)(32 + j) * ldc] : 0.f;
+      if (kChunks > 1) load(cB, cp, ncol, 32);
       // one lane waits, the warp follows (tcgen05.ld below is warp-collective)
       int okw = 0;
       if (lane == 0) okw = mbar_wait_ab(smem_u32(&acc_full[buf]), (uint32_t)(u & 1), ab) ? 1 : 0;
@@ -304,23 +309,24 @@ __global__ void __launch_bounds__(kPThreads, 1) tc_gemm_sub_kernel(
       if (!okw) break;
       tc_fence_after();
       const uint32_t ta = tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)(buf * BN + h * kHalf);
-      uint32_t v[32];
-      tmem_ld32(ta, v);
+      float* cp_nx = cp;
+      int ncol_nx = 0;
+      const bool has_next = t + gridDim.x < ntiles;
+      if (has_next) locate(t + gridDim.x, &cp_nx, &ncol_nx);
 #pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j < ncol) cp[(long)j * ldc] = c0[j] - __uint_as_float(v[j]);
-      // next tile: its first chunk goes in flight before this tile's second chunk
-      float* cp_cur = cp;
-      const int ncol_cur = ncol;
-      if (t + gridDim.x < ntiles) {
-        locate(t + gridDim.x);
+      for (int j = 0; j < kChunks; ++j) {
+        float* cur = (j & 1) ? cB : cA;
+        uint32_t v[32];
+        tmem_ld32(ta + 32 * j, v);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) c0[j] = j < ncol ? cp[(long)j * ldc] : 0.f;
+        for (int q = 0; q < 32; ++q)
+          if (32 * j + q < ncol) cp[(long)(32 * j + q) * ldc] = cur[q] - __uint_as_float(v[q]);
+        if (j + 2 < kChunks) load(cur, cp, ncol, 32 * (j + 2));
+        else if (j + 2 == kChunks && has_next) load(cur, cp_nx, ncol_nx, 0);
       }
-      tmem_ld32(ta + 32, v);
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (32 + j < ncol_cur) cp_cur[(long)(32 + j) * ldc] = c1[j] - __uint_as_float(v[j]);
+      if (kChunks == 1 && has_next) load(cA, cp_nx, ncol_nx, 0);
+      cp = cp_nx;
+      ncol = ncol_nx;
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&acc_empty[buf]));
@@ -415,7 +421,7 @@ cudaError_t encode_operand(CUtensorMap* map, float* P, int rows, int Kp, int bat
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-constexpr int kBN = 128;
+constexpr int kBN = 256;
 constexpr int kStages = 4;
 constexpr size_t kSmem = (size_t)kStages * (kBM * kBK * 4 + kBN * kBK * 4) + 1024;
 int g_num_sms[64] = {0};
