@@ -584,6 +584,23 @@ __global__ void __launch_bounds__(256) gemm_sub_kernel(int M, int N, int K, cons
   const int r0 = tr * TILE, c0 = tc * TILE;
   __shared__ T As[kNB][TILE];
   __shared__ T Bs[kNB][TILE + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  // FP32: this thread's C entries are loaded first, so their latency overlaps the
+  // staging of A and B and the products (the update is bound by C traffic); FP64
+  // is bound by the FP64 pipe and keeps its registers for occupancy
+  constexpr bool kPre = sizeof(T) == sizeof(float);
+  T cpre[R][R];
+  if constexpr (kPre) {
+#pragma unroll
+    for (int b = 0; b < R; ++b) {
+      const int c = c0 + ty + 16 * b;
+#pragma unroll
+      for (int a = 0; a < R; ++a) {
+        const int r = r0 + tx + 16 * a;
+        cpre[a][b] = (r < M && c < N) ? C[r + (long)c * ldc] : (T)0;
+      }
+    }
+  }
   for (int e = threadIdx.x; e < K * TILE; e += blockDim.x) {
     int i = e % TILE, l = e / TILE;
     int r = r0 + i;
@@ -595,7 +612,6 @@ __global__ void __launch_bounds__(256) gemm_sub_kernel(int M, int N, int K, cons
     Bs[l][jc] = (c < N) ? B[l + (long)c * ldb] : (T)0;
   }
   __syncthreads();
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   T acc[R][R];
 #pragma unroll
   for (int a = 0; a < R; ++a)
@@ -619,7 +635,10 @@ __global__ void __launch_bounds__(256) gemm_sub_kernel(int M, int N, int K, cons
 #pragma unroll
     for (int a = 0; a < R; ++a) {
       int r = r0 + tx + 16 * a;
-      if (r < M) C[r + (long)c * ldc] -= acc[a][b];
+      if (r < M) {
+        if constexpr (kPre) C[r + (long)c * ldc] = cpre[a][b] - acc[a][b];
+        else C[r + (long)c * ldc] -= acc[a][b];
+      }
     }
   }
 }
