@@ -10,10 +10,6 @@ namespace {
 
 constexpr int kThr = 256;
 
-__device__ __forceinline__ double2 conj_mul(double2 a, double2 b) {  // conj(a) * b
-  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -a.y * b.x));
-}
-
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
@@ -25,21 +21,47 @@ __device__ __forceinline__ void chunk_of(long N, long* c0, long* c1) {
   *c1 = min(N, *c0 + per);
 }
 
-// partial[j * nblk + blk] = sum over the CTA's chunk of conj(V_j) w
+// partial[j * nblk + blk] = sum over the CTA's chunk of conj(V_j) w.  Each thread
+// walks its elements of the chunk with w[i] in registers and accumulates eight
+// vectors at a time (independent FMA chains; w is re-read once per eight
+// vectors, V once); the sums are reduced over the CTA in shared memory in a fixed
+// order.
 __device__ void chunk_dots(const double2* V, long ldv, int nv, const double2* w, long c0, long c1,
                            double2* partial) {
+  constexpr int kJ = 8;
+  __shared__ double2 red[kJ][kThr / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = warp; j < nv; j += nw) {
-    const double2* v = V + (long)j * ldv;
-    double sr = 0, si = 0;
-    for (long i = c0 + lane; i < c1; i += 32) {
-      double2 p = conj_mul(v[i], w[i]);
-      sr += p.x;
-      si += p.y;
+  for (int j0 = 0; j0 < nv; j0 += kJ) {
+    const int nj = min(kJ, nv - j0);
+    double sr[kJ], si[kJ];
+#pragma unroll
+    for (int q = 0; q < kJ; ++q) sr[q] = si[q] = 0.0;
+    for (long i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+      const double2 wi = w[i];
+#pragma unroll
+      for (int q = 0; q < kJ; ++q) {
+        if (q < nj) {
+          const double2 v = V[(long)(j0 + q) * ldv + i];  // conj(v) w
+          sr[q] = fma(v.x, wi.x, fma(v.y, wi.y, sr[q]));
+          si[q] = fma(v.x, wi.y, fma(-v.y, wi.x, si[q]));
+        }
+      }
     }
-    sr = warp_sum(sr);
-    si = warp_sum(si);
-    if (lane == 0) partial[(long)j * gridDim.x + blockIdx.x] = make_double2(sr, si);
+#pragma unroll
+    for (int q = 0; q < kJ; ++q) {
+      const double a = warp_sum(sr[q]), b = warp_sum(si[q]);
+      if (lane == 0) red[q][warp] = make_double2(a, b);
+    }
+    __syncthreads();
+    if (threadIdx.x < nj) {
+      double a = 0, b = 0;
+      for (int x = 0; x < nw; ++x) {
+        a += red[threadIdx.x][x].x;
+        b += red[threadIdx.x][x].y;
+      }
+      partial[(long)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = make_double2(a, b);
+    }
+    __syncthreads();
   }
 }
 
@@ -59,13 +81,25 @@ __global__ void __launch_bounds__(kThr) update_dots_kernel(const double2* V, lon
   long c0, c1;
   chunk_of(N, &c0, &c1);
   for (long i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
-    double2 acc = w[i];
-    for (int j = 0; j < nv; ++j) {
-      double2 v = V[(long)j * ldv + i], hj = hs[j];
-      acc.x -= fma(v.x, hj.x, -v.y * hj.y);
-      acc.y -= fma(v.x, hj.y, v.y * hj.x);
+    // w_i - sum_j V_j[i] h_j with four independent partial sums (FP64 FMA latency)
+    double ax[4] = {0, 0, 0, 0}, ay[4] = {0, 0, 0, 0};
+    int j = 0;
+    for (; j + 4 <= nv; j += 4) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const double2 v = V[(long)(j + q) * ldv + i], hj = hs[j + q];
+        ax[q] = fma(v.x, hj.x, fma(-v.y, hj.y, ax[q]));
+        ay[q] = fma(v.x, hj.y, fma(v.y, hj.x, ay[q]));
+      }
     }
-    w[i] = acc;
+    for (; j < nv; ++j) {
+      const double2 v = V[(long)j * ldv + i], hj = hs[j];
+      ax[0] = fma(v.x, hj.x, fma(-v.y, hj.y, ax[0]));
+      ay[0] = fma(v.x, hj.y, fma(v.y, hj.x, ay[0]));
+    }
+    const double2 wi = w[i];
+    w[i] = make_double2(wi.x - ((ax[0] + ax[1]) + (ax[2] + ax[3])),
+                        wi.y - ((ay[0] + ay[1]) + (ay[2] + ay[3])));
   }
   if (partial) {
     __syncthreads();
