@@ -72,6 +72,9 @@ def parse():
     p.add_argument("--no-batch", action="store_true",
                    help="skip the batched heterogeneous 2D workload (64 problems x 8 right-hand sides)")
     p.add_argument("--batch-workers", type=int, default=8)
+    p.add_argument("--no-autotune", action="store_true",
+                   help="2D contexts keep the built-in launch-shape heuristics instead of "
+                        "tuning them at set-up (sp_opts.autotune; results are bit-identical)")
     return p.parse_args()
 
 
@@ -375,7 +378,8 @@ def run_ours(args):
     def make(prec):
         out = []
         for p in probs:
-            S = B.Solver(p["d"], p["n"], p["b"], p["s"], prec=prec, device=local)
+            S = B.Solver(p["d"], p["n"], p["b"], p["s"], prec=prec, device=local,
+                         autotune=not args.no_autotune)
             out.append(dict(S=S, q=torch.from_numpy(p["q"]).cuda(),
                             f=torch.from_numpy(p["f"]).cuda(),
                             u=torch.empty(N, dtype=torch.complex128, device="cuda")))
@@ -459,6 +463,8 @@ def run_ours(args):
         return ms / K, wall, infos
 
     fp64 = make(B.SP_PREC_FP64)
+    L2d = int(np.log2(probs[0]["n"] // probs[0]["b"]))
+    shapes64 = [B.sp_tuning(fp64[0]["S"].ctx, l) for l in range(L2d + 1)]
     sampler = ClockSampler(local)
     sampler.start()
     ms64, wall64, infos64 = timed(fp64, args.steps, args.warmup)
@@ -582,6 +588,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": "512^2", "b": 16, "solves_per_step": 2,
                        "tol": 1e-8, "l2": "flushed between steps (256 MB write)",
+                       "autotune": not args.no_autotune, "fp64_tile_shapes_by_level": shapes64,
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
             "iters": [i["iters"] for i in infos64[:solves_per_step]],
             "true_relres": [i["true_relres"] for i in infos64[:solves_per_step]],

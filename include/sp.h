@@ -77,6 +77,11 @@ typedef struct {
   int device;        /* CUDA device ordinal the context lives on (default 0) */
   int host_threads;  /* threads for the host set-up (0 = all hardware threads) */
   double inner_tol;  /* SP_PREC_MIXED: relative tolerance of each inner solve (default 1e-5) */
+  int autotune;      /* 1: sp_setup times the factorisation's launch-shape candidates
+                        of every level (Schur-update and block-inverse GEMM tiles,
+                        32 or 64) on a placeholder medium (q = 0) and keeps the
+                        fastest; every result is bit-identical to the untuned
+                        context's.  0 (default): built-in heuristics */
 } sp_opts;
 
 typedef struct {
@@ -224,6 +229,11 @@ sp_status sp_profile_read(sp_ctx *ctx, int cap, double *ms, int *launches, doubl
 sp_status sp_schur_update(sp_precision prec, int M, int N, int K, const void *A, int lda,
                           long long sA, const void *B, int ldb, long long sB, void *C, int ldc,
                           long long sC, int batch, void *stream);
+
+/* Launch shapes of nested-dissection level `level` (0 = leaves): Schur-update
+ * tile and block-inverse GEMM tile (32 or 64); 0 means the built-in heuristic
+ * (sp_opts.autotune = 0).  SP_ERR_ARG for a level outside 0 ... L. */
+sp_status sp_tuning(const sp_ctx *ctx, int level, int *gemm_tile, int *gen_tile);
 
 /* g = G f for callers that cannot allocate device memory when they call (for
  * example code running inside a CUDA-graph stream capture, or under a fixed,

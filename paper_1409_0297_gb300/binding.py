@@ -23,7 +23,8 @@ EXPORTED = [
     "sp_default_opts", "sp_setup", "sp_factor", "sp_apply", "sp_solve", "sp_factor_host",
     "sp_solve_host", "sp_matvec", "sp_green", "sp_qapply", "sp_get_table", "sp_stencil_table",
     "sp_front_sizes", "sp_level_info", "sp_costs", "sp_medium_helmholtz", "sp_medium_schrodinger", "sp_profile",
-    "sp_profile_read", "sp_green_static", "sp_schur_update", "sp_destroy", "sp_status_str",
+    "sp_profile_read", "sp_green_static", "sp_schur_update", "sp_tuning", "sp_destroy",
+    "sp_status_str",
 ]
 PROF_CLASSES = ["assemble", "lu_panel", "lu_trsm", "lu_gemm", "qapply", "forward", "backward",
                 "fft", "krylov", "lu_trinv", "lu_tc"]
@@ -32,7 +33,8 @@ PROF_CLASSES = ["assemble", "lu_panel", "lu_trsm", "lu_gemm", "qapply", "forward
 class sp_opts(ctypes.Structure):
     _fields_ = [("maxit", ctypes.c_int), ("restart", ctypes.c_int), ("tol", ctypes.c_double),
                 ("pivot_tol", ctypes.c_double), ("device", ctypes.c_int),
-                ("host_threads", ctypes.c_int), ("inner_tol", ctypes.c_double)]
+                ("host_threads", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("autotune", ctypes.c_int)]
 
 
 class sp_info(ctypes.Structure):
@@ -78,6 +80,7 @@ def _load() -> ctypes.CDLL:
         "sp_green_static": (I, [I, I, D, P, P, P]),
         "sp_schur_update": (I, [I, I, I, I, P, I, ctypes.c_longlong, P, I, ctypes.c_longlong, P, I,
                                 ctypes.c_longlong, I, P]),
+        "sp_tuning": (I, [P, I, pI, pI]),
         "sp_destroy": (V, [P]),
         "sp_status_str": (ctypes.c_char_p, [I]),
     }
@@ -283,6 +286,13 @@ def sp_schur_update(prec: int, M: int, N: int, K: int, A_dev: int, lda: int, sA:
                                stream), "sp_schur_update")
 
 
+def sp_tuning(ctx: int, level: int) -> dict:
+    """Launch shapes of one level (0 = built-in heuristic)."""
+    v = [ctypes.c_int() for _ in range(2)]
+    _check(LIB.sp_tuning(ctx, level, *[ctypes.byref(x) for x in v]), "sp_tuning")
+    return dict(gemm_tile=v[0].value, gen_tile=v[1].value)
+
+
 def sp_destroy(ctx: int) -> None:
     LIB.sp_destroy(ctx)
 
@@ -295,10 +305,11 @@ class Solver:
 
     def __init__(self, d: int, n: int, b: int, s: float, prec: int = SP_PREC_FP64,
                  maxit: int = 500, restart: int = 200, tol: float = 1e-8, device: int = 0,
-                 stream: int = 0, host_threads: int = 0):
+                 stream: int = 0, host_threads: int = 0, autotune: bool = False):
         o = sp_default_opts()
         o.maxit, o.restart, o.tol, o.device = maxit, restart, tol, device
         o.host_threads = host_threads
+        o.autotune = 1 if autotune else 0
         self.d, self.n, self.b, self.s, self.prec = d, n, b, s, prec
         self.N = n ** d
         self.ctx = sp_setup(d, n, b, s, prec, o, stream)

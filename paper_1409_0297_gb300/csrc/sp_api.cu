@@ -195,6 +195,66 @@ sp_status factor_direct(sp_ctx* c, const double* q, cudaStream_t st) {
   return SP_OK;
 }
 
+// Smallest of reps timings of fn() on stream st with CUDA events (ms).
+template <class Fn>
+float time_ms(cudaStream_t st, int reps, Fn fn) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  float best = 1e30f;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return best;
+  for (int r = 0; r < reps; ++r) {
+    cudaEventRecord(a, st);
+    fn();
+    cudaEventRecord(b, st);
+    if (cudaEventSynchronize(b) != cudaSuccess) break;
+    float t = 0;
+    cudaEventElapsedTime(&t, a, b);
+    best = std::min(best, t);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return best;
+}
+
+// Greedy per-level autotuning of the factorisation's GEMM tiles (shapes that
+// leave every result bit-identical: each output entry is summed in the same
+// order): each candidate of a level is timed on that level alone (a level's
+// factorisation re-assembles its fronts from its children), bottom-up, with the
+// medium in qbuf (zero at set-up: P = Q).
+sp_status autotune(sp_ctx* c) {
+  cudaStream_t st = c->stream;
+  SP_CK(cudaMemsetAsync(c->status, 0, sizeof(int), st));
+  sp_status fs = factor_direct(c, c->qbuf, st);  // warm-up; leaves a valid factor
+  if (fs != SP_OK) return fs;
+  for (int l = 0; l <= c->L; ++l) {
+    DevLevel& D = c->lv[l];
+    const DevLevel* ch = l ? &c->lv[l - 1] : nullptr;
+    auto run = [&]() {
+      factor_level(c->prec, c->d, D, ch, c->Qcat, c->Ccat, c->qbuf, c->opts.pivot_tol, c->status,
+                   c->work, st);
+    };
+    int* knobs[2] = {&D.gemm_tile, &D.gen_tile};
+    for (int kn = 0; kn < (D.inv ? 2 : 1); ++kn) {
+      int best = 0;
+      float tbest = 1e30f;
+      for (int cand : {32, 64}) {
+        *knobs[kn] = cand;
+        run();  // first launch of a shape outside the timing
+        const float t = time_ms(st, 2, run);
+        if (t < tbest) {
+          tbest = t;
+          best = cand;
+        }
+      }
+      *knobs[kn] = best;
+    }
+    run();
+  }
+  SP_CK(cudaGetLastError());
+  SP_CK(cudaMemsetAsync(c->status, 0, sizeof(int), st));
+  SP_CK(cudaStreamSynchronize(st));
+  return cuda_status(cudaGetLastError());
+}
+
 // Captures fn(cap stream) into an executable graph; leaves *out null on failure
 // (the callers then launch directly).
 template <class Fn>
@@ -228,6 +288,7 @@ void sp_default_opts(sp_opts* o) {
   o->device = 0;
   o->host_threads = 0;
   o->inner_tol = 1e-5;
+  o->autotune = 0;
 }
 
 const char* sp_status_str(sp_status st) {
@@ -611,6 +672,10 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   // only this context's streams are synchronised: a device-wide synchronisation
   // would break a graph capture that another thread's context has in progress
   SP_CK(cudaStreamSynchronize(c->stream));
+  if (c->opts.autotune) {
+    sp_status ts = autotune(c.get());
+    if (ts != SP_OK) return ts;
+  }
   // graphs (a failed capture only means direct launches later)
   if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
@@ -909,6 +974,14 @@ sp_status sp_schur_update(sp_precision prec, int M, int N, int K, const void* A,
   if (pb) cudaFree(pb);
   if (status) cudaFree(status);
   return rs;
+}
+
+sp_status sp_tuning(const sp_ctx* c, int level, int* gemm_tile, int* gen_tile) {
+  if (!c || level < 0 || level > c->L) return SP_ERR_ARG;
+  const DevLevel& D = c->lv[level];
+  if (gemm_tile) *gemm_tile = D.gemm_tile;
+  if (gen_tile) *gen_tile = D.gen_tile;
+  return SP_OK;
 }
 
 sp_status sp_get_table(const sp_ctx* c, int t, double* Q_out, double* C_out, int* rows, int* cols,

@@ -845,12 +845,12 @@ __global__ void trinv_store_kernel(T* fronts, int m, const T* Xl, const T* Xu, l
 
 template <class T>
 void gemm_sub(int M, int N, int K, const T* A, int lda, long sA, const T* B, int ldb, long sB,
-              T* C, int ldc, long sC, int batch, cudaStream_t st) {
+              T* C, int ldc, long sC, int batch, cudaStream_t st, int tile = 0) {
   if (M <= 0 || N <= 0 || K <= 0) return;
   // padded work of 64- and 32-wide tiles relative to M N
   const double w64 = (double)((M + 63) / 64 * 64) * ((N + 63) / 64 * 64);
   const double w32 = (double)((M + 31) / 32 * 32) * ((N + 31) / 32 * 32);
-  if (w64 > 1.1 * w32) {
+  if (tile == 32 || (tile == 0 && w64 > 1.1 * w32)) {
     int tilesM = (M + 31) / 32, tilesN = (N + 31) / 32;
     dim3 g(tilesM * tilesN, batch);
     gemm_sub_kernel<T, 32><<<g, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, tilesM);
@@ -864,10 +864,11 @@ void gemm_sub(int M, int N, int K, const T* A, int lda, long sA, const T* B, int
 template <class T>
 void gemm_gen(int M, int N, int K, T alpha, bool beta_one, const T* A, int lda, long sA,
               const T* B, int ldb, long sB, T* C, int ldc, long sC, int batch, int tri_a,
-              int tri_b, cudaStream_t st, int nb2 = 1, long sA2 = 0, long sB2 = 0, long sC2 = 0) {
+              int tri_b, cudaStream_t st, int nb2 = 1, long sA2 = 0, long sB2 = 0, long sC2 = 0,
+              int tile = 0) {
   if (M <= 0 || N <= 0 || K <= 0 || batch <= 0 || nb2 <= 0) return;
   int tilesM = (M + kTile - 1) / kTile, tilesN = (N + kTile - 1) / kTile;
-  if ((long)tilesM * tilesN * batch * nb2 < 304) {
+  if (tile == 32 || (tile == 0 && (long)tilesM * tilesN * batch * nb2 < 304)) {
     // small problem: 32 x 32 tiles give four times the CTAs
     tilesM = (M + 31) / 32;
     tilesN = (N + 31) / 32;
@@ -936,14 +937,16 @@ void invert_triangles(DevLevel& L, T* scratch, int Bsz, cudaStream_t st) {
       const int a0 = p0 * 2 * s, c0 = a0 + s;
       // lower: W = B Ainv (B = L[c0.., a0..], Ainv lower), Xl[c0.., a0..] = -Cinv W
       gemm_gen<T>(sc, s, s, (T)1, false, F + c0 + (long)a0 * m, m, mm, Xl + a0 + (long)a0 * ldx,
-                  ldx, sX, W + a0, k, sW, nf, 0, 1, st, cnt, ps_m, ps_x, ps_w);
+                  ldx, sX, W + a0, k, sW, nf, 0, 1, st, cnt, ps_m, ps_x, ps_w, L.gen_tile);
       gemm_gen<T>(sc, s, sc, (T)-1, false, Xl + c0 + (long)c0 * ldx, ldx, sX, W + a0, k, sW,
-                  Xl + c0 + (long)a0 * ldx, ldx, sX, nf, 1, 0, st, cnt, ps_x, ps_w, ps_x);
+                  Xl + c0 + (long)a0 * ldx, ldx, sX, nf, 1, 0, st, cnt, ps_x, ps_w, ps_x,
+                  L.gen_tile);
       // upper: W = Ainv B (B = U[a0.., c0..], Ainv upper), Xu[a0.., c0..] = -W Cinv
       gemm_gen<T>(s, sc, s, (T)1, false, Xu + a0 + (long)a0 * ldx, ldx, sX, F + a0 + (long)c0 * m,
-                  m, mm, W + a0, k, sW, nf, 2, 0, st, cnt, ps_x, ps_m, ps_w);
+                  m, mm, W + a0, k, sW, nf, 2, 0, st, cnt, ps_x, ps_m, ps_w, L.gen_tile);
       gemm_gen<T>(s, sc, sc, (T)-1, false, W + a0, k, sW, Xu + c0 + (long)c0 * ldx, ldx, sX,
-                  Xu + a0 + (long)c0 * ldx, ldx, sX, nf, 0, 2, st, cnt, ps_w, ps_x, ps_x);
+                  Xu + a0 + (long)c0 * ldx, ldx, sX, nf, 0, 2, st, cnt, ps_w, ps_x, ps_x,
+                  L.gen_tile);
     }
   }
   const long nbk = (k + Bsz - 1) / Bsz;
@@ -1045,7 +1048,8 @@ void schur_update(DevLevel& L, T* F, int M, int N, int K, long offA, long offB, 
   const double fl = 2.0 * M * N * K * L.nf;
   if (K <= kNB) {
     ProfScope pg(PROF_LU_GEMM, st);
-    gemm_sub<T>(M, N, K, F + offA, L.m, mm, F + offB, L.m, mm, F + offC, L.m, mm, L.nf, st);
+    gemm_sub<T>(M, N, K, F + offA, L.m, mm, F + offB, L.m, mm, F + offC, L.m, mm, L.nf, st,
+                L.gemm_tile);
     pg.done(fl, 1, st);
     return;
   }

@@ -73,6 +73,10 @@ struct DevLevel {
   void* y = nullptr;        // nf x k complex forward-sweep results
   bool inv = false;         // L11, U11 replaced by their inverses; sweeps are GEMVs
   void* tmp = nullptr;      // nf x m complex work vector of the GEMV sweeps (inv levels)
+  // launch shapes (0 = built-in heuristic; set by the autotuner): Schur-update tile
+  // (32 or 64) and general GEMM tile of the block inverses (32 or 64); every output
+  // entry keeps its summation order, so the choice never changes a result
+  int gemm_tile = 0, gen_tile = 0;
 };
 
 // ---------------------------------------------------------------- FFT (sp_fft.cu)

@@ -93,3 +93,11 @@ def test_medium_split_matches_oracle():
     s1, q1 = B.sp_medium_helmholtz(d, n, 2 * np.pi * 5, np.ones(n * n))
     s0, q0 = O.helmholtz_shift(d, n, 2 * np.pi * 5, np.ones(n * n))
     assert abs(s1 - s0) <= 1e-12 * s0 and s1 != (2 * np.pi * 5) ** 2
+
+
+def test_default_opts_layout():
+    """sp_opts as the binding lays it out: the defaults documented in include/sp.h."""
+    B = _binding()
+    o = B.sp_default_opts()
+    assert (o.maxit, o.restart, o.tol, o.pivot_tol) == (500, 200, 1e-8, 1e-14)
+    assert (o.device, o.host_threads, o.inner_tol, o.autotune) == (0, 0, 1e-5, 0)
