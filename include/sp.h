@@ -82,6 +82,8 @@ typedef struct {
                         32 or 64) on a placeholder medium (q = 0) and keeps the
                         fastest; every result is bit-identical to the untuned
                         context's.  0 (default): built-in heuristics */
+  int max_rhs;       /* right-hand sides sp_solve_many may take at once, 1 ... 8
+                        (default 1); the solve workspace is sized for it */
 } sp_opts;
 
 typedef struct {
@@ -126,6 +128,17 @@ sp_status sp_factor(sp_ctx *ctx, const double *q_dev);
  * stencil apply, forward sweep leaves to root, backward sweep root to leaves.
  * r_dev, z_dev: N complex128 on the device, must not alias. */
 sp_status sp_apply(sp_ctx *ctx, const void *r_dev, void *z_dev);
+
+/* Solve (I + G q) u_r = G f_r for nrhs right-hand sides with the current factor
+ * (Section 2.2): nrhs independent GMRES iterations (each as sp_solve: its own
+ * Krylov basis, restarts and stopping test) advanced in lockstep, sharing every
+ * preconditioner application and operator product, so the factor is read once
+ * per step for all right-hand sides.  Each u_r is bit-identical to sp_solve's
+ * for f_r.  F_dev, U_dev: nrhs x N complex128 on the device, right-hand side r at
+ * offset r N; infos: nrhs sp_info or NULL.  1 <= nrhs <= opts.max_rhs, else
+ * SP_ERR_ARG; SP_ERR_NOCONV if any right-hand side stopped above tol.  The
+ * mixed-precision form solves the right-hand sides one after the other. */
+sp_status sp_solve_many(sp_ctx *ctx, int nrhs, const void *F_dev, void *U_dev, sp_info *infos);
 
 /* Solve (I + G q) u = G f by GMRES right-preconditioned with P^{-1} Q
  * (Section 2.2; GMRES of Saad and Schultz), zero initial guess, classical

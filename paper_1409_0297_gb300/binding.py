@@ -23,8 +23,8 @@ EXPORTED = [
     "sp_default_opts", "sp_setup", "sp_factor", "sp_apply", "sp_solve", "sp_factor_host",
     "sp_solve_host", "sp_matvec", "sp_green", "sp_qapply", "sp_get_table", "sp_stencil_table",
     "sp_front_sizes", "sp_level_info", "sp_costs", "sp_medium_helmholtz", "sp_medium_schrodinger", "sp_profile",
-    "sp_profile_read", "sp_green_static", "sp_schur_update", "sp_tuning", "sp_destroy",
-    "sp_status_str",
+    "sp_profile_read", "sp_green_static", "sp_schur_update", "sp_tuning", "sp_solve_many",
+    "sp_destroy", "sp_status_str",
 ]
 PROF_CLASSES = ["assemble", "lu_panel", "lu_trsm", "lu_gemm", "qapply", "forward", "backward",
                 "fft", "krylov", "lu_trinv", "lu_tc"]
@@ -34,7 +34,7 @@ class sp_opts(ctypes.Structure):
     _fields_ = [("maxit", ctypes.c_int), ("restart", ctypes.c_int), ("tol", ctypes.c_double),
                 ("pivot_tol", ctypes.c_double), ("device", ctypes.c_int),
                 ("host_threads", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("max_rhs", ctypes.c_int)]
 
 
 class sp_info(ctypes.Structure):
@@ -81,6 +81,7 @@ def _load() -> ctypes.CDLL:
         "sp_schur_update": (I, [I, I, I, I, P, I, ctypes.c_longlong, P, I, ctypes.c_longlong, P, I,
                                 ctypes.c_longlong, I, P]),
         "sp_tuning": (I, [P, I, pI, pI]),
+        "sp_solve_many": (I, [P, I, P, P, ctypes.POINTER(sp_info)]),
         "sp_destroy": (V, [P]),
         "sp_status_str": (ctypes.c_char_p, [I]),
     }
@@ -168,6 +169,20 @@ def sp_solve(ctx: int, f_dev: int, u_dev: int, hist_cap: int = 1024, allow_nocon
     st = LIB.sp_solve(ctx, f_dev, u_dev, ctypes.byref(info))
     _check(st, "sp_solve", (SP_OK, SP_ERR_NOCONV) if allow_noconv else (SP_OK,))
     return _info_dict(info, hist, st)
+
+
+def sp_solve_many(ctx: int, nrhs: int, F_dev: int, U_dev: int, hist_cap: int = 1024,
+                  allow_noconv=False) -> list:
+    """nrhs right-hand sides stacked N apart; one info dict per right-hand side."""
+    infos = (sp_info * nrhs)()
+    hists = []
+    for i in range(nrhs):
+        info, hist = _info(hist_cap)
+        infos[i] = info  # copies the struct, including the pointer to hist
+        hists.append(hist)
+    st = LIB.sp_solve_many(ctx, nrhs, F_dev, U_dev, infos)
+    _check(st, "sp_solve_many", (SP_OK, SP_ERR_NOCONV) if allow_noconv else (SP_OK,))
+    return [_info_dict(infos[i], hists[i], st) for i in range(nrhs)]
 
 
 def sp_solve_host(ctx: int, f_host, u_host, hist_cap: int = 1024, allow_noconv=False) -> dict:
@@ -305,11 +320,13 @@ class Solver:
 
     def __init__(self, d: int, n: int, b: int, s: float, prec: int = SP_PREC_FP64,
                  maxit: int = 500, restart: int = 200, tol: float = 1e-8, device: int = 0,
-                 stream: int = 0, host_threads: int = 0, autotune: bool = False):
+                 stream: int = 0, host_threads: int = 0, autotune: bool = False,
+                 max_rhs: int = 1):
         o = sp_default_opts()
         o.maxit, o.restart, o.tol, o.device = maxit, restart, tol, device
         o.host_threads = host_threads
         o.autotune = 1 if autotune else 0
+        o.max_rhs = max_rhs
         self.d, self.n, self.b, self.s, self.prec = d, n, b, s, prec
         self.N = n ** d
         self.ctx = sp_setup(d, n, b, s, prec, o, stream)
@@ -321,6 +338,16 @@ class Solver:
                 x.is_contiguous() and x.numel() == self.N):
             raise ValueError(f"expected a contiguous CUDA {dtype} tensor of {self.N} entries")
         return x.data_ptr()
+
+    def solve_many(self, F, U, **kw):
+        """F, U: contiguous CUDA complex128 tensors of nrhs x N entries."""
+        import torch
+        nrhs = F.numel() // self.N
+        for x in (F, U):
+            if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.complex128 and
+                    x.is_contiguous() and x.numel() == nrhs * self.N and nrhs >= 1):
+                raise ValueError("expected contiguous CUDA complex128 tensors of nrhs x N entries")
+        return sp_solve_many(self.ctx, nrhs, F.data_ptr(), U.data_ptr(), **kw)
 
     def factor(self, q):
         import torch

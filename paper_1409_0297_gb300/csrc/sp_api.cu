@@ -109,8 +109,9 @@ struct sp_ctx {
   // captured once at set-up on an internal stream and replayed on `stream`
   cudaStream_t cap = nullptr;
   cudaGraphExec_t g_apply = nullptr, g_factor = nullptr;
-  double2* app_in = nullptr;   // fixed input / output of the apply graph
-  double2* app_out = nullptr;
+  double2* app_in = nullptr;   // fixed input / output of the apply graph (max_rhs N: the
+  double2* app_out = nullptr;  // block input and output of sp_solve_many)
+  double2* blk_w = nullptr;    // max_rhs N: operator outputs of sp_solve_many
   double factor_entries = 0, factor_flops = 0, apply_bytes = 0;
 };
 
@@ -289,6 +290,7 @@ void sp_default_opts(sp_opts* o) {
   o->host_threads = 0;
   o->inner_tol = 1e-5;
   o->autotune = 0;
+  o->max_rhs = 1;
 }
 
 const char* sp_status_str(sp_status st) {
@@ -477,6 +479,8 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   if (opts) c->opts = *opts;
   if (c->opts.maxit < 1 || c->opts.restart < 1 || c->opts.restart > 1000 || !(c->opts.tol > 0))
     return SP_ERR_ARG;
+  if (c->opts.max_rhs < 1 || c->opts.max_rhs > sweep_max_vectors()) return SP_ERR_ARG;
+  const size_t RH = (size_t)c->opts.max_rhs;
   c->d = d;
   c->n = n;
   c->b = b;
@@ -577,15 +581,15 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
     SP_CK(dalloc(c.get(), &D.perm, sizeof(int) * (size_t)S.nf * std::max(1, S.k)));
     SP_CK(dalloc(c.get(), &D.piv, sizeof(int) * (size_t)S.nf * std::max(1, S.k)));
     SP_CK(dalloc(c.get(), &D.scale, sizeof(double) * S.nf));
-    SP_CK(dalloc(c.get(), &D.upd, vsz * (size_t)S.nf * std::max(1, S.m - S.k)));
-    SP_CK(dalloc(c.get(), &D.y, vsz * (size_t)S.nf * std::max(1, S.k)));
+    SP_CK(dalloc(c.get(), &D.upd, vsz * RH * (size_t)S.nf * std::max(1, S.m - S.k)));
+    SP_CK(dalloc(c.get(), &D.y, vsz * RH * (size_t)S.nf * std::max(1, S.k)));
     if (factor_panel_width(prec, S.m) == 0) return SP_ERR_ARG;  // front too large to stage
     // few fronts: keep the inverses of the diagonal blocks of L11 and U11 so the
     // sweeps spread over the GPU; in the FP32 form every level does (the block
     // inverses cost little in FP32 and the sweeps become matrix-vector products)
     D.inv = S.nf < 152 || prec == SP_PREC_FP32 || vsz * (size_t)(S.m + S.k) > 192 * 1024;
     if (D.inv) {
-      SP_CK(dalloc(c.get(), &D.tmp, vsz * (size_t)S.nf * S.m));
+      SP_CK(dalloc(c.get(), &D.tmp, vsz * RH * (size_t)S.nf * S.m));
       scratch_bytes = std::max(scratch_bytes, fsz * invert_scratch_elems(S.nf, S.k));
     }
     if (factor_grid_panel(prec, S.m)) gp_words = std::max(gp_words, grid_panel_pub_words(S.nf));
@@ -597,7 +601,7 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   }
   c->apply_bytes = c->factor_entries * fsz;
   if (scratch_bytes) SP_CK(dalloc(c.get(), &c->work.inv, scratch_bytes));
-  SP_CK(dalloc(c.get(), &c->gemv_part, sweep_partial_bytes()));
+  SP_CK(dalloc(c.get(), &c->gemv_part, sweep_partial_bytes((int)RH)));
   if (gp_words) SP_CK(dalloc(c.get(), &c->work.gpub, sizeof(unsigned long long) * gp_words));
   if (pack_floats) {
     SP_CK(dalloc(c.get(), &c->work.packA, sizeof(float) * pack_floats));
@@ -629,7 +633,7 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
       Dn[j] = 1.0 / (4.0 * kPi * kPi * k2 - s) / (double)N;
     }
     SP_CK(upload(c.get(), &P.Dn, Dn));
-    SP_CK(dalloc(c.get(), &P.tmp, sizeof(double2) * N));
+    SP_CK(dalloc(c.get(), &P.tmp, sizeof(double2) * N * RH));
     if (mixed) {
       std::vector<float2> tw32(tw.size());
       for (size_t i = 0; i < tw.size(); ++i) tw32[i] = make_float2((float)tw[i].x, (float)tw[i].y);
@@ -643,31 +647,34 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   }
   // ---- solve workspace
   c->maxv = c->opts.restart + 1;
-  SP_CK(dalloc(c.get(), &c->rhsQ, vsz * N));
+  SP_CK(dalloc(c.get(), &c->rhsQ, vsz * N * RH));
   SP_CK(dalloc(c.get(), &c->status, sizeof(int)));
   SP_CK(dalloc(c.get(), &c->qbuf, sizeof(double) * N));
-  SP_CK(dalloc(c.get(), &c->V, sizeof(double2) * N * c->maxv));
-  SP_CK(dalloc(c.get(), &c->Z, sizeof(double2) * N * c->opts.restart));
-  SP_CK(dalloc(c.get(), &c->H, sizeof(double2) * c->maxv * c->opts.restart));
-  SP_CK(dalloc(c.get(), &c->gam, sizeof(double2) * (c->maxv + 1)));
-  SP_CK(dalloc(c.get(), &c->sn, sizeof(double2) * (c->maxv + 1)));
-  SP_CK(dalloc(c.get(), &c->cs, sizeof(double) * (c->maxv + 1)));
-  SP_CK(dalloc(c.get(), &c->h1, sizeof(double2) * 1024));
-  SP_CK(dalloc(c.get(), &c->h2, sizeof(double2) * 1024));
-  SP_CK(dalloc(c.get(), &c->y, sizeof(double2) * 1024));
-  SP_CK(dalloc(c.get(), &c->nrm, sizeof(double) * 4));
-  SP_CK(dalloc(c.get(), &c->est, sizeof(double) * 4));
-  SP_CK(dalloc(c.get(), &c->g, sizeof(double2) * N));
-  SP_CK(dalloc(c.get(), &c->r, sizeof(double2) * N));
-  SP_CK(dalloc(c.get(), &c->t, sizeof(double2) * N));
+  // Krylov workspace, one slice per right-hand side of sp_solve_many (slice 0 is
+  // sp_solve's)
+  SP_CK(dalloc(c.get(), &c->V, sizeof(double2) * N * c->maxv * RH));
+  SP_CK(dalloc(c.get(), &c->Z, sizeof(double2) * N * c->opts.restart * RH));
+  SP_CK(dalloc(c.get(), &c->H, sizeof(double2) * c->maxv * c->opts.restart * RH));
+  SP_CK(dalloc(c.get(), &c->gam, sizeof(double2) * (c->maxv + 1) * RH));
+  SP_CK(dalloc(c.get(), &c->sn, sizeof(double2) * (c->maxv + 1) * RH));
+  SP_CK(dalloc(c.get(), &c->cs, sizeof(double) * (c->maxv + 1) * RH));
+  SP_CK(dalloc(c.get(), &c->h1, sizeof(double2) * 1024 * RH));
+  SP_CK(dalloc(c.get(), &c->h2, sizeof(double2) * 1024 * RH));
+  SP_CK(dalloc(c.get(), &c->y, sizeof(double2) * 1024 * RH));
+  SP_CK(dalloc(c.get(), &c->nrm, sizeof(double) * 4 * RH));
+  SP_CK(dalloc(c.get(), &c->est, sizeof(double) * 4 * RH));
+  SP_CK(dalloc(c.get(), &c->g, sizeof(double2) * N * RH));
+  SP_CK(dalloc(c.get(), &c->r, sizeof(double2) * N * RH));
+  SP_CK(dalloc(c.get(), &c->t, sizeof(double2) * N * RH));
   SP_CK(dalloc(c.get(), &c->fbuf, sizeof(double2) * N));
   SP_CK(dalloc(c.get(), &c->ubuf, sizeof(double2) * N));
   c->K.nblk = (int)std::min<long>(304, std::max<long>(1, (N + 1023) / 1024));
   SP_CK(dalloc(c.get(), &c->K.partial, sizeof(double2) * (size_t)c->K.nblk * 1024));
   SP_CK(dalloc(c.get(), &c->K.h, sizeof(double2) * 1024));
-  SP_CK(cudaMallocHost(&c->host_sc, 8 * sizeof(double)));
-  SP_CK(dalloc(c.get(), &c->app_in, sizeof(double2) * N));
-  SP_CK(dalloc(c.get(), &c->app_out, sizeof(double2) * N));
+  SP_CK(cudaMallocHost(&c->host_sc, 8 * sizeof(double) * RH));
+  SP_CK(dalloc(c.get(), &c->app_in, sizeof(double2) * N * RH));
+  SP_CK(dalloc(c.get(), &c->app_out, sizeof(double2) * N * RH));
+  if (RH > 1) SP_CK(dalloc(c.get(), &c->blk_w, sizeof(double2) * N * RH));
   SP_CK(cudaMemsetAsync(c->qbuf, 0, sizeof(double) * N, c->stream));
   // only this context's streams are synchronised: a device-wide synchronisation
   // would break a graph capture that another thread's context has in progress
@@ -925,6 +932,170 @@ static sp_status solve_mixed(sp_ctx* c, const double2* f, double2* u, sp_info* i
     info->true_relres = rel;
   }
   return rel <= tol ? SP_OK : SP_ERR_NOCONV;
+}
+
+// z = P^{-1} Q r for nv stacked vectors (direct launches; each vector's result
+// equals apply_direct's for it)
+sp_status apply_block(sp_ctx* c, int nv, const double2* r, double2* z, cudaStream_t st) {
+  SP_CK(q_apply(c->prec, c->d, c->n, c->nl, c->qtypes, c->Tcat, c->Tcat32, r, c->rhsQ, st, nv));
+  for (int l = 0; l <= c->L; ++l)
+    SP_CK(forward_level(c->prec, c->d, c->lv[l], l ? &c->lv[l - 1] : nullptr, c->rhsQ,
+                        c->gemv_part, st, nv, c->N));
+  for (int l = c->L; l >= 0; --l)
+    SP_CK(backward_level(c->prec, c->d, c->lv[l], z, c->gemv_part, st, nv, c->N));
+  return SP_OK;
+}
+
+sp_status sp_solve_many(sp_ctx* c, int nrhs, const void* F_dev, void* U_dev, sp_info* infos) {
+  if (!c || !F_dev || !U_dev || nrhs < 1 || nrhs > c->opts.max_rhs) return SP_ERR_ARG;
+  if (!c->factored) return SP_ERR_STATE;
+  SP_CK(cudaSetDevice(c->opts.device));
+  const long N = c->N;
+  const double2* F = (const double2*)F_dev;
+  double2* U = (double2*)U_dev;
+  if (c->mixed || nrhs == 1) {
+    sp_status worst = SP_OK;
+    for (int r = 0; r < nrhs; ++r) {
+      sp_status s1 = sp_solve(c, F + r * N, U + r * N, infos ? infos + r : nullptr);
+      if (s1 != SP_OK && s1 != SP_ERR_NOCONV) return s1;
+      if (s1 != SP_OK) worst = s1;
+    }
+    return worst;
+  }
+  ProfGuard pg_(c);
+  cudaStream_t st = c->stream;
+  const int restart = c->opts.restart, maxit = c->opts.maxit, mv = c->maxv;
+  const double tol = c->opts.tol;
+  double* hsc = c->host_sc;
+  // per right-hand side r: slices of the Krylov workspace
+  auto V = [&](int r) { return c->V + (long)r * mv * N; };
+  auto Z = [&](int r) { return c->Z + (long)r * restart * N; };
+  auto H = [&](int r) { return c->H + (long)r * mv * restart; };
+  auto GAM = [&](int r) { return c->gam + (long)r * (mv + 1); };
+  auto SN = [&](int r) { return c->sn + (long)r * (mv + 1); };
+  auto CS = [&](int r) { return c->cs + (long)r * (mv + 1); };
+  auto H1 = [&](int r) { return c->h1 + (long)r * 1024; };
+  auto H2 = [&](int r) { return c->h2 + (long)r * 1024; };
+  auto Y = [&](int r) { return c->y + (long)r * 1024; };
+  auto NRM = [&](int r) { return c->nrm + (long)r * 4; };
+  auto EST = [&](int r) { return c->est + (long)r * 4; };
+  auto Gv = [&](int r) { return c->g + (long)r * N; };
+  auto Rv = [&](int r) { return c->r + (long)r * N; };
+  auto Tv = [&](int r) { return c->t + (long)r * N; };
+  struct Rhs {
+    double bnorm = 0, est_rel = 1, true_rel = 1;
+    int j = 0, total = 0, restarts = 0;
+    bool done = false;
+  };
+  std::vector<Rhs> R(nrhs);
+  auto push_hist = [&](int r, double v) {
+    sp_info* in = infos ? infos + r : nullptr;
+    if (in && in->hist && in->hist_len < in->hist_cap) in->hist[in->hist_len++] = v;
+  };
+  if (infos)
+    for (int r = 0; r < nrhs; ++r) {
+      infos[r].iters = 0;
+      infos[r].restarts = 0;
+      infos[r].hist_len = 0;
+      infos[r].s_used = c->s;
+    }
+  // g_r = G f_r, ||g_r||
+  SP_CK(fft_green_apply(c->fft, F, nullptr, false, c->g, st, nrhs));
+  for (int r = 0; r < nrhs; ++r) SP_CK(kr_norm(Gv(r), N, c->K, NRM(r) + 2, st));
+  SP_CK(cudaMemcpy2DAsync(hsc, sizeof(double), c->nrm + 2, 4 * sizeof(double), sizeof(double),
+                          nrhs, cudaMemcpyDeviceToHost, st));
+  SP_CK(cudaMemsetAsync(U, 0, sizeof(double2) * N * nrhs, st));
+  SP_CK(cudaStreamSynchronize(st));
+  for (int r = 0; r < nrhs; ++r) {
+    R[r].bnorm = hsc[r];
+    push_hist(r, 1.0);
+    if (R[r].bnorm == 0.0) {
+      R[r].done = true;
+      R[r].est_rel = R[r].true_rel = 0.0;
+      continue;
+    }
+    SP_CK(cudaMemcpyAsync(Rv(r), Gv(r), sizeof(double2) * N, cudaMemcpyDeviceToDevice, st));
+    SP_CK(cudaMemcpyAsync(NRM(r) + 3, NRM(r) + 2, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    SP_CK(kr_start(Rv(r), N, NRM(r) + 3, V(r), GAM(r), mv + 1, st));
+  }
+  // u_r += Z_r y, true residual, then either stop or restart
+  auto finish_cycle = [&](int r, int k) -> sp_status {
+    Rhs& h = R[r];
+    double2* u = U + (long)r * N;
+    SP_CK(kr_update_solution(H(r), mv, k, GAM(r), Y(r), Z(r), N, N, u, st));
+    SP_CK(fft_green_apply(c->fft, u, c->q, true, Tv(r), st));
+    SP_CK(kr_sub(Gv(r), Tv(r), N, Rv(r), st));
+    SP_CK(kr_norm(Rv(r), N, c->K, NRM(r) + 3, st));
+    SP_CK(cudaMemcpyAsync(hsc, NRM(r) + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SP_CK(cudaStreamSynchronize(st));
+    h.true_rel = hsc[0] / h.bnorm;
+    if (h.true_rel <= tol || h.total >= maxit) {
+      h.done = true;
+    } else {
+      ++h.restarts;
+      h.j = 0;
+      SP_CK(kr_start(Rv(r), N, NRM(r) + 3, V(r), GAM(r), mv + 1, st));
+    }
+    return SP_OK;
+  };
+  std::vector<int> act;
+  for (;;) {
+    act.clear();
+    for (int r = 0; r < nrhs; ++r)
+      if (!R[r].done) act.push_back(r);
+    if (act.empty()) break;
+    const int na = (int)act.size();
+    const size_t vb = sizeof(double2) * N;
+    for (int s = 0; s < na; ++s)
+      SP_CK(cudaMemcpyAsync(c->app_in + s * N, V(act[s]) + (long)R[act[s]].j * N, vb,
+                            cudaMemcpyDeviceToDevice, st));
+    sp_status ss = apply_block(c, na, c->app_in, c->app_out, st);
+    if (ss != SP_OK) return ss;
+    SP_CK(fft_green_apply(c->fft, c->app_out, c->q, true, c->blk_w, st, na));
+    for (int s = 0; s < na; ++s) {
+      const int r = act[s], j = R[r].j;
+      double2* w = V(r) + (long)(j + 1) * N;
+      SP_CK(cudaMemcpyAsync(Z(r) + (long)j * N, c->app_out + s * N, vb, cudaMemcpyDeviceToDevice,
+                            st));
+      SP_CK(cudaMemcpyAsync(w, c->blk_w + s * N, vb, cudaMemcpyDeviceToDevice, st));
+      // classical Gram-Schmidt, twice
+      SP_CK(kr_dots(V(r), N, j + 1, w, N, c->K, H1(r), st));
+      SP_CK(kr_update_dots(V(r), N, j + 1, w, N, H1(r), c->K, H2(r), st));
+      SP_CK(kr_update_dots(V(r), N, j + 1, w, N, H2(r), c->K, nullptr, st));
+      SP_CK(kr_norm(w, N, c->K, NRM(r), st));
+      SP_CK(kr_givens(H(r), mv, j, H1(r), H2(r), NRM(r), CS(r), SN(r), GAM(r), EST(r), st));
+    }
+    SP_CK(cudaMemcpyAsync(hsc, c->est, 4 * sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+    SP_CK(cudaStreamSynchronize(st));
+    std::vector<double> est(hsc, hsc + 4 * nrhs);
+    for (int s = 0; s < na; ++s) {
+      const int r = act[s];
+      Rhs& h = R[r];
+      ++h.total;
+      const int k = h.j + 1;
+      h.est_rel = est[4 * r] / h.bnorm;
+      push_hist(r, h.est_rel);
+      if (h.est_rel <= tol || h.total >= maxit || est[4 * r + 1] == 0.0 || k == restart) {
+        sp_status fs = finish_cycle(r, k);
+        if (fs != SP_OK) return fs;
+      } else {
+        double2* w = V(r) + (long)k * N;
+        SP_CK(kr_scale(w, N, NRM(r), w, st));
+        h.j = k;
+      }
+    }
+  }
+  bool all = true;
+  for (int r = 0; r < nrhs; ++r) {
+    if (infos) {
+      infos[r].iters = R[r].total;
+      infos[r].restarts = R[r].restarts;
+      infos[r].est_relres = R[r].est_rel;
+      infos[r].true_relres = R[r].true_rel;
+    }
+    if (!(R[r].true_rel <= tol)) all = false;
+  }
+  return all ? SP_OK : SP_ERR_NOCONV;
 }
 
 sp_status sp_solve_host(sp_ctx* c, const void* f_host, void* u_host, sp_info* info) {

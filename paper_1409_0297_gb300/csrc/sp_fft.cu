@@ -57,7 +57,8 @@ struct PassArgs {
   const VT* addx;  // POST_ADD
   const VT* tw;         // w_n^t = exp(-2 pi i t / n), t < n / 2
   long S;               // stride between consecutive elements of a line
-  long nlines;          // number of lines of this axis
+  long nlines;          // number of lines of this axis, all vectors
+  long vlines, vstride; // lines per vector, entries per vector (vectors stacked)
   int n, W, pad;
   int R, M, logM;       // n = R M, R in {1, 3}, M = 2^logM
   int mode;             // 0 forward, 1 inverse, 2 middle (forward, scale, inverse)
@@ -81,11 +82,17 @@ __device__ __forceinline__ VT tw_at(const PassArgs<VT>& a, int t) {
   return v;
 }
 
-// global address of element i of line t
+// address of element i of line t within its vector (q and the symbol are shared
+// by every vector), and the offset of that vector
 template <class VT>
 __device__ __forceinline__ long line_addr(const PassArgs<VT>& a, long t, int i) {
-  long lo = t % a.S, hi = t / a.S;
+  const long tl = t % a.vlines;
+  long lo = tl % a.S, hi = tl / a.S;
   return lo + hi * a.S * a.n + (long)i * a.S;
+}
+template <class VT>
+__device__ __forceinline__ long vec_off(const PassArgs<VT>& a, long t) {
+  return (t / a.vlines) * a.vstride;
 }
 
 // radix-2 stages of the W R sub-lines of length M (sub-line r of row w at
@@ -202,7 +209,7 @@ __global__ void __launch_bounds__(kThreads) fft_pass_kernel(PassArgs<VT> a) {
     long t = t0 + w;
     if (t >= a.nlines) continue;
     long g = line_addr(a, t, i);
-    VT v = a.in[g];
+    VT v = a.in[vec_off(a, t) + g];
     if (a.q) {
       T qq = a.q[g];
       v.x *= qq;
@@ -253,7 +260,7 @@ __global__ void __launch_bounds__(kThreads) fft_pass_kernel(PassArgs<VT> a) {
     }
     long t = t0 + w;
     if (t >= a.nlines) continue;
-    long g = line_addr(a, t, i);
+    long g = vec_off(a, t) + line_addr(a, t, i);
     int pos = bitrev_store ? perm_pos<R>(a, i) : i;
     VT v = sm[w * ld + pos];
     if (a.addx) v = cadd(v, a.addx[g]);
@@ -274,7 +281,7 @@ int lines_per_cta(int n, long nlines, int esize) {
 template <class VT>
 cudaError_t run_pass(int d, int n, const VT* tw, const typename Real<VT>::T* Dn, int axis,
                      int mode, const VT* in, VT* out, const typename Real<VT>::T* q,
-                     const VT* addx, cudaStream_t st) {
+                     const VT* addx, int nvec, cudaStream_t st) {
   PassArgs<VT> a{};
   a.mode = mode;
   a.in = in;
@@ -293,7 +300,9 @@ cudaError_t run_pass(int d, int n, const VT* tw, const typename Real<VT>::T* Dn,
   a.S = S;
   long N = 1;
   for (int i = 0; i < d; ++i) N *= n;
-  a.nlines = N / n;
+  a.vlines = N / n;
+  a.vstride = N;
+  a.nlines = a.vlines * nvec;
   a.W = lines_per_cta(n, a.nlines, (int)sizeof(VT));
   // axis > 0 lines are grouped W at a time inside one S-block: W must divide S
   if (axis > 0)
@@ -313,7 +322,8 @@ cudaError_t run_pass(int d, int n, const VT* tw, const typename Real<VT>::T* Dn,
     fft_pass_kernel<VT, 3><<<(unsigned)grid, kThreads, smem, st>>>(a);
   else
     fft_pass_kernel<VT, 1><<<(unsigned)grid, kThreads, smem, st>>>(a);
-  ps.done((double)N * (2 * es + (q ? es / 2 : 0.0) + (mode == 2 ? es / 2 : 0.0) + (addx ? es : 0.0)),
+  ps.done((double)N * nvec * (2 * es + (q ? es / 2 : 0.0) + (mode == 2 ? es / 2 : 0.0) +
+                             (addx ? es : 0.0)),
           1, st);
   return cudaGetLastError();
 }
@@ -321,21 +331,21 @@ cudaError_t run_pass(int d, int n, const VT* tw, const typename Real<VT>::T* Dn,
 template <class VT>
 cudaError_t green_apply_t(int d, int n, const VT* tw, const typename Real<VT>::T* Dn,
                           VT* tmp, const VT* x, const typename Real<VT>::T* q, bool add_x, VT* out,
-                          cudaStream_t st) {
+                          int nvec, cudaStream_t st) {
   cudaError_t e;
   // forward along axes 0..d-2, middle pass on axis d-1, inverse along d-2..0
   const VT* src = x;
   for (int ax = 0; ax < d - 1; ++ax) {
-    e = run_pass<VT>(d, n, tw, Dn, ax, 0, src, tmp, ax == 0 ? q : nullptr, nullptr, st);
+    e = run_pass<VT>(d, n, tw, Dn, ax, 0, src, tmp, ax == 0 ? q : nullptr, nullptr, nvec, st);
     if (e != cudaSuccess) return e;
     src = tmp;
   }
-  e = run_pass<VT>(d, n, tw, Dn, d - 1, 2, src, tmp, nullptr, nullptr, st);
+  e = run_pass<VT>(d, n, tw, Dn, d - 1, 2, src, tmp, nullptr, nullptr, nvec, st);
   if (e != cudaSuccess) return e;
   for (int ax = d - 2; ax >= 0; --ax) {
     bool last = (ax == 0);
     e = run_pass<VT>(d, n, tw, Dn, ax, 1, tmp, last ? out : tmp, nullptr,
-                     (last && add_x) ? x : nullptr, st);
+                     (last && add_x) ? x : nullptr, nvec, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -349,13 +359,13 @@ __global__ void to_float_kernel(const double* a, float* b, long N) {
 }  // namespace
 
 cudaError_t fft_green_apply(const FftPlan& P, const double2* x, const double* q, bool add_x,
-                            double2* out, cudaStream_t st) {
-  return green_apply_t<double2>(P.d, P.n, P.tw, P.Dn, P.tmp, x, q, add_x, out, st);
+                            double2* out, cudaStream_t st, int nvec) {
+  return green_apply_t<double2>(P.d, P.n, P.tw, P.Dn, P.tmp, x, q, add_x, out, nvec, st);
 }
 
 cudaError_t fft_green_apply32(const FftPlan& P, const float2* x, const float* q, bool add_x,
                               float2* out, cudaStream_t st) {
-  return green_apply_t<float2>(P.d, P.n, P.tw32, P.Dn32, P.tmp32, x, q, add_x, out, st);
+  return green_apply_t<float2>(P.d, P.n, P.tw32, P.Dn32, P.tmp32, x, q, add_x, out, 1, st);
 }
 
 cudaError_t to_float(const double* a, float* b, long N, cudaStream_t st) {

@@ -84,14 +84,15 @@ struct FftPlan {
   int d = 0, n = 0, logn = 0;  // n = 2^p or 3 2^p
   double2* tw = nullptr;   // exp(-2 pi i t / n), t < n/2
   double* Dn = nullptr;    // 1 / (4 pi^2 |k|^2 - s) / N, flat
-  double2* tmp = nullptr;  // N work
+  double2* tmp = nullptr;  // N work (times the context's max_rhs)
   float2* tw32 = nullptr;  // FP32 copies for the mixed-precision inner solve
   float* Dn32 = nullptr;
   float2* tmp32 = nullptr;
 };
 // w = x + G (q x) when q != null and add_x; g = G f when q == null and !add_x.
+// nvec vectors stacked N apart (the plan's tmp holds nvec N entries).
 cudaError_t fft_green_apply(const FftPlan& P, const double2* x, const double* q, bool add_x,
-                            double2* out, cudaStream_t st);
+                            double2* out, cudaStream_t st, int nvec = 1);
 cudaError_t fft_green_apply32(const FftPlan& P, const float2* x, const float* q, bool add_x,
                               float2* out, cudaStream_t st);
 cudaError_t to_float(const double* a, float* b, long N, cudaStream_t st);
@@ -153,14 +154,19 @@ struct QTypeDev {
 };
 // y = Q r = r_S - T_S r_beta(S) per set instance (VT = double2 (FP64) or float2
 // (FP32) for y; r is complex128).
+// nv stacked vectors (1 <= nv <= sweep_max_vectors()): global vectors (r, y, x,
+// the stencil output) N apart, a level's work vectors (tmp nf m, y nf k, upd
+// nf (m - k)) vector-major; each vector's result equals its single-vector result.
 cudaError_t q_apply(int prec, int d, int n, int nl, const std::vector<QTypeDev>& types,
                     const double* Tcat, const float* Tcat32, const double2* r, void* y,
-                    cudaStream_t st);
-// part: sweep_partial_bytes() of work for the split row products (shared by levels)
+                    cudaStream_t st, int nv = 1);
+// part: sweep_partial_bytes(nv) of work for the split row products (shared by levels)
 cudaError_t forward_level(int prec, int d, DevLevel& L, const DevLevel* child, const void* rhsQ,
-                          void* part, cudaStream_t st);
-cudaError_t backward_level(int prec, int d, DevLevel& L, double2* x, void* part, cudaStream_t st);
-size_t sweep_partial_bytes();
+                          void* part, cudaStream_t st, int nv = 1, long N = 0);
+cudaError_t backward_level(int prec, int d, DevLevel& L, double2* x, void* part, cudaStream_t st,
+                           int nv = 1, long N = 0);
+size_t sweep_partial_bytes(int nv = 1);
+int sweep_max_vectors();
 
 // ---------------------------------------------------------------- Krylov (sp_krylov.cu)
 struct KrylovWork {

@@ -55,13 +55,16 @@ __device__ __forceinline__ void axpy(VT& acc, T a, VT x) {  // acc += a * x
 
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-// y[S instance] = r[S instance] - T_t r[beta instance]; one CTA per instance of type t.
+// y[S instance] = r[S instance] - T_t r[beta instance]; one CTA per instance of type t
+// (and per stacked vector, blockIdx.y, vectors N apart).
 template <class VT, class T>
 __global__ void qapply_kernel(int d, int n, int nl, int nS, int nB, const int* __restrict__ Soff,
                               const int* __restrict__ Boff, const T* __restrict__ Tt,
-                              const double2* __restrict__ r, VT* y) {
+                              const double2* __restrict__ r, VT* y, long N) {
   extern __shared__ unsigned char smraw[];
   VT* rb = reinterpret_cast<VT*>(smraw);
+  r += blockIdx.y * N;
+  y += blockIdx.y * N;
   int box = blockIdx.x, o[3] = {0, 0, 0};
   for (int a = 0; a < d; ++a) {
     o[a] = (box % nl) * (n / nl);
@@ -126,13 +129,20 @@ template <class VT, class T>
 __global__ void __launch_bounds__(256) forward_kernel(
     int d, const T* __restrict__ fronts, int m, int k, int nb1, const int* __restrict__ gidx,
     const int* __restrict__ perm, const VT* __restrict__ rhsQ, const VT* __restrict__ cupd, int mc,
-    int kc, const int* __restrict__ ea_map, VT* upd, VT* yout) {
+    int kc, const int* __restrict__ ea_map, VT* upd, VT* yout, long N, long custr) {
   extern __shared__ unsigned char smraw[];
   VT* b = reinterpret_cast<VT*>(smraw);  // m
   VT* b1 = b + m;                         // k (permuted eliminated part)
   __shared__ T Ld[kBS][kBS + 1];
   __shared__ VT yd[kBS];
   const int f = blockIdx.x;
+  {  // stacked vector blockIdx.y
+    const long v = blockIdx.y, nf = gridDim.x;
+    rhsQ += v * N;
+    if (cupd) cupd += v * custr;
+    upd += v * nf * (m - k);
+    yout += v * nf * k;
+  }
   const T* A = fronts + (long)f * m * m;
   gather_rhs(d, f, m, k, nb1, gidx, rhsQ, cupd, mc, kc, ea_map, b);
   const int* pr = perm + (long)f * k;
@@ -181,9 +191,12 @@ __global__ void __launch_bounds__(256) forward_kernel(
 template <class VT, class T>
 __global__ void __launch_bounds__(256) backward_kernel(const T* __restrict__ fronts, int m, int k,
                                                         const int* __restrict__ gidx,
-                                                        const VT* __restrict__ yin, double2* x) {
+                                                        const VT* __restrict__ yin, double2* x,
+                                                        long N) {
   extern __shared__ unsigned char smraw[];
   VT* xb = reinterpret_cast<VT*>(smraw);  // m: x1 then x2
+  yin += (long)blockIdx.y * gridDim.x * k;
+  x += blockIdx.y * N;
   __shared__ T Ud[kBS][kBS + 1];
   __shared__ VT xd[kBS];
   const int f = blockIdx.x;
@@ -240,10 +253,13 @@ template <class VT>
 __global__ void __launch_bounds__(256) inv_gather_kernel(
     int d, int m, int k, int nb1, const int* __restrict__ gidx, const int* __restrict__ perm,
     const VT* __restrict__ rhsQ, const VT* __restrict__ cupd, int mc, int kc,
-    const int* __restrict__ ea_map, VT* tmp) {
+    const int* __restrict__ ea_map, VT* tmp, long N, long custr) {
   extern __shared__ unsigned char smraw[];
   VT* b = reinterpret_cast<VT*>(smraw);
   const int f = blockIdx.x;
+  rhsQ += blockIdx.y * N;
+  if (cupd) cupd += blockIdx.y * custr;
+  tmp += (long)blockIdx.y * gridDim.x * m;
   gather_rhs(d, f, m, k, nb1, gidx, rhsQ, cupd, mc, kc, ea_map, b);
   const int* pr = perm + (long)f * k;
   VT* t = tmp + (long)f * m;
@@ -258,8 +274,12 @@ template <class VT>
 __global__ void __launch_bounds__(1024) inv_gather_global_kernel(
     int d, int m, int k, int nb1, const int* __restrict__ gidx, const int* __restrict__ perm,
     const VT* __restrict__ rhsQ, const VT* __restrict__ cupd, int mc, int kc,
-    const int* __restrict__ ea_map, VT* tmp, VT* ybuf) {
+    const int* __restrict__ ea_map, VT* tmp, VT* ybuf, long N, long custr) {
   const int f = blockIdx.x;
+  rhsQ += blockIdx.y * N;
+  if (cupd) cupd += blockIdx.y * custr;
+  tmp += (long)blockIdx.y * gridDim.x * m;
+  ybuf += (long)blockIdx.y * gridDim.x * k;
   VT* t = tmp + (long)f * m;
   for (int v = threadIdx.x; v < m; v += blockDim.x)
     t[v] = (v < k) ? rhsQ[gidx[(long)f * m + v]] : vzero<VT>();
@@ -309,9 +329,16 @@ template <class VT, class T, int RB>
 __global__ void __launch_bounds__(256) inv_gemv_kernel(int mode, const T* __restrict__ fronts,
                                                         int m, int k, int j0, int j1,
                                                         const int* __restrict__ gidx, VT* tmp,
-                                                        VT* y, VT* upd, double2* x) {
+                                                        VT* y, VT* upd, double2* x, long N) {
   extern __shared__ unsigned char smraw[];
   VT* v = reinterpret_cast<VT*>(smraw);  // input vector entries [vlo, vhi)
+  {  // stacked vector blockIdx.z
+    const long vz = blockIdx.z, nf = gridDim.y;
+    tmp += vz * nf * m;
+    y += vz * nf * k;
+    upd += vz * nf * (m - k);
+    if (x) x += vz * N;
+  }
   constexpr int CL = 256 / RB;  // column lanes per row
   __shared__ VT red[CL][RB + 1];
   const int f = blockIdx.y;
@@ -413,25 +440,34 @@ __device__ __forceinline__ void gemv_out(int op, int m, int k, int r, VT s, VT* 
     tf[r] = VT{o.x - s.x, o.y - s.y};
   }
 }
-template <class VT, class T>
+// NV: vectors per thread (compile-time bound; nv <= NV run), stacked vector-major
+// (level work vectors nf m / nf k / nf (m - k) apart, global ones N apart).  Each
+// vector is summed in the same order for every NV, so stacking vectors never
+// changes a result.
+template <class VT, class T, int NV>
 __global__ void __launch_bounds__(256) gemv_kernel(GemvArgs ga, const T* __restrict__ fronts,
                                                     int m, int k, const int* __restrict__ gidx,
                                                     VT* tmp, VT* y, VT* upd, const double2* x,
-                                                    int nsplit, VT* part) {
-  __shared__ VT vs[1024];
+                                                    int nsplit, VT* part, int nv, long N) {
+  constexpr int CH = 1024 / NV;  // columns of one staged chunk
+  __shared__ VT vs[CH * NV];     // vs[j NV + v]
   const int f = blockIdx.z, sp = blockIdx.y, nf = gridDim.z;
   const T* A = fronts + (long)f * m * m;
-  VT* tf = tmp + (long)f * m;
-  VT* yf = y + (long)f * k;
+  const long tstr = (long)nf * m, ystr = (long)nf * k, ustr = (long)nf * (m - k);
   const int r = ga.rlo + blockIdx.x * 256 + threadIdx.x;
   const int per = (ga.vhi - ga.vlo + nsplit - 1) / nsplit;
   const int cb = ga.vlo + sp * per, ce = min(ga.vhi, cb + per);
-  VT acc = vzero<VT>();
-  for (int c0 = cb; c0 < ce; c0 += 1024) {
-    const int cn = min(1024, ce - c0);
+  VT acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = vzero<VT>();
+  for (int c0 = cb; c0 < ce; c0 += CH) {
+    const int cn = min(CH, ce - c0);
     __syncthreads();
-    for (int i = threadIdx.x; i < cn; i += 256)
-      vs[i] = ga.vsrc ? from_d2<VT>(x[gidx[(long)f * m + c0 + i]]) : yf[c0 + i];
+    for (int i = threadIdx.x; i < cn * nv; i += 256) {
+      const int j = i / nv, v = i - j * nv;
+      vs[j * NV + v] = ga.vsrc ? from_d2<VT>(x[v * N + gidx[(long)f * m + c0 + j]])
+                               : y[v * ystr + (long)f * k + c0 + j];
+    }
     __syncthreads();
     if (r < ga.rhi) {
       const T* Ar = A + r + (long)c0 * m;
@@ -441,33 +477,49 @@ __global__ void __launch_bounds__(256) gemv_kernel(GemvArgs ga, const T* __restr
 #pragma unroll
         for (int u = 0; u < 8; ++u) a[u] = Ar[(long)(j + u) * m];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) axpy(acc, a[u], vs[j + u]);
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int v = 0; v < NV; ++v)
+            if (v < nv) axpy(acc[v], a[u], vs[(j + u) * NV + v]);
       }
-      for (; j < cn; ++j) axpy(acc, Ar[(long)j * m], vs[j]);
+      for (; j < cn; ++j) {
+        const T a = Ar[(long)j * m];
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+          if (v < nv) axpy(acc[v], a, vs[j * NV + v]);
+      }
     }
   }
   if (r >= ga.rhi) return;
-  if (nsplit == 1) gemv_out(ga.op, m, k, r, acc, tf, yf, upd, f);
-  else part[((long)sp * nf + f) * (ga.rhi - ga.rlo) + (r - ga.rlo)] = acc;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    if (v >= nv) break;
+    if (nsplit == 1)
+      gemv_out(ga.op, m, k, r, acc[v], tmp + v * tstr + (long)f * m, y + v * ystr + (long)f * k,
+               upd + v * ustr, f);
+    else
+      part[(((long)sp * nv + v) * nf + f) * (ga.rhi - ga.rlo) + (r - ga.rlo)] = acc[v];
+  }
 }
 template <class VT>
 __global__ void gemv_finish_kernel(GemvArgs ga, int m, int k, VT* tmp, VT* y, VT* upd, int nsplit,
                                    const VT* __restrict__ part) {
-  const int f = blockIdx.y, nf = gridDim.y;
+  const int f = blockIdx.y, nf = gridDim.y, v = blockIdx.z, nv = gridDim.z;
   const int r = ga.rlo + blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= ga.rhi) return;
   VT s = vzero<VT>();
   for (int sp = 0; sp < nsplit; ++sp) {
-    const VT p = part[((long)sp * nf + f) * (ga.rhi - ga.rlo) + (r - ga.rlo)];
+    const VT p = part[(((long)sp * nv + v) * nf + f) * (ga.rhi - ga.rlo) + (r - ga.rlo)];
     s.x += p.x;
     s.y += p.y;
   }
-  gemv_out(ga.op, m, k, r, s, tmp + (long)f * m, y + (long)f * k, upd, f);
+  gemv_out(ga.op, m, k, r, s, tmp + (long)v * nf * m + (long)f * m,
+           y + (long)v * nf * k + (long)f * k, upd + (long)v * nf * (m - k), f);
 }
 
 template <class VT>
 cudaError_t q_apply_t(int d, int n, int nl, const std::vector<QTypeDev>& types, const void* Tt,
-                      const double2* r, VT* y, cudaStream_t st) {
+                      const double2* r, VT* y, int nv, long N, cudaStream_t st) {
   using T = typename Scalar<VT>::T;
   long ninst = 1;
   for (int a = 0; a < d; ++a) ninst *= nl;
@@ -475,9 +527,11 @@ cudaError_t q_apply_t(int d, int n, int nl, const std::vector<QTypeDev>& types, 
   double bytes = 0;
   for (const auto& ty : types) {
     size_t smem = sizeof(VT) * (ty.nB > 0 ? ty.nB : 1);
-    qapply_kernel<VT, T><<<(unsigned)ninst, 128, smem, st>>>(
-        d, n, nl, ty.nS, ty.nB, ty.S, ty.Bt, (const T*)Tt + ty.t_off, r, y);
-    bytes += (double)ninst * ty.nS * (sizeof(double2) + sizeof(VT)) + sizeof(T) * ty.nS * ty.nB;
+    dim3 g((unsigned)ninst, nv);
+    qapply_kernel<VT, T><<<g, 128, smem, st>>>(d, n, nl, ty.nS, ty.nB, ty.S, ty.Bt,
+                                               (const T*)Tt + ty.t_off, r, y, N);
+    bytes += (double)ninst * nv * ty.nS * (sizeof(double2) + sizeof(VT)) +
+             sizeof(T) * ty.nS * ty.nB;
   }
   ps.done(bytes, (int)types.size(), st);
   return cudaGetLastError();
@@ -495,6 +549,7 @@ void set_attrs() {
 }
 
 constexpr int kGemvTarget = 1216;  // CTAs a row-parallel product aims for (8 per SM)
+constexpr int kMaxVec = 8;         // stacked vectors of one sweep launch
 
 int gemv_splits(int rows, int cols, int nf) {
   const long tiles = (long)((rows + 255) / 256) * nf;
@@ -502,77 +557,92 @@ int gemv_splits(int rows, int cols, int nf) {
   return (int)std::max<long>(1, std::min<long>((kGemvTarget + tiles - 1) / tiles, cols / 128));
 }
 
-// One off-diagonal product (gemv_kernel, + gemv_finish_kernel when split).
+// One off-diagonal product (gemv_kernel, + gemv_finish_kernel when split) for nv
+// stacked vectors.
 template <class VT, class T>
-int gemv(const GemvArgs& ga, DevLevel& L, const double2* x, void* part, cudaStream_t st) {
+int gemv(const GemvArgs& ga, DevLevel& L, const double2* x, void* part, int nv, long N,
+         cudaStream_t st) {
   const int rows = ga.rhi - ga.rlo, cols = ga.vhi - ga.vlo;
   if (rows <= 0) return 0;
   int ns = cols > 0 ? gemv_splits(rows, cols, L.nf) : 1;
   if (!part) ns = 1;
   dim3 g((rows + 255) / 256, ns, L.nf);
-  gemv_kernel<VT, T><<<g, 256, 0, st>>>(ga, (const T*)L.front, L.m, L.k, L.gidx, (VT*)L.tmp,
-                                        (VT*)L.y, (VT*)L.upd, x, ns, (VT*)part);
+  if (nv == 1)
+    gemv_kernel<VT, T, 1><<<g, 256, 0, st>>>(ga, (const T*)L.front, L.m, L.k, L.gidx, (VT*)L.tmp,
+                                             (VT*)L.y, (VT*)L.upd, x, ns, (VT*)part, 1, N);
+  else
+    gemv_kernel<VT, T, kMaxVec><<<g, 256, 0, st>>>(ga, (const T*)L.front, L.m, L.k, L.gidx,
+                                                   (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x, ns,
+                                                   (VT*)part, nv, N);
   if (ns == 1) return 1;
-  dim3 gf((rows + 255) / 256, L.nf);
+  dim3 gf((rows + 255) / 256, L.nf, nv);
   gemv_finish_kernel<VT><<<gf, 256, 0, st>>>(ga, L.m, L.k, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, ns,
                                              (const VT*)part);
   return 2;
 }
 
-// One inv_gemv launch over rows [rlo, rhi) of every front: 16 rows per CTA, or 4
-// rows per CTA (64 column lanes) when that leaves fewer CTAs than SMs.
+// One inv_gemv launch over rows [rlo, rhi) of every front and stacked vector: 16
+// rows per CTA, or 4 rows per CTA (64 column lanes) when that leaves fewer CTAs
+// than SMs.
 template <class VT, class T>
 void inv_gemv(int mode, DevLevel& L, int j0, int j1, int rlo, int rhi, size_t smem, double2* x,
-              cudaStream_t st) {
+              int nv, long N, cudaStream_t st) {
   const int rows = rhi - rlo;
   if ((long)((rows + 15) / 16) * L.nf >= 152) {
-    dim3 g((rows + 15) / 16, L.nf);
+    dim3 g((rows + 15) / 16, L.nf, nv);
     inv_gemv_kernel<VT, T, 16><<<g, 256, smem, st>>>(mode, (const T*)L.front, L.m, L.k, j0, j1,
-                                                     L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x);
+                                                     L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x,
+                                                     N);
   } else {
-    dim3 g((rows + 3) / 4, L.nf);
+    dim3 g((rows + 3) / 4, L.nf, nv);
     inv_gemv_kernel<VT, T, 4><<<g, 256, smem, st>>>(mode, (const T*)L.front, L.m, L.k, j0, j1,
-                                                    L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x);
+                                                    L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x,
+                                                    N);
   }
 }
 
 template <class VT>
 cudaError_t forward_t(int d, DevLevel& L, const DevLevel* child, const void* rhsQ, void* part,
-                      cudaStream_t st) {
+                      int nv, long N, cudaStream_t st) {
   using T = typename Scalar<VT>::T;
   static bool attr = false;
   if (!attr) {
     set_attrs<VT, T>();
     attr = true;
   }
+  if (nv < 1 || nv > kMaxVec) return cudaErrorInvalidValue;
   const double kk = L.k, mk = L.m - L.k;
   ProfScope ps(PROF_FORWARD, st);
   const VT* cup = child ? (const VT*)child->upd : nullptr;
+  const long custr = child ? (long)child->nf * (child->m - child->k) : 0;
   int launches = 1;
   if (!L.inv) {
-    forward_kernel<VT, T><<<L.nf, 256, sweep_smem(L.m, L.k, sizeof(VT)), st>>>(
+    dim3 g(L.nf, nv);
+    forward_kernel<VT, T><<<g, 256, sweep_smem(L.m, L.k, sizeof(VT)), st>>>(
         d, (const T*)L.front, L.m, L.k, L.nb1, L.gidx, L.perm, (const VT*)rhsQ, cup, L.mc, L.kc,
-        L.ea_map, (VT*)L.upd, (VT*)L.y);
+        L.ea_map, (VT*)L.upd, (VT*)L.y, N, custr);
   } else {
+    dim3 g(L.nf, nv);
     if (sizeof(VT) * (size_t)L.m <= kVecSmem)
-      inv_gather_kernel<VT><<<L.nf, 256, sizeof(VT) * L.m, st>>>(
+      inv_gather_kernel<VT><<<g, 256, sizeof(VT) * L.m, st>>>(
           d, L.m, L.k, L.nb1, L.gidx, L.perm, (const VT*)rhsQ, cup, L.mc, L.kc, L.ea_map,
-          (VT*)L.tmp);
+          (VT*)L.tmp, N, custr);
     else
-      inv_gather_global_kernel<VT><<<L.nf, 1024, 0, st>>>(d, L.m, L.k, L.nb1, L.gidx, L.perm,
-                                                           (const VT*)rhsQ, cup, L.mc, L.kc,
-                                                           L.ea_map, (VT*)L.tmp, (VT*)L.y);
+      inv_gather_global_kernel<VT><<<g, 1024, 0, st>>>(d, L.m, L.k, L.nb1, L.gidx, L.perm,
+                                                        (const VT*)rhsQ, cup, L.mc, L.kc,
+                                                        L.ea_map, (VT*)L.tmp, (VT*)L.y, N,
+                                                        custr);
     launches = 1;
     // right-looking: after the diagonal block [j0, j1) of y, the rows below take
     // that column block's contribution; the last block's rows are those of L21,
     // which hand their result to the parent as the update vector
     for (int j0 = 0; j0 < L.k; j0 += kInvBlockSize) {
       const int j1 = min(L.k, j0 + kInvBlockSize);
-      inv_gemv<VT, T>(0, L, j0, j1, j0, j1, sizeof(VT) * (j1 - j0), nullptr, st);
+      inv_gemv<VT, T>(0, L, j0, j1, j0, j1, sizeof(VT) * (j1 - j0), nullptr, nv, N, st);
       ++launches;
       if (j1 < L.m) {
         const GemvArgs ga{j1, L.m, j0, j1, 0, j1 == L.k ? 1 : 0};
-        launches += gemv<VT, T>(ga, L, nullptr, part, st);
+        launches += gemv<VT, T>(ga, L, nullptr, part, nv, N, st);
       }
     }
   }
@@ -581,34 +651,36 @@ cudaError_t forward_t(int d, DevLevel& L, const DevLevel* child, const void* rhs
 }
 
 template <class VT>
-cudaError_t backward_t(DevLevel& L, double2* x, void* part, cudaStream_t st) {
+cudaError_t backward_t(DevLevel& L, double2* x, void* part, int nv, long N, cudaStream_t st) {
   using T = typename Scalar<VT>::T;
+  if (nv < 1 || nv > kMaxVec) return cudaErrorInvalidValue;
   const double kk = L.k, mk = L.m - L.k;
   ProfScope ps(PROF_BACKWARD, st);
   int launches = 1;
   if (!L.inv) {
-    backward_kernel<VT, T><<<L.nf, 256, sizeof(VT) * (size_t)L.m, st>>>(
-        (const T*)L.front, L.m, L.k, L.gidx, (const VT*)L.y, x);
+    dim3 g(L.nf, nv);
+    backward_kernel<VT, T><<<g, 256, sizeof(VT) * (size_t)L.m, st>>>(
+        (const T*)L.front, L.m, L.k, L.gidx, (const VT*)L.y, x, N);
   } else {
     launches = 0;
     if (L.m > L.k) {
       const GemvArgs ga{0, L.k, L.k, L.m, 1, 2};  // t = y1 - U12 x2
-      launches += gemv<VT, T>(ga, L, x, part, st);
+      launches += gemv<VT, T>(ga, L, x, part, nv, N, st);
     } else {
-      // root: t = y1
-      cudaMemcpy2DAsync(L.tmp, sizeof(VT) * L.m, L.y, sizeof(VT) * L.k, sizeof(VT) * L.k, L.nf,
-                        cudaMemcpyDeviceToDevice, st);
+      // root: t = y1 (the stacked vectors' fronts are consecutive rows of both)
+      cudaMemcpy2DAsync(L.tmp, sizeof(VT) * L.m, L.y, sizeof(VT) * L.k, sizeof(VT) * L.k,
+                        (size_t)L.nf * nv, cudaMemcpyDeviceToDevice, st);
     }
     // right-looking: after the diagonal block [j0, j1) of x1, the rows above take
     // that column block's contribution
     const int nbk = (L.k + kInvBlockSize - 1) / kInvBlockSize;
     for (int bi = nbk - 1; bi >= 0; --bi) {
       const int j0 = bi * kInvBlockSize, j1 = min(L.k, j0 + kInvBlockSize);
-      inv_gemv<VT, T>(3, L, j0, j1, j0, j1, sizeof(VT) * (j1 - j0), x, st);
+      inv_gemv<VT, T>(3, L, j0, j1, j0, j1, sizeof(VT) * (j1 - j0), x, nv, N, st);
       ++launches;
       if (j0 > 0) {
         const GemvArgs ga{0, j0, j0, j1, 0, 0};
-        launches += gemv<VT, T>(ga, L, x, part, st);
+        launches += gemv<VT, T>(ga, L, x, part, nv, N, st);
       }
     }
   }
@@ -620,23 +692,31 @@ cudaError_t backward_t(DevLevel& L, double2* x, void* part, cudaStream_t st) {
 
 cudaError_t q_apply(int prec, int d, int n, int nl, const std::vector<QTypeDev>& types,
                     const double* Tcat, const float* Tcat32, const double2* r, void* y,
-                    cudaStream_t st) {
-  if (prec == SP_PREC_FP32) return q_apply_t<float2>(d, n, nl, types, Tcat32, r, (float2*)y, st);
-  return q_apply_t<double2>(d, n, nl, types, Tcat, r, (double2*)y, st);
+                    cudaStream_t st, int nv) {
+  long N = 1;
+  for (int a = 0; a < d; ++a) N *= n;
+  if (prec == SP_PREC_FP32)
+    return q_apply_t<float2>(d, n, nl, types, Tcat32, r, (float2*)y, nv, N, st);
+  return q_apply_t<double2>(d, n, nl, types, Tcat, r, (double2*)y, nv, N, st);
 }
 
 cudaError_t forward_level(int prec, int d, DevLevel& L, const DevLevel* child, const void* rhsQ,
-                          void* part, cudaStream_t st) {
-  if (prec == SP_PREC_FP32) return forward_t<float2>(d, L, child, rhsQ, part, st);
-  return forward_t<double2>(d, L, child, rhsQ, part, st);
+                          void* part, cudaStream_t st, int nv, long N) {
+  if (prec == SP_PREC_FP32) return forward_t<float2>(d, L, child, rhsQ, part, nv, N, st);
+  return forward_t<double2>(d, L, child, rhsQ, part, nv, N, st);
 }
 
-cudaError_t backward_level(int prec, int d, DevLevel& L, double2* x, void* part, cudaStream_t st) {
+cudaError_t backward_level(int prec, int d, DevLevel& L, double2* x, void* part, cudaStream_t st,
+                           int nv, long N) {
   (void)d;
-  if (prec == SP_PREC_FP32) return backward_t<float2>(L, x, part, st);
-  return backward_t<double2>(L, x, part, st);
+  if (prec == SP_PREC_FP32) return backward_t<float2>(L, x, part, nv, N, st);
+  return backward_t<double2>(L, x, part, nv, N, st);
 }
 
-size_t sweep_partial_bytes() { return (size_t)2 * kGemvTarget * 256 * sizeof(double2); }
+int sweep_max_vectors() { return kMaxVec; }
+
+size_t sweep_partial_bytes(int nv) {
+  return (size_t)2 * kGemvTarget * 256 * sizeof(double2) * (size_t)nv;
+}
 
 }  // namespace sp
