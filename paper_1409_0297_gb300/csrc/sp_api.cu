@@ -112,6 +112,8 @@ struct sp_ctx {
   double2* app_in = nullptr;   // fixed input / output of the apply graph (max_rhs N: the
   double2* app_out = nullptr;  // block input and output of sp_solve_many)
   double2* blk_w = nullptr;    // max_rhs N: operator outputs of sp_solve_many
+  cudaGraphExec_t g_block[9] = {};  // block applications of nv = 2 ... max_rhs stacked
+  bool g_block_tried[9] = {};       // vectors, captured on first use
   double factor_entries = 0, factor_flops = 0, apply_bytes = 0;
 };
 
@@ -448,6 +450,8 @@ void sp_destroy(sp_ctx* c) {
   if (c->host_sc) cudaFreeHost(c->host_sc);
   c->prof.destroy();
   if (c->g_apply) cudaGraphExecDestroy(c->g_apply);
+  for (auto& g : c->g_block)
+    if (g) cudaGraphExecDestroy(g);
   if (c->g_factor) cudaGraphExecDestroy(c->g_factor);
   if (c->cap) cudaStreamDestroy(c->cap);
   cudaSetDevice(dev);
@@ -936,7 +940,7 @@ static sp_status solve_mixed(sp_ctx* c, const double2* f, double2* u, sp_info* i
 
 // z = P^{-1} Q r for nv stacked vectors (direct launches; each vector's result
 // equals apply_direct's for it)
-sp_status apply_block(sp_ctx* c, int nv, const double2* r, double2* z, cudaStream_t st) {
+static sp_status apply_block(sp_ctx* c, int nv, const double2* r, double2* z, cudaStream_t st) {
   SP_CK(q_apply(c->prec, c->d, c->n, c->nl, c->qtypes, c->Tcat, c->Tcat32, r, c->rhsQ, st, nv));
   for (int l = 0; l <= c->L; ++l)
     SP_CK(forward_level(c->prec, c->d, c->lv[l], l ? &c->lv[l - 1] : nullptr, c->rhsQ,
@@ -1049,8 +1053,21 @@ sp_status sp_solve_many(sp_ctx* c, int nrhs, const void* F_dev, void* U_dev, sp_
     for (int s = 0; s < na; ++s)
       SP_CK(cudaMemcpyAsync(c->app_in + s * N, V(act[s]) + (long)R[act[s]].j * N, vb,
                             cudaMemcpyDeviceToDevice, st));
-    sp_status ss = apply_block(c, na, c->app_in, c->app_out, st);
-    if (ss != SP_OK) return ss;
+    if (!c->g_block_tried[na] && !c->profiling && c->cap) {
+      // capture the block application of na vectors once (app_in -> app_out); the
+      // capture stream waits for the copies just issued
+      c->g_block_tried[na] = true;
+      SP_CK(cudaStreamSynchronize(st));
+      capture_graph(c, &c->g_block[na], [c, na](cudaStream_t s2) {
+        return apply_block(c, na, c->app_in, c->app_out, s2);
+      });
+    }
+    if (c->g_block[na] && !c->profiling) {
+      SP_CK(cudaGraphLaunch(c->g_block[na], st));
+    } else {
+      sp_status ss = apply_block(c, na, c->app_in, c->app_out, st);
+      if (ss != SP_OK) return ss;
+    }
     SP_CK(fft_green_apply(c->fft, c->app_out, c->q, true, c->blk_w, st, na));
     for (int s = 0; s < na; ++s) {
       const int r = act[s], j = R[r].j;
