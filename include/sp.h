@@ -84,6 +84,12 @@ typedef struct {
                         context's.  0 (default): built-in heuristics */
   int max_rhs;       /* right-hand sides sp_solve_many may take at once, 1 ... 8
                         (default 1); the solve workspace is sized for it */
+  int setup_route;   /* how sp_setup forms T_S = G(S, gamma^c) G(beta, gamma^c)^+:
+                        0 (default) TSQR of [B^T | A^T] over the N - |gamma| points of
+                        gamma^c and an SVD of R11 (accuracy ~cond(B) eps); 1 the Gram
+                        route B B^T = (G^2)(beta, beta) - G(beta, gamma) G(gamma, beta),
+                        A B^T likewise, and an eigen-decomposition of B B^T: cost
+                        independent of N, accuracy ~cond(B)^2 eps */
 } sp_opts;
 
 typedef struct {
@@ -173,10 +179,11 @@ sp_status sp_get_table(const sp_ctx *ctx, int t, double *Q_out, double *C_out, i
                        int *cols, int *rank);
 
 /* Host-only (no GPU): the same tables as sp_setup computes for (d, n, b, s),
- * type t.  Pass Q_out = C_out = NULL to query *rows / *cols first.
- * sigma_out (may be NULL) receives min(|beta|, 64) leading singular values of
- * G(beta, gamma^c) in descending order. */
-sp_status sp_stencil_table(int d, int n, int b, double s, int t, int host_threads,
+ * type t, by route 0 (TSQR + SVD) or 1 (Gram, see sp_opts.setup_route).  Pass
+ * Q_out = C_out = NULL to query *rows / *cols first.  sigma_out (may be NULL)
+ * receives min(|beta|, 64) leading singular values of G(beta, gamma^c) in
+ * descending order (route 1: square roots of the eigenvalues of B B^T). */
+sp_status sp_stencil_table(int d, int n, int b, double s, int t, int route, int host_threads,
                            double *Q_out, double *C_out, int *rows, int *cols, int *rank,
                            double *sigma_out);
 

@@ -293,6 +293,7 @@ void sp_default_opts(sp_opts* o) {
   o->inner_tol = 1e-5;
   o->autotune = 0;
   o->max_rhs = 1;
+  o->setup_route = 0;
 }
 
 const char* sp_status_str(sp_status st) {
@@ -322,8 +323,10 @@ sp_status sp_front_sizes(int d, int n, int b, int cap, int* nlevels, int* nfront
   return SP_OK;
 }
 
-sp_status sp_stencil_table(int d, int n, int b, double s, int t, int host_threads, double* Q_out,
-                           double* C_out, int* rows, int* cols, int* rank, double* sigma_out) {
+sp_status sp_stencil_table(int d, int n, int b, double s, int t, int route, int host_threads,
+                           double* Q_out, double* C_out, int* rows, int* cols, int* rank,
+                           double* sigma_out) {
+  if (route != 0 && route != 1) return SP_ERR_ARG;
   int L;
   if (check_grid(d, n, b, &L) || t < 0 || t >= (1 << d)) return SP_ERR_ARG;
   if (!rows || !cols) return SP_ERR_ARG;
@@ -338,9 +341,11 @@ sp_status sp_stencil_table(int d, int n, int b, double s, int t, int host_thread
   if (!Q_out && !C_out && !sigma_out && !rank) return SP_OK;
   if (shift_gap(d, n, s) < 1e-6) return SP_ERR_RESONANT;
   try {
-    std::vector<double> g = green_kernel(d, n, s);
+    std::vector<double> g = green_kernel(d, n, s), g2;
+    if (route == 1) g2 = green_kernel_sq(d, n, s);
     StencilTable tb;
-    if (stencil_table(d, n, b, t, g, host_threads, &tb)) return SP_ERR_ARG;
+    if (stencil_table(d, n, b, t, g, host_threads, &tb, route == 1 ? &g2 : nullptr))
+      return SP_ERR_ARG;
     if (Q_out) std::memcpy(Q_out, tb.Q.data(), tb.Q.size() * sizeof(double));
     if (C_out) std::memcpy(C_out, tb.C.data(), tb.C.size() * sizeof(double));
     if (rank) *rank = tb.rank;
@@ -484,6 +489,7 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   if (c->opts.maxit < 1 || c->opts.restart < 1 || c->opts.restart > 1000 || !(c->opts.tol > 0))
     return SP_ERR_ARG;
   if (c->opts.max_rhs < 1 || c->opts.max_rhs > sweep_max_vectors()) return SP_ERR_ARG;
+  if (c->opts.setup_route != 0 && c->opts.setup_route != 1) return SP_ERR_ARG;
   const size_t RH = (size_t)c->opts.max_rhs;
   c->d = d;
   c->n = n;
@@ -503,10 +509,13 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   SP_CK(cudaSetDevice(c->opts.device));
   // ---- host set-up: Green's kernel, stencil tables, symbolic structure
   try {
-    std::vector<double> g = green_kernel(d, n, s);
+    std::vector<double> g = green_kernel(d, n, s), g2;
+    if (c->opts.setup_route == 1) g2 = green_kernel_sq(d, n, s);
     c->tabs.resize(1 << d);
     for (int t = 0; t < (1 << d); ++t)
-      if (stencil_table(d, n, b, t, g, c->opts.host_threads, &c->tabs[t])) return SP_ERR_ARG;
+      if (stencil_table(d, n, b, t, g, c->opts.host_threads, &c->tabs[t],
+                        c->opts.setup_route == 1 ? &g2 : nullptr))
+        return SP_ERR_ARG;
     if (build_symbolic(d, n, b, c->tabs, &c->sym)) return SP_ERR_ARG;
   } catch (const std::bad_alloc&) {
     return SP_ERR_OOM;

@@ -95,6 +95,27 @@ std::vector<double> green_kernel(int d, int n, double s) {
   return g;
 }
 
+std::vector<double> green_kernel_sq(int d, int n, double s) {
+  size_t N = 1;
+  for (int i = 0; i < d; ++i) N *= n;
+  std::vector<cd> a(N);
+  for (size_t j = 0; j < N; ++j) {
+    size_t r = j;
+    double k2 = 0;
+    for (int ax = 0; ax < d; ++ax) {
+      int k = kfreq((int)(r % n), n);
+      r /= n;
+      k2 += (double)k * k;
+    }
+    const double dk = 1.0 / (4.0 * kPi * kPi * k2 - s);
+    a[j] = dk * dk;
+  }
+  fft_nd(a, d, n, +1);
+  std::vector<double> g(N);
+  for (size_t j = 0; j < N; ++j) g[j] = a[j].real() / (double)N;
+  return g;
+}
+
 double resonance_gap(int d, int n, double s) {
   double kappa = s / (4.0 * kPi * kPi);
   double best = 1e300;
@@ -266,8 +287,69 @@ static void jacobi_svd(int r, std::vector<double> A, std::vector<double>* U,
 }
 
 // ---------------------------------------------------------------- stencil tables
+static int finish_table(int d, int n, StencilTable& T, const std::vector<double>& g,
+                        const std::vector<double>& Tm);
+
+// Gram route (g2 given): with B = G(beta, gamma^c), A = G(S, gamma^c) and G
+// symmetric, B B^T = (G^2)(beta, beta) - G(beta, gamma) G(gamma, beta) and
+// A B^T = (G^2)(S, beta) - G(S, gamma) G(gamma, beta), both |gamma|-sized; then
+// T = A B^T pinv(B B^T), the pseudoinverse from the eigen-decomposition of the
+// symmetric B B^T (one-sided Jacobi), eigenvalues lambda = sigma(B)^2 cut at the
+// same tolerance on sigma as the SVD route.  Cost O(|beta|^2 |gamma|) instead of
+// O(|gamma|^2 N); accuracy ~cond(B)^2 eps instead of ~cond(B) eps.
+static void gram_route(int d, int n, const StencilTable& T, const std::vector<double>& g,
+                       const std::vector<double>& g2, long Np, std::vector<double>* Tm,
+                       std::vector<double>* sigma, int* rank_out) {
+  const int r = T.nB, p = T.nS, nG = T.nG;
+  auto gk = [&](const std::vector<double>& k, const int* x, const int* y) {
+    int dp[3];
+    for (int a = 0; a < d; ++a) dp[a] = x[a] - y[a];
+    return k[flat_of(dp, d, n)];
+  };
+  // G(beta, gamma) (r x nG) and G(S, gamma) (p x nG), row-major
+  std::vector<double> Gbg((size_t)r * nG), Gsg((size_t)p * nG);
+  for (int a = 0; a < r; ++a)
+    for (int c = 0; c < nG; ++c) Gbg[(size_t)a * nG + c] = gk(g, &T.Bt[(size_t)a * d], &T.G[(size_t)c * d]);
+  for (int a = 0; a < p; ++a)
+    for (int c = 0; c < nG; ++c) Gsg[(size_t)a * nG + c] = gk(g, &T.S[(size_t)a * d], &T.G[(size_t)c * d]);
+  std::vector<double> M((size_t)r * r), AB((size_t)p * r);  // M column-major, AB row-major
+  for (int bq = 0; bq < r; ++bq) {
+    for (int a = 0; a < r; ++a) {
+      double acc = 0;
+      for (int c = 0; c < nG; ++c) acc += Gbg[(size_t)a * nG + c] * Gbg[(size_t)bq * nG + c];
+      M[(size_t)bq * r + a] = gk(g2, &T.Bt[(size_t)a * d], &T.Bt[(size_t)bq * d]) - acc;
+    }
+    for (int a = 0; a < p; ++a) {
+      double acc = 0;
+      for (int c = 0; c < nG; ++c) acc += Gsg[(size_t)a * nG + c] * Gbg[(size_t)bq * nG + c];
+      AB[(size_t)a * r + bq] = gk(g2, &T.S[(size_t)a * d], &T.Bt[(size_t)bq * d]) - acc;
+    }
+  }
+  std::vector<double> U, lam, V;
+  jacobi_svd(r, M, &U, &lam, &V);
+  sigma->assign(r, 0.0);
+  for (int i = 0; i < r; ++i) (*sigma)[i] = std::sqrt(std::max(0.0, lam[i]));
+  const double smax = r ? (*sigma)[0] : 0.0;
+  int rank = 0;
+  if (smax > 0) {
+    const double tol = (double)std::max<long>(r, Np) * std::ldexp(1.0, std::ilogb(smax) - 52);
+    for (int i = 0; i < r; ++i)
+      if ((*sigma)[i] > tol) ++rank;
+  }
+  *rank_out = rank;
+  // T[a][q] = sum_i (AB[a] . u_i) v_i[q] / lambda_i
+  Tm->assign((size_t)p * r, 0.0);
+  for (int a = 0; a < p; ++a)
+    for (int i = 0; i < rank; ++i) {
+      double w = 0;
+      for (int k = 0; k < r; ++k) w += AB[(size_t)a * r + k] * U[(size_t)i * r + k];
+      w /= lam[i];
+      for (int q = 0; q < r; ++q) (*Tm)[(size_t)a * r + q] += w * V[(size_t)i * r + q];
+    }
+}
+
 int stencil_table(int d, int n, int b, int t, const std::vector<double>& g, int threads,
-                  StencilTable* out) {
+                  StencilTable* out, const std::vector<double>* g2) {
   StencilTable& T = *out;
   T.t = t;
   set_geometry(d, b, t, &T.S, &T.G, &T.Bt);
@@ -276,6 +358,13 @@ int stencil_table(int d, int n, int b, int t, const std::vector<double>& g, int 
   T.nB = (int)T.Bt.size() / d;
   long N = 1;
   for (int a = 0; a < d; ++a) N *= n;
+  std::vector<double> Tm;
+  if (g2) {
+    int rank = 0;
+    gram_route(d, n, T, g, *g2, N - T.nG, &Tm, &T.sigma, &rank);
+    T.rank = rank;
+    return finish_table(d, n, T, g, Tm);
+  }
   // complement of gamma (flat indices)
   std::vector<char> ing(N, 0);
   for (int i = 0; i < T.nG; ++i) ing[flat_of(&T.G[(size_t)i * d], d, n)] = 1;
@@ -382,13 +471,21 @@ int stencil_table(int d, int n, int b, int t, const std::vector<double>& g, int 
       for (int k = 0; k < r; ++k) acc += U[(size_t)i * r + k] * R12[(size_t)col * r + k];
       W[(size_t)col * rank + i] = acc / sg[i];
     }
-  std::vector<double> Tm((size_t)p * r, 0.0);  // row-major p x r
+  Tm.assign((size_t)p * r, 0.0);  // row-major p x r
   for (int a = 0; a < p; ++a)
     for (int q = 0; q < r; ++q) {
       double acc = 0;
       for (int i = 0; i < rank; ++i) acc += V[(size_t)i * r + q] * W[(size_t)a * rank + i];
       Tm[(size_t)a * r + q] = acc;
     }
+  return finish_table(d, n, T, g, Tm);
+}
+
+// Q(S, gamma) = [I, -T] and C(S, gamma) = Q(S, gamma) G(gamma, gamma) from T (row-major
+// p x r over (S, beta)).
+static int finish_table(int d, int n, StencilTable& T, const std::vector<double>& g,
+                        const std::vector<double>& Tm) {
+  const int p = T.nS, r = T.nB;
   // Q(S, gamma) = [I, -T] on (S, beta), placed in gamma order
   T.Q.assign((size_t)p * T.nG, 0.0);
   {

@@ -43,13 +43,16 @@ struct Symbolic {
 // g = inverse DFT of 1/(4 pi^2 |k|^2 - s) with the 1/N of the unitary pair (Eq. G):
 // G(i, j) = g[(i - j) mod n].  Flat, axis 0 fastest.
 std::vector<double> green_kernel(int d, int n, double s);
+// the same for G^2: inverse DFT of 1/(4 pi^2 |k|^2 - s)^2 with the 1/N
+std::vector<double> green_kernel_sq(int d, int n, double s);
 
 // min_k |kappa - |k|^2| / max(1, kappa), kappa = s / (4 pi^2).
 double resonance_gap(int d, int n, double s);
 
-// Tables of one type (Section 2.3).  g: the Green kernel.
+// Tables of one type (Section 2.3).  g: the Green kernel.  g2 (the kernel of G^2)
+// selects the Gram route for T_S instead of the TSQR + SVD route.
 int stencil_table(int d, int n, int b, int t, const std::vector<double>& g, int threads,
-                  StencilTable* out);
+                  StencilTable* out, const std::vector<double>* g2 = nullptr);
 
 // Nested-dissection structure.
 int build_symbolic(int d, int n, int b, const std::vector<StencilTable>& tabs, Symbolic* out);

@@ -257,6 +257,27 @@ def test_solve_512(B, which, prec):
     S.close()
 
 
+@pytest.mark.parametrize("name,make", [SMALL[0], SMALL[4]], ids=[SMALL[0][0], SMALL[4][0]])
+def test_solve_gram_route(B, name, make):
+    """Contexts whose stencil tables come from the Gram route (setup_route = 1) solve
+    to the same tolerance in the same number of iterations (+-1) as the default."""
+    w = make()
+    d, n, b = w["d"], w["n"], w["b"]
+    s, q, f = medium(w)
+    its = []
+    for route in (0, 1):
+        S = B.Solver(d, n, b, s, prec=0, setup_route=route)
+        S.factor(dev(q))
+        u = torch.empty(n ** d, dtype=torch.complex128, device="cuda")
+        info = S.solve(dev(f), u)
+        g = O.apply_green(d, n, s, f)
+        true = float(np.linalg.norm(g - O.apply_operator(d, n, s, q, host(u))) / np.linalg.norm(g))
+        assert true <= 1e-8
+        its.append(info["iters"])
+        S.close()
+    assert abs(its[0] - its[1]) <= 1
+
+
 def test_zero_rhs_and_state_errors(B):
     w = sm.helmholtz_centre_gaussian_64()
     d, n, b = w["d"], w["n"], w["b"]
