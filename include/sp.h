@@ -90,6 +90,11 @@ typedef struct {
                         route B B^T = (G^2)(beta, beta) - G(beta, gamma) G(gamma, beta),
                         A B^T likewise, and an eigen-decomposition of B B^T: cost
                         independent of N, accuracy ~cond(B)^2 eps */
+  int stencil;       /* 0 (default): the set stencils of Section 2.3, Q(S, gamma(S)) for
+                        cells, faces, edges and vertices; 1: per-point stencils
+                        Q(j, gamma({j})) on the 3^d neighbourhood of every point j
+                        (one T for all points by translation invariance), the
+                        sparsifying operator of the earlier per-point construction */
 } sp_opts;
 
 typedef struct {
@@ -179,13 +184,14 @@ sp_status sp_get_table(const sp_ctx *ctx, int t, double *Q_out, double *C_out, i
                        int *cols, int *rank);
 
 /* Host-only (no GPU): the same tables as sp_setup computes for (d, n, b, s),
- * type t, by route 0 (TSQR + SVD) or 1 (Gram, see sp_opts.setup_route).  Pass
+ * type t, by route 0 (TSQR + SVD) or 1 (Gram, see sp_opts.setup_route), of
+ * kind 0 (set stencils) or 1 (per-point stencils, see sp_opts.stencil).  Pass
  * Q_out = C_out = NULL to query *rows / *cols first.  sigma_out (may be NULL)
  * receives min(|beta|, 64) leading singular values of G(beta, gamma^c) in
  * descending order (route 1: square roots of the eigenvalues of B B^T). */
-sp_status sp_stencil_table(int d, int n, int b, double s, int t, int route, int host_threads,
-                           double *Q_out, double *C_out, int *rows, int *cols, int *rank,
-                           double *sigma_out);
+sp_status sp_stencil_table(int d, int n, int b, double s, int t, int route, int kind,
+                           int host_threads, double *Q_out, double *C_out, int *rows, int *cols,
+                           int *rank, double *sigma_out);
 
 /* Host-only: the nested-dissection structure (Fig. nd).  Writes, for levels
  * 0 (leaves) .. L (root), the number of fronts, eliminated unknowns k and front

@@ -137,6 +137,48 @@ def stencil_tables(d: int, n: int, b: int, s: float, origin=None, types=None,
     return out
 
 
+def pointwise_stencil_tables(d: int, n: int, b: int, s: float) -> list[dict]:
+    """The per-point sparsifying stencils mu(j) = gamma({j}) (the construction the
+    paper's set stencils generalise, Section 2.3): for every point j of every set
+    type, independently, A = G(j, gamma({j})^c), B = G(beta_j, gamma({j})^c) with
+    gamma({j}) the 3^d neighbourhood of j and beta_j = gamma({j}) minus j,
+    T_j = A pinv(B), Q(j, gamma({j})) = [1, -T_j], C(j, gamma({j})) =
+    Q(j, gamma({j})) G(gamma({j}), gamma({j})).  Returned in the set tables' layout
+    (rows in S order, columns in gamma(S) order, zero outside gamma({j}))."""
+    g = green_kernel(d, n, s)
+    N = n ** d
+    offs = _box_points([range(-1, 2)] * d)  # gamma({0}), axis 0 fastest
+    out = []
+    for t in range(1 << d):
+        S = canonical_set(d, b, t)
+        gam = canonical_gamma(d, b, t)
+        col = {tuple(p): i for i, p in enumerate(gam)}
+        Q = np.zeros((S.shape[0], gam.shape[0]))
+        C = np.zeros_like(Q)
+        rank = None
+        for a, p in enumerate(S):
+            gj = p + offs
+            gj_flat = flat_index(gj, n)
+            mask = np.ones(N, dtype=bool)
+            mask[gj_flat] = False
+            comp = np.nonzero(mask)[0]
+            centre = np.all(gj == p, axis=1)
+            beta = gj[~centre]
+            A = green_block(g, n, p[None, :], comp)
+            Bm = green_block(g, n, beta, comp)
+            Bp, rank, _ = matlab_pinv(Bm)
+            Tj = (A @ Bp)[0]
+            qrow = np.zeros(gj.shape[0])
+            qrow[centre] = 1.0
+            qrow[~centre] = -Tj
+            crow = qrow @ green_block(g, n, gj, gj_flat)
+            cols = [col[tuple(x)] for x in gj]
+            Q[a, cols] = qrow
+            C[a, cols] = crow
+        out.append(dict(t=t, S=S, gamma=gam, Q=Q, C=C, rank=rank))
+    return out
+
+
 def annihilation_ratio(tab: dict) -> float:
     """||Q(S,gamma) G(gamma,gamma^c)||_F / ||G(S,gamma^c)||_F = ||A - T B|| / ||A|| (Eq. Qc)."""
     return tab["ratio"]

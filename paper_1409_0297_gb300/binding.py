@@ -35,7 +35,7 @@ class sp_opts(ctypes.Structure):
                 ("pivot_tol", ctypes.c_double), ("device", ctypes.c_int),
                 ("host_threads", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("autotune", ctypes.c_int), ("max_rhs", ctypes.c_int),
-                ("setup_route", ctypes.c_int)]
+                ("setup_route", ctypes.c_int), ("stencil", ctypes.c_int)]
 
 
 class sp_info(ctypes.Structure):
@@ -70,7 +70,7 @@ def _load() -> ctypes.CDLL:
         "sp_green": (I, [P, P, P]),
         "sp_qapply": (I, [P, P, P]),
         "sp_get_table": (I, [P, I, pD, pD, pI, pI, pI]),
-        "sp_stencil_table": (I, [I, I, I, D, I, I, I, pD, pD, pI, pI, pI, pD]),
+        "sp_stencil_table": (I, [I, I, I, D, I, I, I, I, pD, pD, pI, pI, pI, pD]),
         "sp_front_sizes": (I, [I, I, I, I, pI, pI, pI, pI]),
         "sp_costs": (I, [P, pD, pD, pD]),
         "sp_level_info": (I, [I, I, I, I, pI, pI, pI, pI, pI, pI, pI, pI, pI, pI]),
@@ -206,21 +206,22 @@ def sp_get_table(ctx: int, t: int):
 
 
 def sp_stencil_table(d: int, n: int, b: int, s: float, t: int, host_threads: int = 0,
-                     route: int = 0):
+                     route: int = 0, kind: int = 0):
     """Host-only stencil tables (no GPU needed): returns (Q, C, rank, sigma).
-    route 0: TSQR + SVD, 1: Gram route."""
+    route 0: TSQR + SVD, 1: Gram route; kind 0: set stencils, 1: per-point stencils."""
     import numpy as np
     rows, cols, rank = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _check(LIB.sp_stencil_table(d, n, b, float(s), t, route, host_threads, None, None,
+    _check(LIB.sp_stencil_table(d, n, b, float(s), t, route, kind, host_threads, None, None,
                                 ctypes.byref(rows), ctypes.byref(cols), None, None),
            "sp_stencil_table")
     Q = np.zeros((rows.value, cols.value))
     C = np.zeros((rows.value, cols.value))
     sig = np.zeros(64)
-    _check(LIB.sp_stencil_table(d, n, b, float(s), t, route, host_threads, _dptr(Q), _dptr(C),
+    _check(LIB.sp_stencil_table(d, n, b, float(s), t, route, kind, host_threads, _dptr(Q),
+                                _dptr(C),
                                 ctypes.byref(rows), ctypes.byref(cols), ctypes.byref(rank),
                                 _dptr(sig)), "sp_stencil_table")
-    nb = Q.shape[1] - Q.shape[0]
+    nb = 3 ** d - 1 if kind else Q.shape[1] - Q.shape[0]  # |beta| of the pseudoinverse
     return Q, C, rank.value, sig[: min(64, nb)]
 
 
@@ -324,13 +325,14 @@ class Solver:
     def __init__(self, d: int, n: int, b: int, s: float, prec: int = SP_PREC_FP64,
                  maxit: int = 500, restart: int = 200, tol: float = 1e-8, device: int = 0,
                  stream: int = 0, host_threads: int = 0, autotune: bool = False,
-                 max_rhs: int = 1, setup_route: int = 0):
+                 max_rhs: int = 1, setup_route: int = 0, stencil: int = 0):
         o = sp_default_opts()
         o.maxit, o.restart, o.tol, o.device = maxit, restart, tol, device
         o.host_threads = host_threads
         o.autotune = 1 if autotune else 0
         o.max_rhs = max_rhs
         o.setup_route = setup_route
+        o.stencil = stencil
         self.d, self.n, self.b, self.s, self.prec = d, n, b, s, prec
         self.N = n ** d
         self.ctx = sp_setup(d, n, b, s, prec, o, stream)

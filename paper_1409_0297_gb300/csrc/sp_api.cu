@@ -294,6 +294,7 @@ void sp_default_opts(sp_opts* o) {
   o->autotune = 0;
   o->max_rhs = 1;
   o->setup_route = 0;
+  o->stencil = 0;
 }
 
 const char* sp_status_str(sp_status st) {
@@ -323,10 +324,10 @@ sp_status sp_front_sizes(int d, int n, int b, int cap, int* nlevels, int* nfront
   return SP_OK;
 }
 
-sp_status sp_stencil_table(int d, int n, int b, double s, int t, int route, int host_threads,
-                           double* Q_out, double* C_out, int* rows, int* cols, int* rank,
-                           double* sigma_out) {
-  if (route != 0 && route != 1) return SP_ERR_ARG;
+sp_status sp_stencil_table(int d, int n, int b, double s, int t, int route, int kind,
+                           int host_threads, double* Q_out, double* C_out, int* rows, int* cols,
+                           int* rank, double* sigma_out) {
+  if ((route != 0 && route != 1) || (kind != 0 && kind != 1)) return SP_ERR_ARG;
   int L;
   if (check_grid(d, n, b, &L) || t < 0 || t >= (1 << d)) return SP_ERR_ARG;
   if (!rows || !cols) return SP_ERR_ARG;
@@ -344,7 +345,7 @@ sp_status sp_stencil_table(int d, int n, int b, double s, int t, int route, int 
     std::vector<double> g = green_kernel(d, n, s), g2;
     if (route == 1) g2 = green_kernel_sq(d, n, s);
     StencilTable tb;
-    if (stencil_table(d, n, b, t, g, host_threads, &tb, route == 1 ? &g2 : nullptr))
+    if (stencil_table(d, n, b, t, g, host_threads, &tb, route == 1 ? &g2 : nullptr, kind))
       return SP_ERR_ARG;
     if (Q_out) std::memcpy(Q_out, tb.Q.data(), tb.Q.size() * sizeof(double));
     if (C_out) std::memcpy(C_out, tb.C.data(), tb.C.size() * sizeof(double));
@@ -490,6 +491,7 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
     return SP_ERR_ARG;
   if (c->opts.max_rhs < 1 || c->opts.max_rhs > sweep_max_vectors()) return SP_ERR_ARG;
   if (c->opts.setup_route != 0 && c->opts.setup_route != 1) return SP_ERR_ARG;
+  if (c->opts.stencil != 0 && c->opts.stencil != 1) return SP_ERR_ARG;
   const size_t RH = (size_t)c->opts.max_rhs;
   c->d = d;
   c->n = n;
@@ -514,7 +516,7 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
     c->tabs.resize(1 << d);
     for (int t = 0; t < (1 << d); ++t)
       if (stencil_table(d, n, b, t, g, c->opts.host_threads, &c->tabs[t],
-                        c->opts.setup_route == 1 ? &g2 : nullptr))
+                        c->opts.setup_route == 1 ? &g2 : nullptr, c->opts.stencil))
         return SP_ERR_ARG;
     if (build_symbolic(d, n, b, c->tabs, &c->sym)) return SP_ERR_ARG;
   } catch (const std::bad_alloc&) {
@@ -552,17 +554,26 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
         }
       }
       if ((int)bcols.size() != tb.nB) return SP_ERR_ARG;
-      for (int cb = 0; cb < tb.nB; ++cb)
+      // per-point stencils: Q(S, S) is not the identity, so the apply runs over
+      // every column of gamma
+      if (c->opts.stencil == 1) {
+        bcols.resize(tb.nG);
+        for (int gi = 0; gi < tb.nG; ++gi) bcols[gi] = gi;
+      }
+      qt.na = (int)bcols.size();
+      qt.self = c->opts.stencil == 1 ? 0 : 1;
+      for (int cb = 0; cb < qt.na; ++cb)
         for (int a = 0; a < tb.nS; ++a) {
           double v = -tb.Q[(size_t)a * tb.nG + bcols[cb]];
           Tc.push_back(v);
           T32.push_back((float)v);
         }
       off += (long)tb.nS * tb.nG;
-      toff += (long)tb.nS * tb.nB;
+      toff += (long)tb.nS * qt.na;
       SP_CK(upload(c.get(), &qt.S, tb.S));
       SP_CK(upload(c.get(), &qt.G, tb.G));
       SP_CK(upload(c.get(), &qt.Bt, tb.Bt));
+      qt.A = qt.self ? qt.Bt : qt.G;
       c->qtypes.push_back(qt);
     }
     SP_CK(upload(c.get(), &c->Qcat, Qc));

@@ -348,11 +348,9 @@ static void gram_route(int d, int n, const StencilTable& T, const std::vector<do
     }
 }
 
-int stencil_table(int d, int n, int b, int t, const std::vector<double>& g, int threads,
-                  StencilTable* out, const std::vector<double>* g2) {
-  StencilTable& T = *out;
-  T.t = t;
-  set_geometry(d, b, t, &T.S, &T.G, &T.Bt);
+// T, Q and C of a table whose geometry (S, gamma, beta) is already set.
+static int set_table(int d, int n, StencilTable& T, const std::vector<double>& g, int threads,
+                     const std::vector<double>* g2) {
   T.nS = (int)T.S.size() / d;
   T.nG = (int)T.G.size() / d;
   T.nB = (int)T.Bt.size() / d;
@@ -525,6 +523,57 @@ static int finish_table(int d, int n, StencilTable& T, const std::vector<double>
       const double* gr = &Ggg[(size_t)i * T.nG];
       double* cr = &T.C[(size_t)a * T.nG];
       for (int j = 0; j < T.nG; ++j) cr[j] += qa * gr[j];
+    }
+  return 0;
+}
+
+int stencil_table(int d, int n, int b, int t, const std::vector<double>& g, int threads,
+                  StencilTable* out, const std::vector<double>* g2, int kind) {
+  StencilTable& T = *out;
+  T.t = t;
+  set_geometry(d, b, t, &T.S, &T.G, &T.Bt);
+  if (kind == 0) return set_table(d, n, T, g, threads, g2);
+  // per-point stencils: the table of the single point 0 (S = {0}, gamma its 3^d
+  // neighbours, axis 0 fastest), the same for every point by translation
+  // invariance; row a of the type's table carries it on the columns
+  // gamma({S_a}) of gamma(S) and is zero elsewhere
+  StencilTable P;
+  P.t = -1;
+  {
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, glo[3] = {-1, -1, -1}, ghi[3] = {1, 1, 1};
+    P.S = box_points(d, lo, hi);
+    P.G = box_points(d, glo, ghi);
+    const int nG = (int)P.G.size() / d;
+    for (int i = 0; i < nG; ++i) {
+      bool zero = true;
+      for (int a = 0; a < d; ++a)
+        if (P.G[(size_t)i * d + a] != 0) zero = false;
+      if (!zero)
+        for (int a = 0; a < d; ++a) P.Bt.push_back(P.G[(size_t)i * d + a]);
+    }
+  }
+  int e = set_table(d, n, P, g, threads, g2);
+  if (e) return e;
+  T.nS = (int)T.S.size() / d;
+  T.nG = (int)T.G.size() / d;
+  T.nB = (int)T.Bt.size() / d;
+  T.rank = P.rank;
+  T.sigma = P.sigma;
+  T.Q.assign((size_t)T.nS * T.nG, 0.0);
+  T.C.assign((size_t)T.nS * T.nG, 0.0);
+  for (int a = 0; a < T.nS; ++a)
+    for (int ie = 0; ie < P.nG; ++ie) {
+      int c = -1;
+      for (int cc = 0; cc < T.nG && c < 0; ++cc) {
+        bool eq = true;
+        for (int ax = 0; ax < d; ++ax)
+          if (T.G[(size_t)cc * d + ax] != T.S[(size_t)a * d + ax] + P.G[(size_t)ie * d + ax])
+            eq = false;
+        if (eq) c = cc;
+      }
+      if (c < 0) return 5;  // gamma({S_a}) lies inside gamma(S) by construction
+      T.Q[(size_t)a * T.nG + c] = P.Q[ie];
+      T.C[(size_t)a * T.nG + c] = P.C[ie];
     }
   return 0;
 }

@@ -50,9 +50,12 @@ std::vector<double> green_kernel_sq(int d, int n, double s);
 double resonance_gap(int d, int n, double s);
 
 // Tables of one type (Section 2.3).  g: the Green kernel.  g2 (the kernel of G^2)
-// selects the Gram route for T_S instead of the TSQR + SVD route.
+// selects the Gram route for T_S instead of the TSQR + SVD route.  kind 0: the
+// paper's set stencils Q(S, gamma(S)); kind 1: per-point stencils Q(j, gamma({j}))
+// (the 3^d neighbourhood of each point j), stored in the same |S| x |gamma(S)|
+// layout with each row zero outside gamma({j}).
 int stencil_table(int d, int n, int b, int t, const std::vector<double>& g, int threads,
-                  StencilTable* out, const std::vector<double>* g2 = nullptr);
+                  StencilTable* out, const std::vector<double>* g2 = nullptr, int kind = 0);
 
 // Nested-dissection structure.
 int build_symbolic(int d, int n, int b, const std::vector<StencilTable>& tabs, Symbolic* out);

@@ -151,8 +151,13 @@ struct QTypeDev {
   int* Bt = nullptr; // nB x d offsets of beta = gamma minus S
   long tab_off = 0;  // offset of the type in the concatenated column-major Q/C tables
   long t_off = 0;    // offset of the type in the concatenated column-major T tables
+  // columns of the stencil apply: beta with Q(S, S) = I (set stencils), or all of
+  // gamma with no identity term (per-point stencils, where Q(S, S) is not I)
+  int na = 0, self = 1;
+  int* A = nullptr;  // na x d offsets (Bt or G)
 };
-// y = Q r = r_S - T_S r_beta(S) per set instance (VT = double2 (FP64) or float2
+// y = Q r per set instance: r_S - T r_beta(S) for set stencils, -T r_gamma(S)
+// with T = -Q(S, gamma(S)) for per-point stencils (VT = double2 (FP64) or float2
 // (FP32) for y; r is complex128).
 // nv stacked vectors (1 <= nv <= sweep_max_vectors()): global vectors (r, y, x,
 // the stencil output) N apart, a level's work vectors (tmp nf m, y nf k, upd

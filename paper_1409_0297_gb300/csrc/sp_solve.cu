@@ -55,12 +55,14 @@ __device__ __forceinline__ void axpy(VT& acc, T a, VT x) {  // acc += a * x
 
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-// y[S instance] = r[S instance] - T_t r[beta instance]; one CTA per instance of type t
+// y[S instance] = self * r[S instance] - T_t r[B instance], B = beta (self = 1, set
+// stencils) or gamma (self = 0, per-point stencils); one CTA per instance of type t
 // (and per stacked vector, blockIdx.y, vectors N apart).
 template <class VT, class T>
-__global__ void qapply_kernel(int d, int n, int nl, int nS, int nB, const int* __restrict__ Soff,
-                              const int* __restrict__ Boff, const T* __restrict__ Tt,
-                              const double2* __restrict__ r, VT* y, long N) {
+__global__ void qapply_kernel(int d, int n, int nl, int nS, int nB, int self,
+                              const int* __restrict__ Soff, const int* __restrict__ Boff,
+                              const T* __restrict__ Tt, const double2* __restrict__ r, VT* y,
+                              long N) {
   extern __shared__ unsigned char smraw[];
   VT* rb = reinterpret_cast<VT*>(smraw);
   r += blockIdx.y * N;
@@ -85,7 +87,7 @@ __global__ void qapply_kernel(int d, int n, int nl, int nS, int nB, const int* _
       g += (long)wrapi(o[a] + Soff[a0 * d + a], n) * s;
       s *= n;
     }
-    VT acc = from_d2<VT>(r[g]);
+    VT acc = self ? from_d2<VT>(r[g]) : VT{0, 0};
     for (int c = 0; c < nB; ++c) axpy_neg(acc, Tt[a0 + (long)c * nS], rb[c]);
     y[g] = acc;
   }
@@ -312,31 +314,24 @@ __global__ void __launch_bounds__(1024) inv_gather_global_kernel(
   for (int j = threadIdx.x; j < k; j += blockDim.x) t[j] = y[j];
 }
 
-// Row-block matrix-vector products of the levels whose diagonal blocks (size
-// kInvBlockSize) hold the inverses of those of L11 / U11.  16 rows per CTA, 16
-// column lanes per row, partial sums reduced in shared memory.  [j0, j1) is the
-// current diagonal block.
-// mode 4 (forward, rows [j0,j1)):  tmp[r] -= sum_{c<j0} L[r,c] y[c]
-// mode 0 (forward, rows [j0,j1)):  y[r] = tmp[r] + sum_{j0<=c<r} Linv[r,c] tmp[c]
-// mode 1 (forward, rows [k,m)):    upd[r] = tmp[r] - sum_{c<k} L21[r,c] y[c]
-// mode 2 (backward, rows [0,k)):   tmp[r] = y[r] - sum_{k<=c<m} U12[r,c] x[c]
-// mode 6 (backward, rows [j0,j1)): tmp[r] -= sum_{j1<=c<k} U[r,c] y[c]
-// mode 3 (backward, rows [j0,j1)): y[r] = x[r] = sum_{r<=c<j1} Uinv[r,c] tmp[c]
-// (in the backward sweep y holds x1 once mode 2 has consumed y1).  The sweeps use
-// modes 0 and 3 (the diagonal blocks); the off-diagonal products go through
-// gemv_kernel below.
+// Diagonal-block products of the levels whose diagonal blocks (size
+// kInvBlockSize) hold the inverses of those of L11 / U11; [j0, j1) is the block.
+//   mode 0 (forward):  y[r] = tmp[r] + sum_{j0<=c<r} Linv[r,c] tmp[c]
+//   mode 3 (backward): y[r] = x[r] = sum_{r<=c<j1} Uinv[r,c] tmp[c]
+// (in the backward sweep y holds x1).  RB rows per CTA, 256 / RB column lanes per
+// row, partial sums reduced in shared memory in a fixed order; the off-diagonal
+// products go through gemv_kernel below.
 template <class VT, class T, int RB>
 __global__ void __launch_bounds__(256) inv_gemv_kernel(int mode, const T* __restrict__ fronts,
                                                         int m, int k, int j0, int j1,
                                                         const int* __restrict__ gidx, VT* tmp,
-                                                        VT* y, VT* upd, double2* x, long N) {
+                                                        VT* y, double2* x, long N) {
   extern __shared__ unsigned char smraw[];
-  VT* v = reinterpret_cast<VT*>(smraw);  // input vector entries [vlo, vhi)
+  VT* v = reinterpret_cast<VT*>(smraw);  // tmp[j0 .. j1)
   {  // stacked vector blockIdx.z
     const long vz = blockIdx.z, nf = gridDim.y;
     tmp += vz * nf * m;
     y += vz * nf * k;
-    upd += vz * nf * (m - k);
     if (x) x += vz * N;
   }
   constexpr int CL = 256 / RB;  // column lanes per row
@@ -345,70 +340,37 @@ __global__ void __launch_bounds__(256) inv_gemv_kernel(int mode, const T* __rest
   const T* A = fronts + (long)f * m * m;
   VT* tf = tmp + (long)f * m;
   VT* yf = y + (long)f * k;
-  int rlo, rhi, vlo, vhi;
-  switch (mode) {
-    case 4: rlo = j0; rhi = j1; vlo = 0; vhi = j0; break;
-    case 0: rlo = j0; rhi = j1; vlo = j0; vhi = j1; break;
-    case 1: rlo = k; rhi = m; vlo = 0; vhi = k; break;
-    case 2: rlo = 0; rhi = k; vlo = k; vhi = m; break;
-    case 6: rlo = j0; rhi = j1; vlo = j1; vhi = k; break;
-    default: rlo = j0; rhi = j1; vlo = j0; vhi = j1; break;  // 3
-  }
-  for (int c = vlo + threadIdx.x; c < vhi; c += blockDim.x) {
-    VT val;
-    if (mode == 0 || mode == 3) val = tf[c];
-    else if (mode == 2) val = from_d2<VT>(x[gidx[(long)f * m + c]]);
-    else val = yf[c];
-    v[c - vlo] = val;
-  }
+  for (int c = j0 + threadIdx.x; c < j1; c += blockDim.x) v[c - j0] = tf[c];
   __syncthreads();
   const int tx = threadIdx.x % RB, ty = threadIdx.x / RB;
-  const int r0 = rlo + blockIdx.x * RB;
+  const int r0 = j0 + blockIdx.x * RB;
   const int r = r0 + tx;
-  int cb = vlo, ce = vhi;  // column range of the whole row block
-  if (mode == 0) ce = min(r0 + RB, vhi);
-  if (mode == 3) cb = max(r0, vlo);
+  // column range of the row block: the lower triangle up to the block's last row
+  // (mode 0) or the upper triangle from its first row (mode 3)
+  const int cb = (mode == 0) ? j0 : max(r0, j0);
+  const int ce = (mode == 0) ? min(r0 + RB, j1) : j1;
   VT acc = vzero<VT>();
-  if (r < rhi) {
+  if (r < j1) {
 #pragma unroll 4
     for (int c = cb + ty; c < ce; c += CL) {
-      bool use = (mode == 0) ? (c < r) : (mode == 3) ? (c >= r) : true;
-      if (use) axpy(acc, A[r + (long)c * m], v[c - vlo]);
+      const bool use = (mode == 0) ? (c < r) : (c >= r);
+      if (use) axpy(acc, A[r + (long)c * m], v[c - j0]);
     }
   }
   red[ty][tx] = acc;
   __syncthreads();
-  if (ty == 0 && r < rhi) {
+  if (ty == 0 && r < j1) {
     VT s = red[0][tx];
     for (int l = 1; l < CL; ++l) {
       s.x += red[l][tx].x;
       s.y += red[l][tx].y;
     }
-    switch (mode) {
-      case 4:
-      case 6: {
-        VT o = tf[r];
-        tf[r] = VT{o.x - s.x, o.y - s.y};
-        break;
-      }
-      case 0: {
-        VT o = tf[r];
-        yf[r] = VT{o.x + s.x, o.y + s.y};
-        break;
-      }
-      case 1: {
-        VT o = tf[r];
-        upd[(long)f * (m - k) + (r - k)] = VT{o.x - s.x, o.y - s.y};
-        break;
-      }
-      case 2: {
-        VT o = yf[r];
-        tf[r] = VT{o.x - s.x, o.y - s.y};
-        break;
-      }
-      default:
-        yf[r] = s;
-        x[gidx[(long)f * m + r]] = to_d2(s);
+    if (mode == 0) {
+      const VT o = tf[r];
+      yf[r] = VT{o.x + s.x, o.y + s.y};
+    } else {
+      yf[r] = s;
+      x[gidx[(long)f * m + r]] = to_d2(s);
     }
   }
 }
@@ -526,12 +488,12 @@ cudaError_t q_apply_t(int d, int n, int nl, const std::vector<QTypeDev>& types, 
   ProfScope ps(PROF_QAPPLY, st);
   double bytes = 0;
   for (const auto& ty : types) {
-    size_t smem = sizeof(VT) * (ty.nB > 0 ? ty.nB : 1);
+    size_t smem = sizeof(VT) * (ty.na > 0 ? ty.na : 1);
     dim3 g((unsigned)ninst, nv);
-    qapply_kernel<VT, T><<<g, 128, smem, st>>>(d, n, nl, ty.nS, ty.nB, ty.S, ty.Bt,
+    qapply_kernel<VT, T><<<g, 128, smem, st>>>(d, n, nl, ty.nS, ty.na, ty.self, ty.S, ty.A,
                                                (const T*)Tt + ty.t_off, r, y, N);
     bytes += (double)ninst * nv * ty.nS * (sizeof(double2) + sizeof(VT)) +
-             sizeof(T) * ty.nS * ty.nB;
+             sizeof(T) * ty.nS * ty.na;
   }
   ps.done(bytes, (int)types.size(), st);
   return cudaGetLastError();
@@ -591,13 +553,11 @@ void inv_gemv(int mode, DevLevel& L, int j0, int j1, int rlo, int rhi, size_t sm
   if ((long)((rows + 15) / 16) * L.nf >= 152) {
     dim3 g((rows + 15) / 16, L.nf, nv);
     inv_gemv_kernel<VT, T, 16><<<g, 256, smem, st>>>(mode, (const T*)L.front, L.m, L.k, j0, j1,
-                                                     L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x,
-                                                     N);
+                                                     L.gidx, (VT*)L.tmp, (VT*)L.y, x, N);
   } else {
     dim3 g((rows + 3) / 4, L.nf, nv);
     inv_gemv_kernel<VT, T, 4><<<g, 256, smem, st>>>(mode, (const T*)L.front, L.m, L.k, j0, j1,
-                                                    L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x,
-                                                    N);
+                                                    L.gidx, (VT*)L.tmp, (VT*)L.y, x, N);
   }
 }
 
