@@ -20,6 +20,9 @@ states:
                 preconditioner M r = P^{-1} Q r.
   gmres.py      right-preconditioned GMRES (Saad-Schultz), classical Gram-Schmidt
                 applied twice, Givens rotations, explicit true residual.
+  fno.py        the Fourier-layer network that supplies the solve's starting vector
+                (not part of the paper: Li et al.'s Fourier neural operator and the
+                Adam optimiser), forward pass, hand-derived gradient, Adam step.
 
 Every function cites the passage it follows.  Readings where the paper is
 silent are stated where they are used.

@@ -195,3 +195,43 @@ def batched_2d_problems(count: int = 64, nrhs: int = 8, seed: int = 3000) -> lis
         out.append(p)
     return out
 
+
+
+# ---------------------------------------------------------------- learned initial guess
+def fno_initial_params(c_in: int = 3, width: int = 32, modes: int = 16, layers: int = 4,
+                       hidden: int = 128, c_out: int = 2, seed: int = 4000) -> np.ndarray:
+    """Seeded initial weights of the Fourier-layer network, flat float64 in the network's
+    parameter order (lift P [W, c_in], p [W]; per layer R [2M, M, W, W, 2], W_l [W, W],
+    b_l [W]; Q1 [H, W], c1 [H], Q2 [c_out, H], c2 [c_out]).  Pointwise weights and biases
+    are uniform in +-1/sqrt(fan_in); the spectral weights' real and imaginary parts are
+    uniform in [0, 1/W^2)."""
+    rng = np.random.default_rng(seed)
+
+    def lin(o, i):
+        k = 1.0 / np.sqrt(i)
+        return [rng.uniform(-k, k, size=(o, i)).ravel(), rng.uniform(-k, k, size=o)]
+
+    W, M = width, modes
+    parts = lin(W, c_in)
+    for _ in range(layers):
+        parts.append(rng.uniform(0.0, 1.0 / (W * W), size=(2 * M, M, W, W, 2)).ravel())
+        parts += lin(W, W)
+    parts += lin(hidden, W) + lin(c_out, hidden)
+    return np.concatenate(parts)
+
+
+def lattice_wells_potential_2d(n: int, ell: float, seed: int, depth=(5.0, 15.0),
+                               width: float = 0.15) -> np.ndarray:
+    """The 2D lattice_wells_potential in separable form: with the per-axis minimum image,
+    exp(-r^2 / (2 w^2)) = ex(x) ey(y), so V = -ex^T D ey over the l x l cells (same seed,
+    same depths, same values up to rounding; fast enough for thousands of media)."""
+    rng = np.random.default_rng(seed)
+    m = int(round(ell))
+    depths = rng.uniform(depth[0], depth[1], size=m * m).reshape(m, m)  # [cell j1][cell j0]
+    x = np.arange(n) * (ell / n)
+    d = x[None, :] - (np.arange(m)[:, None] + 0.5)
+    d = d - ell * np.round(d / ell)
+    e = np.exp(-d * d / (2.0 * width * width))                           # [cell][point]
+    # np.indices ordering: cell index (i0, i1) flattened with i1 fastest; i0 is axis 0 (j0)
+    V = -np.einsum("ab,ay,bx->yx", depths.T, e, e)
+    return V.ravel()
