@@ -72,6 +72,14 @@ def parse():
     p.add_argument("--no-batch", action="store_true",
                    help="skip the batched heterogeneous 2D workload (64 problems x 8 right-hand sides)")
     p.add_argument("--batch-workers", type=int, default=8)
+    p.add_argument("--no-learned", action="store_true",
+                   help="skip the learned-initial-guess workload")
+    p.add_argument("--learned-media", type=int, default=512)
+    p.add_argument("--learned-eval", type=int, default=512)
+    p.add_argument("--learned-epochs", type=int, default=10)
+    p.add_argument("--learned-lr", type=float, default=1e-3)
+    p.add_argument("--only-learned", action="store_true",
+                   help="run the learned-initial-guess workload alone and print its JSON")
     p.add_argument("--no-autotune", action="store_true",
                    help="2D contexts keep the built-in launch-shape heuristics instead of "
                         "tuning them at set-up (sp_opts.autotune; results are bit-identical)")
@@ -349,6 +357,142 @@ def measure_batch(args, B, torch, dist, world):
             "by_grid": by_n, "data": "synthetic"}
 
 
+LEARNED_N, LEARNED_B, LEARNED_ELL, LEARNED_E = 256, 8, 8.0, 10.0
+
+
+def measure_learned(args, B, torch, dist, world):
+    """Learned initial guess on 2D 256^2 Schroedinger problems (l = 8, E = 10, random 8 x 8
+    lattice wells, b = 8), all sharing one context (one shift s; the solution does not
+    depend on s).  Training triples: `learned_media` potentials (seeds 5000 + m) x 8
+    random Gaussian sources (seeds 6000 + 8 m + r), each solved in FP64 by sp_factor +
+    sp_solve_many; the network input is (q / (10 l^2), g / c), its target u / c, with the
+    complex scale c = rms|g| e^{i phi}, phi = arg(sum g^2) / 2 (the solution is complex-linear
+    in the source, so c removes the source's size and phase).
+    Training: Adam on batches of 16 with a cosine learning-rate decay, every kernel in
+    the library.  Held-out: `learned_eval` problems (potential seed 7000 + i, source seed
+    8000 + i), each factored once and solved twice, from zero (sp_solve) and from the
+    network's guess (features + forward + guess + sp_solve_x0), both timed with CUDA
+    events; the solve stops at the same true residual 1e-8 in both arms."""
+    n, b, ell, E = LEARNED_N, LEARNED_B, LEARNED_ELL, LEARNED_E
+    N = n * n
+    nm, nrhs, ne = args.learned_media, 8, args.learned_eval
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    qs = 1.0 / (10.0 * ell * ell)
+    V0 = sm.lattice_wells_potential_2d(n, ell, 5000)
+    s, _ = B.sp_medium_schrodinger(2, n, ell, E, V0)
+    S = B.Solver(2, n, b, s, prec=B.SP_PREC_FP64, restart=200, device=local, max_rhs=nrhs)
+    net = B.Fno(n, sm.fno_initial_params(seed=4000), batch_max=16)
+    ntr = nm * nrhs
+    X = torch.empty((ntr, 3, N), dtype=torch.float32, device="cuda")
+    T = torch.empty((ntr, 2, N), dtype=torch.float32, device="cuda")
+    sig = torch.empty(ntr, dtype=torch.complex128, device="cuda")
+    g = torch.empty(N, dtype=torch.complex128, device="cuda")
+    t0 = time.perf_counter()
+    gen_iters = []
+    for m in range(nm):
+        V = sm.lattice_wells_potential_2d(n, ell, 5000 + m)
+        q = torch.from_numpy(B.sp_medium_schrodinger_at(2, n, ell, E, V, s)).cuda()
+        F = torch.from_numpy(np.stack([sm.random_gaussian_source(2, n, 6000 + nrhs * m + r) * ell ** 2
+                                       for r in range(nrhs)])).cuda()
+        U = torch.empty_like(F)
+        S.factor(q)
+        infos = S.solve_many(F.view(-1), U.view(-1))
+        gen_iters += [i["iters"] for i in infos]
+        for r in range(nrhs):
+            k = m * nrhs + r
+            S.green(F[r], g)
+            net.features(q, qs, g, X[k], sig[k:k + 1])
+            net.target(U[r], sig[k:k + 1], T[k])
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    # training
+    bs, epochs = 16, args.learned_epochs
+    nsteps = epochs * (ntr // bs)
+    lr0 = args.learned_lr
+    rng = np.random.default_rng(9000)
+    xb = torch.empty((bs, 3, N), dtype=torch.float32, device="cuda")
+    tb = torch.empty((bs, 2, N), dtype=torch.float32, device="cuda")
+    losses = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    step = 0
+    for ep in range(epochs):
+        perm = torch.from_numpy(rng.permutation(ntr)).cuda()
+        for j in range(ntr // bs):
+            idx = perm[j * bs:(j + 1) * bs]
+            torch.index_select(X, 0, idx, out=xb)
+            torch.index_select(T, 0, idx, out=tb)
+            lr = 0.5 * lr0 * (1 + np.cos(np.pi * step / nsteps))
+            last = j == ntr // bs - 1
+            L = net.train_step(xb, tb, bs, lr, sync=last)
+            if last:
+                losses.append(L)
+            step += 1
+    ev1.record()
+    torch.cuda.synchronize()
+    train_ms = ev0.elapsed_time(ev1)
+    # held-out evaluation
+    x1 = torch.empty((1, 3, N), dtype=torch.float32, device="cuda")
+    y1 = torch.empty((1, 2, N), dtype=torch.float32, device="cuda")
+    s1 = torch.empty(1, dtype=torch.complex128, device="cuda")
+    u0 = torch.empty(N, dtype=torch.complex128, device="cuda")
+    uz = torch.empty(N, dtype=torch.complex128, device="cuda")
+    ug = torch.empty(N, dtype=torch.complex128, device="cuda")
+    ms_zero = ms_guess = ms_factor = 0.0
+    it_zero, it_guess, g_rel, u_err, used, worst = [], [], [], [], 0, 0.0
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    for i in range(ne):
+        V = sm.lattice_wells_potential_2d(n, ell, 7000 + i)
+        q = torch.from_numpy(B.sp_medium_schrodinger_at(2, n, ell, E, V, s)).cuda()
+        f = torch.from_numpy(sm.random_gaussian_source(2, n, 8000 + i) * ell ** 2).cuda()
+        evs[0].record()
+        S.factor(q)
+        evs[1].record()
+        iz = S.solve(f, uz)
+        evs[2].record()
+        S.green(f, g)
+        net.features(q, qs, g, x1[0], s1)
+        net.forward(x1, y1, 1)
+        net.guess(y1[0], s1, u0)
+        evs[3].record()
+        ig = S.solve_x0(f, u0, ug)
+        evs[4].record()
+        torch.cuda.synchronize()
+        ms_factor += evs[0].elapsed_time(evs[1])
+        ms_zero += evs[1].elapsed_time(evs[2])
+        ms_guess += evs[2].elapsed_time(evs[4])
+        it_zero.append(iz["iters"])
+        it_guess.append(ig["iters"])
+        g_rel.append(ig["guess_relres"])
+        used += int(ig["guess_used"])
+        worst = max(worst, iz["true_relres"], ig["true_relres"])
+        u_err.append(float(torch.linalg.vector_norm(u0 - uz) / torch.linalg.vector_norm(uz)))
+    S.close()
+    net.close()
+    torch.cuda.synchronize()
+    zero_v = ne / ((ms_factor + ms_zero) / 1e3)
+    guess_v = ne / ((ms_factor + ms_guess) / 1e3)
+    return {"workload": f"learned initial guess: 2D {n}^2 Schroedinger, l = {ell:g}, E = {E:g}, random "
+                        f"8 x 8 lattice wells, b = {b}; {ntr} training triples ({nm} potentials x "
+                        f"{nrhs} sources), {ne} held-out (potential, source) pairs",
+            "network": "Fourier layers: 4 x width 32, 16 modes, projection 128; bf16 weights, "
+                       "bf16 activations, FP32 accumulation; Adam",
+            "form": "plain FP64 solve in both arms",
+            "value": guess_v, "unit": "solves/s", "zero_guess_value": zero_v,
+            "speedup_vs_zero_guess": guess_v / zero_v,
+            "iters_zero_mean": float(np.mean(it_zero)), "iters_guess_mean": float(np.mean(it_guess)),
+            "guess_relres_median": float(np.median(g_rel)), "guess_used": used,
+            "guess_solution_relerr_median": float(np.median(u_err)),
+            "max_true_relres": worst,
+            "ms_per_solve": {"factor": ms_factor / ne, "zero_solve": ms_zero / ne,
+                             "guess_and_solve": ms_guess / ne},
+            "data_generation_s": gen_s, "data_iters_mean": float(np.mean(gen_iters)),
+            "training": {"epochs": epochs, "batch": bs, "steps": nsteps, "lr0": lr0,
+                         "ms": train_ms, "samples_per_s": nsteps * bs / (train_ms / 1e3),
+                         "loss_by_epoch": losses},
+            "data": "synthetic"}
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
@@ -363,6 +507,12 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+
+    if args.only_learned:
+        if rank == 0:
+            print(json.dumps({"workload_learned": measure_learned(args, B, torch, dist, world)}),
+                  flush=True)
+        return
 
     probs = []
     for w in problems(args.problems):
@@ -572,6 +722,9 @@ def run_ours(args):
     wbatch = None
     if not args.no_batch:
         wbatch = measure_batch(args, B, torch, dist, world)
+    wlearn = None
+    if not args.no_learned:
+        wlearn = measure_learned(args, B, torch, dist, world)
     w3d = None
     if not args.no_3d:
         w3d = measure_3d(args, B, torch, flush, peaks, dist, world)
@@ -601,6 +754,7 @@ def run_ours(args):
             "chosen_form": chosen, "forms": {k: {kk: v[kk] for kk in ("value", "ms_per_step", "iters")}
                                              for k, v in forms.items()},
             "clocks": clocks, "cpu_baseline": cpu, "workload_3d": w3d, "workload_batch": wbatch,
+            "workload_learned": wlearn,
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -106,6 +106,8 @@ typedef struct {
   double *hist;        /* optional caller buffer for the estimate per iteration */
   int hist_cap;        /* its capacity (entries) */
   int hist_len;        /* entries written (iters + 1, capped) */
+  double guess_relres; /* sp_solve_x0: ||g - (I + G q) u0|| / ||g|| of the given start (1 otherwise) */
+  int guess_used;      /* sp_solve_x0: 1 if the start was kept, 0 if it fell back to zero */
 } sp_info;
 
 /* Fill *o with the defaults listed above. */
@@ -160,6 +162,16 @@ sp_status sp_solve_many(sp_ctx *ctx, int nrhs, const void *F_dev, void *U_dev, s
  * N complex128 on the device.  info may be NULL.  Returns SP_ERR_NOCONV when
  * maxit is reached above tol. */
 sp_status sp_solve(sp_ctx *ctx, const void *f_dev, void *u_dev, sp_info *info);
+
+/* sp_solve from the starting vector u0_dev (N complex128 on the device; may equal
+ * u_dev; NULL means zero).  The start is kept only if its residual
+ * ||g - (I + G q) u0|| is below ||g||, the residual of the zero vector; otherwise
+ * the solve starts from zero (info->guess_used = 0).  GMRES then runs on the
+ * residual equation, the iterations counted from the start, the same stopping test
+ * (relative to ||g||) and the same explicit true residual decide convergence.  A
+ * start already within tol returns after 0 iterations. */
+sp_status sp_solve_x0(sp_ctx *ctx, const void *f_dev, const void *u0_dev, void *u_dev,
+                      sp_info *info);
 
 /* Host-buffer forms of sp_factor and sp_solve: the same work with the input
  * copied host->device and the result device->host inside the call. */
@@ -226,6 +238,11 @@ sp_status sp_medium_helmholtz(int d, int n, double omega, const double *c_host, 
                               double *q_host);
 sp_status sp_medium_schrodinger(int d, int n, double ell, double E, const double *V_host,
                                 double *s_out, double *q_host);
+/* q = l^2 V - l^2 E + s for a caller-chosen shift s (a family of potentials sharing
+ * one context: the exact solution does not depend on s, only the preconditioner
+ * does).  The caller checks s with sp_setup (SP_ERR_RESONANT). */
+sp_status sp_medium_schrodinger_at(int d, int n, double ell, double E, const double *V_host,
+                                   double s, double *q_host);
 
 /* Kernel-class timing for roofline measurements: with sp_profile(ctx, 1) every
  * later call records CUDA events around its kernel launches on the context's

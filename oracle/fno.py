@@ -116,7 +116,7 @@ def spectral_forward(v: np.ndarray, M: int) -> np.ndarray:
     """V[b, c, ky', kx] = sum_{j1, j0} v[b, c, j1, j0] Fy[ky', j1] Fx[kx, j0]."""
     n = v.shape[-1]
     Fx, Fy = dft_mats(n, M)
-    return np.einsum("bcyx,ky,qx->bckq", v, Fy, Fx)
+    return np.einsum("bcyx,ky,qx->bckq", v, Fy, Fx, optimize=True)
 
 
 def spectral_inverse(Y: np.ndarray, n: int, w0: float, w1: float) -> np.ndarray:
@@ -126,7 +126,7 @@ def spectral_inverse(Y: np.ndarray, n: int, w0: float, w1: float) -> np.ndarray:
     Fx, Fy = dft_mats(n, M)
     w = np.full(M, w1)
     w[0] = w0
-    return np.einsum("bckq,ky,qx,q->bcyx", Y, Fy.conj(), Fx.conj(), w).real
+    return np.einsum("bckq,ky,qx,q->bcyx", Y, Fy.conj(), Fx.conj(), w, optimize=True).real
 
 
 def mix(V: np.ndarray, R: np.ndarray) -> np.ndarray:

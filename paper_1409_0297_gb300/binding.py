@@ -1,4 +1,4 @@
-"""ctypes binding of the C ABI in include/sp.h (argument marshalling only).
+"""ctypes binding of the C ABI in include/sp.h and include/sp_fno.h (argument marshalling only).
 
 Every function below forwards to the function of the same name in
 libsp_gb300.so; all arithmetic happens in the library's CUDA kernels.  Device
@@ -24,7 +24,10 @@ EXPORTED = [
     "sp_solve_host", "sp_matvec", "sp_green", "sp_qapply", "sp_get_table", "sp_stencil_table",
     "sp_front_sizes", "sp_level_info", "sp_costs", "sp_medium_helmholtz", "sp_medium_schrodinger", "sp_profile",
     "sp_profile_read", "sp_green_static", "sp_schur_update", "sp_tuning", "sp_solve_many",
-    "sp_destroy", "sp_status_str",
+    "sp_solve_x0", "sp_medium_schrodinger_at", "sp_destroy", "sp_status_str",
+    "sp_fno_param_count", "sp_fno_create", "sp_fno_destroy", "sp_fno_set_params",
+    "sp_fno_get_params", "sp_fno_forward", "sp_fno_gradient", "sp_fno_train_step",
+    "sp_fno_features", "sp_fno_guess", "sp_fno_target",
 ]
 PROF_CLASSES = ["assemble", "lu_panel", "lu_trsm", "lu_gemm", "qapply", "forward", "backward",
                 "fft", "krylov", "lu_trinv", "lu_tc"]
@@ -42,7 +45,19 @@ class sp_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int),
                 ("est_relres", ctypes.c_double), ("true_relres", ctypes.c_double),
                 ("s_used", ctypes.c_double), ("hist", ctypes.POINTER(ctypes.c_double)),
-                ("hist_cap", ctypes.c_int), ("hist_len", ctypes.c_int)]
+                ("hist_cap", ctypes.c_int), ("hist_len", ctypes.c_int),
+                ("guess_relres", ctypes.c_double), ("guess_used", ctypes.c_int)]
+
+
+class sp_fno_dims(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("c_in", ctypes.c_int), ("width", ctypes.c_int),
+                ("modes", ctypes.c_int), ("layers", ctypes.c_int), ("hidden", ctypes.c_int),
+                ("c_out", ctypes.c_int), ("batch_max", ctypes.c_int), ("act_fp32", ctypes.c_int)]
+
+
+class sp_adam(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double)]
 
 
 class SpError(RuntimeError):
@@ -83,6 +98,19 @@ def _load() -> ctypes.CDLL:
                                 ctypes.c_longlong, I, P]),
         "sp_tuning": (I, [P, I, pI, pI]),
         "sp_solve_many": (I, [P, I, P, P, ctypes.POINTER(sp_info)]),
+        "sp_solve_x0": (I, [P, P, P, P, ctypes.POINTER(sp_info)]),
+        "sp_medium_schrodinger_at": (I, [I, I, D, D, P, D, P]),
+        "sp_fno_param_count": (ctypes.c_longlong, [ctypes.POINTER(sp_fno_dims)]),
+        "sp_fno_create": (I, [ctypes.POINTER(sp_fno_dims), P, P, ctypes.POINTER(P)]),
+        "sp_fno_destroy": (V, [P]),
+        "sp_fno_set_params": (I, [P, P]),
+        "sp_fno_get_params": (I, [P, P]),
+        "sp_fno_forward": (I, [P, I, P, P]),
+        "sp_fno_gradient": (I, [P, I, P, P, P, pD, P]),
+        "sp_fno_train_step": (I, [P, I, P, P, ctypes.POINTER(sp_adam), pD]),
+        "sp_fno_features": (I, [P, P, D, P, P, P]),
+        "sp_fno_guess": (I, [P, P, P, P]),
+        "sp_fno_target": (I, [P, P, P, P]),
         "sp_destroy": (V, [P]),
         "sp_status_str": (ctypes.c_char_p, [I]),
     }
@@ -162,13 +190,22 @@ def _info(hist_cap: int):
 def _info_dict(info, hist, st):
     return dict(status=st, iters=info.iters, restarts=info.restarts, est_relres=info.est_relres,
                 true_relres=info.true_relres, s_used=info.s_used,
-                hist=hist[: info.hist_len].copy())
+                hist=hist[: info.hist_len].copy(), guess_relres=info.guess_relres,
+                guess_used=bool(info.guess_used))
 
 
 def sp_solve(ctx: int, f_dev: int, u_dev: int, hist_cap: int = 1024, allow_noconv=False) -> dict:
     info, hist = _info(hist_cap)
     st = LIB.sp_solve(ctx, f_dev, u_dev, ctypes.byref(info))
     _check(st, "sp_solve", (SP_OK, SP_ERR_NOCONV) if allow_noconv else (SP_OK,))
+    return _info_dict(info, hist, st)
+
+
+def sp_solve_x0(ctx: int, f_dev: int, u0_dev: int | None, u_dev: int, hist_cap: int = 1024,
+                allow_noconv=False) -> dict:
+    info, hist = _info(hist_cap)
+    st = LIB.sp_solve_x0(ctx, f_dev, u0_dev, u_dev, ctypes.byref(info))
+    _check(st, "sp_solve_x0", (SP_OK, SP_ERR_NOCONV) if allow_noconv else (SP_OK,))
     return _info_dict(info, hist, st)
 
 
@@ -278,6 +315,15 @@ def sp_medium_schrodinger(d: int, n: int, ell: float, E: float, V):
     return s.value, q
 
 
+def sp_medium_schrodinger_at(d: int, n: int, ell: float, E: float, V, s: float):
+    import numpy as np
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    q = np.empty_like(V)
+    _check(LIB.sp_medium_schrodinger_at(d, n, float(ell), float(E), V.ctypes.data, float(s),
+                                        q.ctypes.data), "sp_medium_schrodinger_at")
+    return q
+
+
 def sp_profile(ctx: int, enable: bool) -> None:
     _check(LIB.sp_profile(ctx, 1 if enable else 0), "sp_profile")
 
@@ -381,6 +427,13 @@ class Solver:
         import torch
         return sp_solve(self.ctx, self._vec(f, torch.complex128), self._vec(u, torch.complex128), **kw)
 
+    def solve_x0(self, f, u0, u, **kw):
+        """sp_solve from the starting vector u0 (None: zero)."""
+        import torch
+        p0 = None if u0 is None else self._vec(u0, torch.complex128)
+        return sp_solve_x0(self.ctx, self._vec(f, torch.complex128), p0,
+                           self._vec(u, torch.complex128), **kw)
+
     def table(self, t: int):
         return sp_get_table(self.ctx, t)
 
@@ -391,6 +444,113 @@ class Solver:
         if self.ctx:
             sp_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ learned initial guess
+def sp_fno_param_count(dims: sp_fno_dims) -> int:
+    return int(LIB.sp_fno_param_count(ctypes.byref(dims)))
+
+
+class Fno:
+    """Owns one network context of include/sp_fno.h.  Batches are contiguous torch
+    float32 CUDA tensors [batch][channels][n*n]; params a float32 host vector in the
+    header's order."""
+
+    def __init__(self, n: int, params, c_in: int = 3, width: int = 32, modes: int = 16,
+                 layers: int = 4, hidden: int = 128, c_out: int = 2, batch_max: int = 16,
+                 act_fp32: bool = False, stream: int = 0):
+        import numpy as np
+        self.dims = sp_fno_dims(n, c_in, width, modes, layers, hidden, c_out, batch_max,
+                                1 if act_fp32 else 0)
+        self.np = sp_fno_param_count(self.dims)
+        if self.np == 0:
+            raise SpError(SP_ERR_ARG, "sp_fno_param_count")
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != self.np:
+            raise ValueError(f"expected {self.np} parameters, got {p.size}")
+        self.N = n * n
+        h = ctypes.c_void_p()
+        _check(LIB.sp_fno_create(ctypes.byref(self.dims), p.ctypes.data, ctypes.c_void_p(stream),
+                                 ctypes.byref(h)), "sp_fno_create")
+        self.h = h.value
+
+    def _t(self, x, channels, batch, dtype=None):
+        import torch
+        dtype = dtype or torch.float32
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == dtype and
+                x.is_contiguous() and x.numel() >= batch * channels * self.N):
+            raise ValueError(f"expected a contiguous CUDA {dtype} tensor of at least "
+                             f"{batch} x {channels} x {self.N} entries")
+        return x.data_ptr()
+
+    def forward(self, x, y, batch: int):
+        _check(LIB.sp_fno_forward(self.h, batch, self._t(x, self.dims.c_in, batch),
+                                  self._t(y, self.dims.c_out, batch)), "sp_fno_forward")
+
+    def gradient(self, x, t, batch: int, y=None, want_grad: bool = True):
+        """(loss, gradient as a float32 numpy vector or None)."""
+        import numpy as np
+        loss = ctypes.c_double()
+        g = np.empty(self.np, dtype=np.float32) if want_grad else None
+        _check(LIB.sp_fno_gradient(self.h, batch, self._t(x, self.dims.c_in, batch),
+                                   self._t(t, self.dims.c_out, batch),
+                                   None if y is None else self._t(y, self.dims.c_out, batch),
+                                   ctypes.byref(loss), None if g is None else g.ctypes.data),
+               "sp_fno_gradient")
+        return loss.value, g
+
+    def train_step(self, x, t, batch: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+                   eps: float = 1e-8, sync: bool = False):
+        """One Adam step; returns the loss before the update when sync, else None."""
+        opt = sp_adam(lr, beta1, beta2, eps)
+        loss = ctypes.c_double()
+        _check(LIB.sp_fno_train_step(self.h, batch, self._t(x, self.dims.c_in, batch),
+                                     self._t(t, self.dims.c_out, batch), ctypes.byref(opt),
+                                     ctypes.byref(loss) if sync else None), "sp_fno_train_step")
+        return loss.value if sync else None
+
+    def params(self):
+        import numpy as np
+        p = np.empty(self.np, dtype=np.float32)
+        _check(LIB.sp_fno_get_params(self.h, p.ctypes.data), "sp_fno_get_params")
+        return p
+
+    def set_params(self, params):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != self.np:
+            raise ValueError(f"expected {self.np} parameters")
+        _check(LIB.sp_fno_set_params(self.h, p.ctypes.data), "sp_fno_set_params")
+
+    def features(self, q, q_scale: float, g, x_slot, scale_slot):
+        """One problem's input (3 x N floats at x_slot) and its complex scale c
+        (scale_slot: one complex128)."""
+        import torch
+        _check(LIB.sp_fno_features(self.h, self._t(q, 1, 1, torch.float64), float(q_scale),
+                                   self._t(g, 1, 1, torch.complex128), self._t(x_slot, 3, 1),
+                                   self._t(scale_slot, 0, 0, torch.complex128)), "sp_fno_features")
+
+    def guess(self, y_slot, scale_slot, u0):
+        import torch
+        _check(LIB.sp_fno_guess(self.h, self._t(y_slot, 2, 1), self._t(scale_slot, 0, 0, torch.complex128),
+                                self._t(u0, 1, 1, torch.complex128)), "sp_fno_guess")
+
+    def target(self, u, scale_slot, t_slot):
+        import torch
+        _check(LIB.sp_fno_target(self.h, self._t(u, 1, 1, torch.complex128),
+                                 self._t(scale_slot, 0, 0, torch.complex128), self._t(t_slot, 2, 1)),
+               "sp_fno_target")
+
+    def close(self):
+        if getattr(self, "h", None):
+            LIB.sp_fno_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:

@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsp_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["sp_host.cpp", "sp_fft.cu", "sp_factor.cu", "sp_solve.cu", "sp_krylov.cu", "sp_api.cu",
-           "sp_static.cu", "sp_tc.cu"]
+           "sp_static.cu", "sp_tc.cu", "sp_fno.cu"]
 HEADERS = ["sp_host.h", "sp_internal.h"]
 
 
@@ -35,7 +35,7 @@ def _stale(obj: str, src: str) -> bool:
         return True
     t = os.path.getmtime(obj)
     deps = [src] + [os.path.join(CSRC, h) for h in HEADERS] + \
-        [os.path.join(HERE, "..", "include", "sp.h")]
+        [os.path.join(HERE, "..", "include", h) for h in ("sp.h", "sp_fno.h")]
     return any(os.path.getmtime(p) > t for p in deps)
 
 

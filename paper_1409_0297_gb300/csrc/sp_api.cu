@@ -446,6 +446,16 @@ sp_status sp_medium_schrodinger(int d, int n, double ell, double E, const double
   return SP_OK;
 }
 
+sp_status sp_medium_schrodinger_at(int d, int n, double ell, double E, const double* V_host,
+                                   double s, double* q_host) {
+  if ((d != 2 && d != 3) || n < 2 || !V_host || !q_host) return SP_ERR_ARG;
+  long N = 1;
+  for (int a = 0; a < d; ++a) N *= n;
+  const double l2 = ell * ell;
+  for (long j = 0; j < N; ++j) q_host[j] = (l2 * V_host[j] - l2 * E) + s;
+  return SP_OK;
+}
+
 void sp_destroy(sp_ctx* c) {
   if (!c) return;
   int dev = 0;
@@ -790,45 +800,81 @@ sp_status sp_green(sp_ctx* c, const void* f_dev, void* g_dev) {
   return cuda_status(fft_green_apply(c->fft, (const double2*)f_dev, nullptr, false, (double2*)g_dev, c->stream));
 }
 
-static sp_status solve_mixed(sp_ctx* c, const double2* f, double2* u, sp_info* info);
+static sp_status solve_mixed(sp_ctx* c, const double2* f, const double2* u0, double2* u,
+                             sp_info* info);
 
-sp_status sp_solve(sp_ctx* c, const void* f_dev, void* u_dev, sp_info* info) {
-  if (!c || !f_dev || !u_dev) return SP_ERR_ARG;
-  ProfGuard pg_(c);
-  if (!c->factored) return SP_ERR_STATE;
-  SP_CK(cudaSetDevice(c->opts.device));
-  if (c->mixed) return solve_mixed(c, (const double2*)f_dev, (double2*)u_dev, info);
+// Start of a solve: g = G f and ||g|| (c->nrm + 2); with a starting vector u0 the
+// residual r = g - (I + G q) u0 and its norm (c->nrm + 3), kept only when it is below
+// ||g|| (otherwise the zero vector, r = g, is the better start).  *bnorm = ||g||,
+// *rel0 = the relative residual of the start.
+static sp_status solve_start(sp_ctx* c, const double2* f, const double2* u0, double2* u,
+                             double* bnorm, double* rel0, sp_info* info) {
   cudaStream_t st = c->stream;
   const long N = c->N;
-  double2* u = (double2*)u_dev;
   double* hsc = c->host_sc;
-  const int restart = c->opts.restart;
-  const double tol = c->opts.tol;
   if (info) {
     info->iters = 0;
     info->restarts = 0;
     info->hist_len = 0;
     info->s_used = c->s;
+    info->guess_relres = 1.0;
+    info->guess_used = 0;
   }
+  SP_CK(fft_green_apply(c->fft, f, nullptr, false, c->g, st));
+  SP_CK(kr_norm(c->g, N, c->K, c->nrm + 2, st));
+  if (u0) {
+    if (u0 != u) SP_CK(cudaMemcpyAsync(u, u0, sizeof(double2) * N, cudaMemcpyDeviceToDevice, st));
+    SP_CK(fft_green_apply(c->fft, u, c->q, true, c->t, st));
+    SP_CK(kr_sub(c->g, c->t, N, c->r, st));
+    SP_CK(kr_norm(c->r, N, c->K, c->nrm + 3, st));
+    SP_CK(cudaMemcpyAsync(hsc + 1, c->nrm + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  SP_CK(cudaMemcpyAsync(hsc, c->nrm + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+  SP_CK(cudaStreamSynchronize(st));
+  *bnorm = hsc[0];
+  *rel0 = 1.0;
+  if (u0 && hsc[0] > 0.0) {
+    const double g0 = hsc[1] / hsc[0];
+    if (info) info->guess_relres = g0;
+    if (g0 < 1.0) {  // the guess beats the zero vector
+      if (info) info->guess_used = 1;
+      *rel0 = g0;
+      return SP_OK;
+    }
+  }
+  SP_CK(cudaMemsetAsync(u, 0, sizeof(double2) * N, st));
+  SP_CK(cudaMemcpyAsync(c->r, c->g, sizeof(double2) * N, cudaMemcpyDeviceToDevice, st));
+  SP_CK(cudaMemcpyAsync(c->nrm + 3, c->nrm + 2, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return SP_OK;
+}
+
+static sp_status solve_impl(sp_ctx* c, const double2* f, const double2* u0, double2* u,
+                            sp_info* info) {
+  if (c->mixed) return solve_mixed(c, f, u0, u, info);
+  cudaStream_t st = c->stream;
+  const long N = c->N;
+  double* hsc = c->host_sc;
+  const int restart = c->opts.restart;
+  const double tol = c->opts.tol;
   auto push_hist = [&](double v) {
     if (info && info->hist && info->hist_len < info->hist_cap) info->hist[info->hist_len++] = v;
   };
-  // g = G f, ||g||
-  SP_CK(fft_green_apply(c->fft, (const double2*)f_dev, nullptr, false, c->g, st));
-  SP_CK(kr_norm(c->g, N, c->K, c->nrm + 2, st));
-  SP_CK(cudaMemcpyAsync(hsc, c->nrm + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
-  SP_CK(cudaMemsetAsync(u, 0, sizeof(double2) * N, st));
-  SP_CK(cudaStreamSynchronize(st));
-  const double bnorm = hsc[0];
-  push_hist(1.0);
+  double bnorm = 0.0, rel0 = 1.0;
+  sp_status s0 = solve_start(c, f, u0, u, &bnorm, &rel0, info);
+  if (s0 != SP_OK) return s0;
+  push_hist(rel0);
   if (bnorm == 0.0) {
+    SP_CK(cudaMemsetAsync(u, 0, sizeof(double2) * N, st));
+    SP_CK(cudaStreamSynchronize(st));
     if (info) info->true_relres = info->est_relres = 0.0;
     return SP_OK;
   }
-  SP_CK(cudaMemcpyAsync(c->r, c->g, sizeof(double2) * N, cudaMemcpyDeviceToDevice, st));
-  SP_CK(cudaMemcpyAsync(c->nrm + 3, c->nrm + 2, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (rel0 <= tol) {
+    if (info) info->true_relres = info->est_relres = rel0;
+    return SP_OK;
+  }
   int total = 0, restarts = 0;
-  double est_rel = 1.0, true_rel = 1.0;
+  double est_rel = rel0, true_rel = rel0;
   const int maxit = c->opts.maxit;
   for (;;) {
     SP_CK(kr_start(c->r, N, c->nrm + 3, c->V, c->gam, c->maxv + 1, st));
@@ -875,37 +921,49 @@ sp_status sp_solve(sp_ctx* c, const void* f_dev, void* u_dev, sp_info* info) {
   return true_rel <= tol ? SP_OK : SP_ERR_NOCONV;
 }
 
+sp_status sp_solve(sp_ctx* c, const void* f_dev, void* u_dev, sp_info* info) {
+  if (!c || !f_dev || !u_dev) return SP_ERR_ARG;
+  ProfGuard pg_(c);
+  if (!c->factored) return SP_ERR_STATE;
+  SP_CK(cudaSetDevice(c->opts.device));
+  return solve_impl(c, (const double2*)f_dev, nullptr, (double2*)u_dev, info);
+}
+
+sp_status sp_solve_x0(sp_ctx* c, const void* f_dev, const void* u0_dev, void* u_dev, sp_info* info) {
+  if (!c || !f_dev || !u_dev) return SP_ERR_ARG;
+  ProfGuard pg_(c);
+  if (!c->factored) return SP_ERR_STATE;
+  SP_CK(cudaSetDevice(c->opts.device));
+  return solve_impl(c, (const double2*)f_dev, (const double2*)u0_dev, (double2*)u_dev, info);
+}
+
 // GMRES-IR: outer refinement in FP64, inner flexible GMRES in complex64.
-static sp_status solve_mixed(sp_ctx* c, const double2* f, double2* u, sp_info* info) {
+static sp_status solve_mixed(sp_ctx* c, const double2* f, const double2* u0, double2* u,
+                             sp_info* info) {
   cudaStream_t st = c->stream;
   const long N = c->N;
   double* hsc = c->host_sc;
   const int restart = c->opts.restart;
   const double tol = c->opts.tol, tin = c->opts.inner_tol;
-  if (info) {
-    info->iters = 0;
-    info->restarts = 0;
-    info->hist_len = 0;
-    info->s_used = c->s;
-  }
   auto push_hist = [&](double v) {
     if (info && info->hist && info->hist_len < info->hist_cap) info->hist[info->hist_len++] = v;
   };
   float2* V32 = reinterpret_cast<float2*>(c->V);  // (restart + 1) complex64 vectors
-  SP_CK(fft_green_apply(c->fft, f, nullptr, false, c->g, st));
-  SP_CK(kr_norm(c->g, N, c->K, c->nrm + 2, st));
-  SP_CK(cudaMemcpyAsync(hsc, c->nrm + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
-  SP_CK(cudaMemsetAsync(u, 0, sizeof(double2) * N, st));
-  SP_CK(cudaStreamSynchronize(st));
-  const double bnorm = hsc[0];
-  push_hist(1.0);
+  double bnorm = 0.0, rel0 = 1.0;
+  sp_status s0 = solve_start(c, f, u0, u, &bnorm, &rel0, info);
+  if (s0 != SP_OK) return s0;
+  push_hist(rel0);
   if (bnorm == 0.0) {
+    SP_CK(cudaMemsetAsync(u, 0, sizeof(double2) * N, st));
+    SP_CK(cudaStreamSynchronize(st));
     if (info) info->true_relres = info->est_relres = 0.0;
     return SP_OK;
   }
-  SP_CK(cudaMemcpyAsync(c->r, c->g, sizeof(double2) * N, cudaMemcpyDeviceToDevice, st));
-  SP_CK(cudaMemcpyAsync(c->nrm + 3, c->nrm + 2, sizeof(double), cudaMemcpyDeviceToDevice, st));
-  double rel = 1.0, est_rel = 1.0;
+  if (rel0 <= tol) {
+    if (info) info->true_relres = info->est_relres = rel0;
+    return SP_OK;
+  }
+  double rel = rel0, est_rel = rel0;
   int total = 0, outer = 0;
   const int maxit = c->opts.maxit;
   for (;;) {
@@ -1022,6 +1080,8 @@ sp_status sp_solve_many(sp_ctx* c, int nrhs, const void* F_dev, void* U_dev, sp_
       infos[r].restarts = 0;
       infos[r].hist_len = 0;
       infos[r].s_used = c->s;
+      infos[r].guess_relres = 1.0;
+      infos[r].guess_used = 0;
     }
   // g_r = G f_r, ||g_r||
   SP_CK(fft_green_apply(c->fft, F, nullptr, false, c->g, st, nrhs));

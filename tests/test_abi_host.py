@@ -23,8 +23,8 @@ def _binding():
 
 def test_header_symbols_exported():
     B = _binding()
-    hdr = open(os.path.join(ROOT, "include", "sp.h")).read()
-    declared = set(re.findall(r"\b(sp_[a-z_]+)\s*\(", hdr))
+    hdr = "".join(open(os.path.join(ROOT, "include", h)).read() for h in ("sp.h", "sp_fno.h"))
+    declared = set(re.findall(r"\b(sp_[a-z0-9_]+)\s*\(", hdr))
     assert declared, "no declarations found"
     for name in declared:
         assert hasattr(B.LIB, name), name
@@ -101,3 +101,14 @@ def test_default_opts_layout():
     o = B.sp_default_opts()
     assert (o.maxit, o.restart, o.tol, o.pivot_tol) == (500, 200, 1e-8, 1e-14)
     assert (o.device, o.host_threads, o.inner_tol, o.autotune) == (0, 0, 1e-5, 0)
+
+
+def test_medium_schrodinger_at_fixed_shift():
+    """q(s) = l^2 V - l^2 E + s: at the context's own s it reproduces sp_medium_schrodinger,
+    and q(s') - q(s) = s' - s everywhere (the operator -Laplace - s + q does not change)."""
+    B = _binding()
+    V = np.random.default_rng(3).uniform(-15, 0, 32 * 32)
+    s, q = B.sp_medium_schrodinger(2, 32, 8.0, 10.0, V)
+    assert np.array_equal(B.sp_medium_schrodinger_at(2, 32, 8.0, 10.0, V, s), q)
+    q2 = B.sp_medium_schrodinger_at(2, 32, 8.0, 10.0, V, s + 7.5)
+    assert np.allclose(q2 - q, 7.5, rtol=0, atol=1e-12)
