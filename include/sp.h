@@ -95,6 +95,12 @@ typedef struct {
                         Q(j, gamma({j})) on the 3^d neighbourhood of every point j
                         (one T for all points by translation invariance), the
                         sparsifying operator of the earlier per-point construction */
+  int inv_block;     /* diagonal-block size of the levels that keep block inverses of
+                        L11 / U11 (their sweeps are chains of k / inv_block matrix-vector
+                        steps): 0 (default) = 2048 on levels with k >= 32768 and 512
+                        elsewhere, else a power of two in 64 ... 2048 for every level;
+                        larger blocks mean fewer, longer launches per sweep and more
+                        work in the block inverses */
 } sp_opts;
 
 typedef struct {

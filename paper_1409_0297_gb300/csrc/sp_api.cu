@@ -295,6 +295,7 @@ void sp_default_opts(sp_opts* o) {
   o->max_rhs = 1;
   o->setup_route = 0;
   o->stencil = 0;
+  o->inv_block = 0;
 }
 
 const char* sp_status_str(sp_status st) {
@@ -502,6 +503,10 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   if (c->opts.max_rhs < 1 || c->opts.max_rhs > sweep_max_vectors()) return SP_ERR_ARG;
   if (c->opts.setup_route != 0 && c->opts.setup_route != 1) return SP_ERR_ARG;
   if (c->opts.stencil != 0 && c->opts.stencil != 1) return SP_ERR_ARG;
+  {
+    const int ib = c->opts.inv_block;
+    if (ib != 0 && (ib < 64 || ib > 2048 || (ib & (ib - 1)) != 0)) return SP_ERR_ARG;
+  }
   const size_t RH = (size_t)c->opts.max_rhs;
   c->d = d;
   c->n = n;
@@ -622,9 +627,14 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
     // sweeps spread over the GPU; in the FP32 form every level does (the block
     // inverses cost little in FP32 and the sweeps become matrix-vector products)
     D.inv = S.nf < 152 || prec == SP_PREC_FP32 || vsz * (size_t)(S.m + S.k) > 192 * 1024;
+    // block inverses: 2048-wide blocks where the fronts are huge (the sweeps of the 3D
+    // root become 48 instead of 189 launch pairs; measured 3D 128^3 TF32: sweeps
+    // 1.95 -> 1.51 s per solve for +0.1 s of inversion), 512 elsewhere (in 2D the
+    // larger inverses cost more than the launches they save)
+    D.ib = c->opts.inv_block > 0 ? c->opts.inv_block : (S.k >= 32768 ? 2048 : kInvBlockSize);
     if (D.inv) {
       SP_CK(dalloc(c.get(), &D.tmp, vsz * RH * (size_t)S.nf * S.m));
-      scratch_bytes = std::max(scratch_bytes, fsz * invert_scratch_elems(S.nf, S.k));
+      scratch_bytes = std::max(scratch_bytes, fsz * invert_scratch_elems(S.nf, S.k, D.ib));
     }
     if (factor_grid_panel(prec, S.m)) gp_words = std::max(gp_words, grid_panel_pub_words(S.nf));
     if (factor_outer_block(prec, tc, S.m, S.k) > 0)

@@ -25,7 +25,6 @@ namespace {
 
 constexpr int kNB = 32;       // panel width
 constexpr int kTile = 64;     // Schur update tile (kTile x kTile per CTA)
-constexpr int kInvBlock = kInvBlockSize;  // diagonal-block size of the inverse-form levels
 constexpr int kTcMinFront = 1024;         // smallest front blocked for the tensor cores
 constexpr int kGridPanelCTAs = 152;       // CTAs of a grid-panel launch (one per SM)
 constexpr size_t kGridPanelSmem = 200 * 1024;  // staged rows of one grid-panel CTA
@@ -1199,8 +1198,8 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
   ProfScope pi(PROF_LU_TRINV, st);
   double bw = 0;
   if (L.inv) {
-    invert_triangles<T>(L, (T*)W.inv, kInvBlock, st);
-    const int Bz = kInvBlock < L.k ? kInvBlock : L.k;
+    invert_triangles<T>(L, (T*)W.inv, L.ib, st);
+    const int Bz = L.ib < L.k ? L.ib : L.k;
     bw = (2.0 / 3.0) * (double)Bz * Bz * L.k * L.nf;
   } else {
     dim3 gd((L.k + kNB - 1) / kNB, L.nf);
@@ -1254,8 +1253,8 @@ int factor_outer_block(int prec, bool tc, int m, int k) {
   return 0;
 }
 
-size_t invert_scratch_elems(int nf, int k) {
-  return (size_t)nf * ((size_t)2 * k * (kInvBlock + 1) + (size_t)k * (kInvBlock / 2));
+size_t invert_scratch_elems(int nf, int k, int ib) {
+  return (size_t)nf * ((size_t)2 * k * (ib + 1) + (size_t)k * (ib / 2));
 }
 
 size_t grid_panel_pub_words(int nf) { return (size_t)nf * 2 * kGridPanelMaxG * kPubWords; }

@@ -77,6 +77,7 @@ struct DevLevel {
   // (32 or 64) and general GEMM tile of the block inverses (32 or 64); every output
   // entry keeps its summation order, so the choice never changes a result
   int gemm_tile = 0, gen_tile = 0;
+  int ib = kInvBlockSize;   // diagonal-block size of the block inverses (inv levels)
 };
 
 // ---------------------------------------------------------------- FFT (sp_fft.cu)
@@ -117,7 +118,7 @@ cudaError_t factor_level(int prec, int d, DevLevel& L, const DevLevel* child, co
 // panel width used for fronts of size m (0 if the staged panel cannot fit)
 int factor_panel_width(int prec, int m);
 // entries of the triangular-inverse scratch of a level with nf fronts of k eliminated
-size_t invert_scratch_elems(int nf, int k);
+size_t invert_scratch_elems(int nf, int k, int ib);
 // whether fronts of size m use the cooperative grid panel; 8-byte words of its
 // publication buffer for nf fronts
 bool factor_grid_panel(int prec, int m);

@@ -314,8 +314,8 @@ __global__ void __launch_bounds__(1024) inv_gather_global_kernel(
   for (int j = threadIdx.x; j < k; j += blockDim.x) t[j] = y[j];
 }
 
-// Diagonal-block products of the levels whose diagonal blocks (size
-// kInvBlockSize) hold the inverses of those of L11 / U11; [j0, j1) is the block.
+// Diagonal-block products of the levels whose diagonal blocks (size L.ib) hold
+// the inverses of those of L11 / U11; [j0, j1) is the block.
 //   mode 0 (forward):  y[r] = tmp[r] + sum_{j0<=c<r} Linv[r,c] tmp[c]
 //   mode 3 (backward): y[r] = x[r] = sum_{r<=c<j1} Uinv[r,c] tmp[c]
 // (in the backward sweep y holds x1).  RB rows per CTA, 256 / RB column lanes per
@@ -596,8 +596,8 @@ cudaError_t forward_t(int d, DevLevel& L, const DevLevel* child, const void* rhs
     // right-looking: after the diagonal block [j0, j1) of y, the rows below take
     // that column block's contribution; the last block's rows are those of L21,
     // which hand their result to the parent as the update vector
-    for (int j0 = 0; j0 < L.k; j0 += kInvBlockSize) {
-      const int j1 = min(L.k, j0 + kInvBlockSize);
+    for (int j0 = 0; j0 < L.k; j0 += L.ib) {
+      const int j1 = min(L.k, j0 + L.ib);
       inv_gemv<VT, T>(0, L, j0, j1, j0, j1, sizeof(VT) * (j1 - j0), nullptr, nv, N, st);
       ++launches;
       if (j1 < L.m) {
@@ -633,9 +633,9 @@ cudaError_t backward_t(DevLevel& L, double2* x, void* part, int nv, long N, cuda
     }
     // right-looking: after the diagonal block [j0, j1) of x1, the rows above take
     // that column block's contribution
-    const int nbk = (L.k + kInvBlockSize - 1) / kInvBlockSize;
+    const int nbk = (L.k + L.ib - 1) / L.ib;
     for (int bi = nbk - 1; bi >= 0; --bi) {
-      const int j0 = bi * kInvBlockSize, j1 = min(L.k, j0 + kInvBlockSize);
+      const int j0 = bi * L.ib, j1 = min(L.k, j0 + L.ib);
       inv_gemv<VT, T>(3, L, j0, j1, j0, j1, sizeof(VT) * (j1 - j0), x, nv, N, st);
       ++launches;
       if (j0 > 0) {
