@@ -69,6 +69,8 @@ def parse():
     p.add_argument("--forms-3d", default="tf32",
                    help="comma list of the tensor-core forms timed at 3D 128^3 (tf32, tf32x3)")
     p.add_argument("--steps-3d", type=int, default=1)
+    p.add_argument("--setup-route-3d", type=int, default=1, choices=[0, 1],
+                   help="stencil set-up of the 3D workload: 0 TSQR + SVD, 1 Gram (default)")
     p.add_argument("--no-batch", action="store_true",
                    help="skip the batched heterogeneous 2D workload (64 problems x 8 right-hand sides)")
     p.add_argument("--batch-workers", type=int, default=8)
@@ -216,7 +218,8 @@ def measure_3d(args, B, torch, flush, peaks, dist, world):
     for name in args.forms_3d.split(","):
         prec = {"tf32": B.SP_PREC_TF32, "tf32x3": B.SP_PREC_TF32X3}[name]
         t0 = time.perf_counter()
-        S = B.Solver(d, n, b, s, prec=prec, device=int(os.environ.get("LOCAL_RANK", "0")))
+        S = B.Solver(d, n, b, s, prec=prec, device=int(os.environ.get("LOCAL_RANK", "0")),
+                     setup_route=args.setup_route_3d)
         setup_s = time.perf_counter() - t0
         for _ in range(args.warmup):
             S.factor(qd)
@@ -244,6 +247,7 @@ def measure_3d(args, B, torch, flush, peaks, dist, world):
         ach = tc_fl / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else 0.0
         out[name] = {
             "value": replica_value(1, world, ms), "ms_per_step": ms, "setup_s": setup_s,
+            "setup_route": "Gram" if args.setup_route_3d == 1 else "TSQR + SVD",
             "iters": infos[0]["iters"], "true_relres": infos[0]["true_relres"],
             "roofline": {"kernel": "lu_tc (tcgen05 TF32 Schur update)", "bound": "tensor",
                          "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s",

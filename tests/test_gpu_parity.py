@@ -351,3 +351,29 @@ def test_pointwise_stencil_variant(B, name, make):
         its[kind] = info["iters"]
         S.close()
     print(f"{name}: set stencils {its[0]} iterations, per-point stencils {its[1]}")
+
+
+@pytest.mark.parametrize("name,make", [SMALL[0], SMALL[4]], ids=[SMALL[0][0], SMALL[4][0]])
+@pytest.mark.parametrize("ib", [64, 128])
+def test_inverse_block_sizes(B, name, make, ib):
+    """Several diagonal blocks per inverse-form level (sp_opts.inv_block below the
+    eliminated counts: 2D 64^2 root k = 252, 3D 16^3 root k = 1352): the FP32 form's
+    preconditioner keeps its backward error, the FP64 form matches the oracle."""
+    w = make()
+    d, n, b = w["d"], w["n"], w["b"]
+    s, q, f = medium(w)
+    for prec in (0, 1):
+        S = B.Solver(d, n, b, s, prec=prec, inv_block=ib)
+        S.factor(dev(q))
+        tabs = _oracle_with_library_tables(S, d, n, b, s, q)
+        M = O.SparsifyingPreconditioner(d, n, b, s, q, tables=tabs)
+        r = sm.random_complex_vector(n ** d, 34)
+        z = torch.empty(n ** d, dtype=torch.complex128, device="cuda")
+        S.apply(dev(r), z)
+        if prec == 0:
+            assert rel(host(z), M.apply(r)) <= 1e-10
+        else:
+            assert M.apply_residual(r, host(z)) <= 5e-3
+        S.close()
+    with pytest.raises(B.SpError):
+        B.Solver(d, n, b, s, inv_block=96)  # not a power of two
