@@ -101,6 +101,10 @@ typedef struct {
                         elsewhere, else a power of two in 64 ... 2048 for every level;
                         larger blocks mean fewer, longer launches per sweep and more
                         work in the block inverses */
+  int tc_epilogue;   /* tensor-core forms: how the Schur update reads C.  0 (default)
+                        or 2: through a shared-memory ring that cp.async fills a tile
+                        ahead (three operand stages); 1: into registers only (four
+                        operand stages).  Both give the same bits. */
 } sp_opts;
 
 typedef struct {

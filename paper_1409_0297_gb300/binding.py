@@ -39,7 +39,7 @@ class sp_opts(ctypes.Structure):
                 ("host_threads", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("autotune", ctypes.c_int), ("max_rhs", ctypes.c_int),
                 ("setup_route", ctypes.c_int), ("stencil", ctypes.c_int),
-                ("inv_block", ctypes.c_int)]
+                ("inv_block", ctypes.c_int), ("tc_epilogue", ctypes.c_int)]
 
 
 class sp_info(ctypes.Structure):
@@ -372,7 +372,8 @@ class Solver:
     def __init__(self, d: int, n: int, b: int, s: float, prec: int = SP_PREC_FP64,
                  maxit: int = 500, restart: int = 200, tol: float = 1e-8, device: int = 0,
                  stream: int = 0, host_threads: int = 0, autotune: bool = False,
-                 max_rhs: int = 1, setup_route: int = 0, stencil: int = 0, inv_block: int = 0):
+                 max_rhs: int = 1, setup_route: int = 0, stencil: int = 0, inv_block: int = 0,
+                 tc_epilogue: int = 0):
         o = sp_default_opts()
         o.maxit, o.restart, o.tol, o.device = maxit, restart, tol, device
         o.host_threads = host_threads
@@ -381,6 +382,7 @@ class Solver:
         o.setup_route = setup_route
         o.stencil = stencil
         o.inv_block = inv_block
+        o.tc_epilogue = tc_epilogue
         self.d, self.n, self.b, self.s, self.prec = d, n, b, s, prec
         self.N = n ** d
         self.ctx = sp_setup(d, n, b, s, prec, o, stream)

@@ -296,6 +296,7 @@ void sp_default_opts(sp_opts* o) {
   o->setup_route = 0;
   o->stencil = 0;
   o->inv_block = 0;
+  o->tc_epilogue = 0;
 }
 
 const char* sp_status_str(sp_status st) {
@@ -507,6 +508,7 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
     const int ib = c->opts.inv_block;
     if (ib != 0 && (ib < 64 || ib > 2048 || (ib & (ib - 1)) != 0)) return SP_ERR_ARG;
   }
+  if (c->opts.tc_epilogue < 0 || c->opts.tc_epilogue > 2) return SP_ERR_ARG;
   const size_t RH = (size_t)c->opts.max_rhs;
   c->d = d;
   c->n = n;
@@ -518,6 +520,7 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   c->mixed = mixed;
   c->work.tc = tc;
   c->work.tc_split = split;
+  c->work.tc_epi = c->opts.tc_epilogue;
   if (mixed && !(c->opts.inner_tol > 0 && c->opts.inner_tol < 1)) return SP_ERR_ARG;
   c->stream = (cudaStream_t)stream;
   c->N = 1;

@@ -1056,7 +1056,8 @@ void schur_update(DevLevel& L, T* F, int M, int N, int K, long offA, long offB, 
     if (W.tc) {
       ProfScope pc(PROF_LU_TC, st);
       tc_schur_update(M, N, K, (const float*)(F + offA), L.m, mm, (const float*)(F + offB), L.m, mm,
-                      (float*)(F + offC), L.m, mm, L.nf, W.packA, W.packB, W.tc_split, status, st);
+                      (float*)(F + offC), L.m, mm, L.nf, W.packA, W.packB, W.tc_split, status, st,
+                      W.tc_epi);
       pc.done(fl, 3, st);
       return;
     }

@@ -106,6 +106,7 @@ struct FactorWork {
   float* packB = nullptr;
   bool tc = false;            // Schur updates of the blocked fronts on the tensor cores
   bool tc_split = false;      // ... as 3xTF32 (hi/lo split, FP32 accuracy)
+  int tc_epi = 0;             // epilogue of the tensor-core update (tc_schur_update's epi)
   // grid panel (fronts too tall for a cluster): per front 2 x kGridPanelMaxG
   // publication slots of grid_panel_pub_words() 8-byte words
   unsigned long long* gpub = nullptr;
@@ -140,9 +141,11 @@ constexpr int kTcMaxK = 512;
 size_t tc_pack_floats(int rows, int K, int batch, bool split);
 // C[M x N] -= A[M x K] B[K x N] (column-major, batch strides sA, sB, sC) with
 // TF32 tensor-core products and FP32 accumulation (split: 3xTF32); K <= kTcMaxK.
+// epi: 0 or 2 = C read a tile ahead through a shared-memory ring (three operand
+// stages), 1 = C in registers (four operand stages); both give the same bits.
 cudaError_t tc_schur_update(int M, int N, int K, const float* A, int lda, long sA, const float* B,
                             int ldb, long sB, float* C, int ldc, long sC, int batch, float* packA,
-                            float* packB, bool split, int* status, cudaStream_t st);
+                            float* packB, bool split, int* status, cudaStream_t st, int epi = 0);
 
 // ---------------------------------------------------------------- solve (sp_solve.cu)
 struct QTypeDev {

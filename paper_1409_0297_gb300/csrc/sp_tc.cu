@@ -16,8 +16,9 @@
 // accumulators in tensor memory (two, so one tile's epilogue overlaps the next
 // tile's products); eight epilogue warps read an accumulator with tcgen05.ld and
 // subtract it from C in global memory (the front keeps its column-major layout
-// with leading dimension m, which needs no alignment).  Persistent: one CTA per
-// SM walks the tiles of all fronts.
+// with leading dimension m, which needs no alignment, so C cannot go through TMA;
+// its loads are issued a tile ahead, half into registers and half by cp.async into
+// a shared-memory ring).  Persistent: one CTA per SM walks the tiles of all fronts.
 //
 // Every wait on an mbarrier is bounded (about 2 s of global timer); a wait that
 // runs out sets bit 2 of *status, the CTA drains the copies it issued, frees its
@@ -170,8 +171,10 @@ __device__ __forceinline__ void tile_coords(long t, int tilesM, int tilesN, int 
 // thread of warp 9 into one of two tensor-memory accumulators, and the epilogue
 // (warps 0-7) draining the other accumulator: warp w reads TMEM lanes 32 (w % 4)
 // .. +31 (tile rows) and column half w / 4, subtracts from C with the C loads of
-// the next chunk (also of the next tile) already in flight.
-template <int BN, int STAGES>
+// later chunks already in flight (CRING = 2: the next tile's four chunks, two in
+// registers and two in shared-memory slots after the STAGES operand stages;
+// CRING = 0: the next chunk, in registers).
+template <int BN, int STAGES, int CRING>
 __global__ void __launch_bounds__(kPThreads, 1) tc_gemm_sub_kernel(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M,
     int N, int nk, float* C, int ldc, long sC, int tilesM, int tilesN, long ntiles, int* status) {
@@ -273,63 +276,152 @@ __global__ void __launch_bounds__(kPThreads, 1) tc_gemm_sub_kernel(
       if (!mbar_wait(smem_u32(&drain), 0)) *ab = 1;
     }
   } else {
-    // epilogue: chunks of 32 columns, two register buffers in rotation so the C
-    // loads of the next chunk (and, at the end of a tile, of the next tile's first
-    // chunk) are in flight while the current one is stored
-    constexpr int kChunks = kHalf / 32;
-    const int qw = warp & 3, h = warp >> 2;
-    float cA[32], cB[32];
-    auto locate = [&](long tt, float** cp, int* ncol) {
-      int f, m0, n0;
-      tile_coords(tt, tilesM, tilesN, BN, &f, &m0, &n0);
-      const int row = m0 + qw * 32 + lane;
-      *ncol = row < M ? min(kHalf, N - (n0 + h * kHalf)) : 0;
-      *cp = C + (long)f * sC + row + (long)(n0 + h * kHalf) * ldc;
-    };
-    auto load = [&](float* buf, const float* cp, int ncol, int c0) {
+    if constexpr (CRING > 0) {
+      // epilogue: four chunks of 32 columns per tile; chunks 0 and 1 of the C tile are
+      // loaded into two register buffers, chunks 2 and 3 by cp.async into two
+      // shared-memory slots, each issued as soon as the same chunk of the previous tile
+      // has been stored, so a whole tile of C loads is in flight ahead of its use
+      static_assert(kHalf == 128, "the C ring assumes BN = 256");
+      const int qw = warp & 3, h = warp >> 2;
+      const int et = threadIdx.x;  // 0 .. 255
+      const uint32_t ring_s = base + STAGES * kStage;
+      const float* ring = reinterpret_cast<const float*>(smraw + (ring_s - smem_u32(smraw)));
+      float cA[32], cB[32];
+      auto locate = [&](long tt, float** cp, int* ncol) {
+        int f, m0, n0;
+        tile_coords(tt, tilesM, tilesN, BN, &f, &m0, &n0);
+        const int row = m0 + qw * 32 + lane;
+        *ncol = row < M ? min(kHalf, N - (n0 + h * kHalf)) : 0;
+        *cp = C + (long)f * sC + row + (long)(n0 + h * kHalf) * ldc;
+      };
+      auto load = [&](float* buf, const float* cp, int ncol, int c0) {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) buf[j] = c0 + j < ncol ? cp[(long)(c0 + j) * ldc] : 0.f;
-    };
-    long t = blockIdx.x;
-    float* cp = C;
-    int ncol = 0;
-    if (t < ntiles) {
-      locate(t, &cp, &ncol);
-      load(cA, cp, ncol, 0);
-    }
-    for (long i = 0; t < ntiles; t += gridDim.x, ++i) {
-      const int buf = (int)(i & 1);
-      const long u = i >> 1;
-      if (kChunks > 1) load(cB, cp, ncol, 32);
-      // one lane waits, the warp follows (tcgen05.ld below is warp-collective)
-      int okw = 0;
-      if (lane == 0) okw = mbar_wait_ab(smem_u32(&acc_full[buf]), (uint32_t)(u & 1), ab) ? 1 : 0;
-      __syncwarp();
-      okw = __shfl_sync(0xffffffffu, okw, 0);
-      if (!okw) break;
-      tc_fence_after();
-      const uint32_t ta = tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)(buf * BN + h * kHalf);
-      float* cp_nx = cp;
-      int ncol_nx = 0;
-      const bool has_next = t + gridDim.x < ntiles;
-      if (has_next) locate(t + gridDim.x, &cp_nx, &ncol_nx);
-#pragma unroll
-      for (int j = 0; j < kChunks; ++j) {
-        float* cur = (j & 1) ? cB : cA;
+        for (int j = 0; j < 32; ++j) buf[j] = c0 + j < ncol ? cp[(long)(c0 + j) * ldc] : 0.f;
+      };
+      auto sload = [&](int slot, const float* cp, int ncol, int c0) {
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j)
+          if (c0 + j < ncol)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                             ring_s + (uint32_t)(((slot * 32 + j) * 256 + et) * 4)),
+                         "l"(cp + (long)(c0 + j) * ldc)
+                         : "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
+      };
+      long t = blockIdx.x;
+      float* cp = C;
+      int ncol = 0;
+      if (t < ntiles) {
+        locate(t, &cp, &ncol);
+        load(cA, cp, ncol, 0);
+        load(cB, cp, ncol, 32);
+        sload(0, cp, ncol, 64);
+        sload(1, cp, ncol, 96);
+      }
+      for (long i = 0; t < ntiles; t += gridDim.x, ++i) {
+        const int buf = (int)(i & 1);
+        const long u = i >> 1;
+        int okw = 0;
+        if (lane == 0) okw = mbar_wait_ab(smem_u32(&acc_full[buf]), (uint32_t)(u & 1), ab) ? 1 : 0;
+        __syncwarp();
+        okw = __shfl_sync(0xffffffffu, okw, 0);
+        if (!okw) break;
+        tc_fence_after();
+        const uint32_t ta = tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)(buf * BN + h * kHalf);
+        float* cp_nx = cp;
+        int ncol_nx = 0;
+        if (t + gridDim.x < ntiles) locate(t + gridDim.x, &cp_nx, &ncol_nx);
         uint32_t v[32];
-        tmem_ld32(ta + 32 * j, v);
+        // chunk 0 (register buffer A)
+        tmem_ld32(ta, v);
 #pragma unroll
         for (int q = 0; q < 32; ++q)
-          if (32 * j + q < ncol) cp[(long)(32 * j + q) * ldc] = cur[q] - __uint_as_float(v[q]);
-        if (j + 2 < kChunks) load(cur, cp, ncol, 32 * (j + 2));
-        else if (j + 2 == kChunks && has_next) load(cur, cp_nx, ncol_nx, 0);
+          if (q < ncol) cp[(long)q * ldc] = cA[q] - __uint_as_float(v[q]);
+        load(cA, cp_nx, ncol_nx, 0);
+        // chunk 1 (register buffer B)
+        tmem_ld32(ta + 32, v);
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+          if (32 + q < ncol) cp[(long)(32 + q) * ldc] = cB[q] - __uint_as_float(v[q]);
+        load(cB, cp_nx, ncol_nx, 32);
+        // chunks 2 and 3 (shared-memory slots; at each point at most the newest
+        // group, the other slot's, is still in flight)
+#pragma unroll
+        for (int sl = 0; sl < 2; ++sl) {
+          asm volatile("cp.async.wait_group 1;" ::: "memory");
+          tmem_ld32(ta + 64 + 32 * sl, v);
+#pragma unroll
+          for (int q = 0; q < 32; ++q)
+            if (64 + 32 * sl + q < ncol)
+              cp[(long)(64 + 32 * sl + q) * ldc] = ring[(sl * 32 + q) * 256 + et] - __uint_as_float(v[q]);
+          sload(sl, cp_nx, ncol_nx, 64 + 32 * sl);
+        }
+        cp = cp_nx;
+        ncol = ncol_nx;
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&acc_empty[buf]));
       }
-      if (kChunks == 1 && has_next) load(cA, cp_nx, ncol_nx, 0);
-      cp = cp_nx;
-      ncol = ncol_nx;
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&acc_empty[buf]));
+      asm volatile("cp.async.wait_all;" ::: "memory");
+    } else {
+      // epilogue: chunks of 32 columns, two register buffers in rotation so the C
+      // loads of the next chunk (and, at the end of a tile, of the next tile's first
+      // chunk) are in flight while the current one is stored
+      constexpr int kChunks = kHalf / 32;
+      const int qw = warp & 3, h = warp >> 2;
+      float cA[32], cB[32];
+      auto locate = [&](long tt, float** cp, int* ncol) {
+        int f, m0, n0;
+        tile_coords(tt, tilesM, tilesN, BN, &f, &m0, &n0);
+        const int row = m0 + qw * 32 + lane;
+        *ncol = row < M ? min(kHalf, N - (n0 + h * kHalf)) : 0;
+        *cp = C + (long)f * sC + row + (long)(n0 + h * kHalf) * ldc;
+      };
+      auto load = [&](float* buf, const float* cp, int ncol, int c0) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) buf[j] = c0 + j < ncol ? cp[(long)(c0 + j) * ldc] : 0.f;
+      };
+      long t = blockIdx.x;
+      float* cp = C;
+      int ncol = 0;
+      if (t < ntiles) {
+        locate(t, &cp, &ncol);
+        load(cA, cp, ncol, 0);
+      }
+      for (long i = 0; t < ntiles; t += gridDim.x, ++i) {
+        const int buf = (int)(i & 1);
+        const long u = i >> 1;
+        if (kChunks > 1) load(cB, cp, ncol, 32);
+        // one lane waits, the warp follows (tcgen05.ld below is warp-collective)
+        int okw = 0;
+        if (lane == 0) okw = mbar_wait_ab(smem_u32(&acc_full[buf]), (uint32_t)(u & 1), ab) ? 1 : 0;
+        __syncwarp();
+        okw = __shfl_sync(0xffffffffu, okw, 0);
+        if (!okw) break;
+        tc_fence_after();
+        const uint32_t ta = tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)(buf * BN + h * kHalf);
+        float* cp_nx = cp;
+        int ncol_nx = 0;
+        const bool has_next = t + gridDim.x < ntiles;
+        if (has_next) locate(t + gridDim.x, &cp_nx, &ncol_nx);
+#pragma unroll
+        for (int j = 0; j < kChunks; ++j) {
+          float* cur = (j & 1) ? cB : cA;
+          uint32_t v[32];
+          tmem_ld32(ta + 32 * j, v);
+#pragma unroll
+          for (int q = 0; q < 32; ++q)
+            if (32 * j + q < ncol) cp[(long)(32 * j + q) * ldc] = cur[q] - __uint_as_float(v[q]);
+          if (j + 2 < kChunks) load(cur, cp, ncol, 32 * (j + 2));
+          else if (j + 2 == kChunks && has_next) load(cur, cp_nx, ncol_nx, 0);
+        }
+        if (kChunks == 1 && has_next) load(cA, cp_nx, ncol_nx, 0);
+        cp = cp_nx;
+        ncol = ncol_nx;
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&acc_empty[buf]));
+      }
     }
   }
   __syncthreads();
@@ -422,8 +514,14 @@ cudaError_t encode_operand(CUtensorMap* map, float* P, int rows, int Kp, int bat
 }
 
 constexpr int kBN = 256;
-constexpr int kStages = 4;
+// two configurations of the same kernel: three operand stages plus two 32 KB
+// shared-memory slots that cp.async fills with C a tile ahead (the default: the
+// epilogue's C loads limit the update; 3D 128^3 TF32 factor: 1.64 s of updates
+// against 1.72 s), or four stages with the C loads in registers only
+constexpr int kStages = 4, kStagesRing = 3;
 constexpr size_t kSmem = (size_t)kStages * (kBM * kBK * 4 + kBN * kBK * 4) + 1024;
+constexpr size_t kSmemRing =
+    (size_t)kStagesRing * (kBM * kBK * 4 + kBN * kBK * 4) + 1024 + 2 * 32 * 256 * 4;
 int g_num_sms[64] = {0};
 
 }  // namespace
@@ -434,13 +532,16 @@ size_t tc_pack_floats(int rows, int K, int batch, bool split) {
 
 cudaError_t tc_schur_update(int M, int N, int K, const float* A, int lda, long sA, const float* B,
                             int ldb, long sB, float* C, int ldc, long sC, int batch, float* packA,
-                            float* packB, bool split, int* status, cudaStream_t st) {
+                            float* packB, bool split, int* status, cudaStream_t st, int epi) {
   if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return cudaSuccess;
   if (K > kTcMaxK || batch > 65535 || !packA || !packB) return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_sub_kernel<kBN, kStages>,
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_sub_kernel<kBN, kStages, 0>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(tc_gemm_sub_kernel<kBN, kStagesRing, 2>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemRing);
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -465,8 +566,12 @@ cudaError_t tc_schur_update(int M, int N, int K, const float* A, int lda, long s
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!g_num_sms[dev]) cudaDeviceGetAttribute(&g_num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
   const unsigned grid = (unsigned)std::min<long>(ntiles, std::max(1, g_num_sms[dev]));
-  tc_gemm_sub_kernel<kBN, kStages><<<grid, kPThreads, kSmem, st>>>(
-      ta, tb, M, N, Ke / kBK, C, ldc, sC, tilesM, tilesN, ntiles, status);
+  if (epi != 1)
+    tc_gemm_sub_kernel<kBN, kStagesRing, 2><<<grid, kPThreads, kSmemRing, st>>>(
+        ta, tb, M, N, Ke / kBK, C, ldc, sC, tilesM, tilesN, ntiles, status);
+  else
+    tc_gemm_sub_kernel<kBN, kStages, 0><<<grid, kPThreads, kSmem, st>>>(
+        ta, tb, M, N, Ke / kBK, C, ldc, sC, tilesM, tilesN, ntiles, status);
   return cudaGetLastError();
 }
 
