@@ -4,10 +4,10 @@
  * A Fourier-layer network (the Fourier neural operator of Li et al., ICLR 2021,
  * Section 4) maps the medium and the right-hand side of one problem to a starting
  * vector u0 for GMRES (sp_solve_x0 in sp.h).  The paper itself has no learned part:
- * the zero-guess preconditioned solve stays both the fallback (a guess whose residual
- * exceeds that of zero is dropped) and the judge of the guess (the true residual
- * decides convergence).  Training data are (medium, source, solution) triples that the
- * solver of sp.h produces.
+ * the zero-guess preconditioned solve stays the fallback (a guess whose residual
+ * exceeds that of zero is dropped) and the measure of the guess (the same explicit
+ * true residual decides convergence).  Training data are (medium, source, solution)
+ * triples that the solver of sp.h produces.
  *
  * Network (L Fourier layers of width W, M modes per axis, projection width H):
  *   v_0 = P a + p;  h_l = W_l v_l + b_l + K_l v_l;  v_{l+1} = gelu(h_l) (l < L-1),

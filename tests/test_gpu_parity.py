@@ -242,7 +242,7 @@ def test_solve_512(B, which, prec):
     rows = np.random.default_rng(5).choice(n * n, 4000, replace=False)
     res = O.sampled_apply_residual(d, n, b, tabs, q, r, host(z), rows)
     # FP32 factor: LU backward error ~ m eps32 (m = 2044, eps32 = 6e-8: 1.2e-4) times
-    # the growth of the fronts and ||P|| ||z|| / ||Q r||; the FP32 form is judged by
+    # the growth of the fronts and ||P|| ||z|| / ||Q r||; the FP32 form is assessed by
     # the FP64 GMRES reaching 1e-8 below, this only guards against a broken factor
     # (TF32 Schur updates: unit roundoff 2^-11, ten times the FP32 allowance)
     assert res <= {0: 1e-10, 1: 5e-3, 2: 5e-3, 3: 5e-2, 4: 5e-3}[prec], res
