@@ -74,6 +74,8 @@ def parse():
     p.add_argument("--no-batch", action="store_true",
                    help="skip the batched heterogeneous 2D workload (64 problems x 8 right-hand sides)")
     p.add_argument("--batch-workers", type=int, default=8)
+    p.add_argument("--no-batch-fp64", action="store_true",
+                   help="skip the plain-FP64 arm of the batched workload")
     p.add_argument("--no-learned", action="store_true",
                    help="skip the learned-initial-guess workload")
     p.add_argument("--learned-media", type=int, default=512)
@@ -288,7 +290,7 @@ def measure_batch(args, B, torch, dist, world):
     t0 = time.perf_counter()
     streams = [torch.cuda.Stream() for _ in probs]
 
-    def setup(i):
+    def setup(i, prec=B.SP_PREC_FP32, batched=True):
         p = probs[i]
         if p["kind"] == "helmholtz":
             s, q = B.sp_medium_helmholtz(2, p["n"], p["omega"], p["c"])
@@ -296,8 +298,8 @@ def measure_batch(args, B, torch, dist, world):
         else:
             s, q = B.sp_medium_schrodinger(2, p["n"], p["ell"], p["E"], p["V"])
             scale = p["ell"] ** 2
-        S = B.Solver(2, p["n"], p["b"], s, prec=B.SP_PREC_FP32, restart=64, device=local,
-                     stream=streams[i].cuda_stream, max_rhs=len(p["rhs"]),
+        S = B.Solver(2, p["n"], p["b"], s, prec=prec, restart=64, device=local,
+                     stream=streams[i].cuda_stream, max_rhs=len(p["rhs"]) if batched else 1,
                      host_threads=max(1, (os.cpu_count() or 1) // nw))
         return S, q, [np.ascontiguousarray(f * scale) for f in p["rhs"]]
 
@@ -313,20 +315,24 @@ def measure_batch(args, B, torch, dist, world):
     order = sorted(range(len(probs)), key=lambda i: -probs[i]["n"])  # largest first
     groups = [order[w::nw] for w in range(nw)]
 
-    def work(w, infos):
+    def work(w, infos, plain=False):
         for i in groups[w]:
             c = ctx[i]
             c["S"].factor(c["q"])
-            for inf in c["S"].solve_many(c["F"].view(-1), c["U"].view(-1)):
-                infos.append((i, inf))
+            if plain:  # one sp_solve per right-hand side
+                for r in range(c["F"].shape[0]):
+                    infos.append((i, c["S"].solve(c["F"][r], c["U"][r])))
+            else:
+                for inf in c["S"].solve_many(c["F"].view(-1), c["U"].view(-1)):
+                    infos.append((i, inf))
 
-    def step(infos):
+    def step(infos, plain=False):
         start = torch.cuda.Event(enable_timing=True)
         start.record()
         for i in range(len(probs)):
             streams[i].wait_event(start)
         with cf.ThreadPoolExecutor(nw) as ex:
-            list(ex.map(lambda w: work(w, infos), range(nw)))
+            list(ex.map(lambda w: work(w, infos, plain), range(nw)))
         cur = torch.cuda.current_stream()
         for st_ in streams:
             ev = torch.cuda.Event()
@@ -352,6 +358,24 @@ def measure_batch(args, B, torch, dist, world):
     for c in ctx:
         c["S"].close()
     torch.cuda.synchronize()
+    # the same 512 solves in the plain FP64 form, one sp_solve per right-hand side
+    # (same host threads and streams): the reference for the precision + batching gain
+    plain = None
+    if not args.no_batch_fp64:
+        with cf.ThreadPoolExecutor(nw) as ex:
+            made = list(ex.map(lambda i: setup(i, B.SP_PREC_FP64, False), range(len(probs))))
+        for c, (S, q, fs) in zip(ctx, made):
+            c["S"] = S
+        torch.cuda.synchronize()
+        step([], True)  # warm-up (one step: the plain form is slow)
+        pinfos = []
+        pms = reduce_max(step(pinfos, True), dist)
+        for c in ctx:
+            c["S"].close()
+        torch.cuda.synchronize()
+        plain = {"form": "plain FP64, one sp_solve per right-hand side", "value":
+                 replica_value(nsolve, world, pms), "ms_per_step": pms,
+                 "max_true_relres": max(inf["true_relres"] for _, inf in pinfos)}
     return {"workload": "batched 2D: 64 problems, n drawn from {128,192,256,384,512} (seed 3000), "
                         "half Helmholtz (omega = 2 pi n / 8, GRF c) half Schroedinger (l x l "
                         "lattice wells, l in {4,8,16}, E = 10), 8 random Gaussian sources each",
@@ -362,6 +386,8 @@ def measure_batch(args, B, torch, dist, world):
                            "sides of a problem in one sp_solve_many (restart 64)",
             "setup_s": setup_s,
             "max_true_relres": max(inf["true_relres"] for _, inf in infos),
+            "plain_fp64": plain,
+            "speedup_vs_plain_fp64": (replica_value(nsolve, world, ms) / plain["value"]) if plain else None,
             "by_grid": by_n, "data": "synthetic"}
 
 

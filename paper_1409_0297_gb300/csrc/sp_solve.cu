@@ -434,6 +434,8 @@ __global__ void __launch_bounds__(256) gemv_kernel(GemvArgs ga, const T* __restr
     if (r < ga.rhi) {
       const T* Ar = A + r + (long)c0 * m;
       int j = 0;
+      // 8 column loads in flight per thread: a launch costs (columns of a split) / 8
+      // memory latencies at least (16 was measured slower on the large 3D launches)
       for (; j + 8 <= cn; j += 8) {
         T a[8];
 #pragma unroll
@@ -513,10 +515,16 @@ void set_attrs() {
 constexpr int kGemvTarget = 1216;  // CTAs a row-parallel product aims for (8 per SM)
 constexpr int kMaxVec = 8;         // stacked vectors of one sweep launch
 
+// Column splits of one row-parallel product: enough CTAs that the active rows fill
+// kGemvTarget CTAs of 256 (a CTA of a 64-row front holds 64 active threads, so such
+// fronts split 4 times as far), at least 32 columns per split.  Whenever it splits,
+// splits x fronts x rows stays below 2 kGemvTarget 256 (sweep_partial_bytes).
 int gemv_splits(int rows, int cols, int nf) {
+  const long rpt = std::min(256, rows);
   const long tiles = (long)((rows + 255) / 256) * nf;
-  if (tiles >= kGemvTarget || cols < 256) return 1;
-  return (int)std::max<long>(1, std::min<long>((kGemvTarget + tiles - 1) / tiles, cols / 128));
+  if (cols < 64) return 1;
+  const long want = ((long)kGemvTarget * 256 + rpt * tiles - 1) / (rpt * tiles);
+  return (int)std::max<long>(1, std::min<long>(want, cols / 32));
 }
 
 // One off-diagonal product (gemv_kernel, + gemv_finish_kernel when split) for nv
