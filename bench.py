@@ -221,8 +221,10 @@ def cpu_sample_text(iters: int, seconds: float) -> str:
 
 
 def cpu_baseline() -> dict:
-    """Bounded oracle sample (see the returned 'sample' text)."""
+    """Bounded oracle sample (see the returned 'sample' text), after one untimed warm-up
+    sample (imports, first factorisation)."""
     prep = cpu_prep()
+    cpu_sample(prep)
     t0 = time.perf_counter()
     it = cpu_sample(prep)
     dt = time.perf_counter() - t0
