@@ -7,7 +7,9 @@ Workload (one "step"): the 2D 512^2 problem pair, complex128 unknowns, b = 16,
       (depth U[5, 15], width 0.15 l-units),
 each with a random-centre, random-phase Gaussian source; for each problem the
 step factors P = Q + C q (sp_factor) and solves to a true relative residual of
-1e-8 (sp_solve).  One step = 2 solves.  The stencil set-up (sp_setup, once per
+1e-8 (sp_solve).  One step = 2 solves; the two independent problems run side by
+side, each context on its own CUDA stream driven by its own host thread
+(--serial-pair: in turn on one stream).  The stencil set-up (sp_setup, once per
 shift s) is outside the timed region.  `value` is the plain FP64 form; the
 reduced-precision preconditioner forms (FP32 factor and sweeps, with or without
 TF32 / 3xTF32 tensor-core Schur updates, GMRES-IR; FP64 operator, Gram-Schmidt
@@ -74,6 +76,8 @@ def parse():
     p.add_argument("--no-batch", action="store_true",
                    help="skip the batched heterogeneous 2D workload (64 problems x 8 right-hand sides)")
     p.add_argument("--batch-workers", type=int, default=8)
+    p.add_argument("--serial-pair", action="store_true",
+                   help="run the two problems of a 2D step in turn on one stream")
     p.add_argument("--no-batch-fp64", action="store_true",
                    help="skip the plain-FP64 arm of the batched workload")
     p.add_argument("--no-learned", action="store_true",
@@ -587,11 +591,34 @@ def run_ours(args):
         probs.append(dict(d=d, n=n, b=b, s=s, q=q, f=np.ascontiguousarray(f)))
     N = probs[0]["n"] ** probs[0]["d"]
 
+    # the two problems of a step are independent: each context gets its own CUDA stream
+    # and the step drives them from two host threads (--serial-pair: one stream, in turn)
+    import concurrent.futures as cf
+    pair_streams = None if args.serial_pair else [torch.cuda.Stream() for _ in probs]
+    pair_pool = None if args.serial_pair else cf.ThreadPoolExecutor(len(probs))
+
+    def run_pair(fn, n_items, concurrent=True):
+        if pair_streams is None or not concurrent:
+            for i in range(n_items):
+                fn(i)
+            return
+        cur = torch.cuda.current_stream()
+        ev = torch.cuda.Event()
+        ev.record(cur)
+        for s_ in pair_streams:
+            s_.wait_event(ev)
+        list(pair_pool.map(fn, range(n_items)))
+        for s_ in pair_streams:
+            e_ = torch.cuda.Event()
+            e_.record(s_)
+            cur.wait_event(e_)
+
     def make(prec):
         out = []
-        for p in probs:
+        for i, p in enumerate(probs):
             S = B.Solver(p["d"], p["n"], p["b"], p["s"], prec=prec, device=local,
-                         autotune=not args.no_autotune)
+                         autotune=not args.no_autotune,
+                         stream=pair_streams[i].cuda_stream if pair_streams else 0)
             out.append(dict(S=S, q=torch.from_numpy(p["q"]).cuda(),
                             f=torch.from_numpy(p["f"]).cuda(),
                             u=torch.empty(N, dtype=torch.complex128, device="cuda")))
@@ -651,12 +678,17 @@ def run_ours(args):
             c["S"].close()
         return
 
-    def step(ctxs, infos=None):
-        for c in ctxs:
+    def step(ctxs, infos=None, concurrent=True):
+        res = [None] * len(ctxs)
+
+        def one(i):
+            c = ctxs[i]
             c["S"].factor(c["q"])
-            info = c["S"].solve(c["f"], c["u"])
-            if infos is not None:
-                infos.append(info)
+            res[i] = c["S"].solve(c["f"], c["u"])
+
+        run_pair(one, len(ctxs), concurrent)
+        if infos is not None:
+            infos.extend(res)
 
     def timed(ctxs, K, W):
         for _ in range(W):
@@ -697,14 +729,17 @@ def run_ours(args):
     pin_f = [torch.from_numpy(p["f"]).pin_memory() for p in probs]
     pin_u = [torch.empty(N, dtype=torch.complex128).pin_memory() for _ in probs]
     import ctypes
-    info_c = B.sp_info()
+
+    infos_c = [B.sp_info() for _ in probs]
 
     def step_host():
-        for c, q, f, u in zip(fp64, pin_q, pin_f, pin_u):
+        def one(i):
+            c, q, f, u = fp64[i], pin_q[i], pin_f[i], pin_u[i]
             B._check(B.LIB.sp_factor_host(c["S"].ctx, ctypes.c_void_p(q.data_ptr())), "sp_factor_host")
             B._check(B.LIB.sp_solve_host(c["S"].ctx, ctypes.c_void_p(f.data_ptr()),
-                                         ctypes.c_void_p(u.data_ptr()), ctypes.byref(info_c)),
+                                         ctypes.c_void_p(u.data_ptr()), ctypes.byref(infos_c[i])),
                      "sp_solve_host")
+        run_pair(one, len(probs))
     step_host()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -717,7 +752,7 @@ def run_ours(args):
     def profiled(ctxs):
         for c in ctxs:
             B.sp_profile(c["S"].ctx, True)
-        step(ctxs)
+        step(ctxs, concurrent=False)  # one problem at a time: per-class times do not overlap
         out = {}
         for c in ctxs:
             for k, (ms_, nl, wk) in B.sp_profile_read(c["S"].ctx).items():
@@ -812,7 +847,9 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "grid": "512^2", "b": 16, "solves_per_step": 2,
                        "tol": 1e-8, "l2": "flushed between steps (256 MB write)",
                        "autotune": not args.no_autotune, "fp64_tile_shapes_by_level": shapes64,
-                       "parallelism": "replicas" if world > 1 else "1 GPU"},
+                       "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "pair_concurrency": "one stream" if args.serial_pair else
+                       "two CUDA streams, one host thread per problem"},
             "iters": [i["iters"] for i in infos64[:solves_per_step]],
             "true_relres": [i["true_relres"] for i in infos64[:solves_per_step]],
             "e2e": {"value": e2e_value, "unit": UNIT,
