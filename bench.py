@@ -75,7 +75,7 @@ def parse():
                    help="stencil set-up of the 3D workload: 0 TSQR + SVD, 1 Gram (default)")
     p.add_argument("--no-batch", action="store_true",
                    help="skip the batched heterogeneous 2D workload (64 problems x 8 right-hand sides)")
-    p.add_argument("--batch-workers", type=int, default=8)
+    p.add_argument("--batch-workers", type=int, default=16)
     p.add_argument("--serial-pair", action="store_true",
                    help="run the two problems of a 2D step in turn on one stream")
     p.add_argument("--no-batch-fp64", action="store_true",
