@@ -49,3 +49,33 @@ def test_single_rank_helpers():
     import bench
     assert bench.reduce_max(3.5) == 3.5
     assert abs(bench.replica_value(2, 1, 250.0) - 8.0) < 1e-12
+
+
+def test_reference_arm_json_contract(tmp_path):
+    """bench.py --impl reference: one JSON line with the arm's metric, a measured value
+    over the K timed steps (not extrapolated), the reference-arm keys, and nothing
+    printed by ranks other than 0."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, RANK="0")
+    p = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                       cwd=root, env=env, timeout=600)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [l for l in p.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "solves/s" and d["higher_is_better"]
+    assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 0
+    assert abs(d["ms_per_step"] - 1e3 / d["value"]) <= 1e-6 * d["ms_per_step"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    # other ranks exit 0 without work or output
+    env1 = dict(os.environ, RANK="1")
+    p1 = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference"],
+                        capture_output=True, text=True, cwd=root, env=env1, timeout=120)
+    assert p1.returncode == 0 and not [l for l in p1.stdout.splitlines() if l.startswith("{")]
