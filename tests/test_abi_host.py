@@ -101,6 +101,27 @@ def test_default_opts_layout():
     o = B.sp_default_opts()
     assert (o.maxit, o.restart, o.tol, o.pivot_tol) == (500, 200, 1e-8, 1e-14)
     assert (o.device, o.host_threads, o.inner_tol, o.autotune) == (0, 0, 1e-5, 0)
+    assert (o.max_rhs, o.setup_route, o.stencil, o.inv_block, o.tc_epilogue) == (1, 0, 0, 0, 0)
+
+
+def test_fno_param_count_matches_oracle_layout():
+    """The library's parameter count of the network equals the oracle's layout and the
+    seeded initial weights' length; dims outside the documented ranges give 0."""
+    from oracle import fno as F
+    B = _binding()
+    for D in (F.FnoDims(n=256), F.FnoDims(n=64, c_in=3, width=8, modes=6, layers=3, hidden=16),
+              F.FnoDims(n=128, c_in=5, width=32, modes=16, layers=8, hidden=128, c_out=8)):
+        dims = B.sp_fno_dims(D.n, D.c_in, D.width, D.modes, D.layers, D.hidden, D.c_out, 4, 0)
+        assert B.sp_fno_param_count(dims) == F.param_count(D)
+    assert B.sp_fno_param_count(B.sp_fno_dims(256, 3, 32, 16, 4, 128, 2, 16, 0)) == \
+        sm.fno_initial_params().size
+    for bad in ((100, 3, 32, 16, 4, 128, 2, 1, 0),    # n not a multiple of 64
+                (64, 3, 33, 16, 4, 128, 2, 1, 0),     # width above 32
+                (64, 3, 32, 17, 4, 128, 2, 1, 0),     # more than 16 modes
+                (64, 3, 32, 16, 4, 129, 2, 1, 0),     # hidden above 128
+                (64, 3, 32, 16, 4, 128, 2, 0, 0),     # batch_max 0
+                (64, 3, 32, 16, 4, 128, 2, 1, 2)):    # act_fp32 not 0/1
+        assert B.sp_fno_param_count(B.sp_fno_dims(*bad)) == 0
 
 
 def test_medium_schrodinger_at_fixed_shift():
