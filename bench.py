@@ -246,7 +246,9 @@ def measure_3d(args, B, torch, flush, peaks, dist, world):
     qd = torch.from_numpy(q).cuda()
     fd = torch.from_numpy(np.ascontiguousarray(w["f"])).cuda()
     u = torch.empty(n ** d, dtype=torch.complex128, device="cuda")
-    tf32_peak = peaks.get("bf16_tflops", 1911.1) * (1.1 / 2.25)
+    # the update is timed inside a seconds-long factor + solve: the sustained BF16 figure
+    # (under the power cap) scaled by the nominal TF32/BF16 ratio is its denominator
+    tf32_peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1911.1)) * (1.1 / 2.25)
     out = {}
     for name in args.forms_3d.split(","):
         prec = {"tf32": B.SP_PREC_TF32, "tf32x3": B.SP_PREC_TF32X3}[name]
@@ -285,7 +287,9 @@ def measure_3d(args, B, torch, flush, peaks, dist, world):
             "roofline": {"kernel": "lu_tc (tcgen05 TF32 Schur update)", "bound": "tensor",
                          "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s",
                          "frac": ach / tf32_peak, "traffic": None,
-                         "peak_source": "measured bf16_tflops x nominal TF32/BF16 ratio 1.1/2.25"},
+                         "peak_source": "measured bf16_tflops_sustained x nominal TF32/BF16 ratio "
+                                        "1.1/2.25 (timed inside a long step)",
+                         "frac_of_burst": ach / (peaks.get("bf16_tflops", 1911.1) * (1.1 / 2.25))},
             "kernel_breakdown_ms_per_step": {
                 k: {"ms": round(v[0], 2), "launches": v[1],
                     "achieved": round(v[2] / (v[0] / 1e3) / (1e12 if k.startswith("lu_") else 1e9), 2)
