@@ -438,7 +438,8 @@ def measure_learned(args, B, torch, dist, world):
     complex scale c = rms|g| e^{i phi}, phi = arg(sum g^2) / 2 (the solution is complex-linear
     in the source, so c removes the source's size and phase).
     Training: Adam on batches of 16 with a cosine learning-rate decay, every kernel in
-    the library.  Held-out: `learned_eval` problems (potential seed 7000 + i, source seed
+    the library (the triples sit in seeded random slots, so a batch is a contiguous slice
+    and an epoch visits the slices in a new random order).  Held-out: `learned_eval` problems (potential seed 7000 + i, source seed
     8000 + i), each factored once and solved twice, from zero (sp_solve) and from the
     network's guess (features + forward + guess + sp_solve_x0), both timed with CUDA
     events; the solve stops at the same true residual 1e-8 in both arms."""
@@ -456,6 +457,9 @@ def measure_learned(args, B, torch, dist, world):
     T = torch.empty((ntr, 2, N), dtype=torch.float32, device="cuda")
     sig = torch.empty(ntr, dtype=torch.complex128, device="cuda")
     g = torch.empty(N, dtype=torch.complex128, device="cuda")
+    # samples go to seeded random slots, so contiguous slices of X / T are shuffled
+    # batches: every epoch visits the batches in a new order with no gather kernel
+    slot = np.random.default_rng(9001).permutation(nm * nrhs)
     t0 = time.perf_counter()
     gen_iters = []
     for m in range(nm):
@@ -468,7 +472,7 @@ def measure_learned(args, B, torch, dist, world):
         infos = S.solve_many(F.view(-1), U.view(-1))
         gen_iters += [i["iters"] for i in infos]
         for r in range(nrhs):
-            k = m * nrhs + r
+            k = int(slot[m * nrhs + r])
             S.green(F[r], g)
             net.features(q, qs, g, X[k], sig[k:k + 1])
             net.target(U[r], sig[k:k + 1], T[k])
@@ -479,21 +483,19 @@ def measure_learned(args, B, torch, dist, world):
     nsteps = epochs * (ntr // bs)
     lr0 = args.learned_lr
     rng = np.random.default_rng(9000)
-    xb = torch.empty((bs, 3, N), dtype=torch.float32, device="cuda")
-    tb = torch.empty((bs, 2, N), dtype=torch.float32, device="cuda")
+    nb = ntr // bs
     losses = []
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
     step = 0
     for ep in range(epochs):
-        perm = torch.from_numpy(rng.permutation(ntr)).cuda()
-        for j in range(ntr // bs):
-            idx = perm[j * bs:(j + 1) * bs]
-            torch.index_select(X, 0, idx, out=xb)
-            torch.index_select(T, 0, idx, out=tb)
+        order = rng.permutation(nb)
+        for j in range(nb):
+            bi = int(order[j])
             lr = 0.5 * lr0 * (1 + np.cos(np.pi * step / nsteps))
-            last = j == ntr // bs - 1
-            L = net.train_step(xb, tb, bs, lr, sync=last)
+            last = j == nb - 1
+            L = net.train_step(X[bi * bs:(bi + 1) * bs], T[bi * bs:(bi + 1) * bs], bs, lr,
+                               sync=last)
             if last:
                 losses.append(L)
             step += 1
