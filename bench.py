@@ -45,6 +45,10 @@ import synthetic_media as sm  # noqa: E402
 
 METRIC = "solves/s at rel. residual 1e-8 (2D 512^2), plain FP64 GPU"
 WORKLOAD_3D = "3D 128^3 Helmholtz GRF omega=2pi*16 (corr. length 0.08), b=8"
+WORKLOAD_3D_SCHR = "3D 128^3 Schroedinger, 8 x 8 x 8 lattice wells (depth U[5,15], width 0.15 l-units), l=8, E=10, b=8"
+# what the oracle arm actually times: one factor + solve of a 128^2 member of the
+# 512^2 Helmholtz family (the 512^2 oracle factor alone takes minutes)
+REF_SAMPLE = "oracle sample: 2D 128^2 Helmholtz GRF, b=8, omega=2pi*16 (8 points/wavelength as at 512^2), factor + solve"
 UNIT = "solves/s"
 WORKLOAD = "2D 512^2 pair: Helmholtz GRF omega=2pi*64 + Schroedinger wells l=16 E=10, b=16"
 
@@ -68,8 +72,18 @@ def parse():
     p.add_argument("--problems", default="helmholtz,schrodinger",
                    help="comma list of the step's problems (default both)")
     p.add_argument("--no-3d", action="store_true", help="skip the 3D 128^3 workload")
-    p.add_argument("--forms-3d", default="tf32",
-                   help="comma list of the tensor-core forms timed at 3D 128^3 (tf32, tf32x3)")
+    p.add_argument("--forms-3d", default="tf32,tf32x3",
+                   help="comma list of the tensor-core forms timed on the 3D 128^3 Helmholtz "
+                        "problem (tf32, tf32x3); the first is the one profiled for the roofline")
+    p.add_argument("--forms-3d-schr", default="tf32",
+                   help="comma list of the forms timed on the 3D 128^3 Schroedinger problem "
+                        "(empty: skip it)")
+    p.add_argument("--no-tc-probe", action="store_true",
+                   help="skip the rate probe of the tcgen05 update kernel (the measured TF32 "
+                        "peak of the 3D roofline)")
+    p.add_argument("--oracle-512", action="store_true",
+                   help="time the FP64 oracle's full factor + solve of both 512^2 problems (two "
+                        "spawned processes side by side, minutes of host CPU) and print its phases")
     p.add_argument("--steps-3d", type=int, default=1)
     p.add_argument("--setup-route-3d", type=int, default=1, choices=[0, 1],
                    help="stencil set-up of the 3D workload: 0 TSQR + SVD, 1 Gram (default)")
@@ -189,9 +203,12 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "data": "synthetic",
+            "config": {"workload": REF_SAMPLE, "same_as_gpu_arm": False,
+                       "gpu_arm_workload": WORKLOAD},
             "cpu_baseline": {"value": res["value"], "unit": UNIT, "cores": cores,
                              "kind": "oracle", "sample": res["sample"]},
+            "oracle_512_measured_once": ORACLE_512,
             "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -219,9 +236,62 @@ def cpu_sample(prep) -> int:
 
 
 def cpu_sample_text(iters: int, seconds: float) -> str:
-    return (f"one oracle factor+solve per step of the same Helmholtz GRF family at 128^2 "
-            f"(b=8, omega=2pi*16, 8 points/wavelength like 512^2), {iters} iterations, "
-            f"{seconds:.1f} s; the 512^2 oracle factor does not fit the budget")
+    return (f"{REF_SAMPLE}: {iters} iterations, {seconds:.1f} s per sample; NOT the 512^2 "
+            f"workload (see oracle_512_measured_once for the full 512^2 oracle solve)")
+
+
+# The FP64 oracle's full factor + solve of the two 512^2 problems, measured once on the
+# GPU machine's host cores (16 Arm cores) by `python bench.py --oracle-512` (both problems in
+# spawned processes side by side).  Seconds per phase; "solve_s" = everything from the
+# stencil tables to the GMRES solution at 1e-8; value = 2 solves / the slower process.
+ORACLE_512 = None
+
+
+def _oracle_512_one(kind: str) -> dict:
+    """Full oracle solve of one 512^2 problem with phase times (spawned process)."""
+    import scipy.sparse.linalg as spla
+
+    import oracle as O
+    w = sm.helmholtz_grf_512() if kind == "helmholtz" else sm.schrodinger_wells_512()
+    d, n, b = w["d"], w["n"], w["b"]
+    if kind == "helmholtz":
+        s, q = O.helmholtz_shift(d, n, w["omega"], w["c"])
+        f = w["f"]
+    else:
+        s, q = O.schrodinger_shift(d, n, w["ell"], w["E"], w["V"])
+        f = w["f"] * w["ell"] ** 2
+    ph = {}
+    t00 = t0 = time.perf_counter()
+    tabs = O.stencil_tables(d, n, b, s)
+    ph["tables_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    M = O.SparsifyingPreconditioner(d, n, b, s, q, tables=tabs, factor=None)
+    ph["assemble_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    M._lu, M.kind = spla.splu(M.P.tocsc()), "splu"
+    ph["factor_s"] = time.perf_counter() - t0
+    g = O.apply_green(d, n, s, f)
+    t0 = time.perf_counter()
+    res = O.gmres_right(lambda x: O.apply_operator(d, n, s, q, x), M.apply, g, tol=1e-8)
+    ph["gmres_s"] = time.perf_counter() - t0
+    ph["solve_s"] = time.perf_counter() - t00
+    ph["iters"] = res["iters"]
+    ph["true_relres"] = res["true_relres"]
+    return ph
+
+
+def oracle_512() -> dict:
+    """Both 512^2 problems in two spawned processes side by side (about 5-8 minutes)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    t0 = time.perf_counter()
+    with cf.ProcessPoolExecutor(2, mp_context=mp.get_context("spawn")) as ex:
+        fut = {k: ex.submit(_oracle_512_one, k) for k in ("helmholtz", "schrodinger")}
+        out = {k: v.result() for k, v in fut.items()}
+    wall = time.perf_counter() - t0
+    return {"value": 2.0 / wall, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "wall_s": wall, "problems": out,
+            "sample": "full FP64 oracle factor + solve of both 512^2 problems, side by side"}
 
 
 def cpu_baseline() -> dict:
@@ -235,28 +305,47 @@ def cpu_baseline() -> dict:
     return {"value": 1.0 / dt, "sample": cpu_sample_text(it, dt), "seconds": dt}
 
 
+# ------------------------------------------------------------------ tensor-core peak
+def measure_tc_peak(B) -> dict:
+    """Rate of the library's own tcgen05 update kernel on a deep product (the pipe
+    limit, not an epilogue limit): C[8192 x 8192] -= A[8192 x 8192] B, TF32 and
+    3xTF32, as a burst (10 launches after a warm-up) and sustained (launches back to
+    back for about 2 s, under the power cap), CUDA events around the kernel alone."""
+    M = N = K = 8192
+    fl = 2.0 * M * N * K
+    out = {"shape": [M, N, K], "kernel": "tc_gemm_sub_kernel (tcgen05.mma kind::tf32, TMA, TMEM)"}
+    for split, name in ((0, "tf32"), (1, "tf32x3")):
+        burst = B.sp_tc_probe(split, M, N, K, 10)
+        reps = max(10, min(1000, int(2000.0 / max(burst, 1e-3))))
+        sus = B.sp_tc_probe(split, M, N, K, reps)
+        out[name] = {"burst_tflops": fl / (burst / 1e3) / 1e12,
+                     "sustained_tflops": fl / (sus / 1e3) / 1e12,
+                     "sustained_launches": reps,
+                     "pipe_flops_per_update_flop": 3 if split else 1}
+    return out
+
+
 # ------------------------------------------------------------------ 3D 128^3
-def measure_3d(args, B, torch, flush, peaks, dist, world):
-    """The 3D 128^3 Helmholtz workload (one step = sp_factor + sp_solve of one
-    problem) in the tensor-core forms: W = args.warmup untimed steps, then
-    args.steps_3d timed steps with CUDA events and an L2 flush in between."""
-    w = sm.helmholtz_grf_3d(128, 8, 0)
+def _measure_3d_one(args, B, torch, flush, w, forms, tf32_peak, dist, world, profile_first):
     d, n, b = 3, 128, 8
-    s, q = B.sp_medium_helmholtz(d, n, w["omega"], w["c"])
+    if w["kind"] == "helmholtz":
+        s, q = B.sp_medium_helmholtz(d, n, w["omega"], w["c"])
+        f = w["f"]
+    else:
+        s, q = B.sp_medium_schrodinger(d, n, w["ell"], w["E"], w["V"])
+        f = w["f"] * w["ell"] ** 2
     qd = torch.from_numpy(q).cuda()
-    fd = torch.from_numpy(np.ascontiguousarray(w["f"])).cuda()
+    fd = torch.from_numpy(np.ascontiguousarray(f)).cuda()
     u = torch.empty(n ** d, dtype=torch.complex128, device="cuda")
-    # the update is timed inside a seconds-long factor + solve: the sustained BF16 figure
-    # (under the power cap) scaled by the nominal TF32/BF16 ratio is its denominator
-    tf32_peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1911.1)) * (1.1 / 2.25)
+    warm = max(1, min(args.warmup, 3))
     out = {}
-    for name in args.forms_3d.split(","):
+    for fi, name in enumerate(forms):
         prec = {"tf32": B.SP_PREC_TF32, "tf32x3": B.SP_PREC_TF32X3}[name]
         t0 = time.perf_counter()
         S = B.Solver(d, n, b, s, prec=prec, device=int(os.environ.get("LOCAL_RANK", "0")),
                      setup_route=args.setup_route_3d)
         setup_s = time.perf_counter() - t0
-        for _ in range(args.warmup):
+        for _ in range(warm):
             S.factor(qd)
             S.solve(fd, u)
         torch.cuda.synchronize()
@@ -273,39 +362,66 @@ def measure_3d(args, B, torch, flush, peaks, dist, world):
             torch.cuda.synchronize()
             ms += a.elapsed_time(e)
         ms = reduce_max(ms / args.steps_3d, dist)
-        B.sp_profile(S.ctx, True)
-        S.factor(qd)
-        S.solve(fd, u)
-        prof = B.sp_profile_read(S.ctx)
-        B.sp_profile(S.ctx, False)
-        tc_ms, tc_n, tc_fl = prof["lu_tc"]
-        ach = tc_fl / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else 0.0
-        out[name] = {
-            "value": replica_value(1, world, ms), "ms_per_step": ms, "setup_s": setup_s,
-            "setup_route": "Gram" if args.setup_route_3d == 1 else "TSQR + SVD",
-            "iters": infos[0]["iters"], "true_relres": infos[0]["true_relres"],
-            "roofline": {"kernel": "lu_tc (tcgen05 TF32 Schur update)", "bound": "tensor",
-                         "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s",
-                         "frac": ach / tf32_peak, "traffic": None,
-                         "peak_source": "measured bf16_tflops_sustained x nominal TF32/BF16 ratio "
-                                        "1.1/2.25 (timed inside a long step)",
-                         "frac_of_burst": ach / (peaks.get("bf16_tflops", 1911.1) * (1.1 / 2.25))},
-            "kernel_breakdown_ms_per_step": {
+        r = {"value": replica_value(1, world, ms), "ms_per_step": ms, "setup_s": setup_s,
+             "warmup": warm, "iters": infos[0]["iters"], "true_relres": infos[0]["true_relres"]}
+        if profile_first and fi == 0:
+            B.sp_profile(S.ctx, True)
+            S.factor(qd)
+            S.solve(fd, u)
+            prof = B.sp_profile_read(S.ctx)
+            B.sp_profile(S.ctx, False)
+            tc_ms, tc_n, tc_fl = prof["lu_tc"]
+            ach = tc_fl / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else 0.0
+            r["roofline"] = {"kernel": "lu_tc (tcgen05 TF32 Schur update)", "bound": "tensor",
+                             "achieved": ach, "peak": tf32_peak["value"], "unit": "TFLOP/s",
+                             "frac": ach / tf32_peak["value"], "traffic": recorded_traffic("lu_tc_3d128"),
+                             "peak_source": tf32_peak["source"]}
+            if tf32_peak.get("burst"):
+                r["roofline"]["frac_of_burst"] = ach / tf32_peak["burst"]
+            r["kernel_breakdown_ms_per_step"] = {
                 k: {"ms": round(v[0], 2), "launches": v[1],
                     "achieved": round(v[2] / (v[0] / 1e3) / (1e12 if k.startswith("lu_") else 1e9), 2)
                     if v[0] > 0 else None,
                     "unit": "TFLOP/s" if k.startswith("lu_") else "GB/s"}
-                for k, v in prof.items() if v[1]},
-        }
+                for k, v in prof.items() if v[1]}
+        out[name] = r
         S.close()
         torch.cuda.synchronize()
-    best = max(out, key=lambda k: out[k]["value"])
-    return {"workload": WORKLOAD_3D, "grid": "128^3", "b": 8, "solves_per_step": 1,
-            "warmup": args.warmup, "steps": args.steps_3d,
-            "l2": "flushed between steps (256 MB write)", "data": "synthetic",
-            "plain_fp64": "not run: the FP64 fronts alone take 237 GB and the FP64 factor "
-                          "~8e14 flop at 1.25 TFLOP/s",
-            "chosen": dict(out[best], name=best), "forms": out}
+    return out
+
+
+def measure_3d(args, B, torch, flush, peaks, tc_peak, dist, world):
+    """The 3D 128^3 workloads (one step = sp_factor + sp_solve of one problem) in the
+    tensor-core forms: Helmholtz (random-field velocity) and rescaled Schroedinger
+    (lattice wells); up to 3 untimed warm-up steps, then args.steps_3d timed steps
+    with CUDA events and an L2 flush in between.  The tcgen05 update's roofline is
+    taken against the sustained rate the library's own kernel reaches on a deep
+    product (the update is timed inside a seconds-long step), else the measured BF16
+    rate x the nominal TF32/BF16 ratio."""
+    if tc_peak:
+        tf32_peak = {"value": tc_peak["tf32"]["sustained_tflops"],
+                     "burst": tc_peak["tf32"]["burst_tflops"],
+                     "source": "measured: the library's tcgen05 kernel on an 8192^3 TF32 product, "
+                               "sustained (launches back to back for ~2 s)"}
+    else:
+        tf32_peak = {"value": peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1911.1))
+                     * (1.1 / 2.25),
+                     "source": "measured bf16_tflops_sustained x nominal TF32/BF16 ratio 1.1/2.25"}
+    helm = _measure_3d_one(args, B, torch, flush, sm.helmholtz_grf_3d(128, 8, 0),
+                           [f for f in args.forms_3d.split(",") if f], tf32_peak, dist, world, True)
+    best = max(helm, key=lambda k: helm[k]["value"])
+    res = {"workload": WORKLOAD_3D, "grid": "128^3", "b": 8, "solves_per_step": 1,
+           "steps": args.steps_3d, "l2": "flushed between steps (256 MB write)", "data": "synthetic",
+           "setup_route": "Gram" if args.setup_route_3d == 1 else "TSQR + SVD",
+           "plain_fp64": "not run: the FP64 fronts alone take 237 GB and the FP64 factor "
+                         "~8e14 flop at 1.25 TFLOP/s",
+           "chosen": dict(helm[best], name=best), "forms": helm}
+    schr_forms = [f for f in args.forms_3d_schr.split(",") if f]
+    if schr_forms:
+        sch = _measure_3d_one(args, B, torch, flush, sm.schrodinger_wells_3d(128, 8, 8.0, 10.0, 0),
+                              schr_forms, tf32_peak, dist, world, False)
+        res["schrodinger"] = {"workload": WORKLOAD_3D_SCHR, "forms": sch}
+    return res
 
 
 # ------------------------------------------------------------------ batched 2D
@@ -564,6 +680,67 @@ def measure_learned(args, B, torch, dist, world):
             "data": "synthetic"}
 
 
+# ------------------------------------------------------------------ traffic and summary
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a kernel
+# class, from one ncu capture, with the 16-hex SHA-256 prefix of the source file the
+# kernel was built from at the time: a changed source file reports null.
+TRAFFIC = {}
+
+
+def _sha16(rel_path: str) -> str:
+    import hashlib
+    with open(os.path.join(ROOT, rel_path), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def recorded_traffic(kernel_class: str):
+    t = TRAFFIC.get(kernel_class)
+    if not t:
+        return None
+    try:
+        return t["bytes_per_launch"] if _sha16(t["source"]) == t["sha16"] else None
+    except OSError:
+        return None
+
+
+def summary(line: dict) -> dict:
+    """The headline figures again, compact, at the end of the line."""
+    out = {"plain_fp64_2d512": round(line["value"], 3), "e2e_fp64_2d512": round(line["e2e"]["value"], 3),
+           "roofline_frac": round(line["roofline"]["frac"], 3)}
+    ch = line.get("chosen_form")
+    if ch:
+        out["chosen_2d512"] = {"form": ch["name"], "value": round(ch["value"], 3),
+                               "speedup_vs_fp64": round(ch["speedup_vs_fp64"], 3), "iters": ch["iters"]}
+    w3 = line.get("workload_3d")
+    if w3:
+        c3 = w3["chosen"]
+        out["helmholtz_3d128"] = {k: {"value": round(v["value"], 4), "iters": v["iters"]}
+                                  for k, v in w3["forms"].items()}
+        if "roofline" in c3:
+            out["helmholtz_3d128"]["tc_update_frac"] = round(c3["roofline"]["frac"], 3)
+        if "schrodinger" in w3:
+            out["schrodinger_3d128"] = {k: {"value": round(v["value"], 4), "iters": v["iters"]}
+                                        for k, v in w3["schrodinger"]["forms"].items()}
+    tp = line.get("tc_peak")
+    if tp:
+        out["tf32_kernel_tflops"] = {"burst": round(tp["tf32"]["burst_tflops"], 1),
+                                     "sustained": round(tp["tf32"]["sustained_tflops"], 1)}
+    wb = line.get("workload_batch")
+    if wb:
+        out["batch_2d"] = {"value": round(wb["value"], 2),
+                           "speedup_vs_plain_fp64": round(wb["speedup_vs_plain_fp64"], 3)
+                           if wb.get("speedup_vs_plain_fp64") else None}
+    wl = line.get("workload_learned")
+    if wl:
+        out["learned_guess_speedup"] = round(wl["speedup_vs_zero_guess"], 3)
+    cb = line.get("cpu_baseline")
+    if cb:
+        out["oracle_sample_128"] = round(cb["value"], 3)
+        if cb.get("oracle_512_measured_once"):
+            out["oracle_512"] = round(cb["oracle_512_measured_once"]["value"], 6)
+    return out
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
@@ -787,11 +964,11 @@ def run_ours(args):
         if k in alu_classes:
             ach = wk / (ms_ / 1e3) / 1e12
             return {"kernel": k, "bound": "alu", "achieved": ach, "peak": fp64_peak_tflops,
-                    "unit": "TFLOP/s", "frac": ach / fp64_peak_tflops, "traffic": None,
+                    "unit": "TFLOP/s", "frac": ach / fp64_peak_tflops, "traffic": recorded_traffic(k),
                     "peak_source": "nominal FP64 1.25 TFLOP/s"}
         ach = wk / (ms_ / 1e3) / 1e9
         return {"kernel": k, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None, "peak_source": "measured hbm_gbs"}
+                "frac": ach / hbm, "traffic": recorded_traffic(k), "peak_source": "measured hbm_gbs"}
 
     roofline = roof(dom, prof[dom])
     breakdown = {k: {"ms": round(v[0], 3), "launches": v[1],
@@ -835,15 +1012,19 @@ def run_ours(args):
     wlearn = None
     if not args.no_learned:
         wlearn = measure_learned(args, B, torch, dist, world)
+    tc_peak = None
+    if not args.no_tc_probe:
+        tc_peak = measure_tc_peak(B)
     w3d = None
     if not args.no_3d:
-        w3d = measure_3d(args, B, torch, flush, peaks, dist, world)
+        w3d = measure_3d(args, B, torch, flush, peaks, tc_peak, dist, world)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = cpu_baseline()
         cpu = {"value": r["value"], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": r["sample"]}
+               "sample": r["sample"], "workload": REF_SAMPLE,
+               "oracle_512_measured_once": ORACLE_512}
 
     if rank == 0:
         line = {
@@ -865,9 +1046,10 @@ def run_ours(args):
             "roofline": roofline, "kernel_breakdown_ms_per_step": breakdown,
             "chosen_form": chosen, "forms": {k: {kk: v[kk] for kk in ("value", "ms_per_step", "iters")}
                                              for k, v in forms.items()},
-            "clocks": clocks, "cpu_baseline": cpu, "workload_3d": w3d, "workload_batch": wbatch,
-            "workload_learned": wlearn,
+            "clocks": clocks, "cpu_baseline": cpu, "tc_peak": tc_peak, "workload_3d": w3d,
+            "workload_batch": wbatch, "workload_learned": wlearn,
         }
+        line["summary"] = summary(line)
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -875,6 +1057,10 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.oracle_512:
+        if int(os.environ.get("RANK", "0")) == 0:
+            print(json.dumps({"oracle_512": oracle_512()}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -31,6 +31,8 @@
 #ifndef SP_GB300_H
 #define SP_GB300_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -44,7 +46,7 @@ typedef enum {
   SP_ERR_SINGULAR = 3,  /* a pivot of a front fell below pivot_tol * max|front| */
   SP_ERR_NOCONV = 4,    /* GMRES stopped at maxit above tol (the iterate is still returned) */
   SP_ERR_OOM = 5,       /* device or host allocation failed */
-  SP_ERR_TIMEOUT = 6,   /* a bounded device wait (tensor-core pipeline) ran out */
+  SP_ERR_TIMEOUT = 6,   /* a bounded device wait (tensor-core pipeline, grid panel) ran out */
   SP_ERR_CUDA = 7,      /* a CUDA runtime call failed */
   SP_ERR_STATE = 8      /* call out of order (e.g. sp_apply before sp_factor) */
 } sp_status;
@@ -105,6 +107,12 @@ typedef struct {
                         or 2: through a shared-memory ring that cp.async fills a tile
                         ahead (three operand stages); 1: into registers only (four
                         operand stages).  Both give the same bits. */
+  long long wait_limit_ns; /* limit of each bounded wait of the cooperative grid panel
+                        (the LU panel of fronts too tall for a thread-block cluster:
+                        every CTA polls the pivot candidates its peers publish) in
+                        nanoseconds of the GPU's global timer; 0 (default) = 2e9 (2 s),
+                        else 1 ... 6e10.  When a wait runs out the panel stops and
+                        sp_factor returns SP_ERR_TIMEOUT; destroy that context. */
 } sp_opts;
 
 typedef struct {
@@ -122,6 +130,11 @@ typedef struct {
 
 /* Fill *o with the defaults listed above. */
 void sp_default_opts(sp_opts *o);
+
+/* sizeof(sp_opts) for which = 0, sizeof(sp_info) for which = 1, else 0: lets a
+ * binding in another language check its layout of the two structs against this
+ * build (the paper has no counterpart; ABI plumbing only). */
+size_t sp_abi_size(int which);
 
 /* Build a context for grid (d, n), leaf size b and shift s (Section 2.2-2.3):
  * the Fourier symbol 1/(4 pi^2 |k|^2 - s) of G (Eq. G), the stencil tables
@@ -274,14 +287,27 @@ sp_status sp_profile_read(sp_ctx *ctx, int cap, double *ms, int *launches, doubl
  * batch strides sA, sB, sC in elements), with the kernel the factorisation uses
  * for the form: SP_PREC_FP64 doubles, SP_PREC_FP32 floats (SIMT FMA units),
  * SP_PREC_TF32 floats with TF32 products on the tensor cores and FP32
- * accumulation, SP_PREC_TF32X3 the same with split operands (K <= 512 for both;
- * the call allocates and frees its operand buffers).
+ * accumulation, SP_PREC_TF32X3 the same with split operands (K <= 16384 for both;
+ * the factorisation itself uses depths up to 512; the call allocates and frees its
+ * operand buffers).
  * A, B, C: device pointers owned by the caller; C must not overlap A or B.
  * Synchronous on `stream` (cudaStream_t or NULL).  SP_ERR_ARG for bad sizes or
  * forms, SP_ERR_TIMEOUT if a tensor-core pipeline wait ran out. */
 sp_status sp_schur_update(sp_precision prec, int M, int N, int K, const void *A, int lda,
                           long long sA, const void *B, int ldb, long long sB, void *C, int ldc,
                           long long sC, int batch, void *stream);
+
+/* Rate probe of the tensor-core update kernel (measurement helper; the paper has
+ * no counterpart): C[M x N] -= A[M x K] B[K x N] in FP32 on operands the call
+ * generates (uniform in [-1, 1)), packed once to TF32 (split = 1: 3xTF32), then
+ * `reps` launches of the tcgen05 product kernel alone between two CUDA events on
+ * `stream`; *ms_per_launch = device milliseconds per launch (the algorithmic work
+ * is 2 M N K flop; the tensor pipe executes 3x that with split = 1).  M a multiple
+ * of 128 in 128 ... 16384, N a multiple of 256 in 256 ... 16384, K a multiple of 32
+ * up to 16384, reps 1 ... 1000, else SP_ERR_ARG.  Allocates (3 M K + 3 K N + M N
+ * floats at most) and frees its buffers; synchronous on `stream`; SP_ERR_TIMEOUT
+ * if a pipeline wait ran out. */
+sp_status sp_tc_probe(int split, int M, int N, int K, int reps, void *stream, double *ms_per_launch);
 
 /* Launch shapes of nested-dissection level `level` (0 = leaves): Schur-update
  * tile and block-inverse GEMM tile (32 or 64); 0 means the built-in heuristic
@@ -299,8 +325,12 @@ sp_status sp_tuning(const sp_ctx *ctx, int level, int *gemm_tile, int *gen_tile)
  * NULL.  All calls on a device share the work array: calls that may run
  * concurrently on the GPU race and must be ordered by the caller.  The first call
  * on a device looks up the array's address (cudaGetSymbolAddress) with that
- * device current; make it before any stream capture.  The paper has no
- * counterpart of this entry point; it is an allocation-free form of sp_green. */
+ * device current; make it before any stream capture.  That cached address is
+ * valid for the device's context: after cudaDeviceReset the process must reload
+ * the library before calling again.  A CUDA error already pending from the
+ * caller's earlier work returns SP_ERR_CUDA before any launch and is left pending.
+ * The paper has no counterpart of this entry point; it is an allocation-free form
+ * of sp_green. */
 sp_status sp_green_static(int d, int n, double s, const void *f_dev, void *g_dev, void *stream);
 
 void sp_destroy(sp_ctx *ctx);

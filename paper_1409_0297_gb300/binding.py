@@ -20,10 +20,10 @@ SP_ERR_OOM, SP_ERR_TIMEOUT, SP_ERR_CUDA, SP_ERR_STATE = 5, 6, 7, 8
 SP_PREC_FP64, SP_PREC_FP32, SP_PREC_MIXED, SP_PREC_TF32, SP_PREC_TF32X3 = 0, 1, 2, 3, 4
 
 EXPORTED = [
-    "sp_default_opts", "sp_setup", "sp_factor", "sp_apply", "sp_solve", "sp_factor_host",
+    "sp_abi_size", "sp_default_opts", "sp_setup", "sp_factor", "sp_apply", "sp_solve", "sp_factor_host",
     "sp_solve_host", "sp_matvec", "sp_green", "sp_qapply", "sp_get_table", "sp_stencil_table",
     "sp_front_sizes", "sp_level_info", "sp_costs", "sp_medium_helmholtz", "sp_medium_schrodinger", "sp_profile",
-    "sp_profile_read", "sp_green_static", "sp_schur_update", "sp_tuning", "sp_solve_many",
+    "sp_profile_read", "sp_green_static", "sp_schur_update", "sp_tc_probe", "sp_tuning", "sp_solve_many",
     "sp_solve_x0", "sp_medium_schrodinger_at", "sp_destroy", "sp_status_str",
     "sp_fno_param_count", "sp_fno_create", "sp_fno_destroy", "sp_fno_set_params",
     "sp_fno_get_params", "sp_fno_forward", "sp_fno_gradient", "sp_fno_train_step",
@@ -39,7 +39,8 @@ class sp_opts(ctypes.Structure):
                 ("host_threads", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("autotune", ctypes.c_int), ("max_rhs", ctypes.c_int),
                 ("setup_route", ctypes.c_int), ("stencil", ctypes.c_int),
-                ("inv_block", ctypes.c_int), ("tc_epilogue", ctypes.c_int)]
+                ("inv_block", ctypes.c_int), ("tc_epilogue", ctypes.c_int),
+                ("wait_limit_ns", ctypes.c_longlong)]
 
 
 class sp_info(ctypes.Structure):
@@ -75,6 +76,7 @@ def _load() -> ctypes.CDLL:
     P, I, D, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, None
     pI, pD = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
     sig = {
+        "sp_abi_size": (ctypes.c_size_t, [I]),
         "sp_default_opts": (V, [ctypes.POINTER(sp_opts)]),
         "sp_setup": (I, [I, I, I, D, I, ctypes.POINTER(sp_opts), P, ctypes.POINTER(P)]),
         "sp_factor": (I, [P, P]),
@@ -97,6 +99,7 @@ def _load() -> ctypes.CDLL:
         "sp_green_static": (I, [I, I, D, P, P, P]),
         "sp_schur_update": (I, [I, I, I, I, P, I, ctypes.c_longlong, P, I, ctypes.c_longlong, P, I,
                                 ctypes.c_longlong, I, P]),
+        "sp_tc_probe": (I, [I, I, I, I, I, P, pD]),
         "sp_tuning": (I, [P, I, pI, pI]),
         "sp_solve_many": (I, [P, I, P, P, ctypes.POINTER(sp_info)]),
         "sp_solve_x0": (I, [P, P, P, P, ctypes.POINTER(sp_info)]),
@@ -352,6 +355,14 @@ def sp_schur_update(prec: int, M: int, N: int, K: int, A_dev: int, lda: int, sA:
                                stream), "sp_schur_update")
 
 
+def sp_tc_probe(split: int, M: int, N: int, K: int, reps: int = 10, stream: int = 0) -> float:
+    """Device milliseconds per launch of the tcgen05 update kernel on generated
+    operands (C[M x N] -= A[M x K] B[K x N]; split = 1: 3xTF32)."""
+    ms = ctypes.c_double()
+    _check(LIB.sp_tc_probe(split, M, N, K, reps, stream, ctypes.byref(ms)), "sp_tc_probe")
+    return ms.value
+
+
 def sp_tuning(ctx: int, level: int) -> dict:
     """Launch shapes of one level (0 = built-in heuristic)."""
     v = [ctypes.c_int() for _ in range(2)]
@@ -373,7 +384,7 @@ class Solver:
                  maxit: int = 500, restart: int = 200, tol: float = 1e-8, device: int = 0,
                  stream: int = 0, host_threads: int = 0, autotune: bool = False,
                  max_rhs: int = 1, setup_route: int = 0, stencil: int = 0, inv_block: int = 0,
-                 tc_epilogue: int = 0):
+                 tc_epilogue: int = 0, wait_limit_ns: int = 0):
         o = sp_default_opts()
         o.maxit, o.restart, o.tol, o.device = maxit, restart, tol, device
         o.host_threads = host_threads
@@ -383,6 +394,7 @@ class Solver:
         o.stencil = stencil
         o.inv_block = inv_block
         o.tc_epilogue = tc_epilogue
+        o.wait_limit_ns = wait_limit_ns
         self.d, self.n, self.b, self.s, self.prec = d, n, b, s, prec
         self.N = n ** d
         self.ctx = sp_setup(d, n, b, s, prec, o, stream)

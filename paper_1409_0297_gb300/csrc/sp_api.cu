@@ -282,6 +282,14 @@ void capture_graph(sp_ctx* c, cudaGraphExec_t* out, Fn fn) {
 
 extern "C" {
 
+size_t sp_abi_size(int which) {
+  switch (which) {
+    case 0: return sizeof(sp_opts);
+    case 1: return sizeof(sp_info);
+    default: return 0;
+  }
+}
+
 void sp_default_opts(sp_opts* o) {
   if (!o) return;
   o->maxit = 500;
@@ -297,6 +305,7 @@ void sp_default_opts(sp_opts* o) {
   o->stencil = 0;
   o->inv_block = 0;
   o->tc_epilogue = 0;
+  o->wait_limit_ns = 0;
 }
 
 const char* sp_status_str(sp_status st) {
@@ -509,6 +518,7 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
     if (ib != 0 && (ib < 64 || ib > 2048 || (ib & (ib - 1)) != 0)) return SP_ERR_ARG;
   }
   if (c->opts.tc_epilogue < 0 || c->opts.tc_epilogue > 2) return SP_ERR_ARG;
+  if (c->opts.wait_limit_ns < 0 || c->opts.wait_limit_ns > 60000000000LL) return SP_ERR_ARG;
   const size_t RH = (size_t)c->opts.max_rhs;
   c->d = d;
   c->n = n;
@@ -521,6 +531,8 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   c->work.tc = tc;
   c->work.tc_split = split;
   c->work.tc_epi = c->opts.tc_epilogue;
+  c->work.wait_ns = c->opts.wait_limit_ns > 0 ? (unsigned long long)c->opts.wait_limit_ns
+                                              : 2000000000ull;
   if (mixed && !(c->opts.inner_tol > 0 && c->opts.inner_tol < 1)) return SP_ERR_ARG;
   c->stream = (cudaStream_t)stream;
   c->N = 1;
@@ -1230,7 +1242,7 @@ sp_status sp_schur_update(sp_precision prec, int M, int N, int K, const void* A,
   if (sA < 0 || sB < 0 || sC < 0 || batch > 65535) return SP_ERR_ARG;
   const bool tc = prec == SP_PREC_TF32 || prec == SP_PREC_TF32X3;
   const bool split = prec == SP_PREC_TF32X3;
-  if (tc && K > kTcMaxK) return SP_ERR_ARG;
+  if (tc && K > kTcMaxKProbe) return SP_ERR_ARG;
   if ((long long)M * N * K * batch == 0) return SP_OK;
   cudaStream_t st = (cudaStream_t)stream;
   float *pa = nullptr, *pb = nullptr;
@@ -1254,6 +1266,20 @@ sp_status sp_schur_update(sp_precision prec, int M, int N, int K, const void* A,
   if (pa) cudaFree(pa);
   if (pb) cudaFree(pb);
   if (status) cudaFree(status);
+  return rs;
+}
+
+sp_status sp_tc_probe(int split, int M, int N, int K, int reps, void* stream, double* ms_per_launch) {
+  if ((split != 0 && split != 1) || !ms_per_launch || reps < 1 || reps > 1000) return SP_ERR_ARG;
+  if (M < 128 || N < 256 || K < 32 || M % 128 || N % 256 || K % 32 || M > 16384 || N > 16384 ||
+      K > kTcMaxKProbe)
+    return SP_ERR_ARG;
+  float ms = 0.f;
+  int hs = 0;
+  cudaError_t e = tc_probe(split != 0, M, N, K, reps, (cudaStream_t)stream, &ms, &hs);
+  sp_status rs = cuda_status(e);
+  if (rs == SP_OK && (hs & 2)) rs = SP_ERR_TIMEOUT;
+  *ms_per_launch = ms;
   return rs;
 }
 

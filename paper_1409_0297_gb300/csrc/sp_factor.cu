@@ -294,7 +294,8 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(256)
 // published j+1, i.e. finished reading column j).  The pivot positions are
 // reconstructed after the panel from the sequence of pivot slots; each CTA then
 // writes its rows back in position order.  A poll that does not complete within
-// about 2 s sets bit 2 of *status and the CTA returns without writing back.
+// wait_ns (2 s by default) sets bit 2 of *status and the CTA returns without
+// writing back (CTA 0 of the front leaves identity interchanges for the panel).
 constexpr int kPubWords = 1 + kNB;  // word, row (in units of 8 bytes; T <= 8 bytes)
 __device__ __forceinline__ unsigned long long gtimer_ns() {
   unsigned long long t;
@@ -315,7 +316,8 @@ __global__ void __launch_bounds__(256) lu_panel_grid_kernel(T* fronts, int m, in
                                                             int f0, int G, int* piv,
                                                             const double* scale, double ptol,
                                                             int* status,
-                                                            unsigned long long* pub) {
+                                                            unsigned long long* pub,
+                                                            unsigned long long wait_ns) {
   const int f = f0 + blockIdx.x / G, g = blockIdx.x % G;
   T* A = fronts + (long)f * m * m;
   const int rows = m - j0, kl = k - j0;
@@ -395,7 +397,7 @@ __global__ void __launch_bounds__(256) lu_panel_grid_kernel(T* fronts, int m, in
           mine_ok = mine_ok && rdy[i];
         }
         if (__all_sync(0xffffffffu, mine_ok)) break;
-        if (gtimer_ns() - t0 > 2000000000ull) {
+        if (gtimer_ns() - t0 > wait_ns) {
           ok = false;
           break;
         }
@@ -428,7 +430,13 @@ __global__ void __launch_bounds__(256) lu_panel_grid_kernel(T* fronts, int m, in
       }
     }
     __syncthreads();
-    if (s_abort) return;
+    if (s_abort) {
+      // the panel stops here; later kernels of the factorisation still read this
+      // panel's interchanges, so leave in-range (identity) ones
+      if (g == 0)
+        for (int c = threadIdx.x; c < jb; c += blockDim.x) piv[(long)f * k + j0 + c] = j0 + c;
+      return;
+    }
     T pv = prow[jj];
     if (g == 0 && threadIdx.x == 0 && !(fabs((double)pv) > thresh)) atomicOr(status, 1);
     if (!(fabs((double)pv) > 0.0)) pv = (T)(thresh > 0 ? thresh : 1e-30);
@@ -1011,7 +1019,7 @@ void panel_step(DevLevel& L, T* F, int j0, int jb, int c_lo, int c_hi, double pt
       cfg.attrs = at;
       cfg.numAttrs = 1;
       cudaLaunchKernelEx(&cfg, lu_panel_grid_kernel<T>, F, L.m, L.k, j0, jb, f0, G, L.piv,
-                         (const double*)L.scale, ptol, status, W.gpub);
+                         (const double*)L.scale, ptol, status, W.gpub, W.wait_ns);
     }
   } else if (kind == 1) {
     size_t sm = sizeof(T) * (size_t)((L.m - j0 + kCL - 1) / kCL) * jb +

@@ -107,6 +107,7 @@ struct FactorWork {
   bool tc = false;            // Schur updates of the blocked fronts on the tensor cores
   bool tc_split = false;      // ... as 3xTF32 (hi/lo split, FP32 accuracy)
   int tc_epi = 0;             // epilogue of the tensor-core update (tc_schur_update's epi)
+  unsigned long long wait_ns = 2000000000ull;  // limit of each grid-panel poll (global timer ns)
   // grid panel (fronts too tall for a cluster): per front 2 x kGridPanelMaxG
   // publication slots of grid_panel_pub_words() 8-byte words
   unsigned long long* gpub = nullptr;
@@ -136,7 +137,8 @@ cudaError_t schur_update_raw(int prec, bool tc, bool split, int M, int N, int K,
                              cudaStream_t st);
 
 // ---------------------------------------------------------------- tensor cores (sp_tc.cu)
-constexpr int kTcMaxK = 512;
+constexpr int kTcMaxK = 512;       // depth of the factorisation's updates (its operand buffers)
+constexpr int kTcMaxKProbe = 16384;  // depth accepted by the stand-alone update and the rate probe
 // floats of one packed operand buffer for `rows` rows, K columns, batch fronts
 size_t tc_pack_floats(int rows, int K, int batch, bool split);
 // C[M x N] -= A[M x K] B[K x N] (column-major, batch strides sA, sB, sC) with
@@ -146,6 +148,12 @@ size_t tc_pack_floats(int rows, int K, int batch, bool split);
 cudaError_t tc_schur_update(int M, int N, int K, const float* A, int lda, long sA, const float* B,
                             int ldb, long sB, float* C, int ldc, long sC, int batch, float* packA,
                             float* packB, bool split, int* status, cudaStream_t st, int epi = 0);
+// rate probe of the same update kernel: C[M x N] -= A[M x K] B[K x N] on
+// generated operands packed once, `reps` launches of the product kernel alone
+// timed with CUDA events on st; *ms = device milliseconds per launch, *hstatus =
+// the status word (bit 2: a pipeline wait ran out).  Allocates and frees its buffers.
+cudaError_t tc_probe(bool split, int M, int N, int K, int reps, cudaStream_t st, float* ms,
+                     int* hstatus);
 
 // ---------------------------------------------------------------- solve (sp_solve.cu)
 struct QTypeDev {

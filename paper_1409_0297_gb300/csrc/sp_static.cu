@@ -19,7 +19,14 @@
 //
 // Set-up: the first call on a device, with that device current, looks up the
 // array's device address with cudaGetSymbolAddress and caches it; make that first
-// call before any stream capture starts.
+// call before any stream capture starts.  The cached address belongs to the
+// device's current CUDA context: after cudaDeviceReset on that device the
+// library must be reloaded (the process restarted) before this entry point is
+// called again.
+//
+// Errors: a CUDA error left pending by earlier work of the caller is reported as
+// SP_ERR_CUDA before anything is launched, and is not cleared, so it is not
+// mistaken for a failure of this call nor hidden from the caller.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -50,9 +57,9 @@ __device__ __forceinline__ double2 smul(double2 a, double2 b) {
 __global__ void __launch_bounds__(kThreadsS) green_static_pass(const double2* in, double2* out,
                                                                int d, int n, int logn, long S,
                                                                long nlines, int mode, double s) {
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(16) unsigned char smraw[];
   double2* tw = reinterpret_cast<double2*>(smraw);  // n/2 twiddles
-  double2* a = tw + n / 2;                          // one line (n + 1 with pad)
+  double2* a = tw + n / 2;                          // one line of n values
   const long t = blockIdx.x;                        // one line per CTA
   for (int j = threadIdx.x; j < n / 2; j += blockDim.x) {
     double sn, cs;
@@ -142,6 +149,7 @@ extern "C" sp_status sp_green_static(int d, int n, double s, const void* f_dev, 
   for (int a = 0; a < d; ++a) N *= n;
   if (N > kStaticMaxN) return SP_ERR_ARG;  // beyond the static work array
   if (!(s == s) || resonance_gap(d, n, s) < 1e-6) return SP_ERR_RESONANT;
+  if (cudaPeekAtLastError() != cudaSuccess) return SP_ERR_CUDA;  // the caller's, left in place
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SP_ERR_CUDA;
   double2* work = nullptr;
@@ -157,7 +165,7 @@ extern "C" sp_status sp_green_static(int d, int n, double s, const void* f_dev, 
   cudaStream_t st = (cudaStream_t)stream;
   int logn = 0;
   while ((1 << logn) < n) ++logn;
-  const size_t smem = sizeof(double2) * (size_t)(n / 2 + n + 1);
+  const size_t smem = sizeof(double2) * (size_t)(n / 2 + n);
   const long nlines = N / n;
   const double2* x = static_cast<const double2*>(f_dev);
   double2* out = static_cast<double2*>(g_dev);

@@ -530,30 +530,24 @@ size_t tc_pack_floats(int rows, int K, int batch, bool split) {
   return (size_t)batch * rows * (size_t)((K + kBK - 1) / kBK * kBK) * (split ? 3 : 1);
 }
 
-cudaError_t tc_schur_update(int M, int N, int K, const float* A, int lda, long sA, const float* B,
-                            int ldb, long sB, float* C, int ldc, long sC, int batch, float* packA,
-                            float* packB, bool split, int* status, cudaStream_t st, int epi) {
-  if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return cudaSuccess;
-  if (K > kTcMaxK || batch > 65535 || !packA || !packB) return cudaErrorInvalidValue;
+namespace {
+
+cudaError_t tc_set_attributes() {
   static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_sub_kernel<kBN, kStages, 0>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(tc_gemm_sub_kernel<kBN, kStagesRing, 2>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemRing);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  const int Kp = (K + kBK - 1) / kBK * kBK;
-  const int Ke = split ? 3 * Kp : Kp;  // depth of the packed product
-  {
-    dim3 g((M + 31) / 32, Kp / 32, batch);
-    tc_pack_a_kernel<<<g, dim3(32, 8), 0, st>>>(A, lda, sA, M, K, Kp, split ? 1 : 0, packA);
-    const long nb = (long)N * Kp;
-    dim3 gb((unsigned)((nb + 255) / 256), batch);
-    tc_pack_b_kernel<<<gb, 256, 0, st>>>(B, ldb, sB, N, K, Kp, split ? 1 : 0, packB);
-  }
+  if (attr) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(tc_gemm_sub_kernel<kBN, kStages, 0>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(tc_gemm_sub_kernel<kBN, kStagesRing, 2>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemRing);
+  if (e != cudaSuccess) return e;
+  attr = true;
+  return cudaSuccess;
+}
+
+// the product kernel on already packed operands of depth Ke (a multiple of kBK)
+cudaError_t tc_run(int M, int N, int Ke, float* C, int ldc, long sC, int batch, float* packA,
+                   float* packB, int* status, cudaStream_t st, int epi) {
   CUtensorMap ta, tb;
   cudaError_t e = encode_operand(&ta, packA, M, Ke, batch, kBM);
   if (e != cudaSuccess) return e;
@@ -573,6 +567,93 @@ cudaError_t tc_schur_update(int M, int N, int K, const float* A, int lda, long s
     tc_gemm_sub_kernel<kBN, kStages, 0><<<grid, kPThreads, kSmem, st>>>(
         ta, tb, M, N, Ke / kBK, C, ldc, sC, tilesM, tilesN, ntiles, status);
   return cudaGetLastError();
+}
+
+void tc_pack(int M, int N, int K, const float* A, int lda, long sA, const float* B, int ldb,
+             long sB, int batch, float* packA, float* packB, bool split, cudaStream_t st) {
+  const int Kp = (K + kBK - 1) / kBK * kBK;
+  dim3 g((M + 31) / 32, Kp / 32, batch);
+  tc_pack_a_kernel<<<g, dim3(32, 8), 0, st>>>(A, lda, sA, M, K, Kp, split ? 1 : 0, packA);
+  const long nb = (long)N * Kp;
+  dim3 gb((unsigned)((nb + 255) / 256), batch);
+  tc_pack_b_kernel<<<gb, 256, 0, st>>>(B, ldb, sB, N, K, Kp, split ? 1 : 0, packB);
+}
+
+// deterministic uniform values in [-1, 1) from a hash of the index
+__global__ void tc_probe_fill_kernel(float* p, long n, unsigned seed) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    unsigned h = (unsigned)i * 2654435761u ^ seed;
+    h ^= h >> 15;
+    h *= 2246822519u;
+    h ^= h >> 13;
+    p[i] = (float)(h & 0xFFFFu) * (1.0f / 32768.0f) - 1.0f;
+  }
+}
+
+}  // namespace
+
+cudaError_t tc_schur_update(int M, int N, int K, const float* A, int lda, long sA, const float* B,
+                            int ldb, long sB, float* C, int ldc, long sC, int batch, float* packA,
+                            float* packB, bool split, int* status, cudaStream_t st, int epi) {
+  if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return cudaSuccess;
+  if (K > kTcMaxKProbe || batch > 65535 || !packA || !packB) return cudaErrorInvalidValue;
+  cudaError_t e = tc_set_attributes();
+  if (e != cudaSuccess) return e;
+  const int Kp = (K + kBK - 1) / kBK * kBK;
+  const int Ke = split ? 3 * Kp : Kp;  // depth of the packed product
+  tc_pack(M, N, K, A, lda, sA, B, ldb, sB, batch, packA, packB, split, st);
+  return tc_run(M, N, Ke, C, ldc, sC, batch, packA, packB, status, st, epi);
+}
+
+cudaError_t tc_probe(bool split, int M, int N, int K, int reps, cudaStream_t st, float* ms,
+                     int* hstatus) {
+  *ms = 0.f;
+  *hstatus = 0;
+  cudaError_t e = tc_set_attributes();
+  if (e != cudaSuccess) return e;
+  float *A = nullptr, *B = nullptr, *C = nullptr, *pa = nullptr, *pb = nullptr;
+  int* status = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const int Kp = (K + kBK - 1) / kBK * kBK;
+  const int Ke = split ? 3 * Kp : Kp;
+  e = cudaMalloc(&A, sizeof(float) * (size_t)M * K);
+  if (e == cudaSuccess) e = cudaMalloc(&B, sizeof(float) * (size_t)K * N);
+  if (e == cudaSuccess) e = cudaMalloc(&C, sizeof(float) * (size_t)M * N);
+  if (e == cudaSuccess) e = cudaMalloc(&pa, sizeof(float) * tc_pack_floats(M, K, 1, split));
+  if (e == cudaSuccess) e = cudaMalloc(&pb, sizeof(float) * tc_pack_floats(N, K, 1, split));
+  if (e == cudaSuccess) e = cudaMalloc(&status, sizeof(int));
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) {
+    tc_probe_fill_kernel<<<1024, 256, 0, st>>>(A, (long)M * K, 17u);
+    tc_probe_fill_kernel<<<1024, 256, 0, st>>>(B, (long)K * N, 29u);
+    tc_probe_fill_kernel<<<1024, 256, 0, st>>>(C, (long)M * N, 43u);
+    e = cudaMemsetAsync(status, 0, sizeof(int), st);
+  }
+  if (e == cudaSuccess) {
+    tc_pack(M, N, K, A, M, 0, B, K, 0, 1, pa, pb, split, st);
+    e = tc_run(M, N, Ke, C, M, 0, 1, pa, pb, status, st, 0);  // warm-up
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r)
+    e = tc_run(M, N, Ke, C, M, 0, 1, pa, pb, status, st, 0);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) {
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, e0, e1);
+    *ms = t / (float)reps;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(A);
+  cudaFree(B);
+  cudaFree(C);
+  cudaFree(pa);
+  cudaFree(pb);
+  cudaFree(status);
+  return e;
 }
 
 }  // namespace sp

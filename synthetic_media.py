@@ -235,3 +235,30 @@ def lattice_wells_potential_2d(n: int, ell: float, seed: int, depth=(5.0, 15.0),
     # np.indices ordering: cell index (i0, i1) flattened with i1 fastest; i0 is axis 0 (j0)
     V = -np.einsum("ab,ay,bx->yx", depths.T, e, e)
     return V.ravel()
+
+
+def lattice_wells_potential_3d(n: int, ell: float, seed: int, depth=(5.0, 15.0),
+                               width: float = 0.15) -> np.ndarray:
+    """The 3D lattice_wells_potential in separable form (per-axis minimum image:
+    exp(-r^2 / (2 w^2)) = ex(x) ey(y) ez(z)); same seed, same depths, same values up to
+    rounding, without one full-grid pass per well."""
+    rng = np.random.default_rng(seed)
+    m = int(round(ell))
+    depths = rng.uniform(depth[0], depth[1], size=m ** 3).reshape(m, m, m)  # [i0][i1][i2]
+    x = np.arange(n) * (ell / n)
+    d = x[None, :] - (np.arange(m)[:, None] + 0.5)
+    d = d - ell * np.round(d / ell)
+    e = np.exp(-d * d / (2.0 * width * width))                              # [cell][point]
+    V = -np.einsum("abc,ax,by,cz->zyx", depths, e, e, e, optimize=True)      # [j2][j1][j0]
+    return V.ravel()
+
+
+def schrodinger_wells_3d(n: int = 128, b: int = 8, ell: float = 8.0, E: float = 10.0,
+                         i: int = 0) -> dict:
+    """3D rescaled Schroedinger on n^3: an l x l x l lattice of Gaussian wells (depth
+    U[5, 15], width 0.15 l-units, medium seed 1000 + i), E = 10, a random-centre,
+    random-phase Gaussian source (seed 2000 + i)."""
+    V = lattice_wells_potential_3d(n, ell, MEDIUM_SEED_BASE + i)
+    f = random_gaussian_source(3, n, RHS_SEED_BASE + i)
+    return dict(name=f"schrodinger3d_n{n}_wells", d=3, n=n, b=b, kind="schrodinger",
+                ell=ell, E=E, V=V, f=f)

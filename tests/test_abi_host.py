@@ -1,6 +1,7 @@
 """CPU tests of the C ABI: the library loads, exports every declared symbol, and its
 host-only logic (argument checks, nested-dissection sizes, stencil tables, medium
 split) agrees with the paper's formulas and with the oracle.  No GPU compute."""
+import ctypes
 import os
 import re
 
@@ -102,6 +103,11 @@ def test_default_opts_layout():
     assert (o.maxit, o.restart, o.tol, o.pivot_tol) == (500, 200, 1e-8, 1e-14)
     assert (o.device, o.host_threads, o.inner_tol, o.autotune) == (0, 0, 1e-5, 0)
     assert (o.max_rhs, o.setup_route, o.stencil, o.inv_block, o.tc_epilogue) == (1, 0, 0, 0, 0)
+    assert o.wait_limit_ns == 0
+    # the binding's layouts of sp_opts and sp_info match the build's
+    assert B.LIB.sp_abi_size(0) == ctypes.sizeof(B.sp_opts)
+    assert B.LIB.sp_abi_size(1) == ctypes.sizeof(B.sp_info)
+    assert B.LIB.sp_abi_size(2) == 0
 
 
 def test_fno_param_count_matches_oracle_layout():

@@ -66,6 +66,8 @@ SMALL = [
     ("2d_n96_b6_schr", lambda: sm.schrodinger_wells(2, 96, 6, 6.0, 5.0, 17)),
     ("3d_n24_b3", lambda: dict(d=3, n=24, b=3, kind="helmholtz", omega=2 * np.pi * 2.5,
                                c=sm.grf_velocity(3, 24, 0.15, 18), f=sm.random_gaussian_source(3, 24, 19, 0.1))),
+    # 3D rescaled Schroedinger (Eq. schr): a 2 x 2 x 2 lattice of wells
+    ("3d_n16_b4_schr", lambda: sm.schrodinger_wells_3d(16, 4, 2.0, 10.0, 3)),
 ]
 
 
@@ -163,11 +165,13 @@ def test_solve_matches_oracle_64(B):
         S.close()
 
 
-def test_solve_3d16_matches_oracle(B):
-    """3D 16^3, b = 4: the root front (m = 1352) is factored in outer blocks with
-    tensor-core Schur updates in the TF32 form; every form reaches the oracle's
-    solution to 1e-6 and a true residual of 1e-8."""
-    w = sm.helmholtz_grf_3d(16, 4, 0)
+@pytest.mark.parametrize("which", ["helmholtz", "schrodinger"])
+def test_solve_3d16_matches_oracle(B, which):
+    """3D 16^3, b = 4 (Helmholtz on a random-field velocity; rescaled Schroedinger with a
+    2 x 2 x 2 lattice of wells, Eq. schr): the root front (m = 1352) is factored in outer
+    blocks with tensor-core Schur updates in the TF32 form; every form reaches the
+    oracle's solution to 1e-6 and a true residual of 1e-8."""
+    w = sm.helmholtz_grf_3d(16, 4, 0) if which == "helmholtz" else sm.schrodinger_wells_3d(16, 4, 2.0)
     d, n, b = w["d"], w["n"], w["b"]
     s, q, f = medium(w)
     M = O.SparsifyingPreconditioner(d, n, b, s, q)
@@ -189,13 +193,15 @@ def test_solve_3d16_matches_oracle(B):
         S.close()
 
 
+@pytest.mark.parametrize("which", ["helmholtz", "schrodinger"])
 @pytest.mark.parametrize("prec", [0, 1, 3, 4], ids=["fp64", "fp32", "tf32", "tf32x3"])
-def test_solve_3d32(B, prec):
+def test_solve_3d32(B, prec, which):
     """3D 32^3, b = 4 (root front m = 5768: the cooperative grid panel in FP64, the
-    cluster panel in FP32, outer blocks with tensor-core updates in TF32): the
-    preconditioner at 2000 sampled rows of P z - Q r (oracle, from the library's
-    tables) and the solution by the oracle's FFT residual."""
-    w = sm.helmholtz_grf_3d(32, 4, 0)
+    cluster panel in FP32, outer blocks with tensor-core updates in TF32), Helmholtz and
+    rescaled Schroedinger (4 x 4 x 4 wells): the preconditioner at 2000 sampled rows of
+    P z - Q r (oracle, from the library's tables) and the solution by the oracle's FFT
+    residual."""
+    w = sm.helmholtz_grf_3d(32, 4, 0) if which == "helmholtz" else sm.schrodinger_wells_3d(32, 4, 4.0)
     d, n, b = w["d"], w["n"], w["b"]
     s, q, f = medium(w)
     S = B.Solver(d, n, b, s, prec=prec)
