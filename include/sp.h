@@ -218,6 +218,16 @@ sp_status sp_qapply(sp_ctx *ctx, const void *r_dev, void *y_dev);
 sp_status sp_get_table(const sp_ctx *ctx, int t, double *Q_out, double *C_out, int *rows,
                        int *cols, int *rank);
 
+/* Replace set type t's tables Q(S, gamma) and C(S, gamma) (Section 2.3) with the
+ * caller's, in sp_get_table's layout (|S| x |gamma| row-major, host memory): for
+ * example tables kept from an earlier set-up of the same (d, n, b, s, stencil), or
+ * computed by another route.  They take effect at the next sp_factor (the context
+ * is marked unfactored); the stencil apply uses T = -Q on the beta columns.  With
+ * set stencils Q(S, S) must be the identity (the form Q(S, gamma) = [I, -T_S]),
+ * else SP_ERR_ARG; non-finite entries give SP_ERR_ARG.  The rank that
+ * sp_get_table reports stays the set-up's.  Synchronises the context's stream. */
+sp_status sp_set_table(sp_ctx *ctx, int t, const double *Q_host, const double *C_host);
+
 /* Host-only (no GPU): the same tables as sp_setup computes for (d, n, b, s),
  * type t, by route 0 (TSQR + SVD) or 1 (Gram, see sp_opts.setup_route), of
  * kind 0 (set stencils) or 1 (per-point stencils, see sp_opts.stencil).  Pass

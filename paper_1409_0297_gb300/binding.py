@@ -21,7 +21,7 @@ SP_PREC_FP64, SP_PREC_FP32, SP_PREC_MIXED, SP_PREC_TF32, SP_PREC_TF32X3 = 0, 1, 
 
 EXPORTED = [
     "sp_abi_size", "sp_default_opts", "sp_setup", "sp_factor", "sp_apply", "sp_solve", "sp_factor_host",
-    "sp_solve_host", "sp_matvec", "sp_green", "sp_qapply", "sp_get_table", "sp_stencil_table",
+    "sp_solve_host", "sp_matvec", "sp_green", "sp_qapply", "sp_get_table", "sp_set_table", "sp_stencil_table",
     "sp_front_sizes", "sp_level_info", "sp_costs", "sp_medium_helmholtz", "sp_medium_schrodinger", "sp_profile",
     "sp_profile_read", "sp_green_static", "sp_schur_update", "sp_tc_probe", "sp_tuning", "sp_solve_many",
     "sp_solve_x0", "sp_medium_schrodinger_at", "sp_destroy", "sp_status_str",
@@ -88,6 +88,7 @@ def _load() -> ctypes.CDLL:
         "sp_green": (I, [P, P, P]),
         "sp_qapply": (I, [P, P, P]),
         "sp_get_table": (I, [P, I, pD, pD, pI, pI, pI]),
+        "sp_set_table": (I, [P, I, pD, pD]),
         "sp_stencil_table": (I, [I, I, I, D, I, I, I, I, pD, pD, pI, pI, pI, pD]),
         "sp_front_sizes": (I, [I, I, I, I, pI, pI, pI, pI]),
         "sp_costs": (I, [P, pD, pD, pD]),
@@ -452,6 +453,16 @@ class Solver:
 
     def table(self, t: int):
         return sp_get_table(self.ctx, t)
+
+    def set_table(self, t: int, Q, C):
+        """Replace type t's Q(S, gamma), C(S, gamma) (row-major |S| x |gamma| float64)."""
+        import numpy as np
+        Qh = np.ascontiguousarray(Q, dtype=np.float64)
+        Ch = np.ascontiguousarray(C, dtype=np.float64)
+        rows, cols = sp_get_table(self.ctx, t)[0].shape
+        if Qh.shape != (rows, cols) or Ch.shape != (rows, cols):
+            raise ValueError(f"type {t} tables are {rows} x {cols}")
+        _check(LIB.sp_set_table(self.ctx, t, _dptr(Qh), _dptr(Ch)), "sp_set_table")
 
     def costs(self):
         return sp_costs(self.ctx)

@@ -1303,6 +1303,68 @@ sp_status sp_get_table(const sp_ctx* c, int t, double* Q_out, double* C_out, int
   return SP_OK;
 }
 
+sp_status sp_set_table(sp_ctx* c, int t, const double* Q_in, const double* C_in) {
+  if (!c || t < 0 || t >= (int)c->tabs.size() || t >= (int)c->qtypes.size() || !Q_in || !C_in)
+    return SP_ERR_ARG;
+  StencilTable& tb = c->tabs[t];
+  const QTypeDev& qt = c->qtypes[t];
+  const size_t ne = (size_t)tb.nS * tb.nG;
+  for (size_t e = 0; e < ne; ++e)
+    if (!std::isfinite(Q_in[e]) || !std::isfinite(C_in[e])) return SP_ERR_ARG;
+  // columns of gamma that are not in S (gamma order lists S and beta interleaved)
+  std::vector<int> scol, bcols;
+  {
+    int sidx = 0;
+    for (int gi = 0; gi < tb.nG; ++gi) {
+      bool inS = sidx < tb.nS;
+      for (int a = 0; a < c->d && inS; ++a)
+        if (tb.G[(size_t)gi * c->d + a] != tb.S[(size_t)sidx * c->d + a]) inS = false;
+      if (inS) {
+        scol.push_back(gi);
+        ++sidx;
+      } else {
+        bcols.push_back(gi);
+      }
+    }
+  }
+  if (qt.self) {
+    if ((int)scol.size() != tb.nS) return SP_ERR_ARG;
+    for (int a = 0; a < tb.nS; ++a)
+      for (int j = 0; j < tb.nS; ++j)
+        if (Q_in[(size_t)a * tb.nG + scol[j]] != (a == j ? 1.0 : 0.0)) return SP_ERR_ARG;
+  } else {
+    bcols.resize(tb.nG);
+    for (int gi = 0; gi < tb.nG; ++gi) bcols[gi] = gi;
+  }
+  if ((int)bcols.size() != qt.na) return SP_ERR_ARG;
+  std::vector<double> Qc(ne), Cc(ne), Tc((size_t)tb.nS * qt.na);
+  std::vector<float> T32(Tc.size());
+  for (int col = 0; col < tb.nG; ++col)
+    for (int a = 0; a < tb.nS; ++a) {
+      Qc[(size_t)col * tb.nS + a] = Q_in[(size_t)a * tb.nG + col];
+      Cc[(size_t)col * tb.nS + a] = C_in[(size_t)a * tb.nG + col];
+    }
+  for (int cb = 0; cb < qt.na; ++cb)
+    for (int a = 0; a < tb.nS; ++a) {
+      const double v = -Q_in[(size_t)a * tb.nG + bcols[cb]];
+      Tc[(size_t)cb * tb.nS + a] = v;
+      T32[(size_t)cb * tb.nS + a] = (float)v;
+    }
+  SP_CK(cudaSetDevice(c->opts.device));
+  cudaStream_t st = c->stream;
+  SP_CK(cudaMemcpyAsync(c->Qcat + qt.tab_off, Qc.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, st));
+  SP_CK(cudaMemcpyAsync(c->Ccat + qt.tab_off, Cc.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, st));
+  SP_CK(cudaMemcpyAsync(c->Tcat + qt.t_off, Tc.data(), sizeof(double) * Tc.size(),
+                        cudaMemcpyHostToDevice, st));
+  SP_CK(cudaMemcpyAsync(c->Tcat32 + qt.t_off, T32.data(), sizeof(float) * T32.size(),
+                        cudaMemcpyHostToDevice, st));
+  SP_CK(cudaStreamSynchronize(st));
+  tb.Q.assign(Q_in, Q_in + ne);
+  tb.C.assign(C_in, C_in + ne);
+  c->factored = false;
+  return SP_OK;
+}
+
 sp_status sp_profile(sp_ctx* c, int enable) {
   if (!c) return SP_ERR_ARG;
   c->profiling = enable != 0;
