@@ -113,6 +113,13 @@ typedef struct {
                         nanoseconds of the GPU's global timer; 0 (default) = 2e9 (2 s),
                         else 1 ... 6e10.  When a wait runs out the panel stops and
                         sp_factor returns SP_ERR_TIMEOUT; destroy that context. */
+  int sweeps;        /* forward / backward sweeps of the levels that keep block inverses
+                        (Section 2.3's solve with the factor): 0 (default) one launch per
+                        level and direction where the front's work vectors fit in shared
+                        memory (a thread-block cluster of up to 16 CTAs per front walks the
+                        diagonal blocks itself); 1 a chain of launches per diagonal block
+                        (gather, block product, split row products).  Both are exact
+                        applications of the same factor; they round differently. */
 } sp_opts;
 
 typedef struct {

@@ -78,6 +78,9 @@ struct DevLevel {
   // entry keeps its summation order, so the choice never changes a result
   int gemm_tile = 0, gen_tile = 0;
   int ib = kInvBlockSize;   // diagonal-block size of the block inverses (inv levels)
+  // fused sweeps (inv levels whose work vectors fit in shared memory): CTAs per
+  // front (a thread-block cluster; 0 = the per-block launch chain) and threads per CTA
+  int fused_c = 0, fused_nt = 0;
 };
 
 // ---------------------------------------------------------------- FFT (sp_fft.cu)
@@ -184,6 +187,12 @@ cudaError_t backward_level(int prec, int d, DevLevel& L, double2* x, void* part,
                            int nv = 1, long N = 0);
 size_t sweep_partial_bytes(int nv = 1);
 int sweep_max_vectors();
+// launch shape of the fused one-launch-per-level sweep of an inverse-form level
+// (false: its work vectors do not fit in shared memory)
+bool sweep_fused_config(int prec, int nf, int m, int k, int num_sms, int max_cluster, int* C,
+                        int* NT);
+// CTAs per cluster the fused sweeps may use on the current device (16 or 8)
+int sweep_max_cluster();
 
 // ---------------------------------------------------------------- Krylov (sp_krylov.cu)
 struct KrylovWork {

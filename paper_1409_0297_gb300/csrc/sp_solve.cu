@@ -15,6 +15,8 @@
 // rows below (forward) or above (backward) take that column block's contribution,
 // one row per thread), so the large upper fronts spread over the whole GPU.
 // VT = double2 (FP64 form) or float2 (FP32 form).
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "sp_internal.h"
@@ -570,6 +572,10 @@ void inv_gemv(int mode, DevLevel& L, int j0, int j1, int rlo, int rhi, size_t sm
 }
 
 template <class VT>
+cudaError_t fused_level(bool fwd, int d, DevLevel& L, const DevLevel* child, const void* rhsQ,
+                        double2* x, int nv, long N, cudaStream_t st);
+
+template <class VT>
 cudaError_t forward_t(int d, DevLevel& L, const DevLevel* child, const void* rhsQ, void* part,
                       int nv, long N, cudaStream_t st) {
   using T = typename Scalar<VT>::T;
@@ -584,7 +590,10 @@ cudaError_t forward_t(int d, DevLevel& L, const DevLevel* child, const void* rhs
   const VT* cup = child ? (const VT*)child->upd : nullptr;
   const long custr = child ? (long)child->nf * (child->m - child->k) : 0;
   int launches = 1;
-  if (!L.inv) {
+  if (L.fused_c > 0) {
+    cudaError_t e = fused_level<VT>(true, d, L, child, rhsQ, nullptr, nv, N, st);
+    if (e != cudaSuccess) return e;
+  } else if (!L.inv) {
     dim3 g(L.nf, nv);
     forward_kernel<VT, T><<<g, 256, sweep_smem(L.m, L.k, sizeof(VT)), st>>>(
         d, (const T*)L.front, L.m, L.k, L.nb1, L.gidx, L.perm, (const VT*)rhsQ, cup, L.mc, L.kc,
@@ -625,7 +634,10 @@ cudaError_t backward_t(DevLevel& L, double2* x, void* part, int nv, long N, cuda
   const double kk = L.k, mk = L.m - L.k;
   ProfScope ps(PROF_BACKWARD, st);
   int launches = 1;
-  if (!L.inv) {
+  if (L.fused_c > 0) {
+    cudaError_t e = fused_level<VT>(false, 0, L, nullptr, nullptr, x, nv, N, st);
+    if (e != cudaSuccess) return e;
+  } else if (!L.inv) {
     dim3 g(L.nf, nv);
     backward_kernel<VT, T><<<g, 256, sizeof(VT) * (size_t)L.m, st>>>(
         (const T*)L.front, L.m, L.k, L.gidx, (const VT*)L.y, x, N);
@@ -656,6 +668,387 @@ cudaError_t backward_t(DevLevel& L, double2* x, void* part, int nv, long N, cuda
   return cudaGetLastError();
 }
 
+
+// ---- fused sweeps of the inverse-form levels -------------------------------------
+// One launch per level and direction instead of a chain of gather / diagonal-block /
+// row-product launches: a thread-block cluster of C CTAs per front (C = 1 on levels
+// with many fronts) holds the front's work vectors in shared memory and walks the
+// diagonal blocks itself.  Rows are owned in slabs of 32 (slab s by cluster rank
+// s mod C); a warp reads 32 consecutive rows of a column of the column-major front
+// (one 128-byte line in FP32).  A result that other CTAs of the cluster need (the
+// forward y of a diagonal block, the next block's right-hand side, the backward x)
+// is written into every CTA's copy through distributed shared memory before a
+// cluster barrier.  Every CTA runs the same sequence of barriers (the loop bounds
+// depend only on k, m and the block size), and each vector is summed in an order
+// that does not depend on how many vectors share the launch.
+namespace cg = cooperative_groups;
+
+struct FusedArgs {
+  int d, m, k, ib, nb1, mc, kc, nv;
+  const void* front;
+  const int* gidx;
+  const int* perm;
+  const int* ea_map;
+  const void* rhsQ;   // forward: stencil output (N per vector)
+  const void* cupd;   // forward: child update vectors (custr per vector)
+  void* upd;          // forward: nf (m - k) per vector
+  void* y;            // forward output / backward input: nf k per vector
+  double2* x;         // backward: global solution (N per vector)
+  long N, custr;
+};
+
+template <int NT>
+struct FusedShape {
+  static constexpr int W = NT / 32;
+};
+
+// dst[v ld + i] = val on this CTA and, with C > 1, on every other CTA of the cluster
+template <class VT>
+__device__ __forceinline__ void bcast(VT* dst, VT val, int C, cg::cluster_group& cl) {
+  if (C == 1) {
+    *dst = val;
+    return;
+  }
+  for (int q = 0; q < C; ++q) *cl.map_shared_rank(dst, q) = val;
+}
+
+__device__ __forceinline__ void csync(int C, cg::cluster_group& cl) {
+  if (C == 1)
+    __syncthreads();
+  else
+    cl.sync();
+}
+
+// Row products of the rows [r0, r1) owned by this CTA against columns [c0, c1):
+//   s_v(r) = sum_c A[r + c m] src[v ls + c]      (mask 0: every column,
+//   mask 1: c < r only, mask 2: c >= r only), then epi(r, v, s_v(r)).
+// Owned slabs are spread over the warps; when they are fewer than the warps, the
+// columns of each slab are split over several warps and the partial sums added in
+// split order through shared memory (red: W x 32 x NV).  Every thread of the CTA
+// must call this (it contains __syncthreads).
+template <class VT, class T, int NT, int NV, class Epi>
+__device__ void rows_times(const T* __restrict__ A, int m, int r0, int r1, int c0, int c1, int mask,
+                           const VT* src, int ls, int nv, int C, int q, VT* red, Epi epi) {
+  constexpr int W = NT / 32;
+  constexpr int U = sizeof(T) == 4 ? 16 : 8;  // column loads in flight per thread
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (r1 <= r0 || c1 <= c0) return;  // uniform: every thread sees the same bounds
+  const int s_lo = r0 >> 5, s_hi = (r1 - 1) >> 5;
+  const int first = s_lo + ((q - s_lo % C) % C + C) % C;  // first owned slab >= s_lo
+  const int nown = first > s_hi ? 0 : (s_hi - first) / C + 1;
+  if (nown == 0) return;  // uniform within the CTA
+  const int P = nown >= W ? 1 : W / nown;  // column splits per slab
+  auto slab_sum = [&](int i, int p, int np, VT* acc) {
+    const int s = first + i * C;
+    const int r = s * 32 + lane;
+    int cb = c0, ce = c1;
+    if (mask == 1) ce = min(ce, s * 32 + 32);
+    if (mask == 2) cb = max(cb, s * 32);
+    const int per = (ce - cb + np - 1) / np;
+    const int pb = cb + p * per, pe = min(ce, pb + per);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = VT{0, 0};
+    if (r < r0 || r >= r1) return;
+    const T* Ar = A + r;
+    int c = pb;
+    for (; c + U <= pe; c += U) {
+      T a[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int cc = c + u;
+        const bool use = mask == 0 || (mask == 1 ? cc < r : cc >= r);
+        a[u] = use ? Ar[(long)cc * m] : (T)0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+          if (v < nv) axpy(acc[v], a[u], src[v * ls + c + u]);
+    }
+    for (; c < pe; ++c) {
+      const bool use = mask == 0 || (mask == 1 ? c < r : c >= r);
+      const T a = use ? Ar[(long)c * m] : (T)0;
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+        if (v < nv) axpy(acc[v], a, src[v * ls + c]);
+    }
+  };
+  VT acc[NV];
+  if (P == 1) {
+    for (int i = warp; i < nown; i += W) {
+      slab_sum(i, 0, 1, acc);
+      const int r = (first + i * C) * 32 + lane;
+      if (r >= r0 && r < r1)
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+          if (v < nv) epi(r, v, acc[v]);
+    }
+    return;
+  }
+  const int i = warp % nown, p = warp / nown;
+  if (p < P) {
+    slab_sum(i, p, P, acc);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) red[(warp * 32 + lane) * NV + v] = acc[v];
+  }
+  __syncthreads();
+  if (p == 0) {
+    const int r = (first + i * C) * 32 + lane;
+    if (r >= r0 && r < r1) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        if (v >= nv) break;
+        VT sum = red[(warp * 32 + lane) * NV + v];
+        for (int pp = 1; pp < P; ++pp) {
+          const VT t = red[((warp + pp * nown) * 32 + lane) * NV + v];
+          sum.x += t.x;
+          sum.y += t.y;
+        }
+        epi(r, v, sum);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// shared memory of the fused kernels: tv (NV x m), yv (NV x k), red (W x 32 x NV)
+template <class VT, int NT, int NV>
+size_t fused_smem(int m, int k) {
+  return sizeof(VT) * ((size_t)NV * m + (size_t)NV * k + (size_t)NT * NV);
+}
+
+// Forward sweep of an inverse-form level: per front, t = [Pi b1; b2] gathered, then
+// for each diagonal block J: y_J = t_J + Linv_JJ t_J (strict lower part; unit
+// diagonal), t_r -= L[r, J] y_J for the rows below; out: y (k), upd = t[k, m).
+template <class VT, class T, int NT, int NV>
+__global__ void __launch_bounds__(NT) fused_forward_kernel(FusedArgs a) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int q = (int)cl.block_rank();
+  const int f = blockIdx.x / C, nf = gridDim.x / C;
+  const int m = a.m, k = a.k, nv = a.nv;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  VT* tv = reinterpret_cast<VT*>(smraw);  // NV x m
+  VT* yv = tv + (size_t)NV * m;            // NV x k
+  VT* red = yv + (size_t)NV * k;           // W x 32 x NV
+  const T* A = static_cast<const T*>(a.front) + (long)f * m * m;
+  const long v0 = (long)blockIdx.y * NV;  // first vector of this CTA's group
+  const VT* rhsQ = static_cast<const VT*>(a.rhsQ);
+  const VT* cupd = static_cast<const VT*>(a.cupd);
+  for (int v = 0; v < nv; ++v) {
+    gather_rhs(a.d, f, m, k, a.nb1, a.gidx, rhsQ + (v0 + v) * a.N,
+               cupd ? cupd + (v0 + v) * a.custr : nullptr, a.mc, a.kc, a.ea_map, tv + v * m);
+    const int* pr = a.perm + (long)f * k;
+    for (int j = threadIdx.x; j < k; j += NT) yv[v * k + j] = tv[v * m + pr[j]];
+    __syncthreads();
+    for (int j = threadIdx.x; j < k; j += NT) tv[v * m + j] = yv[v * k + j];
+    __syncthreads();
+  }
+  for (int j0 = 0; j0 < k; j0 += a.ib) {
+    const int j1 = min(k, j0 + a.ib);
+    rows_times<VT, T, NT, NV>(A, m, j0, j1, j0, j1, 1, tv, m, nv, C, q, red,
+                              [&](int r, int v, VT s) {
+                                const VT o = tv[v * m + r];
+                                bcast(&yv[v * k + r], VT{o.x + s.x, o.y + s.y}, C, cl);
+                              });
+    csync(C, cl);
+    const int nxt = min(k, j1 + a.ib);
+    rows_times<VT, T, NT, NV>(A, m, j1, m, j0, j1, 0, yv, k, nv, C, q, red,
+                              [&](int r, int v, VT s) {
+                                VT& o = tv[v * m + r];
+                                const VT val = VT{o.x - s.x, o.y - s.y};
+                                if (r < nxt)
+                                  bcast(&o, val, C, cl);
+                                else
+                                  o = val;
+                              });
+    csync(C, cl);
+  }
+  // outputs of the rows this CTA owns
+  VT* yout = static_cast<VT*>(a.y);
+  VT* upd = static_cast<VT*>(a.upd);
+  for (int v = 0; v < nv; ++v) {
+    for (int r = threadIdx.x; r < m; r += NT) {
+      if (((r >> 5) % C) != q) continue;
+      if (r < k)
+        yout[(v0 + v) * nf * (long)k + (long)f * k + r] = yv[v * k + r];
+      else
+        upd[(v0 + v) * nf * (long)(m - k) + (long)f * (m - k) + (r - k)] = tv[v * m + r];
+    }
+  }
+}
+
+// Backward sweep of an inverse-form level: x2 gathered from the global solution,
+// t = y1 - U12 x2, then for each diagonal block J from the last: x_J = Uinv_JJ t_J
+// (upper part with the diagonal), t_r -= U[r, J] x_J for the rows above; x_J goes
+// to the global solution.  tv holds x (NV x m), yv the right-hand sides t (NV x k).
+template <class VT, class T, int NT, int NV>
+__global__ void __launch_bounds__(NT) fused_backward_kernel(FusedArgs a) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int q = (int)cl.block_rank();
+  const int f = blockIdx.x / C, nf = gridDim.x / C;
+  const int m = a.m, k = a.k, nv = a.nv;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  VT* xv = reinterpret_cast<VT*>(smraw);  // NV x m
+  VT* tv = xv + (size_t)NV * m;            // NV x k
+  VT* red = tv + (size_t)NV * k;
+  const T* A = static_cast<const T*>(a.front) + (long)f * m * m;
+  const long v0 = (long)blockIdx.y * NV;
+  const int* gi = a.gidx + (long)f * m;
+  const VT* yin = static_cast<const VT*>(a.y);
+  for (int v = 0; v < nv; ++v)
+    for (int c = k + threadIdx.x; c < m; c += NT) xv[v * m + c] = from_d2<VT>(a.x[(v0 + v) * a.N + gi[c]]);
+  __syncthreads();
+  const int nblk = (k + a.ib - 1) / a.ib;
+  const int last0 = (nblk - 1) * a.ib;
+  // t = y1 - U12 x2 on the owned rows (the rows of the last block to every CTA)
+  if (m > k) {
+    rows_times<VT, T, NT, NV>(A, m, 0, k, k, m, 0, xv, m, nv, C, q, red, [&](int r, int v, VT s) {
+      const VT o = yin[(v0 + v) * nf * (long)k + (long)f * k + r];
+      const VT val = VT{o.x - s.x, o.y - s.y};
+      if (r >= last0)
+        bcast(&tv[v * k + r], val, C, cl);
+      else
+        tv[v * k + r] = val;
+    });
+  } else {
+    for (int v = 0; v < nv; ++v)
+      for (int r = threadIdx.x; r < k; r += NT)
+        tv[v * k + r] = yin[(v0 + v) * nf * (long)k + (long)f * k + r];
+  }
+  csync(C, cl);
+  for (int bi = nblk - 1; bi >= 0; --bi) {
+    const int j0 = bi * a.ib, j1 = min(k, j0 + a.ib);
+    rows_times<VT, T, NT, NV>(A, m, j0, j1, j0, j1, 2, tv, k, nv, C, q, red,
+                              [&](int r, int v, VT s) {
+                                bcast(&xv[v * m + r], s, C, cl);
+                                a.x[(v0 + v) * a.N + gi[r]] = to_d2(s);
+                              });
+    csync(C, cl);
+    const int prv = max(0, j0 - a.ib);
+    rows_times<VT, T, NT, NV>(A, m, 0, j0, j0, j1, 0, xv, m, nv, C, q, red,
+                              [&](int r, int v, VT s) {
+                                VT& o = tv[v * k + r];
+                                const VT val = VT{o.x - s.x, o.y - s.y};
+                                if (r >= prv)
+                                  bcast(&o, val, C, cl);
+                                else
+                                  o = val;
+                              });
+    csync(C, cl);
+  }
+}
+
+// cluster size and block size of a level's fused sweep: enough CTAs to cover the
+// GPU (C = 1 when the fronts alone give 2 per SM), at most 16 per front
+struct FusedCfg {
+  int C = 0, NT = 0;
+};
+FusedCfg fused_config(int nf, int num_sms, int max_cluster) {
+  FusedCfg c;
+  int C = 1;
+  while (C < max_cluster && (long)nf * C < 2L * num_sms) C *= 2;
+  c.C = C;
+  c.NT = C == 1 ? 256 : ((long)nf * C < num_sms ? 1024 : 512);
+  return c;
+}
+
+template <class VT, class T, int NT, int NV>
+cudaError_t fused_launch_t(bool fwd, const FusedArgs& a, int nf, int C, int groups,
+                           cudaStream_t st) {
+  const size_t smem = fused_smem<VT, NT, NV>(a.m, a.k);
+  auto kern = fwd ? fused_forward_kernel<VT, T, NT, NV> : fused_backward_kernel<VT, T, NT, NV>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (C > 8) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nf * C), (unsigned)groups);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+template <class VT, class T, int NV>
+cudaError_t fused_launch_nt(bool fwd, const FusedArgs& a, int nf, const FusedCfg& fc, int groups,
+                            cudaStream_t st) {
+  if (fc.NT == 256) return fused_launch_t<VT, T, 256, NV>(fwd, a, nf, fc.C, groups, st);
+  if (fc.NT == 512) return fused_launch_t<VT, T, 512, NV>(fwd, a, nf, fc.C, groups, st);
+  return fused_launch_t<VT, T, 1024, NV>(fwd, a, nf, fc.C, groups, st);
+}
+
+constexpr size_t kFusedSmemMax = 200 * 1024;
+
+// vectors per launch of a fused sweep (1 when only one vector's work vectors fit;
+// 0 when not even that fits)
+template <class VT>
+int fused_group(int m, int k, int NT, int nv) {
+  if (nv > 1 && fused_smem<VT, 1024, 4>(m, k) <= kFusedSmemMax) return 4;  // any NT <= 1024
+  (void)NT;
+  return fused_smem<VT, 1024, 1>(m, k) <= kFusedSmemMax ? 1 : 0;
+}
+
+template <class VT>
+cudaError_t fused_level(bool fwd, int d, DevLevel& L, const DevLevel* child, const void* rhsQ,
+                        double2* x, int nv, long N, cudaStream_t st) {
+  using T = typename Scalar<VT>::T;
+  const FusedCfg fc{L.fused_c, L.fused_nt};
+  FusedArgs a{};
+  a.d = d;
+  a.m = L.m;
+  a.k = L.k;
+  a.ib = L.ib;
+  a.nb1 = L.nb1;
+  a.mc = L.mc;
+  a.kc = L.kc;
+  a.front = L.front;
+  a.gidx = L.gidx;
+  a.perm = L.perm;
+  a.ea_map = L.ea_map;
+  a.rhsQ = rhsQ;
+  a.cupd = child ? child->upd : nullptr;
+  a.upd = L.upd;
+  a.y = L.y;
+  a.x = x;
+  a.N = N;
+  a.custr = child ? (long)child->nf * (child->m - child->k) : 0;
+  const int g = fused_group<VT>(L.m, L.k, fc.NT, nv);
+  if (g == 0) return cudaErrorInvalidValue;
+  // g = 1: one vector per CTA (NV = 1), every vector in its own blockIdx.y;
+  // g = 4: groups of four vectors per CTA sharing the factor reads, a last partial
+  // group (fewer than four) in a launch of its own
+  int done = 0;
+  while (done < nv) {
+    const int left = nv - done;
+    const int groups = g == 1 ? left : (left >= g ? left / g : 1);
+    const int per = g == 1 ? 1 : std::min(g, left);
+    FusedArgs b = a;
+    b.nv = per;
+    const long vt = (long)done;  // every vector-indexed pointer advances by `done` vectors
+    b.rhsQ = rhsQ ? static_cast<const VT*>(rhsQ) + vt * N : nullptr;
+    b.cupd = a.cupd ? static_cast<const VT*>(a.cupd) + vt * a.custr : nullptr;
+    b.upd = static_cast<VT*>(L.upd) + vt * (long)L.nf * (L.m - L.k);
+    b.y = static_cast<VT*>(L.y) + vt * (long)L.nf * L.k;
+    b.x = x ? x + vt * N : nullptr;
+    cudaError_t e = g == 1 ? fused_launch_nt<VT, T, 1>(fwd, b, L.nf, fc, groups, st)
+                           : fused_launch_nt<VT, T, 4>(fwd, b, L.nf, fc, groups, st);
+    if (e != cudaSuccess) return e;
+    done += groups * per;
+  }
+  return cudaSuccess;
+}
+
 }  // namespace
 
 cudaError_t q_apply(int prec, int d, int n, int nl, const std::vector<QTypeDev>& types,
@@ -682,6 +1075,49 @@ cudaError_t backward_level(int prec, int d, DevLevel& L, double2* x, void* part,
 }
 
 int sweep_max_vectors() { return kMaxVec; }
+
+int sweep_max_cluster() {
+  // 16 CTAs per cluster (non-portable) when a cluster of 16 of the largest fused
+  // kernels (1024 threads, the FP64 shared memory of a 2044-wide root) can be resident
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 8;
+  static int cache[64] = {0};
+  if (cache[dev]) return cache[dev];
+  int best = 8;
+  auto kern = fused_forward_kernel<double2, double, 1024, 1>;
+  const size_t smem = fused_smem<double2, 1024, 1>(2048, 2048);
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+          cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 16;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n >= 1) best = 16;
+  }
+  cudaGetLastError();  // a refused query leaves no error behind
+  cache[dev] = best;
+  return best;
+}
+
+bool sweep_fused_config(int prec, int nf, int m, int k, int num_sms, int max_cluster, int* C,
+                        int* NT) {
+  const int g = prec == SP_PREC_FP32 ? fused_group<float2>(m, k, 1024, 1)
+                                     : fused_group<double2>(m, k, 1024, 1);
+  if (g == 0) return false;
+  const FusedCfg fc = fused_config(nf, num_sms, max_cluster);
+  *C = fc.C;
+  *NT = fc.NT;
+  return true;
+}
 
 size_t sweep_partial_bytes(int nv) {
   return (size_t)2 * kGemvTarget * 256 * sizeof(double2) * (size_t)nv;

@@ -122,14 +122,15 @@ def test_preconditioner_apply(B, name, make, prec):
             assert rel(zh, M_own.apply(r)) <= 1e-10
             assert M.apply_residual(r, zh) <= 1e-12
         elif prec in (1, 4):
-            # FP32 factor of P (3xTF32 updates are FP32-accurate): backward error at
-            # single precision (see test_solve_512)
-            assert M.apply_residual(r, zh) <= 5e-3
+            # FP32 factor of P (3xTF32 updates are FP32-accurate): the backward error
+            # ||P z - Q r|| / ||Q r|| measured on these cases is at most 1.6e-4 (2D 64^2;
+            # 3D 16^3 3.5e-5): bound 5e-4
+            assert M.apply_residual(r, zh) <= 5e-4
         else:
             # TF32 products in the Schur updates of fronts with m >= 1024 (the 3D 16^3
-            # root, m = 1352): unit roundoff 2^-11 = 4.9e-4 instead of 6e-8, the same
-            # growth factors as the FP32 bound, so ten times the FP32 allowance
-            assert M.apply_residual(r, zh) <= 5e-2
+            # root, m = 1352; unit roundoff 2^-11 instead of 2^-24): measured at most
+            # 4.7e-3 (3D 16^3): bound 1.5e-2
+            assert M.apply_residual(r, zh) <= 1.5e-2
     S.close()
 
 
@@ -215,7 +216,9 @@ def test_solve_3d32(B, prec, which):
     S.apply(dev(r), z)
     rows = np.random.default_rng(5).choice(n ** d, 2000, replace=False)
     res = O.sampled_apply_residual(d, n, b, tabs, q, r, host(z), rows)
-    assert res <= {0: 1e-10, 1: 5e-3, 3: 5e-2, 4: 5e-3}[prec], res
+    # measured at most: FP32 5.1e-6, TF32 3.1e-3, 3xTF32 6.1e-6 (Helmholtz; Schroedinger
+    # lower): bounds about three times those
+    assert res <= {0: 1e-10, 1: 2e-5, 3: 1e-2, 4: 2e-5}[prec], res
     u = torch.empty(n ** d, dtype=torch.complex128, device="cuda")
     info = S.solve(dev(f), u)
     g = O.apply_green(d, n, s, f)
@@ -247,11 +250,10 @@ def test_solve_512(B, which, prec):
     S.apply(dev(r), z)
     rows = np.random.default_rng(5).choice(n * n, 4000, replace=False)
     res = O.sampled_apply_residual(d, n, b, tabs, q, r, host(z), rows)
-    # FP32 factor: LU backward error ~ m eps32 (m = 2044, eps32 = 6e-8: 1.2e-4) times
-    # the growth of the fronts and ||P|| ||z|| / ||Q r||; the FP32 form is assessed by
-    # the FP64 GMRES reaching 1e-8 below, this only guards against a broken factor
-    # (TF32 Schur updates: unit roundoff 2^-11, ten times the FP32 allowance)
-    assert res <= {0: 1e-10, 1: 5e-3, 2: 5e-3, 3: 5e-2, 4: 5e-3}[prec], res
+    # backward error of the reduced-precision factors measured at 4000 sampled rows:
+    # FP32 / mixed 2.8e-4, 3xTF32 2.4e-4, TF32 2.5e-2 (Helmholtz; Schroedinger
+    # 2e-6 / 2.5e-6 / 2.4e-4): bounds about three times the Helmholtz values
+    assert res <= {0: 1e-10, 1: 1e-3, 2: 1e-3, 3: 8e-2, 4: 1e-3}[prec], res
     u = torch.empty(n * n, dtype=torch.complex128, device="cuda")
     info = S.solve(dev(f), u)
     uh = host(u)
@@ -379,7 +381,8 @@ def test_inverse_block_sizes(B, name, make, ib):
         if prec == 0:
             assert rel(host(z), M.apply(r)) <= 1e-10
         else:
-            assert M.apply_residual(r, host(z)) <= 5e-3
+            # FP32 backward error measured at most 1.6e-4 (2D 64^2, inv_block 64)
+            assert M.apply_residual(r, host(z)) <= 5e-4
         S.close()
     with pytest.raises(B.SpError):
         B.Solver(d, n, b, s, inv_block=96)  # not a power of two
@@ -459,5 +462,5 @@ def test_solve_3d128_tf32_full_size(B):
     S.apply(dev(r), z)
     rows = np.random.default_rng(6).choice(n ** d, 2000, replace=False)
     res = O.sampled_apply_residual(d, n, b, tabs, q, r, host(z), rows)
-    assert res <= 0.5, res
+    assert res <= 0.35, res  # 0.28 measured
     S.close()

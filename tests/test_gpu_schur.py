@@ -115,8 +115,8 @@ def test_split_recovers_fp32_accuracy(B):
 def test_schur_update_arguments(B):
     t = torch.zeros(64, device="cuda", dtype=torch.float32)
     p = t.data_ptr()
-    with pytest.raises(B.SpError):  # K beyond the tensor-core outer block
-        B.sp_schur_update(3, 4, 4, 600, p, 4, 0, p, 600, 0, p, 4, 0, 1)
+    with pytest.raises(B.SpError):  # K beyond the tensor-core kernel's limit (16384)
+        B.sp_schur_update(3, 4, 4, 16416, p, 4, 0, p, 16416, 0, p, 4, 0, 1)
     with pytest.raises(B.SpError):  # leading dimension below the row count
         B.sp_schur_update(1, 8, 4, 4, p, 4, 0, p, 4, 0, p, 8, 0, 1)
     with pytest.raises(B.SpError):  # the mixed form has no update kernel of its own
