@@ -31,7 +31,7 @@ from .spectral import (wavenumber_grid, laplacian_symbol, green_symbol, green_ke
                        apply_green, apply_operator, helmholtz_shift, schrodinger_shift,
                        resonance_gap, dft_matrix)
 from .stencil import (set_types, canonical_set, canonical_gamma, canonical_beta, green_block,
-                      stencil_tables, pointwise_stencil_tables, matlab_pinv,
+                      stencil_tables, tables_from_T, pointwise_stencil_tables, matlab_pinv,
                       annihilation_ratio)
 from .precond import SparsifyingPreconditioner, assemble_sparse, sampled_rows, sampled_apply_residual
 from .gmres import gmres_right
@@ -40,7 +40,7 @@ __all__ = [
     "wavenumber_grid", "laplacian_symbol", "green_symbol", "green_kernel", "apply_green",
     "apply_operator", "helmholtz_shift", "schrodinger_shift", "resonance_gap", "dft_matrix",
     "set_types", "canonical_set", "canonical_gamma", "canonical_beta", "green_block",
-    "stencil_tables", "pointwise_stencil_tables", "matlab_pinv", "annihilation_ratio",
+    "stencil_tables", "tables_from_T", "pointwise_stencil_tables", "matlab_pinv", "annihilation_ratio",
     "SparsifyingPreconditioner", "assemble_sparse", "sampled_rows", "sampled_apply_residual",
     "gmres_right",
 ]

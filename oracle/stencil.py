@@ -90,6 +90,32 @@ def matlab_pinv(B: np.ndarray):
     return pinv, r, sig
 
 
+def _q_and_c(g: np.ndarray, n: int, S: np.ndarray, gam: np.ndarray, T: np.ndarray):
+    """Q(S, gamma) = [I, -T] on the columns (S, beta) in gamma order and
+    C(S, gamma) = Q(S, gamma) G(gamma, gamma) (Section 2.3)."""
+    S_set = {tuple(p) for p in S}
+    in_S = np.array([tuple(p) in S_set for p in gam])
+    Qg = np.zeros((S.shape[0], gam.shape[0]))
+    Qg[:, np.nonzero(in_S)[0]] = np.eye(S.shape[0])
+    Qg[:, np.nonzero(~in_S)[0]] = -T
+    Ggg = green_block(g, n, gam, flat_index(gam, n))
+    return Qg, Qg @ Ggg
+
+
+def tables_from_T(d: int, n: int, b: int, s: float, Ts: list) -> list[dict]:
+    """The set-type tables of Section 2.3 from given T_S (one |S| x |beta| array per
+    type t, rows in S order, columns in beta order): Q(S, gamma) = [I, -T_S] and
+    C(S, gamma) = Q(S, gamma) G(gamma, gamma), as stencil_tables forms them."""
+    g = green_kernel(d, n, s)
+    out = []
+    for t, T in enumerate(Ts):
+        S = canonical_set(d, b, t)
+        gam = canonical_gamma(d, b, t)
+        Q, C = _q_and_c(g, n, S, gam, np.asarray(T, dtype=np.float64))
+        out.append(dict(t=t, S=S, gamma=gam, beta=canonical_beta(d, b, t), T=T, Q=Q, C=C))
+    return out
+
+
 def stencil_tables(d: int, n: int, b: int, s: float, origin=None, types=None,
                    keep_blocks: bool = False) -> list[dict]:
     """T_t, Q_t(S, gamma) and C_t(S, gamma) for every set type (Section 2.3).
@@ -120,13 +146,7 @@ def stencil_tables(d: int, n: int, b: int, s: float, origin=None, types=None,
         B = green_block(g, n, beta, comp)
         Bp, rank, sig = matlab_pinv(B)
         T = A @ Bp
-        S_set = {tuple(p) for p in S}
-        in_S = np.array([tuple(p) in S_set for p in gam])
-        Qg = np.zeros((S.shape[0], gam.shape[0]))
-        Qg[:, np.nonzero(in_S)[0]] = np.eye(S.shape[0])
-        Qg[:, np.nonzero(~in_S)[0]] = -T
-        Ggg = green_block(g, n, gam, gam_flat)
-        C = Qg @ Ggg
+        Qg, C = _q_and_c(g, n, S, gam, T)
         resid = A - T @ B
         tab = dict(t=t, S=S - o, gamma=gam - o, beta=beta - o, T=T, Q=Qg, C=C,
                    rank=rank, sigma=sig,

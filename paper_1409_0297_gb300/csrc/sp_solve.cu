@@ -844,6 +844,9 @@ __global__ void __launch_bounds__(NT) fused_forward_kernel(FusedArgs a) {
     for (int j = threadIdx.x; j < k; j += NT) tv[v * m + j] = yv[v * k + j];
     __syncthreads();
   }
+  // every CTA of the cluster has finished using yv as the permutation buffer (and has
+  // started) before any y value is written into it
+  csync(C, cl);
   for (int j0 = 0; j0 < k; j0 += a.ib) {
     const int j1 = min(k, j0 + a.ib);
     rows_times<VT, T, NT, NV>(A, m, j0, j1, j0, j1, 1, tv, m, nv, C, q, red,
@@ -899,7 +902,7 @@ __global__ void __launch_bounds__(NT) fused_backward_kernel(FusedArgs a) {
   const VT* yin = static_cast<const VT*>(a.y);
   for (int v = 0; v < nv; ++v)
     for (int c = k + threadIdx.x; c < m; c += NT) xv[v * m + c] = from_d2<VT>(a.x[(v0 + v) * a.N + gi[c]]);
-  __syncthreads();
+  csync(C, cl);  // every CTA of the cluster has started before the first remote write
   const int nblk = (k + a.ib - 1) / a.ib;
   const int last0 = (nblk - 1) * a.ib;
   // t = y1 - U12 x2 on the owned rows (the rows of the last block to every CTA)
@@ -940,6 +943,8 @@ __global__ void __launch_bounds__(NT) fused_backward_kernel(FusedArgs a) {
   }
 }
 
+constexpr size_t kFusedSmemMax = 200 * 1024;
+
 // cluster size and block size of a level's fused sweep: enough CTAs to cover the
 // GPU (C = 1 when the fronts alone give 2 per SM), at most 16 per front
 struct FusedCfg {
@@ -958,12 +963,20 @@ template <class VT, class T, int NT, int NV>
 cudaError_t fused_launch_t(bool fwd, const FusedArgs& a, int nf, int C, int groups,
                            cudaStream_t st) {
   const size_t smem = fused_smem<VT, NT, NV>(a.m, a.k);
+  if (smem > kFusedSmemMax) return cudaErrorInvalidValue;
   auto kern = fwd ? fused_forward_kernel<VT, T, NT, NV> : fused_backward_kernel<VT, T, NT, NV>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  if (C > 8) {
+  // the attributes are set once per kernel, to the largest size any level may ask
+  // for: a launch captured into a graph keeps its own request, and lowering the
+  // attribute later would make that graph's launch fail
+  static bool attr_fwd = false, attr_bwd = false;
+  bool& attr = fwd ? attr_fwd : attr_bwd;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kFusedSmemMax);
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
+    attr = true;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(nf * C), (unsigned)groups);
@@ -987,8 +1000,6 @@ cudaError_t fused_launch_nt(bool fwd, const FusedArgs& a, int nf, const FusedCfg
   if (fc.NT == 512) return fused_launch_t<VT, T, 512, NV>(fwd, a, nf, fc.C, groups, st);
   return fused_launch_t<VT, T, 1024, NV>(fwd, a, nf, fc.C, groups, st);
 }
-
-constexpr size_t kFusedSmemMax = 200 * 1024;
 
 // vectors per launch of a fused sweep (1 when only one vector's work vectors fit;
 // 0 when not even that fits)
@@ -1087,7 +1098,7 @@ int sweep_max_cluster() {
   auto kern = fused_forward_kernel<double2, double, 1024, 1>;
   const size_t smem = fused_smem<double2, 1024, 1>(2048, 2048);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemMax) ==
           cudaSuccess) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(16);
