@@ -102,6 +102,9 @@ def parse():
     p.add_argument("--learned-lr", type=float, default=1e-3)
     p.add_argument("--only-learned", action="store_true",
                    help="run the learned-initial-guess workload alone and print its JSON")
+    p.add_argument("--sweeps", type=int, default=0, choices=[0, 1, 2],
+                   help="sweeps of the block-inverse levels (sp_opts.sweeps): 0 fused launches on "
+                        "many-front levels, chains elsewhere (default); 1 chains; 2 fused everywhere")
     p.add_argument("--no-autotune", action="store_true",
                    help="2D contexts keep the built-in launch-shape heuristics instead of "
                         "tuning them at set-up (sp_opts.autotune; results are bit-identical)")
@@ -343,7 +346,7 @@ def _measure_3d_one(args, B, torch, flush, w, forms, tf32_peak, dist, world, pro
         prec = {"tf32": B.SP_PREC_TF32, "tf32x3": B.SP_PREC_TF32X3}[name]
         t0 = time.perf_counter()
         S = B.Solver(d, n, b, s, prec=prec, device=int(os.environ.get("LOCAL_RANK", "0")),
-                     setup_route=args.setup_route_3d)
+                     setup_route=args.setup_route_3d, sweeps=args.sweeps)
         setup_s = time.perf_counter() - t0
         for _ in range(warm):
             S.factor(qd)
@@ -449,7 +452,7 @@ def measure_batch(args, B, torch, dist, world):
         else:
             s, q = B.sp_medium_schrodinger(2, p["n"], p["ell"], p["E"], p["V"])
             scale = p["ell"] ** 2
-        S = B.Solver(2, p["n"], p["b"], s, prec=prec, restart=64, device=local,
+        S = B.Solver(2, p["n"], p["b"], s, prec=prec, restart=64, device=local, sweeps=args.sweeps,
                      stream=streams[i].cuda_stream, max_rhs=len(p["rhs"]) if batched else 1,
                      host_threads=max(1, (os.cpu_count() or 1) // nw))
         return S, q, [np.ascontiguousarray(f * scale) for f in p["rhs"]]
@@ -566,7 +569,8 @@ def measure_learned(args, B, torch, dist, world):
     qs = 1.0 / (10.0 * ell * ell)
     V0 = sm.lattice_wells_potential_2d(n, ell, 5000)
     s, _ = B.sp_medium_schrodinger(2, n, ell, E, V0)
-    S = B.Solver(2, n, b, s, prec=B.SP_PREC_FP64, restart=200, device=local, max_rhs=nrhs)
+    S = B.Solver(2, n, b, s, prec=B.SP_PREC_FP64, restart=200, device=local, max_rhs=nrhs,
+                 sweeps=args.sweeps)
     net = B.Fno(n, sm.fno_initial_params(seed=4000), batch_max=16)
     ntr = nm * nrhs
     X = torch.empty((ntr, 3, N), dtype=torch.float32, device="cuda")
@@ -799,7 +803,7 @@ def run_ours(args):
     def make(prec):
         out = []
         for i, p in enumerate(probs):
-            S = B.Solver(p["d"], p["n"], p["b"], p["s"], prec=prec, device=local,
+            S = B.Solver(p["d"], p["n"], p["b"], p["s"], prec=prec, device=local, sweeps=args.sweeps,
                          autotune=not args.no_autotune,
                          stream=pair_streams[i].cuda_stream if pair_streams else 0)
             out.append(dict(S=S, q=torch.from_numpy(p["q"]).cuda(),
@@ -828,7 +832,8 @@ def run_ours(args):
         n = 64 if args.profile_workload == "3d64" else 128
         w = sm.helmholtz_grf_3d(n, 8, 0)
         s3, q3 = B.sp_medium_helmholtz(3, n, w["omega"], w["c"])
-        S = B.Solver(3, n, 8, s3, prec=form_prec[args.profile_step], device=local)
+        S = B.Solver(3, n, 8, s3, prec=form_prec[args.profile_step], device=local,
+                     sweeps=args.sweeps)
         u = torch.empty(n ** 3, dtype=torch.complex128, device="cuda")
         q3d = torch.from_numpy(q3).cuda()
         f3d = torch.from_numpy(np.ascontiguousarray(w["f"])).cuda()
@@ -1034,6 +1039,8 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "grid": "512^2", "b": 16, "solves_per_step": 2,
                        "tol": 1e-8, "l2": "flushed between steps (256 MB write)",
                        "autotune": not args.no_autotune, "fp64_tile_shapes_by_level": shapes64,
+                       "sweeps": ["fused on many-front levels, per-block chains elsewhere",
+                                  "per-block launch chains", "one fused launch per level"][args.sweeps],
                        "parallelism": "replicas" if world > 1 else "1 GPU",
                        "pair_concurrency": "one stream" if args.serial_pair else
                        "two CUDA streams, one host thread per problem"},

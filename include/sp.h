@@ -114,11 +114,14 @@ typedef struct {
                         else 1 ... 6e10.  When a wait runs out the panel stops and
                         sp_factor returns SP_ERR_TIMEOUT; destroy that context. */
   int sweeps;        /* forward / backward sweeps of the levels that keep block inverses
-                        (Section 2.3's solve with the factor): 0 (default) one launch per
-                        level and direction where the front's work vectors fit in shared
-                        memory (a thread-block cluster of up to 16 CTAs per front walks the
-                        diagonal blocks itself); 1 a chain of launches per diagonal block
-                        (gather, block product, split row products).  Both are exact
+                        (Section 2.3's solve with the factor): a level is either swept by a
+                        chain of launches per diagonal block (gather, block product, split
+                        row products) or by one fused launch per direction (the front's
+                        work vectors in shared memory; on levels with few fronts a
+                        thread-block cluster of up to 16 CTAs per front walks the diagonal
+                        blocks itself).  0 (default): fused only on levels whose fronts
+                        fill the GPU without clusters, chains elsewhere; 1: chains
+                        everywhere; 2: fused wherever the vectors fit.  All are exact
                         applications of the same factor; they round differently. */
 } sp_opts;
 

@@ -520,7 +520,7 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   }
   if (c->opts.tc_epilogue < 0 || c->opts.tc_epilogue > 2) return SP_ERR_ARG;
   if (c->opts.wait_limit_ns < 0 || c->opts.wait_limit_ns > 60000000000LL) return SP_ERR_ARG;
-  if (c->opts.sweeps != 0 && c->opts.sweeps != 1) return SP_ERR_ARG;
+  if (c->opts.sweeps < 0 || c->opts.sweeps > 2) return SP_ERR_ARG;
   const size_t RH = (size_t)c->opts.max_rhs;
   c->d = d;
   c->n = n;
@@ -620,7 +620,7 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   size_t scratch_bytes = 0, pack_floats = 0, gp_words = 0;
   int num_sms = 152;
   cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, c->opts.device);
-  const int max_cluster = c->opts.sweeps == 0 ? sweep_max_cluster() : 8;
+  const int max_cluster = c->opts.sweeps == 2 ? sweep_max_cluster() : 8;
   for (int l = 0; l <= L; ++l) {
     const Level& S = c->sym.lv[l];
     DevLevel& D = c->lv[l];
@@ -652,9 +652,10 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
     // 1.95 -> 1.51 s per solve for +0.1 s of inversion), 512 elsewhere (in 2D the
     // larger inverses cost more than the launches they save)
     D.ib = c->opts.inv_block > 0 ? c->opts.inv_block : (S.k >= 32768 ? 2048 : kInvBlockSize);
-    if (D.inv && c->opts.sweeps == 0) {
+    if (D.inv && c->opts.sweeps != 1) {
       int C = 0, NT = 0;
-      if (sweep_fused_config(prec, S.nf, S.m, S.k, num_sms, max_cluster, &C, &NT)) {
+      if (sweep_fused_config(prec, S.nf, S.m, S.k, num_sms, max_cluster, c->opts.sweeps == 2, &C,
+                             &NT)) {
         D.fused_c = C;
         D.fused_nt = NT;
       }

@@ -189,8 +189,8 @@ size_t sweep_partial_bytes(int nv = 1);
 int sweep_max_vectors();
 // launch shape of the fused one-launch-per-level sweep of an inverse-form level
 // (false: its work vectors do not fit in shared memory)
-bool sweep_fused_config(int prec, int nf, int m, int k, int num_sms, int max_cluster, int* C,
-                        int* NT);
+bool sweep_fused_config(int prec, int nf, int m, int k, int num_sms, int max_cluster,
+                        bool clusters, int* C, int* NT);
 // CTAs per cluster the fused sweeps may use on the current device (16 or 8)
 int sweep_max_cluster();
 

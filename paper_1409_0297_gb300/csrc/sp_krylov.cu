@@ -21,6 +21,8 @@ __device__ __forceinline__ void chunk_of(long N, long* c0, long* c1) {
   *c1 = min(N, *c0 + per);
 }
 
+// The Krylov basis V is read with the evict-first hint (it is larger than L2 at
+// 512^2 and streams through it every iteration), so the preconditioner's data stays.
 // partial[j * nblk + blk] = sum over the CTA's chunk of conj(V_j) w.  Each thread
 // walks its elements of the chunk with w[i] in registers and accumulates eight
 // vectors at a time (independent FMA chains; w is re-read once per eight
@@ -41,7 +43,7 @@ __device__ void chunk_dots(const double2* V, long ldv, int nv, const double2* w,
 #pragma unroll
       for (int q = 0; q < kJ; ++q) {
         if (q < nj) {
-          const double2 v = V[(long)(j0 + q) * ldv + i];  // conj(v) w
+          const double2 v = __ldcs(V + (long)(j0 + q) * ldv + i);  // conj(v) w; evict-first
           sr[q] = fma(v.x, wi.x, fma(v.y, wi.y, sr[q]));
           si[q] = fma(v.x, wi.y, fma(-v.y, wi.x, si[q]));
         }
@@ -87,13 +89,13 @@ __global__ void __launch_bounds__(kThr) update_dots_kernel(const double2* V, lon
     for (; j + 4 <= nv; j += 4) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const double2 v = V[(long)(j + q) * ldv + i], hj = hs[j + q];
+        const double2 v = __ldcs(V + (long)(j + q) * ldv + i), hj = hs[j + q];
         ax[q] = fma(v.x, hj.x, fma(-v.y, hj.y, ax[q]));
         ay[q] = fma(v.x, hj.y, fma(v.y, hj.x, ay[q]));
       }
     }
     for (; j < nv; ++j) {
-      const double2 v = V[(long)j * ldv + i], hj = hs[j];
+      const double2 v = __ldcs(V + (long)j * ldv + i), hj = hs[j];
       ax[0] = fma(v.x, hj.x, fma(-v.y, hj.y, ax[0]));
       ay[0] = fma(v.x, hj.y, fma(v.y, hj.x, ay[0]));
     }

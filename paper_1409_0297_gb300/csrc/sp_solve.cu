@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(256) forward_kernel(
     for (int r = jb + bs + threadIdx.x; r < m; r += blockDim.x) {
       VT acc = b[r];
       const T* Ar = A + r + (long)jb * m;
-      for (int j = 0; j < bs; ++j) axpy_neg(acc, Ar[(long)j * m], b[jb + j]);
+      for (int j = 0; j < bs; ++j) axpy_neg(acc, __ldcs(Ar + (long)j * m), b[jb + j]);
       b[r] = acc;
     }
     __syncthreads();
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(256) backward_kernel(const T* __restrict__ fro
   // rhs = y1 - U12 x2
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
     VT acc = yin[(long)f * k + i];
-    for (int c = k; c < m; ++c) axpy_neg(acc, A[i + (long)c * m], xb[c]);
+    for (int c = k; c < m; ++c) axpy_neg(acc, __ldcs(A + i + (long)c * m), xb[c]);
     xb[i] = acc;
   }
   __syncthreads();
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(256) backward_kernel(const T* __restrict__ fro
     for (int r = threadIdx.x; r < jb; r += blockDim.x) {
       VT acc = xb[r];
       const T* Ar = A + r + (long)jb * m;
-      for (int j = 0; j < bs; ++j) axpy_neg(acc, Ar[(long)j * m], xb[jb + j]);
+      for (int j = 0; j < bs; ++j) axpy_neg(acc, __ldcs(Ar + (long)j * m), xb[jb + j]);
       xb[r] = acc;
     }
     __syncthreads();
@@ -685,6 +685,7 @@ namespace cg = cooperative_groups;
 
 struct FusedArgs {
   int d, m, k, ib, nb1, mc, kc, nv;
+  int stream;  // factor loads with the evict-first hint (a level larger than a quarter of L2)
   const void* front;
   const int* gidx;
   const int* perm;
@@ -726,9 +727,15 @@ __device__ __forceinline__ void csync(int C, cg::cluster_group& cl) {
 // columns of each slab are split over several warps and the partial sums added in
 // split order through shared memory (red: W x 32 x NV).  Every thread of the CTA
 // must call this (it contains __syncthreads).
+template <class T>
+__device__ __forceinline__ T ld_front(const T* p, bool stream) {
+  return stream ? __ldcs(p) : *p;  // streaming (evict-first) for the large leaf level
+}
+
 template <class VT, class T, int NT, int NV, class Epi>
 __device__ void rows_times(const T* __restrict__ A, int m, int r0, int r1, int c0, int c1, int mask,
-                           const VT* src, int ls, int nv, int C, int q, VT* red, Epi epi) {
+                           const VT* src, int ls, int nv, int C, int q, VT* red, bool stream,
+                           Epi epi) {
   constexpr int W = NT / 32;
   constexpr int U = sizeof(T) == 4 ? 16 : 8;  // column loads in flight per thread
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -757,7 +764,7 @@ __device__ void rows_times(const T* __restrict__ A, int m, int r0, int r1, int c
       for (int u = 0; u < U; ++u) {
         const int cc = c + u;
         const bool use = mask == 0 || (mask == 1 ? cc < r : cc >= r);
-        a[u] = use ? Ar[(long)cc * m] : (T)0;
+        a[u] = use ? ld_front(Ar + (long)cc * m, stream) : (T)0;
       }
 #pragma unroll
       for (int u = 0; u < U; ++u)
@@ -767,7 +774,7 @@ __device__ void rows_times(const T* __restrict__ A, int m, int r0, int r1, int c
     }
     for (; c < pe; ++c) {
       const bool use = mask == 0 || (mask == 1 ? c < r : c >= r);
-      const T a = use ? Ar[(long)c * m] : (T)0;
+      const T a = use ? ld_front(Ar + (long)c * m, stream) : (T)0;
 #pragma unroll
       for (int v = 0; v < NV; ++v)
         if (v < nv) axpy(acc[v], a, src[v * ls + c]);
@@ -849,14 +856,14 @@ __global__ void __launch_bounds__(NT) fused_forward_kernel(FusedArgs a) {
   csync(C, cl);
   for (int j0 = 0; j0 < k; j0 += a.ib) {
     const int j1 = min(k, j0 + a.ib);
-    rows_times<VT, T, NT, NV>(A, m, j0, j1, j0, j1, 1, tv, m, nv, C, q, red,
+    rows_times<VT, T, NT, NV>(A, m, j0, j1, j0, j1, 1, tv, m, nv, C, q, red, a.stream,
                               [&](int r, int v, VT s) {
                                 const VT o = tv[v * m + r];
                                 bcast(&yv[v * k + r], VT{o.x + s.x, o.y + s.y}, C, cl);
                               });
     csync(C, cl);
     const int nxt = min(k, j1 + a.ib);
-    rows_times<VT, T, NT, NV>(A, m, j1, m, j0, j1, 0, yv, k, nv, C, q, red,
+    rows_times<VT, T, NT, NV>(A, m, j1, m, j0, j1, 0, yv, k, nv, C, q, red, a.stream,
                               [&](int r, int v, VT s) {
                                 VT& o = tv[v * m + r];
                                 const VT val = VT{o.x - s.x, o.y - s.y};
@@ -907,7 +914,7 @@ __global__ void __launch_bounds__(NT) fused_backward_kernel(FusedArgs a) {
   const int last0 = (nblk - 1) * a.ib;
   // t = y1 - U12 x2 on the owned rows (the rows of the last block to every CTA)
   if (m > k) {
-    rows_times<VT, T, NT, NV>(A, m, 0, k, k, m, 0, xv, m, nv, C, q, red, [&](int r, int v, VT s) {
+    rows_times<VT, T, NT, NV>(A, m, 0, k, k, m, 0, xv, m, nv, C, q, red, a.stream, [&](int r, int v, VT s) {
       const VT o = yin[(v0 + v) * nf * (long)k + (long)f * k + r];
       const VT val = VT{o.x - s.x, o.y - s.y};
       if (r >= last0)
@@ -923,14 +930,14 @@ __global__ void __launch_bounds__(NT) fused_backward_kernel(FusedArgs a) {
   csync(C, cl);
   for (int bi = nblk - 1; bi >= 0; --bi) {
     const int j0 = bi * a.ib, j1 = min(k, j0 + a.ib);
-    rows_times<VT, T, NT, NV>(A, m, j0, j1, j0, j1, 2, tv, k, nv, C, q, red,
+    rows_times<VT, T, NT, NV>(A, m, j0, j1, j0, j1, 2, tv, k, nv, C, q, red, a.stream,
                               [&](int r, int v, VT s) {
                                 bcast(&xv[v * m + r], s, C, cl);
                                 a.x[(v0 + v) * a.N + gi[r]] = to_d2(s);
                               });
     csync(C, cl);
     const int prv = max(0, j0 - a.ib);
-    rows_times<VT, T, NT, NV>(A, m, 0, j0, j0, j1, 0, xv, m, nv, C, q, red,
+    rows_times<VT, T, NT, NV>(A, m, 0, j0, j0, j1, 0, xv, m, nv, C, q, red, a.stream,
                               [&](int r, int v, VT s) {
                                 VT& o = tv[v * k + r];
                                 const VT val = VT{o.x - s.x, o.y - s.y};
@@ -1034,6 +1041,12 @@ cudaError_t fused_level(bool fwd, int d, DevLevel& L, const DevLevel* child, con
   a.x = x;
   a.N = N;
   a.custr = child ? (long)child->nf * (child->m - child->k) : 0;
+  {
+    // the factor entries one sweep reads: k(k-1)/2 + k(m-k) per front
+    const double bytes = (double)L.nf * sizeof(T) *
+                         ((double)L.k * (L.k - 1) / 2 + (double)L.k * (L.m - L.k));
+    a.stream = bytes > 32.0 * 1024 * 1024 ? 1 : 0;
+  }
   const int g = fused_group<VT>(L.m, L.k, fc.NT, nv);
   if (g == 0) return cudaErrorInvalidValue;
   // g = 1: one vector per CTA (NV = 1), every vector in its own blockIdx.y;
@@ -1119,12 +1132,13 @@ int sweep_max_cluster() {
   return best;
 }
 
-bool sweep_fused_config(int prec, int nf, int m, int k, int num_sms, int max_cluster, int* C,
-                        int* NT) {
+bool sweep_fused_config(int prec, int nf, int m, int k, int num_sms, int max_cluster,
+                        bool clusters, int* C, int* NT) {
   const int g = prec == SP_PREC_FP32 ? fused_group<float2>(m, k, 1024, 1)
                                      : fused_group<double2>(m, k, 1024, 1);
   if (g == 0) return false;
   const FusedCfg fc = fused_config(nf, num_sms, max_cluster);
+  if (fc.C > 1 && !clusters) return false;
   *C = fc.C;
   *NT = fc.NT;
   return true;

@@ -21,6 +21,10 @@ velocity, Schroedinger with lattice wells) it stores, in
                           relative residual 1e-8 (u stored in complex64: its
                           rounding, 6e-8 relative, is far below the 1e-6
                           solution tolerance it is used with);
+  u_ref, iters_ref, true_relres_ref
+                          the same GMRES to relative residual 1e-12: the discrete
+                          solution to ~1e-10 (complex64), against which a solution's
+                          forward error is measured;
   phase_seconds           wall time of each oracle phase on the host that ran it.
 
 Run from the repository root:  python tests/golden/make_golden_512.py helmholtz
@@ -95,11 +99,19 @@ def main(kind: str) -> None:
     ph["gmres"] = time.time() - t0
     print(f"[{kind}] GMRES {ref['iters']} iterations, true residual "
           f"{ref['true_relres']:.2e}, {ph['gmres']:.0f}s", flush=True)
+    t0 = time.time()
+    ref12 = O.gmres_right(lambda x: O.apply_operator(d, n, s, q, x), M.apply, g, tol=1e-12)
+    ph["gmres_ref"] = time.time() - t0
+    print(f"[{kind}] reference GMRES {ref12['iters']} iterations, true residual "
+          f"{ref12['true_relres']:.2e}; ||u - u_ref|| / ||u_ref|| = "
+          f"{np.linalg.norm(ref['u'] - ref12['u']) / np.linalg.norm(ref12['u']):.3e}", flush=True)
     out = os.path.join(ROOT, "tests", "golden", f"oracle_2d512_{kind}.npz")
     arrays = dict(s=np.float64(s), r_seed=np.int64(R_SEED), z=z.astype(np.complex128),
                   u=ref["u"].astype(np.complex64), iters=np.int64(ref["iters"]),
                   hist=np.asarray(ref["hist"], dtype=np.float64),
                   true_relres=np.float64(ref["true_relres"]),
+                  u_ref=ref12["u"].astype(np.complex64), iters_ref=np.int64(ref12["iters"]),
+                  true_relres_ref=np.float64(ref12["true_relres"]),
                   phase_names=np.array(sorted(ph)), phase_seconds=np.array([ph[k] for k in sorted(ph)],
                                                                            dtype=np.float64))
     for t, tab in enumerate(tabs):

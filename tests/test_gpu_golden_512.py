@@ -10,10 +10,14 @@ Per problem (Helmholtz on a random-field velocity, rescaled Schroedinger with a
     C(S, gamma) = Q(S, gamma) G(gamma, gamma) to the rounding of that product;
   * the FP64 preconditioner application z = P^{-1} Q r (Section 2.2) at 1e-10
     relative, element by element over all 262144 entries, on the oracle's tables;
-  * GMRES (Section 3; tolerance 1e-8): the FP64 form's iteration count within +-1 of
-    the oracle's and its residual estimates at 1e-6 relative; every precision form's
-    solution within 1e-6 relative of the oracle's u and a true residual
-    ||g - (I + G q) u|| / ||g|| <= 1e-8 by the oracle's FFT operator.
+  * GMRES (Section 3; tolerance 1e-8): every precision form reaches a true residual
+    ||g - (I + G q) u|| / ||g|| <= 1e-8 by the oracle's FFT operator; the FP64 form's
+    iteration count is within +-1 of the oracle's, its residual estimates agree at
+    1e-6 and its solution is within 1e-6 of the oracle's;
+  * forward accuracy: every form is within 1e-6 of the converged oracle solution
+    (GMRES to 1e-12) at tolerance 1e-8 for the Helmholtz problem and at 1e-9 for
+    both (the Schroedinger problem's solution amplifies residuals ~240-fold, so at
+    1e-8 even the oracle's own iterate is 2.3e-6 away from it).
 The library's contexts are built with the default (TSQR + SVD) set-up route, the
 benchmark's choice in 2D.
 """
@@ -116,6 +120,15 @@ def test_apply_512(B, kind):
 @pytest.mark.parametrize("kind", ["helmholtz", "schrodinger"])
 @pytest.mark.parametrize("prec", [0, 1, 2, 3, 4], ids=["fp64", "fp32", "mixed", "tf32", "tf32x3"])
 def test_solve_512_matches_oracle(B, kind, prec):
+    """GMRES at the benchmark's tolerance 1e-8: every form reaches a true residual of
+    1e-8 (the oracle's FFT operator); the FP64 form runs the oracle's Krylov iteration
+    (the same preconditioner to 1e-10), so its iteration count is within +-1, its
+    residual estimates agree to 1e-6 and its iterate is within 1e-6 of the oracle's
+    1e-8 iterate.  Every form is also within 1e-6 of the converged solution u_ref
+    (the oracle's GMRES to 1e-12) when the forward-error bound allows it: the oracle's
+    own 1e-8 iterate is 1.7e-7 from u_ref for the Helmholtz problem but 2.3e-6 for the
+    Schroedinger one (its solution amplifies residuals ~240-fold), so there the check
+    is test_forward_accuracy_512's, at tolerance 1e-9."""
     G = _load(kind)
     s, q, f = _problem(kind)
     S = B.Solver(2, 512, 16, s, prec=prec)
@@ -127,9 +140,31 @@ def test_solve_512_matches_oracle(B, kind, prec):
     g = O.apply_green(2, 512, s, f)
     true = float(np.linalg.norm(g - O.apply_operator(2, 512, s, q, uh)) / np.linalg.norm(g))
     assert true <= 1e-8, (true, info)
-    assert rel(uh, G["u"].astype(np.complex128)) <= 1e-6, rel(uh, G["u"].astype(np.complex128))
+    u_ref = G["u_ref"].astype(np.complex128)
+    if kind == "helmholtz":
+        assert rel(uh, u_ref) <= 1e-6, rel(uh, u_ref)
     if prec == 0:
+        assert rel(uh, G["u"].astype(np.complex128)) <= 1e-6, rel(uh, G["u"].astype(np.complex128))
         assert abs(info["iters"] - int(G["iters"])) <= 1, (info["iters"], int(G["iters"]))
         h = G["hist"]
         m = min(len(h), len(info["hist"]))
         assert np.allclose(info["hist"][:m], h[:m], rtol=1e-6, atol=1e-12)
+
+
+@pytest.mark.parametrize("kind", ["helmholtz", "schrodinger"])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4], ids=["fp64", "fp32", "mixed", "tf32", "tf32x3"])
+def test_forward_accuracy_512(B, kind, prec):
+    """Every form, solved to a true residual of 1e-9, is within 1e-6 relative of the
+    converged oracle solution u_ref (GMRES to 1e-12): the forward-error bar for both
+    512^2 problems, the Schroedinger one included."""
+    G = _load(kind)
+    s, q, f = _problem(kind)
+    S = B.Solver(2, 512, 16, s, prec=prec, tol=1e-9)
+    S.factor(torch.from_numpy(q).cuda())
+    u = torch.empty(512 * 512, dtype=torch.complex128, device="cuda")
+    info = S.solve(torch.from_numpy(f).cuda(), u)
+    uh = u.cpu().numpy()
+    S.close()
+    assert info["true_relres"] <= 1e-9, info
+    u_ref = G["u_ref"].astype(np.complex128)
+    assert rel(uh, u_ref) <= 1e-6, rel(uh, u_ref)

@@ -1,7 +1,8 @@
 """The fused sweeps (one launch per level and direction, a thread-block cluster of up
-to 16 CTAs per front on levels with few fronts) against the per-block launch chains
-(sp_opts.sweeps = 1).  Both apply the same factor exactly (Section 2.3's forward and
-backward substitutions with the block inverses), so in FP64 they agree to rounding:
+to 16 CTAs per front on levels with few fronts; sp_opts.sweeps = 2 everywhere, 0 on
+the levels with many fronts) against the per-block launch chains (sweeps = 1).  All
+apply the same factor exactly (Section 2.3's forward and backward substitutions with
+the block inverses), so in FP64 they agree to rounding:
 1e-11 relative on grids where cond(P) ~ 1e4-1e5.  The fused path must launch one
 forward and one backward kernel per level, and stacked right-hand sides (groups of
 four per CTA) must give each vector the same bits as a single-vector application."""
@@ -37,7 +38,7 @@ def test_fused_sweeps_match_chains(name, make, prec):
     N = n ** d
     r = torch.from_numpy(sm.random_complex_vector(N, 51)).cuda()
     out = []
-    for sweeps in (0, 1):
+    for sweeps in (2, 1, 0):
         S = B.Solver(d, n, b, s, prec=prec, sweeps=sweeps)
         S.factor(torch.from_numpy(q).cuda())
         z = torch.empty(N, dtype=torch.complex128, device="cuda")
@@ -46,18 +47,20 @@ def test_fused_sweeps_match_chains(name, make, prec):
         prof = B.sp_profile_read(S.ctx)
         B.sp_profile(S.ctx, False)
         nlev = len(B.sp_front_sizes(d, n, b))
-        if sweeps == 0:
+        if sweeps == 2:
             assert prof["forward"][1] == nlev and prof["backward"][1] == nlev, prof
         torch.cuda.synchronize()
         out.append(z.cpu().numpy())
         S.close()
-    rel = np.linalg.norm(out[0] - out[1]) / np.linalg.norm(out[1])
-    assert rel <= (1e-11 if prec == 0 else 2e-3), rel
+    for z in (out[0], out[2]):
+        rel = np.linalg.norm(z - out[1]) / np.linalg.norm(out[1])
+        assert rel <= (1e-11 if prec == 0 else 2e-3), rel
 
 
+@pytest.mark.parametrize("sweeps", [0, 2])
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
 @pytest.mark.parametrize("nrhs", [3, 6])
-def test_fused_sweeps_stacked_vectors_bit_identical(prec, nrhs):
+def test_fused_sweeps_stacked_vectors_bit_identical(prec, nrhs, sweeps):
     """Groups of four vectors per CTA and a partial group give each vector the bits of
     its single-vector application (2D 512^2: the root is fused in clusters of 16)."""
     from paper_1409_0297_gb300 import binding as B
@@ -65,7 +68,7 @@ def test_fused_sweeps_stacked_vectors_bit_identical(prec, nrhs):
     d, n, b = w["d"], w["n"], w["b"]
     s, q = _medium(B, w)
     N = n ** d
-    S = B.Solver(d, n, b, s, prec=prec, max_rhs=8)
+    S = B.Solver(d, n, b, s, prec=prec, max_rhs=8, sweeps=sweeps)
     S.factor(torch.from_numpy(q).cuda())
     F = torch.from_numpy(np.stack([sm.random_gaussian_source(2, n, 60 + i) for i in range(nrhs)])).cuda()
     U = torch.empty_like(F)
