@@ -123,6 +123,16 @@ typedef struct {
                         fill the GPU without clusters, chains elsewhere; 1: chains
                         everywhere; 2: fused wherever the vectors fit.  All are exact
                         applications of the same factor; they round differently. */
+  int panel_pivoting; /* pivoting of the cooperative grid panel in the FP32 forms (fronts too
+                        tall for a thread-block cluster, the 3D upper levels): 0 (default)
+                        partial pivoting column by column (two publication rounds per
+                        column); 1 tournament pivoting (communication-avoiding LU: each CTA
+                        picks 32 candidate rows by partial pivoting on its rows, groups of
+                        16 CTAs and then all CTAs play the winners off, and every row is
+                        eliminated against the 32 chosen ones at once: three publication
+                        rounds per panel, but three 32-step eliminations in sequence; 3D
+                        128^3 TF32 panels 1.22 s against 1.03 s).  FP64 grid panels always
+                        pivot column by column. */
 } sp_opts;
 
 typedef struct {

@@ -40,7 +40,8 @@ class sp_opts(ctypes.Structure):
                 ("autotune", ctypes.c_int), ("max_rhs", ctypes.c_int),
                 ("setup_route", ctypes.c_int), ("stencil", ctypes.c_int),
                 ("inv_block", ctypes.c_int), ("tc_epilogue", ctypes.c_int),
-                ("wait_limit_ns", ctypes.c_longlong), ("sweeps", ctypes.c_int)]
+                ("wait_limit_ns", ctypes.c_longlong), ("sweeps", ctypes.c_int),
+                ("panel_pivoting", ctypes.c_int)]
 
 
 class sp_info(ctypes.Structure):
@@ -385,7 +386,8 @@ class Solver:
                  maxit: int = 500, restart: int = 200, tol: float = 1e-8, device: int = 0,
                  stream: int = 0, host_threads: int = 0, autotune: bool = False,
                  max_rhs: int = 1, setup_route: int = 0, stencil: int = 0, inv_block: int = 0,
-                 tc_epilogue: int = 0, wait_limit_ns: int = 0, sweeps: int = 0):
+                 tc_epilogue: int = 0, wait_limit_ns: int = 0, sweeps: int = 0,
+                 panel_pivoting: int = 0):
         o = sp_default_opts()
         o.maxit, o.restart, o.tol, o.device = maxit, restart, tol, device
         o.host_threads = host_threads
@@ -397,6 +399,7 @@ class Solver:
         o.tc_epilogue = tc_epilogue
         o.wait_limit_ns = wait_limit_ns
         o.sweeps = sweeps
+        o.panel_pivoting = panel_pivoting
         self.d, self.n, self.b, self.s, self.prec = d, n, b, s, prec
         self.N = n ** d
         self.ctx = sp_setup(d, n, b, s, prec, o, stream)

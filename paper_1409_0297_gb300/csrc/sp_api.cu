@@ -307,6 +307,7 @@ void sp_default_opts(sp_opts* o) {
   o->tc_epilogue = 0;
   o->wait_limit_ns = 0;
   o->sweeps = 0;
+  o->panel_pivoting = 0;
 }
 
 const char* sp_status_str(sp_status st) {
@@ -521,6 +522,7 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   if (c->opts.tc_epilogue < 0 || c->opts.tc_epilogue > 2) return SP_ERR_ARG;
   if (c->opts.wait_limit_ns < 0 || c->opts.wait_limit_ns > 60000000000LL) return SP_ERR_ARG;
   if (c->opts.sweeps < 0 || c->opts.sweeps > 2) return SP_ERR_ARG;
+  if (c->opts.panel_pivoting != 0 && c->opts.panel_pivoting != 1) return SP_ERR_ARG;
   const size_t RH = (size_t)c->opts.max_rhs;
   c->d = d;
   c->n = n;
@@ -535,6 +537,7 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   c->work.tc_epi = c->opts.tc_epilogue;
   c->work.wait_ns = c->opts.wait_limit_ns > 0 ? (unsigned long long)c->opts.wait_limit_ns
                                               : 2000000000ull;
+  c->work.calu = c->opts.panel_pivoting == 1 ? 1 : 0;
   if (mixed && !(c->opts.inner_tol > 0 && c->opts.inner_tol < 1)) return SP_ERR_ARG;
   c->stream = (cudaStream_t)stream;
   c->N = 1;

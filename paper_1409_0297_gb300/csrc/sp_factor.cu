@@ -498,6 +498,322 @@ __global__ void __launch_bounds__(256) lu_panel_grid_kernel(T* fronts, int m, in
   }
 }
 
+// ---- tournament pivoting of the grid panel (FP32 forms) -------------------------
+// Communication-avoiding LU of the panel (Grigori, Demmel and Xiang, "CALU", 2011):
+// instead of one publication round per pivot column, the jb pivot rows are chosen
+// by a tournament, then every row is eliminated against them at once.
+//   1. each CTA runs partial-pivoting elimination on its candidate rows (slot below
+//      k - j0) and publishes the ORIGINAL values of its jb winners (read again
+//      from the front, which the panel does not change until its write-back);
+//   2. the first CTA of every group of kCaluGroup CTAs gathers the group's winners,
+//      runs the same elimination on them and publishes its jb winners' originals;
+//   3. every CTA gathers the groups' winners and runs the same elimination, which
+//      fixes the panel's pivot rows in order and their factored values [L11 | U11]
+//      (every CTA computes identical values from identical inputs);
+//   4. every other row gets its multipliers l = a U11^{-1} from its original values;
+//   5. the interchanges and the write-back are those of lu_panel_grid_kernel.
+// Pivots are chosen by FP32 magnitude with ties to the smaller slot.  Each wait on a
+// publication gives up after wait_ns (status bit 2, identity interchanges, return).
+constexpr int kCaluGroup = 16;
+constexpr int kCaluMaxGroups = (kGridPanelMaxG + kCaluGroup - 1) / kCaluGroup;
+constexpr int kCaluRow = kNB + 1;  // words of a published row: jb values, then the slot
+constexpr long kCaluTagWords = 256;  // u64 words: tags of level 1 (G) and level 2 (groups)
+constexpr long kCaluFrontWords =
+    kCaluTagWords + ((long)(kGridPanelMaxG + kCaluMaxGroups) * kNB * kCaluRow + 1) / 2;
+constexpr size_t kCaluBuf = sizeof(float) * (size_t)kCaluGroup * kNB * kCaluRow;  // gather buffer
+
+// Partial-pivoting elimination of the rows [0, R) of the shared-memory matrix
+// M(r, c) = M[r rs + c cs] (jb columns), candidates cand(r); up to jb pivots in order
+// into sel[] (row indices), *nsel their count.  Rows are owned round-robin by the
+// threads; two barriers per pivot.  used: R bytes of shared memory.
+template <class Cand, class Slot>
+__device__ void calu_gepp(float* M, int rs, int cs, int R, int jb, Cand cand, Slot slot,
+                          unsigned char* used, int* sel, int* nsel, unsigned long long* wkey) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  auto keyof = [&](int r, int c) -> unsigned long long {
+    const float v = fabsf(M[r * rs + c * cs]);
+    return ((unsigned long long)__float_as_uint(v) << 32) |
+           ((unsigned long long)(0xFFFFFu - (unsigned)slot(r)) << 12) | (unsigned long long)r;
+  };
+  for (int r = threadIdx.x; r < R; r += blockDim.x) used[r] = cand(r) ? 0 : 1;
+  __syncthreads();
+  unsigned long long key = 0ull;
+  for (int r = threadIdx.x; r < R; r += blockDim.x)
+    if (!used[r]) {
+      const unsigned long long kk = keyof(r, 0);  // nonzero even for a zero entry (slot field)
+      key = (kk > key) ? kk : key;
+    }
+  int n = 0;
+  for (int jj = 0; jj < jb; ++jj) {
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long ok = __shfl_down_sync(0xffffffffu, key, o);
+      key = ok > key ? ok : key;
+    }
+    if (lane == 0) wkey[warp] = key;
+    __syncthreads();
+    unsigned long long kb = 0ull;
+    for (int w = 0; w < nw; ++w) kb = wkey[w] > kb ? wkey[w] : kb;
+    // a candidate row always carries a key > 0 (its slot field is nonzero)
+    if (kb == 0ull) break;
+    const int p = (int)(kb & 0xFFFull);
+    if (threadIdx.x == 0) sel[jj] = p;
+    n = jj + 1;
+    float pv = M[p * rs + jj * cs];
+    if (!(fabsf(pv) > 0.f)) pv = 1e-30f;
+    const float inv = 1.f / pv;
+    key = 0ull;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+      if (used[r]) continue;
+      if (r == p) {
+        used[r] = 1;
+        continue;
+      }
+      const float l = M[r * rs + jj * cs] * inv;
+      M[r * rs + jj * cs] = l;
+      for (int c = jj + 1; c < jb; ++c) M[r * rs + c * cs] -= l * M[p * rs + c * cs];
+      if (jj + 1 < jb) {
+        const unsigned long long kk = keyof(r, jj + 1);
+        key = kk > key ? kk : key;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *nsel = n;
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) lu_panel_calu_kernel(float* fronts, int m, int k, int j0,
+                                                             int jb, int f0, int G, int* piv,
+                                                             const double* scale, double ptol,
+                                                             int* status, unsigned long long* pub,
+                                                             unsigned long long wait_ns) {
+  const int fl = blockIdx.x / G, g = blockIdx.x % G;
+  const int f = f0 + fl;
+  float* A = fronts + (long)f * m * m;
+  const int rows = m - j0, kl = k - j0;
+  const int chunk = (rows + G - 1) / G;
+  const int s0 = min(rows, g * chunk), s1 = min(rows, s0 + chunk), nmy = s1 - s0;
+  const int ngroups = (G + kCaluGroup - 1) / kCaluGroup;
+  unsigned long long* tags = pub + (long)f * kCaluFrontWords;  // [G] then [ngroups]
+  float* cand1 = reinterpret_cast<float*>(tags + kCaluTagWords);  // [G][jb][kCaluRow]
+  float* cand2 = cand1 + (long)kGridPanelMaxG * kNB * kCaluRow;   // [groups][jb][kCaluRow]
+  extern __shared__ unsigned long long smraw_u64[];
+  float* P = reinterpret_cast<float*>(smraw_u64);              // chunk x jb, column-major
+  float* Bf = P + (long)chunk * jb;                              // gather buffer, row-major
+  unsigned char* used = reinterpret_cast<unsigned char*>(Bf + (long)kCaluGroup * kNB * kCaluRow);
+  // used: max(chunk, kCaluGroup jb) bytes; pivj: chunk ints after it
+  int* pivj = reinterpret_cast<int*>(used + ((max(chunk, kCaluGroup * kNB) + 15) & ~15));
+  __shared__ float UF[kNB][kNB + 1];
+  __shared__ int sel[kNB], pslot[kNB], bslot[kCaluGroup * kNB];
+  __shared__ unsigned long long wkey[8];
+  __shared__ int s_n, s_abort;
+  __shared__ int ds[2 * kNB], dp[2 * kNB];
+  __shared__ int s_nd, s_ok;
+  __shared__ int cnt[kGridPanelMaxG], offs[kGridPanelMaxG + 1];
+  const double thresh = ptol * scale[f];
+  if (threadIdx.x == 0) s_abort = 0;
+  // ---- 1. local tournament on the chunk
+  for (long e = threadIdx.x; e < (long)nmy * jb; e += blockDim.x) {
+    const int r = (int)(e % nmy), c = (int)(e / nmy);
+    P[r + (long)c * chunk] = A[(j0 + s0 + r) + (long)(j0 + c) * m];
+  }
+  __syncthreads();
+  calu_gepp(P, 1, chunk, nmy, jb, [&](int r) { return s0 + r < kl; }, [&](int r) { return s0 + r; },
+            used, sel, &s_n, wkey);
+  const int n1 = s_n;
+  {
+    float* out = cand1 + (long)g * kNB * kCaluRow;  // this CTA's level-1 block of its front
+    for (int e = threadIdx.x; e < n1 * jb; e += blockDim.x) {
+      const int i = e / jb, c = e % jb;
+      const int r = sel[i];
+      out[(long)i * kCaluRow + c] = A[(j0 + s0 + r) + (long)(j0 + c) * m];
+      if (c == 0) out[(long)i * kCaluRow + jb] = __int_as_float(s0 + r);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) st_release64(tags + g, ((unsigned long long)n1 << 8) | 1ull);
+  }
+  // bounded wait for the tags [t0, t1) of `tags`; returns the candidate counts in cnt
+  auto wait_tags = [&](const unsigned long long* tg, int t0, int t1) -> bool {
+    if (threadIdx.x < 32) {
+      const unsigned long long tstart = gtimer_ns();
+      bool ok = true;
+      for (int i = t0 + (int)threadIdx.x; i < t1; i += 32) {
+        unsigned long long v = ld_acquire64(tg + i);
+        while ((v & 0xFFull) != 1ull) {
+          if (gtimer_ns() - tstart > wait_ns) {
+            ok = false;
+            break;
+          }
+          v = ld_acquire64(tg + i);
+        }
+        if (!ok) break;
+        cnt[i - t0] = (int)(v >> 8);
+      }
+      ok = __all_sync(0xffffffffu, ok);
+      if (threadIdx.x == 0) s_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    return s_ok != 0;
+  };
+  // gathers the candidate blocks [b0, b1) of `src` (counts in cnt) into Bf (row-major,
+  // kCaluRow words per row; block b's rows start at offs[b - b0])
+  auto gather = [&](const float* src, int b0, int b1) -> int {
+    if (threadIdx.x == 0) {
+      offs[0] = 0;
+      for (int b = b0; b < b1; ++b) offs[b - b0 + 1] = offs[b - b0] + cnt[b - b0];
+    }
+    __syncthreads();
+    const int tot = offs[b1 - b0];
+    for (int b = b0; b < b1; ++b) {
+      const float* blk = src + (long)b * kNB * kCaluRow;
+      const int nb = cnt[b - b0], o = offs[b - b0];
+      for (int e = threadIdx.x; e < nb * kCaluRow; e += blockDim.x)
+        Bf[(long)o * kCaluRow + e] = __ldcg(blk + e);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < tot; i += blockDim.x) bslot[i] = __float_as_int(Bf[(long)i * kCaluRow + jb]);
+    __syncthreads();
+    return tot;
+  };
+  // ---- 2. group tournament (first CTA of each group)
+  const int grp = g / kCaluGroup;
+  if (g % kCaluGroup == 0) {
+    const int b0 = grp * kCaluGroup, b1 = min(G, b0 + kCaluGroup);
+    if (!wait_tags(tags, b0, b1)) {
+      if (threadIdx.x == 0) {
+        s_abort = 1;
+        atomicOr(status, 2);
+      }
+    } else {
+      const int tot = gather(cand1, b0, b1);
+      calu_gepp(Bf, kCaluRow, 1, tot, jb, [&](int) { return true; }, [&](int r) { return bslot[r]; },
+                used, sel, &s_n, wkey);
+      const int n2 = s_n;
+      float* out = cand2 + (long)grp * kNB * kCaluRow;
+      // the winners' original rows: re-read from the level-1 area (Bf was eliminated)
+      for (int e = threadIdx.x; e < n2 * kCaluRow; e += blockDim.x) {
+        const int i = e / kCaluRow, c = e % kCaluRow;
+        const int r = sel[i];
+        // row r of Bf came from level-1 block b at row r - offs[b - b0]
+        int b = b0;
+        while (b + 1 < b1 && r >= offs[b + 1 - b0]) ++b;
+        out[(long)i * kCaluRow + c] =
+            __ldcg(cand1 + (long)b * kNB * kCaluRow + (long)(r - offs[b - b0]) * kCaluRow + c);
+      }
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) st_release64(tags + G + grp, ((unsigned long long)n2 << 8) | 1ull);
+    }
+  }
+  __syncthreads();
+  // ---- 3. final tournament (every CTA)
+  if (!s_abort) {
+    if (!wait_tags(tags + G, 0, ngroups)) {
+      if (threadIdx.x == 0) {
+        s_abort = 1;
+        atomicOr(status, 2);
+      }
+    }
+  }
+  __syncthreads();
+  if (s_abort) {
+    if (g == 0)
+      for (int c = threadIdx.x; c < jb; c += blockDim.x) piv[(long)f * k + j0 + c] = j0 + c;
+    return;
+  }
+  {
+    const int tot = gather(cand2, 0, ngroups);
+    calu_gepp(Bf, kCaluRow, 1, tot, jb, [&](int) { return true; }, [&](int r) { return bslot[r]; },
+              used, sel, &s_n, wkey);
+    if (s_n < jb) {  // fewer candidates than columns: cannot happen inside k
+      if (threadIdx.x == 0) atomicOr(status, 1);
+    }
+    for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) {
+      const int j = e / jb, c = e % jb;
+      UF[j][c] = j < s_n ? Bf[(long)sel[j] * kCaluRow + c] : (c == j ? 1.f : 0.f);
+    }
+    for (int j = threadIdx.x; j < jb; j += blockDim.x) pslot[j] = j < s_n ? bslot[sel[j]] : -1;
+    __syncthreads();
+    for (int j = threadIdx.x; j < jb; j += blockDim.x) {
+      float d = UF[j][j];
+      if (g == 0 && !(fabs((double)d) > thresh)) atomicOr(status, 1);
+      if (!(fabsf(d) > 0.f)) UF[j][j] = (float)(thresh > 0 ? thresh : 1e-30);
+    }
+  }
+  // ---- 4. rows of the chunk: pivot rows take their factored values, the others
+  // their multipliers from the original values
+  for (int r = threadIdx.x; r < nmy; r += blockDim.x) pivj[r] = -1;
+  __syncthreads();
+  for (int j = threadIdx.x; j < jb; j += blockDim.x)
+    if (pslot[j] >= s0 && pslot[j] < s1) pivj[pslot[j] - s0] = j;
+  for (long e = threadIdx.x; e < (long)nmy * jb; e += blockDim.x) {
+    const int r = (int)(e % nmy), c = (int)(e / nmy);
+    P[r + (long)c * chunk] = A[(j0 + s0 + r) + (long)(j0 + c) * m];
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < nmy; r += blockDim.x) {
+    float* pr = P + r;
+    const int j = pivj[r];
+    if (j >= 0) {
+      for (int c = 0; c < jb; ++c) pr[(long)c * chunk] = UF[j][c];
+      continue;
+    }
+    for (int c = 0; c < jb; ++c) {
+      float a = pr[(long)c * chunk];
+      for (int i = 0; i < c; ++i) a -= pr[(long)i * chunk] * UF[i][c];
+      pr[(long)c * chunk] = a / UF[c][c];
+    }
+  }
+  // ---- 5. positions of the interchanges (pivot slot pslot[jj] to position jj) and
+  // the write-back, as in lu_panel_grid_kernel
+  if (threadIdx.x == 0) {
+    int nd = 0;
+    for (int jj = 0; jj < jb; ++jj) {
+      const int sb = pslot[jj];
+      int p = sb, ib = -1, sa = jj, ia = -1;
+      for (int i = 0; i < nd; ++i) {
+        if (ds[i] == sb) {
+          p = dp[i];
+          ib = i;
+        }
+      }
+      for (int i = 0; i < nd; ++i)
+        if (dp[i] == jj) {
+          sa = ds[i];
+          ia = i;
+        }
+      if (ia < 0)
+        for (int i = 0; i < nd; ++i)
+          if (ds[i] == sa) ia = i;
+      if (ib < 0) {
+        ib = nd++;
+        ds[ib] = sb;
+      }
+      dp[ib] = jj;
+      if (sa != sb) {
+        if (ia < 0) {
+          ia = nd++;
+          ds[ia] = sa;
+        }
+        dp[ia] = p;
+      }
+      if (g == 0) piv[(long)f * k + j0 + jj] = j0 + p;
+    }
+    s_nd = nd;
+  }
+  __syncthreads();
+  const int nd = s_nd;
+  for (long e = threadIdx.x; e < (long)nmy * jb; e += blockDim.x) {
+    const int r = (int)(e % nmy), c = (int)(e / nmy);
+    const int sl = s0 + r;
+    int pos = sl;
+    for (int i = 0; i < nd; ++i)
+      if (ds[i] == sl) pos = dp[i];
+    A[(j0 + pos) + (long)(j0 + c) * m] = P[r + (long)c * chunk];
+  }
+}
+
 // Interchanges of the panel's pivots and the row-block solve
 // A[j0:j0+jb, c] = L_pp^{-1} A[j0:j0+jb, c] on the columns c in [c_lo, c_hi)
 // outside the panel [j0, j0+jb): columns left of the panel get the interchanges
@@ -978,6 +1294,20 @@ void grid_panel_shape(int nf, int rows, int* nfl, int* G) {
   *G = std::max(1, std::min(kGridPanelMaxG, std::min(kGridPanelCTAs / *nfl, (rows + 31) / 32)));
 }
 
+// the tournament panel's shared memory: the chunk (jb floats per row), the gather
+// buffer, the row flags and the pivot map
+size_t calu_smem(int chunk) {
+  return sizeof(float) * (size_t)chunk * kNB + kCaluBuf +
+         (size_t)((std::max(chunk, kCaluGroup * kNB) + 15) & ~15) + sizeof(int) * (size_t)chunk;
+}
+void calu_shape(int nf, int rows, int* nfl, int* G) {
+  const long per_row = sizeof(float) * kNB + 1 + sizeof(int);
+  const long cmax = (long)(kGridPanelSmem - kCaluBuf - kCaluGroup * kNB - 16) / per_row;
+  const int gmin = (int)std::max<long>(1, (rows + cmax - 1) / cmax);
+  *nfl = std::max(1, std::min(nf, kGridPanelCTAs / gmin));
+  *G = std::max(1, std::min(kGridPanelMaxG, std::min(kGridPanelCTAs / *nfl, (rows + 31) / 32)));
+}
+
 template <class T>
 int panel_kind(int m) {  // 0 one CTA, 1 cluster, 2 grid
   if ((size_t)m * kNB * sizeof(T) <= 160 * 1024) return 0;
@@ -995,7 +1325,32 @@ void panel_step(DevLevel& L, T* F, int j0, int jb, int c_lo, int c_hi, double pt
   for (int j = j0; j < j0 + jb; ++j) pf += (double)(L.m - j - 1) * (1.0 + 2.0 * (j0 + jb - j - 1));
   ProfScope pp(PROF_LU_PANEL, st);
   const int kind = panel_kind<T>(L.m);
-  if (kind == 2) {
+  if (kind == 2 && sizeof(T) == sizeof(float) && W.calu) {
+    const int rows = L.m - j0;
+    if (rows >= (1 << 20)) return;  // slot field of the pivot key; factor_level_t rejects it
+    int nfl, G;
+    calu_shape(L.nf, rows, &nfl, &G);
+    const int chunk = (rows + G - 1) / G;
+    for (int f0 = 0; f0 < L.nf; f0 += nfl) {
+      const int nfg = std::min(nfl, L.nf - f0);
+      // fresh publication tags for every launch (graph replays reuse the buffer)
+      for (int fi = 0; fi < nfg; ++fi)
+        cudaMemsetAsync(W.gpub + (size_t)(f0 + fi) * kCaluFrontWords, 0,
+                        sizeof(unsigned long long) * kCaluTagWords, st);
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(nfg * G));
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = calu_smem(chunk);
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeCooperative;
+      at[0].val.cooperative = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      cudaLaunchKernelEx(&cfg, lu_panel_calu_kernel, (float*)F, L.m, L.k, j0, jb, f0, G, L.piv,
+                         (const double*)L.scale, ptol, status, W.gpub, W.wait_ns);
+    }
+  } else if (kind == 2) {
     const int rows = L.m - j0;
     if (rows >= (1 << 20)) return;  // slot field of the pivot word; factor_level_t rejects it
     int nfl, G;
@@ -1086,6 +1441,8 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
     cudaFuncSetAttribute(lu_panel_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
     cudaFuncSetAttribute(lu_panel_grid_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kGridPanelSmem + 1024);
+    cudaFuncSetAttribute(lu_panel_calu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kGridPanelSmem + 1024);
     attr = true;
   }
@@ -1266,7 +1623,9 @@ size_t invert_scratch_elems(int nf, int k, int ib) {
   return (size_t)nf * ((size_t)2 * k * (ib + 1) + (size_t)k * (ib / 2));
 }
 
-size_t grid_panel_pub_words(int nf) { return (size_t)nf * 2 * kGridPanelMaxG * kPubWords; }
+size_t grid_panel_pub_words(int nf) {
+  return (size_t)nf * std::max<size_t>((size_t)2 * kGridPanelMaxG * kPubWords, kCaluFrontWords);
+}
 
 bool factor_grid_panel(int prec, int m) {
   return prec == SP_PREC_FP32 ? panel_kind<float>(m) == 2 : panel_kind<double>(m) == 2;

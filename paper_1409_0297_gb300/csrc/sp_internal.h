@@ -111,6 +111,7 @@ struct FactorWork {
   bool tc_split = false;      // ... as 3xTF32 (hi/lo split, FP32 accuracy)
   int tc_epi = 0;             // epilogue of the tensor-core update (tc_schur_update's epi)
   unsigned long long wait_ns = 2000000000ull;  // limit of each grid-panel poll (global timer ns)
+  int calu = 0;               // FP32 grid panels by tournament pivoting (0: column by column)
   // grid panel (fronts too tall for a cluster): per front 2 x kGridPanelMaxG
   // publication slots of grid_panel_pub_words() 8-byte words
   unsigned long long* gpub = nullptr;

@@ -29,6 +29,7 @@ def B():
 
 SMALL = F.FnoDims(n=64, c_in=3, width=8, modes=6, layers=3, hidden=16, c_out=2)
 FULL = F.FnoDims(n=64)  # width 32, 16 modes, 4 layers, hidden 128
+WORKLOAD = F.FnoDims(n=256)  # the learned-guess workload's network at its grid size
 
 
 def params(D, seed):
@@ -61,7 +62,7 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-@pytest.mark.parametrize("D", [SMALL, FULL], ids=["small", "full"])
+@pytest.mark.parametrize("D", [SMALL, FULL, WORKLOAD], ids=["small", "full", "n256"])
 @pytest.mark.parametrize("act_fp32", [True, False], ids=["fp32act", "bf16act"])
 def test_forward_matches_oracle(B, D, act_fp32):
     th = params(D, 11)
@@ -80,7 +81,7 @@ def test_forward_matches_oracle(B, D, act_fp32):
     net.close()
 
 
-@pytest.mark.parametrize("D", [SMALL, FULL], ids=["small", "full"])
+@pytest.mark.parametrize("D", [SMALL, FULL, WORKLOAD], ids=["small", "full", "n256"])
 def test_gradient_matches_oracle(B, D):
     th = params(D, 21)
     a, t = inputs(D, 2, 22)

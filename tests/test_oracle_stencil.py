@@ -153,3 +153,21 @@ def test_C_is_QG_on_the_pattern_and_P(d, n, b):
     # the truncation only drops the far field: Q(I + G q) - P is small compared with P
     full = Q @ (np.eye(n ** d) + G * q[None, :])
     assert np.linalg.norm(full - P) < 0.2 * np.linalg.norm(P)
+
+
+@pytest.mark.parametrize("d,n,b", [(2, 16, 4), (3, 8, 2), (2, 24, 3)])
+def test_tables_from_T_rebuilds_stencil_tables(d, n, b):
+    """tables_from_T (Q = [I, -T], C = Q G(gamma, gamma) from a given T) reproduces
+    stencil_tables' Q and C exactly when handed its T, and a perturbed T moves Q by
+    exactly that perturbation on the beta columns (the identity block stays)."""
+    s = 4 * np.pi ** 2 * 2.37
+    tabs = O.stencil_tables(d, n, b, s)
+    rebuilt = O.tables_from_T(d, n, b, s, [t["T"] for t in tabs])
+    for a, c in zip(tabs, rebuilt):
+        assert np.array_equal(a["Q"], c["Q"]) and np.array_equal(a["C"], c["C"])
+    T0 = tabs[0]["T"] + 1e-3
+    Q1 = O.tables_from_T(d, n, b, s, [T0] + [t["T"] for t in tabs[1:]])[0]["Q"]
+    diff = Q1 - tabs[0]["Q"]
+    assert np.allclose(np.abs(diff).sum(), 1e-3 * tabs[0]["T"].size)
+    S_cols = [i for i, p in enumerate(map(tuple, tabs[0]["gamma"])) if p in set(map(tuple, tabs[0]["S"]))]
+    assert np.array_equal(Q1[:, S_cols], np.eye(len(S_cols)))
