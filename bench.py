@@ -557,34 +557,41 @@ LEARNED_N, LEARNED_B, LEARNED_ELL, LEARNED_E = 256, 8, 8.0, 10.0
 def measure_learned(args, B, torch, dist, world):
     """Learned initial guess on 2D 256^2 Schroedinger problems (l = 8, E = 10, random 8 x 8
     lattice wells, b = 8), all sharing one context (one shift s; the solution does not
-    depend on s).  Training triples: `learned_media` potentials (seeds 5000 + m) x 8
-    random Gaussian sources (seeds 6000 + 8 m + r), each solved in FP64 by sp_factor +
-    sp_solve_many; the network input is (q / (10 l^2), g / c), its target u / c, with the
-    complex scale c = rms|g| e^{i phi}, phi = arg(sum g^2) / 2 (the solution is complex-linear
-    in the source, so c removes the source's size and phase).
-    Training: Adam on batches of 16 with a cosine learning-rate decay, every kernel in
-    the library (the triples sit in seeded random slots, so a batch is a contiguous slice
-    and an epoch visits the slices in a new random order).  Held-out: `learned_eval` problems (potential seed 7000 + i, source seed
-    8000 + i), each factored once and solved twice, from zero (sp_solve) and from the
-    network's guess (features + forward + guess + sp_solve_x0), both timed with CUDA
-    events; the solve stops at the same true residual 1e-8 in both arms."""
+    depend on s).  The network learns a correction to the method's own first estimate
+    z = M g = P^{-1} Q g (one preconditioner application): input (q / (10 l^2), g / c,
+    z / c), target (u - z) / c, guess u0 = z + c y, with the complex scale
+    c = rms|g| e^{i phi}, phi = arg(sum g^2) / 2 (the solution is complex-linear in the
+    source, so c removes the source's size and phase).
+    Training triples: `learned_media` potentials (seeds 5000 + m) x 8 random Gaussian
+    sources (seeds 6000 + 8 m + r), each solved in FP64 by sp_factor + sp_solve_many;
+    Adam on batches of 16 with a cosine learning-rate decay, every kernel in the library.
+    The triples sit in slots permuted once (seeded), so a batch is a contiguous slice:
+    batch membership is fixed across epochs and each epoch visits the batches in a new
+    order.  Per epoch: the mean training loss over all its batches and the loss on 64
+    validation problems (potential seeds 9000 + i, source seeds 9500 + i).
+    Held-out: `learned_eval` problems (potential seed 7000 + i, source seed 8000 + i),
+    each factored once and solved three times, every arm timed with CUDA events and
+    stopped at the same true residual 1e-8: from zero (sp_solve), from z alone (the
+    control: sp_apply + sp_solve_x0) and from the network's guess (sp_apply + features
+    + forward + guess + sp_solve_x0)."""
     n, b, ell, E = LEARNED_N, LEARNED_B, LEARNED_ELL, LEARNED_E
     N = n * n
     nm, nrhs, ne = args.learned_media, 8, args.learned_eval
+    nval = 64
     local = int(os.environ.get("LOCAL_RANK", "0"))
     qs = 1.0 / (10.0 * ell * ell)
     V0 = sm.lattice_wells_potential_2d(n, ell, 5000)
     s, _ = B.sp_medium_schrodinger(2, n, ell, E, V0)
     S = B.Solver(2, n, b, s, prec=B.SP_PREC_FP64, restart=200, device=local, max_rhs=nrhs,
                  sweeps=args.sweeps)
-    net = B.Fno(n, sm.fno_initial_params(seed=4000), batch_max=16)
+    cin = 5
+    net = B.Fno(n, sm.fno_initial_params(c_in=cin, seed=4000), c_in=cin, batch_max=16)
     ntr = nm * nrhs
-    X = torch.empty((ntr, 3, N), dtype=torch.float32, device="cuda")
+    X = torch.empty((ntr, cin, N), dtype=torch.float32, device="cuda")
     T = torch.empty((ntr, 2, N), dtype=torch.float32, device="cuda")
     sig = torch.empty(ntr, dtype=torch.complex128, device="cuda")
     g = torch.empty(N, dtype=torch.complex128, device="cuda")
-    # samples go to seeded random slots, so contiguous slices of X / T are shuffled
-    # batches: every epoch visits the batches in a new order with no gather kernel
+    z = torch.empty(N, dtype=torch.complex128, device="cuda")
     slot = np.random.default_rng(9001).permutation(nm * nrhs)
     t0 = time.perf_counter()
     gen_iters = []
@@ -600,44 +607,68 @@ def measure_learned(args, B, torch, dist, world):
         for r in range(nrhs):
             k = int(slot[m * nrhs + r])
             S.green(F[r], g)
-            net.features(q, qs, g, X[k], sig[k:k + 1])
-            net.target(U[r], sig[k:k + 1], T[k])
+            S.apply(g, z)
+            net.features_prior(q, qs, g, z, X[k], sig[k:k + 1])
+            net.target_prior(U[r], sig[k:k + 1], z, T[k])
+    # validation problems (their own potentials and sources)
+    Xv = torch.empty((nval, cin, N), dtype=torch.float32, device="cuda")
+    Tv = torch.empty((nval, 2, N), dtype=torch.float32, device="cuda")
+    sv = torch.empty(nval, dtype=torch.complex128, device="cuda")
+    uv = torch.empty(N, dtype=torch.complex128, device="cuda")
+    for i in range(nval):
+        V = sm.lattice_wells_potential_2d(n, ell, 9000 + i)
+        q = torch.from_numpy(B.sp_medium_schrodinger_at(2, n, ell, E, V, s)).cuda()
+        f = torch.from_numpy(sm.random_gaussian_source(2, n, 9500 + i) * ell ** 2).cuda()
+        S.factor(q)
+        S.solve(f, uv)
+        S.green(f, g)
+        S.apply(g, z)
+        net.features_prior(q, qs, g, z, Xv[i], sv[i:i + 1])
+        net.target_prior(uv, sv[i:i + 1], z, Tv[i])
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
+
+    def val_loss():
+        tot = 0.0
+        for i0 in range(0, nval, 16):
+            L, _ = net.gradient(Xv[i0:i0 + 16], Tv[i0:i0 + 16], 16, want_grad=False)
+            tot += L * 16
+        return tot / nval
+
     # training
     bs, epochs = 16, args.learned_epochs
-    nsteps = epochs * (ntr // bs)
+    nb = ntr // bs
+    nsteps = epochs * nb
     lr0 = args.learned_lr
     rng = np.random.default_rng(9000)
-    nb = ntr // bs
-    losses = []
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
+    losses, vlosses = [], [val_loss()]
+    train_ms = 0.0
     step = 0
     for ep in range(epochs):
         order = rng.permutation(nb)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        tot = 0.0
         for j in range(nb):
             bi = int(order[j])
             lr = 0.5 * lr0 * (1 + np.cos(np.pi * step / nsteps))
-            last = j == nb - 1
-            L = net.train_step(X[bi * bs:(bi + 1) * bs], T[bi * bs:(bi + 1) * bs], bs, lr,
-                               sync=last)
-            if last:
-                losses.append(L)
+            tot += net.train_step(X[bi * bs:(bi + 1) * bs], T[bi * bs:(bi + 1) * bs], bs, lr, sync=True)
             step += 1
-    ev1.record()
-    torch.cuda.synchronize()
-    train_ms = ev0.elapsed_time(ev1)
+        ev1.record()
+        torch.cuda.synchronize()
+        train_ms += ev0.elapsed_time(ev1)
+        losses.append(tot / nb)
+        vlosses.append(val_loss())
     # held-out evaluation
-    x1 = torch.empty((1, 3, N), dtype=torch.float32, device="cuda")
+    x1 = torch.empty((1, cin, N), dtype=torch.float32, device="cuda")
     y1 = torch.empty((1, 2, N), dtype=torch.float32, device="cuda")
     s1 = torch.empty(1, dtype=torch.complex128, device="cuda")
     u0 = torch.empty(N, dtype=torch.complex128, device="cuda")
     uz = torch.empty(N, dtype=torch.complex128, device="cuda")
     ug = torch.empty(N, dtype=torch.complex128, device="cuda")
-    ms_zero = ms_guess = ms_factor = 0.0
-    it_zero, it_guess, g_rel, u_err, used, worst = [], [], [], [], 0, 0.0
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    ms_zero = ms_prior = ms_guess = ms_factor = 0.0
+    it_zero, it_prior, it_guess, g_rel, p_rel, u_err, used, worst = [], [], [], [], [], [], 0, 0.0
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
     for i in range(ne):
         V = sm.lattice_wells_potential_2d(n, ell, 7000 + i)
         q = torch.from_numpy(B.sp_medium_schrodinger_at(2, n, ell, E, V, s)).cuda()
@@ -648,45 +679,58 @@ def measure_learned(args, B, torch, dist, world):
         iz = S.solve(f, uz)
         evs[2].record()
         S.green(f, g)
-        net.features(q, qs, g, x1[0], s1)
-        net.forward(x1, y1, 1)
-        net.guess(y1[0], s1, u0)
+        S.apply(g, z)
+        ip = S.solve_x0(f, z, ug)
         evs[3].record()
-        ig = S.solve_x0(f, u0, ug)
+        S.green(f, g)
+        S.apply(g, z)
+        net.features_prior(q, qs, g, z, x1[0], s1)
+        net.forward(x1, y1, 1)
+        net.guess_prior(y1[0], s1, z, u0)
         evs[4].record()
+        ig = S.solve_x0(f, u0, ug)
+        evs[5].record()
         torch.cuda.synchronize()
         ms_factor += evs[0].elapsed_time(evs[1])
         ms_zero += evs[1].elapsed_time(evs[2])
-        ms_guess += evs[2].elapsed_time(evs[4])
+        ms_prior += evs[2].elapsed_time(evs[3])
+        ms_guess += evs[3].elapsed_time(evs[5])
         it_zero.append(iz["iters"])
+        it_prior.append(ip["iters"])
         it_guess.append(ig["iters"])
         g_rel.append(ig["guess_relres"])
+        p_rel.append(ip["guess_relres"])
         used += int(ig["guess_used"])
-        worst = max(worst, iz["true_relres"], ig["true_relres"])
+        worst = max(worst, iz["true_relres"], ip["true_relres"], ig["true_relres"])
         u_err.append(float(torch.linalg.vector_norm(u0 - uz) / torch.linalg.vector_norm(uz)))
     S.close()
     net.close()
     torch.cuda.synchronize()
     zero_v = ne / ((ms_factor + ms_zero) / 1e3)
+    prior_v = ne / ((ms_factor + ms_prior) / 1e3)
     guess_v = ne / ((ms_factor + ms_guess) / 1e3)
     return {"workload": f"learned initial guess: 2D {n}^2 Schroedinger, l = {ell:g}, E = {E:g}, random "
                         f"8 x 8 lattice wells, b = {b}; {ntr} training triples ({nm} potentials x "
                         f"{nrhs} sources), {ne} held-out (potential, source) pairs",
-            "network": "Fourier layers: 4 x width 32, 16 modes, projection 128; bf16 weights, "
-                       "bf16 activations, FP32 accumulation; Adam",
-            "form": "plain FP64 solve in both arms",
+            "network": "Fourier layers: 4 x width 32, 16 modes, projection 128; input (q, g, z = M g) "
+                       "scaled, output the correction to z; bf16 weights, bf16 activations, "
+                       "FP32 accumulation; Adam",
+            "form": "plain FP64 solve in every arm",
             "value": guess_v, "unit": "solves/s", "zero_guess_value": zero_v,
             "speedup_vs_zero_guess": guess_v / zero_v,
+            "prior_only": {"value": prior_v, "speedup_vs_zero_guess": prior_v / zero_v,
+                           "iters_mean": float(np.mean(it_prior)),
+                           "start_relres_median": float(np.median(p_rel))},
             "iters_zero_mean": float(np.mean(it_zero)), "iters_guess_mean": float(np.mean(it_guess)),
             "guess_relres_median": float(np.median(g_rel)), "guess_used": used,
             "guess_solution_relerr_median": float(np.median(u_err)),
             "max_true_relres": worst,
             "ms_per_solve": {"factor": ms_factor / ne, "zero_solve": ms_zero / ne,
-                             "guess_and_solve": ms_guess / ne},
+                             "prior_and_solve": ms_prior / ne, "guess_and_solve": ms_guess / ne},
             "data_generation_s": gen_s, "data_iters_mean": float(np.mean(gen_iters)),
             "training": {"epochs": epochs, "batch": bs, "steps": nsteps, "lr0": lr0,
                          "ms": train_ms, "samples_per_s": nsteps * bs / (train_ms / 1e3),
-                         "loss_by_epoch": losses},
+                         "epoch_mean_loss": losses, "validation_loss_by_epoch": vlosses},
             "data": "synthetic"}
 
 

@@ -108,6 +108,18 @@ sp_status sp_fno_guess(sp_fno *f, const float *y_dev, const void *scale_dev, voi
  * t[0] + i t[1] = u / c. */
 sp_status sp_fno_target(sp_fno *f, const void *u_dev, const void *scale_dev, float *t_dev);
 
+/* The same three with a prior estimate z of the solution (the network then learns a
+ * correction to it; not in the paper: z is the preconditioner applied to g, the
+ * first approximation the method itself offers, z = P^{-1} Q g, sp_apply).  Features
+ * (c_in must be 5): x[0..2] as sp_fno_features, x[3] + i x[4] = z / c.  Guess:
+ * u0 = z + c (y[0] + i y[1]).  Target: t[0] + i t[1] = (u - z) / c.  z_dev: N complex128. */
+sp_status sp_fno_features_prior(sp_fno *f, const double *q_dev, double q_scale, const void *g_dev,
+                                const void *z_dev, float *x_dev, void *scale_dev);
+sp_status sp_fno_guess_prior(sp_fno *f, const float *y_dev, const void *scale_dev, const void *z_dev,
+                             void *u0_dev);
+sp_status sp_fno_target_prior(sp_fno *f, const void *u_dev, const void *scale_dev, const void *z_dev,
+                              float *t_dev);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,8 @@ EXPORTED = [
     "sp_solve_x0", "sp_medium_schrodinger_at", "sp_destroy", "sp_status_str",
     "sp_fno_param_count", "sp_fno_create", "sp_fno_destroy", "sp_fno_set_params",
     "sp_fno_get_params", "sp_fno_forward", "sp_fno_gradient", "sp_fno_train_step",
-    "sp_fno_features", "sp_fno_guess", "sp_fno_target",
+    "sp_fno_features", "sp_fno_guess", "sp_fno_target", "sp_fno_features_prior",
+    "sp_fno_guess_prior", "sp_fno_target_prior",
 ]
 PROF_CLASSES = ["assemble", "lu_panel", "lu_trsm", "lu_gemm", "qapply", "forward", "backward",
                 "fft", "krylov", "lu_trinv", "lu_tc"]
@@ -117,6 +118,9 @@ def _load() -> ctypes.CDLL:
         "sp_fno_features": (I, [P, P, D, P, P, P]),
         "sp_fno_guess": (I, [P, P, P, P]),
         "sp_fno_target": (I, [P, P, P, P]),
+        "sp_fno_features_prior": (I, [P, P, D, P, P, P, P]),
+        "sp_fno_guess_prior": (I, [P, P, P, P, P]),
+        "sp_fno_target_prior": (I, [P, P, P, P, P]),
         "sp_destroy": (V, [P]),
         "sp_status_str": (ctypes.c_char_p, [I]),
     }
@@ -577,6 +581,29 @@ class Fno:
         _check(LIB.sp_fno_target(self.h, self._t(u, 1, 1, torch.complex128),
                                  self._t(scale_slot, 0, 0, torch.complex128), self._t(t_slot, 2, 1)),
                "sp_fno_target")
+
+    def features_prior(self, q, q_scale: float, g, z, x_slot, scale_slot):
+        """One problem's input with the prior z (5 x N floats at x_slot) and its scale."""
+        import torch
+        _check(LIB.sp_fno_features_prior(self.h, self._t(q, 1, 1, torch.float64), float(q_scale),
+                                         self._t(g, 1, 1, torch.complex128),
+                                         self._t(z, 1, 1, torch.complex128), self._t(x_slot, 5, 1),
+                                         self._t(scale_slot, 0, 0, torch.complex128)),
+               "sp_fno_features_prior")
+
+    def guess_prior(self, y_slot, scale_slot, z, u0):
+        import torch
+        _check(LIB.sp_fno_guess_prior(self.h, self._t(y_slot, 2, 1),
+                                      self._t(scale_slot, 0, 0, torch.complex128),
+                                      self._t(z, 1, 1, torch.complex128),
+                                      self._t(u0, 1, 1, torch.complex128)), "sp_fno_guess_prior")
+
+    def target_prior(self, u, scale_slot, z, t_slot):
+        import torch
+        _check(LIB.sp_fno_target_prior(self.h, self._t(u, 1, 1, torch.complex128),
+                                       self._t(scale_slot, 0, 0, torch.complex128),
+                                       self._t(z, 1, 1, torch.complex128), self._t(t_slot, 2, 1)),
+               "sp_fno_target_prior")
 
     def close(self):
         if getattr(self, "h", None):

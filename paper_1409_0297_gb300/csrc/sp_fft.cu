@@ -143,6 +143,110 @@ __device__ __forceinline__ void dif_stages(VT* sm, const PassArgs<VT>& a, bool c
   }
 }
 
+// The same transforms with the radix-2 stages taken two at a time (radix 4): three
+// twiddle products and one barrier per pair of stages instead of four and two.
+//   DIT stages s, s+1 (h = 2^(s-1)): with t1 = w_{2h}^j, t2 = w_{4h}^j,
+//     u0 = x0, u1 = t1 x1, u2 = t2 x2, u3 = t1 t2 x3 (x_q at base + j + q h),
+//     y0 = (u0 + u1) + (u2 + u3), y2 = (u0 + u1) - (u2 + u3),
+//     y1 = (u0 - u1) - i (u2 - u3), y3 = (u0 - u1) + i (u2 - u3);
+//   DIF stages s, s-1 (q = 2^(s-2)) of the conjugate (inverse) transform: with
+//     t1 = conj w_{4q}^j, t2 = conj w_{2q}^j, s0 = x0 + x2, s1 = x0 - x2, s2 = x1 + x3,
+//     s3 = x1 - x3 (x_r at base + j + r q): y0 = s0 + s2, y1 = (s0 - s2) t2,
+//     y2 = (s1 + i s3) t1, y3 = (s1 - i s3) t1 t2.
+// An odd stage count leaves one radix-2 stage (first for DIT, last for DIF).
+template <class VT>
+__device__ __forceinline__ VT mul_i(VT v) {  // i v
+  VT r;
+  r.x = -v.y;
+  r.y = v.x;
+  return r;
+}
+template <int R, class VT>
+__device__ __forceinline__ void dit_stages4(VT* sm, const PassArgs<VT>& a) {
+  const int M = a.M, ld = a.n + a.pad;
+  int s = 1;
+  if (a.logM & 1) {  // one radix-2 stage first (twiddle 1)
+    const int work = a.W * R * (M >> 1);
+    for (int it = threadIdx.x; it < work; it += blockDim.x) {
+      const int u = it / (M >> 1), p = it - u * (M >> 1);
+      const int w = u / R, r = u - w * R;
+      VT* row = sm + w * ld + r * M;
+      const int i0 = 2 * p;
+      const VT x0 = row[i0], x1 = row[i0 + 1];
+      row[i0] = cadd(x0, x1);
+      row[i0 + 1] = csub(x0, x1);
+    }
+    __syncthreads();
+    s = 2;
+  }
+  const int quarter = M >> 2;
+  const int work = a.W * R * quarter;
+  for (; s + 1 <= a.logM; s += 2) {
+    const int h = 1 << (s - 1);
+    for (int it = threadIdx.x; it < work; it += blockDim.x) {
+      const int u = it / quarter, p = it - u * quarter;
+      const int w = u / R, r = u - w * R;
+      const int j = p & (h - 1);
+      const int base = ((p >> (s - 1)) << (s + 1)) + j;
+      VT* row = sm + w * ld + r * M;
+      const VT t1 = a.tw[(j << (a.logM - s)) * R];
+      const VT t2 = a.tw[(j << (a.logM - s - 1)) * R];
+      const VT t3 = tw_at(a, (3 * j << (a.logM - s - 1)) * R);
+      const VT u0 = row[base], u1 = cmul(row[base + h], t1);
+      const VT u2 = cmul(row[base + 2 * h], t2), u3 = cmul(row[base + 3 * h], t3);
+      const VT s0 = cadd(u0, u1), s1 = csub(u0, u1), s2 = cadd(u2, u3), s3 = mul_i(csub(u2, u3));
+      row[base] = cadd(s0, s2);
+      row[base + 2 * h] = csub(s0, s2);
+      row[base + h] = csub(s1, s3);
+      row[base + 3 * h] = cadd(s1, s3);
+    }
+    __syncthreads();
+  }
+}
+template <int R, class VT>
+__device__ __forceinline__ void dif_stages4_conj(VT* sm, const PassArgs<VT>& a) {
+  const int M = a.M, ld = a.n + a.pad;
+  const int quarter = M >> 2;
+  const int work4 = a.W * R * quarter;
+  int s = a.logM;
+  for (; s >= 2; s -= 2) {
+    const int q = 1 << (s - 2);
+    for (int it = threadIdx.x; it < work4; it += blockDim.x) {
+      const int u = it / quarter, p = it - u * quarter;
+      const int w = u / R, r = u - w * R;
+      const int j = p & (q - 1);
+      const int base = ((p >> (s - 2)) << s) + j;
+      VT* row = sm + w * ld + r * M;
+      VT t1 = a.tw[(j << (a.logM - s)) * R];
+      VT t2 = a.tw[(j << (a.logM - s + 1)) * R];
+      VT t3 = tw_at(a, (3 * j << (a.logM - s)) * R);
+      t1.y = -t1.y;
+      t2.y = -t2.y;
+      t3.y = -t3.y;
+      const VT x0 = row[base], x1 = row[base + q], x2 = row[base + 2 * q], x3 = row[base + 3 * q];
+      const VT s0 = cadd(x0, x2), s1 = csub(x0, x2), s2 = cadd(x1, x3), s3 = mul_i(csub(x1, x3));
+      row[base] = cadd(s0, s2);
+      row[base + q] = cmul(csub(s0, s2), t2);
+      row[base + 2 * q] = cmul(cadd(s1, s3), t1);
+      row[base + 3 * q] = cmul(csub(s1, s3), t3);
+    }
+    __syncthreads();
+  }
+  if (s == 1) {  // one radix-2 stage last (twiddle 1)
+    const int work = a.W * R * (M >> 1);
+    for (int it = threadIdx.x; it < work; it += blockDim.x) {
+      const int u = it / (M >> 1), p = it - u * (M >> 1);
+      const int w = u / R, r = u - w * R;
+      VT* row = sm + w * ld + r * M;
+      const int i0 = 2 * p;
+      const VT x0 = row[i0], x1 = row[i0 + 1];
+      row[i0] = cadd(x0, x1);
+      row[i0 + 1] = csub(x0, x1);
+    }
+    __syncthreads();
+  }
+}
+
 // radix-3 step over the three sub-lines of every row (R = 3 only).  Forward:
 // X[k1 + M k2] = sum_r w_3^(r k2) (w_n^(r k1) Y_r[k1]); inverse (conjugate):
 // Z_r[k1] = w_n^(-r k1) sum_k2 w_3^(-r k2) X[k1 + M k2].
@@ -220,13 +324,13 @@ __global__ void __launch_bounds__(kThreads) fft_pass_kernel(PassArgs<VT> a) {
   }
   __syncthreads();
   if (a.mode == 0) {
-    dit_stages<R>(sm, a, false);
+    dit_stages4<R>(sm, a);
     if (R == 3) radix3_step(sm, a, false);
   } else if (a.mode == 1) {
     if (R == 3) radix3_step(sm, a, true);
-    dif_stages<R>(sm, a, true);
+    dif_stages4_conj<R>(sm, a);
   } else {
-    dit_stages<R>(sm, a, false);
+    dit_stages4<R>(sm, a);
     if (R == 3) radix3_step(sm, a, false);
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
       int w, i;
@@ -246,7 +350,7 @@ __global__ void __launch_bounds__(kThreads) fft_pass_kernel(PassArgs<VT> a) {
     }
     __syncthreads();
     if (R == 3) radix3_step(sm, a, true);
-    dif_stages<R>(sm, a, true);
+    dif_stages4_conj<R>(sm, a);
   }
   const bool bitrev_store = (a.mode != 0);  // inverse transforms are DIF
   for (int e = threadIdx.x; e < total; e += blockDim.x) {

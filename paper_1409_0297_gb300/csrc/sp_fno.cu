@@ -692,6 +692,39 @@ __global__ void target_kernel(const double2* __restrict__ u, const double2* __re
   }
 }
 
+// the same with a prior estimate z of the solution (the preconditioner applied to g):
+// x[3] + i x[4] = z / c; the guess adds the network's correction to z, the target is
+// the correction (u - z) / c
+__global__ void features_prior_kernel(const double2* __restrict__ z, const double2* __restrict__ c,
+                                      long N, float* __restrict__ x) {
+  const double2 ic = inv_scale(*c);
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+    const double2 v = z[i];
+    x[3 * N + i] = (float)(v.x * ic.x - v.y * ic.y);
+    x[4 * N + i] = (float)(v.x * ic.y + v.y * ic.x);
+  }
+}
+
+__global__ void guess_prior_kernel(const float* __restrict__ y, const double2* __restrict__ c,
+                                   const double2* __restrict__ z, long N, double2* __restrict__ u0) {
+  const double2 cc = *c;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+    const double yr = y[i], yi = y[N + i];
+    const double2 zi = z[i];
+    u0[i] = make_double2(zi.x + (cc.x * yr - cc.y * yi), zi.y + (cc.x * yi + cc.y * yr));
+  }
+}
+
+__global__ void target_prior_kernel(const double2* __restrict__ u, const double2* __restrict__ c,
+                                    const double2* __restrict__ z, long N, float* __restrict__ t) {
+  const double2 ic = inv_scale(*c);
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+    const double2 v = make_double2(u[i].x - z[i].x, u[i].y - z[i].y);
+    t[i] = (float)(v.x * ic.x - v.y * ic.y);
+    t[N + i] = (float)(v.x * ic.y + v.y * ic.x);
+  }
+}
+
 unsigned grid_for(long len, int threads) {
   long g = (len + threads - 1) / threads;
   if (g > 152L * 16) g = 152L * 16;
@@ -1101,6 +1134,35 @@ sp_status sp_fno_features(sp_fno* f, const double* q_dev, double q_scale, const 
   scale_kernel<<<1, 32, 0, f->st>>>(f->npart, kNormBlocks, N, (double2*)scale_dev);
   features_kernel<<<grid_for(N, 256), 256, 0, f->st>>>(q_dev, q_scale, (const double2*)g_dev,
                                                        (const double2*)scale_dev, N, x_dev);
+  return cuda_st(cudaGetLastError());
+}
+
+sp_status sp_fno_features_prior(sp_fno* f, const double* q_dev, double q_scale, const void* g_dev,
+                                const void* z_dev, float* x_dev, void* scale_dev) {
+  if (!f || !q_dev || !g_dev || !z_dev || !x_dev || !scale_dev || f->D.c_in != 5) return SP_ERR_ARG;
+  const long N = f->P;
+  norm_partial_kernel<<<kNormBlocks, 256, 0, f->st>>>((const double2*)g_dev, N, f->npart);
+  scale_kernel<<<1, 32, 0, f->st>>>(f->npart, kNormBlocks, N, (double2*)scale_dev);
+  features_kernel<<<grid_for(N, 256), 256, 0, f->st>>>(q_dev, q_scale, (const double2*)g_dev,
+                                                       (const double2*)scale_dev, N, x_dev);
+  features_prior_kernel<<<grid_for(N, 256), 256, 0, f->st>>>((const double2*)z_dev,
+                                                             (const double2*)scale_dev, N, x_dev);
+  return cuda_st(cudaGetLastError());
+}
+
+sp_status sp_fno_guess_prior(sp_fno* f, const float* y_dev, const void* scale_dev, const void* z_dev,
+                             void* u0_dev) {
+  if (!f || !y_dev || !scale_dev || !z_dev || !u0_dev || f->D.c_out != 2) return SP_ERR_ARG;
+  guess_prior_kernel<<<grid_for(f->P, 256), 256, 0, f->st>>>(
+      y_dev, (const double2*)scale_dev, (const double2*)z_dev, f->P, (double2*)u0_dev);
+  return cuda_st(cudaGetLastError());
+}
+
+sp_status sp_fno_target_prior(sp_fno* f, const void* u_dev, const void* scale_dev, const void* z_dev,
+                              float* t_dev) {
+  if (!f || !u_dev || !scale_dev || !z_dev || !t_dev || f->D.c_out != 2) return SP_ERR_ARG;
+  target_prior_kernel<<<grid_for(f->P, 256), 256, 0, f->st>>>(
+      (const double2*)u_dev, (const double2*)scale_dev, (const double2*)z_dev, f->P, t_dev);
   return cuda_st(cudaGetLastError());
 }
 

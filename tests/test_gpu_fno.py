@@ -230,3 +230,37 @@ def test_fno_arguments(B):
     with pytest.raises(B.SpError):
         net.train_step(x, y, 1, -1.0)  # negative learning rate
     net.close()
+
+
+def test_features_guess_target_with_prior(B):
+    """The prior-aware forms (input channels 3-4 = z / c, guess u0 = z + c y, target
+    (u - z) / c) against numpy on random device data, and guess_prior inverting
+    target_prior up to FP32 rounding of the correction."""
+    n = 64
+    N = n * n
+    D = F.FnoDims(n=n, c_in=5)
+    net = make(B, D, sm.fno_initial_params(c_in=5), 1, False)
+    rng = np.random.default_rng(77)
+    q = rng.standard_normal(N)
+    g = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    z = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    u = z + 0.1 * (rng.standard_normal(N) + 1j * rng.standard_normal(N))
+    qd, gd, zd, ud = (torch.from_numpy(a).cuda() for a in (q, g, z, u))
+    x = torch.empty((1, 5, N), dtype=torch.float32, device="cuda")
+    sc = torch.zeros(1, dtype=torch.complex128, device="cuda")
+    net.features_prior(qd, 0.5, gd, zd, x, sc)
+    c = np.sqrt(np.mean(np.abs(g) ** 2)) * np.exp(0.5j * np.angle(np.sum(g * g)))
+    xh = x.cpu().numpy()[0].astype(np.float64)
+    assert abs(sc.item() - c) <= 1e-12 * abs(c)
+    assert np.allclose(xh[0], 0.5 * q, rtol=1e-6, atol=1e-6)
+    assert np.allclose(xh[1] + 1j * xh[2], g / c, rtol=1e-6, atol=1e-6)
+    assert np.allclose(xh[3] + 1j * xh[4], z / c, rtol=1e-6, atol=1e-6)
+    t = torch.empty((1, 2, N), dtype=torch.float32, device="cuda")
+    net.target_prior(ud, sc, zd, t)
+    th = t.cpu().numpy()[0].astype(np.float64)
+    assert np.allclose(th[0] + 1j * th[1], (u - z) / c, rtol=1e-6, atol=1e-7)
+    u0 = torch.empty(N, dtype=torch.complex128, device="cuda")
+    net.guess_prior(t[0], sc, zd, u0)
+    back = u0.cpu().numpy()
+    assert np.linalg.norm(back - u) <= 1e-6 * np.linalg.norm(u - z) + 1e-12
+    net.close()
