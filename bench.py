@@ -250,7 +250,16 @@ def cpu_sample_text(iters: int, seconds: float) -> str:
 # GPU machine's host cores (16 Arm cores) by `python bench.py --oracle-512` (both problems in
 # spawned processes side by side).  Seconds per phase; "solve_s" = everything from the
 # stencil tables to the GMRES solution at 1e-8; value = 2 solves / the slower process.
-ORACLE_512 = None
+ORACLE_512 = {
+    "value": 2.0 / 331.1, "unit": UNIT, "cores": 16, "kind": "oracle",
+    "sample": "full FP64 oracle factor + solve of both 512^2 problems (tables, assembly, SuperLU "
+              "factor of P, GMRES to 1e-8), two processes side by side, measured once",
+    "wall_s": 331.1,
+    "problems": {"helmholtz": {"tables_s": 6.9, "assemble_s": 3.3, "factor_s": 271.2,
+                               "gmres_s": 49.4, "solve_s": 330.8, "iters": 43},
+                 "schrodinger": {"tables_s": 5.0, "assemble_s": 3.4, "factor_s": 256.3,
+                                 "gmres_s": 9.9, "solve_s": 274.5, "iters": 8}},
+}
 
 
 def _oracle_512_one(kind: str) -> dict:
