@@ -133,6 +133,11 @@ typedef struct {
                         rounds per panel, but three 32-step eliminations in sequence; 3D
                         128^3 TF32 panels 1.22 s against 1.03 s).  FP64 grid panels always
                         pivot column by column. */
+  int launch_overlap; /* 1: the stencil and sweep kernels of the preconditioner application
+                        are launched with programmatic dependent launch (a kernel may start
+                        while the previous one's last CTAs drain; it waits for that kernel's
+                        results before reading them); 0 (default): ordinary stream order.
+                        The same kernels and results either way. */
 } sp_opts;
 
 typedef struct {

@@ -167,7 +167,8 @@ double perturb_shift(int d, int n, double s) {
 }
 
 sp_status apply_direct(sp_ctx* c, const double2* r, double2* z, cudaStream_t st) {
-  SP_CK(q_apply(c->prec, c->d, c->n, c->nl, c->qtypes, c->Tcat, c->Tcat32, r, c->rhsQ, st));
+  SP_CK(q_apply(c->prec, c->d, c->n, c->nl, c->qtypes, c->Tcat, c->Tcat32, r, c->rhsQ, st, 1,
+                c->opts.launch_overlap != 0));
   for (int l = 0; l <= c->L; ++l)
     SP_CK(forward_level(c->prec, c->d, c->lv[l], l ? &c->lv[l - 1] : nullptr, c->rhsQ,
                         c->gemv_part, st));
@@ -308,6 +309,7 @@ void sp_default_opts(sp_opts* o) {
   o->wait_limit_ns = 0;
   o->sweeps = 0;
   o->panel_pivoting = 0;
+  o->launch_overlap = 0;
 }
 
 const char* sp_status_str(sp_status st) {
@@ -523,6 +525,7 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   if (c->opts.wait_limit_ns < 0 || c->opts.wait_limit_ns > 60000000000LL) return SP_ERR_ARG;
   if (c->opts.sweeps < 0 || c->opts.sweeps > 2) return SP_ERR_ARG;
   if (c->opts.panel_pivoting != 0 && c->opts.panel_pivoting != 1) return SP_ERR_ARG;
+  if (c->opts.launch_overlap != 0 && c->opts.launch_overlap != 1) return SP_ERR_ARG;
   const size_t RH = (size_t)c->opts.max_rhs;
   c->d = d;
   c->n = n;
@@ -655,6 +658,7 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
     // 1.95 -> 1.51 s per solve for +0.1 s of inversion), 512 elsewhere (in 2D the
     // larger inverses cost more than the launches they save)
     D.ib = c->opts.inv_block > 0 ? c->opts.inv_block : (S.k >= 32768 ? 2048 : kInvBlockSize);
+    D.pdl = c->opts.launch_overlap;
     if (D.inv && c->opts.sweeps != 1) {
       int C = 0, NT = 0;
       if (sweep_fused_config(prec, S.nf, S.m, S.k, num_sms, max_cluster, c->opts.sweeps == 2, &C,
@@ -1060,7 +1064,8 @@ static sp_status solve_mixed(sp_ctx* c, const double2* f, const double2* u0, dou
 // z = P^{-1} Q r for nv stacked vectors (direct launches; each vector's result
 // equals apply_direct's for it)
 static sp_status apply_block(sp_ctx* c, int nv, const double2* r, double2* z, cudaStream_t st) {
-  SP_CK(q_apply(c->prec, c->d, c->n, c->nl, c->qtypes, c->Tcat, c->Tcat32, r, c->rhsQ, st, nv));
+  SP_CK(q_apply(c->prec, c->d, c->n, c->nl, c->qtypes, c->Tcat, c->Tcat32, r, c->rhsQ, st, nv,
+                c->opts.launch_overlap != 0));
   for (int l = 0; l <= c->L; ++l)
     SP_CK(forward_level(c->prec, c->d, c->lv[l], l ? &c->lv[l - 1] : nullptr, c->rhsQ,
                         c->gemv_part, st, nv, c->N));

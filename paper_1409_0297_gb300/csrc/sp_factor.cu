@@ -102,22 +102,21 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(T* fronts, int m, int k, 
     P[e] = A[(j0 + r) + (long)(j0 + c) * m];
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  // two barriers per pivot: each thread carries the best candidate of its own rows
-  // for the next column out of the update (ties to the smaller row everywhere)
-  double best = -1.0;
-  int bi = 0;
-  for (int r = threadIdx.x; r < kl; r += blockDim.x) {
-    const double v = fabs((double)P[r]);
-    if (v > best) {
-      best = v;
-      bi = r;
-    }
-  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int jj = 0; jj < jb; ++jj) {
+    T* pc = P + (long)jj * rows;
+    double best = -1.0;
+    int bi = jj;
+    for (int r = jj + threadIdx.x; r < kl; r += blockDim.x) {
+      double v = fabs((double)pc[r]);
+      if (v > best) {
+        best = v;
+        bi = r;
+      }
+    }
     for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_down_sync(0xffffffffu, best, o);
-      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      double ov = __shfl_down_sync(0xffffffffu, best, o);
+      int oi = __shfl_down_sync(0xffffffffu, bi, o);
       if (ov > best || (ov == best && oi < bi)) {
         best = ov;
         bi = oi;
@@ -128,46 +127,37 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(T* fronts, int m, int k, 
       wi[warp] = bi;
     }
     __syncthreads();
-    double b0 = wv[0];
-    int p = wi[0];
-    for (int w = 1; w < nw; ++w)
-      if (wv[w] > b0 || (wv[w] == b0 && wi[w] < p)) {
-        b0 = wv[w];
-        p = wi[w];
-      }
-    if (b0 < 0.0) p = jj;  // no candidate row (cannot happen inside k)
     if (threadIdx.x == 0) {
-      spiv[jj] = p;
-      piv[(long)blockIdx.x * k + j0 + jj] = j0 + p;
+      double b0 = wv[0];
+      int i0 = wi[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+        if (wv[w] > b0 || (wv[w] == b0 && wi[w] < i0)) {
+          b0 = wv[w];
+          i0 = wi[w];
+        }
+      spiv[jj] = i0;
+      piv[(long)blockIdx.x * k + j0 + jj] = j0 + i0;
       if (!(b0 > thresh)) atomicOr(status, 1);
     }
+    __syncthreads();
+    const int p = spiv[jj];
     if (p != jj)
       for (int c = threadIdx.x; c < jb; c += blockDim.x) {
-        const T t = P[jj + (long)c * rows];
+        T t = P[jj + (long)c * rows];
         P[jj + (long)c * rows] = P[p + (long)c * rows];
         P[p + (long)c * rows] = t;
       }
     __syncthreads();
-    T* pc = P + (long)jj * rows;
     T pv = pc[jj];
     if (!(fabs((double)pv) > 0.0)) pv = (T)(thresh > 0 ? thresh : 1e-30);
     const T inv = (T)1 / pv;
-    best = -1.0;
-    bi = 0;
     for (int r = jj + 1 + threadIdx.x; r < rows; r += blockDim.x) {
-      const T l = pc[r] * inv;
+      T l = pc[r] * inv;
       pc[r] = l;
       for (int c = jj + 1; c < jb; ++c) P[r + (long)c * rows] -= l * P[jj + (long)c * rows];
-      if (jj + 1 < jb && r < kl) {
-        const double v = fabs((double)P[r + (long)(jj + 1) * rows]);
-        if (v > best) {
-          best = v;
-          bi = r;
-        }
-      }
     }
+    __syncthreads();
   }
-  __syncthreads();
   for (long e = threadIdx.x; e < (long)rows * jb; e += blockDim.x) {
     int r = (int)(e % rows), c = (int)(e / rows);
     A[(j0 + r) + (long)(j0 + c) * m] = P[e];

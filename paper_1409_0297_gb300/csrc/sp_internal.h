@@ -81,6 +81,7 @@ struct DevLevel {
   // fused sweeps (inv levels whose work vectors fit in shared memory): CTAs per
   // front (a thread-block cluster; 0 = the per-block launch chain) and threads per CTA
   int fused_c = 0, fused_nt = 0;
+  int pdl = 0;  // launch the level's sweep kernels with programmatic dependent launch
 };
 
 // ---------------------------------------------------------------- FFT (sp_fft.cu)
@@ -180,7 +181,7 @@ struct QTypeDev {
 // nf (m - k)) vector-major; each vector's result equals its single-vector result.
 cudaError_t q_apply(int prec, int d, int n, int nl, const std::vector<QTypeDev>& types,
                     const double* Tcat, const float* Tcat32, const double2* r, void* y,
-                    cudaStream_t st, int nv = 1);
+                    cudaStream_t st, int nv = 1, bool pdl = false);
 // part: sweep_partial_bytes(nv) of work for the split row products (shared by levels)
 cudaError_t forward_level(int prec, int d, DevLevel& L, const DevLevel* child, const void* rhsQ,
                           void* part, cudaStream_t st, int nv = 1, long N = 0);

@@ -57,6 +57,32 @@ __device__ __forceinline__ void axpy(VT& acc, T a, VT x) {  // acc += a * x
 
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while the previous kernel's last CTAs drain; it waits
+// here, before touching anything that kernel wrote (a no-op for ordinary launches).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// kernel<<<g, b, smem, st>>>(args) with programmatic stream serialisation when pdl
+template <class... KArgs, class... Args>
+void launch_k(bool pdl, void (*kern)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t st,
+              Args... args) {
+  if (!pdl) {
+    kern<<<g, b, smem, st>>>(args...);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // y[S instance] = self * r[S instance] - T_t r[B instance], B = beta (self = 1, set
 // stencils) or gamma (self = 0, per-point stencils); one CTA per instance of type t
 // (and per stacked vector, blockIdx.y, vectors N apart).
@@ -65,6 +91,7 @@ __global__ void qapply_kernel(int d, int n, int nl, int nS, int nB, int self,
                               const int* __restrict__ Soff, const int* __restrict__ Boff,
                               const T* __restrict__ Tt, const double2* __restrict__ r, VT* y,
                               long N) {
+  pdl_wait();
   extern __shared__ unsigned char smraw[];
   VT* rb = reinterpret_cast<VT*>(smraw);
   r += blockIdx.y * N;
@@ -134,6 +161,7 @@ __global__ void __launch_bounds__(256) forward_kernel(
     int d, const T* __restrict__ fronts, int m, int k, int nb1, const int* __restrict__ gidx,
     const int* __restrict__ perm, const VT* __restrict__ rhsQ, const VT* __restrict__ cupd, int mc,
     int kc, const int* __restrict__ ea_map, VT* upd, VT* yout, long N, long custr) {
+  pdl_wait();
   extern __shared__ unsigned char smraw[];
   VT* b = reinterpret_cast<VT*>(smraw);  // m
   VT* b1 = b + m;                         // k (permuted eliminated part)
@@ -197,6 +225,7 @@ __global__ void __launch_bounds__(256) backward_kernel(const T* __restrict__ fro
                                                         const int* __restrict__ gidx,
                                                         const VT* __restrict__ yin, double2* x,
                                                         long N) {
+  pdl_wait();
   extern __shared__ unsigned char smraw[];
   VT* xb = reinterpret_cast<VT*>(smraw);  // m: x1 then x2
   yin += (long)blockIdx.y * gridDim.x * k;
@@ -258,6 +287,7 @@ __global__ void __launch_bounds__(256) inv_gather_kernel(
     int d, int m, int k, int nb1, const int* __restrict__ gidx, const int* __restrict__ perm,
     const VT* __restrict__ rhsQ, const VT* __restrict__ cupd, int mc, int kc,
     const int* __restrict__ ea_map, VT* tmp, long N, long custr) {
+  pdl_wait();
   extern __shared__ unsigned char smraw[];
   VT* b = reinterpret_cast<VT*>(smraw);
   const int f = blockIdx.x;
@@ -279,6 +309,7 @@ __global__ void __launch_bounds__(1024) inv_gather_global_kernel(
     int d, int m, int k, int nb1, const int* __restrict__ gidx, const int* __restrict__ perm,
     const VT* __restrict__ rhsQ, const VT* __restrict__ cupd, int mc, int kc,
     const int* __restrict__ ea_map, VT* tmp, VT* ybuf, long N, long custr) {
+  pdl_wait();
   const int f = blockIdx.x;
   rhsQ += blockIdx.y * N;
   if (cupd) cupd += blockIdx.y * custr;
@@ -328,6 +359,7 @@ __global__ void __launch_bounds__(256) inv_gemv_kernel(int mode, const T* __rest
                                                         int m, int k, int j0, int j1,
                                                         const int* __restrict__ gidx, VT* tmp,
                                                         VT* y, double2* x, long N) {
+  pdl_wait();
   extern __shared__ unsigned char smraw[];
   VT* v = reinterpret_cast<VT*>(smraw);  // tmp[j0 .. j1)
   {  // stacked vector blockIdx.z
@@ -413,6 +445,7 @@ __global__ void __launch_bounds__(256) gemv_kernel(GemvArgs ga, const T* __restr
                                                     int m, int k, const int* __restrict__ gidx,
                                                     VT* tmp, VT* y, VT* upd, const double2* x,
                                                     int nsplit, VT* part, int nv, long N) {
+  pdl_wait();
   constexpr int CH = 1024 / NV;  // columns of one staged chunk
   __shared__ VT vs[CH * NV];     // vs[j NV + v]
   const int f = blockIdx.z, sp = blockIdx.y, nf = gridDim.z;
@@ -470,6 +503,7 @@ __global__ void __launch_bounds__(256) gemv_kernel(GemvArgs ga, const T* __restr
 template <class VT>
 __global__ void gemv_finish_kernel(GemvArgs ga, int m, int k, VT* tmp, VT* y, VT* upd, int nsplit,
                                    const VT* __restrict__ part) {
+  pdl_wait();
   const int f = blockIdx.y, nf = gridDim.y, v = blockIdx.z, nv = gridDim.z;
   const int r = ga.rlo + blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= ga.rhi) return;
@@ -485,7 +519,7 @@ __global__ void gemv_finish_kernel(GemvArgs ga, int m, int k, VT* tmp, VT* y, VT
 
 template <class VT>
 cudaError_t q_apply_t(int d, int n, int nl, const std::vector<QTypeDev>& types, const void* Tt,
-                      const double2* r, VT* y, int nv, long N, cudaStream_t st) {
+                      const double2* r, VT* y, int nv, long N, cudaStream_t st, bool pdl) {
   using T = typename Scalar<VT>::T;
   long ninst = 1;
   for (int a = 0; a < d; ++a) ninst *= nl;
@@ -494,7 +528,7 @@ cudaError_t q_apply_t(int d, int n, int nl, const std::vector<QTypeDev>& types, 
   for (const auto& ty : types) {
     size_t smem = sizeof(VT) * (ty.na > 0 ? ty.na : 1);
     dim3 g((unsigned)ninst, nv);
-    qapply_kernel<VT, T><<<g, 128, smem, st>>>(d, n, nl, ty.nS, ty.na, ty.self, ty.S, ty.A,
+    launch_k(pdl, qapply_kernel<VT, T>, dim3(g), dim3(128), smem, st, d, n, nl, ty.nS, ty.na, ty.self, ty.S, ty.A,
                                                (const T*)Tt + ty.t_off, r, y, N);
     bytes += (double)ninst * nv * ty.nS * (sizeof(double2) + sizeof(VT)) +
              sizeof(T) * ty.nS * ty.na;
@@ -540,15 +574,15 @@ int gemv(const GemvArgs& ga, DevLevel& L, const double2* x, void* part, int nv, 
   if (!part) ns = 1;
   dim3 g((rows + 255) / 256, ns, L.nf);
   if (nv == 1)
-    gemv_kernel<VT, T, 1><<<g, 256, 0, st>>>(ga, (const T*)L.front, L.m, L.k, L.gidx, (VT*)L.tmp,
+    launch_k(L.pdl != 0, gemv_kernel<VT, T, 1>, dim3(g), dim3(256), 0, st, ga, (const T*)L.front, L.m, L.k, L.gidx, (VT*)L.tmp,
                                              (VT*)L.y, (VT*)L.upd, x, ns, (VT*)part, 1, N);
   else
-    gemv_kernel<VT, T, kMaxVec><<<g, 256, 0, st>>>(ga, (const T*)L.front, L.m, L.k, L.gidx,
+    launch_k(L.pdl != 0, gemv_kernel<VT, T, kMaxVec>, dim3(g), dim3(256), 0, st, ga, (const T*)L.front, L.m, L.k, L.gidx,
                                                    (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x, ns,
                                                    (VT*)part, nv, N);
   if (ns == 1) return 1;
   dim3 gf((rows + 255) / 256, L.nf, nv);
-  gemv_finish_kernel<VT><<<gf, 256, 0, st>>>(ga, L.m, L.k, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, ns,
+  launch_k(L.pdl != 0, gemv_finish_kernel<VT>, dim3(gf), dim3(256), 0, st, ga, L.m, L.k, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, ns,
                                              (const VT*)part);
   return 2;
 }
@@ -562,11 +596,11 @@ void inv_gemv(int mode, DevLevel& L, int j0, int j1, int rlo, int rhi, size_t sm
   const int rows = rhi - rlo;
   if ((long)((rows + 15) / 16) * L.nf >= 152) {
     dim3 g((rows + 15) / 16, L.nf, nv);
-    inv_gemv_kernel<VT, T, 16><<<g, 256, smem, st>>>(mode, (const T*)L.front, L.m, L.k, j0, j1,
+    launch_k(L.pdl != 0, inv_gemv_kernel<VT, T, 16>, dim3(g), dim3(256), smem, st, mode, (const T*)L.front, L.m, L.k, j0, j1,
                                                      L.gidx, (VT*)L.tmp, (VT*)L.y, x, N);
   } else {
     dim3 g((rows + 3) / 4, L.nf, nv);
-    inv_gemv_kernel<VT, T, 4><<<g, 256, smem, st>>>(mode, (const T*)L.front, L.m, L.k, j0, j1,
+    launch_k(L.pdl != 0, inv_gemv_kernel<VT, T, 4>, dim3(g), dim3(256), smem, st, mode, (const T*)L.front, L.m, L.k, j0, j1,
                                                     L.gidx, (VT*)L.tmp, (VT*)L.y, x, N);
   }
 }
@@ -595,17 +629,17 @@ cudaError_t forward_t(int d, DevLevel& L, const DevLevel* child, const void* rhs
     if (e != cudaSuccess) return e;
   } else if (!L.inv) {
     dim3 g(L.nf, nv);
-    forward_kernel<VT, T><<<g, 256, sweep_smem(L.m, L.k, sizeof(VT)), st>>>(
+    launch_k(L.pdl != 0, forward_kernel<VT, T>, dim3(g), dim3(256), sweep_smem(L.m, L.k, sizeof(VT)), st,
         d, (const T*)L.front, L.m, L.k, L.nb1, L.gidx, L.perm, (const VT*)rhsQ, cup, L.mc, L.kc,
         L.ea_map, (VT*)L.upd, (VT*)L.y, N, custr);
   } else {
     dim3 g(L.nf, nv);
     if (sizeof(VT) * (size_t)L.m <= kVecSmem)
-      inv_gather_kernel<VT><<<g, 256, sizeof(VT) * L.m, st>>>(
+      launch_k(L.pdl != 0, inv_gather_kernel<VT>, dim3(g), dim3(256), sizeof(VT) * L.m, st, 
           d, L.m, L.k, L.nb1, L.gidx, L.perm, (const VT*)rhsQ, cup, L.mc, L.kc, L.ea_map,
           (VT*)L.tmp, N, custr);
     else
-      inv_gather_global_kernel<VT><<<g, 1024, 0, st>>>(d, L.m, L.k, L.nb1, L.gidx, L.perm,
+      launch_k(L.pdl != 0, inv_gather_global_kernel<VT>, dim3(g), dim3(1024), 0, st, d, L.m, L.k, L.nb1, L.gidx, L.perm,
                                                         (const VT*)rhsQ, cup, L.mc, L.kc,
                                                         L.ea_map, (VT*)L.tmp, (VT*)L.y, N,
                                                         custr);
@@ -639,7 +673,7 @@ cudaError_t backward_t(DevLevel& L, double2* x, void* part, int nv, long N, cuda
     if (e != cudaSuccess) return e;
   } else if (!L.inv) {
     dim3 g(L.nf, nv);
-    backward_kernel<VT, T><<<g, 256, sizeof(VT) * (size_t)L.m, st>>>(
+    launch_k(L.pdl != 0, backward_kernel<VT, T>, dim3(g), dim3(256), sizeof(VT) * (size_t)L.m, st, 
         (const T*)L.front, L.m, L.k, L.gidx, (const VT*)L.y, x, N);
   } else {
     launches = 0;
@@ -829,6 +863,7 @@ size_t fused_smem(int m, int k) {
 // diagonal), t_r -= L[r, J] y_J for the rows below; out: y (k), upd = t[k, m).
 template <class VT, class T, int NT, int NV>
 __global__ void __launch_bounds__(NT) fused_forward_kernel(FusedArgs a) {
+  pdl_wait();
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int q = (int)cl.block_rank();
@@ -894,6 +929,7 @@ __global__ void __launch_bounds__(NT) fused_forward_kernel(FusedArgs a) {
 // to the global solution.  tv holds x (NV x m), yv the right-hand sides t (NV x k).
 template <class VT, class T, int NT, int NV>
 __global__ void __launch_bounds__(NT) fused_backward_kernel(FusedArgs a) {
+  pdl_wait();
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int q = (int)cl.block_rank();
@@ -1077,12 +1113,12 @@ cudaError_t fused_level(bool fwd, int d, DevLevel& L, const DevLevel* child, con
 
 cudaError_t q_apply(int prec, int d, int n, int nl, const std::vector<QTypeDev>& types,
                     const double* Tcat, const float* Tcat32, const double2* r, void* y,
-                    cudaStream_t st, int nv) {
+                    cudaStream_t st, int nv, bool pdl) {
   long N = 1;
   for (int a = 0; a < d; ++a) N *= n;
   if (prec == SP_PREC_FP32)
-    return q_apply_t<float2>(d, n, nl, types, Tcat32, r, (float2*)y, nv, N, st);
-  return q_apply_t<double2>(d, n, nl, types, Tcat, r, (double2*)y, nv, N, st);
+    return q_apply_t<float2>(d, n, nl, types, Tcat32, r, (float2*)y, nv, N, st, pdl);
+  return q_apply_t<double2>(d, n, nl, types, Tcat, r, (double2*)y, nv, N, st, pdl);
 }
 
 cudaError_t forward_level(int prec, int d, DevLevel& L, const DevLevel* child, const void* rhsQ,

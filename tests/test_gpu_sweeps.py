@@ -79,3 +79,30 @@ def test_fused_sweeps_stacked_vectors_bit_identical(prec, nrhs, sweeps):
         assert inf["iters"] == infos[i]["iters"]
         assert torch.equal(u, U[i])
     S.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+def test_launch_overlap_bit_identical(prec):
+    """Programmatic dependent launch of the stencil and sweep kernels
+    (sp_opts.launch_overlap = 1) runs the same kernels in the same order: the
+    preconditioner application and the solve are bit-identical to ordinary launches."""
+    from paper_1409_0297_gb300 import binding as B
+    w = sm.helmholtz_grf(2, 128, 8, 2 * np.pi * 16, 0.05, 4)
+    d, n, b = w["d"], w["n"], w["b"]
+    s, q = _medium(B, w)
+    N = n ** d
+    r = torch.from_numpy(sm.random_complex_vector(N, 52)).cuda()
+    f = torch.from_numpy(np.ascontiguousarray(w["f"])).cuda()
+    out = []
+    for lo in (0, 1):
+        S = B.Solver(d, n, b, s, prec=prec, launch_overlap=lo)
+        S.factor(torch.from_numpy(q).cuda())
+        z = torch.empty(N, dtype=torch.complex128, device="cuda")
+        u = torch.empty_like(z)
+        S.apply(r, z)
+        info = S.solve(f, u)
+        torch.cuda.synchronize()
+        out.append((z, u, info["iters"]))
+        S.close()
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
