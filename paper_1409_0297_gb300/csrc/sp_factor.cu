@@ -14,6 +14,9 @@
 // the FP64 form, float for the FP32 preconditioner form.
 #include <cooperative_groups.h>
 
+#include <functional>
+#include <vector>
+
 #include <algorithm>
 #include <cfloat>
 
@@ -24,6 +27,7 @@ namespace sp {
 namespace {
 
 constexpr int kNB = 32;       // panel width
+constexpr int kInnerBlock = 128;  // innermost block of the tensor-core LU (depth of its updates)
 constexpr int kTile = 64;     // Schur update tile (kTile x kTile per CTA)
 constexpr int kTcMinFront = 1024;         // smallest front blocked for the tensor cores
 constexpr int kGridPanelCTAs = 152;       // CTAs of a grid-panel launch (one per SM)
@@ -1500,7 +1504,12 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
     // other columns, the row band U12 = L11^{-1} A12 is solved in the same
     // sub-block pattern, and the trailing matrix gets one update of depth OB.
     // The updates of depth > 32 run on the tensor cores in the tensor-core forms.
+    // block sizes from the outer block down to the panels: OB, 256, 128, 32
     const int IB = std::min(OB, kTcMaxK / 2);
+    std::vector<int> bsz = {OB};
+    if (IB < OB) bsz.push_back(IB);
+    if (kInnerBlock > NB && kInnerBlock < bsz.back()) bsz.push_back(kInnerBlock);
+    bsz.push_back(NB);
     auto laswp = [&](int p0, int cnt, int a0, int a1, int b0, int b1) {
       const int ncols = std::max(0, a1 - a0) + std::max(0, b1 - b0);
       if (ncols <= 0 || cnt <= 0) return;
@@ -1510,14 +1519,16 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
                                             std::max(b0, b1));
       pt.done(0, 1, st);
     };
-    // row band [r0, r1) x [c0, m') solved with the unit lower block at [r0, r1),
-    // sub-blocks of IB rows, 32-row steps inside a sub-block
-    auto band = [&](int r0, int r1, int c0, int c1) {
-      if (c1 <= c0) return;
-      for (int B0 = r0; B0 < r1; B0 += IB) {
-        const int B1 = std::min(r1, B0 + IB);
-        for (int j0 = B0; j0 < B1; j0 += NB) {
-          const int jb = std::min(NB, B1 - j0);
+    // row band [r0, r1) x [c0, c1) solved with the unit lower block at [r0, r1): the
+    // rows split in blocks of bsz[lev] (recursively down to 32-row solve steps), each
+    // block's update of the rows below it of depth bsz[lev]
+    std::function<void(int, int, int, int, int)> band = [&](int r0, int r1, int c0, int c1,
+                                                            int lev) {
+      if (c1 <= c0 || r1 <= r0) return;
+      const int bs = bsz[lev];
+      if (bs == NB) {
+        for (int j0 = r0; j0 < r1; j0 += NB) {
+          const int jb = std::min(NB, r1 - j0);
           {
             const int ncol = c1 - c0;
             const int tb = ((long)((ncol + 255) / 256) * L.nf >= 152) ? 256 : 64;
@@ -1527,34 +1538,51 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
             pt.done((double)ncol * jb * (jb - 1) * L.nf, 1, st);
           }
           const int base = j0 + jb;
-          schur_update<T>(L, F, B1 - base, c1 - c0, jb, base + (long)j0 * m, j0 + (long)c0 * m,
+          schur_update<T>(L, F, r1 - base, c1 - c0, jb, base + (long)j0 * m, j0 + (long)c0 * m,
                           base + (long)c0 * m, W, status, st);
         }
+        return;
+      }
+      for (int B0 = r0; B0 < r1; B0 += bs) {
+        const int B1 = std::min(r1, B0 + bs);
+        band(B0, B1, c0, c1, lev + 1);
         schur_update<T>(L, F, r1 - B1, c1 - c0, B1 - B0, B1 + (long)B0 * m, B0 + (long)c0 * m,
                         B1 + (long)c0 * m, W, status, st);
       }
     };
-    for (int J0 = 0; J0 < k; J0 += OB) {
-      const int e1 = std::min(k, J0 + OB);
-      for (int J1 = J0; J1 < e1; J1 += IB) {
-        const int e2 = std::min(e1, J1 + IB);
-        for (int j0 = J1; j0 < e2; j0 += NB) {
-          const int jb = std::min(NB, e2 - j0);
-          panel_step<T>(L, F, j0, jb, J1, e2, ptol, status, W, st);
+    // LU of the columns [J, e) (rows J .. m) whose width is at most bsz[lev]: sub-blocks
+    // of bsz[lev + 1] columns factored in turn (32-column panel steps at the bottom),
+    // each followed by its interchanges on the block's other columns, the row band of
+    // the block's columns to its right and their update of depth bsz[lev + 1]
+    std::function<void(int, int, int)> block = [&](int J, int e, int lev) {
+      const int bs = bsz[lev + 1];
+      if (bs == NB) {
+        for (int j0 = J; j0 < e; j0 += NB) {
+          const int jb = std::min(NB, e - j0);
+          panel_step<T>(L, F, j0, jb, J, e, ptol, status, W, st);
           const int base = j0 + jb;
-          schur_update<T>(L, F, m - base, e2 - base, jb, base + (long)j0 * m, j0 + (long)base * m,
+          schur_update<T>(L, F, m - base, e - base, jb, base + (long)j0 * m, j0 + (long)base * m,
                           base + (long)base * m, W, status, st);
         }
-        laswp(J1, e2 - J1, J0, J1, e2, e1);
-        if (e2 < e1) {
-          band(J1, e2, e2, e1);
-          schur_update<T>(L, F, m - e2, e1 - e2, e2 - J1, e2 + (long)J1 * m, J1 + (long)e2 * m,
+        return;
+      }
+      for (int J1 = J; J1 < e; J1 += bs) {
+        const int e2 = std::min(e, J1 + bs);
+        block(J1, e2, lev + 1);
+        laswp(J1, e2 - J1, J, J1, e2, e);
+        if (e2 < e) {
+          band(J1, e2, e2, e, lev + 2);
+          schur_update<T>(L, F, m - e2, e - e2, e2 - J1, e2 + (long)J1 * m, J1 + (long)e2 * m,
                           e2 + (long)e2 * m, W, status, st);
         }
       }
+    };
+    for (int J0 = 0; J0 < k; J0 += OB) {
+      const int e1 = std::min(k, J0 + OB);
+      block(J0, e1, 0);
       laswp(J0, e1 - J0, 0, J0, e1, m);
       if (e1 < m) {
-        band(J0, e1, e1, m);
+        band(J0, e1, e1, m, 1);
         schur_update<T>(L, F, m - e1, m - e1, e1 - J0, e1 + (long)J0 * m, J0 + (long)e1 * m,
                         e1 + (long)e1 * m, W, status, st);
       }
