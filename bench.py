@@ -108,6 +108,9 @@ def parse():
     p.add_argument("--sweeps", type=int, default=0, choices=[0, 1, 2],
                    help="sweeps of the block-inverse levels (sp_opts.sweeps): 0 fused launches on "
                         "many-front levels, chains elsewhere (default); 1 chains; 2 fused everywhere")
+    p.add_argument("--device-loop", type=int, default=1, choices=[0, 1],
+                   help="sp_opts.device_loop: 1 runs each GMRES restart cycle as one CUDA "
+                        "graph (conditional while node), 0 lets the host drive each iteration")
     p.add_argument("--no-autotune", action="store_true",
                    help="2D contexts keep the built-in launch-shape heuristics instead of "
                         "tuning them at set-up (sp_opts.autotune; results are bit-identical)")
@@ -358,7 +361,8 @@ def _measure_3d_one(args, B, torch, flush, w, forms, tf32_peak, dist, world, pro
         prec = {"tf32": B.SP_PREC_TF32, "tf32x3": B.SP_PREC_TF32X3}[name]
         t0 = time.perf_counter()
         S = B.Solver(d, n, b, s, prec=prec, device=int(os.environ.get("LOCAL_RANK", "0")),
-                     setup_route=args.setup_route_3d, sweeps=args.sweeps)
+                     setup_route=args.setup_route_3d, sweeps=args.sweeps,
+                     device_loop=args.device_loop)
         setup_s = time.perf_counter() - t0
         for _ in range(warm):
             S.factor(qd)
@@ -468,6 +472,7 @@ def measure_batch(args, B, torch, dist, world):
             s, q = B.sp_medium_schrodinger(2, p["n"], p["ell"], p["E"], p["V"])
             scale = p["ell"] ** 2
         S = B.Solver(2, p["n"], p["b"], s, prec=prec, restart=64, device=local, sweeps=args.sweeps,
+                     device_loop=args.device_loop,
                      stream=streams[i].cuda_stream, max_rhs=len(p["rhs"]) if batched else 1,
                      host_threads=max(1, (os.cpu_count() or 1) // nw))
         return S, q, [np.ascontiguousarray(f * scale) for f in p["rhs"]]
@@ -592,7 +597,7 @@ def measure_learned(args, B, torch, dist, world):
     V0 = sm.lattice_wells_potential_2d(n, ell, 5000)
     s, _ = B.sp_medium_schrodinger(2, n, ell, E, V0)
     S = B.Solver(2, n, b, s, prec=B.SP_PREC_FP64, restart=200, device=local, max_rhs=nrhs,
-                 sweeps=args.sweeps)
+                 sweeps=args.sweeps, device_loop=args.device_loop)
     cin = 5
     net = B.Fno(n, sm.fno_initial_params(c_in=cin, seed=4000), c_in=cin, batch_max=16)
     ntr = nm * nrhs
@@ -873,6 +878,7 @@ def run_ours(args):
         out = []
         for i, p in enumerate(probs):
             S = B.Solver(p["d"], p["n"], p["b"], p["s"], prec=prec, device=local, sweeps=args.sweeps,
+                         device_loop=args.device_loop,
                          autotune=not args.no_autotune,
                          stream=pair_streams[i].cuda_stream if pair_streams else 0)
             out.append(dict(S=S, q=torch.from_numpy(p["q"]).cuda(),
@@ -906,7 +912,7 @@ def run_ours(args):
         w = sm.helmholtz_grf_3d(n, 8, 0)
         s3, q3 = B.sp_medium_helmholtz(3, n, w["omega"], w["c"])
         S = B.Solver(3, n, 8, s3, prec=form_prec[args.profile_step], device=local,
-                     sweeps=args.sweeps)
+                     sweeps=args.sweeps, device_loop=args.device_loop)
         u = torch.empty(n ** 3, dtype=torch.complex128, device="cuda")
         q3d = torch.from_numpy(q3).cuda()
         f3d = torch.from_numpy(np.ascontiguousarray(w["f"])).cuda()

@@ -138,6 +138,16 @@ typedef struct {
                         while the previous one's last CTAs drain; it waits for that kernel's
                         results before reading them); 0 (default): ordinary stream order.
                         The same kernels and results either way. */
+  int device_loop;   /* 1 (default): sp_solve runs each GMRES restart cycle as one CUDA graph whose
+                        Arnoldi steps repeat under a conditional (while) graph node: the
+                        stopping test runs on the device and the host waits once per
+                        cycle instead of once per iteration (Section 2.2's GMRES loop;
+                        the same kernels, order and results as 0).  The graph is
+                        captured on the first such solve (again after sp_factor with a
+                        new medium pointer); a failed capture returns SP_ERR_CUDA.
+                        Ignored by SP_PREC_MIXED, sp_solve_many and while sp_profile is
+                        on.  0: the host drives every iteration (reads the estimate
+                        after each step).  Default 1. */
 } sp_opts;
 
 typedef struct {

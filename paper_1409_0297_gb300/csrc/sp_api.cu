@@ -114,6 +114,14 @@ struct sp_ctx {
   double2* blk_w = nullptr;    // max_rhs N: operator outputs of sp_solve_many
   cudaGraphExec_t g_block[9] = {};  // block applications of nv = 2 ... max_rhs stacked
   bool g_block_tried[9] = {};       // vectors, captured on first use
+  // device-resident restart cycle (opts.device_loop): its graph, the medium pointer it
+  // was captured with, its state (a LoopHead, then maxit doubles of estimates) on the
+  // device and a pinned copy
+  cudaGraphExec_t g_loop = nullptr;
+  const double* g_loop_q = nullptr;
+  LoopHead* loop = nullptr;
+  LoopHead* host_loop = nullptr;
+  size_t loop_bytes = 0;
   double factor_entries = 0, factor_flops = 0, apply_bytes = 0;
 };
 
@@ -279,6 +287,92 @@ void capture_graph(sp_ctx* c, cudaGraphExec_t* out, Fn fn) {
   cudaGetLastError();
 }
 
+// The restart cycle of sp_solve as one CUDA graph (opts.device_loop): V_0 = r / |r|,
+// then a conditional while node whose body is one Arnoldi step (the column index on
+// the device; the step's last kernels run the stopping test and end the loop), then
+// u += Z y, the true residual r = g - A u and a copy of the cycle's state to the
+// host.  Works on the context's own vectors (u in ubuf) and its medium pointer c->q,
+// so it is captured again when sp_factor is given another medium pointer.
+sp_status build_loop_graph(sp_ctx* c) {
+  if (c->g_loop) {
+    cudaGraphExecDestroy(c->g_loop);
+    c->g_loop = nullptr;
+  }
+  if (!c->cap) return SP_ERR_CUDA;
+  cudaStream_t s = c->cap;
+  const long N = c->N;
+  const int mv = c->maxv;
+  double* hist = reinterpret_cast<double*>(c->loop + 1);
+  cudaGraph_t g = nullptr;
+  SP_CK(cudaGraphCreate(&g, 0));
+  struct Owner {
+    cudaGraph_t g;
+    ~Owner() { cudaGraphDestroy(g); }
+  } owner{g};
+  cudaGraphConditionalHandle cond = 0;
+  SP_CK(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+  cudaGraph_t body = nullptr;
+  auto outer = [&]() -> sp_status {
+    SP_CK(kr_start(c->r, N, c->nrm + 3, c->V, c->gam, mv + 1, s));
+    SP_CK(kr_loop_begin(c->loop, s));
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    SP_CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &nd));
+    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+    p.conditional.handle = cond;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t wn = nullptr;
+    SP_CK(cudaGraphAddNode(&wn, g, deps, nullptr, nd, &p));
+    body = p.conditional.phGraph_out[0];
+    SP_CK(cudaStreamUpdateCaptureDependencies(s, &wn, nullptr, 1, cudaStreamSetCaptureDependencies));
+    SP_CK(kr_update_solution_dev(c->H, mv, &c->loop->k, c->gam, c->y, c->Z, N, N, c->ubuf, s));
+    SP_CK(fft_green_apply(c->fft, c->ubuf, c->q, true, c->t, s));
+    SP_CK(kr_sub(c->g, c->t, N, c->r, s));
+    SP_CK(kr_norm(c->r, N, c->K, c->nrm + 3, s));
+    SP_CK(kr_loop_finish(c->loop, c->nrm, s));
+    SP_CK(cudaMemcpyAsync(c->host_loop, c->loop, c->loop_bytes, cudaMemcpyDeviceToHost, s));
+    return SP_OK;
+  };
+  SP_CK(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  sp_status so = outer();
+  cudaGraph_t got = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &got);
+  if (so != SP_OK) return so;
+  SP_CK(e);
+  if (!body) return SP_ERR_CUDA;
+  // the body: one Arnoldi step with j = loop->j (the host loop's kernels, in its order)
+  auto step = [&]() -> sp_status {
+    const int* jp = &c->loop->j;
+    double2* w = c->t;
+    SP_CK(kr_copy_col(c->V, N, c->app_in, 0, jp, N, s));
+    sp_status a = apply_direct(c, c->app_in, c->app_out, s);
+    if (a != SP_OK) return a;
+    SP_CK(kr_copy_col(c->app_out, 0, c->Z, N, jp, N, s));
+    SP_CK(fft_green_apply(c->fft, c->app_out, c->q, true, w, s));
+    // classical Gram-Schmidt, twice
+    SP_CK(kr_dots_dev(c->V, N, mv, jp, w, N, c->K, c->h1, s));
+    SP_CK(kr_update_dots_dev(c->V, N, mv, jp, w, N, c->h1, c->K, c->h2, s));
+    SP_CK(kr_update_dots_dev(c->V, N, mv, jp, w, N, c->h2, c->K, nullptr, s));
+    SP_CK(kr_norm(w, N, c->K, c->nrm, s));
+    SP_CK(kr_givens_dev(c->H, mv, jp, c->h1, c->h2, c->nrm, c->cs, c->sn, c->gam, c->est, s));
+    SP_CK(kr_loop_step(c->loop, hist, c->est, c->nrm + 2, c->opts.tol, c->opts.maxit,
+                       c->opts.restart, cond, s));
+    SP_CK(kr_loop_scale(w, N, c->nrm, c->V, c->loop, s));
+    return SP_OK;
+  };
+  SP_CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  sp_status sb = step();
+  got = nullptr;
+  e = cudaStreamEndCapture(s, &got);
+  if (sb != SP_OK) return sb;
+  SP_CK(e);
+  SP_CK(cudaGraphInstantiate(&c->g_loop, g, 0));
+  c->g_loop_q = c->q;
+  return SP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -310,6 +404,7 @@ void sp_default_opts(sp_opts* o) {
   o->sweeps = 0;
   o->panel_pivoting = 0;
   o->launch_overlap = 0;
+  o->device_loop = 1;
 }
 
 const char* sp_status_str(sp_status st) {
@@ -484,6 +579,8 @@ void sp_destroy(sp_ctx* c) {
   for (auto& g : c->g_block)
     if (g) cudaGraphExecDestroy(g);
   if (c->g_factor) cudaGraphExecDestroy(c->g_factor);
+  if (c->g_loop) cudaGraphExecDestroy(c->g_loop);
+  if (c->host_loop) cudaFreeHost(c->host_loop);
   if (c->cap) cudaStreamDestroy(c->cap);
   cudaSetDevice(dev);
   delete c;
@@ -526,6 +623,7 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   if (c->opts.sweeps < 0 || c->opts.sweeps > 2) return SP_ERR_ARG;
   if (c->opts.panel_pivoting != 0 && c->opts.panel_pivoting != 1) return SP_ERR_ARG;
   if (c->opts.launch_overlap != 0 && c->opts.launch_overlap != 1) return SP_ERR_ARG;
+  if (c->opts.device_loop != 0 && c->opts.device_loop != 1) return SP_ERR_ARG;
   const size_t RH = (size_t)c->opts.max_rhs;
   c->d = d;
   c->n = n;
@@ -751,6 +849,9 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   SP_CK(dalloc(c.get(), &c->K.partial, sizeof(double2) * (size_t)c->K.nblk * 1024));
   SP_CK(dalloc(c.get(), &c->K.h, sizeof(double2) * 1024));
   SP_CK(cudaMallocHost(&c->host_sc, 8 * sizeof(double) * RH));
+  c->loop_bytes = sizeof(LoopHead) + sizeof(double) * (size_t)c->opts.maxit;
+  SP_CK(dalloc(c.get(), &c->loop, c->loop_bytes));
+  SP_CK(cudaMallocHost(&c->host_loop, c->loop_bytes));
   SP_CK(dalloc(c.get(), &c->app_in, sizeof(double2) * N * RH));
   SP_CK(dalloc(c.get(), &c->app_out, sizeof(double2) * N * RH));
   if (RH > 1) SP_CK(dalloc(c.get(), &c->blk_w, sizeof(double2) * N * RH));
@@ -893,9 +994,66 @@ static sp_status solve_start(sp_ctx* c, const double2* f, const double2* u0, dou
   return SP_OK;
 }
 
+// sp_solve with the restart cycles run by the graph of build_loop_graph: the host
+// waits once per cycle (the true residual decides about a restart) instead of once
+// per iteration.  Same kernels in the same order as solve_impl's loop: the same bits.
+static sp_status solve_loop(sp_ctx* c, const double2* f, const double2* u0, double2* u,
+                            sp_info* info) {
+  cudaStream_t st = c->stream;
+  const long N = c->N;
+  const double tol = c->opts.tol;
+  const int maxit = c->opts.maxit;
+  auto push_hist = [&](double v) {
+    if (info && info->hist && info->hist_len < info->hist_cap) info->hist[info->hist_len++] = v;
+  };
+  if (!c->g_loop || c->g_loop_q != c->q) {
+    SP_CK(cudaStreamSynchronize(st));
+    sp_status bs = build_loop_graph(c);
+    if (bs != SP_OK) return bs;
+  }
+  double2* uw = c->ubuf;
+  double bnorm = 0.0, rel0 = 1.0;
+  sp_status s0 = solve_start(c, f, u0, uw, &bnorm, &rel0, info);
+  if (s0 != SP_OK) return s0;
+  push_hist(rel0);
+  if (bnorm == 0.0) {
+    SP_CK(cudaMemsetAsync(u, 0, sizeof(double2) * N, st));
+    SP_CK(cudaStreamSynchronize(st));
+    if (info) info->true_relres = info->est_relres = 0.0;
+    return SP_OK;
+  }
+  int total = 0, restarts = 0;
+  double est_rel = rel0, true_rel = rel0;
+  if (rel0 > tol) {
+    SP_CK(cudaMemsetAsync(c->loop, 0, sizeof(LoopHead), st));
+    for (;;) {
+      SP_CK(cudaGraphLaunch(c->g_loop, st));
+      SP_CK(cudaStreamSynchronize(st));
+      const LoopHead& h = *c->host_loop;
+      const double* hh = reinterpret_cast<const double*>(c->host_loop + 1);
+      for (int i = total; i < h.total && i < maxit; ++i) push_hist(hh[i]);
+      total = h.total;
+      est_rel = h.est_rel;
+      true_rel = h.rnorm / bnorm;
+      if (true_rel <= tol || total >= maxit) break;
+      ++restarts;
+    }
+  }
+  if (u != uw) SP_CK(cudaMemcpyAsync(u, uw, sizeof(double2) * N, cudaMemcpyDeviceToDevice, st));
+  SP_CK(cudaStreamSynchronize(st));
+  if (info) {
+    info->iters = total;
+    info->restarts = restarts;
+    info->est_relres = est_rel;
+    info->true_relres = true_rel;
+  }
+  return true_rel <= tol ? SP_OK : SP_ERR_NOCONV;
+}
+
 static sp_status solve_impl(sp_ctx* c, const double2* f, const double2* u0, double2* u,
                             sp_info* info) {
   if (c->mixed) return solve_mixed(c, f, u0, u, info);
+  if (c->opts.device_loop && !c->profiling) return solve_loop(c, f, u0, u, info);
   cudaStream_t st = c->stream;
   const long N = c->N;
   double* hsc = c->host_sc;

@@ -231,6 +231,46 @@ cudaError_t kr_combine(const double2* Z, long ldz, int k, const double2* y, long
 // gam = [beta, 0, ...]; V0 = r / beta
 cudaError_t kr_start(const double2* r, long N, const double* nrm, double2* V0, double2* gam,
                      int len, cudaStream_t st);
+// Device-resident restart cycle (the loop of one cycle as a conditional while node
+// of a CUDA graph): the step's state on the device.
+struct LoopHead {
+  int j;           // column of the current Arnoldi step
+  int k;           // columns of the cycle once it stopped
+  int total;       // iterations so far, all cycles
+  int cont;        // 1 while the cycle goes on
+  double est_rel;  // last estimate |gamma_{j+1}| / ||g||
+  double bnorm;    // ||g||           (written at the end of the cycle)
+  double rnorm;    // ||g - A u||     (written at the end of the cycle)
+  double pad;
+};
+// j = 0, cont = 1
+cudaError_t kr_loop_begin(LoopHead* h, cudaStream_t st);
+// dst[j dst_ld ...] = src[j src_ld ...] for j = *jp (ld 0: a fixed vector)
+cudaError_t kr_copy_col(const double2* src, long src_ld, double2* dst, long dst_ld, const int* jp,
+                        long N, cudaStream_t st);
+// kr_dots / kr_update_dots / kr_givens with j = *jp (nv = *jp + 1 <= nv_max)
+cudaError_t kr_dots_dev(const double2* V, long ldv, int nv_max, const int* jp, const double2* w,
+                        long N, KrylovWork& K, double2* h_out, cudaStream_t st);
+cudaError_t kr_update_dots_dev(const double2* V, long ldv, int nv_max, const int* jp, double2* w,
+                               long N, const double2* h, KrylovWork& K, double2* h2_out,
+                               cudaStream_t st);
+cudaError_t kr_givens_dev(double2* H, int ldh, const int* jp, const double2* h1, const double2* h2,
+                          const double* nrm, double* cs, double2* sn, double2* gam, double* est,
+                          cudaStream_t st);
+// count the iteration, record est[0] / bnorm[0] in hist, advance j or stop the cycle
+// (setting cond to 0)
+cudaError_t kr_loop_step(LoopHead* h, double* hist, const double* est, const double* bnorm,
+                         double tol, int maxit, int restart, cudaGraphConditionalHandle cond,
+                         cudaStream_t st);
+// V[h->j] = w / nrm[0] if the cycle goes on
+cudaError_t kr_loop_scale(const double2* w, long N, const double* nrm, double2* V,
+                          const LoopHead* h, cudaStream_t st);
+// kr_update_solution with k = *kp
+cudaError_t kr_update_solution_dev(const double2* H, int ldh, const int* kp, const double2* gam,
+                                   double2* y, const double2* Z, long ldz, long N, double2* u,
+                                   cudaStream_t st);
+// h->bnorm = nrm[2], h->rnorm = nrm[3]
+cudaError_t kr_loop_finish(LoopHead* h, const double* nrm, cudaStream_t st);
 // complex64 counterparts for the inner solve of the mixed-precision form
 cudaError_t kr32_dots(const float2* V, long ldv, int nv, const float2* w, long N, KrylovWork& K,
                       double2* h_out, cudaStream_t st);

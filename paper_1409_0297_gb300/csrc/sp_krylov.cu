@@ -67,8 +67,12 @@ __device__ void chunk_dots(const double2* V, long ldv, int nv, const double2* w,
   }
 }
 
+// jdev != null: the vector count is *jdev + 1, read on the device (the
+// device-resident iteration; nv is then only the launch bound).
 __global__ void __launch_bounds__(kThr) dots_kernel(const double2* V, long ldv, int nv,
-                                                    const double2* w, long N, double2* partial) {
+                                                    const double2* w, long N, double2* partial,
+                                                    const int* jdev) {
+  if (jdev) nv = *jdev + 1;
   long c0, c1;
   chunk_of(N, &c0, &c1);
   chunk_dots(V, ldv, nv, w, c0, c1, partial);
@@ -76,7 +80,8 @@ __global__ void __launch_bounds__(kThr) dots_kernel(const double2* V, long ldv, 
 
 __global__ void __launch_bounds__(kThr) update_dots_kernel(const double2* V, long ldv, int nv,
                                                            double2* w, long N, const double2* h,
-                                                           double2* partial) {
+                                                           double2* partial, const int* jdev) {
+  if (jdev) nv = *jdev + 1;
   __shared__ double2 hs[1024];
   for (int j = threadIdx.x; j < nv; j += blockDim.x) hs[j] = h[j];
   __syncthreads();
@@ -110,7 +115,9 @@ __global__ void __launch_bounds__(kThr) update_dots_kernel(const double2* V, lon
 }
 
 // out[j] = sum_b partial[j * nblk + b]  (one warp per j, fixed order)
-__global__ void reduce_partials_kernel(const double2* partial, int nblk, int nv, double2* out) {
+__global__ void reduce_partials_kernel(const double2* partial, int nblk, int nv, double2* out,
+                                       const int* jdev) {
+  if (jdev) nv = *jdev + 1;
   const int lane = threadIdx.x & 31;
   const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (j >= nv) return;
@@ -177,8 +184,9 @@ __device__ __forceinline__ double cabs2(double2 a) { return hypot(a.x, a.y); }
 // residual estimate |gamma_{j+1}|.  Single thread.
 __global__ void givens_kernel(double2* H, int ldh, int j, const double2* h1, const double2* h2,
                               const double* nrm, double* cs, double2* sn, double2* gam,
-                              double* est) {
+                              double* est, const int* jdev) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (jdev) j = *jdev;
   double2* col = H + (long)j * ldh;
   for (int i = 0; i <= j; ++i) col[i] = make_double2(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
   col[j + 1] = make_double2(nrm[0], 0.0);
@@ -220,7 +228,9 @@ __global__ void givens_kernel(double2* H, int ldh, int j, const double2* h1, con
 }
 
 // y = R^{-1} gam (upper triangular, column-major, leading dimension ldh); one CTA
-__global__ void trisolve_kernel(const double2* H, int ldh, int k, const double2* gam, double2* y) {
+__global__ void trisolve_kernel(const double2* H, int ldh, int k, const double2* gam, double2* y,
+                                const int* kdev) {
+  if (kdev) k = *kdev;
   __shared__ double2 g[1024];
   for (int i = threadIdx.x; i < k; i += blockDim.x) g[i] = gam[i];
   __syncthreads();
@@ -243,7 +253,8 @@ __global__ void trisolve_kernel(const double2* H, int ldh, int k, const double2*
 }
 
 __global__ void combine_kernel(const double2* Z, long ldz, int k, const double2* y, long N,
-                               double2* u) {
+                               double2* u, const int* kdev) {
+  if (kdev) k = *kdev;
   __shared__ double2 ys[1024];
   for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = y[j];
   __syncthreads();
@@ -263,8 +274,8 @@ __global__ void combine_kernel(const double2* Z, long ldz, int k, const double2*
 cudaError_t kr_dots(const double2* V, long ldv, int nv, const double2* w, long N, KrylovWork& K,
                     double2* h_out, cudaStream_t st) {
   ProfScope ps(PROF_KRYLOV, st);
-  dots_kernel<<<K.nblk, kThr, 0, st>>>(V, ldv, nv, w, N, K.partial);
-  reduce_partials_kernel<<<(nv + 7) / 8, 256, 0, st>>>(K.partial, K.nblk, nv, h_out);
+  dots_kernel<<<K.nblk, kThr, 0, st>>>(V, ldv, nv, w, N, K.partial, nullptr);
+  reduce_partials_kernel<<<(nv + 7) / 8, 256, 0, st>>>(K.partial, K.nblk, nv, h_out, nullptr);
   ps.done(16.0 * N * (nv + 1), 2, st);
   return cudaGetLastError();
 }
@@ -272,8 +283,10 @@ cudaError_t kr_dots(const double2* V, long ldv, int nv, const double2* w, long N
 cudaError_t kr_update_dots(const double2* V, long ldv, int nv, double2* w, long N,
                            const double2* h, KrylovWork& K, double2* h2_out, cudaStream_t st) {
   ProfScope ps(PROF_KRYLOV, st);
-  update_dots_kernel<<<K.nblk, kThr, 0, st>>>(V, ldv, nv, w, N, h, h2_out ? K.partial : nullptr);
-  if (h2_out) reduce_partials_kernel<<<(nv + 7) / 8, 256, 0, st>>>(K.partial, K.nblk, nv, h2_out);
+  update_dots_kernel<<<K.nblk, kThr, 0, st>>>(V, ldv, nv, w, N, h, h2_out ? K.partial : nullptr,
+                                              nullptr);
+  if (h2_out)
+    reduce_partials_kernel<<<(nv + 7) / 8, 256, 0, st>>>(K.partial, K.nblk, nv, h2_out, nullptr);
   ps.done(16.0 * N * (nv + 2), h2_out ? 2 : 1, st);
   return cudaGetLastError();
 }
@@ -281,7 +294,7 @@ cudaError_t kr_update_dots(const double2* V, long ldv, int nv, double2* w, long 
 cudaError_t kr_norm(const double2* w, long N, KrylovWork& K, double* nrm_out, cudaStream_t st) {
   ProfScope ps(PROF_KRYLOV, st);
   norm2_kernel<<<K.nblk, kThr, 0, st>>>(w, N, K.partial);
-  reduce_partials_kernel<<<1, 32, 0, st>>>(K.partial, K.nblk, 1, K.h + 1023);
+  reduce_partials_kernel<<<1, 32, 0, st>>>(K.partial, K.nblk, 1, K.h + 1023, nullptr);
   sqrt_kernel<<<1, 1, 0, st>>>(K.h + 1023, nrm_out);
   ps.done(16.0 * N, 3, st);
   return cudaGetLastError();
@@ -305,7 +318,7 @@ cudaError_t kr_givens(double2* H, int ldh, int j, const double2* h1, const doubl
                       const double* nrm, double* cs, double2* sn, double2* gam, double* est,
                       cudaStream_t st) {
   ProfScope ps(PROF_KRYLOV, st);
-  givens_kernel<<<1, 32, 0, st>>>(H, ldh, j, h1, h2, nrm, cs, sn, gam, est);
+  givens_kernel<<<1, 32, 0, st>>>(H, ldh, j, h1, h2, nrm, cs, sn, gam, est, nullptr);
   ps.done(0.0, 1, st);
   return cudaGetLastError();
 }
@@ -313,22 +326,22 @@ cudaError_t kr_givens(double2* H, int ldh, int j, const double2* h1, const doubl
 cudaError_t kr_update_solution(const double2* H, int ldh, int k, const double2* gam, double2* y,
                                const double2* Z, long ldz, long N, double2* u, cudaStream_t st) {
   ProfScope ps(PROF_KRYLOV, st);
-  trisolve_kernel<<<1, 256, 0, st>>>(H, ldh, k, gam, y);
-  combine_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(Z, ldz, k, y, N, u);
+  trisolve_kernel<<<1, 256, 0, st>>>(H, ldh, k, gam, y, nullptr);
+  combine_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(Z, ldz, k, y, N, u, nullptr);
   ps.done(16.0 * N * (k + 2), 2, st);
   return cudaGetLastError();
 }
 
 cudaError_t kr_trisolve(const double2* H, int ldh, int k, const double2* gam, double2* y,
                         cudaStream_t st) {
-  trisolve_kernel<<<1, 256, 0, st>>>(H, ldh, k, gam, y);
+  trisolve_kernel<<<1, 256, 0, st>>>(H, ldh, k, gam, y, nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t kr_combine(const double2* Z, long ldz, int k, const double2* y, long N, double2* u,
                        cudaStream_t st) {
   ProfScope ps(PROF_KRYLOV, st);
-  combine_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(Z, ldz, k, y, N, u);
+  combine_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(Z, ldz, k, y, N, u, nullptr);
   ps.done(16.0 * N * (k + 2), 1, st);
   return cudaGetLastError();
 }
@@ -339,6 +352,135 @@ cudaError_t kr_start(const double2* r, long N, const double* nrm, double2* V0, d
   ProfScope ps(PROF_KRYLOV, st);
   start_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(r, N, nrm, V0, gam, len);
   ps.done(32.0 * N, 1, st);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// Device-resident restart cycle: the Arnoldi step's column index j lives in device
+// memory (LoopHead), every kernel of the step reads it there, and the stopping test
+// runs on the device and ends the conditional (while) node of the CUDA graph that
+// repeats the step, so a whole cycle runs without a host round trip.  The
+// arithmetic is that of the host-driven iteration above, kernel for kernel.
+namespace {
+
+__global__ void loop_begin_kernel(LoopHead* h) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    h->j = 0;
+    h->cont = 1;
+  }
+}
+
+// dst[j * dst_ld + i] = src[j * src_ld + i], j = *jp (an ld of 0: a fixed vector)
+__global__ void copy_col_kernel(const double2* src, long src_ld, double2* dst, long dst_ld,
+                                const int* jp, long N) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const long j = *jp;
+  dst[j * dst_ld + i] = src[j * src_ld + i];
+}
+
+// One thread: count the iteration, record the estimate, and either advance j or
+// stop the cycle (k columns) and end the while node.  The test is the host loop's:
+// estimate <= tol, the iteration budget, a zero new column (breakdown) or a full
+// basis.
+__global__ void loop_step_kernel(LoopHead* h, double* hist, const double* est,
+                                 const double* bnorm, double tol, int maxit, int restart,
+                                 cudaGraphConditionalHandle cond) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int k = h->j + 1, total = h->total + 1;
+  const double rel = est[0] / bnorm[0];
+  h->total = total;
+  h->est_rel = rel;
+  if (total <= maxit) hist[total - 1] = rel;
+  if (rel <= tol || total >= maxit || est[1] == 0.0 || k == restart) {
+    h->k = k;
+    h->cont = 0;
+    cudaGraphSetConditional(cond, 0);
+  } else {
+    h->j = k;
+    h->cont = 1;
+  }
+}
+
+// V[j] = w / nrm for the column the step advanced to (nothing when it stopped)
+__global__ void loop_scale_kernel(const double2* w, long N, const double* nrm, double2* V,
+                                  const LoopHead* h) {
+  if (!h->cont) return;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double a = nrm[0] > 0 ? 1.0 / nrm[0] : 0.0;
+  const double2 v = w[i];
+  V[(long)h->j * N + i] = make_double2(v.x * a, v.y * a);
+}
+
+__global__ void loop_finish_kernel(LoopHead* h, const double* nrm) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    h->bnorm = nrm[2];
+    h->rnorm = nrm[3];
+  }
+}
+
+}  // namespace
+
+cudaError_t kr_loop_begin(LoopHead* h, cudaStream_t st) {
+  loop_begin_kernel<<<1, 32, 0, st>>>(h);
+  return cudaGetLastError();
+}
+
+cudaError_t kr_copy_col(const double2* src, long src_ld, double2* dst, long dst_ld, const int* jp,
+                        long N, cudaStream_t st) {
+  copy_col_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(src, src_ld, dst, dst_ld, jp, N);
+  return cudaGetLastError();
+}
+
+cudaError_t kr_dots_dev(const double2* V, long ldv, int nv_max, const int* jp, const double2* w,
+                        long N, KrylovWork& K, double2* h_out, cudaStream_t st) {
+  dots_kernel<<<K.nblk, kThr, 0, st>>>(V, ldv, nv_max, w, N, K.partial, jp);
+  reduce_partials_kernel<<<(nv_max + 7) / 8, 256, 0, st>>>(K.partial, K.nblk, nv_max, h_out, jp);
+  return cudaGetLastError();
+}
+
+cudaError_t kr_update_dots_dev(const double2* V, long ldv, int nv_max, const int* jp, double2* w,
+                               long N, const double2* h, KrylovWork& K, double2* h2_out,
+                               cudaStream_t st) {
+  update_dots_kernel<<<K.nblk, kThr, 0, st>>>(V, ldv, nv_max, w, N, h,
+                                              h2_out ? K.partial : nullptr, jp);
+  if (h2_out)
+    reduce_partials_kernel<<<(nv_max + 7) / 8, 256, 0, st>>>(K.partial, K.nblk, nv_max, h2_out,
+                                                             jp);
+  return cudaGetLastError();
+}
+
+cudaError_t kr_givens_dev(double2* H, int ldh, const int* jp, const double2* h1, const double2* h2,
+                          const double* nrm, double* cs, double2* sn, double2* gam, double* est,
+                          cudaStream_t st) {
+  givens_kernel<<<1, 32, 0, st>>>(H, ldh, 0, h1, h2, nrm, cs, sn, gam, est, jp);
+  return cudaGetLastError();
+}
+
+cudaError_t kr_loop_step(LoopHead* h, double* hist, const double* est, const double* bnorm,
+                         double tol, int maxit, int restart, cudaGraphConditionalHandle cond,
+                         cudaStream_t st) {
+  loop_step_kernel<<<1, 32, 0, st>>>(h, hist, est, bnorm, tol, maxit, restart, cond);
+  return cudaGetLastError();
+}
+
+cudaError_t kr_loop_scale(const double2* w, long N, const double* nrm, double2* V,
+                          const LoopHead* h, cudaStream_t st) {
+  loop_scale_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(w, N, nrm, V, h);
+  return cudaGetLastError();
+}
+
+cudaError_t kr_update_solution_dev(const double2* H, int ldh, const int* kp, const double2* gam,
+                                   double2* y, const double2* Z, long ldz, long N, double2* u,
+                                   cudaStream_t st) {
+  trisolve_kernel<<<1, 256, 0, st>>>(H, ldh, 0, gam, y, kp);
+  combine_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(Z, ldz, 0, y, N, u, kp);
+  return cudaGetLastError();
+}
+
+cudaError_t kr_loop_finish(LoopHead* h, const double* nrm, cudaStream_t st) {
+  loop_finish_kernel<<<1, 32, 0, st>>>(h, nrm);
   return cudaGetLastError();
 }
 
@@ -459,7 +601,7 @@ cudaError_t kr32_dots(const float2* V, long ldv, int nv, const float2* w, long N
                       double2* h_out, cudaStream_t st) {
   ProfScope ps(PROF_KRYLOV, st);
   dots32_kernel<<<K.nblk, kThr, 0, st>>>(V, ldv, nv, w, N, K.partial);
-  reduce_partials_kernel<<<(nv + 7) / 8, 256, 0, st>>>(K.partial, K.nblk, nv, h_out);
+  reduce_partials_kernel<<<(nv + 7) / 8, 256, 0, st>>>(K.partial, K.nblk, nv, h_out, nullptr);
   ps.done(8.0 * N * (nv + 1), 2, st);
   return cudaGetLastError();
 }
@@ -468,7 +610,8 @@ cudaError_t kr32_update_dots(const float2* V, long ldv, int nv, float2* w, long 
                              KrylovWork& K, double2* h2_out, cudaStream_t st) {
   ProfScope ps(PROF_KRYLOV, st);
   update_dots32_kernel<<<K.nblk, kThr, 0, st>>>(V, ldv, nv, w, N, h, h2_out ? K.partial : nullptr);
-  if (h2_out) reduce_partials_kernel<<<(nv + 7) / 8, 256, 0, st>>>(K.partial, K.nblk, nv, h2_out);
+  if (h2_out)
+    reduce_partials_kernel<<<(nv + 7) / 8, 256, 0, st>>>(K.partial, K.nblk, nv, h2_out, nullptr);
   ps.done(8.0 * N * (nv + 2), h2_out ? 2 : 1, st);
   return cudaGetLastError();
 }
@@ -476,7 +619,7 @@ cudaError_t kr32_update_dots(const float2* V, long ldv, int nv, float2* w, long 
 cudaError_t kr32_norm(const float2* w, long N, KrylovWork& K, double* nrm_out, cudaStream_t st) {
   ProfScope ps(PROF_KRYLOV, st);
   norm32_kernel<<<K.nblk, kThr, 0, st>>>(w, N, K.partial);
-  reduce_partials_kernel<<<1, 32, 0, st>>>(K.partial, K.nblk, 1, K.h + 1023);
+  reduce_partials_kernel<<<1, 32, 0, st>>>(K.partial, K.nblk, 1, K.h + 1023, nullptr);
   sqrt_kernel<<<1, 1, 0, st>>>(K.h + 1023, nrm_out);
   ps.done(8.0 * N, 3, st);
   return cudaGetLastError();
