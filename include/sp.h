@@ -185,6 +185,30 @@ size_t sp_abi_size(int which);
 sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_opts *opts,
                    void *stream, sp_ctx **out);
 
+/* A problem group: one context for P independent problems of the same grid (d, n)
+ * and leaf size b, problem p with shift shifts[p] (its own Green's function, stencil
+ * tables and, at sp_factor, medium).  The nested-dissection structure depends on
+ * the grid and leaf size only (Section 2.3), so every level of all P problems has
+ * fronts of one size: each factorisation and sweep launch covers the P nf fronts of
+ * a level at once, the operator and stencil launches cover the P vectors, and the P
+ * GMRES iterations advance together (batched Krylov kernels, restart cycles as CUDA
+ * graphs; see sp_opts.device_loop).  Every vector of the context then holds P N
+ * entries, problem p's at offset p N: q of sp_factor, r / z of sp_apply, f / u of
+ * sp_solve, x / w of sp_matvec, f / g of sp_green, r / y of sp_qapply; sp_solve and
+ * sp_solve_host fill P info records in problem order, sp_solve_many nrhs P (right-hand side r
+ * of problem p at index and vector offset r P + p); sp_get_table / sp_set_table take
+ * t = p 2^d + type.  1 <= P, P opts.max_rhs <= 1024; SP_PREC_MIXED and sp_solve_x0
+ * with a start vector take P = 1 only (else SP_ERR_ARG).  The other arguments and
+ * errors are sp_setup's, checked for every shift.  A group's problems give the
+ * results of separate contexts up to rounding: launch shapes that depend on the
+ * number of fronts (row splits of the sweeps' matrix-vector products, fused or
+ * chained sweeps, block inverses on FP64 levels) may sum in another order. */
+sp_status sp_setup_group(int d, int n, int b, int P, const double *shifts, sp_precision prec,
+                         const sp_opts *opts, void *stream, sp_ctx **out);
+
+/* *P = the context's number of problems (1 unless made by sp_setup_group). */
+sp_status sp_problems(const sp_ctx *ctx, int *P);
+
 /* Assemble P = Q + C diag(q) into the fronts and factor it (Section 2.2, Fig. nd):
  * per level, leaves to root, extend-add of the children's Schur complements,
  * partial-pivot LU of the eliminated block, panels and Schur update.  q_dev: N

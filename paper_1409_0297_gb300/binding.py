@@ -20,7 +20,7 @@ SP_ERR_OOM, SP_ERR_TIMEOUT, SP_ERR_CUDA, SP_ERR_STATE = 5, 6, 7, 8
 SP_PREC_FP64, SP_PREC_FP32, SP_PREC_MIXED, SP_PREC_TF32, SP_PREC_TF32X3 = 0, 1, 2, 3, 4
 
 EXPORTED = [
-    "sp_abi_size", "sp_default_opts", "sp_setup", "sp_factor", "sp_apply", "sp_solve", "sp_factor_host",
+    "sp_abi_size", "sp_default_opts", "sp_setup", "sp_setup_group", "sp_problems", "sp_factor", "sp_apply", "sp_solve", "sp_factor_host",
     "sp_solve_host", "sp_matvec", "sp_green", "sp_qapply", "sp_get_table", "sp_set_table", "sp_stencil_table",
     "sp_front_sizes", "sp_level_info", "sp_costs", "sp_medium_helmholtz", "sp_medium_schrodinger", "sp_profile",
     "sp_profile_read", "sp_green_static", "sp_schur_update", "sp_tc_probe", "sp_tuning", "sp_solve_many",
@@ -82,6 +82,8 @@ def _load() -> ctypes.CDLL:
         "sp_abi_size": (ctypes.c_size_t, [I]),
         "sp_default_opts": (V, [ctypes.POINTER(sp_opts)]),
         "sp_setup": (I, [I, I, I, D, I, ctypes.POINTER(sp_opts), P, ctypes.POINTER(P)]),
+        "sp_setup_group": (I, [I, I, I, I, pD, I, ctypes.POINTER(sp_opts), P, ctypes.POINTER(P)]),
+        "sp_problems": (I, [P, pI]),
         "sp_factor": (I, [P, P]),
         "sp_apply": (I, [P, P, P]),
         "sp_solve": (I, [P, P, P, ctypes.POINTER(sp_info)]),
@@ -165,6 +167,24 @@ def sp_setup(d: int, n: int, b: int, s: float, prec: int = SP_PREC_FP64, opts: s
     return ctx.value
 
 
+def sp_setup_group(d: int, n: int, b: int, shifts, prec: int = SP_PREC_FP64,
+                   opts: sp_opts | None = None, stream: int = 0) -> int:
+    """A context of len(shifts) problems of one grid and leaf size (a problem group)."""
+    import numpy as np
+    sh = np.ascontiguousarray(np.asarray(shifts, dtype=np.float64).ravel())
+    ctx = ctypes.c_void_p()
+    _check(LIB.sp_setup_group(d, n, b, int(sh.size), _dptr(sh), prec,
+                              ctypes.byref(opts) if opts else None, ctypes.c_void_p(stream),
+                              ctypes.byref(ctx)), "sp_setup_group")
+    return ctx.value
+
+
+def sp_problems(ctx: int) -> int:
+    P = ctypes.c_int()
+    _check(LIB.sp_problems(ctx, ctypes.byref(P)), "sp_problems")
+    return P.value
+
+
 def sp_factor(ctx: int, q_dev: int) -> None:
     _check(LIB.sp_factor(ctx, q_dev), "sp_factor")
 
@@ -205,11 +225,24 @@ def _info_dict(info, hist, st):
                 guess_used=bool(info.guess_used))
 
 
-def sp_solve(ctx: int, f_dev: int, u_dev: int, hist_cap: int = 1024, allow_noconv=False) -> dict:
-    info, hist = _info(hist_cap)
-    st = LIB.sp_solve(ctx, f_dev, u_dev, ctypes.byref(info))
+def _infos(count: int, hist_cap: int):
+    infos = (sp_info * count)()
+    hists = []
+    for i in range(count):
+        info, hist = _info(hist_cap)
+        infos[i] = info  # copies the struct, including the pointer to hist
+        hists.append(hist)
+    return infos, hists
+
+
+def sp_solve(ctx: int, f_dev: int, u_dev: int, hist_cap: int = 1024, allow_noconv=False,
+             nprob: int = 1):
+    """One info dict; a list of nprob dicts for a group of nprob problems."""
+    infos, hists = _infos(nprob, hist_cap)
+    st = LIB.sp_solve(ctx, f_dev, u_dev, infos)
     _check(st, "sp_solve", (SP_OK, SP_ERR_NOCONV) if allow_noconv else (SP_OK,))
-    return _info_dict(info, hist, st)
+    out = [_info_dict(infos[i], hists[i], st) for i in range(nprob)]
+    return out[0] if nprob == 1 else out
 
 
 def sp_solve_x0(ctx: int, f_dev: int, u0_dev: int | None, u_dev: int, hist_cap: int = 1024,
@@ -221,24 +254,22 @@ def sp_solve_x0(ctx: int, f_dev: int, u0_dev: int | None, u_dev: int, hist_cap: 
 
 
 def sp_solve_many(ctx: int, nrhs: int, F_dev: int, U_dev: int, hist_cap: int = 1024,
-                  allow_noconv=False) -> list:
-    """nrhs right-hand sides stacked N apart; one info dict per right-hand side."""
-    infos = (sp_info * nrhs)()
-    hists = []
-    for i in range(nrhs):
-        info, hist = _info(hist_cap)
-        infos[i] = info  # copies the struct, including the pointer to hist
-        hists.append(hist)
+                  allow_noconv=False, nprob: int = 1) -> list:
+    """nrhs right-hand sides of each of the nprob problems (right-hand side r of
+    problem p at offset (r nprob + p) N); one info dict per (r, p), in that order."""
+    infos, hists = _infos(nrhs * nprob, hist_cap)
     st = LIB.sp_solve_many(ctx, nrhs, F_dev, U_dev, infos)
     _check(st, "sp_solve_many", (SP_OK, SP_ERR_NOCONV) if allow_noconv else (SP_OK,))
-    return [_info_dict(infos[i], hists[i], st) for i in range(nrhs)]
+    return [_info_dict(infos[i], hists[i], st) for i in range(nrhs * nprob)]
 
 
-def sp_solve_host(ctx: int, f_host, u_host, hist_cap: int = 1024, allow_noconv=False) -> dict:
-    info, hist = _info(hist_cap)
-    st = LIB.sp_solve_host(ctx, f_host.ctypes.data, u_host.ctypes.data, ctypes.byref(info))
+def sp_solve_host(ctx: int, f_host, u_host, hist_cap: int = 1024, allow_noconv=False,
+                  nprob: int = 1):
+    infos, hists = _infos(nprob, hist_cap)
+    st = LIB.sp_solve_host(ctx, f_host.ctypes.data, u_host.ctypes.data, infos)
     _check(st, "sp_solve_host", (SP_OK, SP_ERR_NOCONV) if allow_noconv else (SP_OK,))
-    return _info_dict(info, hist, st)
+    out = [_info_dict(infos[i], hists[i], st) for i in range(nprob)]
+    return out[0] if nprob == 1 else out
 
 
 def sp_get_table(ctx: int, t: int):
@@ -385,9 +416,11 @@ def sp_destroy(ctx: int) -> None:
 class Solver:
     """Owns one context.  Vectors are torch complex128 CUDA tensors of n^d entries,
     q a float64 CUDA tensor; the solver keeps a reference to q (the library reads
-    it until the next factor call)."""
+    it until the next factor call).  With a sequence of shifts s the context is a
+    problem group (sp_setup_group): vectors and q hold P n^d entries, problem p's at
+    p n^d, and solve returns one info dict per problem."""
 
-    def __init__(self, d: int, n: int, b: int, s: float, prec: int = SP_PREC_FP64,
+    def __init__(self, d: int, n: int, b: int, s, prec: int = SP_PREC_FP64,
                  maxit: int = 500, restart: int = 200, tol: float = 1e-8, device: int = 0,
                  stream: int = 0, host_threads: int = 0, autotune: bool = False,
                  max_rhs: int = 1, setup_route: int = 0, stencil: int = 0, inv_block: int = 0,
@@ -409,25 +442,32 @@ class Solver:
         o.device_loop = device_loop
         self.d, self.n, self.b, self.s, self.prec = d, n, b, s, prec
         self.N = n ** d
-        self.ctx = sp_setup(d, n, b, s, prec, o, stream)
+        if isinstance(s, (int, float)):
+            self.P = 1
+            self.ctx = sp_setup(d, n, b, s, prec, o, stream)
+        else:
+            self.P = len(s)
+            self.ctx = sp_setup_group(d, n, b, s, prec, o, stream)
+        self.NP = self.P * self.N
         self._q = None
 
     def _vec(self, x, dtype):
         import torch
         if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == dtype and
-                x.is_contiguous() and x.numel() == self.N):
-            raise ValueError(f"expected a contiguous CUDA {dtype} tensor of {self.N} entries")
+                x.is_contiguous() and x.numel() == self.NP):
+            raise ValueError(f"expected a contiguous CUDA {dtype} tensor of {self.NP} entries")
         return x.data_ptr()
 
     def solve_many(self, F, U, **kw):
-        """F, U: contiguous CUDA complex128 tensors of nrhs x N entries."""
+        """F, U: contiguous CUDA complex128 tensors of nrhs x P x N entries."""
         import torch
-        nrhs = F.numel() // self.N
+        nrhs = F.numel() // self.NP
         for x in (F, U):
             if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.complex128 and
-                    x.is_contiguous() and x.numel() == nrhs * self.N and nrhs >= 1):
-                raise ValueError("expected contiguous CUDA complex128 tensors of nrhs x N entries")
-        return sp_solve_many(self.ctx, nrhs, F.data_ptr(), U.data_ptr(), **kw)
+                    x.is_contiguous() and x.numel() == nrhs * self.NP and nrhs >= 1):
+                raise ValueError("expected contiguous CUDA complex128 tensors of nrhs x P x N "
+                                 "entries")
+        return sp_solve_many(self.ctx, nrhs, F.data_ptr(), U.data_ptr(), nprob=self.P, **kw)
 
     def factor(self, q):
         import torch
@@ -453,7 +493,8 @@ class Solver:
 
     def solve(self, f, u, **kw):
         import torch
-        return sp_solve(self.ctx, self._vec(f, torch.complex128), self._vec(u, torch.complex128), **kw)
+        return sp_solve(self.ctx, self._vec(f, torch.complex128), self._vec(u, torch.complex128),
+                        nprob=self.P, **kw)
 
     def solve_x0(self, f, u0, u, **kw):
         """sp_solve from the starting vector u0 (None: zero)."""

@@ -114,14 +114,24 @@ struct sp_ctx {
   double2* blk_w = nullptr;    // max_rhs N: operator outputs of sp_solve_many
   cudaGraphExec_t g_block[9] = {};  // block applications of nv = 2 ... max_rhs stacked
   bool g_block_tried[9] = {};       // vectors, captured on first use
-  // device-resident restart cycle (opts.device_loop): its graph, the medium pointer it
-  // was captured with, its state (a LoopHead, then maxit doubles of estimates) on the
-  // device and a pinned copy
-  cudaGraphExec_t g_loop = nullptr;
-  const double* g_loop_q = nullptr;
-  LoopHead* loop = nullptr;
-  LoopHead* host_loop = nullptr;
-  size_t loop_bytes = 0;
+  // problem group: P problems of one grid and leaf size (shifts[p]); vectors of the
+  // context hold P N entries, problem p's at p N
+  int P = 1;
+  long NP = 0;
+  std::vector<double> shifts;
+  long t_stride = 0;  // entries between two problems' T tables (Tcat, Tcat32)
+  int IM = 1;         // Krylov instances the workspace holds: P max_rhs
+  // batched Krylov processes (sp_solve and sp_solve_many through the cycle graphs):
+  // per-instance state on the device and pinned copies, one cycle graph per
+  // right-hand-side count R (R P instances) and the medium pointer it was captured with
+  LoopHead* heads = nullptr;
+  LoopHead* host_heads = nullptr;
+  double* hist = nullptr;  // IM x maxit estimates
+  double* host_hist = nullptr;
+  int* run = nullptr;
+  int* host_run = nullptr;
+  cudaGraphExec_t g_cycle[9] = {};
+  const double* g_cycle_q[9] = {};
   double factor_entries = 0, factor_flops = 0, apply_bytes = 0;
 };
 
@@ -174,15 +184,10 @@ double perturb_shift(int d, int n, double s) {
   return s;
 }
 
+sp_status apply_block(sp_ctx* c, int nv, const double2* r, double2* z, cudaStream_t st);
+
 sp_status apply_direct(sp_ctx* c, const double2* r, double2* z, cudaStream_t st) {
-  SP_CK(q_apply(c->prec, c->d, c->n, c->nl, c->qtypes, c->Tcat, c->Tcat32, r, c->rhsQ, st, 1,
-                c->opts.launch_overlap != 0));
-  for (int l = 0; l <= c->L; ++l)
-    SP_CK(forward_level(c->prec, c->d, c->lv[l], l ? &c->lv[l - 1] : nullptr, c->rhsQ,
-                        c->gemv_part, st));
-  for (int l = c->L; l >= 0; --l)
-    SP_CK(backward_level(c->prec, c->d, c->lv[l], z, c->gemv_part, st));
-  return SP_OK;
+  return apply_block(c, 1, r, z, st);
 }
 
 // z = P^{-1} Q r: the captured graph when there is one and no kernel timing is
@@ -190,7 +195,7 @@ sp_status apply_direct(sp_ctx* c, const double2* r, double2* z, cudaStream_t st)
 sp_status apply_impl(sp_ctx* c, const double2* r, double2* z) {
   cudaStream_t st = c->stream;
   if (c->g_apply && !c->profiling) {
-    const size_t bytes = sizeof(double2) * (size_t)c->N;
+    const size_t bytes = sizeof(double2) * (size_t)c->NP;
     SP_CK(cudaMemcpyAsync(c->app_in, r, bytes, cudaMemcpyDeviceToDevice, st));
     SP_CK(cudaGraphLaunch(c->g_apply, st));
     SP_CK(cudaMemcpyAsync(z, c->app_out, bytes, cudaMemcpyDeviceToDevice, st));
@@ -287,22 +292,70 @@ void capture_graph(sp_ctx* c, cudaGraphExec_t* out, Fn fn) {
   cudaGetLastError();
 }
 
-// The restart cycle of sp_solve as one CUDA graph (opts.device_loop): V_0 = r / |r|,
-// then a conditional while node whose body is one Arnoldi step (the column index on
-// the device; the step's last kernels run the stopping test and end the loop), then
-// u += Z y, the true residual r = g - A u and a copy of the cycle's state to the
-// host.  Works on the context's own vectors (u in ubuf) and its medium pointer c->q,
-// so it is captured again when sp_factor is given another medium pointer.
-sp_status build_loop_graph(sp_ctx* c) {
-  if (c->g_loop) {
-    cudaGraphExecDestroy(c->g_loop);
-    c->g_loop = nullptr;
+// Application of the preconditioner to nv stacked vectors of the context (each P N
+// entries, nv P problem vectors N apart): stencil, forward sweep, backward sweep.
+sp_status apply_block(sp_ctx* c, int nv, const double2* r, double2* z, cudaStream_t st) {
+  SP_CK(q_apply(c->prec, c->d, c->n, c->nl, c->qtypes, c->Tcat, c->Tcat32, r, c->rhsQ, st, nv,
+                c->opts.launch_overlap != 0, c->P, c->t_stride));
+  for (int l = 0; l <= c->L; ++l)
+    SP_CK(forward_level(c->prec, c->d, c->lv[l], l ? &c->lv[l - 1] : nullptr, c->rhsQ,
+                        c->gemv_part, st, nv, c->NP));
+  for (int l = c->L; l >= 0; --l)
+    SP_CK(backward_level(c->prec, c->d, c->lv[l], z, c->gemv_part, st, nv, c->NP));
+  return SP_OK;
+}
+
+// The instances' Krylov workspace slices (instance i = r P + p: right-hand side r of
+// problem p; every vector N entries, instance i's at i N).
+KBatch make_batch(sp_ctx* c) {
+  KBatch b;
+  const long N = c->N;
+  const int mv = c->maxv, restart = c->opts.restart;
+  b.V = c->V;
+  b.Z = c->Z;
+  b.H = c->H;
+  b.gam = c->gam;
+  b.sn = c->sn;
+  b.cs = c->cs;
+  b.h1 = c->h1;
+  b.h2 = c->h2;
+  b.y = c->y;
+  b.nrm = c->nrm;
+  b.est = c->est;
+  b.partial = c->K.partial;
+  b.w = c->t;
+  b.head = c->heads;
+  b.run = c->run;
+  b.N = N;
+  b.sV = (long)mv * N;
+  b.sZ = (long)restart * N;
+  b.sH = (long)mv * restart;
+  b.sG = mv + 1;
+  b.sh = 1024;
+  b.sP = (long)c->K.nblk * 1024;
+  b.ldh = mv;
+  b.nblk = c->K.nblk;
+  return b;
+}
+
+// One GMRES restart cycle of R P instances as one CUDA graph: V_0 = r / |r| for the
+// running instances, then a conditional while node whose body is one Arnoldi step of
+// every instance still in its cycle (the apply of the R stacked vectors, the operator,
+// Gram-Schmidt twice, the Givens rotation, the stopping test; the test ends the node
+// when no instance goes on), then u += Z y, the true residual r = g - A u and a copy
+// of the heads and estimates to the host.  The graph works on the context's own
+// vectors (u in ubuf) and the medium pointer c->q, so it is captured again when
+// sp_factor is given another medium pointer.
+sp_status build_cycle_graph(sp_ctx* c, int R) {
+  if (c->g_cycle[R]) {
+    cudaGraphExecDestroy(c->g_cycle[R]);
+    c->g_cycle[R] = nullptr;
   }
   if (!c->cap) return SP_ERR_CUDA;
   cudaStream_t s = c->cap;
   const long N = c->N;
-  const int mv = c->maxv;
-  double* hist = reinterpret_cast<double*>(c->loop + 1);
+  const int I = R * c->P, mv = c->maxv, maxit = c->opts.maxit;
+  const KBatch b = make_batch(c);
   cudaGraph_t g = nullptr;
   SP_CK(cudaGraphCreate(&g, 0));
   struct Owner {
@@ -313,8 +366,8 @@ sp_status build_loop_graph(sp_ctx* c) {
   SP_CK(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
   cudaGraph_t body = nullptr;
   auto outer = [&]() -> sp_status {
-    SP_CK(kr_start(c->r, N, c->nrm + 3, c->V, c->gam, mv + 1, s));
-    SP_CK(kr_loop_begin(c->loop, s));
+    SP_CK(kb_start(b, I, c->r, mv + 1, s));
+    SP_CK(kb_begin(b, I, s));
     cudaStreamCaptureStatus cs;
     const cudaGraphNode_t* deps = nullptr;
     size_t nd = 0;
@@ -327,12 +380,14 @@ sp_status build_loop_graph(sp_ctx* c) {
     SP_CK(cudaGraphAddNode(&wn, g, deps, nullptr, nd, &p));
     body = p.conditional.phGraph_out[0];
     SP_CK(cudaStreamUpdateCaptureDependencies(s, &wn, nullptr, 1, cudaStreamSetCaptureDependencies));
-    SP_CK(kr_update_solution_dev(c->H, mv, &c->loop->k, c->gam, c->y, c->Z, N, N, c->ubuf, s));
-    SP_CK(fft_green_apply(c->fft, c->ubuf, c->q, true, c->t, s));
-    SP_CK(kr_sub(c->g, c->t, N, c->r, s));
-    SP_CK(kr_norm(c->r, N, c->K, c->nrm + 3, s));
-    SP_CK(kr_loop_finish(c->loop, c->nrm, s));
-    SP_CK(cudaMemcpyAsync(c->host_loop, c->loop, c->loop_bytes, cudaMemcpyDeviceToHost, s));
+    SP_CK(kb_update_solution(b, I, c->ubuf, s));
+    SP_CK(fft_green_apply(c->fft, c->ubuf, c->q, true, c->t, s, I, c->P));
+    SP_CK(kr_sub(c->g, c->t, (long)I * N, c->r, s));
+    SP_CK(kb_norm(b, I, c->r, 3, s));
+    SP_CK(kb_finish(b, I, s));
+    SP_CK(cudaMemcpyAsync(c->host_heads, c->heads, sizeof(LoopHead) * I, cudaMemcpyDeviceToHost, s));
+    SP_CK(cudaMemcpyAsync(c->host_hist, c->hist, sizeof(double) * maxit * I,
+                          cudaMemcpyDeviceToHost, s));
     return SP_OK;
   };
   SP_CK(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
@@ -342,24 +397,14 @@ sp_status build_loop_graph(sp_ctx* c) {
   if (so != SP_OK) return so;
   SP_CK(e);
   if (!body) return SP_ERR_CUDA;
-  // the body: one Arnoldi step with j = loop->j (the host loop's kernels, in its order)
   auto step = [&]() -> sp_status {
-    const int* jp = &c->loop->j;
-    double2* w = c->t;
-    SP_CK(kr_copy_col(c->V, N, c->app_in, 0, jp, N, s));
-    sp_status a = apply_direct(c, c->app_in, c->app_out, s);
+    SP_CK(kb_copy_in(b, I, c->app_in, s));
+    sp_status a = apply_block(c, R, c->app_in, c->app_out, s);
     if (a != SP_OK) return a;
-    SP_CK(kr_copy_col(c->app_out, 0, c->Z, N, jp, N, s));
-    SP_CK(fft_green_apply(c->fft, c->app_out, c->q, true, w, s));
-    // classical Gram-Schmidt, twice
-    SP_CK(kr_dots_dev(c->V, N, mv, jp, w, N, c->K, c->h1, s));
-    SP_CK(kr_update_dots_dev(c->V, N, mv, jp, w, N, c->h1, c->K, c->h2, s));
-    SP_CK(kr_update_dots_dev(c->V, N, mv, jp, w, N, c->h2, c->K, nullptr, s));
-    SP_CK(kr_norm(w, N, c->K, c->nrm, s));
-    SP_CK(kr_givens_dev(c->H, mv, jp, c->h1, c->h2, c->nrm, c->cs, c->sn, c->gam, c->est, s));
-    SP_CK(kr_loop_step(c->loop, hist, c->est, c->nrm + 2, c->opts.tol, c->opts.maxit,
-                       c->opts.restart, cond, s));
-    SP_CK(kr_loop_scale(w, N, c->nrm, c->V, c->loop, s));
+    SP_CK(kb_copy_out(b, I, c->app_out, s));
+    SP_CK(fft_green_apply(c->fft, c->app_out, c->q, true, b.w, s, I, c->P));
+    SP_CK(kb_arnoldi(b, I, mv, s));
+    SP_CK(kb_step(b, I, c->hist, maxit, c->opts.tol, maxit, c->opts.restart, cond, s));
     return SP_OK;
   };
   SP_CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
@@ -368,8 +413,8 @@ sp_status build_loop_graph(sp_ctx* c) {
   e = cudaStreamEndCapture(s, &got);
   if (sb != SP_OK) return sb;
   SP_CK(e);
-  SP_CK(cudaGraphInstantiate(&c->g_loop, g, 0));
-  c->g_loop_q = c->q;
+  SP_CK(cudaGraphInstantiate(&c->g_cycle[R], g, 0));
+  c->g_cycle_q[R] = c->q;
   return SP_OK;
 }
 
@@ -579,16 +624,19 @@ void sp_destroy(sp_ctx* c) {
   for (auto& g : c->g_block)
     if (g) cudaGraphExecDestroy(g);
   if (c->g_factor) cudaGraphExecDestroy(c->g_factor);
-  if (c->g_loop) cudaGraphExecDestroy(c->g_loop);
-  if (c->host_loop) cudaFreeHost(c->host_loop);
+  for (auto& g : c->g_cycle)
+    if (g) cudaGraphExecDestroy(g);
+  if (c->host_heads) cudaFreeHost(c->host_heads);
+  if (c->host_hist) cudaFreeHost(c->host_hist);
+  if (c->host_run) cudaFreeHost(c->host_run);
   if (c->cap) cudaStreamDestroy(c->cap);
   cudaSetDevice(dev);
   delete c;
 }
 
-sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_opts* opts,
-                   void* stream, sp_ctx** out) {
-  if (!out) return SP_ERR_ARG;
+static sp_status setup_impl(int d, int n, int b, int P, const double* shifts, sp_precision prec,
+                            const sp_opts* opts, void* stream, sp_ctx** out) {
+  if (!out || !shifts || P < 1) return SP_ERR_ARG;
   *out = nullptr;
   int L;
   if (check_grid(d, n, b, &L)) return SP_ERR_ARG;
@@ -603,8 +651,12 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   const bool tc = (prec == SP_PREC_TF32 || prec == SP_PREC_TF32X3);
   const bool split = (prec == SP_PREC_TF32X3);
   if (mixed || tc) prec = SP_PREC_FP32;
-  if (!(std::isfinite(s))) return SP_ERR_ARG;
-  if (shift_gap(d, n, s) < 1e-6) return SP_ERR_RESONANT;
+  if (mixed && P > 1) return SP_ERR_ARG;
+  for (int p = 0; p < P; ++p) {
+    if (!(std::isfinite(shifts[p]))) return SP_ERR_ARG;
+    if (shift_gap(d, n, shifts[p]) < 1e-6) return SP_ERR_RESONANT;
+  }
+  const double s = shifts[0];
   std::unique_ptr<sp_ctx> c(new (std::nothrow) sp_ctx());
   if (!c) return SP_ERR_OOM;
   sp_default_opts(&c->opts);
@@ -625,6 +677,13 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   if (c->opts.launch_overlap != 0 && c->opts.launch_overlap != 1) return SP_ERR_ARG;
   if (c->opts.device_loop != 0 && c->opts.device_loop != 1) return SP_ERR_ARG;
   const size_t RH = (size_t)c->opts.max_rhs;
+  // every Krylov instance (right-hand side of a problem) is one thread of the batched
+  // stopping test
+  if ((size_t)P * RH > 1024) return SP_ERR_ARG;
+  c->P = P;
+  c->shifts.assign(shifts, shifts + P);
+  c->IM = (int)(P * RH);
+  const size_t IM = (size_t)c->IM;
   c->d = d;
   c->n = n;
   c->b = b;
@@ -644,17 +703,24 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   c->N = 1;
   for (int a = 0; a < d; ++a) c->N *= n;
   const long N = c->N;
+  c->NP = (long)P * N;
+  const long NP = c->NP;
   SP_CK(cudaSetDevice(c->opts.device));
   // ---- host set-up: Green's kernel, stencil tables, symbolic structure
   try {
-    std::vector<double> g = green_kernel(d, n, s), g2;
-    if (c->opts.setup_route == 1) g2 = green_kernel_sq(d, n, s);
-    c->tabs.resize(1 << d);
-    for (int t = 0; t < (1 << d); ++t)
-      if (stencil_table(d, n, b, t, g, c->opts.host_threads, &c->tabs[t],
-                        c->opts.setup_route == 1 ? &g2 : nullptr, c->opts.stencil))
-        return SP_ERR_ARG;
-    if (build_symbolic(d, n, b, c->tabs, &c->sym)) return SP_ERR_ARG;
+    // tables of every problem, problem-major (problem p's type t at p 2^d + t)
+    c->tabs.resize((size_t)P << d);
+    for (int p = 0; p < P; ++p) {
+      std::vector<double> g = green_kernel(d, n, shifts[p]), g2;
+      if (c->opts.setup_route == 1) g2 = green_kernel_sq(d, n, shifts[p]);
+      for (int t = 0; t < (1 << d); ++t)
+        if (stencil_table(d, n, b, t, g, c->opts.host_threads, &c->tabs[((size_t)p << d) + t],
+                          c->opts.setup_route == 1 ? &g2 : nullptr, c->opts.stencil))
+          return SP_ERR_ARG;
+    }
+    // the symbolic structure depends on the sets only (the same for every problem)
+    std::vector<StencilTable> t0(c->tabs.begin(), c->tabs.begin() + (1 << d));
+    if (build_symbolic(d, n, b, t0, &c->sym)) return SP_ERR_ARG;
   } catch (const std::bad_alloc&) {
     return SP_ERR_OOM;
   }
@@ -663,9 +729,12 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   {
     std::vector<double> Qc, Cc, Tc;
     std::vector<float> T32;
+    // problem after problem (all have the same table shapes): the offsets of the
+    // first problem address every problem's tables, tab_stride / t_stride apart
     long off = 0, toff = 0;
-    for (int t = 0; t < (1 << d); ++t) {
-      const StencilTable& tb = c->tabs[t];
+    for (int pt = 0; pt < (P << d); ++pt) {
+      const int t = pt & ((1 << d) - 1);
+      const StencilTable& tb = c->tabs[pt];
       QTypeDev qt;
       qt.nS = tb.nS;
       qt.nG = tb.nG;
@@ -706,6 +775,11 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
         }
       off += (long)tb.nS * tb.nG;
       toff += (long)tb.nS * qt.na;
+      if (pt == (1 << d) - 1) {
+        c->work.tab_stride = off;
+        c->t_stride = toff;
+      }
+      if (pt != t) continue;
       SP_CK(upload(c.get(), &qt.S, tb.S));
       SP_CK(upload(c.get(), &qt.G, tb.G));
       SP_CK(upload(c.get(), &qt.Bt, tb.Bt));
@@ -728,29 +802,38 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   for (int l = 0; l <= L; ++l) {
     const Level& S = c->sym.lv[l];
     DevLevel& D = c->lv[l];
-    D.nf = S.nf;
+    D.nfp = S.nf;
+    D.nf = P * S.nf;
     D.k = S.k;
     D.m = S.m;
     D.nb1 = S.nb1;
     D.mc = S.mc;
     D.kc = S.kc;
     D.nasm = (int)S.asm_row.size();
-    SP_CK(upload(c.get(), &D.gidx, S.gidx));
+    if (P == 1) {
+      SP_CK(upload(c.get(), &D.gidx, S.gidx));
+    } else {  // problem p's fronts index its vector segment [p N, (p + 1) N)
+      std::vector<int> gg;
+      gg.reserve(S.gidx.size() * P);
+      for (int p = 0; p < P; ++p)
+        for (int v : S.gidx) gg.push_back(v + (int)((long)p * N));
+      SP_CK(upload(c.get(), &D.gidx, gg));
+    }
     SP_CK(upload(c.get(), &D.asm_row, S.asm_row));
     SP_CK(upload(c.get(), &D.asm_tidx, S.asm_tidx));
     SP_CK(upload(c.get(), &D.asm_cvar, S.asm_cvar));
     SP_CK(upload(c.get(), &D.ea_map, S.ea_map));
-    SP_CK(dalloc(c.get(), &D.front, fsz * (size_t)S.nf * S.m * S.m));
-    SP_CK(dalloc(c.get(), &D.perm, sizeof(int) * (size_t)S.nf * std::max(1, S.k)));
-    SP_CK(dalloc(c.get(), &D.piv, sizeof(int) * (size_t)S.nf * std::max(1, S.k)));
-    SP_CK(dalloc(c.get(), &D.scale, sizeof(double) * S.nf));
-    SP_CK(dalloc(c.get(), &D.upd, vsz * RH * (size_t)S.nf * std::max(1, S.m - S.k)));
-    SP_CK(dalloc(c.get(), &D.y, vsz * RH * (size_t)S.nf * std::max(1, S.k)));
+    SP_CK(dalloc(c.get(), &D.front, fsz * (size_t)D.nf * S.m * S.m));
+    SP_CK(dalloc(c.get(), &D.perm, sizeof(int) * (size_t)D.nf * std::max(1, S.k)));
+    SP_CK(dalloc(c.get(), &D.piv, sizeof(int) * (size_t)D.nf * std::max(1, S.k)));
+    SP_CK(dalloc(c.get(), &D.scale, sizeof(double) * D.nf));
+    SP_CK(dalloc(c.get(), &D.upd, vsz * RH * (size_t)D.nf * std::max(1, S.m - S.k)));
+    SP_CK(dalloc(c.get(), &D.y, vsz * RH * (size_t)D.nf * std::max(1, S.k)));
     if (factor_panel_width(prec, S.m) == 0) return SP_ERR_ARG;  // front too large to stage
     // few fronts: keep the inverses of the diagonal blocks of L11 and U11 so the
     // sweeps spread over the GPU; in the FP32 form every level does (the block
     // inverses cost little in FP32 and the sweeps become matrix-vector products)
-    D.inv = S.nf < 152 || prec == SP_PREC_FP32 || vsz * (size_t)(S.m + S.k) > 192 * 1024;
+    D.inv = D.nf < 152 || prec == SP_PREC_FP32 || vsz * (size_t)(S.m + S.k) > 192 * 1024;
     // block inverses: 2048-wide blocks where the fronts are huge (the sweeps of the 3D
     // root become 48 instead of 189 launch pairs; measured 3D 128^3 TF32: sweeps
     // 1.95 -> 1.51 s per solve for +0.1 s of inversion), 512 elsewhere (in 2D the
@@ -759,22 +842,22 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
     D.pdl = c->opts.launch_overlap;
     if (D.inv && c->opts.sweeps != 1) {
       int C = 0, NT = 0;
-      if (sweep_fused_config(prec, S.nf, S.m, S.k, num_sms, max_cluster, c->opts.sweeps == 2, &C,
+      if (sweep_fused_config(prec, D.nf, S.m, S.k, num_sms, max_cluster, c->opts.sweeps == 2, &C,
                              &NT)) {
         D.fused_c = C;
         D.fused_nt = NT;
       }
     }
     if (D.inv) {
-      SP_CK(dalloc(c.get(), &D.tmp, vsz * RH * (size_t)S.nf * S.m));
-      scratch_bytes = std::max(scratch_bytes, fsz * invert_scratch_elems(S.nf, S.k, D.ib));
+      SP_CK(dalloc(c.get(), &D.tmp, vsz * RH * (size_t)D.nf * S.m));
+      scratch_bytes = std::max(scratch_bytes, fsz * invert_scratch_elems(D.nf, S.k, D.ib));
     }
-    if (factor_grid_panel(prec, S.m)) gp_words = std::max(gp_words, grid_panel_pub_words(S.nf));
+    if (factor_grid_panel(prec, S.m)) gp_words = std::max(gp_words, grid_panel_pub_words(D.nf));
     if (factor_outer_block(prec, tc, S.m, S.k) > 0)
-      pack_floats = std::max(pack_floats, tc_pack_floats(S.m, kTcMaxK, S.nf, split));
+      pack_floats = std::max(pack_floats, tc_pack_floats(S.m, kTcMaxK, D.nf, split));
     double k = S.k, mk = S.m - S.k;
-    c->factor_entries += S.nf * (k * k + 2 * k * mk);
-    c->factor_flops += S.nf * ((2.0 / 3.0) * k * k * k + 2 * k * k * mk + 2 * k * mk * mk);
+    c->factor_entries += D.nf * (k * k + 2 * k * mk);
+    c->factor_flops += D.nf * ((2.0 / 3.0) * k * k * k + 2 * k * k * mk + 2 * k * mk * mk);
   }
   c->apply_bytes = c->factor_entries * fsz;
   if (scratch_bytes) SP_CK(dalloc(c.get(), &c->work.inv, scratch_bytes));
@@ -797,20 +880,21 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
       tw[t] = make_double2(std::cos(a), -std::sin(a));
     }
     SP_CK(upload(c.get(), &P.tw, tw));
-    std::vector<double> Dn(N);
-    for (long j = 0; j < N; ++j) {
-      long r = j;
-      double k2 = 0;
-      for (int a = 0; a < d; ++a) {
-        int i = (int)(r % n);
-        r /= n;
-        int k = i < n / 2 ? i : i - n;
-        k2 += (double)k * k;
+    std::vector<double> Dn(NP);
+    for (int p = 0; p < c->P; ++p)
+      for (long j = 0; j < N; ++j) {
+        long r = j;
+        double k2 = 0;
+        for (int a = 0; a < d; ++a) {
+          int i = (int)(r % n);
+          r /= n;
+          int k = i < n / 2 ? i : i - n;
+          k2 += (double)k * k;
+        }
+        Dn[p * N + j] = 1.0 / (4.0 * kPi * kPi * k2 - shifts[p]) / (double)N;
       }
-      Dn[j] = 1.0 / (4.0 * kPi * kPi * k2 - s) / (double)N;
-    }
     SP_CK(upload(c.get(), &P.Dn, Dn));
-    SP_CK(dalloc(c.get(), &P.tmp, sizeof(double2) * N * RH));
+    SP_CK(dalloc(c.get(), &P.tmp, sizeof(double2) * N * IM));
     if (mixed) {
       std::vector<float2> tw32(tw.size());
       for (size_t i = 0; i < tw.size(); ++i) tw32[i] = make_float2((float)tw[i].x, (float)tw[i].y);
@@ -824,38 +908,41 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   }
   // ---- solve workspace
   c->maxv = c->opts.restart + 1;
-  SP_CK(dalloc(c.get(), &c->rhsQ, vsz * N * RH));
+  SP_CK(dalloc(c.get(), &c->rhsQ, vsz * NP * RH));
   SP_CK(dalloc(c.get(), &c->status, sizeof(int)));
-  SP_CK(dalloc(c.get(), &c->qbuf, sizeof(double) * N));
-  // Krylov workspace, one slice per right-hand side of sp_solve_many (slice 0 is
-  // sp_solve's)
-  SP_CK(dalloc(c.get(), &c->V, sizeof(double2) * N * c->maxv * RH));
-  SP_CK(dalloc(c.get(), &c->Z, sizeof(double2) * N * c->opts.restart * RH));
-  SP_CK(dalloc(c.get(), &c->H, sizeof(double2) * c->maxv * c->opts.restart * RH));
-  SP_CK(dalloc(c.get(), &c->gam, sizeof(double2) * (c->maxv + 1) * RH));
-  SP_CK(dalloc(c.get(), &c->sn, sizeof(double2) * (c->maxv + 1) * RH));
-  SP_CK(dalloc(c.get(), &c->cs, sizeof(double) * (c->maxv + 1) * RH));
-  SP_CK(dalloc(c.get(), &c->h1, sizeof(double2) * 1024 * RH));
-  SP_CK(dalloc(c.get(), &c->h2, sizeof(double2) * 1024 * RH));
-  SP_CK(dalloc(c.get(), &c->y, sizeof(double2) * 1024 * RH));
-  SP_CK(dalloc(c.get(), &c->nrm, sizeof(double) * 4 * RH));
-  SP_CK(dalloc(c.get(), &c->est, sizeof(double) * 4 * RH));
-  SP_CK(dalloc(c.get(), &c->g, sizeof(double2) * N * RH));
-  SP_CK(dalloc(c.get(), &c->r, sizeof(double2) * N * RH));
-  SP_CK(dalloc(c.get(), &c->t, sizeof(double2) * N * RH));
-  SP_CK(dalloc(c.get(), &c->fbuf, sizeof(double2) * N));
-  SP_CK(dalloc(c.get(), &c->ubuf, sizeof(double2) * N));
+  SP_CK(dalloc(c.get(), &c->qbuf, sizeof(double) * NP));
+  // Krylov workspace, one slice per instance (right-hand side r of problem p: slice
+  // r P + p; slice 0 is sp_solve's on a single-problem context)
+  SP_CK(dalloc(c.get(), &c->V, sizeof(double2) * N * c->maxv * IM));
+  SP_CK(dalloc(c.get(), &c->Z, sizeof(double2) * N * c->opts.restart * IM));
+  SP_CK(dalloc(c.get(), &c->H, sizeof(double2) * c->maxv * c->opts.restart * IM));
+  SP_CK(dalloc(c.get(), &c->gam, sizeof(double2) * (c->maxv + 1) * IM));
+  SP_CK(dalloc(c.get(), &c->sn, sizeof(double2) * (c->maxv + 1) * IM));
+  SP_CK(dalloc(c.get(), &c->cs, sizeof(double) * (c->maxv + 1) * IM));
+  SP_CK(dalloc(c.get(), &c->h1, sizeof(double2) * 1024 * IM));
+  SP_CK(dalloc(c.get(), &c->h2, sizeof(double2) * 1024 * IM));
+  SP_CK(dalloc(c.get(), &c->y, sizeof(double2) * 1024 * IM));
+  SP_CK(dalloc(c.get(), &c->nrm, sizeof(double) * 4 * IM));
+  SP_CK(dalloc(c.get(), &c->est, sizeof(double) * 4 * IM));
+  SP_CK(dalloc(c.get(), &c->g, sizeof(double2) * N * IM));
+  SP_CK(dalloc(c.get(), &c->r, sizeof(double2) * N * IM));
+  SP_CK(dalloc(c.get(), &c->t, sizeof(double2) * N * IM));
+  SP_CK(dalloc(c.get(), &c->fbuf, sizeof(double2) * NP));
+  SP_CK(dalloc(c.get(), &c->ubuf, sizeof(double2) * N * IM));
   c->K.nblk = (int)std::min<long>(304, std::max<long>(1, (N + 1023) / 1024));
-  SP_CK(dalloc(c.get(), &c->K.partial, sizeof(double2) * (size_t)c->K.nblk * 1024));
+  SP_CK(dalloc(c.get(), &c->K.partial, sizeof(double2) * (size_t)c->K.nblk * 1024 * IM));
   SP_CK(dalloc(c.get(), &c->K.h, sizeof(double2) * 1024));
-  SP_CK(cudaMallocHost(&c->host_sc, 8 * sizeof(double) * RH));
-  c->loop_bytes = sizeof(LoopHead) + sizeof(double) * (size_t)c->opts.maxit;
-  SP_CK(dalloc(c.get(), &c->loop, c->loop_bytes));
-  SP_CK(cudaMallocHost(&c->host_loop, c->loop_bytes));
-  SP_CK(dalloc(c.get(), &c->app_in, sizeof(double2) * N * RH));
-  SP_CK(dalloc(c.get(), &c->app_out, sizeof(double2) * N * RH));
-  if (RH > 1) SP_CK(dalloc(c.get(), &c->blk_w, sizeof(double2) * N * RH));
-  SP_CK(cudaMemsetAsync(c->qbuf, 0, sizeof(double) * N, c->stream));
+  SP_CK(cudaMallocHost(&c->host_sc, 8 * sizeof(double) * IM));
+  SP_CK(dalloc(c.get(), &c->heads, sizeof(LoopHead) * IM));
+  SP_CK(dalloc(c.get(), &c->hist, sizeof(double) * c->opts.maxit * IM));
+  SP_CK(dalloc(c.get(), &c->run, sizeof(int) * IM));
+  SP_CK(cudaMallocHost(&c->host_heads, sizeof(LoopHead) * IM));
+  SP_CK(cudaMallocHost(&c->host_hist, sizeof(double) * c->opts.maxit * IM));
+  SP_CK(cudaMallocHost(&c->host_run, sizeof(int) * IM));
+  SP_CK(dalloc(c.get(), &c->app_in, sizeof(double2) * N * IM));
+  SP_CK(dalloc(c.get(), &c->app_out, sizeof(double2) * N * IM));
+  if (IM > 1) SP_CK(dalloc(c.get(), &c->blk_w, sizeof(double2) * N * IM));
+  SP_CK(cudaMemsetAsync(c->qbuf, 0, sizeof(double) * NP, c->stream));
   // only this context's streams are synchronised: a device-wide synchronisation
   // would break a graph capture that another thread's context has in progress
   SP_CK(cudaStreamSynchronize(c->stream));
@@ -881,6 +968,22 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
   return SP_OK;
 }
 
+sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_opts* opts,
+                   void* stream, sp_ctx** out) {
+  return setup_impl(d, n, b, 1, &s, prec, opts, stream, out);
+}
+
+sp_status sp_setup_group(int d, int n, int b, int P, const double* shifts, sp_precision prec,
+                         const sp_opts* opts, void* stream, sp_ctx** out) {
+  return setup_impl(d, n, b, P, shifts, prec, opts, stream, out);
+}
+
+sp_status sp_problems(const sp_ctx* c, int* P) {
+  if (!c || !P) return SP_ERR_ARG;
+  *P = c->P;
+  return SP_OK;
+}
+
 sp_status sp_factor(sp_ctx* c, const double* q_dev) {
   if (!c || !q_dev) return SP_ERR_ARG;
   ProfGuard pg_(c);
@@ -889,7 +992,7 @@ sp_status sp_factor(sp_ctx* c, const double* q_dev) {
   c->factored = false;
   // the context keeps its own copy of q: the factor graph and the operator read it
   if (q_dev != c->qbuf)
-    SP_CK(cudaMemcpyAsync(c->qbuf, q_dev, sizeof(double) * c->N, cudaMemcpyDeviceToDevice, st));
+    SP_CK(cudaMemcpyAsync(c->qbuf, q_dev, sizeof(double) * c->NP, cudaMemcpyDeviceToDevice, st));
   c->q = c->qbuf;
   if (c->g_factor && !c->profiling) {
     SP_CK(cudaGraphLaunch(c->g_factor, st));
@@ -910,7 +1013,7 @@ sp_status sp_factor(sp_ctx* c, const double* q_dev) {
 sp_status sp_factor_host(sp_ctx* c, const double* q_host) {
   if (!c || !q_host) return SP_ERR_ARG;
   SP_CK(cudaSetDevice(c->opts.device));
-  SP_CK(cudaMemcpyAsync(c->qbuf, q_host, sizeof(double) * c->N, cudaMemcpyHostToDevice, c->stream));
+  SP_CK(cudaMemcpyAsync(c->qbuf, q_host, sizeof(double) * c->NP, cudaMemcpyHostToDevice, c->stream));
   return sp_factor(c, c->qbuf);
 }
 
@@ -928,7 +1031,8 @@ sp_status sp_qapply(sp_ctx* c, const void* r_dev, void* y_dev) {
   SP_CK(cudaSetDevice(c->opts.device));
   // always the FP64 tables: the output is complex128 in both forms
   return cuda_status(q_apply(SP_PREC_FP64, c->d, c->n, c->nl, c->qtypes, c->Tcat, c->Tcat32,
-                             (const double2*)r_dev, y_dev, c->stream));
+                             (const double2*)r_dev, y_dev, c->stream, 1, false, c->P,
+                             c->t_stride));
 }
 
 sp_status sp_matvec(sp_ctx* c, const void* x_dev, void* w_dev) {
@@ -936,14 +1040,16 @@ sp_status sp_matvec(sp_ctx* c, const void* x_dev, void* w_dev) {
   ProfGuard pg_(c);
   if (!c->q) return SP_ERR_STATE;
   SP_CK(cudaSetDevice(c->opts.device));
-  return cuda_status(fft_green_apply(c->fft, (const double2*)x_dev, c->q, true, (double2*)w_dev, c->stream));
+  return cuda_status(fft_green_apply(c->fft, (const double2*)x_dev, c->q, true, (double2*)w_dev,
+                                     c->stream, c->P, c->P));
 }
 
 sp_status sp_green(sp_ctx* c, const void* f_dev, void* g_dev) {
   if (!c || !f_dev || !g_dev) return SP_ERR_ARG;
   ProfGuard pg_(c);
   SP_CK(cudaSetDevice(c->opts.device));
-  return cuda_status(fft_green_apply(c->fft, (const double2*)f_dev, nullptr, false, (double2*)g_dev, c->stream));
+  return cuda_status(fft_green_apply(c->fft, (const double2*)f_dev, nullptr, false,
+                                     (double2*)g_dev, c->stream, c->P, c->P));
 }
 
 static sp_status solve_mixed(sp_ctx* c, const double2* f, const double2* u0, double2* u,
@@ -994,66 +1100,115 @@ static sp_status solve_start(sp_ctx* c, const double2* f, const double2* u0, dou
   return SP_OK;
 }
 
-// sp_solve with the restart cycles run by the graph of build_loop_graph: the host
-// waits once per cycle (the true residual decides about a restart) instead of once
-// per iteration.  Same kernels in the same order as solve_impl's loop: the same bits.
-static sp_status solve_loop(sp_ctx* c, const double2* f, const double2* u0, double2* u,
-                            sp_info* info) {
+// R right-hand sides of every problem of the context (R P instances; instance
+// i = r P + p, right-hand side r of problem p, at offset i N of F and U) through the
+// cycle graph of build_cycle_graph: the host waits once per restart cycle, where the
+// true residuals decide which instances restart.  u0 (one instance only): the start
+// of sp_solve_x0.  Every instance runs the kernels of the host-driven iteration with
+// the same operands, so its result is bit-identical to that iteration's for its
+// right-hand side and problem.
+static sp_status solve_batch(sp_ctx* c, int R, const double2* F, const double2* u0, double2* U,
+                             sp_info* infos) {
   cudaStream_t st = c->stream;
   const long N = c->N;
+  const int I = R * c->P;
   const double tol = c->opts.tol;
   const int maxit = c->opts.maxit;
-  auto push_hist = [&](double v) {
-    if (info && info->hist && info->hist_len < info->hist_cap) info->hist[info->hist_len++] = v;
-  };
-  if (!c->g_loop || c->g_loop_q != c->q) {
+  if (R < 1 || R > c->opts.max_rhs || (u0 && I != 1)) return SP_ERR_ARG;
+  if (!c->g_cycle[R] || c->g_cycle_q[R] != c->q) {
     SP_CK(cudaStreamSynchronize(st));
-    sp_status bs = build_loop_graph(c);
+    sp_status bs = build_cycle_graph(c, R);
     if (bs != SP_OK) return bs;
   }
+  const KBatch b = make_batch(c);
   double2* uw = c->ubuf;
-  double bnorm = 0.0, rel0 = 1.0;
-  sp_status s0 = solve_start(c, f, u0, uw, &bnorm, &rel0, info);
-  if (s0 != SP_OK) return s0;
-  push_hist(rel0);
-  if (bnorm == 0.0) {
-    SP_CK(cudaMemsetAsync(u, 0, sizeof(double2) * N, st));
+  std::vector<double> bnorm(I, 0.0), rel0(I, 1.0);
+  if (u0) {
+    sp_status s0 = solve_start(c, F, u0, uw, &bnorm[0], &rel0[0], infos);
+    if (s0 != SP_OK) return s0;
+  } else {
+    if (infos)
+      for (int i = 0; i < I; ++i) {
+        infos[i].iters = 0;
+        infos[i].restarts = 0;
+        infos[i].hist_len = 0;
+        infos[i].s_used = c->shifts[i % c->P];
+        infos[i].guess_relres = 1.0;
+        infos[i].guess_used = 0;
+      }
+    // g_i = G_p f_i, ||g_i||; u = 0, r = g
+    SP_CK(fft_green_apply(c->fft, F, nullptr, false, c->g, st, I, c->P));
+    SP_CK(kb_norm(b, I, c->g, 2, st));
+    SP_CK(cudaMemsetAsync(uw, 0, sizeof(double2) * N * I, st));
+    SP_CK(cudaMemcpyAsync(c->r, c->g, sizeof(double2) * N * I, cudaMemcpyDeviceToDevice, st));
+    SP_CK(kb_copy_nrm(b, I, 2, 3, st));
+    SP_CK(cudaMemcpy2DAsync(c->host_sc, sizeof(double), c->nrm + 2, 4 * sizeof(double),
+                            sizeof(double), I, cudaMemcpyDeviceToHost, st));
     SP_CK(cudaStreamSynchronize(st));
-    if (info) info->true_relres = info->est_relres = 0.0;
-    return SP_OK;
+    for (int i = 0; i < I; ++i) bnorm[i] = c->host_sc[i];
   }
-  int total = 0, restarts = 0;
-  double est_rel = rel0, true_rel = rel0;
-  if (rel0 > tol) {
-    SP_CK(cudaMemsetAsync(c->loop, 0, sizeof(LoopHead), st));
-    for (;;) {
-      SP_CK(cudaGraphLaunch(c->g_loop, st));
-      SP_CK(cudaStreamSynchronize(st));
-      const LoopHead& h = *c->host_loop;
-      const double* hh = reinterpret_cast<const double*>(c->host_loop + 1);
-      for (int i = total; i < h.total && i < maxit; ++i) push_hist(hh[i]);
-      total = h.total;
-      est_rel = h.est_rel;
-      true_rel = h.rnorm / bnorm;
-      if (true_rel <= tol || total >= maxit) break;
-      ++restarts;
+  auto push = [&](int i, double v) {
+    sp_info* in = infos ? infos + i : nullptr;
+    if (in && in->hist && in->hist_len < in->hist_cap) in->hist[in->hist_len++] = v;
+  };
+  std::vector<int> total(I, 0), restarts(I, 0);
+  std::vector<double> est(I), tr(I);
+  int nrun = 0;
+  for (int i = 0; i < I; ++i) {
+    push(i, rel0[i]);
+    est[i] = tr[i] = rel0[i];
+    int run = 0;
+    if (bnorm[i] == 0.0) {
+      est[i] = tr[i] = 0.0;
+      SP_CK(cudaMemsetAsync(uw + i * N, 0, sizeof(double2) * N, st));
+    } else if (rel0[i] > tol) {
+      run = 1;
+      ++nrun;
+    }
+    c->host_run[i] = run;
+  }
+  if (nrun) SP_CK(cudaMemsetAsync(c->heads, 0, sizeof(LoopHead) * I, st));
+  while (nrun) {
+    SP_CK(cudaMemcpyAsync(c->run, c->host_run, sizeof(int) * I, cudaMemcpyHostToDevice, st));
+    SP_CK(cudaGraphLaunch(c->g_cycle[R], st));
+    SP_CK(cudaStreamSynchronize(st));
+    nrun = 0;
+    for (int i = 0; i < I; ++i) {
+      if (!c->host_run[i]) continue;
+      const LoopHead& h = c->host_heads[i];
+      for (int t = total[i]; t < h.total && t < maxit; ++t)
+        push(i, c->host_hist[(long)i * maxit + t]);
+      total[i] = h.total;
+      est[i] = h.est_rel;
+      tr[i] = h.rnorm / bnorm[i];
+      if (tr[i] <= tol || total[i] >= maxit) {
+        c->host_run[i] = 0;
+      } else {
+        ++restarts[i];
+        ++nrun;
+      }
     }
   }
-  if (u != uw) SP_CK(cudaMemcpyAsync(u, uw, sizeof(double2) * N, cudaMemcpyDeviceToDevice, st));
+  if (U != uw) SP_CK(cudaMemcpyAsync(U, uw, sizeof(double2) * N * I, cudaMemcpyDeviceToDevice, st));
   SP_CK(cudaStreamSynchronize(st));
-  if (info) {
-    info->iters = total;
-    info->restarts = restarts;
-    info->est_relres = est_rel;
-    info->true_relres = true_rel;
+  bool all = true;
+  for (int i = 0; i < I; ++i) {
+    if (infos) {
+      infos[i].iters = total[i];
+      infos[i].restarts = restarts[i];
+      infos[i].est_relres = est[i];
+      infos[i].true_relres = tr[i];
+    }
+    if (!(tr[i] <= tol)) all = false;
   }
-  return true_rel <= tol ? SP_OK : SP_ERR_NOCONV;
+  return all ? SP_OK : SP_ERR_NOCONV;
 }
 
 static sp_status solve_impl(sp_ctx* c, const double2* f, const double2* u0, double2* u,
                             sp_info* info) {
   if (c->mixed) return solve_mixed(c, f, u0, u, info);
-  if (c->opts.device_loop && !c->profiling) return solve_loop(c, f, u0, u, info);
+  if (c->P > 1 || (c->opts.device_loop && !c->profiling))
+    return solve_batch(c, 1, f, u0, u, info);
   cudaStream_t st = c->stream;
   const long N = c->N;
   double* hsc = c->host_sc;
@@ -1133,7 +1288,7 @@ sp_status sp_solve(sp_ctx* c, const void* f_dev, void* u_dev, sp_info* info) {
 }
 
 sp_status sp_solve_x0(sp_ctx* c, const void* f_dev, const void* u0_dev, void* u_dev, sp_info* info) {
-  if (!c || !f_dev || !u_dev) return SP_ERR_ARG;
+  if (!c || !f_dev || !u_dev || (u0_dev && c->P > 1)) return SP_ERR_ARG;
   ProfGuard pg_(c);
   if (!c->factored) return SP_ERR_STATE;
   SP_CK(cudaSetDevice(c->opts.device));
@@ -1221,17 +1376,6 @@ static sp_status solve_mixed(sp_ctx* c, const double2* f, const double2* u0, dou
 
 // z = P^{-1} Q r for nv stacked vectors (direct launches; each vector's result
 // equals apply_direct's for it)
-static sp_status apply_block(sp_ctx* c, int nv, const double2* r, double2* z, cudaStream_t st) {
-  SP_CK(q_apply(c->prec, c->d, c->n, c->nl, c->qtypes, c->Tcat, c->Tcat32, r, c->rhsQ, st, nv,
-                c->opts.launch_overlap != 0));
-  for (int l = 0; l <= c->L; ++l)
-    SP_CK(forward_level(c->prec, c->d, c->lv[l], l ? &c->lv[l - 1] : nullptr, c->rhsQ,
-                        c->gemv_part, st, nv, c->N));
-  for (int l = c->L; l >= 0; --l)
-    SP_CK(backward_level(c->prec, c->d, c->lv[l], z, c->gemv_part, st, nv, c->N));
-  return SP_OK;
-}
-
 sp_status sp_solve_many(sp_ctx* c, int nrhs, const void* F_dev, void* U_dev, sp_info* infos) {
   if (!c || !F_dev || !U_dev || nrhs < 1 || nrhs > c->opts.max_rhs) return SP_ERR_ARG;
   if (!c->factored) return SP_ERR_STATE;
@@ -1239,6 +1383,10 @@ sp_status sp_solve_many(sp_ctx* c, int nrhs, const void* F_dev, void* U_dev, sp_
   const long N = c->N;
   const double2* F = (const double2*)F_dev;
   double2* U = (double2*)U_dev;
+  if (!c->mixed && (c->P > 1 || (c->opts.device_loop && !c->profiling))) {
+    ProfGuard pg_(c);
+    return solve_batch(c, nrhs, F, nullptr, U, infos);
+  }
   if (c->mixed || nrhs == 1) {
     sp_status worst = SP_OK;
     for (int r = 0; r < nrhs; ++r) {
@@ -1402,10 +1550,10 @@ sp_status sp_solve_many(sp_ctx* c, int nrhs, const void* F_dev, void* U_dev, sp_
 sp_status sp_solve_host(sp_ctx* c, const void* f_host, void* u_host, sp_info* info) {
   if (!c || !f_host || !u_host) return SP_ERR_ARG;
   SP_CK(cudaSetDevice(c->opts.device));
-  SP_CK(cudaMemcpyAsync(c->fbuf, f_host, sizeof(double2) * c->N, cudaMemcpyHostToDevice, c->stream));
+  SP_CK(cudaMemcpyAsync(c->fbuf, f_host, sizeof(double2) * c->NP, cudaMemcpyHostToDevice, c->stream));
   sp_status st = sp_solve(c, c->fbuf, c->ubuf, info);
   if (st != SP_OK && st != SP_ERR_NOCONV) return st;
-  SP_CK(cudaMemcpyAsync(u_host, c->ubuf, sizeof(double2) * c->N, cudaMemcpyDeviceToHost, c->stream));
+  SP_CK(cudaMemcpyAsync(u_host, c->ubuf, sizeof(double2) * c->NP, cudaMemcpyDeviceToHost, c->stream));
   SP_CK(cudaStreamSynchronize(c->stream));
   return st;
 }
@@ -1483,10 +1631,12 @@ sp_status sp_get_table(const sp_ctx* c, int t, double* Q_out, double* C_out, int
 }
 
 sp_status sp_set_table(sp_ctx* c, int t, const double* Q_in, const double* C_in) {
-  if (!c || t < 0 || t >= (int)c->tabs.size() || t >= (int)c->qtypes.size() || !Q_in || !C_in)
-    return SP_ERR_ARG;
+  if (!c || t < 0 || t >= (int)c->tabs.size() || !Q_in || !C_in) return SP_ERR_ARG;
   StencilTable& tb = c->tabs[t];
-  const QTypeDev& qt = c->qtypes[t];
+  // table t of a group: problem t / 2^d, type t mod 2^d
+  const long pg = t >> c->d;
+  const QTypeDev& qt = c->qtypes[t & ((1 << c->d) - 1)];
+  const long toff = qt.tab_off + pg * c->work.tab_stride, tt_off = qt.t_off + pg * c->t_stride;
   const size_t ne = (size_t)tb.nS * tb.nG;
   for (size_t e = 0; e < ne; ++e)
     if (!std::isfinite(Q_in[e]) || !std::isfinite(C_in[e])) return SP_ERR_ARG;
@@ -1531,11 +1681,11 @@ sp_status sp_set_table(sp_ctx* c, int t, const double* Q_in, const double* C_in)
     }
   SP_CK(cudaSetDevice(c->opts.device));
   cudaStream_t st = c->stream;
-  SP_CK(cudaMemcpyAsync(c->Qcat + qt.tab_off, Qc.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, st));
-  SP_CK(cudaMemcpyAsync(c->Ccat + qt.tab_off, Cc.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, st));
-  SP_CK(cudaMemcpyAsync(c->Tcat + qt.t_off, Tc.data(), sizeof(double) * Tc.size(),
+  SP_CK(cudaMemcpyAsync(c->Qcat + toff, Qc.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, st));
+  SP_CK(cudaMemcpyAsync(c->Ccat + toff, Cc.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, st));
+  SP_CK(cudaMemcpyAsync(c->Tcat + tt_off, Tc.data(), sizeof(double) * Tc.size(),
                         cudaMemcpyHostToDevice, st));
-  SP_CK(cudaMemcpyAsync(c->Tcat32 + qt.t_off, T32.data(), sizeof(float) * T32.size(),
+  SP_CK(cudaMemcpyAsync(c->Tcat32 + tt_off, T32.data(), sizeof(float) * T32.size(),
                         cudaMemcpyHostToDevice, st));
   SP_CK(cudaStreamSynchronize(st));
   tb.Q.assign(Q_in, Q_in + ne);

@@ -37,11 +37,13 @@ template <class T>
 __global__ void assemble_kernel(T* fronts, int m, int nasm, const int* __restrict__ row,
                                 const int* __restrict__ tidx, const int* __restrict__ cvar,
                                 const int* __restrict__ gidx, const double* __restrict__ Qcat,
-                                const double* __restrict__ Ccat, const double* __restrict__ q) {
+                                const double* __restrict__ Ccat, const double* __restrict__ q,
+                                int nfp, long tstride) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nasm) return;
   long f = blockIdx.y;
-  int ti = tidx[e];
+  // fronts of a problem group: problem f / nfp reads its own tables (tstride apart)
+  const long ti = tidx[e] + (f / nfp) * tstride;
   const int c = cvar[e];
   double qi = q[gidx[f * m + c]];
   fronts[f * (long)m * m + row[e] + (long)c * m] = (T)fma(Ccat[ti], qi, Qcat[ti]);
@@ -62,6 +64,7 @@ __global__ void extend_add_kernel(T* parent, int m, int nb1, const T* __restrict
     cid += (2 * bc + ((delta >> a) & 1)) * stride;
     stride *= 2 * nb1;
   }
+  cid += ff * stride;  // problem ff of a group: its children follow the earlier problems'
   int i = (int)(e % nbd), j = (int)(e / nbd);
   const T v = child[(long)cid * mc * mc + (long)(kc + i) + (long)(kc + j) * mc];
   parent[(long)f * m * m + map[i] + (long)map[j] * m] += v;
@@ -1460,7 +1463,8 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
   if (L.nasm > 0) {
     dim3 g((L.nasm + 255) / 256, L.nf);
     assemble_kernel<T><<<g, 256, 0, st>>>(F, L.m, L.nasm, L.asm_row, L.asm_tidx, L.asm_cvar,
-                                          L.gidx, Qcat, Ccat, q);
+                                          L.gidx, Qcat, Ccat, q, L.nfp > 0 ? L.nfp : L.nf,
+                                          W.tab_stride);
     ++na;
   }
   double abytes = (double)sizeof(T) * mm * L.nf;

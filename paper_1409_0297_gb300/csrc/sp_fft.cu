@@ -62,6 +62,7 @@ struct PassArgs {
   int n, W, pad;
   int R, M, logM;       // n = R M, R in {1, 3}, M = 2^logM
   int mode;             // 0 forward, 1 inverse, 2 middle (forward, scale, inverse)
+  int qper;             // q and Dn per vector: vector v reads those of v % qper (vstride apart)
 };
 
 // position in the staged row of element i of a line in permuted (DIT input /
@@ -315,7 +316,7 @@ __global__ void __launch_bounds__(kThreads) fft_pass_kernel(PassArgs<VT> a) {
     long g = line_addr(a, t, i);
     VT v = a.in[vec_off(a, t) + g];
     if (a.q) {
-      T qq = a.q[g];
+      T qq = a.q[(a.qper > 1 ? (t / a.vlines) % a.qper * a.vstride : 0) + g];
       v.x *= qq;
       v.y *= qq;
     }
@@ -343,7 +344,7 @@ __global__ void __launch_bounds__(kThreads) fft_pass_kernel(PassArgs<VT> a) {
       }
       long t = t0 + w;
       if (t >= a.nlines) continue;
-      T dn = a.Dn[line_addr(a, t, i)];
+      T dn = a.Dn[(a.qper > 1 ? (t / a.vlines) % a.qper * a.vstride : 0) + line_addr(a, t, i)];
       VT* p = &sm[w * ld + i];
       p->x *= dn;
       p->y *= dn;
@@ -385,9 +386,10 @@ int lines_per_cta(int n, long nlines, int esize) {
 template <class VT>
 cudaError_t run_pass(int d, int n, const VT* tw, const typename Real<VT>::T* Dn, int axis,
                      int mode, const VT* in, VT* out, const typename Real<VT>::T* q,
-                     const VT* addx, int nvec, cudaStream_t st) {
+                     const VT* addx, int nvec, int qper, cudaStream_t st) {
   PassArgs<VT> a{};
   a.mode = mode;
+  a.qper = qper;
   a.in = in;
   a.out = out;
   a.q = q;
@@ -435,21 +437,21 @@ cudaError_t run_pass(int d, int n, const VT* tw, const typename Real<VT>::T* Dn,
 template <class VT>
 cudaError_t green_apply_t(int d, int n, const VT* tw, const typename Real<VT>::T* Dn,
                           VT* tmp, const VT* x, const typename Real<VT>::T* q, bool add_x, VT* out,
-                          int nvec, cudaStream_t st) {
+                          int nvec, int qper, cudaStream_t st) {
   cudaError_t e;
   // forward along axes 0..d-2, middle pass on axis d-1, inverse along d-2..0
   const VT* src = x;
   for (int ax = 0; ax < d - 1; ++ax) {
-    e = run_pass<VT>(d, n, tw, Dn, ax, 0, src, tmp, ax == 0 ? q : nullptr, nullptr, nvec, st);
+    e = run_pass<VT>(d, n, tw, Dn, ax, 0, src, tmp, ax == 0 ? q : nullptr, nullptr, nvec, qper, st);
     if (e != cudaSuccess) return e;
     src = tmp;
   }
-  e = run_pass<VT>(d, n, tw, Dn, d - 1, 2, src, tmp, nullptr, nullptr, nvec, st);
+  e = run_pass<VT>(d, n, tw, Dn, d - 1, 2, src, tmp, nullptr, nullptr, nvec, qper, st);
   if (e != cudaSuccess) return e;
   for (int ax = d - 2; ax >= 0; --ax) {
     bool last = (ax == 0);
     e = run_pass<VT>(d, n, tw, Dn, ax, 1, tmp, last ? out : tmp, nullptr,
-                     (last && add_x) ? x : nullptr, nvec, st);
+                     (last && add_x) ? x : nullptr, nvec, qper, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -463,13 +465,14 @@ __global__ void to_float_kernel(const double* a, float* b, long N) {
 }  // namespace
 
 cudaError_t fft_green_apply(const FftPlan& P, const double2* x, const double* q, bool add_x,
-                            double2* out, cudaStream_t st, int nvec) {
-  return green_apply_t<double2>(P.d, P.n, P.tw, P.Dn, P.tmp, x, q, add_x, out, nvec, st);
+                            double2* out, cudaStream_t st, int nvec, int qper) {
+  if (qper < 1 || nvec % qper) return cudaErrorInvalidValue;
+  return green_apply_t<double2>(P.d, P.n, P.tw, P.Dn, P.tmp, x, q, add_x, out, nvec, qper, st);
 }
 
 cudaError_t fft_green_apply32(const FftPlan& P, const float2* x, const float* q, bool add_x,
                               float2* out, cudaStream_t st) {
-  return green_apply_t<float2>(P.d, P.n, P.tw32, P.Dn32, P.tmp32, x, q, add_x, out, 1, st);
+  return green_apply_t<float2>(P.d, P.n, P.tw32, P.Dn32, P.tmp32, x, q, add_x, out, 1, 1, st);
 }
 
 cudaError_t to_float(const double* a, float* b, long N, cudaStream_t st) {

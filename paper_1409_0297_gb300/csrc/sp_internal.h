@@ -82,22 +82,27 @@ struct DevLevel {
   // front (a thread-block cluster; 0 = the per-block launch chain) and threads per CTA
   int fused_c = 0, fused_nt = 0;
   int pdl = 0;  // launch the level's sweep kernels with programmatic dependent launch
+  // fronts per problem: a context of P problems (a problem group) holds P nfp fronts
+  // per level, problem p's at [p nfp, (p + 1) nfp) with grid indices offset by p N
+  int nfp = 0;
 };
 
 // ---------------------------------------------------------------- FFT (sp_fft.cu)
 struct FftPlan {
   int d = 0, n = 0, logn = 0;  // n = 2^p or 3 2^p
   double2* tw = nullptr;   // exp(-2 pi i t / n), t < n/2
-  double* Dn = nullptr;    // 1 / (4 pi^2 |k|^2 - s) / N, flat
+  double* Dn = nullptr;    // 1 / (4 pi^2 |k|^2 - s) / N, flat (one per problem of a group)
   double2* tmp = nullptr;  // N work (times the context's max_rhs)
   float2* tw32 = nullptr;  // FP32 copies for the mixed-precision inner solve
   float* Dn32 = nullptr;
   float2* tmp32 = nullptr;
 };
 // w = x + G (q x) when q != null and add_x; g = G f when q == null and !add_x.
-// nvec vectors stacked N apart (the plan's tmp holds nvec N entries).
+// nvec vectors stacked N apart (the plan's tmp holds nvec N entries).  qper > 1 (a
+// problem group): the plan holds qper symbols Dn N apart and q holds qper media N
+// apart; vector v uses those of problem v % qper (nvec a multiple of qper).
 cudaError_t fft_green_apply(const FftPlan& P, const double2* x, const double* q, bool add_x,
-                            double2* out, cudaStream_t st, int nvec = 1);
+                            double2* out, cudaStream_t st, int nvec = 1, int qper = 1);
 cudaError_t fft_green_apply32(const FftPlan& P, const float2* x, const float* q, bool add_x,
                               float2* out, cudaStream_t st);
 cudaError_t to_float(const double* a, float* b, long N, cudaStream_t st);
@@ -113,6 +118,7 @@ struct FactorWork {
   int tc_epi = 0;             // epilogue of the tensor-core update (tc_schur_update's epi)
   unsigned long long wait_ns = 2000000000ull;  // limit of each grid-panel poll (global timer ns)
   int calu = 0;               // FP32 grid panels by tournament pivoting (0: column by column)
+  long tab_stride = 0;        // problem group: entries between two problems' Q / C tables
   // grid panel (fronts too tall for a cluster): per front 2 x kGridPanelMaxG
   // publication slots of grid_panel_pub_words() 8-byte words
   unsigned long long* gpub = nullptr;
@@ -181,7 +187,8 @@ struct QTypeDev {
 // nf (m - k)) vector-major; each vector's result equals its single-vector result.
 cudaError_t q_apply(int prec, int d, int n, int nl, const std::vector<QTypeDev>& types,
                     const double* Tcat, const float* Tcat32, const double2* r, void* y,
-                    cudaStream_t st, int nv = 1, bool pdl = false);
+                    cudaStream_t st, int nv = 1, bool pdl = false, int P = 1,
+                    long t_stride = 0);
 // part: sweep_partial_bytes(nv) of work for the split row products (shared by levels)
 cudaError_t forward_level(int prec, int d, DevLevel& L, const DevLevel* child, const void* rhsQ,
                           void* part, cudaStream_t st, int nv = 1, long N = 0);
@@ -231,46 +238,55 @@ cudaError_t kr_combine(const double2* Z, long ldz, int k, const double2* y, long
 // gam = [beta, 0, ...]; V0 = r / beta
 cudaError_t kr_start(const double2* r, long N, const double* nrm, double2* V0, double2* gam,
                      int len, cudaStream_t st);
-// Device-resident restart cycle (the loop of one cycle as a conditional while node
-// of a CUDA graph): the step's state on the device.
+// Batched Krylov processes ("instances": right-hand sides, problems of a group),
+// advanced together with each instance's Arnoldi state in device memory, so that a
+// restart cycle of all of them is one CUDA graph: the Arnoldi step repeats under a
+// conditional while node until no instance goes on.
 struct LoopHead {
-  int j;           // column of the current Arnoldi step
+  int j;           // column of the instance's current Arnoldi step
   int k;           // columns of the cycle once it stopped
   int total;       // iterations so far, all cycles
-  int cont;        // 1 while the cycle goes on
+  int cont;        // 1 while the instance's cycle goes on
   double est_rel;  // last estimate |gamma_{j+1}| / ||g||
   double bnorm;    // ||g||           (written at the end of the cycle)
   double rnorm;    // ||g - A u||     (written at the end of the cycle)
   double pad;
 };
-// j = 0, cont = 1
-cudaError_t kr_loop_begin(LoopHead* h, cudaStream_t st);
-// dst[j dst_ld ...] = src[j src_ld ...] for j = *jp (ld 0: a fixed vector)
-cudaError_t kr_copy_col(const double2* src, long src_ld, double2* dst, long dst_ld, const int* jp,
-                        long N, cudaStream_t st);
-// kr_dots / kr_update_dots / kr_givens with j = *jp (nv = *jp + 1 <= nv_max)
-cudaError_t kr_dots_dev(const double2* V, long ldv, int nv_max, const int* jp, const double2* w,
-                        long N, KrylovWork& K, double2* h_out, cudaStream_t st);
-cudaError_t kr_update_dots_dev(const double2* V, long ldv, int nv_max, const int* jp, double2* w,
-                               long N, const double2* h, KrylovWork& K, double2* h2_out,
-                               cudaStream_t st);
-cudaError_t kr_givens_dev(double2* H, int ldh, const int* jp, const double2* h1, const double2* h2,
-                          const double* nrm, double* cs, double2* sn, double2* gam, double* est,
-                          cudaStream_t st);
-// count the iteration, record est[0] / bnorm[0] in hist, advance j or stop the cycle
-// (setting cond to 0)
-cudaError_t kr_loop_step(LoopHead* h, double* hist, const double* est, const double* bnorm,
-                         double tol, int maxit, int restart, cudaGraphConditionalHandle cond,
-                         cudaStream_t st);
-// V[h->j] = w / nrm[0] if the cycle goes on
-cudaError_t kr_loop_scale(const double2* w, long N, const double* nrm, double2* V,
-                          const LoopHead* h, cudaStream_t st);
-// kr_update_solution with k = *kp
-cudaError_t kr_update_solution_dev(const double2* H, int ldh, const int* kp, const double2* gam,
-                                   double2* y, const double2* Z, long ldz, long N, double2* u,
-                                   cudaStream_t st);
-// h->bnorm = nrm[2], h->rnorm = nrm[3]
-cudaError_t kr_loop_finish(LoopHead* h, const double* nrm, cudaStream_t st);
+// Instance i's slices: V + i sV (maxv vectors of N), Z + i sZ, H + i sH (leading
+// dimension ldh), gam / sn / cs + i sG, h1 / h2 / y + i sh, nrm / est + 4 i,
+// partial + i sP (nblk partial sums per column), w + i N (the new vector of a step).
+struct KBatch {
+  double2 *V = nullptr, *Z = nullptr, *H = nullptr, *gam = nullptr, *sn = nullptr;
+  double2 *h1 = nullptr, *h2 = nullptr, *y = nullptr, *partial = nullptr, *w = nullptr;
+  double *cs = nullptr, *nrm = nullptr, *est = nullptr;
+  LoopHead* head = nullptr;  // I heads
+  const int* run = nullptr;  // I flags: the instance runs in this cycle
+  long N = 0, sV = 0, sZ = 0, sH = 0, sG = 0, sh = 0, sP = 0;
+  int ldh = 0, nblk = 0;
+};
+// head.j = 0, head.cont = run
+cudaError_t kb_begin(const KBatch& b, int I, cudaStream_t st);
+// running instances: V_i[0] = r_i / nrm_i[3], gam_i = [nrm_i[3], 0, ...] (len entries)
+cudaError_t kb_start(const KBatch& b, int I, const double2* r, int len, cudaStream_t st);
+// instances in a step: dst_i = V_i[j_i] / Z_i[j_i] = src_i (vectors N apart)
+cudaError_t kb_copy_in(const KBatch& b, int I, double2* dst, cudaStream_t st);
+cudaError_t kb_copy_out(const KBatch& b, int I, const double2* src, cudaStream_t st);
+// instances in a step: classical Gram-Schmidt twice of w_i against V_i[0..j_i],
+// nrm_i[0] = ||w_i||, Hessenberg column j_i and its Givens rotation (est_i)
+cudaError_t kb_arnoldi(const KBatch& b, int I, int nv_max, cudaStream_t st);
+// nrm_i[slot] = ||x_i|| for every instance (x_i = x + i N)
+cudaError_t kb_norm(const KBatch& b, int I, const double2* x, int slot, cudaStream_t st);
+// the stopping test of every instance in a step (estimate, budget, breakdown, full
+// basis), hist_i[total - 1] = estimate; V_i[j_i + 1] = w_i / nrm_i[0] for those that
+// go on; cond = 0 when none does.  I <= 1024.
+cudaError_t kb_step(const KBatch& b, int I, double* hist, int hstride, double tol, int maxit,
+                    int restart, cudaGraphConditionalHandle cond, cudaStream_t st);
+// running instances: y_i = R_i^{-1} gam_i (k_i columns), U_i += Z_i y_i
+cudaError_t kb_update_solution(const KBatch& b, int I, double2* U, cudaStream_t st);
+// head.bnorm = nrm[2], head.rnorm = nrm[3]
+cudaError_t kb_finish(const KBatch& b, int I, cudaStream_t st);
+// nrm_i[to] = nrm_i[from]
+cudaError_t kb_copy_nrm(const KBatch& b, int I, int from, int to, cudaStream_t st);
 // complex64 counterparts for the inner solve of the mixed-precision form
 cudaError_t kr32_dots(const float2* V, long ldv, int nv, const float2* w, long N, KrylovWork& K,
                       double2* h_out, cudaStream_t st);

@@ -85,17 +85,19 @@ void launch_k(bool pdl, void (*kern)(KArgs...), dim3 g, dim3 b, size_t smem, cud
 
 // y[S instance] = self * r[S instance] - T_t r[B instance], B = beta (self = 1, set
 // stencils) or gamma (self = 0, per-point stencils); one CTA per instance of type t
-// (and per stacked vector, blockIdx.y, vectors N apart).
+// (and per stacked vector, blockIdx.y, vectors N apart).  In a problem group of P
+// problems vector v belongs to problem v % P, whose tables are t_stride apart.
 template <class VT, class T>
 __global__ void qapply_kernel(int d, int n, int nl, int nS, int nB, int self,
                               const int* __restrict__ Soff, const int* __restrict__ Boff,
                               const T* __restrict__ Tt, const double2* __restrict__ r, VT* y,
-                              long N) {
+                              long N, int P, long t_stride) {
   pdl_wait();
   extern __shared__ unsigned char smraw[];
   VT* rb = reinterpret_cast<VT*>(smraw);
   r += blockIdx.y * N;
   y += blockIdx.y * N;
+  Tt += (blockIdx.y % P) * t_stride;
   int box = blockIdx.x, o[3] = {0, 0, 0};
   for (int a = 0; a < d; ++a) {
     o[a] = (box % nl) * (n / nl);
@@ -142,6 +144,7 @@ __device__ void gather_rhs(int d, int f, int m, int k, int nb1, const int* __res
         cid += (2 * bc + ((dl >> a) & 1)) * stride;
         stride *= 2 * nb1;
       }
+      cid += ff * stride;  // problem ff of a group
       const VT* cu = cupd + (long)cid * nbd;
       const int* mp = ea_map + (long)dl * nbd;
       for (int i = threadIdx.x; i < nbd; i += blockDim.x) {
@@ -329,6 +332,7 @@ __global__ void __launch_bounds__(1024) inv_gather_global_kernel(
         cid += (2 * bc + ((dl >> a) & 1)) * stride;
         stride *= 2 * nb1;
       }
+      cid += ff * stride;  // problem ff of a group
       const VT* cu = cupd + (long)cid * nbd;
       const int* mp = ea_map + (long)dl * nbd;
       for (int i = threadIdx.x; i < nbd; i += blockDim.x) {
@@ -519,7 +523,8 @@ __global__ void gemv_finish_kernel(GemvArgs ga, int m, int k, VT* tmp, VT* y, VT
 
 template <class VT>
 cudaError_t q_apply_t(int d, int n, int nl, const std::vector<QTypeDev>& types, const void* Tt,
-                      const double2* r, VT* y, int nv, long N, cudaStream_t st, bool pdl) {
+                      const double2* r, VT* y, int nv, long N, cudaStream_t st, bool pdl, int P,
+                      long t_stride) {
   using T = typename Scalar<VT>::T;
   long ninst = 1;
   for (int a = 0; a < d; ++a) ninst *= nl;
@@ -527,10 +532,10 @@ cudaError_t q_apply_t(int d, int n, int nl, const std::vector<QTypeDev>& types, 
   double bytes = 0;
   for (const auto& ty : types) {
     size_t smem = sizeof(VT) * (ty.na > 0 ? ty.na : 1);
-    dim3 g((unsigned)ninst, nv);
-    launch_k(pdl, qapply_kernel<VT, T>, dim3(g), dim3(128), smem, st, d, n, nl, ty.nS, ty.na, ty.self, ty.S, ty.A,
-                                               (const T*)Tt + ty.t_off, r, y, N);
-    bytes += (double)ninst * nv * ty.nS * (sizeof(double2) + sizeof(VT)) +
+    dim3 g((unsigned)ninst, nv * P);
+    launch_k(pdl, qapply_kernel<VT, T>, dim3(g), dim3(128), smem, st, d, n, nl, ty.nS, ty.na,
+             ty.self, ty.S, ty.A, (const T*)Tt + ty.t_off, r, y, N, P, t_stride);
+    bytes += (double)ninst * nv * P * ty.nS * (sizeof(double2) + sizeof(VT)) +
              sizeof(T) * ty.nS * ty.na;
   }
   ps.done(bytes, (int)types.size(), st);
@@ -1113,12 +1118,12 @@ cudaError_t fused_level(bool fwd, int d, DevLevel& L, const DevLevel* child, con
 
 cudaError_t q_apply(int prec, int d, int n, int nl, const std::vector<QTypeDev>& types,
                     const double* Tcat, const float* Tcat32, const double2* r, void* y,
-                    cudaStream_t st, int nv, bool pdl) {
+                    cudaStream_t st, int nv, bool pdl, int P, long t_stride) {
   long N = 1;
   for (int a = 0; a < d; ++a) N *= n;
   if (prec == SP_PREC_FP32)
-    return q_apply_t<float2>(d, n, nl, types, Tcat32, r, (float2*)y, nv, N, st, pdl);
-  return q_apply_t<double2>(d, n, nl, types, Tcat, r, (double2*)y, nv, N, st, pdl);
+    return q_apply_t<float2>(d, n, nl, types, Tcat32, r, (float2*)y, nv, N, st, pdl, P, t_stride);
+  return q_apply_t<double2>(d, n, nl, types, Tcat, r, (double2*)y, nv, N, st, pdl, P, t_stride);
 }
 
 cudaError_t forward_level(int prec, int d, DevLevel& L, const DevLevel* child, const void* rhsQ,

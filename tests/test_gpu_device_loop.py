@@ -5,7 +5,8 @@ host loop's order with the same operands, so every result must be bit-identical 
 device_loop = 0: the solution, the iteration and restart counts, the estimate
 history and both residuals.  Cases: FP64 and FP32 forms in 2D and 3D, several
 restart cycles, the iteration budget running out, a starting vector, a new medium
-tensor between solves (the graph is captured again) and the host-buffer solve."""
+between solves, the host-buffer solve and several right-hand sides (sp_solve_many,
+batched instances)."""
 import numpy as np
 import pytest
 
@@ -96,8 +97,8 @@ def test_device_loop_start_vector():
 
 def test_device_loop_new_medium_and_host_buffers():
     """Two media of one shift in two different tensors, factored and solved in turn
-    on one context (the loop graph holds the medium pointer, so it is captured again
-    for the second), then the host-buffer solve; each against a host-loop context."""
+    on one context (the graph reads the context's copy of the medium), then the
+    host-buffer solve; each against a host-loop context."""
     from paper_1409_0297_gb300 import binding as B
     w = sm.helmholtz_grf(2, 128, 8, 2 * np.pi * 16, 0.05, 4)
     d, n, b = w["d"], w["n"], w["b"]
@@ -127,3 +128,32 @@ def test_device_loop_new_medium_and_host_buffers():
         _same(x, y)
     assert res[1][0][1]["iters"] != res[1][1][1]["iters"] or not torch.equal(res[1][0][0],
                                                                              res[1][1][0])
+
+
+@pytest.mark.parametrize("prec,restart", [(0, 200), (1, 7)], ids=["fp64", "fp32_restart7"])
+def test_device_loop_many_rhs(prec, restart):
+    """sp_solve_many through the batched cycle graph (4 Krylov instances, one a zero
+    right-hand side) against the host-driven lockstep iteration."""
+    from paper_1409_0297_gb300 import binding as B
+    w = sm.helmholtz_grf(2, 128, 8, 2 * np.pi * 16, 0.05, 4)
+    d, n, b = w["d"], w["n"], w["b"]
+    s, q = _medium(B, w)
+    N = n ** d
+    F = np.stack([sm.random_gaussian_source(d, n, 2600 + r, 0.05 + 0.02 * r) for r in range(4)])
+    F[2] = 0.0
+    Fd = torch.from_numpy(F).cuda().contiguous()
+    res = []
+    for loop in (0, 1):
+        S = B.Solver(d, n, b, s, prec=prec, restart=restart, max_rhs=4, device_loop=loop)
+        S.factor(torch.from_numpy(q).cuda())
+        U = torch.empty_like(Fd)
+        infos = S.solve_many(Fd.view(-1), U.view(-1))
+        torch.cuda.synchronize()
+        res.append((U, infos))
+        S.close()
+    assert torch.equal(res[0][0], res[1][0])
+    for a, c in zip(res[0][1], res[1][1]):
+        for key in ("iters", "restarts", "est_relres", "true_relres"):
+            assert a[key] == c[key], key
+        assert np.array_equal(a["hist"], c["hist"])
+    assert res[1][1][2]["iters"] == 0
