@@ -93,6 +93,10 @@ def parse():
     p.add_argument("--no-batch", action="store_true",
                    help="skip the batched heterogeneous 2D workload (64 problems x 8 right-hand sides)")
     p.add_argument("--batch-workers", type=int, default=16)
+    p.add_argument("--no-batch-groups", action="store_true",
+                   help="skip the problem-group arm of the batched workload")
+    p.add_argument("--group-points", type=int, default=512 * 256,
+                   help="problem groups of the batched workload hold about this many grid points")
     p.add_argument("--serial-pair", action="store_true",
                    help="run the two problems of a 2D step in turn on one stream")
     p.add_argument("--no-batch-fp64", action="store_true",
@@ -532,6 +536,8 @@ def measure_batch(args, B, torch, dist, world):
     for c in ctx:
         c["S"].close()
     torch.cuda.synchronize()
+    grouped = None if args.no_batch_groups else measure_batch_groups(args, B, torch, dist, world,
+                                                                     probs, nw, local)
     # the same 512 solves in the plain FP64 form, one sp_solve per right-hand side
     # (same host threads and streams): the reference for the precision + batching gain
     plain = None
@@ -562,7 +568,109 @@ def measure_batch(args, B, torch, dist, world):
             "max_true_relres": max(inf["true_relres"] for _, inf in infos),
             "plain_fp64": plain,
             "speedup_vs_plain_fp64": (replica_value(nsolve, world, ms) / plain["value"]) if plain else None,
+            "problem_groups": grouped,
             "by_grid": by_n, "data": "synthetic"}
+
+
+def measure_batch_groups(args, B, torch, dist, world, probs, nw, local):
+    """The batched workload with the problems of each (grid, family) in one problem group
+    (sp_setup_group): every factorisation and sweep launch covers the fronts of all the
+    group's problems and one sp_solve_many advances the 8 right-hand sides of every
+    problem of the group together (8 P Krylov instances, one CUDA graph per restart
+    cycle); one host thread and one CUDA stream per group."""
+    import concurrent.futures as cf
+    t0 = time.perf_counter()
+    # buckets of one (grid, family), split into groups of about args.group_points grid
+    # points (so a group of small problems is as large as one big problem and the big
+    # ones keep running side by side)
+    keys, members = [], []
+    for k in sorted({(p["n"], p["kind"]) for p in probs}, key=lambda k: (-k[0], k[1])):
+        ids = [i for i, p in enumerate(probs) if (p["n"], p["kind"]) == k]
+        per = max(1, args.group_points // (k[0] * k[0]))
+        for j in range(0, len(ids), per):
+            keys.append(k)
+            members.append(ids[j:j + per])
+    streams = [torch.cuda.Stream() for _ in keys]
+    nthreads = min(nw, len(keys))
+
+    def setup(gi):
+        n, kind = keys[gi]
+        shifts, qs, rhs = [], [], []
+        for i in members[gi]:
+            p = probs[i]
+            if kind == "helmholtz":
+                s, q = B.sp_medium_helmholtz(2, n, p["omega"], p["c"])
+                scale = 1.0
+            else:
+                s, q = B.sp_medium_schrodinger(2, n, p["ell"], p["E"], p["V"])
+                scale = p["ell"] ** 2
+            shifts.append(s)
+            qs.append(q)
+            rhs.append([f * scale for f in p["rhs"]])
+        R = len(rhs[0])
+        S = B.Solver(2, n, probs[members[gi][0]]["b"], shifts if len(shifts) > 1 else shifts[0],
+                     prec=B.SP_PREC_FP32, restart=64, device=local, sweeps=args.sweeps,
+                     device_loop=args.device_loop, stream=streams[gi].cuda_stream, max_rhs=R,
+                     host_threads=max(1, (os.cpu_count() or 1) // nthreads))
+        # right-hand side r of member p at (r P + p) N
+        F = np.stack([np.concatenate([rhs[p][r] for p in range(len(rhs))]) for r in range(R)])
+        return S, np.concatenate(qs), F
+
+    with cf.ThreadPoolExecutor(nthreads) as ex:
+        made = list(ex.map(setup, range(len(keys))))
+    setup_s = time.perf_counter() - t0
+    units = []
+    for S, q, F in made:
+        Fd = torch.from_numpy(np.ascontiguousarray(F)).cuda().contiguous()
+        units.append(dict(S=S, q=torch.from_numpy(q).cuda(), F=Fd, U=torch.empty_like(Fd)))
+    torch.cuda.synchronize()
+
+    # groups largest first, dealt round-robin to the host threads
+    order = sorted(range(len(keys)), key=lambda gi: -keys[gi][0] ** 2 * len(members[gi]))
+    share = [order[w::nthreads] for w in range(nthreads)]
+
+    def work(w, infos):
+        for gi in share[w]:
+            u = units[gi]
+            u["S"].factor(u["q"])
+            infos.extend(u["S"].solve_many(u["F"].view(-1), u["U"].view(-1)))
+
+    def step(infos):
+        start = torch.cuda.Event(enable_timing=True)
+        start.record()
+        for st_ in streams:
+            st_.wait_event(start)
+        with cf.ThreadPoolExecutor(nthreads) as ex:
+            list(ex.map(lambda w: work(w, infos), range(nthreads)))
+        cur = torch.cuda.current_stream()
+        for st_ in streams:
+            ev = torch.cuda.Event()
+            ev.record(st_)
+            cur.wait_event(ev)
+        end = torch.cuda.Event(enable_timing=True)
+        end.record()
+        torch.cuda.synchronize()
+        return start.elapsed_time(end)
+
+    for _ in range(args.warmup):
+        step([])
+    if dist:
+        dist.barrier()
+    infos = []
+    ms = reduce_max(step(infos), dist)
+    nsolve = sum(len(p["rhs"]) for p in probs)
+    for u in units:
+        u["S"].close()
+    torch.cuda.synchronize()
+    return {"form": f"FP32 preconditioner, problem groups of one (grid, family) and about "
+                    f"{args.group_points} grid points",
+            "value": replica_value(nsolve, world, ms), "unit": "solves/s", "ms_per_step": ms,
+            "groups": [{"n": k[0], "kind": k[1], "problems": len(m)} for k, m in zip(keys, members)],
+            "concurrency": f"{len(keys)} groups on {nthreads} host threads, one CUDA stream per "
+                           "group; all right-hand sides of a group in one sp_solve_many "
+                           "(restart 64)",
+            "setup_s": setup_s, "solves_per_step": nsolve,
+            "max_true_relres": max(inf["true_relres"] for inf in infos)}
 
 
 LEARNED_N, LEARNED_B, LEARNED_ELL, LEARNED_E = 256, 8, 8.0, 10.0

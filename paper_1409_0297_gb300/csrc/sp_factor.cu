@@ -27,7 +27,6 @@ namespace sp {
 namespace {
 
 constexpr int kNB = 32;       // panel width
-constexpr int kInnerBlock = 128;  // innermost block of the tensor-core LU (depth of its updates)
 constexpr int kTile = 64;     // Schur update tile (kTile x kTile per CTA)
 constexpr int kTcMinFront = 1024;         // smallest front blocked for the tensor cores
 constexpr int kGridPanelCTAs = 152;       // CTAs of a grid-panel launch (one per SM)
@@ -1508,11 +1507,13 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
     // other columns, the row band U12 = L11^{-1} A12 is solved in the same
     // sub-block pattern, and the trailing matrix gets one update of depth OB.
     // The updates of depth > 32 run on the tensor cores in the tensor-core forms.
-    // block sizes from the outer block down to the panels: OB, 256, 128, 32
+    // block sizes from the outer block down to the panels: OB, 256, 32.  (A third
+    // level of 128 columns, whose depth-128 updates would run on the tensor cores
+    // too, leaves too much TF32 rounding in the columns next to the panels: at 3D
+    // 128^3 one Helmholtz medium's preconditioner stalled GMRES at 0.42 with it.)
     const int IB = std::min(OB, kTcMaxK / 2);
     std::vector<int> bsz = {OB};
     if (IB < OB) bsz.push_back(IB);
-    if (kInnerBlock > NB && kInnerBlock < bsz.back()) bsz.push_back(kInnerBlock);
     bsz.push_back(NB);
     auto laswp = [&](int p0, int cnt, int a0, int a1, int b0, int b1) {
       const int ncols = std::max(0, a1 - a0) + std::max(0, b1 - b0);

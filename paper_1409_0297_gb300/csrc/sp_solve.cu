@@ -124,6 +124,91 @@ __global__ void qapply_kernel(int d, int n, int nl, int nS, int nB, int self,
   }
 }
 
+// The same product tiled over instances, so a chunk of T_t staged in shared memory
+// serves kQIt instances at once (the kernel above re-reads the whole T_t from L2
+// for every instance).  CTA (instance block, stacked vector, row tile): rows
+// [z kQRt, z kQRt + kQRt) of S for kQIt consecutive instances; per 32-column chunk
+// of B the CTA stages T_t(rows, chunk) and the gathered r(B chunk, instances) in
+// shared memory; each thread keeps 4 rows x 2 instances.  Every output is summed in
+// the order of the kernel above (self term first, then the columns of B in order),
+// so both give the same bits.
+constexpr int kQRt = 64, kQIt = 32, kQK = 32;
+// grid index of the point at offset off from an instance's origin o
+__device__ __forceinline__ long q_addr(int d, int n, const int* o, const int* off) {
+  long g = wrapi(o[0] + off[0], n);
+  if (d > 1) g += (long)wrapi(o[1] + off[1], n) * n;
+  if (d > 2) g += (long)wrapi(o[2] + off[2], n) * n * n;
+  return g;
+}
+template <class VT, class T>
+__global__ void __launch_bounds__(256) qgemm_kernel(int d, int n, int nl, int nS, int nB, int self,
+                                                    const int* __restrict__ Soff,
+                                                    const int* __restrict__ Boff,
+                                                    const T* __restrict__ Tt,
+                                                    const double2* __restrict__ r, VT* y, long N,
+                                                    int P, long t_stride, long ninst) {
+  pdl_wait();
+  __shared__ T Ts[kQK][kQRt];
+  __shared__ VT Rs[kQK][kQIt];
+  __shared__ int org[kQIt][3];
+  r += blockIdx.y * N;
+  y += blockIdx.y * N;
+  Tt += (blockIdx.y % P) * t_stride;
+  const long i0 = (long)blockIdx.x * kQIt;
+  const int row0 = blockIdx.z * kQRt;
+  const int tid = threadIdx.x, ig = tid & 15, rg = tid >> 4;
+  const int side = n / nl;
+  if (tid < kQIt) {
+    long box = i0 + tid;
+    for (int a = 0; a < 3; ++a) {
+      org[tid][a] = (a < d) ? (int)(box % nl) * side : 0;
+      if (a < d) box /= nl;
+    }
+  }
+  __syncthreads();
+  VT acc[4][2];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int row = row0 + rg * 4 + q, ii = ig * 2 + j;
+      acc[q][j] = VT{0, 0};
+      if (self && row < nS && i0 + ii < ninst)
+        acc[q][j] = from_d2<VT>(r[q_addr(d, n, org[ii], Soff + row * d)]);
+    }
+  for (int k0 = 0; k0 < nB; k0 += kQK) {
+    const int kc = min(kQK, nB - k0);
+    for (int e = tid; e < kQK * kQRt; e += 256) {
+      const int rr = e % kQRt, kk = e / kQRt;
+      Ts[kk][rr] = (row0 + rr < nS && kk < kc) ? Tt[(row0 + rr) + (long)(k0 + kk) * nS] : T(0);
+    }
+    for (int e = tid; e < kQK * kQIt; e += 256) {
+      const int ii = e % kQIt, kk = e / kQIt;
+      Rs[kk][ii] = (kk < kc && i0 + ii < ninst)
+                       ? from_d2<VT>(r[q_addr(d, n, org[ii], Boff + (k0 + kk) * d)])
+                       : VT{0, 0};
+    }
+    __syncthreads();
+    for (int kk = 0; kk < kc; ++kk) {
+      const VT r0 = Rs[kk][ig * 2], r1 = Rs[kk][ig * 2 + 1];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const T t = Ts[kk][rg * 4 + q];
+        axpy_neg(acc[q][0], t, r0);
+        axpy_neg(acc[q][1], t, r1);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int row = row0 + rg * 4 + q, ii = ig * 2 + j;
+      if (row < nS && i0 + ii < ninst) y[q_addr(d, n, org[ii], Soff + row * d)] = acc[q][j];
+    }
+}
+
 // Gathers the front's right-hand side: the stencil output at the eliminated
 // unknowns plus the children's update vectors (one child position at a time, so
 // no two threads add into one entry).  b: m entries of shared memory.
@@ -532,9 +617,19 @@ cudaError_t q_apply_t(int d, int n, int nl, const std::vector<QTypeDev>& types, 
   double bytes = 0;
   for (const auto& ty : types) {
     size_t smem = sizeof(VT) * (ty.na > 0 ? ty.na : 1);
-    dim3 g((unsigned)ninst, nv * P);
-    launch_k(pdl, qapply_kernel<VT, T>, dim3(g), dim3(128), smem, st, d, n, nl, ty.nS, ty.na,
-             ty.self, ty.S, ty.A, (const T*)Tt + ty.t_off, r, y, N, P, t_stride);
+    // the tiled product for the large FP32 tables (cells; faces in 3D), where the
+    // per-instance kernel's re-reads of T_t from L2 dominate; FP64 products are bound
+    // by the FP64 pipe either way and small tables stay in L1 (both kernels give the
+    // same bits)
+    if (sizeof(T) == sizeof(float) && ninst >= kQIt && ty.nS >= kQRt / 2) {
+      dim3 g((unsigned)((ninst + kQIt - 1) / kQIt), nv * P, (unsigned)((ty.nS + kQRt - 1) / kQRt));
+      launch_k(pdl, qgemm_kernel<VT, T>, dim3(g), dim3(256), 0, st, d, n, nl, ty.nS, ty.na,
+               ty.self, ty.S, ty.A, (const T*)Tt + ty.t_off, r, y, N, P, t_stride, ninst);
+    } else {
+      dim3 g((unsigned)ninst, nv * P);
+      launch_k(pdl, qapply_kernel<VT, T>, dim3(g), dim3(128), smem, st, d, n, nl, ty.nS, ty.na,
+               ty.self, ty.S, ty.A, (const T*)Tt + ty.t_off, r, y, N, P, t_stride);
+    }
     bytes += (double)ninst * nv * P * ty.nS * (sizeof(double2) + sizeof(VT)) +
              sizeof(T) * ty.nS * ty.na;
   }
