@@ -75,10 +75,11 @@ def parse():
     p.add_argument("--problems", default="helmholtz,schrodinger",
                    help="comma list of the step's problems (default both)")
     p.add_argument("--no-3d", action="store_true", help="skip the 3D 128^3 workload")
-    p.add_argument("--forms-3d", default="tf32,tf32x3",
+    p.add_argument("--forms-3d", default="tf32,tf32h,tf32x3",
                    help="comma list of the tensor-core forms timed on the 3D 128^3 Helmholtz "
-                        "problem (tf32, tf32x3); the first is the one profiled for the roofline")
-    p.add_argument("--forms-3d-schr", default="tf32",
+                        "problem (tf32, tf32x3; a trailing h: sweeps from the FP16 copy of the "
+                        "factor); each is profiled once for the breakdown and the roofline")
+    p.add_argument("--forms-3d-schr", default="tf32,tf32h",
                    help="comma list of the forms timed on the 3D 128^3 Schroedinger problem "
                         "(empty: skip it)")
     p.add_argument("--no-tc-probe", action="store_true",
@@ -362,11 +363,13 @@ def _measure_3d_one(args, B, torch, flush, w, forms, tf32_peak, dist, world, pro
     warm = max(1, min(args.warmup, 3))
     out = {}
     for fi, name in enumerate(forms):
-        prec = {"tf32": B.SP_PREC_TF32, "tf32x3": B.SP_PREC_TF32X3}[name]
+        # a trailing "h": the sweeps read the FP16 copy of the factor (factor_storage 1)
+        half = name.endswith("h")
+        prec = {"tf32": B.SP_PREC_TF32, "tf32x3": B.SP_PREC_TF32X3}[name[:-1] if half else name]
         t0 = time.perf_counter()
         S = B.Solver(d, n, b, s, prec=prec, device=int(os.environ.get("LOCAL_RANK", "0")),
                      setup_route=args.setup_route_3d, sweeps=args.sweeps,
-                     device_loop=args.device_loop)
+                     device_loop=args.device_loop, factor_storage=1 if half else 0)
         setup_s = time.perf_counter() - t0
         for _ in range(warm):
             S.factor(qd)
@@ -387,7 +390,7 @@ def _measure_3d_one(args, B, torch, flush, w, forms, tf32_peak, dist, world, pro
         ms = reduce_max(ms / args.steps_3d, dist)
         r = {"value": replica_value(1, world, ms), "ms_per_step": ms, "setup_s": setup_s,
              "warmup": warm, "iters": infos[0]["iters"], "true_relres": infos[0]["true_relres"]}
-        if profile_first and fi == 0:
+        if profile_first:
             B.sp_profile(S.ctx, True)
             S.factor(qd)
             S.solve(fd, u)

@@ -148,6 +148,15 @@ typedef struct {
                         Ignored by SP_PREC_MIXED, sp_solve_many and while sp_profile is
                         on.  0: the host drives every iteration (reads the estimate
                         after each step).  Default 1. */
+  int factor_storage; /* FP32-family forms (FP32, mixed, TF32, 3xTF32): 1 keeps, after each
+                        factorisation, an FP16 copy of the fronts of the levels whose sweeps
+                        run as chains of block products (the large upper levels), each front
+                        scaled by a power of two so its largest entry stays below 2^15; those
+                        sweeps then read half the bytes and sum in FP32 (Section 2.3's solve
+                        with the factor, at FP16 accuracy of the factor entries: measured at
+                        3D 128^3 TF32, Helmholtz 86 -> 89 GMRES iterations).  0 (default):
+                        the sweeps read the factor in the form's precision.  SP_ERR_ARG for
+                        SP_PREC_FP64. */
 } sp_opts;
 
 typedef struct {

@@ -43,7 +43,7 @@ class sp_opts(ctypes.Structure):
                 ("inv_block", ctypes.c_int), ("tc_epilogue", ctypes.c_int),
                 ("wait_limit_ns", ctypes.c_longlong), ("sweeps", ctypes.c_int),
                 ("panel_pivoting", ctypes.c_int), ("launch_overlap", ctypes.c_int),
-                ("device_loop", ctypes.c_int)]
+                ("device_loop", ctypes.c_int), ("factor_storage", ctypes.c_int)]
 
 
 class sp_info(ctypes.Structure):
@@ -425,7 +425,8 @@ class Solver:
                  stream: int = 0, host_threads: int = 0, autotune: bool = False,
                  max_rhs: int = 1, setup_route: int = 0, stencil: int = 0, inv_block: int = 0,
                  tc_epilogue: int = 0, wait_limit_ns: int = 0, sweeps: int = 0,
-                 panel_pivoting: int = 0, launch_overlap: int = 0, device_loop: int = 1):
+                 panel_pivoting: int = 0, launch_overlap: int = 0, device_loop: int = 1,
+                 factor_storage: int = 0):
         o = sp_default_opts()
         o.maxit, o.restart, o.tol, o.device = maxit, restart, tol, device
         o.host_threads = host_threads
@@ -440,6 +441,7 @@ class Solver:
         o.panel_pivoting = panel_pivoting
         o.launch_overlap = launch_overlap
         o.device_loop = device_loop
+        o.factor_storage = factor_storage
         self.d, self.n, self.b, self.s, self.prec = d, n, b, s, prec
         self.N = n ** d
         if isinstance(s, (int, float)):

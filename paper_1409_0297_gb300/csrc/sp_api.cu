@@ -209,6 +209,7 @@ sp_status factor_direct(sp_ctx* c, const double* q, cudaStream_t st) {
   for (int l = 0; l <= c->L; ++l)
     SP_CK(factor_level(c->prec, c->d, c->lv[l], l ? &c->lv[l - 1] : nullptr, c->Qcat, c->Ccat, q,
                        c->opts.pivot_tol, c->status, c->work, st));
+  for (int l = 0; l <= c->L; ++l) SP_CK(factor_copy16(c->lv[l], st));
   return SP_OK;
 }
 
@@ -450,6 +451,7 @@ void sp_default_opts(sp_opts* o) {
   o->panel_pivoting = 0;
   o->launch_overlap = 0;
   o->device_loop = 1;
+  o->factor_storage = 0;
 }
 
 const char* sp_status_str(sp_status st) {
@@ -676,6 +678,8 @@ static sp_status setup_impl(int d, int n, int b, int P, const double* shifts, sp
   if (c->opts.panel_pivoting != 0 && c->opts.panel_pivoting != 1) return SP_ERR_ARG;
   if (c->opts.launch_overlap != 0 && c->opts.launch_overlap != 1) return SP_ERR_ARG;
   if (c->opts.device_loop != 0 && c->opts.device_loop != 1) return SP_ERR_ARG;
+  if (c->opts.factor_storage != 0 && c->opts.factor_storage != 1) return SP_ERR_ARG;
+  if (c->opts.factor_storage == 1 && prec == SP_PREC_FP64) return SP_ERR_ARG;
   const size_t RH = (size_t)c->opts.max_rhs;
   // every Krylov instance (right-hand side of a problem) is one thread of the batched
   // stopping test
@@ -848,6 +852,10 @@ static sp_status setup_impl(int d, int n, int b, int P, const double* shifts, sp
         D.fused_nt = NT;
       }
     }
+    if (D.inv && D.fused_c == 0 && c->opts.factor_storage == 1) {
+      SP_CK(dalloc(c.get(), &D.front16, (size_t)2 * D.nf * S.m * ((S.m + 1) & ~1)));
+      SP_CK(dalloc(c.get(), &D.fscale16, sizeof(float) * D.nf * S.m));
+    }
     if (D.inv) {
       SP_CK(dalloc(c.get(), &D.tmp, vsz * RH * (size_t)D.nf * S.m));
       scratch_bytes = std::max(scratch_bytes, fsz * invert_scratch_elems(D.nf, S.k, D.ib));
@@ -860,6 +868,12 @@ static sp_status setup_impl(int d, int n, int b, int P, const double* shifts, sp
     c->factor_flops += D.nf * ((2.0 / 3.0) * k * k * k + 2 * k * k * mk + 2 * k * mk * mk);
   }
   c->apply_bytes = c->factor_entries * fsz;
+  if (c->opts.factor_storage == 1) {  // the chained levels' sweeps read half as many bytes
+    double e16 = 0;
+    for (const DevLevel& D : c->lv)
+      if (D.front16) e16 += D.nf * ((double)D.k * D.k + 2.0 * D.k * (D.m - D.k));
+    c->apply_bytes -= e16 * (fsz - 2);
+  }
   if (scratch_bytes) SP_CK(dalloc(c.get(), &c->work.inv, scratch_bytes));
   SP_CK(dalloc(c.get(), &c->gemv_part, sweep_partial_bytes((int)RH)));
   if (gp_words) SP_CK(dalloc(c.get(), &c->work.gpub, sizeof(unsigned long long) * gp_words));

@@ -20,6 +20,8 @@
 #include <algorithm>
 #include <cfloat>
 
+#include <cuda_fp16.h>
+
 #include "sp_internal.h"
 
 namespace sp {
@@ -67,6 +69,34 @@ __global__ void extend_add_kernel(T* parent, int m, int nb1, const T* __restrict
   int i = (int)(e % nbd), j = (int)(e / nbd);
   const T v = child[(long)cid * mc * mc + (long)(kc + i) + (long)(kc + j) * mc];
   parent[(long)f * m * m + map[i] + (long)map[j] * m] += v;
+}
+
+// FP16 copy of the factor for the chained sweeps (sp_opts.factor_storage = 1), with a
+// power-of-two scale per front column: column c of front f is stored as entry /
+// 2^(e - 15), with max |entry| = mant 2^e (mant in [0.5, 1)) over the rows the sweeps
+// read (all rows for c < k; rows < k, the U12 block, for c >= k), so every stored
+// magnitude is below 2^15 (FP16's largest finite value is 65504), the scaling is
+// exact, and a column's entries keep FP16's 11 significant bits down to 2^-29 of its
+// largest.  One warp per column; columns ld16 = m rounded up to even apart (the pad
+// row zero).
+__global__ void f16_copy_kernel(const float* fronts, int m, int k, __half* out, float* fsc) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (c >= m) return;
+  const long f = blockIdx.y, mm = (long)m * m;
+  const int ld16 = (m + 1) & ~1;  // even column stride: row pairs load as half2
+  const float* col = fronts + f * mm + (long)c * m;
+  __half* hc = out + f * (long)m * ld16 + (long)c * ld16;
+  const int rows = c < k ? m : k;
+  if (lane == 0 && ld16 > m) hc[m] = __float2half_rn(0.f);
+  float mx = 0.f;
+  for (int r = lane; r < rows; r += 32) mx = fmaxf(mx, fabsf(col[r]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  int e = 0;
+  if (mx > 0.f) frexpf(mx, &e);
+  const float inv = ldexpf(1.0f, 15 - e);
+  if (lane == 0) fsc[f * m + c] = ldexpf(1.0f, e - 15);
+  for (int r = lane; r < rows; r += 32) hc[r] = __float2half_rn(col[r] * inv);
 }
 
 // max |entry| of every front: CTAs over (chunk, front), atomicMax on the bit
@@ -1654,6 +1684,14 @@ int factor_outer_block(int prec, bool tc, int m, int k) {
 
 size_t invert_scratch_elems(int nf, int k, int ib) {
   return (size_t)nf * ((size_t)2 * k * (ib + 1) + (size_t)k * (ib / 2));
+}
+
+cudaError_t factor_copy16(DevLevel& L, cudaStream_t st) {
+  if (!L.front16) return cudaSuccess;
+  dim3 g((unsigned)((L.m + 7) / 8), L.nf);
+  f16_copy_kernel<<<g, 256, 0, st>>>((const float*)L.front, L.m, L.k, (__half*)L.front16,
+                                     L.fscale16);
+  return cudaGetLastError();
 }
 
 size_t grid_panel_pub_words(int nf) {

@@ -85,6 +85,11 @@ struct DevLevel {
   // fronts per problem: a context of P problems (a problem group) holds P nfp fronts
   // per level, problem p's at [p nfp, (p + 1) nfp) with grid indices offset by p N
   int nfp = 0;
+  // FP16 copy of the fronts for the chained sweeps (sp_opts.factor_storage = 1):
+  // entry (r, c) of front f stored as entry / fscale16[f m + c] rounded to half, a
+  // power-of-two scale per column (the Schur block, rows and columns >= k, not copied)
+  void* front16 = nullptr;       // nf m ld16 halves, ld16 = m rounded up to even
+  float* fscale16 = nullptr;     // nf m
 };
 
 // ---------------------------------------------------------------- FFT (sp_fft.cu)
@@ -135,6 +140,8 @@ size_t invert_scratch_elems(int nf, int k, int ib);
 // whether fronts of size m use the cooperative grid panel; 8-byte words of its
 // publication buffer for nf fronts
 bool factor_grid_panel(int prec, int m);
+// the level's FP16 copy of its fronts (when it has one; after the factorisation)
+cudaError_t factor_copy16(DevLevel& L, cudaStream_t st);
 size_t grid_panel_pub_words(int nf);
 // outer block width of the blocked LU of a front (0: the 32-column right-looking
 // LU with a Schur update after every panel)

@@ -16,6 +16,7 @@
 // one row per thread), so the large upper fronts spread over the whole GPU.
 // VT = double2 (FP64 form) or float2 (FP32 form).
 #include <cooperative_groups.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 
@@ -31,6 +32,22 @@ constexpr size_t kVecSmem = 192 * 1024;  // largest vector staged in shared memo
 template <class VT> struct Scalar;
 template <> struct Scalar<double2> { using T = double; };
 template <> struct Scalar<float2> { using T = float; };
+
+// Factor entries as the sweeps compute with them: FP64 and FP32 fronts as stored, the
+// FP16 copy (sp_opts.factor_storage = 1) widened to FP32; its power-of-two column
+// scales multiply the vector entries as they are staged (exact), so
+// sum_c A[r, c] v[c] = sum_c A16[r, c] (scale[c] v[c])
+__device__ __forceinline__ double fac(double a) { return a; }
+__device__ __forceinline__ float fac(float a) { return a; }
+__device__ __forceinline__ float fac(__half a) { return __half2float(a); }
+template <class VT> __device__ __forceinline__ VT vscale(VT v, const float* sc, long c) {
+  if (sc) {
+    const float s = sc[c];
+    v.x *= s;
+    v.y *= s;
+  }
+  return v;
+}
 
 template <class VT> __device__ __forceinline__ VT vzero();
 template <> __device__ __forceinline__ double2 vzero<double2>() { return make_double2(0, 0); }
@@ -51,8 +68,9 @@ __device__ __forceinline__ void axpy_neg(VT& acc, T a, VT x) {  // acc -= a * x
 }
 template <class VT, class T>
 __device__ __forceinline__ void axpy(VT& acc, T a, VT x) {  // acc += a * x
-  acc.x = fma(a, x.x, acc.x);
-  acc.y = fma(a, x.y, acc.y);
+  using C = decltype(acc.x);
+  acc.x = fma((C)a, x.x, acc.x);
+  acc.y = fma((C)a, x.y, acc.y);
 }
 
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
@@ -447,7 +465,8 @@ template <class VT, class T, int RB>
 __global__ void __launch_bounds__(256) inv_gemv_kernel(int mode, const T* __restrict__ fronts,
                                                         int m, int k, int j0, int j1,
                                                         const int* __restrict__ gidx, VT* tmp,
-                                                        VT* y, double2* x, long N) {
+                                                        VT* y, double2* x, long N,
+                                                        const float* __restrict__ fsc, int lda) {
   pdl_wait();
   extern __shared__ unsigned char smraw[];
   VT* v = reinterpret_cast<VT*>(smraw);  // tmp[j0 .. j1)
@@ -460,10 +479,11 @@ __global__ void __launch_bounds__(256) inv_gemv_kernel(int mode, const T* __rest
   constexpr int CL = 256 / RB;  // column lanes per row
   __shared__ VT red[CL][RB + 1];
   const int f = blockIdx.y;
-  const T* A = fronts + (long)f * m * m;
+  const T* A = fronts + (long)f * m * lda;  // columns lda apart (m, or the FP16 copy's even m)
   VT* tf = tmp + (long)f * m;
   VT* yf = y + (long)f * k;
-  for (int c = j0 + threadIdx.x; c < j1; c += blockDim.x) v[c - j0] = tf[c];
+  const float* sc = fsc ? fsc + (long)f * m : nullptr;  // column scales of the FP16 copy
+  for (int c = j0 + threadIdx.x; c < j1; c += blockDim.x) v[c - j0] = vscale(tf[c], sc, c);
   __syncthreads();
   const int tx = threadIdx.x % RB, ty = threadIdx.x / RB;
   const int r0 = j0 + blockIdx.x * RB;
@@ -477,7 +497,7 @@ __global__ void __launch_bounds__(256) inv_gemv_kernel(int mode, const T* __rest
 #pragma unroll 4
     for (int c = cb + ty; c < ce; c += CL) {
       const bool use = (mode == 0) ? (c < r) : (c >= r);
-      if (use) axpy(acc, A[r + (long)c * m], v[c - j0]);
+      if (use) axpy(acc, fac(A[r + (long)c * lda]), v[c - j0]);
     }
   }
   red[ty][tx] = acc;
@@ -533,12 +553,14 @@ template <class VT, class T, int NV>
 __global__ void __launch_bounds__(256) gemv_kernel(GemvArgs ga, const T* __restrict__ fronts,
                                                     int m, int k, const int* __restrict__ gidx,
                                                     VT* tmp, VT* y, VT* upd, const double2* x,
-                                                    int nsplit, VT* part, int nv, long N) {
+                                                    int nsplit, VT* part, int nv, long N,
+                                                    const float* __restrict__ fsc) {
   pdl_wait();
   constexpr int CH = 1024 / NV;  // columns of one staged chunk
   __shared__ VT vs[CH * NV];     // vs[j NV + v]
   const int f = blockIdx.z, sp = blockIdx.y, nf = gridDim.z;
   const T* A = fronts + (long)f * m * m;
+  const float* sc = fsc ? fsc + (long)f * m : nullptr;  // column scales of the FP16 copy
   const long tstr = (long)nf * m, ystr = (long)nf * k, ustr = (long)nf * (m - k);
   const int r = ga.rlo + blockIdx.x * 256 + threadIdx.x;
   const int per = (ga.vhi - ga.vlo + nsplit - 1) / nsplit;
@@ -551,8 +573,9 @@ __global__ void __launch_bounds__(256) gemv_kernel(GemvArgs ga, const T* __restr
     __syncthreads();
     for (int i = threadIdx.x; i < cn * nv; i += 256) {
       const int j = i / nv, v = i - j * nv;
-      vs[j * NV + v] = ga.vsrc ? from_d2<VT>(x[v * N + gidx[(long)f * m + c0 + j]])
-                               : y[v * ystr + (long)f * k + c0 + j];
+      vs[j * NV + v] = vscale(ga.vsrc ? from_d2<VT>(x[v * N + gidx[(long)f * m + c0 + j]])
+                                      : y[v * ystr + (long)f * k + c0 + j],
+                              sc, c0 + j);
     }
     __syncthreads();
     if (r < ga.rhi) {
@@ -561,9 +584,9 @@ __global__ void __launch_bounds__(256) gemv_kernel(GemvArgs ga, const T* __restr
       // 8 column loads in flight per thread: a launch costs (columns of a split) / 8
       // memory latencies at least (16 was measured slower on the large 3D launches)
       for (; j + 8 <= cn; j += 8) {
-        T a[8];
+        decltype(fac(T())) a[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) a[u] = Ar[(long)(j + u) * m];
+        for (int u = 0; u < 8; ++u) a[u] = fac(Ar[(long)(j + u) * m]);
 #pragma unroll
         for (int u = 0; u < 8; ++u)
 #pragma unroll
@@ -571,7 +594,7 @@ __global__ void __launch_bounds__(256) gemv_kernel(GemvArgs ga, const T* __restr
             if (v < nv) axpy(acc[v], a[u], vs[(j + u) * NV + v]);
       }
       for (; j < cn; ++j) {
-        const T a = Ar[(long)j * m];
+        const auto a = fac(Ar[(long)j * m]);
 #pragma unroll
         for (int v = 0; v < NV; ++v)
           if (v < nv) axpy(acc[v], a, vs[j * NV + v]);
@@ -589,6 +612,88 @@ __global__ void __launch_bounds__(256) gemv_kernel(GemvArgs ga, const T* __restr
       part[(((long)sp * nv + v) * nf + f) * (ga.rhi - ga.rlo) + (r - ga.rlo)] = acc[v];
   }
 }
+// gemv_kernel on the FP16 copy of the factor (columns ld16 = m rounded up to even
+// apart): each thread owns a pair of rows (r0, r0 + 1), r0 even, and reads both with
+// one half2 load, so a warp still moves 128 contiguous bytes of a column per load;
+// the column scales multiply the staged vector entries.
+template <class VT, int NV>
+__global__ void __launch_bounds__(256) gemv16_kernel(GemvArgs ga, const __half* __restrict__ fronts,
+                                                     int m, int ld16, int k,
+                                                     const int* __restrict__ gidx, VT* tmp, VT* y,
+                                                     VT* upd, const double2* x, int nsplit, VT* part,
+                                                     int nv, long N, const float* __restrict__ fsc) {
+  pdl_wait();
+  constexpr int CH = 1024 / NV;
+  __shared__ VT vs[CH * NV];
+  const int f = blockIdx.z, sp = blockIdx.y, nf = gridDim.z;
+  const __half* A = fronts + (long)f * m * ld16;
+  const float* sc = fsc + (long)f * m;
+  const long tstr = (long)nf * m, ystr = (long)nf * k, ustr = (long)nf * (m - k);
+  const int r0 = (ga.rlo & ~1) + 2 * (blockIdx.x * 256 + threadIdx.x);
+  const int per = (ga.vhi - ga.vlo + nsplit - 1) / nsplit;
+  const int cb = ga.vlo + sp * per, ce = min(ga.vhi, cb + per);
+  VT acc0[NV], acc1[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc0[v] = acc1[v] = vzero<VT>();
+  const bool live = r0 < ga.rhi;
+  for (int c0 = cb; c0 < ce; c0 += CH) {
+    const int cn = min(CH, ce - c0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < cn * nv; i += 256) {
+      const int j = i / nv, v = i - j * nv;
+      vs[j * NV + v] = vscale(ga.vsrc ? from_d2<VT>(x[v * N + gidx[(long)f * m + c0 + j]])
+                                      : y[v * ystr + (long)f * k + c0 + j],
+                              sc, c0 + j);
+    }
+    __syncthreads();
+    if (live) {
+      const __half2* Ar = reinterpret_cast<const __half2*>(A + r0 + (long)c0 * ld16);
+      const long cs = ld16 / 2;  // column stride in half2
+      int j = 0;
+      for (; j + 8 <= cn; j += 8) {
+        __half2 h[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) h[u] = Ar[(long)(j + u) * cs];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const float2 a = __half22float2(h[u]);
+#pragma unroll
+          for (int v = 0; v < NV; ++v)
+            if (v < nv) {
+              axpy(acc0[v], a.x, vs[(j + u) * NV + v]);
+              axpy(acc1[v], a.y, vs[(j + u) * NV + v]);
+            }
+        }
+      }
+      for (; j < cn; ++j) {
+        const float2 a = __half22float2(Ar[(long)j * cs]);
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+          if (v < nv) {
+            axpy(acc0[v], a.x, vs[j * NV + v]);
+            axpy(acc1[v], a.y, vs[j * NV + v]);
+          }
+      }
+    }
+  }
+  if (!live) return;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int r = r0 + h;
+    if (r < ga.rlo || r >= ga.rhi) continue;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      if (v >= nv) break;
+      const VT a = h ? acc1[v] : acc0[v];
+      if (nsplit == 1)
+        gemv_out(ga.op, m, k, r, a, tmp + v * tstr + (long)f * m, y + v * ystr + (long)f * k,
+                 upd + v * ustr, f);
+      else
+        part[(((long)sp * nv + v) * nf + f) * (ga.rhi - ga.rlo) + (r - ga.rlo)] = a;
+    }
+  }
+}
+
 template <class VT>
 __global__ void gemv_finish_kernel(GemvArgs ga, int m, int k, VT* tmp, VT* y, VT* upd, int nsplit,
                                    const VT* __restrict__ part) {
@@ -646,6 +751,8 @@ void set_attrs() {
   cudaFuncSetAttribute(inv_gather_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(inv_gemv_kernel<VT, T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(inv_gemv_kernel<VT, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(inv_gemv_kernel<VT, __half, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(inv_gemv_kernel<VT, __half, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 constexpr int kGemvTarget = 1216;  // CTAs a row-parallel product aims for (8 per SM)
@@ -665,21 +772,44 @@ int gemv_splits(int rows, int cols, int nf) {
 
 // One off-diagonal product (gemv_kernel, + gemv_finish_kernel when split) for nv
 // stacked vectors.
+// The factor comes from the level's FP16 copy when it has one (T = __half, scaled
+// per front), else from the fronts.
 template <class VT, class T>
 int gemv(const GemvArgs& ga, DevLevel& L, const double2* x, void* part, int nv, long N,
          cudaStream_t st) {
+  const T* fr = (const T*)L.front;
   const int rows = ga.rhi - ga.rlo, cols = ga.vhi - ga.vlo;
   if (rows <= 0) return 0;
   int ns = cols > 0 ? gemv_splits(rows, cols, L.nf) : 1;
   if (!part) ns = 1;
   dim3 g((rows + 255) / 256, ns, L.nf);
-  if (nv == 1)
-    launch_k(L.pdl != 0, gemv_kernel<VT, T, 1>, dim3(g), dim3(256), 0, st, ga, (const T*)L.front, L.m, L.k, L.gidx, (VT*)L.tmp,
-                                             (VT*)L.y, (VT*)L.upd, x, ns, (VT*)part, 1, N);
+  if (L.front16) {  // row pairs from the FP16 copy
+    const int ld16 = (L.m + 1) & ~1;
+    const int pairs = ((ga.rhi + 1) >> 1) - (ga.rlo >> 1);
+    // a thread's column walk is a chain of memory latencies: as many CTAs as the FP32
+    // form launches, so twice the column splits, within the partial-sum buffer's
+    // bound (splits x fronts x rows <= 2 kGemvTarget 256)
+    if (part && cols > 0) {
+      const long cap = std::max<long>(1, (2L * kGemvTarget * 256) / ((long)L.nf * rows));
+      ns = (int)std::min<long>(gemv_splits(pairs, cols, L.nf), cap);
+    }
+    dim3 g16((pairs + 255) / 256, ns, L.nf);
+    if (nv == 1)
+      launch_k(L.pdl != 0, gemv16_kernel<VT, 1>, dim3(g16), dim3(256), 0, st, ga,
+               (const __half*)L.front16, L.m, ld16, L.k, L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd,
+               x, ns, (VT*)part, 1, N, (const float*)L.fscale16);
+    else
+      launch_k(L.pdl != 0, gemv16_kernel<VT, kMaxVec>, dim3(g16), dim3(256), 0, st, ga,
+               (const __half*)L.front16, L.m, ld16, L.k, L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd,
+               x, ns, (VT*)part, nv, N, (const float*)L.fscale16);
+  } else if (nv == 1)
+    launch_k(L.pdl != 0, gemv_kernel<VT, T, 1>, dim3(g), dim3(256), 0, st, ga, fr, L.m, L.k,
+             L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x, ns, (VT*)part, 1, N,
+             (const float*)nullptr);
   else
-    launch_k(L.pdl != 0, gemv_kernel<VT, T, kMaxVec>, dim3(g), dim3(256), 0, st, ga, (const T*)L.front, L.m, L.k, L.gidx,
-                                                   (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x, ns,
-                                                   (VT*)part, nv, N);
+    launch_k(L.pdl != 0, gemv_kernel<VT, T, kMaxVec>, dim3(g), dim3(256), 0, st, ga, fr, L.m, L.k,
+             L.gidx, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, x, ns, (VT*)part, nv, N,
+             (const float*)nullptr);
   if (ns == 1) return 1;
   dim3 gf((rows + 255) / 256, L.nf, nv);
   launch_k(L.pdl != 0, gemv_finish_kernel<VT>, dim3(gf), dim3(256), 0, st, ga, L.m, L.k, (VT*)L.tmp, (VT*)L.y, (VT*)L.upd, ns,
@@ -693,15 +823,18 @@ int gemv(const GemvArgs& ga, DevLevel& L, const double2* x, void* part, int nv, 
 template <class VT, class T>
 void inv_gemv(int mode, DevLevel& L, int j0, int j1, int rlo, int rhi, size_t smem, double2* x,
               int nv, long N, cudaStream_t st) {
+  const T* fr = (const T*)(L.front16 ? L.front16 : L.front);
+  const float* fsc = L.front16 ? L.fscale16 : nullptr;
+  const int lda = L.front16 ? ((L.m + 1) & ~1) : L.m;
   const int rows = rhi - rlo;
   if ((long)((rows + 15) / 16) * L.nf >= 152) {
     dim3 g((rows + 15) / 16, L.nf, nv);
-    launch_k(L.pdl != 0, inv_gemv_kernel<VT, T, 16>, dim3(g), dim3(256), smem, st, mode, (const T*)L.front, L.m, L.k, j0, j1,
-                                                     L.gidx, (VT*)L.tmp, (VT*)L.y, x, N);
+    launch_k(L.pdl != 0, inv_gemv_kernel<VT, T, 16>, dim3(g), dim3(256), smem, st, mode, fr, L.m,
+             L.k, j0, j1, L.gidx, (VT*)L.tmp, (VT*)L.y, x, N, fsc, lda);
   } else {
     dim3 g((rows + 3) / 4, L.nf, nv);
-    launch_k(L.pdl != 0, inv_gemv_kernel<VT, T, 4>, dim3(g), dim3(256), smem, st, mode, (const T*)L.front, L.m, L.k, j0, j1,
-                                                    L.gidx, (VT*)L.tmp, (VT*)L.y, x, N);
+    launch_k(L.pdl != 0, inv_gemv_kernel<VT, T, 4>, dim3(g), dim3(256), smem, st, mode, fr, L.m,
+             L.k, j0, j1, L.gidx, (VT*)L.tmp, (VT*)L.y, x, N, fsc, lda);
   }
 }
 
@@ -749,7 +882,10 @@ cudaError_t forward_t(int d, DevLevel& L, const DevLevel* child, const void* rhs
     // which hand their result to the parent as the update vector
     for (int j0 = 0; j0 < L.k; j0 += L.ib) {
       const int j1 = min(L.k, j0 + L.ib);
-      inv_gemv<VT, T>(0, L, j0, j1, j0, j1, sizeof(VT) * (j1 - j0), nullptr, nv, N, st);
+      if (L.front16)
+        inv_gemv<VT, __half>(0, L, j0, j1, j0, j1, sizeof(VT) * (j1 - j0), nullptr, nv, N, st);
+      else
+        inv_gemv<VT, T>(0, L, j0, j1, j0, j1, sizeof(VT) * (j1 - j0), nullptr, nv, N, st);
       ++launches;
       if (j1 < L.m) {
         const GemvArgs ga{j1, L.m, j0, j1, 0, j1 == L.k ? 1 : 0};
@@ -757,7 +893,8 @@ cudaError_t forward_t(int d, DevLevel& L, const DevLevel* child, const void* rhs
       }
     }
   }
-  ps.done(L.nf * sizeof(T) * (kk * (kk - 1) / 2 + mk * kk), launches, st);
+  ps.done(L.nf * (L.front16 ? 2.0 : (double)sizeof(T)) * (kk * (kk - 1) / 2 + mk * kk), launches,
+          st);
   return cudaGetLastError();
 }
 
@@ -790,7 +927,10 @@ cudaError_t backward_t(DevLevel& L, double2* x, void* part, int nv, long N, cuda
     const int nbk = (L.k + L.ib - 1) / L.ib;
     for (int bi = nbk - 1; bi >= 0; --bi) {
       const int j0 = bi * L.ib, j1 = min(L.k, j0 + L.ib);
-      inv_gemv<VT, T>(3, L, j0, j1, j0, j1, sizeof(VT) * (j1 - j0), x, nv, N, st);
+      if (L.front16)
+        inv_gemv<VT, __half>(3, L, j0, j1, j0, j1, sizeof(VT) * (j1 - j0), x, nv, N, st);
+      else
+        inv_gemv<VT, T>(3, L, j0, j1, j0, j1, sizeof(VT) * (j1 - j0), x, nv, N, st);
       ++launches;
       if (j0 > 0) {
         const GemvArgs ga{0, j0, j0, j1, 0, 0};
@@ -798,7 +938,8 @@ cudaError_t backward_t(DevLevel& L, double2* x, void* part, int nv, long N, cuda
       }
     }
   }
-  ps.done(L.nf * sizeof(T) * (kk * (kk + 1) / 2 + mk * kk), launches, st);
+  ps.done(L.nf * (L.front16 ? 2.0 : (double)sizeof(T)) * (kk * (kk + 1) / 2 + mk * kk), launches,
+          st);
   return cudaGetLastError();
 }
 

@@ -104,7 +104,7 @@ def test_default_opts_layout():
     assert (o.device, o.host_threads, o.inner_tol, o.autotune) == (0, 0, 1e-5, 0)
     assert (o.max_rhs, o.setup_route, o.stencil, o.inv_block, o.tc_epilogue) == (1, 0, 0, 0, 0)
     assert o.wait_limit_ns == 0 and o.sweeps == 0 and o.panel_pivoting == 0
-    assert o.launch_overlap == 0 and o.device_loop == 1
+    assert o.launch_overlap == 0 and o.device_loop == 1 and o.factor_storage == 0
     # the binding's layouts of sp_opts and sp_info match the build's
     assert B.LIB.sp_abi_size(0) == ctypes.sizeof(B.sp_opts)
     assert B.LIB.sp_abi_size(1) == ctypes.sizeof(B.sp_info)
