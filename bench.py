@@ -61,7 +61,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-chosen", action="store_true")
-    p.add_argument("--profile-step", default=None, choices=["fp64", "fp32", "tf32", "tf32x3"],
+    p.add_argument("--profile-step", default=None,
+                   choices=["fp64", "fp32", "tf32", "tf32x3", "tf32h", "tf32x3h"],
                    help="run exactly one untimed step (factor + solve of both problems) in the "
                         "given form after set-up and exit: the command profiled under ncu")
     p.add_argument("--profile-workload", default="2d512", choices=["2d512", "3d64", "3d128"],
@@ -919,6 +920,8 @@ def summary(line: dict) -> dict:
         out["batch_2d"] = {"value": round(wb["value"], 2),
                            "speedup_vs_plain_fp64": round(wb["speedup_vs_plain_fp64"], 3)
                            if wb.get("speedup_vs_plain_fp64") else None}
+        if wb.get("problem_groups"):
+            out["batch_2d"]["problem_groups"] = round(wb["problem_groups"]["value"], 2)
     wl = line.get("workload_learned")
     if wl:
         out["learned_guess_speedup"] = round(wl["speedup_vs_zero_guess"], 3)
@@ -1022,8 +1025,10 @@ def run_ours(args):
         n = 64 if args.profile_workload == "3d64" else 128
         w = sm.helmholtz_grf_3d(n, 8, 0)
         s3, q3 = B.sp_medium_helmholtz(3, n, w["omega"], w["c"])
-        S = B.Solver(3, n, 8, s3, prec=form_prec[args.profile_step], device=local,
-                     sweeps=args.sweeps, device_loop=args.device_loop)
+        half = args.profile_step.endswith("h")
+        S = B.Solver(3, n, 8, s3, prec=form_prec[args.profile_step.rstrip("h")], device=local,
+                     sweeps=args.sweeps, device_loop=args.device_loop,
+                     factor_storage=1 if half else 0)
         u = torch.empty(n ** 3, dtype=torch.complex128, device="cuda")
         q3d = torch.from_numpy(q3).cuda()
         f3d = torch.from_numpy(np.ascontiguousarray(w["f"])).cuda()
@@ -1038,6 +1043,8 @@ def run_ours(args):
         S.close()
         return
     if args.profile_step:
+        if args.profile_step.endswith("h"):
+            raise SystemExit("the FP16 factor copy is profiled on the 3D workloads")
         ctxs = make(form_prec[args.profile_step])
         torch.cuda.synchronize()
         infos = []
