@@ -61,7 +61,7 @@ typedef enum {
                         inner_tol; the outer FP64 refinement forms u += d and the
                         true residual r = g - A u with the FP64 operator */
   SP_PREC_TF32 = 3,  /* as SP_PREC_FP32, and fronts with m >= 1024 are factored in
-                        outer blocks of 512 columns (sub-blocks of 256) whose
+                        outer blocks of 1024 columns (sub-blocks of 256) whose
                         Schur updates S -= L21 U12 run on the tensor cores (TF32
                         products, FP32 accumulation; Section 2.3's update
                         S = F22 - L21 U12) */

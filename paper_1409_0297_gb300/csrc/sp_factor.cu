@@ -1541,7 +1541,7 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
     // level of 128 columns, whose depth-128 updates would run on the tensor cores
     // too, leaves too much TF32 rounding in the columns next to the panels: at 3D
     // 128^3 one Helmholtz medium's preconditioner stalled GMRES at 0.42 with it.)
-    const int IB = std::min(OB, kTcMaxK / 2);
+    const int IB = std::min(OB, kTcSubBlock);
     std::vector<int> bsz = {OB};
     if (IB < OB) bsz.push_back(IB);
     bsz.push_back(NB);

@@ -155,7 +155,8 @@ cudaError_t schur_update_raw(int prec, bool tc, bool split, int M, int N, int K,
                              cudaStream_t st);
 
 // ---------------------------------------------------------------- tensor cores (sp_tc.cu)
-constexpr int kTcMaxK = 512;       // depth of the factorisation's updates (its operand buffers)
+constexpr int kTcMaxK = 1024;      // depth of the factorisation's updates (its operand buffers)
+constexpr int kTcSubBlock = 256;   // sub-blocks of an outer block (depth of the updates inside it)
 constexpr int kTcMaxKProbe = 16384;  // depth accepted by the stand-alone update and the rate probe
 // floats of one packed operand buffer for `rows` rows, K columns, batch fronts
 size_t tc_pack_floats(int rows, int K, int batch, bool split);

@@ -1,6 +1,7 @@
 // Schur-complement update of the large fronts on the tensor cores, for the
 // tensor-core form of the preconditioner (Section 2.3: S = F22 - L21 U12 of each
-// front, here with the K = 256 columns of one outer block of the blocked LU):
+// front, here with the K = 1024 or 256 columns of one outer block or sub-block of the
+// blocked LU):
 //
 //   C[M x N] -= A[M x K] B[K x N]      (column-major, batched over fronts)
 //
