@@ -117,6 +117,8 @@ def parse():
     p.add_argument("--device-loop", type=int, default=1, choices=[0, 1],
                    help="sp_opts.device_loop: 1 runs each GMRES restart cycle as one CUDA "
                         "graph (conditional while node), 0 lets the host drive each iteration")
+    p.add_argument("--tc-epilogue", type=int, default=0, choices=[0, 1, 2, 3],
+                   help="sp_opts.tc_epilogue of the 3D tensor-core forms (C reads of the update)")
     p.add_argument("--no-autotune", action="store_true",
                    help="2D contexts keep the built-in launch-shape heuristics instead of "
                         "tuning them at set-up (sp_opts.autotune; results are bit-identical)")
@@ -370,7 +372,8 @@ def _measure_3d_one(args, B, torch, flush, w, forms, tf32_peak, dist, world, pro
         t0 = time.perf_counter()
         S = B.Solver(d, n, b, s, prec=prec, device=int(os.environ.get("LOCAL_RANK", "0")),
                      setup_route=args.setup_route_3d, sweeps=args.sweeps,
-                     device_loop=args.device_loop, factor_storage=1 if half else 0)
+                     device_loop=args.device_loop, factor_storage=1 if half else 0,
+                     tc_epilogue=args.tc_epilogue)
         setup_s = time.perf_counter() - t0
         for _ in range(warm):
             S.factor(qd)

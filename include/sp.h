@@ -104,9 +104,11 @@ typedef struct {
                         larger blocks mean fewer, longer launches per sweep and more
                         work in the block inverses */
   int tc_epilogue;   /* tensor-core forms: how the Schur update reads C.  0 (default)
-                        or 2: through a shared-memory ring that cp.async fills a tile
-                        ahead (three operand stages); 1: into registers only (four
-                        operand stages).  Both give the same bits. */
+                        or 3: a tile ahead, three of its four 32-column chunks in
+                        registers and one in a shared-memory slot that cp.async fills
+                        (four operand stages); 2: two chunks in registers and two slots
+                        (three operand stages); 1: the next chunk only, in registers
+                        (four operand stages).  All give the same bits. */
   long long wait_limit_ns; /* limit of each bounded wait of the cooperative grid panel
                         (the LU panel of fronts too tall for a thread-block cluster:
                         every CTA polls the pivot candidates its peers publish) in

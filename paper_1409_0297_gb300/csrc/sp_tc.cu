@@ -173,7 +173,8 @@ __device__ __forceinline__ void tile_coords(long t, int tilesM, int tilesN, int 
 // (warps 0-7) draining the other accumulator: warp w reads TMEM lanes 32 (w % 4)
 // .. +31 (tile rows) and column half w / 4, subtracts from C with the C loads of
 // later chunks already in flight (CRING = 2: the next tile's four chunks, two in
-// registers and two in shared-memory slots after the STAGES operand stages;
+// registers and two in shared-memory slots after the STAGES operand stages; CRING = 1:
+// three in registers and one slot, which leaves room for four operand stages;
 // CRING = 0: the next chunk, in registers).
 template <int BN, int STAGES, int CRING>
 __global__ void __launch_bounds__(kPThreads, 1) tc_gemm_sub_kernel(
@@ -278,16 +279,17 @@ __global__ void __launch_bounds__(kPThreads, 1) tc_gemm_sub_kernel(
     }
   } else {
     if constexpr (CRING > 0) {
-      // epilogue: four chunks of 32 columns per tile; chunks 0 and 1 of the C tile are
-      // loaded into two register buffers, chunks 2 and 3 by cp.async into two
-      // shared-memory slots, each issued as soon as the same chunk of the previous tile
-      // has been stored, so a whole tile of C loads is in flight ahead of its use
+      // epilogue: four chunks of 32 columns per tile; the first 4 - CRING chunks of the
+      // C tile are loaded into register buffers, the last CRING by cp.async into
+      // shared-memory slots, each issued as soon as the same chunk of the previous
+      // tile has been stored, so a whole tile of C loads is in flight ahead of its use
       static_assert(kHalf == 128, "the C ring assumes BN = 256");
+      constexpr int kReg = 4 - CRING;
       const int qw = warp & 3, h = warp >> 2;
       const int et = threadIdx.x;  // 0 .. 255
       const uint32_t ring_s = base + STAGES * kStage;
       const float* ring = reinterpret_cast<const float*>(smraw + (ring_s - smem_u32(smraw)));
-      float cA[32], cB[32];
+      float creg[kReg][32];
       auto locate = [&](long tt, float** cp, int* ncol) {
         int f, m0, n0;
         tile_coords(tt, tilesM, tilesN, BN, &f, &m0, &n0);
@@ -314,10 +316,10 @@ __global__ void __launch_bounds__(kPThreads, 1) tc_gemm_sub_kernel(
       int ncol = 0;
       if (t < ntiles) {
         locate(t, &cp, &ncol);
-        load(cA, cp, ncol, 0);
-        load(cB, cp, ncol, 32);
-        sload(0, cp, ncol, 64);
-        sload(1, cp, ncol, 96);
+#pragma unroll
+        for (int j = 0; j < kReg; ++j) load(creg[j], cp, ncol, 32 * j);
+#pragma unroll
+        for (int sl = 0; sl < CRING; ++sl) sload(sl, cp, ncol, 32 * (kReg + sl));
       }
       for (long i = 0; t < ntiles; t += gridDim.x, ++i) {
         const int buf = (int)(i & 1);
@@ -333,29 +335,30 @@ __global__ void __launch_bounds__(kPThreads, 1) tc_gemm_sub_kernel(
         int ncol_nx = 0;
         if (t + gridDim.x < ntiles) locate(t + gridDim.x, &cp_nx, &ncol_nx);
         uint32_t v[32];
-        // chunk 0 (register buffer A)
-        tmem_ld32(ta, v);
+        // register chunks: store this tile's, load the next tile's
 #pragma unroll
-        for (int q = 0; q < 32; ++q)
-          if (q < ncol) cp[(long)q * ldc] = cA[q] - __uint_as_float(v[q]);
-        load(cA, cp_nx, ncol_nx, 0);
-        // chunk 1 (register buffer B)
-        tmem_ld32(ta + 32, v);
-#pragma unroll
-        for (int q = 0; q < 32; ++q)
-          if (32 + q < ncol) cp[(long)(32 + q) * ldc] = cB[q] - __uint_as_float(v[q]);
-        load(cB, cp_nx, ncol_nx, 32);
-        // chunks 2 and 3 (shared-memory slots; at each point at most the newest
-        // group, the other slot's, is still in flight)
-#pragma unroll
-        for (int sl = 0; sl < 2; ++sl) {
-          asm volatile("cp.async.wait_group 1;" ::: "memory");
-          tmem_ld32(ta + 64 + 32 * sl, v);
+        for (int j = 0; j < kReg; ++j) {
+          tmem_ld32(ta + 32 * j, v);
 #pragma unroll
           for (int q = 0; q < 32; ++q)
-            if (64 + 32 * sl + q < ncol)
-              cp[(long)(64 + 32 * sl + q) * ldc] = ring[(sl * 32 + q) * 256 + et] - __uint_as_float(v[q]);
-          sload(sl, cp_nx, ncol_nx, 64 + 32 * sl);
+            if (32 * j + q < ncol) cp[(long)(32 * j + q) * ldc] = creg[j][q] - __uint_as_float(v[q]);
+          load(creg[j], cp_nx, ncol_nx, 32 * j);
+        }
+        // shared-memory chunks (at each point at most the groups of the later slots
+        // are still in flight: groups complete in order)
+#pragma unroll
+        for (int sl = 0; sl < CRING; ++sl) {
+          if constexpr (CRING == 2)
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+          else
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+          const int c0 = 32 * (kReg + sl);
+          tmem_ld32(ta + c0, v);
+#pragma unroll
+          for (int q = 0; q < 32; ++q)
+            if (c0 + q < ncol)
+              cp[(long)(c0 + q) * ldc] = ring[(sl * 32 + q) * 256 + et] - __uint_as_float(v[q]);
+          sload(sl, cp_nx, ncol_nx, c0);
         }
         cp = cp_nx;
         ncol = ncol_nx;
@@ -515,14 +518,20 @@ cudaError_t encode_operand(CUtensorMap* map, float* P, int rows, int Kp, int bat
 }
 
 constexpr int kBN = 256;
-// two configurations of the same kernel: three operand stages plus two 32 KB
-// shared-memory slots that cp.async fills with C a tile ahead (the default: the
-// epilogue's C loads limit the update; 3D 128^3 TF32 factor: 1.64 s of updates
-// against 1.72 s), or four stages with the C loads in registers only
+// three configurations of the same kernel: four operand stages plus one 32 KB
+// shared-memory slot that cp.async fills with C a tile ahead, the other three chunks
+// of the next C tile in registers (the default; 3D 128^3 TF32 factor, depth-1024
+// updates: 646 TFLOP/s); three stages plus two slots (583 TFLOP/s); four stages with
+// only the next chunk of C in registers (at depth 512: 1.72 s of updates against
+// 1.64 s with two slots)
 constexpr int kStages = 4, kStagesRing = 3;
 constexpr size_t kSmem = (size_t)kStages * (kBM * kBK * 4 + kBN * kBK * 4) + 1024;
 constexpr size_t kSmemRing =
     (size_t)kStagesRing * (kBM * kBK * 4 + kBN * kBK * 4) + 1024 + 2 * 32 * 256 * 4;
+// four stages and one 32 KB C slot (three C chunks a tile ahead in registers): 225 KB
+constexpr size_t kSmemRing1 =
+    (size_t)kStages * (kBM * kBK * 4 + kBN * kBK * 4) + 1024 + 1 * 32 * 256 * 4;
+static_assert(kSmemRing1 <= 227 * 1024 - 512, "dynamic shared memory of the 4-stage ring");
 int g_num_sms[64] = {0};
 
 }  // namespace
@@ -541,6 +550,9 @@ cudaError_t tc_set_attributes() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(tc_gemm_sub_kernel<kBN, kStagesRing, 2>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemRing);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(tc_gemm_sub_kernel<kBN, kStages, 1>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemRing1);
   if (e != cudaSuccess) return e;
   attr = true;
   return cudaSuccess;
@@ -561,7 +573,10 @@ cudaError_t tc_run(int M, int N, int Ke, float* C, int ldc, long sC, int batch, 
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!g_num_sms[dev]) cudaDeviceGetAttribute(&g_num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
   const unsigned grid = (unsigned)std::min<long>(ntiles, std::max(1, g_num_sms[dev]));
-  if (epi != 1)
+  if (epi == 0 || epi == 3)
+    tc_gemm_sub_kernel<kBN, kStages, 1><<<grid, kPThreads, kSmemRing1, st>>>(
+        ta, tb, M, N, Ke / kBK, C, ldc, sC, tilesM, tilesN, ntiles, status);
+  else if (epi != 1)
     tc_gemm_sub_kernel<kBN, kStagesRing, 2><<<grid, kPThreads, kSmemRing, st>>>(
         ta, tb, M, N, Ke / kBK, C, ldc, sC, tilesM, tilesN, ntiles, status);
   else

@@ -389,15 +389,16 @@ def test_inverse_block_sizes(B, name, make, ib):
 
 
 def test_tc_epilogues_bit_identical(B):
-    """Both epilogues of the tensor-core Schur update (C in registers with four operand
-    stages, or the cp.async shared-memory ring with three) read the same C and add the
-    same FP32 accumulator: the factor, and so the preconditioner, is bit-identical."""
+    """The epilogues of the tensor-core Schur update (C in registers with four operand
+    stages; the cp.async shared-memory ring with two slots and three stages, or one slot
+    and four stages) read the same C and add the same FP32 accumulator: the factor, and
+    so the preconditioner, is bit-identical."""
     w = sm.helmholtz_grf_3d(16, 4, 0)
     d, n, b = w["d"], w["n"], w["b"]
     s, q, f = medium(w)
     r = dev(sm.random_complex_vector(n ** d, 35))
     out = []
-    for epi in (1, 2, 0):
+    for epi in (1, 2, 0, 3):
         S = B.Solver(d, n, b, s, prec=3, tc_epilogue=epi)
         S.factor(dev(q))
         z = torch.empty(n ** d, dtype=torch.complex128, device="cuda")
@@ -405,9 +406,9 @@ def test_tc_epilogues_bit_identical(B):
         torch.cuda.synchronize()
         out.append(z)
         S.close()
-    assert torch.equal(out[0], out[1]) and torch.equal(out[0], out[2])
+    assert all(torch.equal(out[0], o) for o in out[1:])
     with pytest.raises(B.SpError):
-        B.Solver(d, n, b, s, prec=3, tc_epilogue=3)
+        B.Solver(d, n, b, s, prec=3, tc_epilogue=4)
 
 
 def test_solve_3d64_tf32_grid_panel(B):
