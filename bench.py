@@ -117,7 +117,7 @@ def parse():
     p.add_argument("--device-loop", type=int, default=1, choices=[0, 1],
                    help="sp_opts.device_loop: 1 runs each GMRES restart cycle as one CUDA "
                         "graph (conditional while node), 0 lets the host drive each iteration")
-    p.add_argument("--tc-epilogue", type=int, default=0, choices=[0, 1, 2, 3],
+    p.add_argument("--tc-epilogue", type=int, default=0, choices=[0, 1, 2, 3, 4],
                    help="sp_opts.tc_epilogue of the 3D tensor-core forms (C reads of the update)")
     p.add_argument("--no-autotune", action="store_true",
                    help="2D contexts keep the built-in launch-shape heuristics instead of "

@@ -108,7 +108,9 @@ typedef struct {
                         registers and one in a shared-memory slot that cp.async fills
                         (four operand stages); 2: two chunks in registers and two slots
                         (three operand stages); 1: the next chunk only, in registers
-                        (four operand stages).  All give the same bits. */
+                        (four operand stages); 4: as 0 in thread-block clusters of two
+                        CTAs that share each B tile by TMA multicast (slower: 557 against
+                        637 TFLOP/s at 3D 128^3).  All give the same bits. */
   long long wait_limit_ns; /* limit of each bounded wait of the cooperative grid panel
                         (the LU panel of fronts too tall for a thread-block cluster:
                         every CTA polls the pivot candidates its peers publish) in

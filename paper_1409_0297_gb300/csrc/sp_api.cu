@@ -672,7 +672,7 @@ static sp_status setup_impl(int d, int n, int b, int P, const double* shifts, sp
     const int ib = c->opts.inv_block;
     if (ib != 0 && (ib < 64 || ib > 2048 || (ib & (ib - 1)) != 0)) return SP_ERR_ARG;
   }
-  if (c->opts.tc_epilogue < 0 || c->opts.tc_epilogue > 3) return SP_ERR_ARG;
+  if (c->opts.tc_epilogue < 0 || c->opts.tc_epilogue > 4) return SP_ERR_ARG;
   if (c->opts.wait_limit_ns < 0 || c->opts.wait_limit_ns > 60000000000LL) return SP_ERR_ARG;
   if (c->opts.sweeps < 0 || c->opts.sweeps > 2) return SP_ERR_ARG;
   if (c->opts.panel_pivoting != 0 && c->opts.panel_pivoting != 1) return SP_ERR_ARG;

@@ -84,6 +84,20 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
       : "memory");
 }
+// the same copy delivered to the CTAs of ctamask (same shared-memory offset and
+// mbarrier offset in each)
+__device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                               int c2, uint32_t bar, uint16_t ctamask) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      ".multicast::cluster [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(dst),
+      "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(bar), "h"(ctamask)
+      : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -109,6 +123,15 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, unsigned long long ad,
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+// arrive (once the MMAs issued so far complete) on the mbarrier at this offset in every
+// CTA of ctamask
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t ctamask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(bar),
+      "h"(ctamask)
       : "memory");
 }
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
@@ -176,7 +199,13 @@ __device__ __forceinline__ void tile_coords(long t, int tilesM, int tilesN, int 
 // registers and two in shared-memory slots after the STAGES operand stages; CRING = 1:
 // three in registers and one slot, which leaves room for four operand stages;
 // CRING = 0: the next chunk, in registers).
-template <int BN, int STAGES, int CRING>
+// CL = 2: the CTAs run in thread-block clusters of two that take row tiles m0 and
+// m0 + 128 of the same column block together; each loads its own A and half of the B
+// tile (tmB's box is 128 rows) and multicasts that half to both, so a stage costs a CTA
+// 32 KB of L2 reads instead of 48; a stage is refilled once both CTAs' products have
+// released it (the MMA commits arrive on both CTAs' empty barriers).  ntiles then
+// counts pairs of row tiles.  The products of every tile are those of CL = 1.
+template <int BN, int STAGES, int CRING, int CL = 1>
 __global__ void __launch_bounds__(kPThreads, 1) tc_gemm_sub_kernel(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M,
     int N, int nk, float* C, int ldc, long sC, int tilesM, int tilesN, long ntiles, int* status) {
@@ -197,11 +226,20 @@ __global__ void __launch_bounds__(kPThreads, 1) tc_gemm_sub_kernel(
   volatile int* ab = &s_abort;
   const uint32_t base = (smem_u32(smraw) + 1023u) & ~1023u;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t crank = 0;
+  if constexpr (CL == 2) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(crank));
+  const long tfirst = CL == 2 ? blockIdx.x / 2 : blockIdx.x;
+  const long tstep = CL == 2 ? gridDim.x / 2 : gridDim.x;
+  const int tilesMu = CL == 2 ? (tilesM + 1) / 2 : tilesM;  // row units: tile pairs for CL = 2
+  auto coords = [&](long t, int* f, int* m0, int* n0) {
+    tile_coords(t, tilesMu, tilesN, BN, f, m0, n0);
+    if constexpr (CL == 2) *m0 = 2 * *m0 + (int)crank * kBM;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
-      mbar_init(smem_u32(&empty[s]), 1);
+      mbar_init(smem_u32(&empty[s]), CL);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&acc_full[b]), 1);
@@ -222,15 +260,16 @@ __global__ void __launch_bounds__(kPThreads, 1) tc_gemm_sub_kernel(
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (CL == 2) cluster_sync_all();  // the peer's barriers exist before any multicast
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
   if (warp == kEpiWarps) {
     if (lane == 0) {  // TMA producer
       long long g = 0;
-      for (long t = blockIdx.x; t < ntiles && !*ab; t += gridDim.x) {
+      for (long t = tfirst; t < ntiles && !*ab; t += tstep) {
         int f, m0, n0;
-        tile_coords(t, tilesM, tilesN, BN, &f, &m0, &n0);
+        coords(t, &f, &m0, &n0);
         for (int kb = 0; kb < nk; ++kb, ++g) {
           const int s = (int)(g % STAGES);
           if (g >= STAGES &&
@@ -239,17 +278,27 @@ __global__ void __launch_bounds__(kPThreads, 1) tc_gemm_sub_kernel(
           const uint32_t fb = smem_u32(&full[s]);
           mbar_expect_tx(fb, kStage);
           tma_load_3d(base + s * kStage, &tmA, kb * kBK, m0, f, fb);
-          tma_load_3d(base + s * kStage + kABytes, &tmB, kb * kBK, n0, f, fb);
+          if constexpr (CL == 2)
+            tma_load_3d_mc(base + s * kStage + kABytes + crank * (kBBytes / 2), &tmB, kb * kBK,
+                           n0 + (int)crank * kHalf, f, fb, (uint16_t)0x3);
+          else
+            tma_load_3d(base + s * kStage + kABytes, &tmB, kb * kBK, n0, f, fb);
         }
         if (*ab) break;
       }
       s_issued = g;
+      if constexpr (CL == 2) {
+        // the last stages' releases, the peer's included, have arrived before this CTA
+        // may leave the cluster
+        for (long long i = g > STAGES ? g - STAGES : 0; i < g && !*ab; ++i)
+          if (!mbar_wait_ab(smem_u32(&empty[i % STAGES]), (uint32_t)((i / STAGES) & 1), ab)) break;
+      }
     }
   } else if (warp == kEpiWarps + 1) {
     if (lane == 0) {  // MMA issuer
       long long g = 0;
       long i = 0;
-      for (long t = blockIdx.x; t < ntiles && !*ab; t += gridDim.x, ++i) {
+      for (long t = tfirst; t < ntiles && !*ab; t += tstep, ++i) {
         const int buf = (int)(i & 1);
         const long u = i >> 1;
         if (u >= 1 && !mbar_wait_ab(smem_u32(&acc_empty[buf]), (uint32_t)((u - 1) & 1), ab)) break;
@@ -268,7 +317,10 @@ __global__ void __launch_bounds__(kPThreads, 1) tc_gemm_sub_kernel(
 #pragma unroll
           for (int kk = 0; kk < kBK / kUK; ++kk)  // +32 bytes along K = +2 in the address field
             mma_tf32(d, ad + 2 * kk, bd + 2 * kk, kIdesc, (kb | kk) != 0 ? 1u : 0u);
-          mma_commit(smem_u32(&empty[s]));
+          if constexpr (CL == 2)
+            mma_commit_mc(smem_u32(&empty[s]), (uint16_t)0x3);
+          else
+            mma_commit(smem_u32(&empty[s]));
         }
         if (!okk) break;
         mma_commit(smem_u32(&acc_full[buf]));
@@ -292,7 +344,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tc_gemm_sub_kernel(
       float creg[kReg][32];
       auto locate = [&](long tt, float** cp, int* ncol) {
         int f, m0, n0;
-        tile_coords(tt, tilesM, tilesN, BN, &f, &m0, &n0);
+        coords(tt, &f, &m0, &n0);
         const int row = m0 + qw * 32 + lane;
         *ncol = row < M ? min(kHalf, N - (n0 + h * kHalf)) : 0;
         *cp = C + (long)f * sC + row + (long)(n0 + h * kHalf) * ldc;
@@ -311,7 +363,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tc_gemm_sub_kernel(
                          : "memory");
         asm volatile("cp.async.commit_group;" ::: "memory");
       };
-      long t = blockIdx.x;
+      long t = tfirst;
       float* cp = C;
       int ncol = 0;
       if (t < ntiles) {
@@ -321,7 +373,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tc_gemm_sub_kernel(
 #pragma unroll
         for (int sl = 0; sl < CRING; ++sl) sload(sl, cp, ncol, 32 * (kReg + sl));
       }
-      for (long i = 0; t < ntiles; t += gridDim.x, ++i) {
+      for (long i = 0; t < ntiles; t += tstep, ++i) {
         const int buf = (int)(i & 1);
         const long u = i >> 1;
         int okw = 0;
@@ -333,7 +385,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tc_gemm_sub_kernel(
         const uint32_t ta = tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)(buf * BN + h * kHalf);
         float* cp_nx = cp;
         int ncol_nx = 0;
-        if (t + gridDim.x < ntiles) locate(t + gridDim.x, &cp_nx, &ncol_nx);
+        if (t + tstep < ntiles) locate(t + tstep, &cp_nx, &ncol_nx);
         uint32_t v[32];
         // register chunks: store this tile's, load the next tile's
 #pragma unroll
@@ -376,7 +428,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tc_gemm_sub_kernel(
       float cA[32], cB[32];
       auto locate = [&](long tt, float** cp, int* ncol) {
         int f, m0, n0;
-        tile_coords(tt, tilesM, tilesN, BN, &f, &m0, &n0);
+        coords(tt, &f, &m0, &n0);
         const int row = m0 + qw * 32 + lane;
         *ncol = row < M ? min(kHalf, N - (n0 + h * kHalf)) : 0;
         *cp = C + (long)f * sC + row + (long)(n0 + h * kHalf) * ldc;
@@ -385,14 +437,14 @@ __global__ void __launch_bounds__(kPThreads, 1) tc_gemm_sub_kernel(
 #pragma unroll
         for (int j = 0; j < 32; ++j) buf[j] = c0 + j < ncol ? cp[(long)(c0 + j) * ldc] : 0.f;
       };
-      long t = blockIdx.x;
+      long t = tfirst;
       float* cp = C;
       int ncol = 0;
       if (t < ntiles) {
         locate(t, &cp, &ncol);
         load(cA, cp, ncol, 0);
       }
-      for (long i = 0; t < ntiles; t += gridDim.x, ++i) {
+      for (long i = 0; t < ntiles; t += tstep, ++i) {
         const int buf = (int)(i & 1);
         const long u = i >> 1;
         if (kChunks > 1) load(cB, cp, ncol, 32);
@@ -406,8 +458,8 @@ __global__ void __launch_bounds__(kPThreads, 1) tc_gemm_sub_kernel(
         const uint32_t ta = tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)(buf * BN + h * kHalf);
         float* cp_nx = cp;
         int ncol_nx = 0;
-        const bool has_next = t + gridDim.x < ntiles;
-        if (has_next) locate(t + gridDim.x, &cp_nx, &ncol_nx);
+        const bool has_next = t + tstep < ntiles;
+        if (has_next) locate(t + tstep, &cp_nx, &ncol_nx);
 #pragma unroll
         for (int j = 0; j < kChunks; ++j) {
           float* cur = (j & 1) ? cB : cA;
@@ -437,6 +489,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tc_gemm_sub_kernel(
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (CL == 2) cluster_sync_all();  // no multicast or remote arrival still targets us
   if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -554,6 +607,9 @@ cudaError_t tc_set_attributes() {
   e = cudaFuncSetAttribute(tc_gemm_sub_kernel<kBN, kStages, 1>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemRing1);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(tc_gemm_sub_kernel<kBN, kStages, 1, 2>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemRing1);
+  if (e != cudaSuccess) return e;
   attr = true;
   return cudaSuccess;
 }
@@ -564,7 +620,8 @@ cudaError_t tc_run(int M, int N, int Ke, float* C, int ldc, long sC, int batch, 
   CUtensorMap ta, tb;
   cudaError_t e = encode_operand(&ta, packA, M, Ke, batch, kBM);
   if (e != cudaSuccess) return e;
-  e = encode_operand(&tb, packB, N, Ke, batch, kBN);
+  // the cluster form loads B in halves (each CTA of a pair multicasts one)
+  e = encode_operand(&tb, packB, N, Ke, batch, epi == 4 ? kBN / 2 : kBN);
   if (e != cudaSuccess) return e;
   const int tilesM = (M + kBM - 1) / kBM, tilesN = (N + kBN - 1) / kBN;
   const long ntiles = (long)tilesM * tilesN * batch;
@@ -573,6 +630,29 @@ cudaError_t tc_run(int M, int N, int Ke, float* C, int ldc, long sC, int batch, 
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!g_num_sms[dev]) cudaDeviceGetAttribute(&g_num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
   const unsigned grid = (unsigned)std::min<long>(ntiles, std::max(1, g_num_sms[dev]));
+  if (epi == 4) {
+    // clusters of two CTAs on pairs of row tiles, as many clusters as fit at once
+    const long npairs = (long)((tilesM + 1) / 2) * tilesN * batch;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kPThreads);
+    cfg.dynamicSmemBytes = kSmemRing1;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3((unsigned)(2 * std::max(1, g_num_sms[dev] / 2)));
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, tc_gemm_sub_kernel<kBN, kStages, 1, 2>, &cfg) !=
+            cudaSuccess || ncl < 1)
+      return cudaErrorInvalidConfiguration;
+    cfg.gridDim = dim3((unsigned)(2 * std::min<long>(ncl, npairs)));
+    return cudaLaunchKernelEx(&cfg, tc_gemm_sub_kernel<kBN, kStages, 1, 2>, ta, tb, M, N,
+                              Ke / kBK, C, ldc, sC, tilesM, tilesN, npairs, status);
+  }
   if (epi == 0 || epi == 3)
     tc_gemm_sub_kernel<kBN, kStages, 1><<<grid, kPThreads, kSmemRing1, st>>>(
         ta, tb, M, N, Ke / kBK, C, ldc, sC, tilesM, tilesN, ntiles, status);

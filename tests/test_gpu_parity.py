@@ -389,16 +389,17 @@ def test_inverse_block_sizes(B, name, make, ib):
 
 
 def test_tc_epilogues_bit_identical(B):
-    """The epilogues of the tensor-core Schur update (C in registers with four operand
-    stages; the cp.async shared-memory ring with two slots and three stages, or one slot
-    and four stages) read the same C and add the same FP32 accumulator: the factor, and
-    so the preconditioner, is bit-identical."""
+    """The configurations of the tensor-core Schur update (C in registers with four
+    operand stages; the cp.async shared-memory ring with two slots and three stages, or
+    one slot and four stages; the same in clusters of two CTAs sharing each B tile by
+    TMA multicast) issue the same products per tile, read the same C and add the same
+    FP32 accumulator: the factor, and so the preconditioner, is bit-identical."""
     w = sm.helmholtz_grf_3d(16, 4, 0)
     d, n, b = w["d"], w["n"], w["b"]
     s, q, f = medium(w)
     r = dev(sm.random_complex_vector(n ** d, 35))
     out = []
-    for epi in (1, 2, 0, 3):
+    for epi in (1, 2, 0, 3, 4):
         S = B.Solver(d, n, b, s, prec=3, tc_epilogue=epi)
         S.factor(dev(q))
         z = torch.empty(n ** d, dtype=torch.complex128, device="cuda")
@@ -408,7 +409,7 @@ def test_tc_epilogues_bit_identical(B):
         S.close()
     assert all(torch.equal(out[0], o) for o in out[1:])
     with pytest.raises(B.SpError):
-        B.Solver(d, n, b, s, prec=3, tc_epilogue=4)
+        B.Solver(d, n, b, s, prec=3, tc_epilogue=5)
 
 
 def test_solve_3d64_tf32_grid_panel(B):
