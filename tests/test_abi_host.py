@@ -63,6 +63,29 @@ def test_argument_checks_need_no_gpu():
     assert e.value.status == B.SP_ERR_RESONANT
 
 
+def test_group_argument_checks_need_no_gpu():
+    """sp_setup_group refuses, before touching the device: no problems, a resonant shift
+    among them, the mixed-precision form with several problems, more than 1024 Krylov
+    instances (P max_rhs), a bad grid; and the FP16 factor copy in the plain FP64 form."""
+    B = _binding()
+    cases = [
+        (dict(shifts=[]), B.SP_ERR_ARG),
+        (dict(shifts=[100.0, 4 * np.pi ** 2 * 25]), B.SP_ERR_RESONANT),
+        (dict(shifts=[100.0, 101.0], prec=B.SP_PREC_MIXED), B.SP_ERR_ARG),
+        (dict(shifts=[100.0] * 129, max_rhs=8), B.SP_ERR_ARG),
+        (dict(shifts=[100.0, 101.0], n=48, b=4), B.SP_ERR_ARG),
+        (dict(shifts=[100.0], factor_storage=1, prec=B.SP_PREC_FP64), B.SP_ERR_ARG),
+    ]
+    for kw, status in cases:
+        o = B.sp_default_opts()
+        o.max_rhs = kw.get("max_rhs", 1)
+        o.factor_storage = kw.get("factor_storage", 0)
+        with pytest.raises(B.SpError) as e:
+            B.sp_setup_group(2, kw.get("n", 64), kw.get("b", 4), kw["shifts"],
+                             kw.get("prec", B.SP_PREC_FP32), o)
+        assert e.value.status == status, kw
+
+
 @pytest.mark.parametrize("d,n,b", [(2, 64, 4), (2, 24, 3), (3, 8, 2), (3, 16, 4)])
 def test_host_tables_match_oracle(d, n, b):
     B = _binding()
