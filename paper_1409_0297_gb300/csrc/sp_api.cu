@@ -1,7 +1,10 @@
-// C ABI of the library (include/sp.h): context set-up, factorisation, preconditioner
-// application and the GMRES driver.  The driver runs on the host but every vector
-// operation is a device kernel; the host reads two scalars per iteration (the
-// Givens estimate and the new Arnoldi norm) to decide whether to stop.
+// C ABI of the library (include/sp.h): context set-up (single problems and problem
+// groups), factorisation, preconditioner application and the GMRES driver.  Every
+// vector operation is a device kernel.  By default a GMRES restart cycle is one CUDA
+// graph whose Arnoldi step repeats under a conditional while node, the stopping test
+// on the device, and the host reads the cycle's outcome once (the true residual
+// decides a restart); with device_loop = 0 the host reads two scalars per iteration
+// (the Givens estimate and the new Arnoldi norm) to decide whether to stop.
 #include <cuda_runtime.h>
 
 #include <algorithm>

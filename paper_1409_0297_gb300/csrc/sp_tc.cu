@@ -575,8 +575,8 @@ constexpr int kBN = 256;
 // shared-memory slot that cp.async fills with C a tile ahead, the other three chunks
 // of the next C tile in registers (the default; 3D 128^3 TF32 factor, depth-1024
 // updates: 646 TFLOP/s); three stages plus two slots (583 TFLOP/s); four stages with
-// only the next chunk of C in registers (at depth 512: 1.72 s of updates against
-// 1.64 s with two slots)
+// only the next chunk of C in registers (at depth 512 slower than two slots: 1.72
+// against 1.64 s of updates per factorisation)
 constexpr int kStages = 4, kStagesRing = 3;
 constexpr size_t kSmem = (size_t)kStages * (kBM * kBK * 4 + kBN * kBK * 4) + 1024;
 constexpr size_t kSmemRing =
