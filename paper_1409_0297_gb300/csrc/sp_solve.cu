@@ -147,7 +147,8 @@ __global__ void qapply_kernel(int d, int n, int nl, int nS, int nB, int self,
 // for every instance).  CTA (instance block, stacked vector, row tile): rows
 // [z kQRt, z kQRt + kQRt) of S for kQIt consecutive instances; per 32-column chunk
 // of B the CTA stages T_t(rows, chunk) and the gathered r(B chunk, instances) in
-// shared memory; each thread keeps 4 rows x 2 instances.  Every output is summed in
+// shared memory (the next chunk's loads in flight meanwhile); each thread keeps 4 rows x
+// 2 instances.  Every output is summed in
 // the order of the kernel above (self term first, then the columns of B in order),
 // so both give the same bits.
 constexpr int kQRt = 64, kQIt = 32, kQK = 32;
@@ -194,19 +195,41 @@ __global__ void __launch_bounds__(256) qgemm_kernel(int d, int n, int nl, int nS
       if (self && row < nS && i0 + ii < ninst)
         acc[q][j] = from_d2<VT>(r[q_addr(d, n, org[ii], Soff + row * d)]);
     }
+  // the next chunk's T entries and gathered r values are loaded into registers while
+  // the current chunk is multiplied (each thread 8 of T, 4 of r)
+  constexpr int kTe = kQK * kQRt / 256, kRe = kQK * kQIt / 256;
+  T tpre[kTe];
+  VT rpre[kRe];
+  auto fetch = [&](int k0) {
+    const int kc = min(kQK, nB - k0);
+#pragma unroll
+    for (int u = 0; u < kTe; ++u) {
+      const int e = tid + 256 * u, rr = e % kQRt, kk = e / kQRt;
+      tpre[u] = (row0 + rr < nS && kk < kc) ? Tt[(row0 + rr) + (long)(k0 + kk) * nS] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kRe; ++u) {
+      const int e = tid + 256 * u, ii = e % kQIt, kk = e / kQIt;
+      rpre[u] = (kk < kc && i0 + ii < ninst)
+                    ? from_d2<VT>(r[q_addr(d, n, org[ii], Boff + (k0 + kk) * d)])
+                    : VT{0, 0};
+    }
+  };
+  fetch(0);
   for (int k0 = 0; k0 < nB; k0 += kQK) {
     const int kc = min(kQK, nB - k0);
-    for (int e = tid; e < kQK * kQRt; e += 256) {
-      const int rr = e % kQRt, kk = e / kQRt;
-      Ts[kk][rr] = (row0 + rr < nS && kk < kc) ? Tt[(row0 + rr) + (long)(k0 + kk) * nS] : T(0);
+#pragma unroll
+    for (int u = 0; u < kTe; ++u) {
+      const int e = tid + 256 * u;
+      Ts[e / kQRt][e % kQRt] = tpre[u];
     }
-    for (int e = tid; e < kQK * kQIt; e += 256) {
-      const int ii = e % kQIt, kk = e / kQIt;
-      Rs[kk][ii] = (kk < kc && i0 + ii < ninst)
-                       ? from_d2<VT>(r[q_addr(d, n, org[ii], Boff + (k0 + kk) * d)])
-                       : VT{0, 0};
+#pragma unroll
+    for (int u = 0; u < kRe; ++u) {
+      const int e = tid + 256 * u;
+      Rs[e / kQIt][e % kQIt] = rpre[u];
     }
     __syncthreads();
+    if (k0 + kQK < nB) fetch(k0 + kQK);
     for (int kk = 0; kk < kc; ++kk) {
       const VT r0 = Rs[kk][ig * 2], r1 = Rs[kk][ig * 2 + 1];
 #pragma unroll
