@@ -89,14 +89,37 @@ __global__ void f16_copy_kernel(const float* fronts, int m, int k, __half* out, 
   __half* hc = out + f * (long)m * ld16 + (long)c * ld16;
   const int rows = c < k ? m : k;
   if (lane == 0 && ld16 > m) hc[m] = __float2half_rn(0.f);
-  float mx = 0.f;
-  for (int r = lane; r < rows; r += 32) mx = fmaxf(mx, fabsf(col[r]));
+  // both passes over the column keep eight loads per lane in flight
+  constexpr int kU = 8;
+  float mxu[kU];
+#pragma unroll
+  for (int u = 0; u < kU; ++u) mxu[u] = 0.f;
+  int r = lane;
+  for (; r + 32 * (kU - 1) < rows; r += 32 * kU) {
+    float v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) v[u] = col[r + 32 * u];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) mxu[u] = fmaxf(mxu[u], fabsf(v[u]));
+  }
+  for (; r < rows; r += 32) mxu[0] = fmaxf(mxu[0], fabsf(col[r]));
+  float mx = mxu[0];
+#pragma unroll
+  for (int u = 1; u < kU; ++u) mx = fmaxf(mx, mxu[u]);
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   int e = 0;
   if (mx > 0.f) frexpf(mx, &e);
   const float inv = ldexpf(1.0f, 15 - e);
   if (lane == 0) fsc[f * m + c] = ldexpf(1.0f, e - 15);
-  for (int r = lane; r < rows; r += 32) hc[r] = __float2half_rn(col[r] * inv);
+  r = lane;
+  for (; r + 32 * (kU - 1) < rows; r += 32 * kU) {
+    float v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) v[u] = col[r + 32 * u];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) hc[r + 32 * u] = __float2half_rn(v[u] * inv);
+  }
+  for (; r < rows; r += 32) hc[r] = __float2half_rn(col[r] * inv);
 }
 
 // max |entry| of every front: CTAs over (chunk, front), atomicMax on the bit
@@ -105,9 +128,25 @@ __global__ void f16_copy_kernel(const float* fronts, int m, int k, __half* out, 
 template <class T>
 __global__ void front_scale_kernel(const T* fronts, long mm, double* scale) {
   const T* A = fronts + blockIdx.y * mm;
-  double mx = 0;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < mm; i += (long)gridDim.x * blockDim.x)
-    mx = fmax(mx, fabs((double)A[i]));
+  // eight independent loads in flight per thread (a loop-carried max with one load per
+  // trip is bound by memory latency, not bandwidth)
+  constexpr int kU = 8;
+  const long stride = (long)gridDim.x * blockDim.x;
+  double mxu[kU];
+#pragma unroll
+  for (int u = 0; u < kU; ++u) mxu[u] = 0;
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (kU - 1) * stride < mm; i += kU * stride) {
+    T v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) v[u] = A[i + u * stride];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) mxu[u] = fmax(mxu[u], fabs((double)v[u]));
+  }
+  for (; i < mm; i += stride) mxu[0] = fmax(mxu[0], fabs((double)A[i]));
+  double mx = mxu[0];
+#pragma unroll
+  for (int u = 1; u < kU; ++u) mx = fmax(mx, mxu[u]);
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0 && mx > 0)
     atomicMax(reinterpret_cast<unsigned long long*>(scale + blockIdx.y),
