@@ -50,12 +50,21 @@ __global__ void assemble_kernel(T* fronts, int m, int nasm, const int* __restric
   fronts[f * (long)m * m + row[e] + (long)c * m] = (T)fma(Ccat[ti], qi, Qcat[ti]);
 }
 
+// One launch per child position: the child's Schur block (rows and columns kc..mc-1 of
+// its front) is added into the parent front through the map.  Each thread adds kEaU
+// entries a block width apart in column-major order: it reads every child value, map
+// entry and parent value first and writes afterwards, so kEaU independent read chains
+// are in flight (the map is injective within one child position, so no two entries of a
+// launch meet in the parent).
+constexpr int kEaU = 4;
+
 template <class T>
 __global__ void extend_add_kernel(T* parent, int m, int nb1, const T* __restrict__ child, int mc,
                                   int kc, const int* __restrict__ map, int delta, int d) {
   const int nbd = mc - kc;
-  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (long)nbd * nbd) return;
+  const long nn = (long)nbd * nbd;
+  const long e0 = (long)blockIdx.x * (kEaU * blockDim.x) + threadIdx.x;
+  if (e0 >= nn) return;
   int f = blockIdx.y;
   // parent box coordinates -> child box id (child grid has 2*nb1 boxes per axis)
   int ff = f, cid = 0, stride = 1;
@@ -66,9 +75,29 @@ __global__ void extend_add_kernel(T* parent, int m, int nb1, const T* __restrict
     stride *= 2 * nb1;
   }
   cid += ff * stride;  // problem ff of a group: its children follow the earlier problems'
-  int i = (int)(e % nbd), j = (int)(e / nbd);
-  const T v = child[(long)cid * mc * mc + (long)(kc + i) + (long)(kc + j) * mc];
-  parent[(long)f * m * m + map[i] + (long)map[j] * m] += v;
+  const T* cf = child + (long)cid * mc * mc + kc + (long)kc * mc;
+  T* pf = parent + (long)f * m * m;
+  int i = (int)(e0 % nbd), j = (int)(e0 / nbd);
+  T v[kEaU];
+  long at[kEaU];
+#pragma unroll
+  for (int u = 0; u < kEaU; ++u) {
+    at[u] = -1;
+    if (e0 + (long)u * blockDim.x < nn) {
+      v[u] = cf[i + (long)j * mc];
+      at[u] = map[i] + (long)map[j] * m;
+    }
+    i += blockDim.x;  // next entry: blockDim.x further in column-major order
+    j += i / nbd;
+    i %= nbd;
+  }
+  T p[kEaU];
+#pragma unroll
+  for (int u = 0; u < kEaU; ++u)
+    if (at[u] >= 0) p[u] = pf[at[u]];
+#pragma unroll
+  for (int u = 0; u < kEaU; ++u)
+    if (at[u] >= 0) pf[at[u]] = p[u] + v[u];
 }
 
 // FP16 copy of the factor for the chained sweeps (sp_opts.factor_storage = 1), with a
@@ -1539,7 +1568,7 @@ cudaError_t factor_level_t(int d, DevLevel& L, const DevLevel* child, const doub
   if (child) {
     const int nbd = L.mc - L.kc;
     long work = (long)nbd * nbd;
-    dim3 g((unsigned)((work + 255) / 256), L.nf);
+    dim3 g((unsigned)((work + 256 * kEaU - 1) / (256 * kEaU)), L.nf);
     for (int dl = 0; dl < (1 << d); ++dl)
       extend_add_kernel<T><<<g, 256, 0, st>>>(F, L.m, L.nb1, (const T*)child->front, L.mc, L.kc,
                                                L.ea_map + (long)dl * nbd, dl, d);
