@@ -50,6 +50,29 @@ def test_spectral_conv_is_truncated_rfft2():
     assert np.allclose(z, z_np, rtol=0, atol=1e-12 * np.abs(z_np).max())
 
 
+def test_network_spectral_branch_is_truncated_irfft2():
+    """Inside the network: with the lift the identity, W_0 = 0 and b_0 = 0, layer 0's
+    pre-activation is the spectral convolution alone, which must equal numpy's irfft2 of
+    the truncated rfft2 spectrum mixed by R_0 (pins the weights the forward pass hands
+    the inverse transform, including the doubling of the kx >= 1 modes)."""
+    D = F.FnoDims(n=16, c_in=3, width=3, modes=5, layers=1, hidden=4, c_out=2)
+    parts = F.unpack(tiny_params(8, D), D)
+    rng = np.random.default_rng(9)
+    parts["P"] = np.eye(3)
+    parts["p"] = np.zeros(3)
+    parts["W0"] = np.zeros((3, 3))
+    parts["b0"] = np.zeros(3)
+    R = rng.standard_normal(parts["R0"].shape) + 1j * rng.standard_normal(parts["R0"].shape)
+    parts["R0"] = R
+    a = rng.standard_normal((2, 3, D.n, D.n))
+    _, cache = F.forward(F.pack(parts, D), a, D, keep=True)
+    ky = F.ky_list(D.n, D.modes)
+    pad = np.zeros((2, 3, D.n, D.n // 2 + 1), dtype=complex)
+    pad[:, :, ky, :D.modes] = F.mix(np.fft.rfft2(a)[:, :, ky, :D.modes], R)
+    z_np = np.fft.irfft2(pad, s=(D.n, D.n))
+    assert np.allclose(cache["h"][0], z_np, rtol=0, atol=1e-12 * np.abs(z_np).max())
+
+
 def test_gelu_is_x_times_normal_cdf():
     x = np.linspace(-6, 6, 101)
     assert np.allclose(F.gelu(x), x * norm.cdf(x), rtol=0, atol=1e-15)

@@ -166,6 +166,37 @@ def test_solve_matches_oracle_64(B):
         S.close()
 
 
+def test_solve_complex_source_matches_oracle(B):
+    """A white-noise source with independent real and imaginary parts, so the Krylov
+    basis, the Hessenberg matrix and the Givens rotations are genuinely complex (a real
+    field times one phase, as the workloads' sources are, keeps them real): the FP64
+    form follows the oracle's GMRES (iterations within one, estimate history to 1e-6)
+    and both the FP64 and the FP32 forms reach its solution to 1e-6."""
+    w = sm.helmholtz_centre_gaussian_64()
+    d, n, b = w["d"], w["n"], w["b"]
+    s, q, _ = medium(w)
+    f = sm.random_complex_vector(n * n, 29)
+    M = O.SparsifyingPreconditioner(d, n, b, s, q)
+    g = O.apply_green(d, n, s, f)
+    ref = O.gmres_right(lambda x: O.apply_operator(d, n, s, q, x), M.apply, g, tol=1e-8)
+    for prec in (0, 1):
+        S = B.Solver(d, n, b, s, prec=prec)
+        S.factor(dev(q))
+        u = torch.empty(n * n, dtype=torch.complex128, device="cuda")
+        info = S.solve(dev(f), u)
+        uh = host(u)
+        true = float(np.linalg.norm(g - O.apply_operator(d, n, s, q, uh)) / np.linalg.norm(g))
+        assert true <= 1e-8 and info["true_relres"] <= 1e-8
+        assert rel(uh, ref["u"]) <= 1e-6
+        if prec == 0:
+            assert abs(info["iters"] - ref["iters"]) <= 1
+            h = np.array(ref["hist"][: len(info["hist"])])
+            assert np.allclose(info["hist"][: len(h)], h, rtol=1e-6, atol=1e-12)
+        else:
+            assert info["iters"] <= ref["iters"] + 3
+        S.close()
+
+
 @pytest.mark.parametrize("which", ["helmholtz", "schrodinger"])
 def test_solve_3d16_matches_oracle(B, which):
     """3D 16^3, b = 4 (Helmholtz on a random-field velocity; rescaled Schroedinger with a

@@ -67,6 +67,35 @@ def test_gmres_equals_dense_pseudospectral_solve():
     assert np.all(np.diff(h) <= 1e-15)
 
 
+@pytest.mark.parametrize("precond,kmax,rtol", [(False, 6, 1e-9), (True, 3, 1e-6)],
+                         ids=["identity", "sparsifying"])
+def test_gmres_minimal_residual_property(precond, kmax, rtol):
+    """GMRES's defining property (Saad and Schultz 1986): after k steps from a zero guess
+    the iterate minimises ||g - A M y|| over y in span{g, (A M) g, ..., (A M)^{k-1} g}.
+    The minimum is computed independently, by least squares on the explicit (normalised)
+    power basis, for a right-hand side with independent real and imaginary parts, so the
+    Hessenberg matrix and the rotations are genuinely complex (a source that is a real
+    field times one phase keeps them real).  Both the true residual of the k-step iterate
+    (maxit = k) and the last estimate must equal that minimum."""
+    d, n, b = 2, 16, 4
+    c = sm.centre_gaussian_velocity(d, n, amplitude=0.3, width=0.15)
+    s, q, M = _setup(d, n, b, 2 * np.pi * 2.6, c)
+    A = lambda x: O.apply_operator(d, n, s, q, x)
+    Mf = M.apply if precond else (lambda x: x)
+    g = O.apply_green(d, n, s, sm.random_complex_vector(n * n, 12))
+    cols, v = [], g.copy()
+    for k in range(1, kmax + 1):
+        v = A(Mf(v))
+        cols.append(v / np.linalg.norm(v))
+        K = np.stack(cols, axis=1)
+        coef = np.linalg.lstsq(K, g, rcond=None)[0]
+        best = np.linalg.norm(g - K @ coef) / np.linalg.norm(g)
+        res = O.gmres_right(A, Mf, g, tol=1e-15, maxit=k)
+        assert res["iters"] == k
+        assert abs(res["true_relres"] - best) <= rtol * best, (k, res["true_relres"], best)
+        assert abs(res["hist"][-1] - best) <= rtol * best, (k, res["hist"][-1], best)
+
+
 def test_constant_medium_one_iteration():
     d, n, b = 2, 32, 4
     c = np.ones(n * n)

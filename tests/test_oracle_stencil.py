@@ -82,6 +82,12 @@ def test_matlab_pinv_truncation():
     assert r == 5
     ref = (V[:, :5] / sig[:5]) @ U[:, :5].T
     assert np.linalg.norm(P - ref) <= 1e-2 * np.linalg.norm(ref)
+    # the cutoff scales with the larger dimension: 5e-15 lies between 6 eps(3) = 2.7e-15
+    # and 40 eps(3) = 1.8e-14, so it is dropped (a cutoff on the smaller dimension keeps it)
+    sig2 = np.array([3.0, 1.0, 1e-3, 1e-8, 5e-15, 1e-16])
+    _, r2, s2 = O.matlab_pinv((U * sig2) @ V.T)
+    assert 6 * 2.0 ** -51 < s2[4] < 40 * 2.0 ** -51
+    assert r2 == 4
 
 
 @pytest.mark.parametrize("d,n,b,origin", [(2, 16, 4, (4, 8)), (2, 24, 3, (21, 6)), (3, 8, 2, (2, 4, 6))])
