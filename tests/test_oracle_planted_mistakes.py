@@ -32,6 +32,7 @@ import test_oracle_sampled_rows as TSr
 import test_oracle_solve as TSo
 import test_oracle_spectral as TSp
 import test_oracle_stencil as TSt
+import test_stencil_pointwise as TPw
 
 _PINV_CUTOFF = (ST, "matlab_pinv", "tol = max(B.shape)", "tol = min(B.shape)")
 
@@ -75,6 +76,22 @@ CASES = [
     ("T_without_pinv", ST, "stencil_tables", "T = A @ Bp", "T = A @ B.T",
      [lambda: TSt.test_T_least_squares(2, 16, 4)], AssertionError),
     ("pinv_cutoff_min_dimension",) + _PINV_CUTOFF + ([TSt.test_matlab_pinv_truncation], AssertionError),
+    ("pointwise_T_sign", ST, "pointwise_stencil_tables", "qrow[~centre] = -Tj",
+     "qrow[~centre] = Tj", [TPw.test_pointwise_least_squares_pin], AssertionError),
+    ("pointwise_C_without_Q", ST, "pointwise_stencil_tables",
+     "crow = qrow @ green_block(g, n, gj, gj_flat)",
+     "crow = green_block(g, n, p[None, :], gj_flat)[0]",
+     [lambda: TPw.test_pointwise_C_is_QG_on_each_stencil(2, 16, 2)], AssertionError),
+    ("pointwise_centre_misplaced", ST, "pointwise_stencil_tables",
+     "centre = np.all(gj == p, axis=1)", "centre = np.all(gj == p + 1, axis=1)",
+     [lambda: TPw.test_pointwise_structure_and_invariance(2, 16, 2, 1.37)], AssertionError),
+    ("solve_P_imaginary_sign", PR, "SparsifyingPreconditioner.solve_P",
+     "return sla.lu_solve(self._lu, y.real) + 1j * sla.lu_solve(self._lu, y.imag)",
+     "return sla.lu_solve(self._lu, y.real) - 1j * sla.lu_solve(self._lu, y.imag)",
+     [lambda: TSo.test_factorisation_independent_of_ordering(2, 16, 4)], AssertionError),
+    ("apply_residual_sign", PR, "SparsifyingPreconditioner.apply_residual",
+     "self.P @ np.asarray(z) - Qr", "self.P @ np.asarray(z) + Qr",
+     [lambda: TSo.test_factorisation_independent_of_ordering(2, 16, 4)], AssertionError),
     ("P_scales_C_by_row_q", PR, "assemble_sparse", "Cv * np.asarray(q, dtype=np.float64)[cols]",
      "Cv * np.asarray(q, dtype=np.float64)[rows]",
      [lambda: TSt.test_C_is_QG_on_the_pattern_and_P(2, 16, 4)], AssertionError),
@@ -146,26 +163,34 @@ CASES = [
 
 
 def _planted(module, name, line, planted):
-    """A copy of module.name with `line` replaced by `planted` (the line must occur once)."""
-    fn = getattr(module, name)
+    """A copy of module.name (a function, or "Class.method") with `line` replaced by
+    `planted` (the line must occur once).  Returns (owner, attribute, original, copy)."""
+    owner, attr = module, name
+    if "." in name:
+        cls, attr = name.split(".")
+        owner = getattr(module, cls)
+    fn = owner.__dict__[attr]
     src = textwrap.dedent(inspect.getsource(fn))
     assert src.count(line) == 1, f"{module.__name__}.{name} no longer holds {line!r}"
     ns = dict(module.__dict__)
     code = compile(src.replace(line, planted), module.__file__, "exec",
                    __future__.annotations.compiler_flag, True)
     exec(code, ns)
-    return fn, ns[name]
+    return owner, attr, fn, ns[attr]
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_planted_mistake_fails_a_pin(case, monkeypatch):
     _, module, name, line, planted, pins, raised = case
-    orig, bad = _planted(module, name, line, planted)
-    bound = [m for mn, m in list(sys.modules.items())
-             if (mn == "oracle" or mn.startswith("oracle.")) and getattr(m, name, None) is orig]
-    assert module in bound
+    owner, attr, orig, bad = _planted(module, name, line, planted)
+    if owner is module:
+        bound = [m for mn, m in list(sys.modules.items())
+                 if (mn == "oracle" or mn.startswith("oracle.")) and getattr(m, attr, None) is orig]
+        assert module in bound
+    else:
+        bound = [owner]  # a method: every module reaches it through the one class object
     for m in bound:
-        monkeypatch.setattr(m, name, bad)
+        monkeypatch.setattr(m, attr, bad)
     failed = []
     for pin in pins:
         try:

@@ -72,3 +72,27 @@ def test_pointwise_least_squares_pin():
     T = -tab["Q"][0, [col[tuple(x)] for x in gj[np.any(offs != 0, axis=1)]]]
     resid = (A - T[None, :] @ Bm) @ Bm.T
     assert np.linalg.norm(resid) <= 1e-10 * np.linalg.norm(A) * np.linalg.norm(Bm)
+
+
+@pytest.mark.parametrize("d,n,b", [(2, 16, 2), (3, 8, 2)])
+def test_pointwise_C_is_QG_on_each_stencil(d, n, b):
+    """Row a of a per-point table holds C(j, gamma({j})) = (Q G)(j, gamma({j})) for the
+    point j = S[a], with G the dense Green's matrix of the whole grid (Eq. G), and zero
+    on the rest of gamma(S): the truncation keeps exactly the point's own stencil."""
+    s = 4 * np.pi ** 2 * 1.37
+    g = O.green_kernel(d, n, s)
+    N = n ** d
+    pts = np.stack([(np.arange(N) // n ** a) % n for a in range(d)], axis=1)
+    G = O.green_block(g, n, pts, np.arange(N))
+    from oracle.stencil import flat_index
+    for tab in O.pointwise_stencil_tables(d, n, b, s):
+        gam_flat = flat_index(tab["gamma"], n)
+        for a, p in enumerate(tab["S"]):
+            qrow = np.zeros(N)
+            np.add.at(qrow, gam_flat, tab["Q"][a])
+            qg = qrow @ G
+            near = np.all(np.abs(tab["gamma"] - p) <= 1, axis=1)
+            assert np.allclose(tab["C"][a, near], qg[gam_flat[near]], rtol=0,
+                               atol=1e-12 * np.abs(qg).max())
+            assert not np.any(tab["C"][a, ~near])
+
