@@ -219,7 +219,8 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
 sp_status sp_setup_group(int d, int n, int b, int P, const double *shifts, sp_precision prec,
                          const sp_opts *opts, void *stream, sp_ctx **out);
 
-/* *P = the context's number of problems (1 unless made by sp_setup_group). */
+/* *P = the context's number of problems (1 unless made by sp_setup_group).  Host
+ * only, no GPU work; SP_ERR_ARG if ctx or P is NULL. */
 sp_status sp_problems(const sp_ctx *ctx, int *P);
 
 /* Assemble P = Q + C diag(q) into the fronts and factor it (Section 2.2, Fig. nd):
