@@ -72,9 +72,9 @@ typedef enum {
 } sp_precision;
 
 typedef struct {
-  int maxit;         /* total GMRES iterations allowed (default 500) */
-  int restart;       /* Krylov vectors kept before a restart (default 200) */
-  double tol;        /* target relative residual ||g - A u|| / ||g|| (default 1e-8) */
+  int maxit;         /* total GMRES iterations allowed (default 500; >= 1) */
+  int restart;       /* Krylov vectors kept before a restart (default 200; 1 ... 1000) */
+  double tol;        /* target relative residual ||g - A u|| / ||g|| (default 1e-8; > 0) */
   double pivot_tol;  /* singular-front threshold, relative to max|front| (default 1e-14) */
   int device;        /* CUDA device ordinal the context lives on (default 0) */
   int host_threads;  /* threads for the host set-up (0 = all hardware threads) */
@@ -149,9 +149,13 @@ typedef struct {
                         the same kernels, order and results as 0).  The graph is
                         captured on the first such solve (again after sp_factor with a
                         new medium pointer); a failed capture returns SP_ERR_CUDA.
-                        Ignored by SP_PREC_MIXED, sp_solve_many and while sp_profile is
-                        on.  0: the host drives every iteration (reads the estimate
-                        after each step).  Default 1. */
+                        sp_solve, sp_solve_host, sp_solve_x0 and sp_solve_many (all its
+                        right-hand sides in one graph) follow it; SP_PREC_MIXED ignores
+                        it, and so does a single-problem context while sp_profile is on
+                        (host-driven, so every kernel class is timed).  A problem group
+                        (sp_setup_group, P > 1) always runs its cycles as graphs.  0: the
+                        host drives every iteration (reads the estimate after each
+                        step).  Default 1. */
   int factor_storage; /* FP32-family forms (FP32, mixed, TF32, 3xTF32): 1 keeps, after each
                         factorisation, an FP16 copy of the fronts of the levels whose sweeps
                         run as chains of block products (the large upper levels), each front

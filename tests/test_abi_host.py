@@ -86,6 +86,26 @@ def test_group_argument_checks_need_no_gpu():
         assert e.value.status == status, kw
 
 
+BAD_OPTS = [("maxit", 0), ("restart", 0), ("restart", 1001), ("tol", 0.0),
+            ("tol", float("nan")), ("max_rhs", 0), ("max_rhs", 9), ("setup_route", 2),
+            ("stencil", 2), ("inv_block", 100), ("inv_block", 32), ("inv_block", 4096),
+            ("tc_epilogue", -1), ("tc_epilogue", 5), ("wait_limit_ns", -1),
+            ("wait_limit_ns", 60000000001), ("sweeps", 3), ("panel_pivoting", 2),
+            ("launch_overlap", 2), ("device_loop", -1), ("factor_storage", 2)]
+
+
+@pytest.mark.parametrize("field,value", BAD_OPTS, ids=[f"{f}={v}" for f, v in BAD_OPTS])
+def test_option_ranges_checked_before_the_device(field, value):
+    """Every sp_opts field outside the range include/sp.h states is refused with
+    SP_ERR_ARG by sp_setup before any device work (so this runs without a GPU)."""
+    B = _binding()
+    o = B.sp_default_opts()
+    setattr(o, field, value)
+    with pytest.raises(B.SpError) as e:
+        B.sp_setup(2, 64, 4, 4 * np.pi ** 2 * 1.37, B.SP_PREC_FP32, o)
+    assert e.value.status == B.SP_ERR_ARG
+
+
 @pytest.mark.parametrize("d,n,b", [(2, 64, 4), (2, 24, 3), (3, 8, 2), (3, 16, 4)])
 def test_host_tables_match_oracle(d, n, b):
     B = _binding()
