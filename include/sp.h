@@ -159,10 +159,11 @@ typedef struct {
   int factor_storage; /* FP32-family forms (FP32, mixed, TF32, 3xTF32): 1 keeps, after each
                         factorisation, an FP16 copy of the fronts of the levels whose sweeps
                         run as chains of block products (the large upper levels), each front
-                        scaled by a power of two so its largest entry stays below 2^15; those
-                        sweeps then read half the bytes and sum in FP32 (Section 2.3's solve
-                        with the factor, at FP16 accuracy of the factor entries: measured at
-                        3D 128^3 TF32, Helmholtz 86 -> 89 GMRES iterations).  0 (default):
+                        column scaled by a power of two so its largest entry stays below
+                        2^15; those sweeps then read half the bytes and sum in FP32 (Section
+                        2.3's solve with the factor, at FP16 accuracy of the factor entries:
+                        measured at 3D 128^3 TF32 Helmholtz, 83 -> 85 GMRES iterations and
+                        5.00 -> 4.75 s per factor and solve).  0 (default):
                         the sweeps read the factor in the form's precision.  SP_ERR_ARG for
                         SP_PREC_FP64. */
 } sp_opts;
@@ -363,7 +364,9 @@ sp_status sp_medium_schrodinger_at(int d, int n, double ell, double E, const dou
  * milliseconds, the number of kernel launches and the algorithmic work (flops
  * for classes 1-3 and 9, bytes for the others: the data a kernel must move at
  * least once; 10 tensor-core Schur updates of the blocked fronts, flops), then
- * clears the record.  Arrays of cap >= 11. */
+ * clears the record.  Arrays of cap >= 11.  A single-problem context's solves run
+ * host-driven while profiling is on; a problem group's GMRES cycles stay CUDA
+ * graphs, whose kernels are not split into classes. */
 sp_status sp_profile(sp_ctx *ctx, int enable);
 sp_status sp_profile_read(sp_ctx *ctx, int cap, double *ms, int *launches, double *work);
 
@@ -375,7 +378,7 @@ sp_status sp_profile_read(sp_ctx *ctx, int cap, double *ms, int *launches, doubl
  * for the form: SP_PREC_FP64 doubles, SP_PREC_FP32 floats (SIMT FMA units),
  * SP_PREC_TF32 floats with TF32 products on the tensor cores and FP32
  * accumulation, SP_PREC_TF32X3 the same with split operands (K <= 16384 for both;
- * the factorisation itself uses depths up to 512; the call allocates and frees its
+ * the factorisation itself uses depths up to 1024; the call allocates and frees its
  * operand buffers).
  * A, B, C: device pointers owned by the caller; C must not overlap A or B.
  * Synchronous on `stream` (cudaStream_t or NULL).  SP_ERR_ARG for bad sizes or
