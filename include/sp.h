@@ -147,8 +147,9 @@ typedef struct {
                         stopping test runs on the device and the host waits once per
                         cycle instead of once per iteration (Section 2.2's GMRES loop;
                         the same kernels, order and results as 0).  The graph is
-                        captured on the first such solve (again after sp_factor with a
-                        new medium pointer); a failed capture returns SP_ERR_CUDA.
+                        captured on the first such solve and reads the context's copy
+                        of the medium, so later factorisations reuse it; a failed
+                        capture returns SP_ERR_CUDA.
                         sp_solve, sp_solve_host, sp_solve_x0 and sp_solve_many (all its
                         right-hand sides in one graph) follow it; SP_PREC_MIXED ignores
                         it, and so does a single-problem context while sp_profile is on

@@ -415,10 +415,9 @@ def sp_destroy(ctx: int) -> None:
 # ------------------------------------------------------------------ convenience class
 class Solver:
     """Owns one context.  Vectors are torch complex128 CUDA tensors of n^d entries,
-    q a float64 CUDA tensor; the solver keeps a reference to q (the library reads
-    it until the next factor call).  With a sequence of shifts s the context is a
-    problem group (sp_setup_group): vectors and q hold P n^d entries, problem p's at
-    p n^d, and solve returns one info dict per problem."""
+    q a float64 CUDA tensor (factor copies it into the context).  With a sequence of
+    shifts s the context is a problem group (sp_setup_group): vectors and q hold P n^d
+    entries, problem p's at p n^d, and solve returns one info dict per problem."""
 
     def __init__(self, d: int, n: int, b: int, s, prec: int = SP_PREC_FP64,
                  maxit: int = 500, restart: int = 200, tol: float = 1e-8, device: int = 0,
@@ -444,9 +443,10 @@ class Solver:
         o.factor_storage = factor_storage
         self.d, self.n, self.b, self.s, self.prec = d, n, b, s, prec
         self.N = n ** d
-        if isinstance(s, (int, float)):
+        import numpy as np
+        if np.ndim(s) == 0:  # one shift (any real scalar); a sequence makes a group
             self.P = 1
-            self.ctx = sp_setup(d, n, b, s, prec, o, stream)
+            self.ctx = sp_setup(d, n, b, float(s), prec, o, stream)
         else:
             self.P = len(s)
             self.ctx = sp_setup_group(d, n, b, s, prec, o, stream)

@@ -348,8 +348,9 @@ KBatch make_batch(sp_ctx* c) {
 // Gram-Schmidt twice, the Givens rotation, the stopping test; the test ends the node
 // when no instance goes on), then u += Z y, the true residual r = g - A u and a copy
 // of the heads and estimates to the host.  The graph works on the context's own
-// vectors (u in ubuf) and the medium pointer c->q, so it is captured again when
-// sp_factor is given another medium pointer.
+// vectors (u in ubuf) and its copy of the medium (c->q = qbuf, which sp_factor
+// refills), so one capture serves every later factorisation; it is captured again
+// only if that pointer ever changes.
 sp_status build_cycle_graph(sp_ctx* c, int R) {
   if (c->g_cycle[R]) {
     cudaGraphExecDestroy(c->g_cycle[R]);

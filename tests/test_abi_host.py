@@ -183,3 +183,28 @@ def test_medium_schrodinger_at_fixed_shift():
     assert np.array_equal(B.sp_medium_schrodinger_at(2, 32, 8.0, 10.0, V, s), q)
     q2 = B.sp_medium_schrodinger_at(2, 32, 8.0, 10.0, V, s + 7.5)
     assert np.allclose(q2 - q, 7.5, rtol=0, atol=1e-12)
+
+
+def test_solver_dispatches_scalars_and_groups(monkeypatch):
+    """Solver makes a single-problem context for any real scalar shift (float, numpy
+    scalar, int) and a problem group for a sequence (list, array), with the options it
+    was given; the set-up and destroy calls are replaced by recorders, so no GPU (and
+    no library context) is touched."""
+    B = _binding()
+    calls = []
+    monkeypatch.setattr(B, "sp_setup", lambda d, n, b, s, prec, o, st: calls.append(
+        ("one", s, o.restart, o.factor_storage)) or 1)
+    monkeypatch.setattr(B, "sp_setup_group", lambda d, n, b, sh, prec, o, st: calls.append(
+        ("group", list(sh), o.restart, o.factor_storage)) or 2)
+    monkeypatch.setattr(B, "sp_destroy", lambda ctx: calls.append(("destroy", ctx)))
+    for s in (101.5, np.float64(101.5), 101, np.int64(101)):
+        S = B.Solver(2, 64, 4, s, prec=B.SP_PREC_FP32, restart=7, factor_storage=1)
+        assert (S.P, S.NP, S.ctx) == (1, 64 * 64, 1)
+        assert calls[-1] == ("one", float(s), 7, 1) and isinstance(calls[-1][1], float)
+        S.close()
+    for sh in ([100.0, 101.0, 102.0], np.array([100.0, 101.0, 102.0])):
+        S = B.Solver(2, 64, 4, sh, prec=B.SP_PREC_FP32, restart=7)
+        assert (S.P, S.NP, S.ctx) == (3, 3 * 64 * 64, 2)
+        assert calls[-1] == ("group", [100.0, 101.0, 102.0], 7, 0)
+        S.close()
+        assert calls[-1] == ("destroy", 2) and S.ctx is None
