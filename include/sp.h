@@ -214,9 +214,10 @@ sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_op
  * graphs; see sp_opts.device_loop).  Every vector of the context then holds P N
  * entries, problem p's at offset p N: q of sp_factor, r / z of sp_apply, f / u of
  * sp_solve, x / w of sp_matvec, f / g of sp_green, r / y of sp_qapply; sp_solve and
- * sp_solve_host fill P info records in problem order, sp_solve_many nrhs P (right-hand side r
- * of problem p at index and vector offset r P + p); sp_get_table / sp_set_table take
- * t = p 2^d + type.  1 <= P, P opts.max_rhs <= 1024; SP_PREC_MIXED and sp_solve_x0
+ * sp_solve_host fill P info records in problem order, sp_solve_many nrhs P
+ * (right-hand side r of problem p at index and vector offset r P + p);
+ * sp_get_table / sp_set_table take t = p 2^d + type.  1 <= P, P opts.max_rhs <=
+ * 1024 and P n^d < 2^31 (grid indices are 32-bit); SP_PREC_MIXED and sp_solve_x0
  * with a start vector take P = 1 only (else SP_ERR_ARG).  The other arguments and
  * errors are sp_setup's, checked for every shift.  A group's problems give the
  * results of separate contexts up to rounding: launch shapes that depend on the

@@ -650,6 +650,11 @@ static sp_status setup_impl(int d, int n, int b, int P, const double* shifts, sp
     const int m2 = (n % 3 == 0) ? n / 3 : n;
     if (m2 < 2 || (m2 & (m2 - 1))) return SP_ERR_ARG;
   }
+  {  // grid indices of a group's fronts are ints offset by p N: P n^d must fit
+    long long NP = P;
+    for (int a = 0; a < d; ++a) NP *= n;
+    if (NP > 2147483647LL) return SP_ERR_ARG;
+  }
   if (prec != SP_PREC_FP64 && prec != SP_PREC_FP32 && prec != SP_PREC_MIXED &&
       prec != SP_PREC_TF32 && prec != SP_PREC_TF32X3)
     return SP_ERR_ARG;

@@ -66,7 +66,8 @@ def test_argument_checks_need_no_gpu():
 def test_group_argument_checks_need_no_gpu():
     """sp_setup_group refuses, before touching the device: no problems, a resonant shift
     among them, the mixed-precision form with several problems, more than 1024 Krylov
-    instances (P max_rhs), a bad grid; and the FP16 factor copy in the plain FP64 form."""
+    instances (P max_rhs), a bad grid, more than 2^31 - 1 grid points in all (P n^d: the
+    fronts' grid indices are ints); and the FP16 factor copy in the plain FP64 form."""
     B = _binding()
     cases = [
         (dict(shifts=[]), B.SP_ERR_ARG),
@@ -74,6 +75,7 @@ def test_group_argument_checks_need_no_gpu():
         (dict(shifts=[100.0, 101.0], prec=B.SP_PREC_MIXED), B.SP_ERR_ARG),
         (dict(shifts=[100.0] * 129, max_rhs=8), B.SP_ERR_ARG),
         (dict(shifts=[100.0, 101.0], n=48, b=4), B.SP_ERR_ARG),
+        (dict(shifts=[100.0 + p for p in range(1024)], d=3, n=128, b=8), B.SP_ERR_ARG),
         (dict(shifts=[100.0], factor_storage=1, prec=B.SP_PREC_FP64), B.SP_ERR_ARG),
     ]
     for kw, status in cases:
@@ -81,7 +83,7 @@ def test_group_argument_checks_need_no_gpu():
         o.max_rhs = kw.get("max_rhs", 1)
         o.factor_storage = kw.get("factor_storage", 0)
         with pytest.raises(B.SpError) as e:
-            B.sp_setup_group(2, kw.get("n", 64), kw.get("b", 4), kw["shifts"],
+            B.sp_setup_group(kw.get("d", 2), kw.get("n", 64), kw.get("b", 4), kw["shifts"],
                              kw.get("prec", B.SP_PREC_FP32), o)
         assert e.value.status == status, kw
 
