@@ -739,34 +739,58 @@ int build_symbolic(int d, int n, int b, const std::vector<StencilTable>& tabs, S
         origins.push_back(o);
       }
     }
+    // a point is eliminated in box 0 of a level below the root iff all its
+    // coordinates lie in [1, B-1] (at the root every point is in the one front)
+    auto in_box0 = [&](long e) {
+      if (l == L) return true;
+      for (int ax = 0; ax < d; ++ax) {
+        const int v = (int)(e % n);
+        e /= n;
+        if (v < 1 || v > V.B - 1) return false;
+      }
+      return true;
+    };
+    // per (type, leaf box): flat index, level and box-0 test of every set point and
+    // every gamma point, once; the (row, column) scan then compares levels only.  A
+    // row eliminated below this level gives no entry here (the earlier endpoint of
+    // each of its entries is eliminated earlier).
+    std::vector<long> jf, cf;
+    std::vector<signed char> jl, cl;
+    std::vector<char> cin;
     for (size_t t = 0; t < tabs.size(); ++t) {
       const StencilTable& tb = tabs[t];
+      jf.resize(tb.nS);
+      jl.resize(tb.nS);
+      cf.resize(tb.nG);
+      cl.resize(tb.nG);
+      cin.resize(tb.nG);
       for (const auto& o : origins) {
+        bool any = false;
         for (int a = 0; a < tb.nS; ++a) {
           int pj[3];
           for (int ax = 0; ax < d; ++ax) pj[ax] = o[ax] + tb.S[(size_t)a * d + ax];
-          long j = flat_of(pj, d, n);
-          int lj = lev[j];
+          jf[a] = flat_of(pj, d, n);
+          jl[a] = lev[jf[a]];
+          any |= jl[a] >= l;
+        }
+        if (!any) continue;
+        for (int c = 0; c < tb.nG; ++c) {
+          int pi[3];
+          for (int ax = 0; ax < d; ++ax) pi[ax] = o[ax] + tb.G[(size_t)c * d + ax];
+          cf[c] = flat_of(pi, d, n);
+          cl[c] = lev[cf[c]];
+          cin[c] = in_box0(cf[c]);
+        }
+        for (int a = 0; a < tb.nS; ++a) {
+          const int lj = jl[a];
+          if (lj < l) continue;
+          const bool jin = in_box0(jf[a]);
           for (int c = 0; c < tb.nG; ++c) {
-            int pi[3];
-            for (int ax = 0; ax < d; ++ax) pi[ax] = o[ax] + tb.G[(size_t)c * d + ax];
-            long i = flat_of(pi, d, n);
-            int li = lev[i];
-            int lm = std::min(lj, li);
-            if (lm != l) continue;
-            long e = (lj <= li) ? j : i;
-            if (l < L) {
-              // eliminated in box 0 iff all coordinates lie in [1, B-1]
-              long ee = e;
-              bool inb = true;
-              for (int ax = 0; ax < d; ++ax) {
-                int v = (int)(ee % n);
-                ee /= n;
-                if (v < 1 || v > V.B - 1) inb = false;
-              }
-              if (!inb) continue;
-            }
-            int rp = pos[j], cp = pos[i];
+            const int li = cl[c];
+            if (std::min(lj, li) != l) continue;
+            // the earlier-eliminated endpoint (the row on ties) must be in box 0
+            if (!(lj <= li ? jin : cin[c])) continue;
+            const int rp = pos[jf[a]], cp = pos[cf[c]];
             if (rp < 0 || cp < 0) return 3;  // structural error
             V.asm_row.push_back(rp);
             V.asm_tidx.push_back((int)(toff[t] + a + (long)c * tb.nS));
