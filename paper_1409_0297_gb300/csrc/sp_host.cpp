@@ -38,37 +38,76 @@ static cd twiddle(long t, long n, int sign) {
   return cd(std::cos(a), sign * std::sin(a));
 }
 
-// Mixed-radix decimation-in-time DFT of the contiguous line x[0..n).
-static void fft_line(cd* x, int n, int sign) {
-  if (n == 1) return;
-  int p = 2;
-  while (n % p) ++p;
-  int m = n / p;
-  std::vector<cd> sub(n);
+// The sub-lengths, radices and twiddle factors of the mixed-radix recursion below for
+// lines of length n: depth q has length len[q] (n, n / p_0, n / (p_0 p_1), ... > 1),
+// smallest prime factor radix[q] and tw[q][t] = twiddle(t, len[q], sign) for
+// t = 0 .. len[q] - 1, so the recursion looks its twiddles up instead of evaluating
+// cos and sin per term.
+struct FftPlan {
+  std::vector<int> len, radix;
+  std::vector<std::vector<cd>> tw;
+};
+
+static FftPlan fft_plan(int n, int sign) {
+  FftPlan P;
+  for (int m = n; m > 1;) {
+    int p = 2;
+    while (m % p) ++p;
+    P.len.push_back(m);
+    P.radix.push_back(p);
+    std::vector<cd> w(m);
+    for (int t = 0; t < m; ++t) w[t] = twiddle(t, m, sign);
+    P.tw.push_back(std::move(w));
+    m /= p;
+  }
+  return P;
+}
+
+// Mixed-radix decimation-in-time DFT of the contiguous line x[0..n), n = P.len[q]
+// (nothing to do at length 1): the p decimated sub-lines are transformed
+// recursively, then X_k = sum_r Sub_r[k mod m] exp(sign 2 pi i r k / n).  scratch
+// holds at least 2n values (this depth's sub-lines, then the deeper ones').
+static void fft_line(cd* x, const FftPlan& P, int q, cd* scratch) {
+  if (q == (int)P.len.size()) return;
+  const int n = P.len[q], p = P.radix[q], m = n / p;
+  cd* sub = scratch;
   for (int r = 0; r < p; ++r)
     for (int j = 0; j < m; ++j) sub[(size_t)r * m + j] = x[(size_t)j * p + r];
-  for (int r = 0; r < p; ++r) fft_line(&sub[(size_t)r * m], m, sign);
+  for (int r = 0; r < p; ++r) fft_line(sub + (size_t)r * m, P, q + 1, scratch + n);
+  const cd* w = P.tw[q].data();
   for (int k = 0; k < n; ++k) {
     cd acc = 0.0;
-    int kk = k % m;
-    for (int r = 0; r < p; ++r) acc += sub[(size_t)r * m + kk] * twiddle((long)r * k, n, sign);
+    const int kk = k % m;
+    for (int r = 0; r < p; ++r) acc += sub[(size_t)r * m + kk] * w[((long)r * k) % n];
     x[k] = acc;
   }
 }
 
+// Transform of the n^d array a along every axis; the lines of an axis are
+// independent and split over host threads.
 static void fft_nd(std::vector<cd>& a, int d, int n, int sign) {
   size_t N = 1;
   for (int i = 0; i < d; ++i) N *= n;
-  std::vector<cd> line(n);
+  const FftPlan P = fft_plan(n, sign);
+  const size_t lines = N / n;
+  int nth = (int)std::max(1u, std::thread::hardware_concurrency());
+  nth = (int)std::min<size_t>({(size_t)nth, (size_t)64, lines});
   size_t S = 1;
   for (int ax = 0; ax < d; ++ax) {
-    // lines along axis ax: element i at base + i*S
-    for (size_t base0 = 0; base0 < N; ++base0) {
-      if ((base0 / S) % n != 0) continue;
-      for (int i = 0; i < n; ++i) line[i] = a[base0 + (size_t)i * S];
-      fft_line(line.data(), n, sign);
-      for (int i = 0; i < n; ++i) a[base0 + (size_t)i * S] = line[i];
-    }
+    // line q of axis ax: element i at base + i S, base = (q mod S) + (q / S) S n
+    auto worker = [&](int id) {
+      std::vector<cd> line(n), scratch(2 * (size_t)n);
+      for (size_t q = id; q < lines; q += nth) {
+        const size_t base = (q % S) + (q / S) * S * n;
+        for (int i = 0; i < n; ++i) line[i] = a[base + (size_t)i * S];
+        fft_line(line.data(), P, 0, scratch.data());
+        for (int i = 0; i < n; ++i) a[base + (size_t)i * S] = line[i];
+      }
+    };
+    std::vector<std::thread> th;
+    for (int i = 1; i < nth; ++i) th.emplace_back(worker, i);
+    worker(0);
+    for (auto& t : th) t.join();
     S *= n;
   }
 }
