@@ -45,7 +45,8 @@ typedef enum {
   SP_ERR_RESONANT = 2,  /* L - s is (numerically) singular: s hits 4 pi^2 |k|^2 */
   SP_ERR_SINGULAR = 3,  /* a pivot of a front fell below pivot_tol * max|front| */
   SP_ERR_NOCONV = 4,    /* GMRES stopped at maxit above tol (the iterate is still returned) */
-  SP_ERR_OOM = 5,       /* device or host allocation failed */
+  SP_ERR_OOM = 5,       /* device or host allocation failed, or the host could not start
+                           the set-up's worker threads */
   SP_ERR_TIMEOUT = 6,   /* a bounded device wait (tensor-core pipeline, grid panel) ran out */
   SP_ERR_CUDA = 7,      /* a CUDA runtime call failed */
   SP_ERR_STATE = 8      /* call out of order (e.g. sp_apply before sp_factor) */

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <memory>
 #include <new>
 #include <vector>
@@ -513,7 +514,7 @@ sp_status sp_stencil_table(int d, int n, int b, double s, int t, int route, int 
     if (rank) *rank = tb.rank;
     if (sigma_out)
       for (int i = 0; i < std::min<int>(64, (int)tb.sigma.size()); ++i) sigma_out[i] = tb.sigma[i];
-  } catch (const std::bad_alloc&) {
+  } catch (const std::exception&) {  // host memory, or the set-up's host threads
     return SP_ERR_OOM;
   }
   return SP_OK;
@@ -571,7 +572,7 @@ sp_status sp_level_info(int d, int n, int b, int level, int* nf, int* k, int* m,
     if (ea_map && !V.ea_map.empty()) std::memcpy(ea_map, V.ea_map.data(), V.ea_map.size() * sizeof(int));
     if (asm_row) std::memcpy(asm_row, V.asm_row.data(), V.asm_row.size() * sizeof(int));
     if (asm_cvar) std::memcpy(asm_cvar, V.asm_cvar.data(), V.asm_cvar.size() * sizeof(int));
-  } catch (const std::bad_alloc&) {
+  } catch (const std::exception&) {  // host memory, or the set-up's host threads
     return SP_ERR_OOM;
   }
   return SP_OK;
@@ -734,7 +735,7 @@ static sp_status setup_impl(int d, int n, int b, int P, const double* shifts, sp
     // the symbolic structure depends on the sets only (the same for every problem)
     std::vector<StencilTable> t0(c->tabs.begin(), c->tabs.begin() + (1 << d));
     if (build_symbolic(d, n, b, t0, &c->sym)) return SP_ERR_ARG;
-  } catch (const std::bad_alloc&) {
+  } catch (const std::exception&) {  // host memory, or the set-up's host threads
     return SP_ERR_OOM;
   }
   // ---- tables on the device (column-major per type, concatenated): Q and C on
@@ -992,13 +993,17 @@ static sp_status setup_impl(int d, int n, int b, int P, const double* shifts, sp
 }
 
 sp_status sp_setup(int d, int n, int b, double s, sp_precision prec, const sp_opts* opts,
-                   void* stream, sp_ctx** out) {
+                   void* stream, sp_ctx** out) try {
   return setup_impl(d, n, b, 1, &s, prec, opts, stream, out);
+} catch (const std::exception&) {  // host memory or threads: no exception crosses the ABI
+  return SP_ERR_OOM;
 }
 
 sp_status sp_setup_group(int d, int n, int b, int P, const double* shifts, sp_precision prec,
-                         const sp_opts* opts, void* stream, sp_ctx** out) {
+                         const sp_opts* opts, void* stream, sp_ctx** out) try {
   return setup_impl(d, n, b, P, shifts, prec, opts, stream, out);
+} catch (const std::exception&) {  // host memory or threads: no exception crosses the ABI
+  return SP_ERR_OOM;
 }
 
 sp_status sp_problems(const sp_ctx* c, int* P) {
@@ -1302,20 +1307,24 @@ static sp_status solve_impl(sp_ctx* c, const double2* f, const double2* u0, doub
   return true_rel <= tol ? SP_OK : SP_ERR_NOCONV;
 }
 
-sp_status sp_solve(sp_ctx* c, const void* f_dev, void* u_dev, sp_info* info) {
+sp_status sp_solve(sp_ctx* c, const void* f_dev, void* u_dev, sp_info* info) try {
   if (!c || !f_dev || !u_dev) return SP_ERR_ARG;
   ProfGuard pg_(c);
   if (!c->factored) return SP_ERR_STATE;
   SP_CK(cudaSetDevice(c->opts.device));
   return solve_impl(c, (const double2*)f_dev, nullptr, (double2*)u_dev, info);
+} catch (const std::exception&) {  // host memory or threads: no exception crosses the ABI
+  return SP_ERR_OOM;
 }
 
-sp_status sp_solve_x0(sp_ctx* c, const void* f_dev, const void* u0_dev, void* u_dev, sp_info* info) {
+sp_status sp_solve_x0(sp_ctx* c, const void* f_dev, const void* u0_dev, void* u_dev, sp_info* info) try {
   if (!c || !f_dev || !u_dev || (u0_dev && c->P > 1)) return SP_ERR_ARG;
   ProfGuard pg_(c);
   if (!c->factored) return SP_ERR_STATE;
   SP_CK(cudaSetDevice(c->opts.device));
   return solve_impl(c, (const double2*)f_dev, (const double2*)u0_dev, (double2*)u_dev, info);
+} catch (const std::exception&) {  // host memory or threads: no exception crosses the ABI
+  return SP_ERR_OOM;
 }
 
 // GMRES-IR: outer refinement in FP64, inner flexible GMRES in complex64.
@@ -1399,7 +1408,7 @@ static sp_status solve_mixed(sp_ctx* c, const double2* f, const double2* u0, dou
 
 // z = P^{-1} Q r for nv stacked vectors (direct launches; each vector's result
 // equals apply_direct's for it)
-sp_status sp_solve_many(sp_ctx* c, int nrhs, const void* F_dev, void* U_dev, sp_info* infos) {
+sp_status sp_solve_many(sp_ctx* c, int nrhs, const void* F_dev, void* U_dev, sp_info* infos) try {
   if (!c || !F_dev || !U_dev || nrhs < 1 || nrhs > c->opts.max_rhs) return SP_ERR_ARG;
   if (!c->factored) return SP_ERR_STATE;
   SP_CK(cudaSetDevice(c->opts.device));
@@ -1568,9 +1577,11 @@ sp_status sp_solve_many(sp_ctx* c, int nrhs, const void* F_dev, void* U_dev, sp_
     if (!(R[r].true_rel <= tol)) all = false;
   }
   return all ? SP_OK : SP_ERR_NOCONV;
+} catch (const std::exception&) {  // host memory or threads: no exception crosses the ABI
+  return SP_ERR_OOM;
 }
 
-sp_status sp_solve_host(sp_ctx* c, const void* f_host, void* u_host, sp_info* info) {
+sp_status sp_solve_host(sp_ctx* c, const void* f_host, void* u_host, sp_info* info) try {
   if (!c || !f_host || !u_host) return SP_ERR_ARG;
   SP_CK(cudaSetDevice(c->opts.device));
   SP_CK(cudaMemcpyAsync(c->fbuf, f_host, sizeof(double2) * c->NP, cudaMemcpyHostToDevice, c->stream));
@@ -1579,6 +1590,8 @@ sp_status sp_solve_host(sp_ctx* c, const void* f_host, void* u_host, sp_info* in
   SP_CK(cudaMemcpyAsync(u_host, c->ubuf, sizeof(double2) * c->NP, cudaMemcpyDeviceToHost, c->stream));
   SP_CK(cudaStreamSynchronize(c->stream));
   return st;
+} catch (const std::exception&) {  // host memory or threads: no exception crosses the ABI
+  return SP_ERR_OOM;
 }
 
 sp_status sp_schur_update(sp_precision prec, int M, int N, int K, const void* A, int lda,
@@ -1653,7 +1666,7 @@ sp_status sp_get_table(const sp_ctx* c, int t, double* Q_out, double* C_out, int
   return SP_OK;
 }
 
-sp_status sp_set_table(sp_ctx* c, int t, const double* Q_in, const double* C_in) {
+sp_status sp_set_table(sp_ctx* c, int t, const double* Q_in, const double* C_in) try {
   if (!c || t < 0 || t >= (int)c->tabs.size() || !Q_in || !C_in) return SP_ERR_ARG;
   StencilTable& tb = c->tabs[t];
   // table t of a group: problem t / 2^d, type t mod 2^d
@@ -1715,6 +1728,8 @@ sp_status sp_set_table(sp_ctx* c, int t, const double* Q_in, const double* C_in)
   tb.C.assign(C_in, C_in + ne);
   c->factored = false;
   return SP_OK;
+} catch (const std::exception&) {  // host memory or threads: no exception crosses the ABI
+  return SP_ERR_OOM;
 }
 
 sp_status sp_profile(sp_ctx* c, int enable) {

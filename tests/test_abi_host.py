@@ -210,3 +210,30 @@ def test_solver_dispatches_scalars_and_groups(monkeypatch):
         assert calls[-1] == ("group", [100.0, 101.0, 102.0], 7, 0)
         S.close()
         assert calls[-1] == ("destroy", 2) and S.ctx is None
+
+
+def test_host_allocation_failure_is_a_status():
+    """A host allocation that fails inside the set-up comes back as SP_ERR_OOM instead
+    of an exception crossing the C ABI (which would end the caller's process).  A child
+    process caps its address space a little above what it already uses and asks for the
+    3D 128^3 nested-dissection structure, whose assembly lists alone need hundreds of MB."""
+    import subprocess
+    import sys
+    code = (
+        "import re, resource, sys\n"
+        "import numpy as np\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "from paper_1409_0297_gb300 import binding as B\n"
+        "vm = int(re.search(r'VmSize:\\s+(\\d+)', open('/proc/self/status').read()).group(1)) * 1024\n"
+        "resource.setrlimit(resource.RLIMIT_AS, (vm + (64 << 20), resource.getrlimit(resource.RLIMIT_AS)[1]))\n"
+        "try:\n"
+        "    B.sp_level_info(3, 128, 8, 0)\n"
+        "    print('no error')\n"
+        "except B.SpError as e:\n"
+        "    print('status', e.status, e.status == B.SP_ERR_OOM)\n")
+    _binding()
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1")
+    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=120)
+    assert p.returncode == 0, p.stderr[-2000:]
+    assert p.stdout.strip() == "status 5 True", p.stdout + p.stderr[-2000:]
