@@ -724,14 +724,10 @@ static sp_status setup_impl(int d, int n, int b, int P, const double* shifts, sp
   try {
     // tables of every problem, problem-major (problem p's type t at p 2^d + t)
     c->tabs.resize((size_t)P << d);
-    for (int p = 0; p < P; ++p) {
-      std::vector<double> g = green_kernel(d, n, shifts[p]), g2;
-      if (c->opts.setup_route == 1) g2 = green_kernel_sq(d, n, shifts[p]);
-      for (int t = 0; t < (1 << d); ++t)
-        if (stencil_table(d, n, b, t, g, c->opts.host_threads, &c->tabs[((size_t)p << d) + t],
-                          c->opts.setup_route == 1 ? &g2 : nullptr, c->opts.stencil))
-          return SP_ERR_ARG;
-    }
+    for (int p = 0; p < P; ++p)
+      if (stencil_tables(d, n, b, shifts[p], c->opts.setup_route, c->opts.stencil,
+                         c->opts.host_threads, &c->tabs[(size_t)p << d]))
+        return SP_ERR_ARG;
     // the symbolic structure depends on the sets only (the same for every problem)
     std::vector<StencilTable> t0(c->tabs.begin(), c->tabs.begin() + (1 << d));
     if (build_symbolic(d, n, b, t0, &c->sym)) return SP_ERR_ARG;

@@ -4,9 +4,13 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <exception>
+#include <mutex>
+#include <system_error>
 #include <thread>
 #include <unordered_map>
 
@@ -614,6 +618,60 @@ int stencil_table(int d, int n, int b, int t, const std::vector<double>& g, int 
       T.Q[(size_t)a * T.nG + c] = P.Q[ie];
       T.C[(size_t)a * T.nG + c] = P.C[ie];
     }
+  return 0;
+}
+
+// Runs f(i) for i = 0 .. count - 1 on up to nth host threads, the calling thread
+// included.  Items come from a shared counter, so when a thread cannot be started the
+// running ones take its share; the first exception an item throws is rethrown here
+// once every thread has joined.
+template <class F>
+static void parallel_items(int count, int nth, F f) {
+  std::atomic<int> next{0};
+  std::mutex mu;
+  std::exception_ptr err;
+  auto run = [&]() {
+    for (int i; (i = next.fetch_add(1)) < count;) {
+      try {
+        f(i);
+      } catch (...) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!err) err = std::current_exception();
+      }
+    }
+  };
+  std::vector<std::thread> th;
+  for (int k = 1; k < std::min(nth, count); ++k) {
+    try {
+      th.emplace_back(run);
+    } catch (const std::system_error&) {
+      break;
+    }
+  }
+  run();
+  for (auto& t : th) t.join();
+  if (err) std::rethrow_exception(err);
+}
+
+int stencil_tables(int d, int n, int b, double s, int route, int kind, int threads,
+                   StencilTable* out) {
+  std::vector<double> g, g2;
+  parallel_items(route == 1 ? 2 : 1, 2, [&](int i) {
+    if (i == 0)
+      g = green_kernel(d, n, s);
+    else
+      g2 = green_kernel_sq(d, n, s);
+  });
+  const int nt = 1 << d;
+  const int hw = threads > 0 ? threads : (int)std::max(1u, std::thread::hardware_concurrency());
+  // the Gram route computes a table on one thread, so the types run side by side; the
+  // TSQR route spreads each table's row blocks over the threads, one type at a time
+  std::vector<int> rc(nt, 0);
+  parallel_items(nt, route == 1 ? hw : 1, [&](int t) {
+    rc[t] = stencil_table(d, n, b, t, g, threads, &out[t], route == 1 ? &g2 : nullptr, kind);
+  });
+  for (int t = 0; t < nt; ++t)
+    if (rc[t]) return rc[t];
   return 0;
 }
 

@@ -57,6 +57,13 @@ double resonance_gap(int d, int n, double s);
 int stencil_table(int d, int n, int b, int t, const std::vector<double>& g, int threads,
                   StencilTable* out, const std::vector<double>* g2 = nullptr, int kind = 0);
 
+// All 2^d tables of one shift s (types t = 0 .. 2^d - 1 into out[0 .. 2^d - 1]):
+// the Green kernel (and, for route 1, the kernel of G^2) and then stencil_table for
+// every type, on up to `threads` host threads (0 = all); the same tables, bit for
+// bit, as stencil_table called type by type.
+int stencil_tables(int d, int n, int b, double s, int route, int kind, int threads,
+                   StencilTable* out);
+
 // Nested-dissection structure.
 int build_symbolic(int d, int n, int b, const std::vector<StencilTable>& tabs, Symbolic* out);
 
