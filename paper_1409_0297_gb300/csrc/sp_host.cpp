@@ -10,7 +10,6 @@
 #include <cstring>
 #include <exception>
 #include <mutex>
-#include <system_error>
 #include <thread>
 #include <unordered_map>
 
@@ -31,6 +30,40 @@ int check_grid(int d, int n, int b, int* L) {
   if (l < 1) return 1;
   if (L) *L = l;
   return 0;
+}
+
+// ---------------------------------------------------------------- host threads
+// Runs f(i) for i = 0 .. count - 1 on up to nth host threads, the calling thread
+// included.  Items come from a shared counter, so when a thread cannot be started the
+// running ones take its share; the first exception an item throws is rethrown here
+// once every thread has joined.
+template <class F>
+static void parallel_items(int count, int nth, F f) {
+  std::atomic<int> next{0};
+  std::mutex mu;
+  std::exception_ptr err;
+  auto run = [&]() {
+    for (int i; (i = next.fetch_add(1)) < count;) {
+      try {
+        f(i);
+      } catch (...) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!err) err = std::current_exception();
+      }
+    }
+  };
+  std::vector<std::thread> th;
+  th.reserve((size_t)std::max(0, std::min(nth, count) - 1));  // no reallocation below
+  for (int k = 1; k < std::min(nth, count); ++k) {
+    try {
+      th.emplace_back(run);
+    } catch (const std::exception&) {
+      break;
+    }
+  }
+  run();
+  for (auto& t : th) t.join();
+  if (err) std::rethrow_exception(err);
 }
 
 // ---------------------------------------------------------------- host FFT
@@ -108,10 +141,7 @@ static void fft_nd(std::vector<cd>& a, int d, int n, int sign) {
         for (int i = 0; i < n; ++i) a[base + (size_t)i * S] = line[i];
       }
     };
-    std::vector<std::thread> th;
-    for (int i = 1; i < nth; ++i) th.emplace_back(worker, i);
-    worker(0);
-    for (auto& t : th) t.join();
+    parallel_items(nth, nth, worker);
     S *= n;
   }
 }
@@ -468,12 +498,7 @@ static int set_table(int d, int n, StencilTable& T, const std::vector<double>& g
       for (int col = 0; col < c; ++col)
         for (int i = 0; i <= col; ++i) Rs[id][(size_t)col * c + i] = X[(size_t)col * h + i];
   };
-  {
-    std::vector<std::thread> th;
-    for (int i = 1; i < nth; ++i) th.emplace_back(worker, i);
-    worker(0);
-    for (auto& x : th) x.join();
-  }
+  parallel_items(nth, nth, worker);
   // combine the per-thread triangles
   std::vector<double> Rf((size_t)c * c, 0.0);
   {
@@ -619,38 +644,6 @@ int stencil_table(int d, int n, int b, int t, const std::vector<double>& g, int 
       T.C[(size_t)a * T.nG + c] = P.C[ie];
     }
   return 0;
-}
-
-// Runs f(i) for i = 0 .. count - 1 on up to nth host threads, the calling thread
-// included.  Items come from a shared counter, so when a thread cannot be started the
-// running ones take its share; the first exception an item throws is rethrown here
-// once every thread has joined.
-template <class F>
-static void parallel_items(int count, int nth, F f) {
-  std::atomic<int> next{0};
-  std::mutex mu;
-  std::exception_ptr err;
-  auto run = [&]() {
-    for (int i; (i = next.fetch_add(1)) < count;) {
-      try {
-        f(i);
-      } catch (...) {
-        std::lock_guard<std::mutex> lk(mu);
-        if (!err) err = std::current_exception();
-      }
-    }
-  };
-  std::vector<std::thread> th;
-  for (int k = 1; k < std::min(nth, count); ++k) {
-    try {
-      th.emplace_back(run);
-    } catch (const std::system_error&) {
-      break;
-    }
-  }
-  run();
-  for (auto& t : th) t.join();
-  if (err) std::rethrow_exception(err);
 }
 
 int stencil_tables(int d, int n, int b, double s, int route, int kind, int threads,
