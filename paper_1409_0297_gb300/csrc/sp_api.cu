@@ -466,7 +466,7 @@ const char* sp_status_str(sp_status st) {
     case SP_ERR_RESONANT: return "L - s is numerically singular (resonant shift)";
     case SP_ERR_SINGULAR: return "singular front pivot";
     case SP_ERR_NOCONV: return "GMRES did not reach the tolerance";
-    case SP_ERR_OOM: return "out of memory";
+    case SP_ERR_OOM: return "out of memory (device or host) or no host thread for the set-up";
     case SP_ERR_TIMEOUT: return "device wait timed out";
     case SP_ERR_CUDA: return "CUDA runtime error";
     case SP_ERR_STATE: return "call out of order";

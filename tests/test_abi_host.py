@@ -237,3 +237,16 @@ def test_host_allocation_failure_is_a_status():
                        timeout=120)
     assert p.returncode == 0, p.stderr[-2000:]
     assert p.stdout.strip() == "status 5 True", p.stdout + p.stderr[-2000:]
+
+
+def test_status_strings():
+    """Every status of the header has its own message; an unknown code is named so."""
+    B = _binding()
+    codes = [B.SP_OK, B.SP_ERR_ARG, B.SP_ERR_RESONANT, B.SP_ERR_SINGULAR, B.SP_ERR_NOCONV,
+             B.SP_ERR_OOM, B.SP_ERR_TIMEOUT, B.SP_ERR_CUDA, B.SP_ERR_STATE]
+    assert codes == list(range(9))
+    msgs = [B.status_str(c) for c in codes]
+    assert len(set(msgs)) == len(msgs) and all(msgs)
+    assert B.status_str(99) == "unknown status"
+    e = B.SpError(B.SP_ERR_ARG, "sp_setup")
+    assert "sp_setup" in str(e) and msgs[1] in str(e) and e.status == B.SP_ERR_ARG
