@@ -442,6 +442,7 @@ class Solver:
         o.device_loop = device_loop
         o.factor_storage = factor_storage
         self.d, self.n, self.b, self.s, self.prec = d, n, b, s, prec
+        self.device = device
         self.N = n ** d
         import numpy as np
         if np.ndim(s) == 0:  # one shift (any real scalar); a sequence makes a group
@@ -456,8 +457,9 @@ class Solver:
     def _vec(self, x, dtype):
         import torch
         if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == dtype and
-                x.is_contiguous() and x.numel() == self.NP):
-            raise ValueError(f"expected a contiguous CUDA {dtype} tensor of {self.NP} entries")
+                x.is_contiguous() and x.numel() == self.NP and x.get_device() == self.device):
+            raise ValueError(f"expected a contiguous {dtype} tensor of {self.NP} entries on "
+                             f"cuda:{self.device}")
         return x.data_ptr()
 
     def solve_many(self, F, U, **kw):
@@ -466,9 +468,10 @@ class Solver:
         nrhs = F.numel() // self.NP
         for x in (F, U):
             if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.complex128 and
-                    x.is_contiguous() and x.numel() == nrhs * self.NP and nrhs >= 1):
-                raise ValueError("expected contiguous CUDA complex128 tensors of nrhs x P x N "
-                                 "entries")
+                    x.is_contiguous() and x.numel() == nrhs * self.NP and nrhs >= 1 and
+                    x.get_device() == self.device):
+                raise ValueError("expected contiguous complex128 tensors of nrhs x P x N entries "
+                                 f"on cuda:{self.device}")
         return sp_solve_many(self.ctx, nrhs, F.data_ptr(), U.data_ptr(), nprob=self.P, **kw)
 
     def factor(self, q):

@@ -250,3 +250,33 @@ def test_status_strings():
     assert B.status_str(99) == "unknown status"
     e = B.SpError(B.SP_ERR_ARG, "sp_setup")
     assert "sp_setup" in str(e) and msgs[1] in str(e) and e.status == B.SP_ERR_ARG
+
+
+def test_solver_rejects_vectors_it_cannot_pass(monkeypatch):
+    """The binding only marshals: a vector of the wrong dtype, size, layout or device is
+    refused before any library call (here on host tensors, with the set-up and every
+    compute call replaced by recorders that must stay silent)."""
+    torch = pytest.importorskip("torch")
+    B = _binding()
+    calls = []
+    monkeypatch.setattr(B, "sp_setup", lambda *a: 1)
+    monkeypatch.setattr(B, "sp_destroy", lambda ctx: None)
+    for name in ("sp_factor", "sp_apply", "sp_solve", "sp_solve_many", "sp_green"):
+        monkeypatch.setattr(B, name, lambda *a, _n=name, **k: calls.append(_n))
+    S = B.Solver(2, 16, 4, 101.5)
+    N = 16 * 16
+    bad_vectors = [torch.zeros(N, dtype=torch.complex128),             # host memory
+                   torch.zeros(N, dtype=torch.complex64),              # wrong dtype
+                   torch.zeros(N - 1, dtype=torch.complex128),         # wrong size
+                   torch.zeros(2 * N, dtype=torch.complex128)[::2]]    # not contiguous
+    for x in bad_vectors:
+        with pytest.raises(ValueError):
+            S.apply(x, x)
+        with pytest.raises(ValueError):
+            S.solve(x, x)
+        with pytest.raises(ValueError):
+            S.solve_many(x, x)
+    with pytest.raises(ValueError):
+        S.factor(torch.zeros(N, dtype=torch.float64))
+    assert calls == []
+    S.close()
