@@ -210,10 +210,10 @@ def run_reference(args):
     prep = cpu_prep()
     for _ in range(args.warmup):
         cpu_sample(prep)
-    t0 = time.perf_counter()
+    t0, c0 = time.perf_counter(), time.process_time()
     for _ in range(max(1, args.steps)):
         it = cpu_sample(prep)
-    dt = time.perf_counter() - t0
+    dt, cpu_s = time.perf_counter() - t0, time.process_time() - c0
     steps = max(1, args.steps)
     res = {"value": steps / dt, "sample": cpu_sample_text(it, dt / steps)}
     line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT,
@@ -224,7 +224,8 @@ def run_reference(args):
             "config": {"workload": REF_SAMPLE, "same_as_gpu_arm": False,
                        "gpu_arm_workload": WORKLOAD},
             "cpu_baseline": {"value": res["value"], "unit": UNIT, "cores": cores,
-                             "kind": "oracle", "sample": res["sample"]},
+                             "cores_busy": round(cpu_s / dt, 2), "kind": "oracle",
+                             "sample": res["sample"]},
             "oracle_512_measured_once": ORACLE_512,
             "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -325,10 +326,11 @@ def cpu_baseline() -> dict:
     sample (imports, first factorisation)."""
     prep = cpu_prep()
     cpu_sample(prep)
-    t0 = time.perf_counter()
+    t0, c0 = time.perf_counter(), time.process_time()
     it = cpu_sample(prep)
-    dt = time.perf_counter() - t0
-    return {"value": 1.0 / dt, "sample": cpu_sample_text(it, dt), "seconds": dt}
+    dt, cpu_s = time.perf_counter() - t0, time.process_time() - c0
+    return {"value": 1.0 / dt, "sample": cpu_sample_text(it, dt), "seconds": dt,
+            "cores_busy": cpu_s / dt}
 
 
 # ------------------------------------------------------------------ tensor-core peak
@@ -1227,7 +1229,8 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = cpu_baseline()
-        cpu = {"value": r["value"], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+        cpu = {"value": r["value"], "unit": UNIT, "cores": os.cpu_count(),
+               "cores_busy": round(r["cores_busy"], 2), "kind": "oracle",
                "sample": r["sample"], "workload": REF_SAMPLE,
                "oracle_512_measured_once": ORACLE_512}
 
