@@ -722,15 +722,11 @@ static sp_status setup_impl(int d, int n, int b, int P, const double* shifts, sp
   SP_CK(cudaSetDevice(c->opts.device));
   // ---- host set-up: Green's kernel, stencil tables, symbolic structure
   try {
-    // tables of every problem, problem-major (problem p's type t at p 2^d + t)
-    c->tabs.resize((size_t)P << d);
-    for (int p = 0; p < P; ++p)
-      if (stencil_tables(d, n, b, shifts[p], c->opts.setup_route, c->opts.stencil,
-                         c->opts.host_threads, &c->tabs[(size_t)p << d]))
-        return SP_ERR_ARG;
-    // the symbolic structure depends on the sets only (the same for every problem)
-    std::vector<StencilTable> t0(c->tabs.begin(), c->tabs.begin() + (1 << d));
-    if (build_symbolic(d, n, b, t0, &c->sym)) return SP_ERR_ARG;
+    // tables of every problem, problem-major (problem p's type t at p 2^d + t), and
+    // the symbolic structure, which depends on the sets only (the same for every problem)
+    if (setup_host(d, n, b, P, shifts, c->opts.setup_route, c->opts.stencil,
+                   c->opts.host_threads, &c->tabs, &c->sym))
+      return SP_ERR_ARG;
   } catch (const std::exception&) {  // host memory, or the set-up's host threads
     return SP_ERR_OOM;
   }

@@ -912,4 +912,30 @@ int build_symbolic(int d, int n, int b, const std::vector<StencilTable>& tabs, S
   return 0;
 }
 
+int setup_host(int d, int n, int b, int P, const double* shifts, int route, int kind,
+               int threads, std::vector<StencilTable>* tabs, Symbolic* sym) {
+  // the symbolic structure reads the sets' geometry only, so it is built from
+  // geometry-only tables while the tables themselves are computed
+  std::vector<StencilTable> geo((size_t)1 << d);
+  for (int t = 0; t < (1 << d); ++t) {
+    StencilTable& T = geo[t];
+    T.t = t;
+    set_geometry(d, b, t, &T.S, &T.G, &T.Bt);
+    T.nS = (int)T.S.size() / d;
+    T.nG = (int)T.G.size() / d;
+    T.nB = (int)T.Bt.size() / d;
+  }
+  tabs->assign((size_t)P << d, StencilTable());
+  int rs = 0, rt = 0;
+  parallel_items(2, 2, [&](int i) {
+    if (i == 0) {
+      rs = build_symbolic(d, n, b, geo, sym);
+      return;
+    }
+    for (int p = 0; p < P && !rt; ++p)
+      rt = stencil_tables(d, n, b, shifts[p], route, kind, threads, tabs->data() + ((size_t)p << d));
+  });
+  return rt ? rt : rs;
+}
+
 }  // namespace sp

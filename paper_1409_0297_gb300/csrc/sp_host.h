@@ -64,6 +64,13 @@ int stencil_table(int d, int n, int b, int t, const std::vector<double>& g, int 
 int stencil_tables(int d, int n, int b, double s, int route, int kind, int threads,
                    StencilTable* out);
 
+// The host set-up of a context of P problems (shifts[0 .. P-1]): tabs gets the
+// 2^d tables of every problem, problem-major (problem p's type t at p 2^d + t), as
+// stencil_tables makes them; sym the nested-dissection structure, built from the
+// sets' geometry while the tables are computed.  0 on success.
+int setup_host(int d, int n, int b, int P, const double* shifts, int route, int kind,
+               int threads, std::vector<StencilTable>* tabs, Symbolic* sym);
+
 // Nested-dissection structure.
 int build_symbolic(int d, int n, int b, const std::vector<StencilTable>& tabs, Symbolic* out);
 
