@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <new>
 #include <vector>
 
@@ -960,12 +961,14 @@ long long sp_fno_param_count(const sp_fno_dims* dims) {
   return dims_ok(dims) ? count_params(dims) : 0;
 }
 
-sp_status sp_fno_create(const sp_fno_dims* dims, const float* params_host, void* stream,
-                        sp_fno** out) {
-  if (!out || !params_host || !dims_ok(dims)) return SP_ERR_ARG;
-  *out = nullptr;
-  sp_fno* f = new (std::nothrow) sp_fno;
-  if (!f) return SP_ERR_OOM;
+}  // extern "C"
+
+namespace {
+
+// Everything sp_fno_create does after allocating the handle: sizes, device buffers,
+// twiddles and the parameters.  On failure the caller deletes f, which frees every
+// device buffer recorded so far.
+sp_status fno_init(sp_fno* f, const sp_fno_dims* dims, const float* params_host, void* stream) {
   f->D = *dims;
   f->st = (cudaStream_t)stream;
   const sp_fno_dims& D = f->D;
@@ -988,10 +991,8 @@ sp_status sp_fno_create(const sp_fno_dims* dims, const float* params_host, void*
   const size_t es = D.act_fp32 ? sizeof(float) : sizeof(bf16);
   const size_t act = (size_t)B * W * f->P * es;
   cudaError_t e = cudaSuccess;
-  auto fail = [&](cudaError_t err) {
-    delete f;
-    return cuda_st(err);
-  };
+  f->allocs.reserve((size_t)3 * L + 32);  // every dalloc below records without reallocating
+  auto fail = [](cudaError_t err) { return cuda_st(err); };
   if ((e = dalloc(f, &f->w, f->np * sizeof(float))) || (e = dalloc(f, &f->m, f->np * sizeof(float))) ||
       (e = dalloc(f, &f->v, f->np * sizeof(float))) || (e = dalloc(f, &f->g, f->np * sizeof(float))) ||
       (e = dalloc(f, &f->wb, f->np * sizeof(bf16))) ||
@@ -1044,7 +1045,25 @@ sp_status sp_fno_create(const sp_fno_dims* dims, const float* params_host, void*
       (e = cudaMemcpyAsync(f->twb, twb.data(), twb.size() * sizeof(float2), cudaMemcpyHostToDevice, f->st)) ||
       (e = cudaStreamSynchronize(f->st)))
     return fail(e);
-  sp_status s = sp_fno_set_params(f, params_host);
+  return sp_fno_set_params(f, params_host);
+}
+
+}  // namespace
+
+extern "C" {
+
+sp_status sp_fno_create(const sp_fno_dims* dims, const float* params_host, void* stream,
+                        sp_fno** out) {
+  if (!out || !params_host || !dims_ok(dims)) return SP_ERR_ARG;
+  *out = nullptr;
+  sp_fno* f = new (std::nothrow) sp_fno;
+  if (!f) return SP_ERR_OOM;
+  sp_status s;
+  try {
+    s = fno_init(f, dims, params_host, stream);
+  } catch (const std::exception&) {  // host memory: no exception crosses the ABI
+    s = SP_ERR_OOM;
+  }
   if (s != SP_OK) {
     delete f;
     return s;
