@@ -1004,7 +1004,7 @@ sp_status sp_problems(const sp_ctx* c, int* P) {
   return SP_OK;
 }
 
-sp_status sp_factor(sp_ctx* c, const double* q_dev) {
+sp_status sp_factor(sp_ctx* c, const double* q_dev) try {
   if (!c || !q_dev) return SP_ERR_ARG;
   ProfGuard pg_(c);
   SP_CK(cudaSetDevice(c->opts.device));
@@ -1028,13 +1028,17 @@ sp_status sp_factor(sp_ctx* c, const double* q_dev) {
   if (hs) return SP_ERR_SINGULAR;
   c->factored = true;
   return SP_OK;
+} catch (const std::exception&) {  // host memory or threads: no exception crosses the ABI
+  return SP_ERR_OOM;
 }
 
-sp_status sp_factor_host(sp_ctx* c, const double* q_host) {
+sp_status sp_factor_host(sp_ctx* c, const double* q_host) try {
   if (!c || !q_host) return SP_ERR_ARG;
   SP_CK(cudaSetDevice(c->opts.device));
   SP_CK(cudaMemcpyAsync(c->qbuf, q_host, sizeof(double) * c->NP, cudaMemcpyHostToDevice, c->stream));
   return sp_factor(c, c->qbuf);
+} catch (const std::exception&) {  // host memory or threads: no exception crosses the ABI
+  return SP_ERR_OOM;
 }
 
 sp_status sp_apply(sp_ctx* c, const void* r_dev, void* z_dev) {
@@ -1588,7 +1592,7 @@ sp_status sp_solve_host(sp_ctx* c, const void* f_host, void* u_host, sp_info* in
 
 sp_status sp_schur_update(sp_precision prec, int M, int N, int K, const void* A, int lda,
                           long long sA, const void* B, int ldb, long long sB, void* C, int ldc,
-                          long long sC, int batch, void* stream) {
+                          long long sC, int batch, void* stream) try {
   if (prec != SP_PREC_FP64 && prec != SP_PREC_FP32 && prec != SP_PREC_TF32 &&
       prec != SP_PREC_TF32X3)
     return SP_ERR_ARG;
@@ -1622,9 +1626,11 @@ sp_status sp_schur_update(sp_precision prec, int M, int N, int K, const void* A,
   if (pb) cudaFree(pb);
   if (status) cudaFree(status);
   return rs;
+} catch (const std::exception&) {  // host memory or threads: no exception crosses the ABI
+  return SP_ERR_OOM;
 }
 
-sp_status sp_tc_probe(int split, int M, int N, int K, int reps, void* stream, double* ms_per_launch) {
+sp_status sp_tc_probe(int split, int M, int N, int K, int reps, void* stream, double* ms_per_launch) try {
   if ((split != 0 && split != 1) || !ms_per_launch || reps < 1 || reps > 1000) return SP_ERR_ARG;
   if (M < 128 || N < 256 || K < 32 || M % 128 || N % 256 || K % 32 || M > 16384 || N > 16384 ||
       K > kTcMaxKProbe)
@@ -1636,6 +1642,8 @@ sp_status sp_tc_probe(int split, int M, int N, int K, int reps, void* stream, do
   if (rs == SP_OK && (hs & 2)) rs = SP_ERR_TIMEOUT;
   *ms_per_launch = ms;
   return rs;
+} catch (const std::exception&) {  // host memory or threads: no exception crosses the ABI
+  return SP_ERR_OOM;
 }
 
 sp_status sp_tuning(const sp_ctx* c, int level, int* gemm_tile, int* gen_tile) {
