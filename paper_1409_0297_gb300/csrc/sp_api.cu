@@ -504,8 +504,8 @@ sp_status sp_stencil_table(int d, int n, int b, double s, int t, int route, int 
   if (!Q_out && !C_out && !sigma_out && !rank) return SP_OK;
   if (shift_gap(d, n, s) < 1e-6) return SP_ERR_RESONANT;
   try {
-    std::vector<double> g = green_kernel(d, n, s), g2;
-    if (route == 1) g2 = green_kernel_sq(d, n, s);
+    std::vector<double> g = green_kernel(d, n, s, host_threads), g2;
+    if (route == 1) g2 = green_kernel_sq(d, n, s, host_threads);
     StencilTable tb;
     if (stencil_table(d, n, b, t, g, host_threads, &tb, route == 1 ? &g2 : nullptr, kind))
       return SP_ERR_ARG;

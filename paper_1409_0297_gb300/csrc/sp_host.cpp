@@ -121,13 +121,13 @@ static void fft_line(cd* x, const FftPlan& P, int q, cd* scratch) {
 }
 
 // Transform of the n^d array a along every axis; the lines of an axis are
-// independent and split over host threads.
-static void fft_nd(std::vector<cd>& a, int d, int n, int sign) {
+// independent and split over up to `threads` host threads (0 = all).
+static void fft_nd(std::vector<cd>& a, int d, int n, int sign, int threads) {
   size_t N = 1;
   for (int i = 0; i < d; ++i) N *= n;
   const FftPlan P = fft_plan(n, sign);
   const size_t lines = N / n;
-  int nth = (int)std::max(1u, std::thread::hardware_concurrency());
+  int nth = threads > 0 ? threads : (int)std::max(1u, std::thread::hardware_concurrency());
   nth = (int)std::min<size_t>({(size_t)nth, (size_t)64, lines});
   size_t S = 1;
   for (int ax = 0; ax < d; ++ax) {
@@ -148,7 +148,7 @@ static void fft_nd(std::vector<cd>& a, int d, int n, int sign) {
 
 static inline int kfreq(int i, int n) { return i < n / 2 ? i : i - n; }
 
-std::vector<double> green_kernel(int d, int n, double s) {
+std::vector<double> green_kernel(int d, int n, double s, int threads) {
   size_t N = 1;
   for (int i = 0; i < d; ++i) N *= n;
   std::vector<cd> a(N);
@@ -162,13 +162,13 @@ std::vector<double> green_kernel(int d, int n, double s) {
     }
     a[j] = 1.0 / (4.0 * kPi * kPi * k2 - s);
   }
-  fft_nd(a, d, n, +1);
+  fft_nd(a, d, n, +1, threads);
   std::vector<double> g(N);
   for (size_t j = 0; j < N; ++j) g[j] = a[j].real() / (double)N;
   return g;
 }
 
-std::vector<double> green_kernel_sq(int d, int n, double s) {
+std::vector<double> green_kernel_sq(int d, int n, double s, int threads) {
   size_t N = 1;
   for (int i = 0; i < d; ++i) N *= n;
   std::vector<cd> a(N);
@@ -183,7 +183,7 @@ std::vector<double> green_kernel_sq(int d, int n, double s) {
     const double dk = 1.0 / (4.0 * kPi * kPi * k2 - s);
     a[j] = dk * dk;
   }
-  fft_nd(a, d, n, +1);
+  fft_nd(a, d, n, +1, threads);
   std::vector<double> g(N);
   for (size_t j = 0; j < N; ++j) g[j] = a[j].real() / (double)N;
   return g;
@@ -648,15 +648,15 @@ int stencil_table(int d, int n, int b, int t, const std::vector<double>& g, int 
 
 int stencil_tables(int d, int n, int b, double s, int route, int kind, int threads,
                    StencilTable* out) {
+  const int hw = threads > 0 ? threads : (int)std::max(1u, std::thread::hardware_concurrency());
   std::vector<double> g, g2;
-  parallel_items(route == 1 ? 2 : 1, 2, [&](int i) {
+  parallel_items(route == 1 ? 2 : 1, std::min(2, hw), [&](int i) {
     if (i == 0)
-      g = green_kernel(d, n, s);
+      g = green_kernel(d, n, s, threads);
     else
-      g2 = green_kernel_sq(d, n, s);
+      g2 = green_kernel_sq(d, n, s, threads);
   });
   const int nt = 1 << d;
-  const int hw = threads > 0 ? threads : (int)std::max(1u, std::thread::hardware_concurrency());
   // the Gram route computes a table on one thread, so the types run side by side; the
   // TSQR route spreads each table's row blocks over the threads, one type at a time
   std::vector<int> rc(nt, 0);
@@ -926,8 +926,9 @@ int setup_host(int d, int n, int b, int P, const double* shifts, int route, int 
     T.nB = (int)T.Bt.size() / d;
   }
   tabs->assign((size_t)P << d, StencilTable());
+  const int hw = threads > 0 ? threads : (int)std::max(1u, std::thread::hardware_concurrency());
   int rs = 0, rt = 0;
-  parallel_items(2, 2, [&](int i) {
+  parallel_items(2, std::min(2, hw), [&](int i) {
     if (i == 0) {
       rs = build_symbolic(d, n, b, geo, sym);
       return;

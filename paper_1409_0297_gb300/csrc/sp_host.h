@@ -41,10 +41,11 @@ struct Symbolic {
 };
 
 // g = inverse DFT of 1/(4 pi^2 |k|^2 - s) with the 1/N of the unitary pair (Eq. G):
-// G(i, j) = g[(i - j) mod n].  Flat, axis 0 fastest.
-std::vector<double> green_kernel(int d, int n, double s);
+// G(i, j) = g[(i - j) mod n].  Flat, axis 0 fastest.  The host FFT runs on up to
+// `threads` host threads (0 = all); the result does not depend on the count.
+std::vector<double> green_kernel(int d, int n, double s, int threads = 0);
 // the same for G^2: inverse DFT of 1/(4 pi^2 |k|^2 - s)^2 with the 1/N
-std::vector<double> green_kernel_sq(int d, int n, double s);
+std::vector<double> green_kernel_sq(int d, int n, double s, int threads = 0);
 
 // min_k |kappa - |k|^2| / max(1, kappa), kappa = s / (4 pi^2).
 double resonance_gap(int d, int n, double s);
