@@ -79,3 +79,20 @@ def test_reference_arm_json_contract(tmp_path):
     p1 = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference"],
                         capture_output=True, text=True, cwd=root, env=env1, timeout=120)
     assert p1.returncode == 0 and not [l for l in p1.stdout.splitlines() if l.startswith("{")]
+
+
+def test_recorded_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
+    """A DRAM traffic figure taken once under ncu is reported only while the kernel it
+    was measured on is unchanged: the bench hashes the kernel's source text and drops
+    the figure (null) when the hash differs or the class has no record."""
+    import bench
+    k = "lu_gemm"
+    rec = bench.TRAFFIC[k]
+    assert bench.recorded_traffic(k) == rec["bytes_per_launch"]
+    assert bench.recorded_traffic("no_such_class") is None
+    src = open(os.path.join(bench.ROOT, rec["source"])).read()
+    marker_line = next(ln for ln in src.split("\n") if rec["kernel"] in ln and "__global__" in ln)
+    changed = src.replace(marker_line, marker_line + "  // edited", 1)
+    (tmp_path / "src.cu").write_text(changed)
+    monkeypatch.setitem(bench.TRAFFIC, k, dict(rec, source=str(tmp_path / "src.cu")))
+    assert bench.recorded_traffic(k) is None
