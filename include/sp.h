@@ -78,7 +78,10 @@ typedef struct {
   double tol;        /* target relative residual ||g - A u|| / ||g|| (default 1e-8; > 0) */
   double pivot_tol;  /* singular-front threshold, relative to max|front| (default 1e-14) */
   int device;        /* CUDA device ordinal the context lives on (default 0) */
-  int host_threads;  /* threads for the host set-up (0 = all hardware threads) */
+  int host_threads;  /* threads for the host set-up (0 = all hardware threads): the
+                        host FFT's lines, the TSQR route's row blocks, the Gram
+                        route's stencil types side by side; the tables and the
+                        symbolic structure do not depend on the count */
   double inner_tol;  /* SP_PREC_MIXED: relative tolerance of each inner solve (default 1e-5) */
   int autotune;      /* 1: sp_setup times the factorisation's launch-shape candidates
                         of every level (Schur-update and block-inverse GEMM tiles,
