@@ -80,8 +80,10 @@ typedef struct {
   int device;        /* CUDA device ordinal the context lives on (default 0) */
   int host_threads;  /* threads for the host set-up (0 = all hardware threads): the
                         host FFT's lines, the TSQR route's row blocks, the Gram
-                        route's stencil types side by side; the tables and the
-                        symbolic structure do not depend on the count */
+                        route's stencil types side by side.  The Gram route's tables
+                        and the symbolic structure do not depend on the count; the
+                        TSQR route combines one triangle per thread, so its tables
+                        change with the count in the last bits (~1e-13 relative) */
   double inner_tol;  /* SP_PREC_MIXED: relative tolerance of each inner solve (default 1e-5) */
   int autotune;      /* 1: sp_setup times the factorisation's launch-shape candidates
                         of every level (Schur-update and block-inverse GEMM tiles,

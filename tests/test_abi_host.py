@@ -280,3 +280,20 @@ def test_solver_rejects_vectors_it_cannot_pass(monkeypatch):
         S.factor(torch.zeros(N, dtype=torch.float64))
     assert calls == []
     S.close()
+
+
+@pytest.mark.parametrize("d,n,b", [(2, 64, 4), (3, 16, 4)])
+def test_tables_and_host_thread_count(d, n, b):
+    """The Gram route computes each table on one thread, so its tables are the same
+    bit for bit whatever sp_opts.host_threads is; the TSQR route combines one R factor
+    per thread, so its tables agree across thread counts to rounding only."""
+    B = _binding()
+    s = 4 * np.pi ** 2 * (n / 8) ** 2 * 1.0137 if d == 2 else 4 * np.pi ** 2 * 7.3
+    for t in range(1 << d):
+        gram = [B.sp_stencil_table(d, n, b, s, t, host_threads=k, route=1) for k in (1, 3, 0)]
+        for g in gram[1:]:
+            assert np.array_equal(g[0], gram[0][0]) and np.array_equal(g[1], gram[0][1])
+        tsqr = [B.sp_stencil_table(d, n, b, s, t, host_threads=k, route=0) for k in (1, 3, 0)]
+        for q in tsqr[1:]:
+            assert np.abs(q[0] - tsqr[0][0]).max() <= 1e-11 * max(1.0, np.abs(tsqr[0][0]).max())
+            assert q[2] == tsqr[0][2]  # the same numerical rank
