@@ -108,7 +108,8 @@ def test_option_ranges_checked_before_the_device(field, value):
     assert e.value.status == B.SP_ERR_ARG
 
 
-@pytest.mark.parametrize("d,n,b", [(2, 64, 4), (2, 24, 3), (3, 8, 2), (3, 16, 4)])
+@pytest.mark.parametrize("d,n,b", [(2, 64, 4), (2, 24, 3), (3, 8, 2), (3, 16, 4),
+                                   (2, 40, 5), (2, 56, 7), (3, 10, 5)])
 def test_host_tables_match_oracle(d, n, b):
     B = _binding()
     s = 4 * np.pi ** 2 * (n / 6) ** 2 * 1.013

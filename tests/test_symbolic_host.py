@@ -25,7 +25,9 @@ def _B():
     return B
 
 
-CASES = [(2, 16, 4), (2, 32, 4), (2, 16, 2), (2, 24, 3), (3, 8, 2), (3, 16, 4)]
+CASES = [(2, 16, 4), (2, 32, 4), (2, 16, 2), (2, 24, 3), (3, 8, 2), (3, 16, 4),
+         # odd and even leaf sizes other than powers of two, deeper trees
+         (2, 20, 5), (2, 56, 7), (2, 48, 6), (2, 40, 5), (3, 10, 5), (3, 12, 3)]
 
 
 @pytest.mark.parametrize("d,n,b", CASES)
