@@ -11,7 +11,8 @@ import pytest
 import oracle as O
 
 EPS = np.finfo(float).eps
-CASES = [(2, 16, 2, 1.37), (2, 32, 4, 3.3), (2, 64, 8, 7.7), (3, 8, 2, 1.37), (2, 48, 3, 5.5)]
+CASES = [(2, 16, 2, 1.37), (2, 32, 4, 3.3), (2, 64, 8, 7.7), (3, 8, 2, 1.37), (2, 48, 3, 5.5),
+         (2, 40, 5, 4.1), (3, 12, 3, 2.2)]  # |beta| <= 64: every singular value returned
 
 
 def _B():

@@ -10,7 +10,7 @@ import pytest
 
 import oracle as O
 
-CASES = [(2, 16, 2, 1.37), (2, 32, 4, 3.3), (3, 8, 2, 1.37)]
+CASES = [(2, 16, 2, 1.37), (2, 32, 4, 3.3), (3, 8, 2, 1.37), (2, 40, 5, 4.1), (3, 12, 3, 2.2)]
 
 
 def _B():
