@@ -14,7 +14,8 @@
  * Conventions for every call below.
  *  - Grid: n points per axis, N = n^d unknowns, flat index j0 + n*j1 (+ n^2*j2)
  *    (axis 0 fastest).  The leaf box size b must divide n with n/b = 2^L, L >= 1,
- *    and b >= 2.
+ *    and b >= 2, and N < 2^31 (grid indices are 32-bit): every call that takes
+ *    (d, n, b) returns SP_ERR_ARG otherwise.
  *  - Vectors (r, z, f, u, g, x, w, y) are complex128: N pairs (re, im) of
  *    double, interleaved, 16-byte aligned.  q is N real doubles.  Pointers named
  *    *_dev are CUDA device pointers on the context's device; *_host are host

@@ -21,6 +21,13 @@ static const double kPi = 3.141592653589793238462643383279502884;
 int check_grid(int d, int n, int b, int* L) {
   if (d != 2 && d != 3) return 1;
   if (b < 2 || n < 2 * b || n % b) return 1;
+  {  // grid indices are ints: n^d must stay below 2^31
+    long long N = 1;
+    for (int a = 0; a < d; ++a) {
+      if (N > 2147483647LL / n) return 1;
+      N *= n;
+    }
+  }
   int r = n / b, l = 0;
   while (r > 1) {
     if (r & 1) return 1;

@@ -79,6 +79,8 @@ int build_symbolic(int d, int n, int b, const std::vector<StencilTable>& tabs, S
 int front_sizes(int d, int n, int b, std::vector<int>* nf, std::vector<int>* k,
                 std::vector<int>* m);
 
+// 0 if d is 2 or 3, b >= 2 divides n, n / b = 2^L with L >= 1 (stored in *L) and
+// n^d < 2^31 (grid indices are ints); 1 otherwise.
 int check_grid(int d, int n, int b, int* L);
 
 }  // namespace sp

@@ -298,3 +298,26 @@ def test_tables_and_host_thread_count(d, n, b):
         for q in tsqr[1:]:
             assert np.abs(q[0] - tsqr[0][0]).max() <= 1e-11 * max(1.0, np.abs(tsqr[0][0]).max())
             assert q[2] == tsqr[0][2]  # the same numerical rank
+
+
+def test_grid_size_limit():
+    """Grid indices are 32-bit, so every call that takes (d, n, b) refuses n^d >= 2^31
+    with SP_ERR_ARG instead of overflowing; just below the limit the level sizes still
+    follow the closed forms (Section 2.3, Fig. nd), computed here in exact integers."""
+    B = _binding()
+    for d, n, b in [(2, 65536, 16), (3, 2048, 16), (3, 1 << 20, 2)]:
+        with pytest.raises(B.SpError) as e:
+            B.sp_front_sizes(d, n, b)
+        assert e.value.status == B.SP_ERR_ARG
+        with pytest.raises(B.SpError):
+            B.sp_level_info(d, n, b, 0)
+    for d, n, b in [(3, 1024, 16), (2, 32768, 16)]:
+        lv = B.sp_front_sizes(d, n, b)
+        L = len(lv) - 1
+        assert 2 ** L * b == n
+        for l, (nf, k, m) in enumerate(lv[:-1]):
+            Bx = b << l
+            kk = (Bx - 1) ** d - (0 if l == 0 else 2 ** d * (Bx // 2 - 1) ** d)
+            assert (nf, k, m) == ((n // Bx) ** d, kk, kk + (Bx + 1) ** d - (Bx - 1) ** d)
+        kr = n ** d - 2 ** d * (n // 2 - 1) ** d
+        assert lv[-1] == (1, kr, kr)
