@@ -353,7 +353,9 @@ sp_status sp_costs(const sp_ctx *ctx, double *factor_entries, double *factor_flo
  * Helmholtz: s = mean(omega^2 / c^2), q = s - omega^2 / c^2.
  * Schroedinger (rescaled, Eq. schr): s = mean(l^2 E - l^2 V), q = l^2 V - l^2 E + s;
  * the caller multiplies f by l^2.  If L - s is numerically singular (see
- * sp_setup) s is raised by 1e-3 * 4 pi^2 until it is not; q follows s. */
+ * sp_setup) s is raised by 1e-3 * 4 pi^2 until it is not; q follows s.
+ * SP_ERR_ARG for a zero or non-finite c, a non-finite V, omega, l or E (nothing
+ * is written then). */
 sp_status sp_medium_helmholtz(int d, int n, double omega, const double *c_host, double *s_out,
                               double *q_host);
 sp_status sp_medium_schrodinger(int d, int n, double ell, double E, const double *V_host,

@@ -580,12 +580,13 @@ sp_status sp_level_info(int d, int n, int b, int level, int* nf, int* k, int* m,
 
 sp_status sp_medium_helmholtz(int d, int n, double omega, const double* c_host, double* s_out,
                               double* q_host) {
-  if ((d != 2 && d != 3) || n < 2 || !c_host || !s_out || !q_host) return SP_ERR_ARG;
+  if ((d != 2 && d != 3) || n < 2 || !c_host || !s_out || !q_host || !std::isfinite(omega))
+    return SP_ERR_ARG;
   long N = 1;
   for (int a = 0; a < d; ++a) N *= n;
   double sum = 0;
   for (long j = 0; j < N; ++j) {
-    if (!(c_host[j] != 0.0)) return SP_ERR_ARG;
+    if (!(std::isfinite(c_host[j]) && c_host[j] != 0.0)) return SP_ERR_ARG;
     sum += omega * omega / (c_host[j] * c_host[j]);
   }
   double s = perturb_shift(d, n, sum / (double)N);
@@ -596,12 +597,17 @@ sp_status sp_medium_helmholtz(int d, int n, double omega, const double* c_host, 
 
 sp_status sp_medium_schrodinger(int d, int n, double ell, double E, const double* V_host,
                                 double* s_out, double* q_host) {
-  if ((d != 2 && d != 3) || n < 2 || !V_host || !s_out || !q_host) return SP_ERR_ARG;
+  if ((d != 2 && d != 3) || n < 2 || !V_host || !s_out || !q_host || !std::isfinite(ell) ||
+      !std::isfinite(E))
+    return SP_ERR_ARG;
   long N = 1;
   for (int a = 0; a < d; ++a) N *= n;
   const double l2 = ell * ell;
   double sum = 0;
-  for (long j = 0; j < N; ++j) sum += -(l2 * V_host[j] - l2 * E);
+  for (long j = 0; j < N; ++j) {
+    if (!std::isfinite(V_host[j])) return SP_ERR_ARG;
+    sum += -(l2 * V_host[j] - l2 * E);
+  }
   double s = perturb_shift(d, n, sum / (double)N);
   for (long j = 0; j < N; ++j) q_host[j] = (l2 * V_host[j] - l2 * E) + s;
   *s_out = s;
@@ -610,10 +616,14 @@ sp_status sp_medium_schrodinger(int d, int n, double ell, double E, const double
 
 sp_status sp_medium_schrodinger_at(int d, int n, double ell, double E, const double* V_host,
                                    double s, double* q_host) {
-  if ((d != 2 && d != 3) || n < 2 || !V_host || !q_host) return SP_ERR_ARG;
+  if ((d != 2 && d != 3) || n < 2 || !V_host || !q_host || !std::isfinite(ell) ||
+      !std::isfinite(E) || !std::isfinite(s))
+    return SP_ERR_ARG;
   long N = 1;
   for (int a = 0; a < d; ++a) N *= n;
   const double l2 = ell * ell;
+  for (long j = 0; j < N; ++j)
+    if (!std::isfinite(V_host[j])) return SP_ERR_ARG;
   for (long j = 0; j < N; ++j) q_host[j] = (l2 * V_host[j] - l2 * E) + s;
   return SP_OK;
 }

@@ -321,3 +321,34 @@ def test_grid_size_limit():
             assert (nf, k, m) == ((n // Bx) ** d, kk, kk + (Bx + 1) ** d - (Bx - 1) ** d)
         kr = n ** d - 2 ** d * (n // 2 - 1) ** d
         assert lv[-1] == (1, kr, kr)
+
+
+def test_medium_helpers_refuse_non_finite_media():
+    """The Section 2.1 splits refuse media that have no meaning (a zero or non-finite
+    wave speed, a non-finite potential or parameter) with SP_ERR_ARG and leave q
+    untouched, instead of handing NaN or infinity to the factorisation."""
+    B = _binding()
+    n = 16
+    c = np.ones(n * n)
+    V = np.zeros(n * n)
+    for bad in (0.0, np.nan, np.inf):
+        cb = c.copy()
+        cb[37] = bad
+        with pytest.raises(B.SpError) as e:
+            B.sp_medium_helmholtz(2, n, 2 * np.pi * 2, cb)
+        assert e.value.status == B.SP_ERR_ARG
+    for bad in (np.nan, -np.inf):
+        Vb = V.copy()
+        Vb[5] = bad
+        with pytest.raises(B.SpError):
+            B.sp_medium_schrodinger(2, n, 4.0, 10.0, Vb)
+        with pytest.raises(B.SpError):
+            B.sp_medium_schrodinger_at(2, n, 4.0, 10.0, Vb, 100.0)
+    with pytest.raises(B.SpError):
+        B.sp_medium_helmholtz(2, n, np.nan, c)
+    with pytest.raises(B.SpError):
+        B.sp_medium_schrodinger(2, n, 4.0, np.inf, V)
+    with pytest.raises(B.SpError):
+        B.sp_medium_schrodinger_at(2, n, 4.0, 10.0, V, np.nan)
+    s, q = B.sp_medium_helmholtz(2, n, 2 * np.pi * 2, c)  # the finite case still splits
+    assert np.all(np.isfinite(q)) and np.isfinite(s)
