@@ -489,7 +489,8 @@ sp_status sp_front_sizes(int d, int n, int b, int cap, int* nlevels, int* nfront
 sp_status sp_stencil_table(int d, int n, int b, double s, int t, int route, int kind,
                            int host_threads, double* Q_out, double* C_out, int* rows, int* cols,
                            int* rank, double* sigma_out) {
-  if ((route != 0 && route != 1) || (kind != 0 && kind != 1)) return SP_ERR_ARG;
+  if ((route != 0 && route != 1) || (kind != 0 && kind != 1) || !std::isfinite(s))
+    return SP_ERR_ARG;
   int L;
   if (check_grid(d, n, b, &L) || t < 0 || t >= (1 << d)) return SP_ERR_ARG;
   if (!rows || !cols) return SP_ERR_ARG;

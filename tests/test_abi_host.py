@@ -350,5 +350,9 @@ def test_medium_helpers_refuse_non_finite_media():
         B.sp_medium_schrodinger(2, n, 4.0, np.inf, V)
     with pytest.raises(B.SpError):
         B.sp_medium_schrodinger_at(2, n, 4.0, 10.0, V, np.nan)
+    for s_bad in (np.nan, np.inf):  # the host tables refuse a non-finite shift too
+        with pytest.raises(B.SpError) as e:
+            B.sp_stencil_table(2, n, 4, s_bad, 0)
+        assert e.value.status == B.SP_ERR_ARG
     s, q = B.sp_medium_helmholtz(2, n, 2 * np.pi * 2, c)  # the finite case still splits
     assert np.all(np.isfinite(q)) and np.isfinite(s)
