@@ -320,7 +320,9 @@ sp_status sp_set_table(sp_ctx *ctx, int t, const double *Q_host, const double *C
  * kind 0 (set stencils) or 1 (per-point stencils, see sp_opts.stencil).  Pass
  * Q_out = C_out = NULL to query *rows / *cols first.  sigma_out (may be NULL)
  * receives min(|beta|, 64) leading singular values of G(beta, gamma^c) in
- * descending order (route 1: square roots of the eigenvalues of B B^T). */
+ * descending order (route 1: square roots of the eigenvalues of B B^T).
+ * SP_ERR_ARG for a bad grid, type, route or kind or a non-finite s,
+ * SP_ERR_RESONANT when L - s is numerically singular. */
 sp_status sp_stencil_table(int d, int n, int b, double s, int t, int route, int kind,
                            int host_threads, double *Q_out, double *C_out, int *rows, int *cols,
                            int *rank, double *sigma_out);
