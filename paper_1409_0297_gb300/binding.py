@@ -189,8 +189,20 @@ def sp_factor(ctx: int, q_dev: int) -> None:
     _check(LIB.sp_factor(ctx, q_dev), "sp_factor")
 
 
+def _host_array(a, dtype, name: str, writeable: bool = False) -> int:
+    """Address of a C-contiguous numpy array of the given dtype (the library reads or
+    writes it as plain memory, so anything else is refused here)."""
+    import numpy as np
+    if not (isinstance(a, np.ndarray) and a.dtype == np.dtype(dtype) and a.flags["C_CONTIGUOUS"]
+            and (a.flags["WRITEABLE"] or not writeable)):
+        raise ValueError(f"{name}: expected a C-contiguous{' writeable' if writeable else ''} "
+                         f"numpy {np.dtype(dtype)} array")
+    return a.ctypes.data
+
+
 def sp_factor_host(ctx: int, q_host) -> None:
-    _check(LIB.sp_factor_host(ctx, q_host.ctypes.data), "sp_factor_host")
+    import numpy as np
+    _check(LIB.sp_factor_host(ctx, _host_array(q_host, np.float64, "q_host")), "sp_factor_host")
 
 
 def sp_apply(ctx: int, r_dev: int, z_dev: int) -> None:
@@ -265,8 +277,13 @@ def sp_solve_many(ctx: int, nrhs: int, F_dev: int, U_dev: int, hist_cap: int = 1
 
 def sp_solve_host(ctx: int, f_host, u_host, hist_cap: int = 1024, allow_noconv=False,
                   nprob: int = 1):
+    import numpy as np
+    pf = _host_array(f_host, np.complex128, "f_host")
+    pu = _host_array(u_host, np.complex128, "u_host", writeable=True)
+    if f_host.size != u_host.size:
+        raise ValueError("f_host and u_host must have the same number of entries")
     infos, hists = _infos(nprob, hist_cap)
-    st = LIB.sp_solve_host(ctx, f_host.ctypes.data, u_host.ctypes.data, infos)
+    st = LIB.sp_solve_host(ctx, pf, pu, infos)
     _check(st, "sp_solve_host", (SP_OK, SP_ERR_NOCONV) if allow_noconv else (SP_OK,))
     out = [_info_dict(infos[i], hists[i], st) for i in range(nprob)]
     return out[0] if nprob == 1 else out

@@ -356,3 +356,36 @@ def test_medium_helpers_refuse_non_finite_media():
         assert e.value.status == B.SP_ERR_ARG
     s, q = B.sp_medium_helmholtz(2, n, 2 * np.pi * 2, c)  # the finite case still splits
     assert np.all(np.isfinite(q)) and np.isfinite(s)
+
+
+def test_host_buffer_calls_refuse_foreign_arrays(monkeypatch):
+    """sp_factor_host / sp_solve_host hand the library plain host memory, so the binding
+    refuses arrays of another dtype, non-contiguous or read-only outputs and unequal
+    sizes before the library is called (the library entry points are replaced by
+    recorders that must stay silent)."""
+    B = _binding()
+    calls = []
+
+    class Lib:
+        def __getattr__(self, name):
+            return lambda *a: calls.append(name) or 0
+    monkeypatch.setattr(B, "LIB", Lib())
+    N = 64
+    with pytest.raises(ValueError):
+        B.sp_factor_host(1, np.zeros(N, dtype=np.float32))
+    with pytest.raises(ValueError):
+        B.sp_factor_host(1, np.zeros(2 * N)[::2])
+    with pytest.raises(ValueError):
+        B.sp_factor_host(1, list(range(N)))
+    f = np.zeros(N, dtype=np.complex128)
+    with pytest.raises(ValueError):
+        B.sp_solve_host(1, f.real.copy(), np.zeros(N, dtype=np.complex128))
+    ro = np.zeros(N, dtype=np.complex128)
+    ro.flags.writeable = False
+    with pytest.raises(ValueError):
+        B.sp_solve_host(1, f, ro)
+    with pytest.raises(ValueError):
+        B.sp_solve_host(1, f, np.zeros(N + 1, dtype=np.complex128))
+    assert calls == []
+    B.sp_factor_host(1, np.zeros(N))  # a valid array reaches the (recorded) library call
+    assert calls == ["sp_factor_host"]
